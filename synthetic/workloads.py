@@ -1,0 +1,76 @@
+"""Named synthetic workloads shaped like the paper's melt-pool problems.
+
+Material constants are the Ti-6Al-4V table of Section 4.3 (Table tab:param_ti64); the
+domain [-300, 300] um^3 and the laser absorptivity 0.35 follow Section 4.3.  The sizes
+and the coefficient recipes are the five benchmark workloads of this library.
+"""
+from dataclasses import dataclass, field, replace
+from typing import Tuple
+
+TI64 = dict(
+    rho_l=4087.0, rho_g=4.087,          # kg/m^3
+    mu_l=3.5e-3, mu_g=3.5e-5,           # kg/(m s)
+    cp_l=1130.0, cp_g=11.3,             # J/(kg K)
+    k_l=28.63, k_g=0.02863,             # W/(m K)
+    t_boil=3133.0,                      # K
+)
+
+
+@dataclass(frozen=True)
+class Workload:
+    name: str
+    kind: str                      # helmholtz | oseen | heat | heat_adjoint | reinit
+    n: int                         # cells per axis (uniform) or base cells per axis (octree)
+    lo: Tuple[float, float, float] = (0.0, 0.0, 0.0)
+    hi: Tuple[float, float, float] = (1.0, 1.0, 1.0)
+    degree: int = 2
+    levels: int = 0                # octree refinement levels
+    nrhs: int = 1
+    seed: int = 1
+    params: dict = field(default_factory=dict)
+
+    @property
+    def h(self):
+        return (self.hi[0] - self.lo[0]) / (self.n << self.levels)
+
+    @property
+    def eps(self):
+        """Interface thickness parameter eps = 2 h_finest (Section 3.1 choice eps = 2h)."""
+        return 2.0 * self.h
+
+
+HELMHOLTZ_SPHERE = Workload(
+    "helmholtz_sphere_q2_16", "helmholtz", 16,
+    params=dict(mass=1.0, a_gas=1.0, a_liquid=1000.0, sphere_radius=0.3, tol=1e-10))
+
+OSEEN_INTERFACE = Workload(
+    "oseen_q2q1_interface_64", "oseen", 64,
+    params=dict(rho_l=TI64["rho_l"], rho_g=TI64["rho_g"], mu_l=TI64["mu_l"], mu_g=TI64["mu_g"],
+                dt_cfl=0.5, restart=50, tol=1e-10, maxit=5000))
+
+_LASER = dict(power=200.0, radius=50e-6, x0=0.0, y0=0.0, absorptivity=0.35)
+
+HEAT_LASER = Workload(
+    "heat_laser_q2_128", "heat", 128, lo=(-3e-4, -3e-4, -3e-4), hi=(3e-4, 3e-4, 3e-4),
+    params=dict(rhocp=TI64["rho_l"] * TI64["cp_l"], k0=TI64["k_l"], t_boil=TI64["t_boil"],
+                dt=1e-5, t_ref=500.0, laser=_LASER, cheby_degree=4, tol=1e-10))
+
+HEAT_ADJOINT = Workload(
+    "heat_adjoint_q2_64", "heat_adjoint", 64, lo=(-3e-4, -3e-4, -3e-4), hi=(3e-4, 3e-4, 3e-4),
+    params=dict(rhocp=TI64["rho_l"] * TI64["cp_l"], k0=TI64["k_l"], t_boil=TI64["t_boil"],
+                dt=1e-5, t_ref=500.0, laser=_LASER, box_half=100e-6, box_depth=100e-6,
+                fd_step=1e-6, tol=1e-12))
+
+REINIT_OCTREE = Workload(
+    "reinit_octree_q2_32_l3", "reinit", 32, levels=3, nrhs=8,
+    params=dict(sphere_radius=0.3, amplitude=0.05, lmax=6, tol=1e-10))
+
+
+def scaled(wl, n, levels=None, nrhs=None):
+    """The same workload recipe on a smaller (or larger) mesh."""
+    kw = dict(n=n, name=f"{wl.name}@n{n}")
+    if levels is not None:
+        kw["levels"] = levels
+    if nrhs is not None:
+        kw["nrhs"] = nrhs
+    return replace(wl, **kw)
