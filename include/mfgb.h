@@ -1,0 +1,228 @@
+/*
+ * mfgb: matrix-free Q_k hexahedral finite element operators on one GB300 (sm_103a).
+ *
+ * C ABI of the library libmfgb.so.  The operators are the discrete forms of the
+ * anisothermal two-phase flow model of arXiv 2501.18781:
+ *   - Section 2.1, eq. (momentum_balance), (continuity): the linearised (Oseen)
+ *     Navier-Stokes operator with Q2 velocity and Q1 pressure (Appendix B: k_u = 2,
+ *     k_p = 1), density by eq. (rhoEff) and viscosity by eq. (muEff);
+ *   - eq. (heat_transfer): one implicit heat step (mass + convection + diffusion);
+ *   - Section 2.2: a variable-coefficient Helmholtz operator with a level-set
+ *     coefficient, and the diffusive part of conservative reinitialisation;
+ *   - eq. (laser_gauss): the Gaussian laser flux as a top-face load.
+ * Appendix B fixes the discretisation: continuous Lagrange Q_k elements on
+ * hexahedra, Gauss quadrature with (k+1)^3 points, adaptive refinement (hanging
+ * nodes), CG for symmetric and GMRES for nonsymmetric systems, matrix-free
+ * operator evaluation.
+ *
+ * Conventions shared by every call:
+ *   - Vectors are caller-owned DEVICE pointers unless a parameter says "host".
+ *     A vector of an operator is the concatenation of its fields' DoF blocks
+ *     (Oseen: u_x, u_y, u_z on the Q2 map, then p on the Q1 map).  For nrhs > 1
+ *     the right-hand sides are stored ld elements apart.
+ *   - DoFs are the free nodes of the lattice of spacing h_finest / k, numbered in
+ *     lexicographic (z, y, x) order of their integer lattice coordinates.
+ *   - Handles are library-owned; each *_destroy frees its handle (NULL is allowed).
+ *     A handle must outlive the handles created from it.
+ *   - Every call returns MF_OK or a negative status and never aborts, throws
+ *     across the ABI or traps the device; mf_last_error() describes the last
+ *     failure of the calling thread.  Work is enqueued on the context's stream;
+ *     calls documented as "synchronising" wait for it before returning.
+ */
+#ifndef MFGB_H
+#define MFGB_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int mf_status;
+#define MF_OK 0
+#define MF_EINVAL (-1)        /* bad argument, size or handle combination */
+#define MF_ENOMEM (-2)        /* a device or host allocation failed */
+#define MF_ECUDA (-3)         /* a CUDA runtime call failed */
+#define MF_ENOTCONV (-4)      /* a solver stopped at maxit above its tolerance */
+#define MF_ETIMEOUT (-5)      /* a device-side bounded wait ran out */
+#define MF_EUNSUPPORTED (-6)  /* valid request that this build does not implement */
+
+typedef enum { MF_F64 = 0, MF_F32 = 1, MF_F16 = 2, MF_BF16 = 3 } mf_dtype;
+
+typedef struct mf_ctx mf_ctx;
+typedef struct mf_mesh mf_mesh;
+typedef struct mf_dofmap mf_dofmap;
+typedef struct mf_op mf_op;
+
+/* Thread-local text of the last failure (owned by the library, valid until the next call). */
+const char* mf_last_error(void);
+
+/* Context on CUDA device `device`; `cuda_stream` is a cudaStream_t (NULL = a stream the
+ * library creates and owns).  The stream is borrowed: it must outlive the context. */
+mf_status mf_context_create(int device, void* cuda_stream, mf_ctx** out);
+void mf_context_destroy(mf_ctx* ctx);
+/* Replace the context's stream (borrowed). */
+mf_status mf_context_set_stream(mf_ctx* ctx, void* cuda_stream);
+
+/* Uniform mesh of n[0] x n[1] x n[2] cube cells filling the box [lo, hi] (host arrays).
+ * The cells must be cubes: (hi-lo)[d] / n[d] equal for d = 0, 1, 2 (else MF_EINVAL).
+ * ctx may be NULL: the mesh and the DoF maps built on it then live on the host only
+ * (for inspection through mf_dofmap_export; no operator can be built on them). */
+mf_status mf_mesh_uniform(mf_ctx* ctx, const int n[3], const double lo[3], const double hi[3],
+                          mf_mesh** out);
+
+/* Adaptively refined mesh (Appendix B: adaptive refinement near the interface) given
+ * by its leaves: host int32 rows (level, i, j, k), 0 <= level <= levels, 0 <= i,j,k <
+ * base * 2^level, on a base^3 root mesh of the cube [lo, hi].  The leaves must tile the
+ * box exactly once and be 2:1 balanced across faces, edges and corners (else MF_EINVAL).
+ * Leaves are ordered internally by the Morton code of their finest-level anchor
+ * (bit b of x, y, z in bits 3b, 3b+1, 3b+2). */
+mf_status mf_mesh_octree(mf_ctx* ctx, int base, int levels, const double lo[3], const double hi[3],
+                         const int32_t* leaves, int64_t nleaves, mf_mesh** out);
+void mf_mesh_destroy(mf_mesh* mesh);
+
+/* Continuous Q_degree DoF map (degree 1 or 2) with hanging-node constraints: a node on
+ * the closure of a leaf that is not a node of that leaf takes the value of the leaf's
+ * Q_k interpolant there; chains are resolved to free DoFs, equal masters summed and
+ * exact zeros dropped.  `dirichlet_faces` bits 0..5 = x-, x+, y-, y+, z-, z+ mark faces
+ * whose DoFs get identity rows and columns in every operator built on this map. */
+mf_status mf_dofmap_create(mf_mesh* mesh, int degree, uint32_t dirichlet_faces, mf_dofmap** out);
+void mf_dofmap_destroy(mf_dofmap* map);
+mf_status mf_dofmap_query(const mf_dofmap* map, int64_t* n_dofs, int64_t* n_cells,
+                          int64_t* n_constraints, int64_t* n_constraint_entries);
+/* Host copies (caller-allocated; any pointer may be NULL to skip that array):
+ *   cell_map[n_cells*(k+1)^3]  per cell (in the map's cell order) and local node
+ *                              (x fastest): the free DoF index, or -(1 + r) for the
+ *                              hanging node of rank r (hanging nodes in lattice order);
+ *   con_rowptr[n_constraints+1], con_cols[n_entries], con_w[n_entries]: CSR rows of the
+ *                              hanging nodes, masters ascending;
+ *   dof_coords[3*n_dofs]       physical coordinates, xyz per DoF;
+ *   dirichlet[n_dofs]          1 for Dirichlet DoFs. */
+mf_status mf_dofmap_export(const mf_dofmap* map, int32_t* cell_map, int64_t* con_rowptr,
+                           int32_t* con_cols, double* con_w, double* dof_coords, uint8_t* dirichlet);
+
+typedef enum {
+  MF_OP_HELMHOLTZ = 0, /* int c u v + a(phi) grad u . grad v,  a = eq. (muEff) with a_l, a_g */
+  MF_OP_HEAT = 1,      /* int rho_cp/dt u v + k grad u . grad v [+ rho_cp v beta . grad u];
+                          k = k0 (1 + 0.5 T/T_b) at T_h^n, or per Gauss point (MF_FIELD_K_QPOINT) */
+  MF_OP_OSEEN = 2,     /* [[sigma M_rho + C_rho(beta) + 2 mu eps:eps, B^T], [B, 0]], B = -div */
+  MF_OP_REINIT = 3     /* int u v / dtau + eps (n . grad u)(n . grad v), n = grad phi_h/|grad phi_h| */
+} mf_op_kind;
+
+typedef enum {
+  MF_HEAVISIDE_TANH = 0, /* H = clamp((1 + phi_h)/2, 0, 1): the Heaviside of phi = tanh(d / 2eps) */
+  MF_HEAVISIDE_SINE = 1  /* eq. (heaviside) with d = 2 eps atanh(phi_h) */
+} mf_heaviside;
+
+typedef enum {
+  MF_COEF_INKERNEL = 0,  /* coefficients re-evaluated from the nodal fields in every apply */
+  MF_COEF_QPOINT = 1     /* coefficients tabulated per Gauss point when fields are set */
+} mf_coef_mode;
+
+typedef struct {
+  int kind;        /* mf_op_kind */
+  int heaviside;   /* mf_heaviside */
+  int coef_mode;   /* mf_coef_mode (Oseen always tabulates) */
+  int reserved;
+  double eps;      /* interface thickness parameter (sine Heaviside, reinit) */
+  double mass_coef, a_liquid, a_gas;            /* Helmholtz */
+  double rhocp, dt, k0, t_boil;                 /* heat */
+  double sigma, rho_l, rho_g, mu_l, mu_g;       /* Oseen */
+  double dtau;                                  /* reinit */
+} mf_op_params;
+
+typedef enum {
+  MF_FIELD_PHI = 0,      /* nodal level set on map 0 (n_dofs values) */
+  MF_FIELD_T_PREV = 1,   /* nodal absolute temperature T^n on map 0 */
+  MF_FIELD_BETA = 2,     /* nodal convection field, 3 blocks of n_dofs (x, y, z) */
+  MF_FIELD_K_QPOINT = 3  /* conductivity per Gauss point, n_cells*27, cell-major, x fastest */
+} mf_field;
+
+/* Operator on `maps` (one map; Oseen: the Q2 velocity map then the Q1 pressure map on the
+ * same uniform mesh).  Parameters are copied. */
+mf_status mf_operator_create(mf_ctx* ctx, const mf_op_params* params, const mf_dofmap* const* maps,
+                             int nmaps, mf_op** out);
+void mf_operator_destroy(mf_op* op);
+/* Vector length of the operator (sum of its fields' DoFs). */
+mf_status mf_operator_size(const mf_op* op, int64_t* n);
+/* Borrow a device field (fp64, `n` values as documented per field); the pointer must stay
+ * valid while the operator is used.  With MF_COEF_QPOINT the Gauss-point table is rebuilt. */
+mf_status mf_operator_set_field(mf_op* op, int field, const void* dev_ptr, int dtype, int64_t n);
+
+/* dst = A src for nrhs vectors stored ld apart (dtype MF_F64 or MF_F32: the arithmetic
+ * precision of the apply).  Dirichlet rows return src.  Asynchronous. */
+mf_status mf_apply(mf_op* op, const void* src, void* dst, int nrhs, int64_t ld, int dtype);
+/* dst = A^T src (Helmholtz, heat with convection, reinit).  Asynchronous. */
+mf_status mf_apply_transpose(mf_op* op, const void* src, void* dst, int nrhs, int64_t ld, int dtype);
+/* dst = diag(A) (Dirichlet rows 1).  Asynchronous. */
+mf_status mf_diagonal(mf_op* op, void* dst, int dtype);
+
+typedef enum { MF_SOLVER_CG = 0, MF_SOLVER_GMRES = 1, MF_SOLVER_DEFECT_CORRECTION = 2 } mf_solver_kind;
+typedef enum { MF_PREC_NONE = 0, MF_PREC_JACOBI = 1, MF_PREC_CHEBYSHEV = 2, MF_PREC_BLOCK_JACOBI = 3 } mf_prec_kind;
+
+typedef struct {
+  int solver;          /* mf_solver_kind */
+  int precond;         /* mf_prec_kind (defect correction: preconditioner of the inner CG) */
+  int inner_dtype;     /* defect correction: precision of the inner solve (MF_F32) */
+  int restart;         /* GMRES restart length */
+  int cheby_degree;    /* operator applications per Chebyshev preconditioner call */
+  int maxit;           /* iteration cap (outer steps for defect correction) */
+  int inner_maxit;     /* defect correction: inner CG cap */
+  int use_graph;       /* capture the CG iteration body in a CUDA graph */
+  double tol;          /* stop when ||b - A x||_2 <= tol ||b||_2 (x0 = 0) */
+  double inner_tol;    /* defect correction: inner relative tolerance */
+  double cheby_ratio;  /* Chebyshev interval [lambda_max/ratio, 1.1 lambda_max] */
+  int lanczos_steps;   /* steps of the lambda_max estimate of D^-1 A */
+  int reserved;
+} mf_solver_params;
+
+typedef struct {
+  int iterations;          /* Krylov iterations (defect correction: inner iterations, summed) */
+  int outer_iterations;    /* defect correction steps */
+  double rel_residual;     /* final ||b - A x|| / ||b|| in fp64 */
+  double lambda_max;       /* Chebyshev estimate used (0 if none) */
+  double seconds;          /* wall time of the call */
+} mf_solve_info;
+
+/* Solve A x = b for each of nrhs right-hand sides (stored n apart), x0 = 0, in fp64 (b, x
+ * fp64 device vectors).  Synchronising.  Returns MF_ENOTCONV with info filled when the
+ * tolerance is not reached within maxit. */
+mf_status mf_solve(mf_op* op, const mf_solver_params* params, const double* b, double* x, int nrhs,
+                   mf_solve_info* info);
+
+typedef struct {
+  double power, radius, x0, y0, absorptivity;
+} mf_laser;
+
+/* Top-face load f_i = int_{z = hi_z} q(x, y) N_i dA of eq. (laser_gauss) (beam along -z,
+ * so <-n . e_L> = 1), (k+1)^2 Gauss points per face, into fp64 device dst[n_dofs]
+ * (overwritten; Dirichlet rows 0).  If d_params is not NULL it receives the four load
+ * vectors of dq/dP, dq/dr, dq/dx0, dq/dy0 (4 blocks of n_dofs).  Asynchronous. */
+mf_status mf_laser_load(mf_op* op, const mf_laser* laser, double* dst, double* d_params);
+
+/* One implicit heat step and its adjoint gradient (HEAT operators).  With theta = T - T_ref:
+ *   A theta = rho_cp/dt M theta_prev + f_laser,  J = 1/2 int_box (theta_h - theta*_h)^2
+ * over the cells whose centre has |x|, |y| <= box_half and z >= hi_z - box_depth.
+ * Outputs: *J (host), dJ_dlaser[4] (host: P, r, x0, y0), dJ_dkq (device, n_cells*27, may be
+ * NULL; needs MF_FIELD_K_QPOINT), theta and lambda (device, n_dofs each, may be NULL).
+ * Forward and adjoint systems are solved with `solver` (GMRES when convection is present).
+ * Synchronising. */
+mf_status mf_heat_step_gradient(mf_op* op, const mf_laser* laser, const mf_solver_params* solver,
+                                const double* theta_prev, const double* theta_target,
+                                double box_half, double box_depth, double* J, double* dJ_dlaser,
+                                double* dJ_dkq, double* theta, double* lambda);
+
+/* Time the apply variants of this operator (cells per block, coefficient mode) and keep
+ * the fastest; results are appended to cache_path (may be NULL).  Synchronising. */
+mf_status mf_autotune(mf_op* op, const char* cache_path);
+
+/* Describe the variant the next apply will launch (host string, owned by the library). */
+const char* mf_operator_variant(const mf_op* op);
+
+/* Number of kernel launches the library has issued on this context so far. */
+int64_t mf_context_launch_count(const mf_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MFGB_H */

@@ -1,0 +1,575 @@
+// C ABI of libmfgb: contexts, meshes, DoF maps, operators, apply / transpose / diagonal.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <string>
+
+#include "ops.h"
+#include "vec.cuh"
+
+namespace mf {
+
+static thread_local std::string g_error;
+
+void set_error(const std::string& msg) { g_error = msg; }
+mf_status fail(mf_status st, const std::string& msg) {
+  set_error(msg);
+  return st;
+}
+
+}  // namespace mf
+
+using namespace mf;
+
+#define MF_GUARD_BEGIN try {
+#define MF_GUARD_END                                                         \
+  }                                                                          \
+  catch (const std::bad_alloc&) { return fail(MF_ENOMEM, "host allocation failed"); } \
+  catch (...) { return fail(MF_EINVAL, "internal exception"); }
+
+extern "C" {
+
+const char* mf_last_error(void) { return mf::g_error.c_str(); }
+
+mf_status mf_context_create(int device, void* cuda_stream, mf_ctx** out) {
+  MF_GUARD_BEGIN
+  if (!out) return fail(MF_EINVAL, "out is NULL");
+  *out = nullptr;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
+    cudaGetLastError();
+    return fail(MF_ECUDA, "no CUDA device visible");
+  }
+  if (device < 0 || device >= ndev) return fail(MF_EINVAL, "device index out of range");
+  MF_CUDA_TRY(cudaSetDevice(device));
+  auto* c = new mf_ctx();
+  c->device = device;
+  if (cuda_stream) c->stream = static_cast<cudaStream_t>(cuda_stream);
+  else {
+    if (cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess) {
+      delete c;
+      return fail(MF_ECUDA, "cudaStreamCreate failed");
+    }
+    c->own_stream = true;
+  }
+  cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, device);
+  mf_status st = c->scratch.alloc(kScratchDoubles * sizeof(double));
+  if (st == MF_OK) st = c->scalars.alloc(sizeof(double) * kScalarsTotal);
+  if (st == MF_OK && cudaMallocHost(&c->host_scalars, sizeof(double) * kScalarsTotal) != cudaSuccess)
+    st = fail(MF_ENOMEM, "pinned host allocation failed");
+  if (st != MF_OK) {
+    mf_context_destroy(c);
+    return st;
+  }
+  *out = c;
+  return MF_OK;
+  MF_GUARD_END
+}
+
+void mf_context_destroy(mf_ctx* c) {
+  if (!c) return;
+  if (c->stream) cudaStreamSynchronize(c->stream);
+  if (c->host_scalars) cudaFreeHost(c->host_scalars);
+  c->scratch.release();
+  c->scalars.release();
+  if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
+  delete c;
+}
+
+mf_status mf_context_set_stream(mf_ctx* c, void* s) {
+  if (!c) return fail(MF_EINVAL, "ctx is NULL");
+  if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
+  c->own_stream = false;
+  c->stream = static_cast<cudaStream_t>(s);
+  return MF_OK;
+}
+
+int64_t mf_context_launch_count(const mf_ctx* c) { return c ? c->launches : 0; }
+
+mf_status mf_mesh_uniform(mf_ctx* c, const int n[3], const double lo[3], const double hi[3], mf_mesh** out) {
+  MF_GUARD_BEGIN
+  if (!n || !lo || !hi || !out) return fail(MF_EINVAL, "NULL argument");
+  *out = nullptr;
+  double h[3];
+  for (int d = 0; d < 3; ++d) {
+    if (n[d] <= 0 || n[d] > 4096) return fail(MF_EINVAL, "cells per axis must be in 1..4096");
+    if (!(hi[d] > lo[d])) return fail(MF_EINVAL, "empty box");
+    h[d] = (hi[d] - lo[d]) / n[d];
+  }
+  if (std::fabs(h[1] - h[0]) > 1e-12 * h[0] || std::fabs(h[2] - h[0]) > 1e-12 * h[0])
+    return fail(MF_EINVAL, "uniform cells must be cubes");
+  auto* m = new mf_mesh();
+  m->ctx = c;
+  for (int d = 0; d < 3; ++d) {
+    m->n[d] = n[d];
+    m->lo[d] = lo[d];
+    m->hi[d] = hi[d];
+  }
+  m->h0 = h[0];
+  *out = m;
+  return MF_OK;
+  MF_GUARD_END
+}
+
+mf_status mf_mesh_octree(mf_ctx* c, int base, int levels, const double lo[3], const double hi[3], const int32_t* leaves,
+                         int64_t nleaves, mf_mesh** out) {
+  MF_GUARD_BEGIN
+  if (!lo || !hi || !out || (!leaves && nleaves)) return fail(MF_EINVAL, "NULL argument");
+  *out = nullptr;
+  if (base <= 0 || levels < 0 || levels > 10) return fail(MF_EINVAL, "base must be > 0 and levels in 0..10");
+  const int64_t nf = int64_t(base) << levels;
+  if (nf > 1024) return fail(MF_EINVAL, "finest level finer than 1024 cells per axis");
+  for (int d = 0; d < 3; ++d)
+    if (!(hi[d] > lo[d]) || std::fabs((hi[d] - lo[d]) - (hi[0] - lo[0])) > 1e-12 * (hi[0] - lo[0]))
+      return fail(MF_EINVAL, "octree domain must be a cube");
+  if (nleaves <= 0) return fail(MF_EINVAL, "no leaves");
+  // tiling and 2:1 balance on the finest grid
+  std::vector<int8_t> lev(size_t(nf * nf * nf), -1);
+  for (int64_t t = 0; t < nleaves; ++t) {
+    const int32_t* lf = leaves + 4 * t;
+    const int l = lf[0];
+    if (l < 0 || l > levels) return fail(MF_EINVAL, "leaf level out of range");
+    const int64_t nl = int64_t(base) << l, s = int64_t(1) << (levels - l);
+    for (int d = 1; d < 4; ++d)
+      if (lf[d] < 0 || lf[d] >= nl) return fail(MF_EINVAL, "leaf coordinate out of range");
+    for (int64_t z = lf[3] * s; z < (lf[3] + 1) * s; ++z)
+      for (int64_t y = lf[2] * s; y < (lf[2] + 1) * s; ++y)
+        for (int64_t x = lf[1] * s; x < (lf[1] + 1) * s; ++x) {
+          int8_t& v = lev[size_t((z * nf + y) * nf + x)];
+          if (v != -1) return fail(MF_EINVAL, "leaves overlap");
+          v = int8_t(l);
+        }
+  }
+  for (size_t i = 0; i < lev.size(); ++i)
+    if (lev[i] < 0) return fail(MF_EINVAL, "leaves do not cover the domain");
+  for (int64_t z = 0; z < nf; ++z)
+    for (int64_t y = 0; y < nf; ++y)
+      for (int64_t x = 0; x < nf; ++x) {
+        const int a = lev[size_t((z * nf + y) * nf + x)];
+        for (int dz = 0; dz <= 1; ++dz)
+          for (int dy = -1; dy <= 1; ++dy)
+            for (int dx = -1; dx <= 1; ++dx) {
+              if (dz == 0 && (dy < 0 || (dy == 0 && dx <= 0))) continue;
+              const int64_t X = x + dx, Y = y + dy, Z = z + dz;
+              if (X < 0 || Y < 0 || X >= nf || Y >= nf || Z >= nf) continue;
+              const int b = lev[size_t((Z * nf + Y) * nf + X)];
+              if (a - b > 1 || b - a > 1) return fail(MF_EINVAL, "leaves are not 2:1 balanced");
+            }
+      }
+  lev.clear();
+  lev.shrink_to_fit();
+  // Morton order of the finest-level anchors
+  std::vector<std::pair<uint64_t, int64_t>> key(nleaves);
+  auto spread = [](uint64_t v) {
+    uint64_t r = 0;
+    for (int b = 0; b < 21; ++b) r |= ((v >> b) & 1ull) << (3 * b);
+    return r;
+  };
+  for (int64_t t = 0; t < nleaves; ++t) {
+    const int32_t* lf = leaves + 4 * t;
+    const int sh = levels - lf[0];
+    key[t] = {spread(uint64_t(lf[1]) << sh) | (spread(uint64_t(lf[2]) << sh) << 1) | (spread(uint64_t(lf[3]) << sh) << 2), t};
+  }
+  std::sort(key.begin(), key.end());
+  auto* m = new mf_mesh();
+  m->ctx = c;
+  m->octree = true;
+  m->base = base;
+  m->levels = levels;
+  for (int d = 0; d < 3; ++d) {
+    m->n[d] = base;
+    m->lo[d] = lo[d];
+    m->hi[d] = hi[d];
+  }
+  m->h0 = (hi[0] - lo[0]) / base;
+  m->leaves.resize(4 * nleaves);
+  for (int64_t t = 0; t < nleaves; ++t) std::memcpy(&m->leaves[4 * t], leaves + 4 * key[t].second, 4 * sizeof(int32_t));
+  *out = m;
+  return MF_OK;
+  MF_GUARD_END
+}
+
+void mf_mesh_destroy(mf_mesh* m) { delete m; }
+
+mf_status mf_dofmap_create(mf_mesh* mesh, int degree, uint32_t faces, mf_dofmap** out) {
+  MF_GUARD_BEGIN
+  if (!mesh || !out) return fail(MF_EINVAL, "NULL argument");
+  *out = nullptr;
+  if (degree != 1 && degree != 2) return fail(MF_EUNSUPPORTED, "degree must be 1 or 2");
+  if (faces >> 6) return fail(MF_EINVAL, "dirichlet_faces has bits above 5");
+  auto* m = new mf_dofmap();
+  m->mesh = mesh;
+  m->degree = degree;
+  m->nb = (degree + 1) * (degree + 1) * (degree + 1);
+  m->dirichlet_faces = faces;
+  mf_status st = mesh->octree ? build_octree_dofmap(m) : build_uniform_dofmap(m);
+  if (st == MF_OK && mesh->ctx) st = upload_dofmap(m);  // host-only maps (NULL context) stay on the host
+  if (st != MF_OK) {
+    delete m;
+    return st;
+  }
+  *out = m;
+  return MF_OK;
+  MF_GUARD_END
+}
+
+void mf_dofmap_destroy(mf_dofmap* m) { delete m; }
+
+mf_status mf_dofmap_query(const mf_dofmap* m, int64_t* nd, int64_t* nc, int64_t* ncon, int64_t* nent) {
+  if (!m) return fail(MF_EINVAL, "map is NULL");
+  if (nd) *nd = m->n_dofs;
+  if (nc) *nc = m->n_cells;
+  if (ncon) *ncon = m->uniform ? 0 : int64_t(m->con_rowptr.size()) - 1;
+  if (nent) *nent = m->uniform ? 0 : int64_t(m->con_cols.size());
+  return MF_OK;
+}
+
+mf_status mf_dofmap_export(const mf_dofmap* m, int32_t* cell_map, int64_t* con_rowptr, int32_t* con_cols, double* con_w,
+                           double* coords, uint8_t* dirichlet) {
+  MF_GUARD_BEGIN
+  if (!m) return fail(MF_EINVAL, "map is NULL");
+  const int k = m->degree, nb = m->nb;
+  const int64_t Rx = m->R[0] + 1, Ry = m->R[1] + 1;
+  if (cell_map) {
+    if (m->uniform) {
+      const int nx = m->mesh->n[0], ny = m->mesh->n[1], nz = m->mesh->n[2];
+      int64_t c = 0;
+      for (int cz = 0; cz < nz; ++cz)
+        for (int cy = 0; cy < ny; ++cy)
+          for (int cx = 0; cx < nx; ++cx, ++c)
+            for (int i = 0, l = 0; i <= k; ++i)
+              for (int j = 0; j <= k; ++j)
+                for (int a = 0; a <= k; ++a, ++l) {
+                  const int64_t x = int64_t(k) * cx + a, y = int64_t(k) * cy + j, z = int64_t(k) * cz + i;
+                  cell_map[c * nb + l] = int32_t(x + Rx * (y + Ry * z));
+                }
+    } else {
+      std::memcpy(cell_map, m->cell_map.data(), m->cell_map.size() * sizeof(int32_t));
+    }
+  }
+  if (!m->uniform) {
+    if (con_rowptr) std::memcpy(con_rowptr, m->con_rowptr.data(), m->con_rowptr.size() * sizeof(int64_t));
+    if (con_cols) std::memcpy(con_cols, m->con_cols.data(), m->con_cols.size() * sizeof(int32_t));
+    if (con_w) std::memcpy(con_w, m->con_w.data(), m->con_w.size() * sizeof(double));
+  } else if (con_rowptr) {
+    con_rowptr[0] = 0;
+  }
+  if (coords) {
+    const mf_mesh* me = m->mesh;
+    double span[3], lo[3];
+    for (int d = 0; d < 3; ++d) {
+      span[d] = (me->hi[d] - me->lo[d]) / double(m->R[d]);
+      lo[d] = me->lo[d];
+    }
+    for (int64_t d = 0; d < m->n_dofs; ++d) {
+      const int64_t key = m->uniform ? d : m->free_keys[d];
+      const int64_t p[3] = {key % Rx, (key / Rx) % Ry, key / (Rx * Ry)};
+      for (int a = 0; a < 3; ++a) coords[3 * d + a] = lo[a] + double(p[a]) * span[a];
+    }
+  }
+  if (dirichlet) std::memcpy(dirichlet, m->dirichlet.data(), m->dirichlet.size());
+  return MF_OK;
+  MF_GUARD_END
+}
+
+// ------------------------------------------------------------------------ operators
+
+static bool is_q2(const mf_dofmap* m) { return m && m->degree == 2; }
+
+mf_status mf_operator_create(mf_ctx* c, const mf_op_params* p, const mf_dofmap* const* maps, int nmaps, mf_op** out) {
+  MF_GUARD_BEGIN
+  if (!c || !p || !maps || !out) return fail(MF_EINVAL, "NULL argument");
+  *out = nullptr;
+  for (int i = 0; i < nmaps; ++i)
+    if (!maps[i] || maps[i]->mesh->ctx != c) return fail(MF_EINVAL, "maps must be built on this context's meshes");
+  if (p->kind < 0 || p->kind > MF_OP_REINIT) return fail(MF_EINVAL, "unknown operator kind");
+  if (p->kind == MF_OP_OSEEN) {
+    if (nmaps != 2 || !is_q2(maps[0]) || !maps[1] || maps[1]->degree != 1 || maps[0]->mesh != maps[1]->mesh ||
+        !maps[0]->uniform)
+      return fail(MF_EINVAL, "Oseen needs a Q2 and a Q1 map on the same uniform mesh");
+    if (maps[1]->dirichlet_faces) return fail(MF_EUNSUPPORTED, "Dirichlet pressure DoFs");
+  } else {
+    if (nmaps != 1 || !is_q2(maps[0])) return fail(MF_EINVAL, "scalar operators need one Q2 map");
+  }
+  if (p->heaviside != 0 && p->heaviside != 1) return fail(MF_EINVAL, "heaviside must be 0 or 1");
+  if (p->heaviside == 1 && !(p->eps > 0)) return fail(MF_EINVAL, "sine Heaviside needs eps > 0");
+  auto* op = new mf_op();
+  op->ctx = c;
+  op->p = *p;
+  op->nmaps = nmaps;
+  for (int i = 0; i < nmaps; ++i) op->map[i] = maps[i];
+  op->n = maps[0]->n_dofs * (p->kind == MF_OP_OSEEN ? 3 : 1) + (nmaps == 2 ? maps[1]->n_dofs : 0);
+  op->ncells = maps[0]->n_cells;
+  op->mode64 = p->kind == MF_OP_OSEEN ? 1 : (p->coef_mode == MF_COEF_INKERNEL ? 0 : 1);
+  op->mode32 = op->mode64;
+  *out = op;
+  return MF_OK;
+  MF_GUARD_END
+}
+
+void mf_operator_destroy(mf_op* op) { delete op; }
+
+mf_status mf_operator_size(const mf_op* op, int64_t* n) {
+  if (!op || !n) return fail(MF_EINVAL, "NULL argument");
+  *n = op->n;
+  return MF_OK;
+}
+
+const char* mf_operator_variant(const mf_op* op) { return op ? op->variant.c_str() : ""; }
+
+mf_status mf_operator_set_field(mf_op* op, int field, const void* ptr, int dtype, int64_t n) {
+  MF_GUARD_BEGIN
+  if (!op || !ptr) return fail(MF_EINVAL, "NULL argument");
+  if (dtype != MF_F64) return fail(MF_EUNSUPPORTED, "fields are fp64");
+  const int64_t nd = op->map[0]->n_dofs;
+  switch (field) {
+    case MF_FIELD_PHI:
+      if (n != nd) return fail(MF_EINVAL, "PHI must have n_dofs values");
+      op->phi = static_cast<const double*>(ptr);
+      break;
+    case MF_FIELD_T_PREV:
+      if (n != nd) return fail(MF_EINVAL, "T_PREV must have n_dofs values");
+      op->tprev = static_cast<const double*>(ptr);
+      break;
+    case MF_FIELD_BETA:
+      if (n != 3 * nd) return fail(MF_EINVAL, "BETA must have 3 * n_dofs values");
+      op->beta = static_cast<const double*>(ptr);
+      break;
+    case MF_FIELD_K_QPOINT:
+      if (n != op->ncells * 27) return fail(MF_EINVAL, "K_QPOINT must have n_cells * 27 values");
+      op->kq_user = static_cast<const double*>(ptr);
+      break;
+    default:
+      return fail(MF_EINVAL, "unknown field");
+  }
+  op->tables_ready = false;
+  op->diag_ready = false;
+  // float copy of the in-kernel nodal field
+  const double* f = op->p.kind == MF_OP_HEAT ? op->tprev : op->phi;
+  if (f && (field == MF_FIELD_PHI || field == MF_FIELD_T_PREV)) {
+    MF_TRY(op->field32.alloc(sizeof(float) * nd));
+    MF_TRY(convert<double, float>(op->ctx, nd, f, op->field32.as<float>()));
+  }
+  return MF_OK;
+  MF_GUARD_END
+}
+
+}  // extern "C"
+
+namespace mf {
+
+int scalar_kind(const mf_op* op) {
+  switch (op->p.kind) {
+    case MF_OP_HELMHOLTZ: return K_HELM;
+    case MF_OP_HEAT: return K_HEAT;
+    case MF_OP_REINIT: return K_REINIT;
+  }
+  return -1;
+}
+
+double value_coef(const mf_op* op) {
+  switch (op->p.kind) {
+    case MF_OP_HELMHOLTZ: return op->p.mass_coef;
+    case MF_OP_HEAT: return op->p.rhocp / op->p.dt;
+    case MF_OP_REINIT: return 1.0 / op->p.dtau;
+  }
+  return 0.0;
+}
+
+mf_status check_fields(const mf_op* op) {
+  switch (op->p.kind) {
+    case MF_OP_HELMHOLTZ:
+      if (!op->phi) return fail(MF_EINVAL, "Helmholtz needs MF_FIELD_PHI");
+      break;
+    case MF_OP_HEAT:
+      if (!op->tprev && !op->kq_user) return fail(MF_EINVAL, "heat needs MF_FIELD_T_PREV or MF_FIELD_K_QPOINT");
+      break;
+    case MF_OP_OSEEN:
+      if (!op->phi || !op->beta) return fail(MF_EINVAL, "Oseen needs MF_FIELD_PHI and MF_FIELD_BETA");
+      break;
+    case MF_OP_REINIT:
+      if (!op->phi) return fail(MF_EINVAL, "reinit needs MF_FIELD_PHI");
+      break;
+  }
+  return MF_OK;
+}
+
+mf_status ensure_tables(mf_op* op) {
+  if (op->tables_ready) return MF_OK;
+  MF_TRY(check_fields(op));
+  const int64_t nc = op->ncells;
+  const mf_op_params& p = op->p;
+  if (p.kind == MF_OP_OSEEN) {
+    MF_TRY(op->rho64.alloc(sizeof(double) * 27 * nc));
+    MF_TRY(op->rho32.alloc(sizeof(float) * 27 * nc));
+    MF_TRY(op->mu64.alloc(sizeof(double) * 27 * nc));
+    MF_TRY(op->mu32.alloc(sizeof(float) * 27 * nc));
+    MF_TRY(op->qvec64.alloc(sizeof(double) * 81 * nc));
+    MF_TRY(op->qvec32.alloc(sizeof(float) * 81 * nc));
+    MF_TRY(launch_oseen_qtables(op->ctx, op->map[0], op->phi, op->beta, p.rho_l, p.rho_g, p.mu_l, p.mu_g, p.heaviside,
+                                p.eps, op->rho64.as<double>(), op->rho32.as<float>(), op->mu64.as<double>(),
+                                op->mu32.as<float>(), op->qvec64.as<double>(), op->qvec32.as<float>()));
+  } else {
+    const int kind = scalar_kind(op);
+    MF_TRY(op->qcoef64.alloc(sizeof(double) * 27 * nc));
+    MF_TRY(op->qcoef32.alloc(sizeof(float) * 27 * nc));
+    const bool vec = (kind == K_REINIT) || (kind == K_HEAT && op->beta);
+    if (vec) {
+      MF_TRY(op->qvec64.alloc(sizeof(double) * 81 * nc));
+      MF_TRY(op->qvec32.alloc(sizeof(float) * 81 * nc));
+    }
+    const double* field = kind == K_HEAT ? op->tprev : op->phi;
+    MF_TRY(launch_scalar_qtables(op->ctx, op->map[0], kind, field, op->kq_user, kind == K_HEAT ? op->beta : nullptr,
+                                 p.k0, 0.5 * p.k0 / (p.t_boil > 0 ? p.t_boil : 1.0), p.a_liquid, p.a_gas, p.heaviside,
+                                 p.eps, p.rhocp, op->qcoef64.as<double>(), op->qcoef32.as<float>(),
+                                 vec ? op->qvec64.as<double>() : nullptr, vec ? op->qvec32.as<float>() : nullptr));
+  }
+  op->tables_ready = true;
+  return MF_OK;
+}
+
+template <typename T> ScalarArgs<T> scalar_args(const mf_op* op, const T* src, T* dst, int nrhs, int64_t ld) {
+  ScalarArgs<T> a{};
+  const bool f32 = sizeof(T) == 4;
+  a.src = src;
+  a.dst = dst;
+  a.nrhs = nrhs;
+  a.ld = ld;
+  a.field = f32 ? reinterpret_cast<const T*>(op->field32.as<float>())
+                : reinterpret_cast<const T*>(op->p.kind == MF_OP_HEAT ? op->tprev : op->phi);
+  a.qcoef = f32 ? reinterpret_cast<const T*>(op->qcoef32.as<float>()) : reinterpret_cast<const T*>(op->qcoef64.as<double>());
+  a.qvec = f32 ? reinterpret_cast<const T*>(op->qvec32.as<float>()) : reinterpret_cast<const T*>(op->qvec64.as<double>());
+  a.ncp = op->ncells;
+  a.mass = T(value_coef(op));
+  a.a_l = T(op->p.a_liquid);
+  a.a_g = T(op->p.a_gas);
+  a.k0 = T(op->p.k0);
+  a.k_slope = T(0.5 * op->p.k0 / (op->p.t_boil > 0 ? op->p.t_boil : 1.0));
+  a.eps = T(op->p.eps);
+  a.heaviside = op->p.heaviside;
+  return a;
+}
+template ScalarArgs<double> scalar_args<double>(const mf_op*, const double*, double*, int, int64_t);
+template ScalarArgs<float> scalar_args<float>(const mf_op*, const float*, float*, int, int64_t);
+
+template <typename T> OseenArgs<T> oseen_args(const mf_op* op, const T* src, T* dst) {
+  OseenArgs<T> a{};
+  const bool f32 = sizeof(T) == 4;
+  a.src = src;
+  a.dst = dst;
+  a.nu = op->map[0]->n_dofs;
+  a.np = op->map[1]->n_dofs;
+  a.rho = f32 ? reinterpret_cast<const T*>(op->rho32.as<float>()) : reinterpret_cast<const T*>(op->rho64.as<double>());
+  a.mu = f32 ? reinterpret_cast<const T*>(op->mu32.as<float>()) : reinterpret_cast<const T*>(op->mu64.as<double>());
+  a.beta = f32 ? reinterpret_cast<const T*>(op->qvec32.as<float>()) : reinterpret_cast<const T*>(op->qvec64.as<double>());
+  a.sigma = T(op->p.sigma);
+  return a;
+}
+template OseenArgs<double> oseen_args<double>(const mf_op*, const double*, double*);
+
+// dst = A src (or A^T src), nrhs vectors ld apart, precision T.
+template <typename T> mf_status apply_impl(mf_op* op, const T* src, T* dst, int nrhs, int64_t ld, bool transpose) {
+  const bool f32 = sizeof(T) == 4;
+  mf_ctx* c = op->ctx;
+  MF_TRY(check_fields(op));
+  const int mode = f32 ? op->mode32 : op->mode64;
+  const bool needs_tables = op->p.kind == MF_OP_OSEEN || mode == 1 || (op->p.kind == MF_OP_HEAT && (op->beta || op->kq_user));
+  if (needs_tables) MF_TRY(ensure_tables(op));
+  if (ld == op->n) MF_CUDA_TRY(cudaMemsetAsync(dst, 0, sizeof(T) * op->n * nrhs, c->stream));
+  else
+    for (int r = 0; r < nrhs; ++r) MF_CUDA_TRY(cudaMemsetAsync(dst + r * ld, 0, sizeof(T) * op->n, c->stream));
+  if (op->p.kind == MF_OP_OSEEN) {
+    if (transpose) return fail(MF_EUNSUPPORTED, "transpose of the Oseen operator");
+    const int64_t nu = op->map[0]->n_dofs;
+    for (int r = 0; r < nrhs; ++r) {
+      OseenArgs<T> a = oseen_args<T>(op, src + r * ld, dst + r * ld);
+      MF_TRY(launch_oseen_apply(c, op->map[0], f32, &a));
+      for (int comp = 0; comp < 3; ++comp)
+        MF_TRY(launch_dirichlet_copy(c, op->map[0], src + r * ld, dst + r * ld, 1, ld, comp * nu, f32));
+    }
+    op->variant = std::string("oseen_q2q1/") + (f32 ? "f32" : "f64") + "/tabulated";
+    return MF_OK;
+  }
+  const int kind = scalar_kind(op);
+  const bool beta = kind == K_HEAT && op->beta;
+  if (transpose && !(kind == K_HEAT && beta)) {
+    // symmetric operators: A^T = A
+    transpose = false;
+  }
+  int m = mode;
+  if (kind == K_HEAT && op->kq_user) m = 1;
+  if (!op->map[0]->uniform && !needs_tables && m == 1) MF_TRY(ensure_tables(op));
+  ScalarArgs<T> a = scalar_args<T>(op, src, dst, nrhs, ld);
+  MF_TRY(launch_scalar_apply(c, op->map[0], kind, m, beta, transpose, f32, &a));
+  MF_TRY(launch_dirichlet_copy(c, op->map[0], src, dst, nrhs, ld, 0, f32));
+  op->variant = std::string(kind == K_HELM ? "helmholtz" : kind == K_HEAT ? "heat" : "reinit") +
+                (op->map[0]->uniform ? "/uniform" : "/octree") + (f32 ? "/f32" : "/f64") +
+                (m == 0 ? "/inkernel" : "/tabulated") + (beta ? (transpose ? "/conv-T" : "/conv") : "");
+  return MF_OK;
+}
+template mf_status apply_impl<double>(mf_op*, const double*, double*, int, int64_t, bool);
+template mf_status apply_impl<float>(mf_op*, const float*, float*, int, int64_t, bool);
+
+mf_status diag64(mf_op* op, double** out) {
+  if (!op->diag_ready) {
+    MF_TRY(ensure_tables(op));
+    if (op->p.kind == MF_OP_OSEEN) {
+      const int64_t nu = op->map[0]->n_dofs, np = op->map[1]->n_dofs;
+      MF_TRY(op->blk64.alloc(sizeof(double) * 9 * nu));
+      MF_TRY(op->pdiag64.alloc(sizeof(double) * np));
+      OseenArgs<double> a = oseen_args<double>(op, nullptr, nullptr);
+      MF_TRY(launch_oseen_blockdiag(op->ctx, op->map[0], op->map[1], a, op->blk64.as<double>(), op->pdiag64.as<double>()));
+    } else {
+      MF_TRY(op->diag64.alloc(sizeof(double) * op->n));
+      ScalarArgs<double> a = scalar_args<double>(op, nullptr, nullptr, 1, op->n);
+      const int kind = scalar_kind(op);
+      MF_TRY(launch_scalar_diag(op->ctx, op->map[0], kind, kind == K_HEAT && op->beta, a, op->diag64.as<double>()));
+    }
+    op->diag_ready = true;
+  }
+  if (out) *out = op->diag64.as<double>();
+  return MF_OK;
+}
+
+}  // namespace mf
+
+extern "C" {
+
+mf_status mf_apply(mf_op* op, const void* src, void* dst, int nrhs, int64_t ld, int dtype) {
+  MF_GUARD_BEGIN
+  if (!op || !src || !dst) return fail(MF_EINVAL, "NULL argument");
+  if (nrhs < 1 || ld < op->n) return fail(MF_EINVAL, "nrhs must be >= 1 and ld >= n");
+  if (dtype == MF_F64) return apply_impl<double>(op, (const double*)src, (double*)dst, nrhs, ld, false);
+  if (dtype == MF_F32) return apply_impl<float>(op, (const float*)src, (float*)dst, nrhs, ld, false);
+  return fail(MF_EUNSUPPORTED, "apply precision must be MF_F64 or MF_F32");
+  MF_GUARD_END
+}
+
+mf_status mf_apply_transpose(mf_op* op, const void* src, void* dst, int nrhs, int64_t ld, int dtype) {
+  MF_GUARD_BEGIN
+  if (!op || !src || !dst) return fail(MF_EINVAL, "NULL argument");
+  if (nrhs < 1 || ld < op->n) return fail(MF_EINVAL, "nrhs must be >= 1 and ld >= n");
+  if (dtype == MF_F64) return apply_impl<double>(op, (const double*)src, (double*)dst, nrhs, ld, true);
+  if (dtype == MF_F32) return apply_impl<float>(op, (const float*)src, (float*)dst, nrhs, ld, true);
+  return fail(MF_EUNSUPPORTED, "apply precision must be MF_F64 or MF_F32");
+  MF_GUARD_END
+}
+
+mf_status mf_diagonal(mf_op* op, void* dst, int dtype) {
+  MF_GUARD_BEGIN
+  if (!op || !dst) return fail(MF_EINVAL, "NULL argument");
+  if (op->p.kind == MF_OP_OSEEN) return fail(MF_EUNSUPPORTED, "Oseen uses nodal block diagonals");
+  double* d;
+  MF_TRY(diag64(op, &d));
+  if (dtype == MF_F64)
+    MF_CUDA_TRY(cudaMemcpyAsync(dst, d, sizeof(double) * op->n, cudaMemcpyDeviceToDevice, op->ctx->stream));
+  else if (dtype == MF_F32)
+    MF_TRY(convert<double, float>(op->ctx, op->n, d, static_cast<float*>(dst)));
+  else
+    return fail(MF_EUNSUPPORTED, "diagonal precision must be MF_F64 or MF_F32");
+  return MF_OK;
+  MF_GUARD_END
+}
+
+}  // extern "C"

@@ -1,0 +1,543 @@
+// Set-up kernels of the operators: Gauss-point coefficient tables (always evaluated in
+// fp64), matrix-free diagonals and block-Jacobi blocks, the laser top-face load of
+// eq. (laser_gauss) and the conductivity gradient of the heat-step adjoint.
+#include <cmath>
+
+#include "scalar_local.cuh"
+
+namespace mf {
+
+MF_DEFINE_TABLE_UPLOAD
+
+UniformGeom uniform_geom(const mf_dofmap* m);
+OctGeom oct_geom(const mf_dofmap* m);
+
+namespace {
+
+// cell index t of the map's natural order -> location
+struct Loc {
+  int64_t cell;
+  int64_t base;
+  uint32_t dmask;
+  double h;
+  int i, j, k;
+};
+
+template <bool OCT>
+__device__ __forceinline__ bool natural_cell(const UniformGeom& ug, const OctGeom& og, int64_t t, Loc& L) {
+  if (OCT) {
+    if (t >= og.ncells) return false;
+    L.cell = t;
+    L.h = og.h0 / double(1 << __ldg(og.level + t));
+    L.base = 0;
+    L.dmask = 0;
+    return true;
+  }
+  const int64_t nc = int64_t(ug.nx) * ug.ny * ug.nz;
+  if (t >= nc) return false;
+  L.i = int(t % ug.nx);
+  L.j = int((t / ug.nx) % ug.ny);
+  L.k = int(t / (int64_t(ug.nx) * ug.ny));
+  L.cell = t;
+  L.base = 2 * int64_t(L.i) + ug.sx * (2 * int64_t(L.j)) + ug.sy * (2 * int64_t(L.k));
+  L.dmask = dirichlet_mask(ug, L.i, L.j, L.k);
+  L.h = ug.h;
+  return true;
+}
+
+template <bool OCT, bool MASK>
+__device__ __forceinline__ void gather64(const UniformGeom& ug, const OctGeom& og, const Loc& L, const double* src,
+                                         double* U) {
+  if (OCT) gather_oct<double, MASK>(og, src, L.cell, U);
+  else gather_uniform<double>(src, L.base, ug.sx, ug.sy, MASK ? L.dmask : 0u, U);
+}
+
+// ---------------------------------------------------------------- Gauss-point tables
+template <bool OCT>
+__global__ void k_scalar_qtables(UniformGeom ug, OctGeom og, int kind, const double* field, const double* kq_user,
+                                 const double* beta, int64_t nd, double k0, double kslope, double a_l, double a_g,
+                                 int hv, double eps, double rhocp, int64_t ncp, double* qc64, float* qc32,
+                                 double* qv64, float* qv32) {
+  Loc L;
+  const int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (!natural_cell<OCT>(ug, og, t, L)) return;
+  double C[27];
+  if (kind == K_HEAT && kq_user) {
+    for (int q = 0; q < 27; ++q) C[q] = kq_user[L.cell * 27 + q];
+  } else if (field) {
+    gather64<OCT, false>(ug, og, L, field, C);
+    to_qpoints<double>(C);
+  }
+  if (kind == K_HELM) {
+    for (int q = 0; q < 27; ++q) {
+      double a = a_g + (a_l - a_g) * heaviside<double>(C[q], hv, eps);
+      qc64[q * ncp + L.cell] = a;
+      qc32[q * ncp + L.cell] = float(a);
+    }
+  } else if (kind == K_HEAT) {
+    for (int q = 0; q < 27; ++q) {
+      double k = kq_user ? C[q] : k0 + kslope * C[q];
+      qc64[q * ncp + L.cell] = k;
+      qc32[q * ncp + L.cell] = float(k);
+    }
+    if (beta) {
+      for (int d = 0; d < 3; ++d) {
+        double B[27];
+        gather64<OCT, false>(ug, og, L, beta + d * nd, B);
+        to_qpoints<double>(B);
+        for (int q = 0; q < 27; ++q) {
+          qv64[(d * 27 + q) * ncp + L.cell] = rhocp * B[q];
+          qv32[(d * 27 + q) * ncp + L.cell] = float(rhocp * B[q]);
+        }
+      }
+    }
+  } else if (kind == K_REINIT) {
+#pragma unroll
+    for (int qc = 0; qc < 3; ++qc)
+#pragma unroll
+      for (int qb = 0; qb < 3; ++qb)
+#pragma unroll
+        for (int qa = 0; qa < 3; ++qa) {
+          const int q = qa + 3 * qb + 9 * qc;
+          double nx, ny, nz;
+          grad_at<double>(C, qa, qb, qc, nx, ny, nz);
+          double nn = sqrt(nx * nx + ny * ny + nz * nz);
+          double inv = nn < 1e-12 ? 0.0 : 1.0 / nn;
+          double n3[3] = {nx * inv, ny * inv, nz * inv};
+          for (int d = 0; d < 3; ++d) {
+            qv64[(d * 27 + q) * ncp + L.cell] = n3[d];
+            qv32[(d * 27 + q) * ncp + L.cell] = float(n3[d]);
+          }
+        }
+  }
+}
+
+__global__ void k_oseen_qtables(UniformGeom ug, const double* phi, const double* beta, double rho_l, double rho_g,
+                                double mu_l, double mu_g, int hv, double eps, double* r64, float* r32, double* m64,
+                                float* m32, double* b64, float* b32) {
+  Loc L;
+  OctGeom og{};
+  const int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (!natural_cell<false>(ug, og, t, L)) return;
+  const int64_t nc = int64_t(ug.nx) * ug.ny * ug.nz;
+  double C[27];
+  gather64<false, false>(ug, og, L, phi, C);
+  to_qpoints<double>(C);
+  for (int q = 0; q < 27; ++q) {
+    double H = heaviside<double>(C[q], hv, eps);
+    double rho = 1.0 / (H / rho_l + (1.0 - H) / rho_g);  // eq. (rhoEff)
+    double mu = H * mu_l + (1.0 - H) * mu_g;              // eq. (muEff)
+    r64[q * nc + L.cell] = rho;
+    r32[q * nc + L.cell] = float(rho);
+    m64[q * nc + L.cell] = mu;
+    m32[q * nc + L.cell] = float(mu);
+  }
+  for (int d = 0; d < 3; ++d) {
+    gather64<false, false>(ug, og, L, beta + d * ug.n_dofs, C);
+    to_qpoints<double>(C);
+    for (int q = 0; q < 27; ++q) {
+      b64[(d * 27 + q) * nc + L.cell] = C[q];
+      b32[(d * 27 + q) * nc + L.cell] = float(C[q]);
+    }
+  }
+}
+
+// ---------------------------------------------------------------- diagonals
+// out[l] += sum_q c[q] X[qa][a] Y[qb][b] Z[qc][c] with 1D tables X, Y, Z (3x3, [q][a]).
+__device__ __forceinline__ void separable_add(const double* c, const double* X, const double* Y, const double* Z,
+                                              double* out) {
+  double t[27];
+#pragma unroll
+  for (int i = 0; i < 27; ++i) t[i] = c[i];
+  // x: t[a, qb, qc] = sum_qa X[qa][a] t[qa, qb, qc]
+#pragma unroll
+  for (int j = 0; j < 9; ++j) {
+    double u0 = t[3 * j], u1 = t[3 * j + 1], u2 = t[3 * j + 2];
+    t[3 * j] = X[0] * u0 + X[3] * u1 + X[6] * u2;
+    t[3 * j + 1] = X[1] * u0 + X[4] * u1 + X[7] * u2;
+    t[3 * j + 2] = X[2] * u0 + X[5] * u1 + X[8] * u2;
+  }
+#pragma unroll
+  for (int j = 0; j < 9; ++j) {
+    const int b = (j % 3) + 9 * (j / 3);
+    double u0 = t[b], u1 = t[b + 3], u2 = t[b + 6];
+    t[b] = Y[0] * u0 + Y[3] * u1 + Y[6] * u2;
+    t[b + 3] = Y[1] * u0 + Y[4] * u1 + Y[7] * u2;
+    t[b + 6] = Y[2] * u0 + Y[5] * u1 + Y[8] * u2;
+  }
+#pragma unroll
+  for (int j = 0; j < 9; ++j) {
+    double u0 = t[j], u1 = t[j + 9], u2 = t[j + 18];
+    out[j] += Z[0] * u0 + Z[3] * u1 + Z[6] * u2;
+    out[j + 9] += Z[1] * u0 + Z[4] * u1 + Z[7] * u2;
+    out[j + 18] += Z[2] * u0 + Z[5] * u1 + Z[8] * u2;
+  }
+}
+
+// Diagonal of the element matrix, summed into diag, for cells without constrained nodes:
+// A_e[l,l] = sum_q w h^3 m N_l^2 + w h (gN_l)^T K (gN_l) + w h^2 N_l c . gN_l
+// with N_l = S_a S_b S_c and reference derivatives S' in one factor.
+template <bool OCT>
+__global__ void k_scalar_diag(ScalarArgs<double> A, int kind, bool beta, UniformGeom ug, OctGeom og, int64_t ncount,
+                              double* diag) {
+  Loc L;
+  int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (t >= ncount) return;
+  if (OCT) t = __ldg(og.order + t);
+  if (!natural_cell<OCT>(ug, og, t, L)) return;
+  const double h = L.h;
+  double out[27], c[27];
+  for (int i = 0; i < 27; ++i) out[i] = 0.0;
+  // mass
+  for (int q = 0; q < 27; ++q) c[q] = cW364[q] * h * h * h * A.mass;
+  separable_add(c, cSS64, cSS64, cSS64, out);
+  if (kind == K_HELM || kind == K_HEAT) {
+    for (int q = 0; q < 27; ++q) c[q] = cW364[q] * h * A.qcoef[q * A.ncp + L.cell];
+    separable_add(c, cSpSp64, cSS64, cSS64, out);
+    separable_add(c, cSS64, cSpSp64, cSS64, out);
+    separable_add(c, cSS64, cSS64, cSpSp64, out);
+  } else if (kind == K_REINIT) {
+    // K = eps n n^T: terms (d, e) with S' in factors d and e
+    for (int d = 0; d < 3; ++d)
+      for (int e = d; e < 3; ++e) {
+        for (int q = 0; q < 27; ++q) {
+          double nd = A.qvec[(d * 27 + q) * A.ncp + L.cell], ne = A.qvec[(e * 27 + q) * A.ncp + L.cell];
+          c[q] = cW364[q] * h * A.eps * nd * ne * (d == e ? 1.0 : 2.0);
+        }
+        const double* F[3] = {cSS64, cSS64, cSS64};
+        if (d == e) F[d] = cSpSp64;
+        else { F[d] = cSSp64; F[e] = cSSp64; }
+        separable_add(c, F[0], F[1], F[2], out);
+      }
+  }
+  if (beta) {
+    for (int d = 0; d < 3; ++d) {
+      for (int q = 0; q < 27; ++q) c[q] = cW364[q] * h * h * A.qvec[(d * 27 + q) * A.ncp + L.cell];
+      const double* F[3] = {cSS64, cSS64, cSS64};
+      F[d] = cSSp64;
+      separable_add(c, F[0], F[1], F[2], out);
+    }
+  }
+  if (OCT) {
+    for (int l = 0; l < 27; ++l) {
+      int32_t id = __ldg(og.cmap + l * og.ncp + L.cell);
+      if (!(og.dflag && og.dflag[id])) atomicAdd(diag + id, out[l]);
+    }
+  } else {
+    for (int l = 0; l < 27; ++l) {
+      if ((L.dmask >> l) & 1u) continue;
+      const int a = l % 3, b = (l / 3) % 3, cc = l / 9;
+      atomicAdd(diag + L.base + a + ug.sx * b + ug.sy * cc, out[l]);
+    }
+  }
+}
+
+// Cells with constrained nodes: dense element matrix from unit vectors, then
+// diag_j += sum_{l,l'} C[l][j] A_e[l][l'] C[l'][j] over the free DoFs j the cell touches.
+template <int KIND, bool BETA>
+__global__ void k_scalar_diag_constrained(ScalarArgs<double> A, OctGeom og, int64_t first, int64_t count,
+                                          double* diag) {
+  const int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (t >= count) return;
+  const int64_t cell = __ldg(og.order + first + t);
+  const double h = og.h0 / double(1 << og.level[cell]);
+  const double mh2 = A.mass * h * h;
+  double C[27];
+  if (KIND != K_REINIT)
+    for (int q = 0; q < 27; ++q) C[q] = A.qcoef[q * A.ncp + cell];
+  double Ae[27][27];
+  for (int l = 0; l < 27; ++l) {
+    double U[27], R[27];
+    for (int i = 0; i < 27; ++i) U[i] = i == l ? 1.0 : 0.0;
+    scalar_local<double, KIND, 1, BETA, false>(A, cell, h, mh2, C, U, R);
+    for (int i = 0; i < 27; ++i) Ae[i][l] = R[i];
+  }
+  for (int l = 0; l < 27; ++l) {
+    int32_t id = og.cmap[l * og.ncp + cell];
+    int eb = 0, ee = 1;
+    if (id < 0) { eb = og.rowptr[-1 - id]; ee = og.rowptr[-id]; }
+    for (int e = eb; e < ee; ++e) {
+      const int32_t j = id >= 0 ? id : og.cols[e];
+      const double wj = id >= 0 ? 1.0 : og.w64[e];
+      if (og.dflag && og.dflag[j]) continue;
+      double acc = 0.0;
+      for (int l2 = 0; l2 < 27; ++l2) {
+        int32_t id2 = og.cmap[l2 * og.ncp + cell];
+        if (id2 >= 0) {
+          if (id2 == j) acc += Ae[l][l2];
+        } else {
+          for (int e2 = og.rowptr[-1 - id2]; e2 < og.rowptr[-id2]; ++e2)
+            if (og.cols[e2] == j) acc += Ae[l][l2] * og.w64[e2];
+        }
+      }
+      atomicAdd(diag + j, wj * acc);
+    }
+  }
+}
+
+__global__ void k_set_dirichlet(double* v, const int32_t* list, int64_t n, double val, int stride) {
+  int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (t < n) v[int64_t(list[t]) * stride] = val;
+}
+
+// Oseen block-Jacobi: 3x3 nodal velocity blocks of A_uu and the pressure scaling.
+__global__ void k_oseen_blocks(OseenArgs<double> A, UniformGeom ug, double* blk, double* pm, double* pk) {
+  Loc L;
+  OctGeom og{};
+  const int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (!natural_cell<false>(ug, og, t, L)) return;
+  const int64_t nc = int64_t(ug.nx) * ug.ny * ug.nz;
+  const double h = L.h;
+  double s[27], c[27];
+  for (int i = 0; i < 27; ++i) s[i] = 0.0;
+  // scalar part: sigma rho mass + rho convection + mu |grad|^2
+  for (int q = 0; q < 27; ++q) c[q] = cW364[q] * h * h * h * A.sigma * A.rho[q * nc + L.cell];
+  separable_add(c, cSS64, cSS64, cSS64, s);
+  for (int d = 0; d < 3; ++d) {
+    for (int q = 0; q < 27; ++q) c[q] = cW364[q] * h * h * A.rho[q * nc + L.cell] * A.beta[(d * 27 + q) * nc + L.cell];
+    const double* F[3] = {cSS64, cSS64, cSS64};
+    F[d] = cSSp64;
+    separable_add(c, F[0], F[1], F[2], s);
+  }
+  for (int q = 0; q < 27; ++q) c[q] = cW364[q] * h * A.mu[q * nc + L.cell];
+  double X[6][27];
+  for (int i = 0; i < 6; ++i)
+    for (int l = 0; l < 27; ++l) X[i][l] = 0.0;
+  separable_add(c, cSpSp64, cSS64, cSS64, X[0]);  // xx
+  separable_add(c, cSS64, cSpSp64, cSS64, X[1]);  // yy
+  separable_add(c, cSS64, cSS64, cSpSp64, X[2]);  // zz
+  separable_add(c, cSSp64, cSSp64, cSS64, X[3]);  // xy
+  separable_add(c, cSSp64, cSS64, cSSp64, X[4]);  // xz
+  separable_add(c, cSS64, cSSp64, cSSp64, X[5]);  // yz
+  for (int l = 0; l < 27; ++l) {
+    if ((L.dmask >> l) & 1u) continue;
+    const int a = l % 3, b = (l / 3) % 3, cc = l / 9;
+    const int64_t id = L.base + a + ug.sx * b + ug.sy * cc;
+    const double lap = X[0][l] + X[1][l] + X[2][l];
+    // B[c][d] = delta_cd (s + mu |grad N|^2) + mu d_d N d_c N
+    double B[9] = {s[l] + lap + X[0][l], X[3][l], X[4][l],
+                   X[3][l], s[l] + lap + X[1][l], X[5][l],
+                   X[4][l], X[5][l], s[l] + lap + X[2][l]};
+    for (int e = 0; e < 9; ++e) atomicAdd(blk + id * 9 + e, B[e]);
+  }
+  // pressure: sum_q w h^3 psi_i^2 / mu and sum_q w h |grad psi_i|^2 / (sigma rho)
+  const int64_t px = ug.nx + 1, pxy = px * (ug.ny + 1);
+  const int64_t pbase = L.i + px * (L.j + (ug.ny + 1) * int64_t(L.k));
+  for (int n = 0; n < 8; ++n) {
+    const int a = n & 1, b = (n >> 1) & 1, cc = n >> 2;
+    double m = 0.0, kk = 0.0;
+    for (int q = 0; q < 27; ++q) {
+      const int qa = q % 3, qb = (q / 3) % 3, qc = q / 9;
+      const double pa = cP64[2 * qa + a], pb = cP64[2 * qb + b], pc = cP64[2 * qc + cc];
+      const double psi = pa * pb * pc;
+      const double g2 = pb * pb * pc * pc + pa * pa * pc * pc + pa * pa * pb * pb;  // |psi'|^2 with P' = -+1
+      m += cW364[q] * h * h * h * psi * psi / A.mu[q * nc + L.cell];
+      kk += cW364[q] * h * g2 / (A.sigma * A.rho[q * nc + L.cell]);
+    }
+    const int64_t id = pbase + a + px * b + pxy * cc;
+    atomicAdd(pm + id, m);
+    atomicAdd(pk + id, kk);
+  }
+}
+
+__global__ void k_invert_blocks(double* blk, const uint8_t* dir, int64_t n) {
+  int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double* B = blk + 9 * i;
+  if (dir && dir[i]) {
+    for (int e = 0; e < 9; ++e) B[e] = (e % 4 == 0) ? 1.0 : 0.0;
+    return;
+  }
+  double a = B[0], b = B[1], c = B[2], d = B[3], e = B[4], f = B[5], g = B[6], hh = B[7], k = B[8];
+  double A0 = e * k - f * hh, A1 = -(d * k - f * g), A2 = d * hh - e * g;
+  double det = a * A0 + b * A1 + c * A2;
+  double inv = 1.0 / det;
+  B[0] = A0 * inv; B[1] = -(b * k - c * hh) * inv; B[2] = (b * f - c * e) * inv;
+  B[3] = A1 * inv; B[4] = (a * k - c * g) * inv; B[5] = -(a * f - c * d) * inv;
+  B[6] = A2 * inv; B[7] = -(a * hh - b * g) * inv; B[8] = (a * e - b * d) * inv;
+}
+
+__global__ void k_pressure_scaling(const double* pm, const double* pk, double* pinv, int64_t n) {
+  int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  // Schur complement diagonal ~ (1/pm + 1/pk)^-1; store its inverse
+  pinv[i] = 1.0 / pm[i] + 1.0 / pk[i];
+}
+
+// ---------------------------------------------------------------- laser load
+__global__ void k_laser(UniformGeom ug, double lox, double loy, double P, double r, double x0, double y0, double chi,
+                        double* f, double* dF) {
+  const int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (t >= int64_t(ug.nx) * ug.ny) return;
+  const int i = int(t % ug.nx), j = int(t / ug.nx), k = ug.nz - 1;
+  const double h = ug.h;
+  const double ox = lox + i * h, oy = loy + j * h;
+  double fe[5][9];
+  for (int p = 0; p < 5; ++p)
+    for (int n = 0; n < 9; ++n) fe[p][n] = 0.0;
+  const double pi = 3.141592653589793;
+  for (int qb = 0; qb < 3; ++qb)
+    for (int qa = 0; qa < 3; ++qa) {
+      const double x = ox + h * cG64[qa], y = oy + h * cG64[qb];
+      const double r2 = (x - x0) * (x - x0) + (y - y0) * (y - y0);
+      const double q = 2.0 * chi * P / (pi * r * r) * exp(-2.0 * r2 / (r * r));
+      const double dq[5] = {q, q / P, q * (-2.0 / r + 4.0 * r2 / (r * r * r)), 4.0 * q * (x - x0) / (r * r),
+                            4.0 * q * (y - y0) / (r * r)};
+      const double w = cW64[qa] * cW64[qb] * h * h;
+      for (int b = 0; b < 3; ++b)
+        for (int a = 0; a < 3; ++a) {
+          const double N = cS64[3 * qa + a] * cS64[3 * qb + b];
+          for (int p = 0; p < 5; ++p) fe[p][a + 3 * b] += w * dq[p] * N;
+        }
+    }
+  const uint32_t dmask = dirichlet_mask(ug, i, j, k);
+  const int64_t base = 2 * int64_t(i) + ug.sx * (2 * int64_t(j)) + ug.sy * (2 * int64_t(k) + 2);
+  for (int b = 0; b < 3; ++b)
+    for (int a = 0; a < 3; ++a) {
+      if ((dmask >> (a + 3 * b + 18)) & 1u) continue;
+      const int64_t id = base + a + ug.sx * b;
+      atomicAdd(f + id, fe[0][a + 3 * b]);
+      if (dF)
+        for (int p = 1; p < 5; ++p) atomicAdd(dF + (p - 1) * ug.n_dofs + id, fe[p][a + 3 * b]);
+    }
+}
+
+// dJ/dk_q = -lambda^T (dA/dk_q) theta = -w_q h grad_ref(lambda) . grad_ref(theta)
+__global__ void k_grad_kq(UniformGeom ug, const double* lam, const double* th, double* out) {
+  Loc L;
+  OctGeom og{};
+  const int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (!natural_cell<false>(ug, og, t, L)) return;
+  double U[27], V[27];
+  gather_uniform<double>(lam, L.base, ug.sx, ug.sy, 0u, U);
+  gather_uniform<double>(th, L.base, ug.sx, ug.sy, 0u, V);
+  to_qpoints<double>(U);
+  to_qpoints<double>(V);
+#pragma unroll
+  for (int qc = 0; qc < 3; ++qc)
+#pragma unroll
+    for (int qb = 0; qb < 3; ++qb)
+#pragma unroll
+      for (int qa = 0; qa < 3; ++qa) {
+        const int q = qa + 3 * qb + 9 * qc;
+        double ax, ay, az, bx, by, bz;
+        grad_at<double>(U, qa, qb, qc, ax, ay, az);
+        grad_at<double>(V, qa, qb, qc, bx, by, bz);
+        out[L.cell * 27 + q] = -cW364[q] * L.h * (ax * bx + ay * by + az * bz);
+      }
+}
+
+inline int blocks(int64_t n, int b) { return int((n + b - 1) / b); }
+
+}  // namespace
+
+mf_status launch_scalar_qtables(mf_ctx* ctx, const mf_dofmap* m, int kind, const double* field, const double* kq_user,
+                                const double* beta, double k0, double k_slope, double a_l, double a_g, int hv,
+                                double eps, double rhocp, double* qc64, float* qc32, double* qv64, float* qv32) {
+  MF_CUDA_TRY(upload_tables_here());
+  UniformGeom ug = m->uniform ? uniform_geom(m) : UniformGeom{};
+  OctGeom og = oct_geom(m);
+  const int64_t ncp = m->n_cells;
+  if (m->uniform)
+    k_scalar_qtables<false><<<blocks(m->n_cells, 128), 128, 0, ctx->stream>>>(
+        ug, og, kind, field, kq_user, beta, m->n_dofs, k0, k_slope, a_l, a_g, hv, eps, rhocp, ncp, qc64, qc32, qv64, qv32);
+  else
+    k_scalar_qtables<true><<<blocks(m->n_cells, 128), 128, 0, ctx->stream>>>(
+        ug, og, kind, field, kq_user, beta, m->n_dofs, k0, k_slope, a_l, a_g, hv, eps, rhocp, ncp, qc64, qc32, qv64, qv32);
+  ctx->launches++;
+  MF_CUDA_TRY(cudaGetLastError());
+  return MF_OK;
+}
+
+mf_status launch_oseen_qtables(mf_ctx* ctx, const mf_dofmap* mu, const double* phi, const double* beta, double rho_l,
+                               double rho_g, double mu_l, double mu_g, int hv, double eps, double* r64, float* r32,
+                               double* m64, float* m32, double* b64, float* b32) {
+  MF_CUDA_TRY(upload_tables_here());
+  UniformGeom ug = uniform_geom(mu);
+  k_oseen_qtables<<<blocks(mu->n_cells, 128), 128, 0, ctx->stream>>>(ug, phi, beta, rho_l, rho_g, mu_l, mu_g, hv, eps,
+                                                                      r64, r32, m64, m32, b64, b32);
+  ctx->launches++;
+  MF_CUDA_TRY(cudaGetLastError());
+  return MF_OK;
+}
+
+mf_status launch_scalar_diag(mf_ctx* ctx, const mf_dofmap* m, int kind, bool beta, const ScalarArgs<double>& a,
+                             double* diag) {
+  MF_CUDA_TRY(upload_tables_here());
+  MF_CUDA_TRY(cudaMemsetAsync(diag, 0, sizeof(double) * m->n_dofs, ctx->stream));
+  UniformGeom ug = m->uniform ? uniform_geom(m) : UniformGeom{};
+  OctGeom og = oct_geom(m);
+  const int64_t nfree = m->uniform ? m->n_cells : m->n_unconstrained;
+  if (m->uniform)
+    k_scalar_diag<false><<<blocks(nfree, 128), 128, 0, ctx->stream>>>(a, kind, beta, ug, og, nfree, diag);
+  else if (nfree > 0)
+    k_scalar_diag<true><<<blocks(nfree, 128), 128, 0, ctx->stream>>>(a, kind, beta, ug, og, nfree, diag);
+  ctx->launches++;
+  MF_CUDA_TRY(cudaGetLastError());
+  if (!m->uniform && m->n_constrained_cells > 0) {
+    const int64_t nc = m->n_constrained_cells;
+    if (beta) return fail(MF_EUNSUPPORTED, "convection on hanging-node meshes");
+    switch (kind) {
+      case K_HELM: k_scalar_diag_constrained<K_HELM, false><<<blocks(nc, 32), 32, 0, ctx->stream>>>(a, og, nfree, nc, diag); break;
+      case K_HEAT: k_scalar_diag_constrained<K_HEAT, false><<<blocks(nc, 32), 32, 0, ctx->stream>>>(a, og, nfree, nc, diag); break;
+      case K_REINIT: k_scalar_diag_constrained<K_REINIT, false><<<blocks(nc, 32), 32, 0, ctx->stream>>>(a, og, nfree, nc, diag); break;
+      default: return fail(MF_EINVAL, "diagonal of this operator kind");
+    }
+    ctx->launches++;
+    MF_CUDA_TRY(cudaGetLastError());
+  }
+  const int64_t nd = int64_t(m->dirichlet_list.size());
+  if (nd) {
+    k_set_dirichlet<<<blocks(nd, 256), 256, 0, ctx->stream>>>(diag, m->d_dir_list.as<int32_t>(), nd, 1.0, 1);
+    ctx->launches++;
+    MF_CUDA_TRY(cudaGetLastError());
+  }
+  return MF_OK;
+}
+
+mf_status launch_oseen_blockdiag(mf_ctx* ctx, const mf_dofmap* mu, const mf_dofmap* mp, const OseenArgs<double>& a,
+                                 double* blk, double* pdiag) {
+  MF_CUDA_TRY(upload_tables_here());
+  UniformGeom ug = uniform_geom(mu);
+  const int64_t nu = mu->n_dofs, np = mp->n_dofs;
+  DevBuf tmp;
+  MF_TRY(tmp.alloc(sizeof(double) * 2 * np));
+  double* pm = tmp.as<double>();
+  double* pk = pm + np;
+  MF_CUDA_TRY(cudaMemsetAsync(blk, 0, sizeof(double) * 9 * nu, ctx->stream));
+  MF_CUDA_TRY(cudaMemsetAsync(pm, 0, sizeof(double) * 2 * np, ctx->stream));
+  k_oseen_blocks<<<blocks(mu->n_cells, 64), 64, 0, ctx->stream>>>(a, ug, blk, pm, pk);
+  DevBuf dflag;
+  if (!mu->dirichlet_list.empty()) MF_TRY(dflag.upload(mu->dirichlet, ctx->stream));
+  k_invert_blocks<<<blocks(nu, 256), 256, 0, ctx->stream>>>(blk, dflag.as<uint8_t>(), nu);
+  k_pressure_scaling<<<blocks(np, 256), 256, 0, ctx->stream>>>(pm, pk, pdiag, np);
+  ctx->launches += 3;
+  MF_CUDA_TRY(cudaGetLastError());
+  MF_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+  return MF_OK;
+}
+
+mf_status launch_laser(mf_ctx* ctx, const mf_dofmap* m, const double lz[5], double* f, double* dF) {
+  MF_CUDA_TRY(upload_tables_here());
+  if (!m->uniform) return fail(MF_EUNSUPPORTED, "laser load on octree maps");
+  UniformGeom ug = uniform_geom(m);
+  MF_CUDA_TRY(cudaMemsetAsync(f, 0, sizeof(double) * m->n_dofs, ctx->stream));
+  if (dF) MF_CUDA_TRY(cudaMemsetAsync(dF, 0, sizeof(double) * 4 * m->n_dofs, ctx->stream));
+  k_laser<<<blocks(int64_t(ug.nx) * ug.ny, 128), 128, 0, ctx->stream>>>(ug, m->mesh->lo[0], m->mesh->lo[1], lz[0], lz[1],
+                                                                         lz[2], lz[3], lz[4], f, dF);
+  ctx->launches++;
+  MF_CUDA_TRY(cudaGetLastError());
+  return MF_OK;
+}
+
+mf_status launch_grad_kq(mf_ctx* ctx, const mf_dofmap* m, const double* lam, const double* theta, double* out) {
+  MF_CUDA_TRY(upload_tables_here());
+  if (!m->uniform) return fail(MF_EUNSUPPORTED, "k_q gradient on octree maps");
+  UniformGeom ug = uniform_geom(m);
+  k_grad_kq<<<blocks(m->n_cells, 128), 128, 0, ctx->stream>>>(ug, lam, theta, out);
+  ctx->launches++;
+  MF_CUDA_TRY(cudaGetLastError());
+  return MF_OK;
+}
+
+}  // namespace mf

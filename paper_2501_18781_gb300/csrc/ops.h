@@ -1,0 +1,91 @@
+// Operator state and kernel launchers (internal).
+#pragma once
+
+#include "cellops.cuh"
+#include "internal.h"
+
+namespace mf {
+
+enum ScalarKind { K_HELM = 0, K_HEAT = 1, K_REINIT = 2, K_MASS = 3 };
+
+// Arguments of the scalar cell kernels.  Vector fields are in the apply precision T.
+template <typename T> struct ScalarArgs {
+  const T* src;
+  T* dst;
+  int nrhs;
+  int64_t ld;
+  const T* field;   // nodal phi (Helmholtz, reinit) or T^n (heat) for in-kernel coefficients
+  const T* qcoef;   // [27][ncp] scalar coefficient per Gauss point (a, k) when tabulated
+  const T* qvec;    // [3][27][ncp] rho_cp beta (heat) or n (reinit) per Gauss point
+  int64_t ncp;      // stride of the Gauss-point tables (number of cells)
+  T mass;           // value-term coefficient
+  T a_l, a_g;       // Helmholtz: a = a_g + (a_l - a_g) H
+  T k0, k_slope;    // heat: k = k0 + k_slope T
+  T eps;            // reinit diffusion / sine Heaviside width
+  int heaviside;    // 0 tanh, 1 sine
+  // K_MASS only: restrict to cells whose centre lies in a box (|x|,|y| <= bx, z >= bz)
+  int use_box;
+  double box_half, box_zmin, lo[3];
+};
+
+template <typename T> struct OseenArgs {
+  const T* src;
+  T* dst;
+  int64_t nu, np;   // velocity DoFs per component, pressure DoFs
+  const T* rho;     // [27][ncells]
+  const T* mu;      // [27][ncells]
+  const T* beta;    // [3][27][ncells]
+  T sigma;
+};
+
+// scalar apply: kind, coefficient mode (0 in-kernel, 1 tabulated), convection, transpose
+mf_status launch_scalar_apply(mf_ctx* ctx, const mf_dofmap* m, int kind, int mode, bool beta, bool transpose,
+                              bool f32, const void* args);
+mf_status launch_oseen_apply(mf_ctx* ctx, const mf_dofmap* mu, bool f32, const void* args);
+// Gauss-point tables from nodal fp64 fields (always evaluated in fp64, stored in both precisions)
+mf_status launch_scalar_qtables(mf_ctx* ctx, const mf_dofmap* m, int kind, const double* field, const double* kq_user,
+                                const double* beta, double k0, double k_slope, double a_l, double a_g, int heaviside,
+                                double eps, double rhocp, double* qcoef64, float* qcoef32, double* qvec64, float* qvec32);
+mf_status launch_oseen_qtables(mf_ctx* ctx, const mf_dofmap* mu, const double* phi, const double* beta, double rho_l,
+                               double rho_g, double mu_l, double mu_g, int heaviside, double eps, double* rho64,
+                               float* rho32, double* muq64, float* muq32, double* beta64, float* beta32);
+// diagonal (scalar ops) in fp64 from tabulated coefficients
+mf_status launch_scalar_diag(mf_ctx* ctx, const mf_dofmap* m, int kind, bool beta, const ScalarArgs<double>& a,
+                             double* diag);
+// Oseen block-Jacobi: 3x3 velocity blocks (inverted in place) and pressure scaling
+mf_status launch_oseen_blockdiag(mf_ctx* ctx, const mf_dofmap* mu, const mf_dofmap* mp, const OseenArgs<double>& a,
+                                 double* blk, double* pdiag);
+// dst[dir] = src[dir] for nrhs vectors (Dirichlet identity rows)
+mf_status launch_dirichlet_copy(mf_ctx* ctx, const mf_dofmap* m, const void* src, void* dst, int nrhs, int64_t ld,
+                                int64_t offset, bool f32);
+// laser top-face load and its parameter derivatives (uniform maps)
+mf_status launch_laser(mf_ctx* ctx, const mf_dofmap* m, const double lz[5], double* f, double* dF);
+// dJ/dk_q = -w_q h grad(lambda) . grad(theta), [cell][27]
+mf_status launch_grad_kq(mf_ctx* ctx, const mf_dofmap* m, const double* lam, const double* theta, double* out);
+
+}  // namespace mf
+
+struct mf_op {
+  mf_ctx* ctx = nullptr;
+  mf_op_params p{};
+  const mf_dofmap* map[2] = {nullptr, nullptr};
+  int nmaps = 1;
+  int64_t n = 0;        // vector length
+  int64_t ncells = 0;
+  // borrowed nodal fields (fp64)
+  const double* phi = nullptr;
+  const double* tprev = nullptr;
+  const double* beta = nullptr;
+  const double* kq_user = nullptr;
+  // owned copies / tables
+  mf::DevBuf field32;             // float copy of the in-kernel nodal field
+  mf::DevBuf qcoef64, qcoef32;    // [27][ncells]
+  mf::DevBuf qvec64, qvec32;      // [3][27][ncells]
+  mf::DevBuf rho64, rho32, mu64, mu32;  // Oseen
+  mf::DevBuf diag64;              // cached diagonal (fp64)
+  mf::DevBuf blk64, pdiag64;      // Oseen block Jacobi
+  bool tables_ready = false;
+  bool diag_ready = false;
+  int mode64 = 1, mode32 = 0;     // coefficient mode per precision (autotuned)
+  std::string variant;
+};

@@ -1,0 +1,731 @@
+// Krylov solvers on the matrix-free operators (Appendix B: CG for symmetric and GMRES for
+// nonsymmetric systems), Jacobi / Chebyshev / block-Jacobi preconditioning, mixed-precision
+// defect correction, the heat-step adjoint gradient and the apply autotuner.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <vector>
+
+#include "ops.h"
+#include "vec.cuh"
+
+namespace mf {
+
+template <typename T> mf_status apply_impl(mf_op* op, const T* src, T* dst, int nrhs, int64_t ld, bool transpose);
+mf_status diag64(mf_op* op, double** out);
+mf_status check_fields(const mf_op* op);
+mf_status ensure_tables(mf_op* op);
+int scalar_kind(const mf_op* op);
+double value_coef(const mf_op* op);
+template <typename T> ScalarArgs<T> scalar_args(const mf_op* op, const T* src, T* dst, int nrhs, int64_t ld);
+
+namespace {
+
+using clk = std::chrono::steady_clock;
+
+template <typename T> struct Vec {
+  DevBuf b;
+  T* p = nullptr;
+  mf_status alloc(int64_t n) {
+    MF_TRY(b.alloc(sizeof(T) * size_t(n)));
+    p = b.as<T>();
+    return MF_OK;
+  }
+};
+
+mf_status sync_copy(mf_ctx* c, double* host, const double* dev, size_t n) {
+  MF_CUDA_TRY(cudaMemcpyAsync(host, dev, n * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  MF_CUDA_TRY(cudaStreamSynchronize(c->stream));
+  return MF_OK;
+}
+
+// largest eigenvalue of the symmetric tridiagonal (a, b) by Sturm-sequence bisection
+double tridiag_max_eig(const std::vector<double>& a, const std::vector<double>& b) {
+  const int m = int(a.size());
+  double lo = 1e300, hi = -1e300;
+  for (int i = 0; i < m; ++i) {
+    double r = (i > 0 ? std::fabs(b[i - 1]) : 0.0) + (i + 1 < m ? std::fabs(b[i]) : 0.0);
+    lo = std::min(lo, a[i] - r);
+    hi = std::max(hi, a[i] + r);
+  }
+  auto count_below = [&](double x) {  // eigenvalues < x
+    int cnt = 0;
+    double d = 1.0;
+    for (int i = 0; i < m; ++i) {
+      d = a[i] - x - (i > 0 ? b[i - 1] * b[i - 1] / d : 0.0);
+      if (d == 0.0) d = -1e-300;
+      if (d < 0) ++cnt;
+    }
+    return cnt;
+  };
+  for (int it = 0; it < 200 && hi - lo > 1e-14 * std::max(1.0, std::fabs(hi)); ++it) {
+    double mid = 0.5 * (lo + hi);
+    if (count_below(mid) == m) hi = mid;
+    else lo = mid;
+  }
+  return hi;
+}
+
+// Preconditioner in precision T for nrhs vectors: none, Jacobi, Chebyshev (on D^-1 A), or
+// the Oseen block Jacobi.
+template <typename T> struct Prec {
+  mf_op* op = nullptr;
+  int kind = MF_PREC_NONE;
+  int degree = 4;
+  double lmin = 0, lmax = 0;
+  Vec<T> dinv, res, d, Ad;
+  int nrhs = 1;
+
+  mf_status setup(mf_op* o, int k, int deg, double ratio, int lanczos_steps, int nr) {
+    op = o;
+    kind = k;
+    degree = deg;
+    nrhs = nr;
+    const int64_t n = op->n;
+    if (kind == MF_PREC_NONE) return MF_OK;
+    if (kind == MF_PREC_BLOCK_JACOBI) {
+      if (op->p.kind != MF_OP_OSEEN) return fail(MF_EINVAL, "block Jacobi is for the Oseen operator");
+      return diag64(op, nullptr);
+    }
+    if (op->p.kind == MF_OP_OSEEN) return fail(MF_EUNSUPPORTED, "Oseen: use block Jacobi");
+    double* d64;
+    MF_TRY(diag64(op, &d64));
+    Vec<double> inv64;
+    MF_TRY(inv64.alloc(n));
+    // dinv = 1 / diag
+    std::vector<double> ones;
+    MF_TRY(dinv.alloc(n));
+    MF_TRY(reciprocal(d64, inv64.p, n));
+    if (sizeof(T) == 8) MF_CUDA_TRY(cudaMemcpyAsync(dinv.p, inv64.p, sizeof(double) * n, cudaMemcpyDeviceToDevice, op->ctx->stream));
+    else MF_TRY(convert<double, float>(op->ctx, n, inv64.p, reinterpret_cast<float*>(dinv.p)));
+    if (kind == MF_PREC_CHEBYSHEV) {
+      MF_TRY(res.alloc(n * nrhs));
+      MF_TRY(d.alloc(n * nrhs));
+      MF_TRY(Ad.alloc(n * nrhs));
+      double lm;
+      MF_TRY(lanczos(inv64.p, lanczos_steps, &lm));
+      lmax = 1.1 * lm;
+      lmin = lmax / ratio;
+    }
+    return MF_OK;
+  }
+
+  mf_status reciprocal(const double* d, double* out, int64_t n) {
+    // out = 1/d via axpby-free path: copy then invert on device with a tiny helper
+    MF_CUDA_TRY(cudaMemcpyAsync(out, d, sizeof(double) * n, cudaMemcpyDeviceToDevice, op->ctx->stream));
+    return invert_inplace(op->ctx, out, n);
+  }
+
+  static mf_status invert_inplace(mf_ctx* c, double* v, int64_t n);
+
+  // lambda_max of D^-1 A (Lanczos on D^-1/2 A D^-1/2), applies in precision T
+  mf_status lanczos(const double* inv64, int steps, double* out) {
+    mf_ctx* c = op->ctx;
+    const int64_t n = op->n;
+    Vec<double> s, v, vp, w;
+    MF_TRY(s.alloc(n));
+    MF_TRY(v.alloc(n));
+    MF_TRY(vp.alloc(n));
+    MF_TRY(w.alloc(n));
+    Vec<T> tv, tw;
+    MF_TRY(tv.alloc(n));
+    MF_TRY(tw.alloc(n));
+    MF_TRY(sqrt_of(c, inv64, s.p, n));
+    MF_TRY(fill_splitmix(c, 0x5eed5eedull, v.p, n));
+    double* hs = c->host_scalars;
+    double* ds = c->scalars.as<double>() + kScalarsLanczos;
+    MF_TRY(norm2_sq(c, v.p, n, ds));
+    MF_TRY(sync_copy(c, hs, ds, 1));
+    MF_TRY(axpby<double, double>(c, n, 1.0 / std::sqrt(hs[0]), v.p, 0.0, v.p));
+    MF_CUDA_TRY(cudaMemsetAsync(vp.p, 0, sizeof(double) * n, c->stream));
+    std::vector<double> al, be;
+    double beta = 0.0;
+    for (int k = 0; k < steps; ++k) {
+      MF_TRY(scale_mul(c, s.p, v.p, tv.p, n));  // tv = s .* v (in T)
+      MF_TRY(apply_impl<T>(op, tv.p, tw.p, 1, n, false));
+      MF_TRY(scale_mul_back(c, s.p, tw.p, w.p, n));  // w = s .* tw
+      MF_TRY(axpby<double, double>(c, n, -beta, vp.p, 1.0, w.p));
+      MF_TRY(dot<double, double>(c, w.p, v.p, n, ds));
+      MF_TRY(sync_copy(c, hs, ds, 1));
+      const double alpha = hs[0];
+      MF_TRY(axpby<double, double>(c, n, -alpha, v.p, 1.0, w.p));
+      MF_TRY(norm2_sq(c, w.p, n, ds));
+      MF_TRY(sync_copy(c, hs, ds, 1));
+      al.push_back(alpha);
+      beta = std::sqrt(hs[0]);
+      if (beta == 0.0 || !std::isfinite(beta)) break;
+      be.push_back(beta);
+      std::swap(vp.p, v.p);
+      std::swap(vp.b.p, v.b.p);
+      MF_TRY(axpby<double, double>(c, n, 1.0 / beta, w.p, 0.0, v.p));
+    }
+    if (al.empty()) return fail(MF_EINVAL, "Lanczos failed");
+    be.resize(al.size() - 1);
+    *out = tridiag_max_eig(al, be);
+    return MF_OK;
+  }
+
+  static mf_status sqrt_of(mf_ctx* c, const double* in, double* out, int64_t n);
+  static mf_status scale_mul(mf_ctx* c, const double* s, const double* v, T* out, int64_t n);
+  static mf_status scale_mul_back(mf_ctx* c, const double* s, const T* v, double* out, int64_t n);
+
+  // z = P r for nrhs vectors
+  mf_status apply(const T* r, T* z) {
+    mf_ctx* c = op->ctx;
+    const int64_t n = op->n;
+    switch (kind) {
+      case MF_PREC_NONE:
+        MF_CUDA_TRY(cudaMemcpyAsync(z, r, sizeof(T) * n * nrhs, cudaMemcpyDeviceToDevice, c->stream));
+        return MF_OK;
+      case MF_PREC_JACOBI:
+        for (int k = 0; k < nrhs; ++k) MF_TRY(pointwise_mul<T>(c, n, dinv.p, r + k * n, z + k * n));
+        return MF_OK;
+      case MF_PREC_BLOCK_JACOBI: {
+        const int64_t nu = op->map[0]->n_dofs, np = op->map[1]->n_dofs;
+        for (int k = 0; k < nrhs; ++k)
+          MF_TRY(block_jacobi<T>(c, nu, np, op->blk64.as<double>(), op->pdiag64.as<double>(), r + k * n, z + k * n));
+        return MF_OK;
+      }
+      case MF_PREC_CHEBYSHEV: {
+        const double theta = 0.5 * (lmax + lmin), delta = 0.5 * (lmax - lmin), sigma = theta / delta;
+        double rho = 1.0 / sigma;
+        MF_TRY(cheb_init<T>(c, n, n, nrhs, r, dinv.p, 1.0 / theta, res.p, d.p, z));
+        for (int k = 0; k < degree; ++k) {
+          MF_TRY(apply_impl<T>(op, d.p, Ad.p, nrhs, n, false));
+          const double rho_new = 1.0 / (2.0 * sigma - rho);
+          MF_TRY(cheb_step<T>(c, n, n, nrhs, z, res.p, Ad.p, d.p, dinv.p, rho_new * rho, 2.0 * rho_new / delta));
+          rho = rho_new;
+        }
+        return add_into<T>(c, n, n, nrhs, d.p, z);
+      }
+    }
+    return fail(MF_EINVAL, "unknown preconditioner");
+  }
+};
+
+}  // namespace
+
+// small device helpers defined in solver_kernels.cu
+mf_status dev_invert(mf_ctx* c, double* v, int64_t n);
+mf_status dev_sqrt(mf_ctx* c, const double* in, double* out, int64_t n);
+template <typename T> mf_status dev_scale_mul(mf_ctx* c, const double* s, const double* v, T* out, int64_t n);
+template <typename T> mf_status dev_scale_mul_back(mf_ctx* c, const double* s, const T* v, double* out, int64_t n);
+mf_status dev_scale_rhs(mf_ctx* c, const double* in, float* out, const double* scale, int64_t n, int nrhs);
+mf_status dev_add_scaled(mf_ctx* c, const float* d, double* x, const double* scale, int64_t n, int nrhs);
+
+template <typename T> mf_status Prec<T>::invert_inplace(mf_ctx* c, double* v, int64_t n) { return dev_invert(c, v, n); }
+template <typename T> mf_status Prec<T>::sqrt_of(mf_ctx* c, const double* in, double* out, int64_t n) {
+  return dev_sqrt(c, in, out, n);
+}
+template <typename T>
+mf_status Prec<T>::scale_mul(mf_ctx* c, const double* s, const double* v, T* out, int64_t n) {
+  return dev_scale_mul<T>(c, s, v, out, n);
+}
+template <typename T>
+mf_status Prec<T>::scale_mul_back(mf_ctx* c, const double* s, const T* v, double* out, int64_t n) {
+  return dev_scale_mul_back<T>(c, s, v, out, n);
+}
+
+namespace {
+
+// Batched preconditioned CG in precision T from x = 0: nrhs systems stored n apart.
+// Stops each system at ||r_k|| <= tol_r ||b_r|| (recursive residual).
+template <typename T> struct CG {
+  mf_op* op;
+  Prec<T>* P;
+  int nrhs;
+  Vec<T> r, z, p, Ap;
+  int check_every = 1;
+  bool use_graph = false;
+  cudaGraphExec_t exec = nullptr;
+
+  ~CG() {
+    if (exec) cudaGraphExecDestroy(exec);
+  }
+
+  mf_status setup(mf_op* o, Prec<T>* pr, int nr) {
+    op = o;
+    P = pr;
+    nrhs = nr;
+    const int64_t n = op->n * nrhs;
+    MF_TRY(r.alloc(n));
+    MF_TRY(p.alloc(n));
+    MF_TRY(Ap.alloc(n));
+    if (P->kind != MF_PREC_NONE) MF_TRY(z.alloc(n));
+    return MF_OK;
+  }
+
+  mf_status iteration(T* x, double* S) {
+    mf_ctx* c = op->ctx;
+    const int64_t n = op->n;
+    MF_TRY(apply_impl<T>(op, p.p, Ap.p, nrhs, n, false));
+    MF_TRY(cg_alpha<T>(c, p.p, Ap.p, n, n, nrhs, S));
+    if (P->kind == MF_PREC_JACOBI) {
+      MF_TRY(cg_update_xr<T>(c, n, n, nrhs, x, r.p, p.p, Ap.p, P->dinv.p, z.p, 1, S));
+      MF_TRY(cg_update_p<T>(c, n, n, nrhs, z.p, p.p, S));
+    } else if (P->kind == MF_PREC_NONE) {
+      MF_TRY(cg_update_xr<T>(c, n, n, nrhs, x, r.p, p.p, Ap.p, nullptr, nullptr, 0, S));
+      MF_TRY(cg_update_p<T>(c, n, n, nrhs, r.p, p.p, S));
+    } else {
+      MF_TRY(cg_update_xr<T>(c, n, n, nrhs, x, r.p, p.p, Ap.p, nullptr, nullptr, 2, S));
+      MF_TRY(P->apply(r.p, z.p));
+      MF_TRY(cg_rz<T>(c, r.p, z.p, n, n, nrhs, S));
+      MF_TRY(cg_update_p<T>(c, n, n, nrhs, z.p, p.p, S));
+    }
+    return MF_OK;
+  }
+
+  // b, x: nrhs vectors (x overwritten).  rr0[r] = ||b_r||^2 on return; iters, final ||r||/||b||.
+  mf_status solve(const T* b, T* x, double tol, int maxit, int* iters, std::vector<double>& relres) {
+    mf_ctx* c = op->ctx;
+    const int64_t n = op->n;
+    double* S = c->scalars.as<double>();
+    double* hS = c->host_scalars;
+    MF_CUDA_TRY(cudaMemsetAsync(x, 0, sizeof(T) * n * nrhs, c->stream));
+    MF_CUDA_TRY(cudaMemcpyAsync(r.p, b, sizeof(T) * n * nrhs, cudaMemcpyDeviceToDevice, c->stream));
+    T* zz = P->kind == MF_PREC_NONE ? r.p : z.p;
+    if (P->kind != MF_PREC_NONE) MF_TRY(P->apply(r.p, z.p));
+    MF_CUDA_TRY(cudaMemcpyAsync(p.p, zz, sizeof(T) * n * nrhs, cudaMemcpyDeviceToDevice, c->stream));
+    for (int k = 0; k < nrhs; ++k) hS[k * S_NSCAL + S_ACTIVE] = 1.0;
+    // active flags first, then r.r and r.z
+    for (int k = 0; k < nrhs; ++k)
+      MF_CUDA_TRY(cudaMemcpyAsync(S + k * S_NSCAL + S_ACTIVE, hS + k * S_NSCAL + S_ACTIVE, sizeof(double),
+                                  cudaMemcpyHostToDevice, c->stream));
+    MF_TRY(cg_init_scalars<T>(c, r.p, zz, n, n, nrhs, S));
+    MF_TRY(sync_copy(c, hS, S, size_t(nrhs) * S_NSCAL));
+    std::vector<double> bb(nrhs), rr(nrhs);
+    std::vector<char> done(nrhs, 0);
+    relres.assign(nrhs, 0.0);
+    int ndone = 0;
+    for (int k = 0; k < nrhs; ++k) {
+      bb[k] = hS[k * S_NSCAL + S_RR];
+      if (bb[k] == 0.0) {
+        done[k] = 1;
+        ++ndone;
+        hS[k * S_NSCAL + S_ACTIVE] = 0.0;
+        MF_CUDA_TRY(cudaMemcpyAsync(S + k * S_NSCAL + S_ACTIVE, hS + k * S_NSCAL + S_ACTIVE, sizeof(double),
+                                    cudaMemcpyHostToDevice, c->stream));
+      }
+    }
+    int it = 0;
+    if (use_graph && !exec) {
+      cudaGraph_t g;
+      MF_CUDA_TRY(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
+      mf_status st = MF_OK;
+      for (int k = 0; k < check_every && st == MF_OK; ++k) st = iteration(x, S);
+      cudaError_t e = cudaStreamEndCapture(c->stream, &g);
+      if (st != MF_OK) return st;
+      if (e != cudaSuccess) return fail(MF_ECUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+      e = cudaGraphInstantiate(&exec, g, 0);
+      cudaGraphDestroy(g);
+      if (e != cudaSuccess) return fail(MF_ECUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
+    }
+    while (ndone < nrhs && it < maxit) {
+      if (exec) {
+        MF_CUDA_TRY(cudaGraphLaunch(exec, c->stream));
+        c->launches++;
+      } else {
+        for (int k = 0; k < check_every; ++k) MF_TRY(iteration(x, S));
+      }
+      it += check_every;
+      MF_TRY(sync_copy(c, hS, S, size_t(nrhs) * S_NSCAL));
+      for (int k = 0; k < nrhs; ++k) {
+        if (done[k]) continue;
+        const double rk = hS[k * S_NSCAL + S_RR];
+        if (!std::isfinite(rk)) return fail(MF_ENOTCONV, "CG breakdown (non-finite residual)");
+        if (rk <= tol * tol * bb[k]) {
+          done[k] = 1;
+          ++ndone;
+          hS[k * S_NSCAL + S_ACTIVE] = 0.0;
+          MF_CUDA_TRY(cudaMemcpyAsync(S + k * S_NSCAL + S_ACTIVE, hS + k * S_NSCAL + S_ACTIVE, sizeof(double),
+                                      cudaMemcpyHostToDevice, c->stream));
+        }
+      }
+    }
+    MF_CUDA_TRY(cudaStreamSynchronize(c->stream));
+    for (int k = 0; k < nrhs; ++k) relres[k] = bb[k] > 0 ? std::sqrt(hS[k * S_NSCAL + S_RR] / bb[k]) : 0.0;
+    *iters = it;
+    return ndone == nrhs ? MF_OK : MF_ENOTCONV;
+  }
+};
+
+// true residual ||b - A x|| / ||b|| per RHS in fp64 (r receives b - A x)
+mf_status true_residual(mf_op* op, const double* b, const double* x, double* r, int nrhs, std::vector<double>& rel,
+                        std::vector<double>* rnorm = nullptr) {
+  mf_ctx* c = op->ctx;
+  const int64_t n = op->n;
+  MF_TRY(apply_impl<double>(op, x, r, nrhs, n, false));
+  rel.assign(nrhs, 0.0);
+  if (rnorm) rnorm->assign(nrhs, 0.0);
+  double* ds = c->scalars.as<double>() + kScalarsResid;
+  for (int k = 0; k < nrhs; ++k) {
+    MF_TRY(axpby<double, double>(c, n, 1.0, b + k * n, -1.0, r + k * n));
+    MF_TRY(norm2_sq(c, r + k * n, n, ds + 2 * k));
+    MF_TRY(norm2_sq(c, b + k * n, n, ds + 2 * k + 1));
+  }
+  std::vector<double> h(2 * nrhs);
+  MF_TRY(sync_copy(c, h.data(), ds, 2 * nrhs));
+  for (int k = 0; k < nrhs; ++k) {
+    rel[k] = h[2 * k + 1] > 0 ? std::sqrt(h[2 * k] / h[2 * k + 1]) : 0.0;
+    if (rnorm) (*rnorm)[k] = std::sqrt(h[2 * k]);
+  }
+  return MF_OK;
+}
+
+// Restarted GMRES(m), right preconditioning, classical Gram-Schmidt with one
+// reorthogonalisation (CGS2), Givens rotations on the host.  fp64, one RHS.
+mf_status gmres(mf_op* op, Prec<double>& P, const double* b, double* x, int m, double tol, int maxit, bool transpose,
+                int* iters, double* relres) {
+  mf_ctx* c = op->ctx;
+  const int64_t n = op->n;
+  Vec<double> V, t, r;
+  MF_TRY(V.alloc(n * (m + 1)));
+  MF_TRY(t.alloc(n));
+  MF_TRY(r.alloc(n));
+  double* dh = c->scalars.as<double>() + kScalarsGmres;  // room for 2 (m+1) <= 128 values
+  if (2 * (m + 1) > 128) return fail(MF_EINVAL, "GMRES restart too long (max 63)");
+  double* hh = c->host_scalars + kScalarsGmres;
+  MF_CUDA_TRY(cudaMemsetAsync(x, 0, sizeof(double) * n, c->stream));
+  MF_TRY(norm2_sq(c, b, n, dh));
+  MF_TRY(sync_copy(c, hh, dh, 1));
+  const double bn = std::sqrt(hh[0]);
+  *iters = 0;
+  if (bn == 0.0) {
+    *relres = 0.0;
+    return MF_OK;
+  }
+  MF_CUDA_TRY(cudaMemcpyAsync(r.p, b, sizeof(double) * n, cudaMemcpyDeviceToDevice, c->stream));
+  double beta = bn;
+  int it = 0;
+  std::vector<double> H((m + 1) * m), cs(m), sn(m), g(m + 1), y(m);
+  while (it < maxit) {
+    MF_TRY(axpby<double, double>(c, n, 1.0 / beta, r.p, 0.0, V.p));
+    std::fill(g.begin(), g.end(), 0.0);
+    g[0] = beta;
+    int j = 0;
+    bool conv = false;
+    for (; j < m && it < maxit; ++j) {
+      double* w = V.p + (j + 1) * n;
+      MF_TRY(P.apply(V.p + j * n, t.p));
+      MF_TRY(apply_impl<double>(op, t.p, w, 1, n, transpose));
+      MF_TRY(multidot(c, V.p, n, j + 1, w, n, dh));
+      MF_TRY(multiaxpy(c, V.p, n, j + 1, dh, -1.0, w, n));
+      MF_TRY(multidot(c, V.p, n, j + 1, w, n, dh + (m + 1)));
+      MF_TRY(multiaxpy(c, V.p, n, j + 1, dh + (m + 1), -1.0, w, n));
+      MF_TRY(norm2_sq(c, w, n, dh + 2 * (m + 1) - 1));
+      MF_TRY(sync_copy(c, hh, dh, 2 * (m + 1)));
+      for (int i = 0; i <= j; ++i) H[i * m + j] = hh[i] + hh[(m + 1) + i];
+      double hn = std::sqrt(hh[2 * (m + 1) - 1]);
+      H[(j + 1) * m + j] = hn;
+      if (hn > 0) MF_TRY(axpby<double, double>(c, n, 1.0 / hn, w, 0.0, w));
+      for (int i = 0; i < j; ++i) {
+        double tmp = cs[i] * H[i * m + j] + sn[i] * H[(i + 1) * m + j];
+        H[(i + 1) * m + j] = -sn[i] * H[i * m + j] + cs[i] * H[(i + 1) * m + j];
+        H[i * m + j] = tmp;
+      }
+      double den = std::hypot(H[j * m + j], H[(j + 1) * m + j]);
+      cs[j] = H[j * m + j] / den;
+      sn[j] = H[(j + 1) * m + j] / den;
+      H[j * m + j] = den;
+      H[(j + 1) * m + j] = 0.0;
+      g[j + 1] = -sn[j] * g[j];
+      g[j] = cs[j] * g[j];
+      ++it;
+      if (std::fabs(g[j + 1]) <= tol * bn || hn == 0.0) {
+        ++j;
+        conv = true;
+        break;
+      }
+    }
+    // y = H^-1 g (upper triangular), x += M^-1 V y
+    for (int i = j - 1; i >= 0; --i) {
+      double s = g[i];
+      for (int k = i + 1; k < j; ++k) s -= H[i * m + k] * y[k];
+      y[i] = s / H[i * m + i];
+    }
+    for (int i = 0; i < j; ++i) hh[i] = y[i];
+    MF_CUDA_TRY(cudaMemcpyAsync(dh, hh, sizeof(double) * j, cudaMemcpyHostToDevice, c->stream));
+    MF_CUDA_TRY(cudaMemsetAsync(r.p, 0, sizeof(double) * n, c->stream));
+    MF_TRY(multiaxpy(c, V.p, n, j, dh, 1.0, r.p, n));
+    MF_TRY(P.apply(r.p, t.p));
+    MF_TRY(axpby<double, double>(c, n, 1.0, t.p, 1.0, x));
+    // true residual
+    MF_TRY(apply_impl<double>(op, x, r.p, 1, n, transpose));
+    MF_TRY(axpby<double, double>(c, n, 1.0, b, -1.0, r.p));
+    MF_TRY(norm2_sq(c, r.p, n, dh));
+    MF_TRY(sync_copy(c, hh, dh, 1));
+    beta = std::sqrt(hh[0]);
+    *relres = beta / bn;
+    if (!std::isfinite(beta)) return fail(MF_ENOTCONV, "GMRES breakdown (non-finite residual)");
+    if (beta <= tol * bn) break;
+    (void)conv;
+  }
+  *iters = it;
+  return *relres <= tol ? MF_OK : MF_ENOTCONV;
+}
+
+}  // namespace
+
+mf_status solve_impl(mf_op* op, const mf_solver_params* sp, const double* b, double* x, int nrhs, mf_solve_info* info,
+                     bool transpose) {
+  auto t0 = clk::now();
+  mf_ctx* c = op->ctx;
+  const int64_t n = op->n;
+  MF_TRY(check_fields(op));
+  mf_solve_info inf{};
+  mf_status st = MF_OK;
+  const double tol = sp->tol > 0 ? sp->tol : 1e-10;
+  const int maxit = sp->maxit > 0 ? sp->maxit : 5000;
+  const int lsteps = sp->lanczos_steps > 0 ? sp->lanczos_steps : 20;
+  const double ratio = sp->cheby_ratio > 0 ? sp->cheby_ratio : 30.0;
+  const int deg = sp->cheby_degree > 0 ? sp->cheby_degree : 4;
+  std::vector<double> rel;
+  if (sp->solver == MF_SOLVER_CG) {
+    if (transpose && op->p.kind == MF_OP_HEAT && op->beta) return fail(MF_EINVAL, "CG on a nonsymmetric operator");
+    Prec<double> P;
+    MF_TRY(P.setup(op, sp->precond, deg, ratio, lsteps, nrhs));
+    inf.lambda_max = P.lmax;
+    CG<double> cg;
+    MF_TRY(cg.setup(op, &P, nrhs));
+    cg.use_graph = sp->use_graph != 0;
+    int its = 0, total = 0;
+    // restart from the true residual if the recursion drifted (at most 3 times)
+    Vec<double> rt, e;
+    MF_TRY(rt.alloc(n * nrhs));
+    MF_TRY(e.alloc(n * nrhs));
+    st = cg.solve(b, x, tol, maxit, &its, rel);
+    total += its;
+    for (int rs = 0; rs < 3 && (st == MF_OK); ++rs) {
+      std::vector<double> rn;
+      MF_TRY(true_residual(op, b, x, rt.p, nrhs, rel, &rn));
+      double worst = *std::max_element(rel.begin(), rel.end());
+      if (worst <= tol) break;
+      // correction: solve A e = r with the tolerance that brings ||b - A x|| under tol ||b||
+      double tol2 = 1.0;
+      for (int k = 0; k < nrhs; ++k)
+        if (rel[k] > 0) tol2 = std::min(tol2, 0.5 * tol / rel[k]);
+      st = cg.solve(rt.p, e.p, tol2, maxit - total, &its, rel);
+      total += its;
+      MF_TRY(axpby<double, double>(c, n * nrhs, 1.0, e.p, 1.0, x));
+    }
+    MF_TRY(true_residual(op, b, x, rt.p, nrhs, rel));
+    inf.iterations = total;
+  } else if (sp->solver == MF_SOLVER_GMRES) {
+    Prec<double> P;
+    MF_TRY(P.setup(op, sp->precond, deg, ratio, lsteps, 1));
+    inf.lambda_max = P.lmax;
+    const int m = sp->restart > 0 ? sp->restart : 50;
+    rel.assign(nrhs, 0.0);
+    for (int k = 0; k < nrhs; ++k) {
+      int its = 0;
+      double rr = 0;
+      mf_status s2 = gmres(op, P, b + k * n, x + k * n, m, tol, maxit, transpose, &its, &rr);
+      if (s2 != MF_OK && s2 != MF_ENOTCONV) return s2;
+      if (s2 == MF_ENOTCONV) st = s2;
+      inf.iterations += its;
+      rel[k] = rr;
+    }
+  } else if (sp->solver == MF_SOLVER_DEFECT_CORRECTION) {
+    if (sp->inner_dtype != MF_F32) return fail(MF_EUNSUPPORTED, "inner precision must be MF_F32");
+    if (op->p.kind == MF_OP_OSEEN) return fail(MF_EUNSUPPORTED, "defect correction uses CG: symmetric operators");
+    Prec<float> P;
+    MF_TRY(P.setup(op, sp->precond, deg, ratio, lsteps, nrhs));
+    inf.lambda_max = P.lmax;
+    CG<float> cg;
+    MF_TRY(cg.setup(op, &P, nrhs));
+    cg.use_graph = sp->use_graph != 0;
+    cg.check_every = 1;
+    Vec<double> r;
+    Vec<float> r32, d32;
+    MF_TRY(r.alloc(n * nrhs));
+    MF_TRY(r32.alloc(n * nrhs));
+    MF_TRY(d32.alloc(n * nrhs));
+    double* dscale = c->scalars.as<double>() + kScalarsScale;
+    MF_CUDA_TRY(cudaMemsetAsync(x, 0, sizeof(double) * n * nrhs, c->stream));
+    MF_CUDA_TRY(cudaMemcpyAsync(r.p, b, sizeof(double) * n * nrhs, cudaMemcpyDeviceToDevice, c->stream));
+    std::vector<double> rn(nrhs), bnorm(nrhs);
+    {
+      std::vector<double> rl;
+      MF_TRY(true_residual(op, b, x, r.p, nrhs, rl, &bnorm));  // x = 0: r = b
+    }
+    const double itol = sp->inner_tol > 0 ? sp->inner_tol : 1e-4;
+    const int imax = sp->inner_maxit > 0 ? sp->inner_maxit : 100;
+    int outer = 0;
+    rel.assign(nrhs, 1.0);
+    while (outer < maxit) {
+      if (*std::max_element(rel.begin(), rel.end()) <= tol) break;
+      for (int k = 0; k < nrhs; ++k) rn[k] = rel[k] * bnorm[k];
+      // inner fp32 solve on the unit-norm residual
+      std::vector<double> sc(nrhs);
+      for (int k = 0; k < nrhs; ++k) sc[k] = rn[k] > 0 ? 1.0 / rn[k] : 0.0;
+      MF_CUDA_TRY(cudaMemcpyAsync(dscale, sc.data(), sizeof(double) * nrhs, cudaMemcpyHostToDevice, c->stream));
+      MF_TRY(dev_scale_rhs(c, r.p, r32.p, dscale, n, nrhs));
+      int its = 0;
+      std::vector<double> irel;
+      mf_status si = cg.solve(r32.p, d32.p, itol, imax, &its, irel);
+      if (si != MF_OK && si != MF_ENOTCONV) return si;
+      inf.iterations += its;
+      for (int k = 0; k < nrhs; ++k) sc[k] = rn[k];
+      MF_CUDA_TRY(cudaMemcpyAsync(dscale, sc.data(), sizeof(double) * nrhs, cudaMemcpyHostToDevice, c->stream));
+      MF_TRY(dev_add_scaled(c, d32.p, x, dscale, n, nrhs));
+      ++outer;
+      MF_TRY(true_residual(op, b, x, r.p, nrhs, rel));
+    }
+    inf.outer_iterations = outer;
+    if (*std::max_element(rel.begin(), rel.end()) > tol) st = MF_ENOTCONV;
+  } else {
+    return fail(MF_EINVAL, "unknown solver");
+  }
+  MF_CUDA_TRY(cudaStreamSynchronize(c->stream));
+  inf.rel_residual = rel.empty() ? 0.0 : *std::max_element(rel.begin(), rel.end());
+  inf.seconds = std::chrono::duration<double>(clk::now() - t0).count();
+  if (info) *info = inf;
+  if (st == MF_ENOTCONV) return fail(MF_ENOTCONV, "solver did not reach the tolerance within maxit");
+  return st;
+}
+
+}  // namespace mf
+
+using namespace mf;
+
+extern "C" {
+
+mf_status mf_solve(mf_op* op, const mf_solver_params* sp, const double* b, double* x, int nrhs, mf_solve_info* info) {
+  try {
+    if (!op || !sp || !b || !x) return fail(MF_EINVAL, "NULL argument");
+    if (nrhs < 1 || nrhs > 64) return fail(MF_EINVAL, "nrhs must be in 1..64");
+    return solve_impl(op, sp, b, x, nrhs, info, false);
+  } catch (...) {
+    return fail(MF_ENOMEM, "exception in mf_solve");
+  }
+}
+
+mf_status mf_laser_load(mf_op* op, const mf_laser* lz, double* dst, double* dF) {
+  if (!op || !lz || !dst) return fail(MF_EINVAL, "NULL argument");
+  if (op->p.kind != MF_OP_HEAT) return fail(MF_EINVAL, "laser load belongs to heat operators");
+  if (!(lz->radius > 0) || !(lz->power > 0)) return fail(MF_EINVAL, "laser power and radius must be > 0");
+  const double p[5] = {lz->power, lz->radius, lz->x0, lz->y0, lz->absorptivity};
+  return launch_laser(op->ctx, op->map[0], p, dst, dF);
+}
+
+mf_status mf_heat_step_gradient(mf_op* op, const mf_laser* lz, const mf_solver_params* sp, const double* theta_prev,
+                                const double* theta_target, double box_half, double box_depth, double* J,
+                                double* dJ_dlaser, double* dJ_dkq, double* theta_out, double* lambda_out) {
+  try {
+    if (!op || !lz || !sp || !theta_prev || !theta_target || !J || !dJ_dlaser) return fail(MF_EINVAL, "NULL argument");
+    if (op->p.kind != MF_OP_HEAT) return fail(MF_EINVAL, "heat operators only");
+    if (dJ_dkq && !op->kq_user) return fail(MF_EINVAL, "dJ/dk_q needs MF_FIELD_K_QPOINT");
+    mf_ctx* c = op->ctx;
+    const mf_dofmap* m = op->map[0];
+    if (!m->uniform) return fail(MF_EUNSUPPORTED, "heat-step gradient on octree maps");
+    const int64_t n = op->n;
+    DevBuf buf;
+    MF_TRY(buf.alloc(sizeof(double) * n * 9));
+    double* f = buf.as<double>();
+    double* dF = f + n;           // 4 n
+    double* bvec = dF + 4 * n;
+    double* th = bvec + n;
+    double* e = th + n;
+    double* lam = e + n;
+    // b = rho_cp/dt M theta_prev + f_laser (Dirichlet rows 0)
+    MF_TRY(mf_laser_load(op, lz, f, dF));
+    ScalarArgs<double> a = scalar_args<double>(op, theta_prev, bvec, 1, n);
+    a.mass = op->p.rhocp / op->p.dt;
+    MF_CUDA_TRY(cudaMemsetAsync(bvec, 0, sizeof(double) * n, c->stream));
+    MF_TRY(launch_scalar_apply(c, m, K_MASS, 1, false, false, false, &a));
+    MF_TRY(axpby<double, double>(c, n, 1.0, f, 1.0, bvec));
+    MF_TRY(zero_list<double>(c, bvec, m->d_dir_list.as<int32_t>(), int64_t(m->dirichlet_list.size())));
+    mf_solve_info inf;
+    mf_status st = solve_impl(op, sp, bvec, th, 1, &inf, false);
+    if (st != MF_OK) return st;
+    // J = 1/2 e^T M_box e, dJ/dtheta = M_box e
+    MF_TRY(axpby<double, double>(c, n, 1.0, th, 0.0, e));
+    MF_TRY(axpby<double, double>(c, n, -1.0, theta_target, 1.0, e));
+    ScalarArgs<double> mb = scalar_args<double>(op, e, f, 1, n);
+    mb.mass = 1.0;
+    mb.use_box = 1;
+    mb.box_half = box_half;
+    mb.box_zmin = m->mesh->hi[2] - box_depth;
+    for (int d = 0; d < 3; ++d) mb.lo[d] = m->mesh->lo[d];
+    MF_CUDA_TRY(cudaMemsetAsync(f, 0, sizeof(double) * n, c->stream));
+    MF_TRY(launch_scalar_apply(c, m, K_MASS, 1, false, false, false, &mb));
+    double* ds = c->scalars.as<double>() + kScalarsHeat;
+    MF_TRY(dot<double, double>(c, e, f, n, ds));
+    MF_TRY(zero_list<double>(c, f, m->d_dir_list.as<int32_t>(), int64_t(m->dirichlet_list.size())));
+    // adjoint: A^T lambda = dJ/dtheta
+    st = solve_impl(op, sp, f, lam, 1, &inf, true);
+    if (st != MF_OK) return st;
+    for (int p = 0; p < 4; ++p) MF_TRY(dot<double, double>(c, dF + p * n, lam, n, ds + 1 + p));
+    double hs[5];
+    MF_TRY(sync_copy(c, hs, ds, 5));
+    *J = 0.5 * hs[0];
+    for (int p = 0; p < 4; ++p) dJ_dlaser[p] = hs[1 + p];
+    if (dJ_dkq) MF_TRY(launch_grad_kq(c, m, lam, th, dJ_dkq));
+    if (theta_out) MF_CUDA_TRY(cudaMemcpyAsync(theta_out, th, sizeof(double) * n, cudaMemcpyDeviceToDevice, c->stream));
+    if (lambda_out) MF_CUDA_TRY(cudaMemcpyAsync(lambda_out, lam, sizeof(double) * n, cudaMemcpyDeviceToDevice, c->stream));
+    MF_CUDA_TRY(cudaStreamSynchronize(c->stream));
+    return MF_OK;
+  } catch (...) {
+    return fail(MF_ENOMEM, "exception in mf_heat_step_gradient");
+  }
+}
+
+mf_status mf_autotune(mf_op* op, const char* cache_path) {
+  try {
+    if (!op) return fail(MF_EINVAL, "NULL argument");
+    MF_TRY(check_fields(op));
+    mf_ctx* c = op->ctx;
+    const int64_t n = op->n;
+    if (op->p.kind == MF_OP_OSEEN) return MF_OK;  // one variant
+    MF_TRY(ensure_tables(op));
+    DevBuf src, dst;
+    MF_TRY(src.alloc(sizeof(double) * n));
+    MF_TRY(dst.alloc(sizeof(double) * n));
+    MF_TRY(fill_splitmix(c, 7, src.as<double>(), n));
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    const bool forced = op->p.kind == MF_OP_HEAT && (op->kq_user || op->beta);
+    double best[2][2] = {{1e30, 1e30}, {1e30, 1e30}};
+    for (int prec = 0; prec < 2; ++prec)
+      for (int mode = 0; mode < 2; ++mode) {
+        if (forced && mode == 0) continue;
+        if (prec == 0) op->mode64 = mode;
+        else op->mode32 = mode;
+        DevBuf s32;
+        if (prec == 1) {
+          MF_TRY(s32.alloc(sizeof(float) * n));
+          MF_TRY(convert<double, float>(c, n, src.as<double>(), s32.as<float>()));
+        }
+        for (int rep = 0; rep < 6; ++rep) {
+          cudaEventRecord(e0, c->stream);
+          if (prec == 0) MF_TRY(apply_impl<double>(op, src.as<double>(), dst.as<double>(), 1, n, false));
+          else MF_TRY(apply_impl<float>(op, s32.as<float>(), reinterpret_cast<float*>(dst.as<double>()), 1, n, false));
+          cudaEventRecord(e1, c->stream);
+          MF_CUDA_TRY(cudaEventSynchronize(e1));
+          float ms;
+          cudaEventElapsedTime(&ms, e0, e1);
+          if (rep > 0) best[prec][mode] = std::min(best[prec][mode], double(ms));
+        }
+      }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    op->mode64 = best[0][0] < best[0][1] ? 0 : 1;
+    op->mode32 = best[1][0] < best[1][1] ? 0 : 1;
+    if (cache_path) {
+      FILE* fp = std::fopen(cache_path, "a");
+      if (fp) {
+        std::fprintf(fp, "{\"kind\": %d, \"n\": %lld, \"f64_inkernel_ms\": %.6g, \"f64_tabulated_ms\": %.6g, "
+                     "\"f32_inkernel_ms\": %.6g, \"f32_tabulated_ms\": %.6g, \"mode64\": %d, \"mode32\": %d}\n",
+                     op->p.kind, (long long)n, best[0][0], best[0][1], best[1][0], best[1][1], op->mode64, op->mode32);
+        std::fclose(fp);
+      }
+    }
+    return MF_OK;
+  } catch (...) {
+    return fail(MF_ENOMEM, "exception in mf_autotune");
+  }
+}
+
+}  // extern "C"

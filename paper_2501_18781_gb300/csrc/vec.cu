@@ -1,0 +1,419 @@
+// Vector kernels of the Krylov solvers.  All reductions accumulate in fp64 over a fixed
+// grid of kRedBlocks blocks, then one block sums the partials in a fixed order, so every
+// dot product is deterministic.
+#include "vec.cuh"
+
+namespace mf {
+
+namespace {
+
+__device__ __forceinline__ double block_sum(double v) {
+  __shared__ double sh[kRedThreads / 32];
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
+  __syncthreads();
+  double s = 0.0;
+  if (threadIdx.x < 32) {
+    s = threadIdx.x < kRedThreads / 32 ? sh[threadIdx.x] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+  }
+  __syncthreads();
+  return s;  // valid in thread 0
+}
+
+// out = sum(part); one block per right-hand side r (blockIdx.x), partial rows of g entries.
+// mode 0: out[r] = sum; 1: pAp and alpha; 2: rr, rz (second row), beta; 3: rz and beta; 4: rr and rz
+__global__ void __launch_bounds__(kRedThreads) k_finish(const double* part, int g, double* out, int mode, double* S) {
+  const int r = blockIdx.x;
+  const double* pr = part + int64_t(r) * 2 * g;
+  double s = 0.0;
+  for (int i = threadIdx.x; i < g; i += blockDim.x) s += pr[i];
+  s = block_sum(s);
+  double s2 = 0.0;
+  if (mode == 2 || mode == 4) {
+    for (int i = threadIdx.x; i < g; i += blockDim.x) s2 += pr[g + i];
+    s2 = block_sum(s2);
+  }
+  if (threadIdx.x == 0) {
+    double* Sr = S ? S + r * S_NSCAL : nullptr;
+    if (mode == 0) out[r] = s;
+    else if (mode == 1) {
+      Sr[S_PAP] = s;
+      Sr[S_ALPHA] = (Sr[S_ACTIVE] != 0.0 && s != 0.0) ? Sr[S_RZ] / s : 0.0;
+    } else if (mode == 2 || mode == 3) {
+      const double rz = mode == 2 ? s2 : s;
+      if (mode == 2) Sr[S_RR] = s;
+      Sr[S_RZN] = rz;
+      Sr[S_BETA] = (Sr[S_ACTIVE] != 0.0 && Sr[S_RZ] != 0.0) ? rz / Sr[S_RZ] : 0.0;
+      Sr[S_RZ] = rz;
+    } else if (mode == 4) {
+      Sr[S_RR] = s;
+      Sr[S_RZ] = s2;
+    } else if (mode == 5) {
+      Sr[S_RR] = s;
+    }
+  }
+}
+
+template <typename TX, typename TY>
+__global__ void __launch_bounds__(kRedThreads) k_dot2_partial(const TX* x, const TY* y, const TX* x2, const TY* y2,
+                                                             int64_t n, int64_t ld, double* part) {
+  const int r = blockIdx.y;
+  x += r * ld; y += r * ld;
+  double s = 0.0, s2 = 0.0;
+  for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x) {
+    s += double(x[i]) * double(y[i]);
+    if (x2) s2 += double(x2[r * ld + i]) * double(y2[r * ld + i]);
+  }
+  s = block_sum(s);
+  if (x2) s2 = block_sum(s2);
+  if (threadIdx.x == 0) {
+    part[int64_t(r) * 2 * gridDim.x + blockIdx.x] = s;
+    part[int64_t(r) * 2 * gridDim.x + gridDim.x + blockIdx.x] = s2;
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kRedThreads) k_cg_xr(int64_t n, int64_t ld, T* x, T* r, const T* p, const T* Ap,
+                                                       const T* dinv, T* z, int zmode, const double* S, double* part) {
+  const int rh = blockIdx.y;
+  const double alpha = S[rh * S_NSCAL + S_ALPHA];
+  const int64_t o = rh * ld;
+  double rr = 0.0, rz = 0.0;
+  for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x) {
+    T xi = x[o + i] + T(alpha) * p[o + i];
+    T ri = r[o + i] - T(alpha) * Ap[o + i];
+    x[o + i] = xi;
+    r[o + i] = ri;
+    rr += double(ri) * double(ri);
+    if (zmode == 1) {
+      T zi = dinv[i] * ri;
+      z[o + i] = zi;
+      rz += double(ri) * double(zi);
+    } else if (zmode == 0) {
+      rz += double(ri) * double(ri);
+    }
+  }
+  rr = block_sum(rr);
+  rz = block_sum(rz);
+  if (threadIdx.x == 0) {
+    part[int64_t(rh) * 2 * gridDim.x + blockIdx.x] = rr;
+    part[int64_t(rh) * 2 * gridDim.x + gridDim.x + blockIdx.x] = rz;
+  }
+}
+
+template <typename T> __global__ void k_cg_p(int64_t n, int64_t ld, const T* z, T* p, const double* S) {
+  const int rh = blockIdx.y;
+  const T beta = T(S[rh * S_NSCAL + S_BETA]);
+  const int64_t o = rh * ld;
+  for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x)
+    p[o + i] = z[o + i] + beta * p[o + i];
+}
+
+template <typename TX, typename TY>
+__global__ void k_axpby(int64_t n, double a, const TX* x, double b, TY* y) {
+  for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x)
+    y[i] = TY(a * double(x[i]) + (b == 0.0 ? 0.0 : b * double(y[i])));
+}
+
+template <typename T> __global__ void k_pmul(int64_t n, const T* d, const T* r, T* z) {
+  for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x)
+    z[i] = d ? d[i] * r[i] : r[i];
+}
+
+template <typename T>
+__global__ void k_block_jacobi(int64_t nu, int64_t np, const double* blk, const double* pinv, const T* r, T* z) {
+  for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < nu + np; i += int64_t(gridDim.x) * blockDim.x) {
+    if (i < nu) {
+      const double* B = blk + 9 * i;
+      double r0 = r[i], r1 = r[nu + i], r2 = r[2 * nu + i];
+      z[i] = T(B[0] * r0 + B[1] * r1 + B[2] * r2);
+      z[nu + i] = T(B[3] * r0 + B[4] * r1 + B[5] * r2);
+      z[2 * nu + i] = T(B[6] * r0 + B[7] * r1 + B[8] * r2);
+    } else {
+      int64_t j = i - nu;
+      z[3 * nu + j] = T(pinv[j] * double(r[3 * nu + j]));
+    }
+  }
+}
+
+template <typename TS, typename TD> __global__ void k_convert(int64_t n, const TS* s, TD* d) {
+  for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x)
+    d[i] = TD(s[i]);
+}
+
+template <typename T>
+__global__ void k_cheb_init(int64_t n, int64_t ld, const T* r, const T* dinv, T inv_theta, T* res, T* d, T* z) {
+  const int64_t o = blockIdx.y * ld;
+  for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x) {
+    T ri = r[o + i];
+    res[o + i] = ri;
+    d[o + i] = inv_theta * dinv[i] * ri;
+    z[o + i] = T(0);
+  }
+}
+
+template <typename T>
+__global__ void k_cheb_step(int64_t n, int64_t ld, T* z, T* res, const T* Ad, T* d, const T* dinv, T c1, T c2) {
+  const int64_t o = blockIdx.y * ld;
+  for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x) {
+    T di = d[o + i];
+    z[o + i] += di;
+    T ri = res[o + i] - Ad[o + i];
+    res[o + i] = ri;
+    d[o + i] = c1 * di + c2 * dinv[i] * ri;
+  }
+}
+
+template <typename T> __global__ void k_add_into(int64_t n, int64_t ld, const T* d, T* z) {
+  const int64_t o = blockIdx.y * ld;
+  for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x)
+    z[o + i] += d[o + i];
+}
+
+// h partials: part[j * G + block] = sum over the block's slice of V_j . w
+__global__ void __launch_bounds__(kRedThreads) k_multidot(const double* V, int64_t ld, int k, const double* w, int64_t n,
+                                                          double* part) {
+  for (int j = 0; j < k; ++j) {
+    double s = 0.0;
+    const double* v = V + j * ld;
+    for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x)
+      s += v[i] * w[i];
+    s = block_sum(s);
+    if (threadIdx.x == 0) part[j * gridDim.x + blockIdx.x] = s;
+  }
+}
+__global__ void __launch_bounds__(kRedThreads) k_multidot_finish(const double* part, int g, double* h) {
+  double s = 0.0;
+  for (int i = threadIdx.x; i < g; i += blockDim.x) s += part[blockIdx.x * g + i];
+  s = block_sum(s);
+  if (threadIdx.x == 0) h[blockIdx.x] = s;
+}
+
+__global__ void k_multiaxpy(const double* V, int64_t ld, int k, const double* h, double sign, double* w, int64_t n) {
+  for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x) {
+    double acc = w[i];
+    for (int j = 0; j < k; ++j) acc += sign * h[j] * V[j * ld + i];
+    w[i] = acc;
+  }
+}
+
+__global__ void k_splitmix(uint64_t seed, double* v, int64_t n) {
+  for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x) {
+    uint64_t z = seed + uint64_t(i + 1) * 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    z = z ^ (z >> 31);
+    v[i] = double(z >> 11) * (1.0 / 9007199254740992.0) * 2.0 - 1.0;
+  }
+}
+
+__global__ void k_set_list(double* v, const int32_t* list, int64_t n, double val) {
+  int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (t < n) v[list[t]] = val;
+}
+template <typename T> __global__ void k_zero_list(T* v, const int32_t* list, int64_t n) {
+  int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (t < n) v[list[t]] = T(0);
+}
+
+inline int grid_for(int64_t n) {
+  int64_t g = (n + 255) / 256;
+  return int(g < 4 * 152 * 4 ? (g < 1 ? 1 : g) : 4 * 152 * 4);
+}
+
+// The reduction scratch is allocated with the context (kScratchDoubles) and never grown, so
+// that solver iterations can be captured in CUDA graphs.
+mf_status scratch(mf_ctx* ctx, size_t doubles, double** p) {
+  if (ctx->scratch.bytes < doubles * sizeof(double))
+    return fail(MF_EINVAL, "reduction scratch too small for this many right-hand sides");
+  *p = ctx->scratch.as<double>();
+  return MF_OK;
+}
+
+}  // namespace
+
+#define LAUNCH_CHECK() \
+  do { ctx->launches++; MF_CUDA_TRY(cudaGetLastError()); } while (0)
+
+template <typename TX, typename TY> mf_status dot(mf_ctx* ctx, const TX* x, const TY* y, int64_t n, double* out) {
+  double* part;
+  MF_TRY(scratch(ctx, 2 * kRedBlocks, &part));
+  k_dot2_partial<TX, TY><<<dim3(kRedBlocks, 1), kRedThreads, 0, ctx->stream>>>(x, y, nullptr, nullptr, n, 0, part);
+  LAUNCH_CHECK();
+  k_finish<<<1, kRedThreads, 0, ctx->stream>>>(part, kRedBlocks, out, 0, nullptr);
+  LAUNCH_CHECK();
+  return MF_OK;
+}
+template mf_status dot<double, double>(mf_ctx*, const double*, const double*, int64_t, double*);
+template mf_status dot<float, float>(mf_ctx*, const float*, const float*, int64_t, double*);
+
+mf_status norm2_sq(mf_ctx* ctx, const double* x, int64_t n, double* out) { return dot<double, double>(ctx, x, x, n, out); }
+
+template <typename TX, typename TY> mf_status axpby(mf_ctx* ctx, int64_t n, double a, const TX* x, double b, TY* y) {
+  k_axpby<TX, TY><<<grid_for(n), 256, 0, ctx->stream>>>(n, a, x, b, y);
+  LAUNCH_CHECK();
+  return MF_OK;
+}
+template mf_status axpby<double, double>(mf_ctx*, int64_t, double, const double*, double, double*);
+template mf_status axpby<float, double>(mf_ctx*, int64_t, double, const float*, double, double*);
+template mf_status axpby<double, float>(mf_ctx*, int64_t, double, const double*, double, float*);
+template mf_status axpby<float, float>(mf_ctx*, int64_t, double, const float*, double, float*);
+
+template <typename T> mf_status pointwise_mul(mf_ctx* ctx, int64_t n, const T* d, const T* r, T* z) {
+  k_pmul<T><<<grid_for(n), 256, 0, ctx->stream>>>(n, d, r, z);
+  LAUNCH_CHECK();
+  return MF_OK;
+}
+template mf_status pointwise_mul<double>(mf_ctx*, int64_t, const double*, const double*, double*);
+template mf_status pointwise_mul<float>(mf_ctx*, int64_t, const float*, const float*, float*);
+
+template <typename T>
+mf_status block_jacobi(mf_ctx* ctx, int64_t nu, int64_t np, const double* blk, const double* pinv, const T* r, T* z) {
+  k_block_jacobi<T><<<grid_for(nu + np), 256, 0, ctx->stream>>>(nu, np, blk, pinv, r, z);
+  LAUNCH_CHECK();
+  return MF_OK;
+}
+template mf_status block_jacobi<double>(mf_ctx*, int64_t, int64_t, const double*, const double*, const double*, double*);
+template mf_status block_jacobi<float>(mf_ctx*, int64_t, int64_t, const double*, const double*, const float*, float*);
+
+template <typename TS, typename TD> mf_status convert(mf_ctx* ctx, int64_t n, const TS* s, TD* d) {
+  k_convert<TS, TD><<<grid_for(n), 256, 0, ctx->stream>>>(n, s, d);
+  LAUNCH_CHECK();
+  return MF_OK;
+}
+template mf_status convert<double, float>(mf_ctx*, int64_t, const double*, float*);
+template mf_status convert<float, double>(mf_ctx*, int64_t, const float*, double*);
+
+template <typename T> mf_status cg_alpha(mf_ctx* ctx, const T* p, const T* Ap, int64_t n, int64_t ld, int nrhs, double* S) {
+  double* part;
+  MF_TRY(scratch(ctx, 2 * kRedBlocks * size_t(nrhs), &part));
+  k_dot2_partial<T, T><<<dim3(kRedBlocks, nrhs), kRedThreads, 0, ctx->stream>>>(p, Ap, nullptr, nullptr, n, ld, part);
+  LAUNCH_CHECK();
+  k_finish<<<nrhs, kRedThreads, 0, ctx->stream>>>(part, kRedBlocks, nullptr, 1, S);
+  LAUNCH_CHECK();
+  return MF_OK;
+}
+template mf_status cg_alpha<double>(mf_ctx*, const double*, const double*, int64_t, int64_t, int, double*);
+template mf_status cg_alpha<float>(mf_ctx*, const float*, const float*, int64_t, int64_t, int, double*);
+
+template <typename T>
+mf_status cg_update_xr(mf_ctx* ctx, int64_t n, int64_t ld, int nrhs, T* x, T* r, const T* p, const T* Ap,
+                       const T* dinv, T* z, int zmode, double* S) {
+  double* part;
+  MF_TRY(scratch(ctx, 2 * kRedBlocks * size_t(nrhs), &part));
+  k_cg_xr<T><<<dim3(kRedBlocks, nrhs), kRedThreads, 0, ctx->stream>>>(n, ld, x, r, p, Ap, dinv, z, zmode, S, part);
+  LAUNCH_CHECK();
+  k_finish<<<nrhs, kRedThreads, 0, ctx->stream>>>(part, kRedBlocks, nullptr, zmode == 2 ? 5 : 2, S);
+  LAUNCH_CHECK();
+  return MF_OK;
+}
+template mf_status cg_update_xr<double>(mf_ctx*, int64_t, int64_t, int, double*, double*, const double*, const double*,
+                                        const double*, double*, int, double*);
+template mf_status cg_update_xr<float>(mf_ctx*, int64_t, int64_t, int, float*, float*, const float*, const float*,
+                                       const float*, float*, int, double*);
+
+template <typename T> mf_status cg_rz(mf_ctx* ctx, const T* r, const T* z, int64_t n, int64_t ld, int nrhs, double* S) {
+  double* part;
+  MF_TRY(scratch(ctx, 2 * kRedBlocks * size_t(nrhs), &part));
+  k_dot2_partial<T, T><<<dim3(kRedBlocks, nrhs), kRedThreads, 0, ctx->stream>>>(r, z, nullptr, nullptr, n, ld, part);
+  LAUNCH_CHECK();
+  k_finish<<<nrhs, kRedThreads, 0, ctx->stream>>>(part, kRedBlocks, nullptr, 3, S);
+  LAUNCH_CHECK();
+  return MF_OK;
+}
+template mf_status cg_rz<double>(mf_ctx*, const double*, const double*, int64_t, int64_t, int, double*);
+template mf_status cg_rz<float>(mf_ctx*, const float*, const float*, int64_t, int64_t, int, double*);
+
+template <typename T>
+mf_status cg_init_scalars(mf_ctx* ctx, const T* r, const T* z, int64_t n, int64_t ld, int nrhs, double* S) {
+  double* part;
+  MF_TRY(scratch(ctx, 2 * kRedBlocks * size_t(nrhs), &part));
+  k_dot2_partial<T, T><<<dim3(kRedBlocks, nrhs), kRedThreads, 0, ctx->stream>>>(r, r, r, z, n, ld, part);
+  LAUNCH_CHECK();
+  k_finish<<<nrhs, kRedThreads, 0, ctx->stream>>>(part, kRedBlocks, nullptr, 4, S);
+  LAUNCH_CHECK();
+  return MF_OK;
+}
+template mf_status cg_init_scalars<double>(mf_ctx*, const double*, const double*, int64_t, int64_t, int, double*);
+template mf_status cg_init_scalars<float>(mf_ctx*, const float*, const float*, int64_t, int64_t, int, double*);
+
+template <typename T> mf_status cg_update_p(mf_ctx* ctx, int64_t n, int64_t ld, int nrhs, const T* z, T* p, double* S) {
+  k_cg_p<T><<<dim3(grid_for(n), nrhs), 256, 0, ctx->stream>>>(n, ld, z, p, S);
+  LAUNCH_CHECK();
+  return MF_OK;
+}
+template mf_status cg_update_p<double>(mf_ctx*, int64_t, int64_t, int, const double*, double*, double*);
+template mf_status cg_update_p<float>(mf_ctx*, int64_t, int64_t, int, const float*, float*, double*);
+
+template <typename T>
+mf_status cheb_init(mf_ctx* ctx, int64_t n, int64_t ld, int nrhs, const T* r, const T* dinv, double inv_theta, T* res,
+                    T* d, T* z) {
+  k_cheb_init<T><<<dim3(grid_for(n), nrhs), 256, 0, ctx->stream>>>(n, ld, r, dinv, T(inv_theta), res, d, z);
+  LAUNCH_CHECK();
+  return MF_OK;
+}
+template mf_status cheb_init<double>(mf_ctx*, int64_t, int64_t, int, const double*, const double*, double, double*,
+                                     double*, double*);
+template mf_status cheb_init<float>(mf_ctx*, int64_t, int64_t, int, const float*, const float*, double, float*, float*,
+                                    float*);
+
+template <typename T>
+mf_status cheb_step(mf_ctx* ctx, int64_t n, int64_t ld, int nrhs, T* z, T* res, const T* Ad, T* d, const T* dinv,
+                    double c1, double c2) {
+  k_cheb_step<T><<<dim3(grid_for(n), nrhs), 256, 0, ctx->stream>>>(n, ld, z, res, Ad, d, dinv, T(c1), T(c2));
+  LAUNCH_CHECK();
+  return MF_OK;
+}
+template mf_status cheb_step<double>(mf_ctx*, int64_t, int64_t, int, double*, double*, const double*, double*,
+                                     const double*, double, double);
+template mf_status cheb_step<float>(mf_ctx*, int64_t, int64_t, int, float*, float*, const float*, float*, const float*,
+                                    double, double);
+
+template <typename T> mf_status add_into(mf_ctx* ctx, int64_t n, int64_t ld, int nrhs, const T* d, T* z) {
+  k_add_into<T><<<dim3(grid_for(n), nrhs), 256, 0, ctx->stream>>>(n, ld, d, z);
+  LAUNCH_CHECK();
+  return MF_OK;
+}
+template mf_status add_into<double>(mf_ctx*, int64_t, int64_t, int, const double*, double*);
+template mf_status add_into<float>(mf_ctx*, int64_t, int64_t, int, const float*, float*);
+
+mf_status multidot(mf_ctx* ctx, const double* V, int64_t ld, int k, const double* w, int64_t n, double* h) {
+  const int g = 152 * 2;
+  double* part;
+  MF_TRY(scratch(ctx, size_t(g) * (k + 1) + 64, &part));
+  k_multidot<<<g, kRedThreads, 0, ctx->stream>>>(V, ld, k, w, n, part);
+  LAUNCH_CHECK();
+  k_multidot_finish<<<k, kRedThreads, 0, ctx->stream>>>(part, g, h);
+  LAUNCH_CHECK();
+  return MF_OK;
+}
+
+mf_status multiaxpy(mf_ctx* ctx, double* V, int64_t ld, int k, const double* h, double sign, double* w, int64_t n) {
+  k_multiaxpy<<<grid_for(n), 256, 0, ctx->stream>>>(V, ld, k, h, sign, w, n);
+  LAUNCH_CHECK();
+  return MF_OK;
+}
+
+mf_status fill_splitmix(mf_ctx* ctx, uint64_t seed, double* v, int64_t n) {
+  k_splitmix<<<grid_for(n), 256, 0, ctx->stream>>>(seed, v, n);
+  LAUNCH_CHECK();
+  return MF_OK;
+}
+
+mf_status set_list(mf_ctx* ctx, double* v, const int32_t* list, int64_t n, double val) {
+  if (n == 0) return MF_OK;
+  k_set_list<<<int((n + 255) / 256), 256, 0, ctx->stream>>>(v, list, n, val);
+  LAUNCH_CHECK();
+  return MF_OK;
+}
+template <typename T> mf_status zero_list(mf_ctx* ctx, T* v, const int32_t* list, int64_t n) {
+  if (n == 0) return MF_OK;
+  k_zero_list<T><<<int((n + 255) / 256), 256, 0, ctx->stream>>>(v, list, n);
+  LAUNCH_CHECK();
+  return MF_OK;
+}
+template mf_status zero_list<double>(mf_ctx*, double*, const int32_t*, int64_t);
+template mf_status zero_list<float>(mf_ctx*, float*, const int32_t*, int64_t);
+
+}  // namespace mf

@@ -1,0 +1,65 @@
+// Vector kernels of the Krylov solvers (internal): deterministic fp64-accumulated dot
+// products, fused CG / Chebyshev updates, CGS2 multi-dot and multi-axpy for GMRES.
+#pragma once
+
+#include "internal.h"
+
+namespace mf {
+
+constexpr int kRedBlocks = 608;   // 4 x 152 SMs: fixed grid, so reductions are deterministic
+constexpr int kRedThreads = 256;
+constexpr size_t kScratchDoubles = size_t(2) * kRedBlocks * 64;  // up to 64 right-hand sides
+
+// partial sums (kRedBlocks doubles) then one-block finish into out[0]
+template <typename TX, typename TY>
+mf_status dot(mf_ctx* ctx, const TX* x, const TY* y, int64_t n, double* out);
+mf_status norm2_sq(mf_ctx* ctx, const double* x, int64_t n, double* out);
+
+// y = a x + b y (host scalars), mixed precisions allowed
+template <typename TX, typename TY>
+mf_status axpby(mf_ctx* ctx, int64_t n, double a, const TX* x, double b, TY* y);
+// z = d .* r (Jacobi); d may be NULL (identity)
+template <typename T> mf_status pointwise_mul(mf_ctx* ctx, int64_t n, const T* d, const T* r, T* z);
+// Oseen block Jacobi: z_u = B^-1 r_u per node, z_p = pinv .* r_p
+template <typename T>
+mf_status block_jacobi(mf_ctx* ctx, int64_t nu, int64_t np, const double* blk, const double* pinv, const T* r, T* z);
+template <typename TS, typename TD> mf_status convert(mf_ctx* ctx, int64_t n, const TS* s, TD* d);
+
+// Batched CG pieces: nrhs systems, vectors ld apart, device scalars S[r * S_NSCAL + k]:
+// 0 rz, 1 pAp, 2 alpha, 3 beta, 4 rr, 5 rz_new, 6 active (1 = still iterating)
+enum { S_RZ = 0, S_PAP = 1, S_ALPHA = 2, S_BETA = 3, S_RR = 4, S_RZN = 5, S_ACTIVE = 6, S_NSCAL = 8 };
+// S[pAp] = p.Ap, S[alpha] = active ? rz / pAp : 0
+template <typename T> mf_status cg_alpha(mf_ctx* ctx, const T* p, const T* Ap, int64_t n, int64_t ld, int nrhs, double* S);
+// x += alpha p; r -= alpha Ap; then (zmode 1) z = dinv .* r, S[rz] = r.z, beta; (zmode 0) z := r
+// implicitly (S[rz] = r.r); (zmode 2) only S[rr]
+template <typename T>
+mf_status cg_update_xr(mf_ctx* ctx, int64_t n, int64_t ld, int nrhs, T* x, T* r, const T* p, const T* Ap,
+                       const T* dinv, T* z, int zmode, double* S);
+// S[rz] = r.z and beta (preconditioner applied separately)
+template <typename T> mf_status cg_rz(mf_ctx* ctx, const T* r, const T* z, int64_t n, int64_t ld, int nrhs, double* S);
+// p = z + beta p (z = r when z is NULL)
+template <typename T> mf_status cg_update_p(mf_ctx* ctx, int64_t n, int64_t ld, int nrhs, const T* z, T* p, double* S);
+// S[rr] = r.r, S[rz] = r.z (initial)
+template <typename T> mf_status cg_init_scalars(mf_ctx* ctx, const T* r, const T* z, int64_t n, int64_t ld, int nrhs, double* S);
+
+// Chebyshev (nrhs vectors ld apart, one diagonal): res = r, d = dinv r / theta, z = 0
+template <typename T>
+mf_status cheb_init(mf_ctx* ctx, int64_t n, int64_t ld, int nrhs, const T* r, const T* dinv, double inv_theta, T* res,
+                    T* d, T* z);
+// z += d; res -= Ad; d = c1 d + c2 dinv res
+template <typename T>
+mf_status cheb_step(mf_ctx* ctx, int64_t n, int64_t ld, int nrhs, T* z, T* res, const T* Ad, T* d, const T* dinv,
+                    double c1, double c2);
+template <typename T> mf_status add_into(mf_ctx* ctx, int64_t n, int64_t ld, int nrhs, const T* d, T* z);
+
+// GMRES: h[0..k) = V^T w (V: k vectors of length n, stride ld), into device h
+mf_status multidot(mf_ctx* ctx, const double* V, int64_t ld, int k, const double* w, int64_t n, double* h);
+// w -= V h (h device, k entries); or x += V y
+mf_status multiaxpy(mf_ctx* ctx, double* V, int64_t ld, int k, const double* h, double sign, double* w, int64_t n);
+// splitmix64 uniform [-1,1) vector (own implementation of the published generator)
+mf_status fill_splitmix(mf_ctx* ctx, uint64_t seed, double* v, int64_t n);
+// v[list[i]] = val
+mf_status set_list(mf_ctx* ctx, double* v, const int32_t* list, int64_t n, double val);
+template <typename T> mf_status zero_list(mf_ctx* ctx, T* v, const int32_t* list, int64_t n);
+
+}  // namespace mf

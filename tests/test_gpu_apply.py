@@ -1,0 +1,132 @@
+"""Operator apply, transpose and diagonal on the GPU against the oracle's assembled matrices.
+
+FP64 bar: |v_gpu - v_oracle|_i <= 1e-12 (|A| |u|)_i for every i (componentwise, robust to
+summation order).  FP32 bar: 2e-5 (|A| |u|)_i (single-precision contractions with O(100)
+roundings per entry).  Sizes span several 8x4x4-cell blocks with ragged tails."""
+import numpy as np
+import pytest
+
+import synthetic as syn
+from problems import band_octree, componentwise_ok, heat, helmholtz, oseen, reinit
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_2501_18781_gb300 import Context, build_library
+    build_library()
+    return Context(0)
+
+
+def check_apply(P, seed=1, nrhs=1, rtol64=1e-12, rtol32=2e-5, transpose=False):
+    n = P["n"]
+    A = P["A"].T.tocsr() if transpose else P["A"]
+    absA = abs(A)
+    for r in range(nrhs):
+        pass
+    U = np.stack([syn.uniform_pm1(seed + r, n) for r in range(nrhs)])
+    src = torch.tensor(U.ravel(), device="cuda")
+    out64 = P["op"].apply(src, nrhs=nrhs, transpose=transpose).cpu().numpy().reshape(nrhs, n)
+    out32 = P["op"].apply(src.float(), nrhs=nrhs, transpose=transpose).cpu().numpy().astype(np.float64).reshape(nrhs, n)
+    for r in range(nrhs):
+        ref = A @ U[r]
+        bound = absA @ np.abs(U[r])
+        ok, worst = componentwise_ok(out64[r], ref, bound, rtol64)
+        assert ok, f"fp64 componentwise error {worst:.3e} (rhs {r})"
+        ok32, worst32 = componentwise_ok(out32[r], ref, bound, rtol32)
+        assert ok32, f"fp32 componentwise error {worst32:.3e} (rhs {r})"
+    return worst, worst32
+
+
+@pytest.mark.parametrize("n", [1, 3, 10])
+@pytest.mark.parametrize("mode", [0, 1])
+def test_helmholtz_uniform(ctx, n, mode):
+    P = helmholtz(n, ctx, coef_mode=mode)
+    check_apply(P)
+
+
+def test_helmholtz_sine_heaviside(ctx):
+    P = helmholtz(9, ctx, heaviside="sine", coef_mode=1)
+    check_apply(P)
+    P0 = helmholtz(9, ctx, heaviside="sine", coef_mode=0)
+    check_apply(P0, rtol32=1e-4)
+
+
+def test_helmholtz_batched_rhs(ctx):
+    P = helmholtz(10, ctx)
+    check_apply(P, nrhs=3)
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_heat_k_of_T_with_dirichlet(ctx, mode):
+    P = heat(10, ctx, coef_mode=mode)
+    check_apply(P)
+    # Dirichlet rows return the input
+    u = torch.tensor(syn.uniform_pm1(3, P["n"]), device="cuda")
+    v = P["op"].apply(u).cpu().numpy()
+    d = P["dm"].dirichlet
+    assert np.array_equal(v[d], u.cpu().numpy()[d])
+
+
+def test_heat_convection_kq_and_transpose(ctx):
+    P = heat(9, ctx, with_beta=True, kq=True)
+    check_apply(P)
+    check_apply(P, transpose=True)
+
+
+def test_oseen_q2q1(ctx):
+    P = oseen(9, ctx)
+    check_apply(P, rtol32=5e-5)
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_helmholtz_octree_hanging_nodes(ctx, mode):
+    P = helmholtz(0, ctx, octree=band_octree(), coef_mode=mode)
+    assert P["map"].n_constraints > 0
+    check_apply(P)
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_reinit_octree_multi_rhs(ctx, mode):
+    P = reinit(band_octree(), ctx, coef_mode=mode)
+    check_apply(P, nrhs=2, rtol32=5e-5)
+
+
+@pytest.mark.parametrize("which", ["helmholtz", "heat_beta", "octree", "reinit"])
+def test_diagonal(ctx, which):
+    if which == "helmholtz":
+        P = helmholtz(10, ctx)
+    elif which == "heat_beta":
+        P = heat(7, ctx, with_beta=True, kq=True)
+    elif which == "octree":
+        P = helmholtz(0, ctx, octree=band_octree())
+    else:
+        P = reinit(band_octree(), ctx)
+    d = P["op"].diagonal().cpu().numpy()
+    ref = P["A"].diagonal()
+    assert np.max(np.abs(d - ref) / np.abs(ref)) <= 1e-12
+
+
+def test_laser_load_and_parameter_derivatives(ctx):
+    from oracle import assemble as asm
+    P = heat(8, ctx)
+    lz = P["wl"].params["laser"]
+    f, dF = P["op"].laser_load(lz["power"], lz["radius"], lz["x0"], lz["y0"], lz["absorptivity"], derivatives=True)
+    ref = asm.laser_rhs(P["dm"], **lz)
+    dref = asm.laser_rhs(P["dm"], **lz, derivatives=True)
+    scale = np.abs(ref).max()
+    assert np.abs(f.cpu().numpy() - ref).max() <= 1e-13 * scale
+    for k in range(4):
+        assert np.abs(dF[k].cpu().numpy() - dref[k]).max() <= 1e-12 * np.abs(dref[k]).max()
+
+
+def test_launch_count_increases(ctx):
+    P = helmholtz(4, ctx)
+    before = ctx.launch_count()
+    P["op"].apply(torch.ones(P["n"], dtype=torch.float64, device="cuda"))
+    assert ctx.launch_count() > before
