@@ -57,8 +57,11 @@ typedef struct mf_op mf_op;
 /* Thread-local text of the last failure (owned by the library, valid until the next call). */
 const char* mf_last_error(void);
 
-/* Context on CUDA device `device`; `cuda_stream` is a cudaStream_t (NULL = a stream the
- * library creates and owns).  The stream is borrowed: it must outlive the context. */
+/* Context on CUDA device `device`; `cuda_stream` is any cudaStream_t, including the special
+ * handles cudaStreamLegacy and cudaStreamPerThread; NULL asks for a non-blocking stream that
+ * the library creates and owns (its work is then unordered with the legacy default stream).
+ * A borrowed stream must outlive the context.  CUDA graphs are captured on a private stream
+ * and launched on this one. */
 mf_status mf_context_create(int device, void* cuda_stream, mf_ctx** out);
 void mf_context_destroy(mf_ctx* ctx);
 /* Replace the context's stream (borrowed). */

@@ -48,8 +48,11 @@ class Context:
         if stream is None:
             stream = torch.cuda.current_stream(device)
         self.stream = stream
+        # torch's default stream has handle 0; hand the library cudaStreamLegacy (0x1) so that
+        # its work stays ordered with torch's copies and kernels
+        handle = stream.cuda_stream or 0x1
         h = C.c_void_p()
-        check(lib.mf_context_create(device, C.c_void_p(stream.cuda_stream), C.byref(h)))
+        check(lib.mf_context_create(device, C.c_void_p(handle), C.byref(h)))
         self.h = h
         self.device = device
 

@@ -74,6 +74,8 @@ void mf_context_destroy(mf_ctx* c) {
   c->scratch.release();
   c->scalars.release();
   if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
+  if (c->capture_stream) cudaStreamDestroy(c->capture_stream);
+  if (c->fence) cudaEventDestroy(c->fence);
   delete c;
 }
 

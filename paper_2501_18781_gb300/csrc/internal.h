@@ -78,9 +78,13 @@ struct mf_ctx {
   bool own_stream = false;
   int64_t launches = 0;
   int sm_count = 0;
-  mf::DevBuf scratch;   // reduction partials (grown on demand)
+  mf::DevBuf scratch;   // reduction partials (fixed size, allocated with the context)
   mf::DevBuf scalars;   // device scalars of the solvers
   double* host_scalars = nullptr;  // pinned
+  // CUDA graphs are captured on a private stream (the legacy default stream cannot be
+  // captured), fenced against `stream` with an event on both sides.
+  cudaStream_t capture_stream = nullptr;
+  cudaEvent_t fence = nullptr;
 };
 
 struct mf_mesh {

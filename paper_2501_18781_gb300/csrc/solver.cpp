@@ -311,10 +311,18 @@ template <typename T> struct CG {
     int it = 0;
     if (use_graph && !exec) {
       cudaGraph_t g;
+      if (!c->capture_stream) {
+        MF_CUDA_TRY(cudaStreamCreateWithFlags(&c->capture_stream, cudaStreamNonBlocking));
+        MF_CUDA_TRY(cudaEventCreateWithFlags(&c->fence, cudaEventDisableTiming));
+      }
+      // capture on the private stream; nothing runs during capture, so no fence is needed here
+      cudaStream_t orig = c->stream;
+      c->stream = c->capture_stream;
       MF_CUDA_TRY(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
       mf_status st = MF_OK;
       for (int k = 0; k < check_every && st == MF_OK; ++k) st = iteration(x, S);
       cudaError_t e = cudaStreamEndCapture(c->stream, &g);
+      c->stream = orig;
       if (st != MF_OK) return st;
       if (e != cudaSuccess) return fail(MF_ECUDA, std::string("graph capture: ") + cudaGetErrorString(e));
       e = cudaGraphInstantiate(&exec, g, 0);

@@ -1,0 +1,160 @@
+"""Krylov solves on the GPU, judged by the TRUE residual computed with the oracle's own
+assembled matrix: ||b - A_oracle x_gpu|| <= tol ||b|| (1 + 1e-3); adjoint gradients against
+the oracle and against central finite differences of the GPU heat step."""
+import numpy as np
+import pytest
+
+import synthetic as syn
+from problems import band_octree, heat, helmholtz, oseen, reinit
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_2501_18781_gb300 import Context, build_library
+    build_library()
+    return Context(0)
+
+
+def true_residual(A, b, x):
+    return np.linalg.norm(b - A @ x) / np.linalg.norm(b)
+
+
+def solve_and_check(P, b, nrhs=1, tol=1e-10, **kw):
+    n = P["n"]
+    x, info = P["op"].solve(torch.tensor(b.ravel(), device="cuda"), nrhs=nrhs, tol=tol, **kw)
+    assert info["status"] == 0, info
+    X = x.cpu().numpy().reshape(nrhs, n)
+    B = b.reshape(nrhs, n)
+    for r in range(nrhs):
+        res = true_residual(P["A"], B[r], X[r])
+        assert res <= tol * (1 + 1e-3), (r, res, info)
+    return info
+
+
+@pytest.mark.parametrize("precond", ["jacobi", "chebyshev", "none"])
+def test_cg_helmholtz(ctx, precond):
+    P = helmholtz(10, ctx)
+    info = solve_and_check(P, syn.uniform_pm1(1, P["n"]), solver="cg", precond=precond)
+    assert info["iterations"] > 0
+
+
+def test_cg_graph_capture_batched(ctx):
+    P = helmholtz(8, ctx)
+    b = np.stack([syn.uniform_pm1(s, P["n"]) for s in (1, 2, 3)])
+    solve_and_check(P, b, nrhs=3, solver="cg", precond="jacobi", use_graph=True)
+
+
+def test_chebyshev_lambda_max_matches_oracle_lanczos(ctx):
+    from oracle import krylov
+    P = helmholtz(8, ctx)
+    _, info = P["op"].solve(torch.tensor(syn.uniform_pm1(1, P["n"]), device="cuda"), solver="cg",
+                            precond="chebyshev")
+    A = P["A"]
+    lam = krylov.lanczos_lambda_max(lambda v: A @ v, A.diagonal(), syn.uniform_pm1(9, P["n"]), steps=60)
+    # 20 Lanczos steps from another start vector: within a few percent of the converged value
+    assert abs(info["lambda_max"] / 1.1 - lam) <= 0.05 * lam
+
+
+def test_gmres_heat_with_convection(ctx):
+    P = heat(7, ctx, with_beta=True, kq=True)
+    b = syn.uniform_pm1(2, P["n"])
+    b[P["dm"].dirichlet] = 0.0
+    solve_and_check(P, b, solver="gmres", precond="jacobi", restart=30)
+
+
+def test_gmres_oseen_block_jacobi(ctx):
+    P = oseen(4, ctx)
+    b = syn.uniform_pm1(1, P["n"])
+    mask = np.concatenate([np.tile(P["dmu"].dirichlet, 3), np.zeros(P["dmp"].n_dofs, bool)])
+    b[mask] = 0.0
+    solve_and_check(P, b, solver="gmres", precond="block_jacobi", restart=50, maxit=20000)
+
+
+def test_defect_correction_mixed_precision_heat(ctx):
+    P = heat(10, ctx)
+    b = syn.uniform_pm1(4, P["n"])
+    b[P["dm"].dirichlet] = 0.0
+    info = solve_and_check(P, b, solver="defect_correction", precond="chebyshev", inner_tol=1e-4,
+                           inner_maxit=100)
+    assert info["outer_iterations"] >= 2
+
+
+def test_defect_correction_batched_reinit_octree(ctx):
+    P = reinit(band_octree(), ctx)
+    b = np.stack([syn.uniform_pm1(s, P["n"]) for s in range(1, 5)])
+    solve_and_check(P, b, nrhs=4, solver="defect_correction", precond="chebyshev")
+
+
+def test_cg_octree_helmholtz(ctx):
+    P = helmholtz(0, ctx, octree=band_octree())
+    solve_and_check(P, syn.uniform_pm1(5, P["n"]), solver="cg", precond="jacobi")
+
+
+def _gradient_case(ctx, n=4):
+    from oracle import heat as oheat
+    P = heat(n, ctx, with_beta=True, kq=True)
+    wl = P["wl"]
+    p = wl.params
+    dm = P["dm"]
+    x = dm.dof_coords()
+    ztop = wl.hi[2]
+    laser = dict(power=200.0, radius=150e-6, x0=0.0, y0=0.0, absorptivity=0.35)
+    th_prev = syn.heat_initial_temperature(*x.T, 150e-6, ztop) - p["t_ref"]
+    th_prev[dm.dirichlet] = 0
+    target = syn.heat_target_temperature(*x.T, ztop, 5, r=160e-6) - p["t_ref"]
+    return P, laser, th_prev, target
+
+
+def test_heat_adjoint_gradient_matches_oracle(ctx):
+    from oracle import heat as oheat
+    P, laser, th_prev, target = _gradient_case(ctx)
+    p = P["wl"].params
+    st = oheat.HeatStep(P["dm"], p["rhocp"], p["dt"], kq=P["kq"], beta=P["beta"])
+    cells = oheat.box_cells(P["dm"], 200e-6, 200e-6)
+    J, gl, gk, th, lam = oheat.gradients(st, th_prev, target, laser, cells)
+    lz = (laser["power"], laser["radius"], laser["x0"], laser["y0"], laser["absorptivity"])
+    Jg, glg, gkg, thg, lamg = P["op"].heat_step_gradient(lz, torch.tensor(th_prev, device="cuda"),
+                                                         torch.tensor(target, device="cuda"), 200e-6, 200e-6,
+                                                         solver="gmres", precond="jacobi", tol=1e-13, restart=50)
+    assert abs(Jg - J) <= 1e-9 * abs(J)
+    assert np.allclose(glg, gl, rtol=1e-8, atol=1e-10 * np.abs(gl).max())
+    gkg = gkg.cpu().numpy().reshape(gk.shape)
+    assert np.abs(gkg - gk).max() <= 1e-8 * np.abs(gk).max()
+
+
+def test_heat_adjoint_gradient_matches_central_differences(ctx):
+    P, laser, th_prev, target = _gradient_case(ctx)
+    tp, tt = torch.tensor(th_prev, device="cuda"), torch.tensor(target, device="cuda")
+    kw = dict(solver="gmres", precond="jacobi", tol=1e-13, restart=50)
+    names = ["power", "radius", "x0", "y0"]
+    lz = [laser[k] for k in names] + [laser["absorptivity"]]
+    J0, g, gk, _, _ = P["op"].heat_step_gradient(lz, tp, tt, 200e-6, 200e-6, **kw)
+    for i, k in enumerate(names):
+        step = 1e-6 * (abs(lz[i]) if k in ("power", "radius") else laser["radius"])
+        a, b = list(lz), list(lz)
+        a[i] += step
+        b[i] -= step
+        Ja = P["op"].heat_step_gradient(a, tp, tt, 200e-6, 200e-6, with_kq=False, **kw)[0]
+        Jb = P["op"].heat_step_gradient(b, tp, tt, 200e-6, 200e-6, with_kq=False, **kw)[0]
+        fd = (Ja - Jb) / (2 * step)
+        assert abs(g[i] - fd) <= 1e-6 * max(abs(fd), 1e-3 * max(abs(v) for v in g)), (k, g[i], fd)
+    # k_q: largest-magnitude entries, perturbing the per-Gauss-point field
+    gk = gk.cpu().numpy()
+    kq = P["kq"].ravel().copy()
+    for flat in np.argsort(-np.abs(gk))[:2]:
+        hh = 1e-6 * kq[flat]
+        vals = []
+        for sgn in (1, -1):
+            k2 = kq.copy()
+            k2[flat] += sgn * hh
+            P["op"].set_field("k_qpoint", torch.tensor(k2, device="cuda"))
+            vals.append(P["op"].heat_step_gradient(lz, tp, tt, 200e-6, 200e-6, with_kq=False, **kw)[0])
+        P["op"].set_field("k_qpoint", torch.tensor(kq, device="cuda"))
+        fd = (vals[0] - vals[1]) / (2 * hh)
+        assert abs(gk[flat] - fd) <= 1e-6 * abs(fd), (flat, gk[flat], fd)
