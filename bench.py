@@ -1,0 +1,366 @@
+#!/usr/bin/env python
+"""Benchmark: matrix-free operator apply throughput (GDoF/s) with its roofline, and the
+time of an implicit heat-step solve in fp64 vs mixed fp32/fp64 precision.
+
+One step = one application of the linearised incompressible Navier-Stokes (Oseen) operator,
+Q2 velocity / Q1 pressure on a uniform 64^3 mesh (6,714,692 DoFs), fp64, with density and
+viscosity from a tanh-smoothed level set (1000:1, 100:1) and a seeded convection field: gather,
+Gauss-point values and gradients, pointwise physics, integration and scatter-add, all in the
+library's CUDA kernels.  Inputs are resident in HBM; L2 is flushed between timed steps.
+
+    python bench.py [--steps K] [--warmup W] [--impl ours|reference] [--no-solve]
+Under torchrun (N > 1) every rank runs an independent replica on its own GPU.
+"""
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "GDoF/s of matrix-free operator apply & %HBM roofline; CG solve time FP64 vs mixed"
+WORKLOAD = "oseen_q2q1_interface_64"
+HBM_FALLBACK_GBS = 6800.0
+FP64_PEAK_TFLOPS = 1.25      # GB300 FP64 (vector and tensor) rate of the profiling recipe's table
+# Algorithmic flops of one Oseen Q2/Q1 cell apply as the kernel performs it (FMA = 2 flops):
+# pressure at the Gauss points and its test terms 945, three velocity components x
+# (3 value sweeps 405 + 27 Gauss points x 84) = 8019, integration sweeps and scaling 1304.
+OSEEN_FLOPS_PER_CELL = 945 + 8019 + 1304
+# Algorithmic HBM bytes of one fp64 Oseen apply: read u, write v (16 B per DoF), the nodal
+# level set and convection field the coefficients come from (4 x 8 B per velocity node).
+OSEEN_BYTES_PER_VEL_NODE = 4 * 8
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except Exception:
+        return {}
+
+
+class ClockSampler:
+    """Samples nvidia-smi SM clocks and throttle reasons every 200 ms while running."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index, self.rows, self.proc = index, [], None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([x.strip() for x in line.split(",")])
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm = [float(r[1]) for r in self.rows if len(r) >= 9 and r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in self.rows if len(r) >= 9 and r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in self.rows if len(r) >= 9 for i in range(4) if r[5 + i] == "Active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.rows)}
+
+
+def kernel_hash():
+    h = hashlib.sha256()
+    for f in ("apply.cu", "cellops.cuh", "scalar_local.cuh", "ops.h"):
+        with open(os.path.join(ROOT, "paper_2501_18781_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(workload):
+    """DRAM bytes per launch of the dominant kernel from the committed ncu summary, if it was
+    taken on the current kernel source (else None)."""
+    p = os.path.join(ROOT, "profiles", "dram_traffic.txt")
+    if not os.path.exists(p):
+        return None
+    kh = kernel_hash()
+    for line in open(p):
+        parts = line.split()
+        if len(parts) >= 3 and not line.startswith("#") and parts[0] == workload and parts[1] == kh:
+            return float(parts[2])
+    return None
+
+
+def build_oseen(ctx, n=64):
+    import numpy as np
+    import torch
+    import synthetic as syn
+    from paper_2501_18781_gb300 import DofMap, Mesh, Operator
+    wl = syn.scaled(syn.OSEEN_INTERFACE, n)
+    p = wl.params
+    mesh = Mesh.uniform(ctx, n, wl.lo, wl.hi)
+    mu, mp = DofMap(mesh, 2, 0b011111), DofMap(mesh, 1, 0)
+    x = mu.coords()
+    t1, t2 = syn.wavy_plane_phases(wl.seed)
+    phi = syn.initial_level_set(syn.wavy_plane_distance(*x.T, t1, t2), wl.eps)
+    beta = np.array(syn.convection_field(*x.T, wl.seed, wl.lo, wl.hi))
+    sigma = 1.0 / (p["dt_cfl"] * wl.h)
+    op = Operator(ctx, "oseen", [mu, mp], sigma=sigma, rho_l=p["rho_l"], rho_g=p["rho_g"], mu_l=p["mu_l"],
+                  mu_g=p["mu_g"], eps=wl.eps)
+    op.set_field("phi", torch.tensor(phi, device="cuda"))
+    op.set_field("beta", torch.tensor(beta.ravel(), device="cuda"))
+    return op, mu, mp, mesh
+
+
+def time_apply(op, src, dst, steps, warmup, flush):
+    import torch
+    for _ in range(warmup):
+        op.apply(src, dst)
+    torch.cuda.synchronize()
+    times = []
+    for _ in range(steps):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        op.apply(src, dst)
+        e1.record()
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1) / 1e3)
+    return times
+
+
+def heat_solve_comparison(ctx, n=128):
+    """Implicit heat step on n^3 Q2 cells: fp64 CG with Chebyshev(4)-Jacobi vs fp32 inner CG
+    (same preconditioner in fp32) inside fp64 defect correction, both to 1e-10."""
+    import numpy as np
+    import torch
+    import synthetic as syn
+    from paper_2501_18781_gb300 import DofMap, Mesh, Operator
+    wl = syn.scaled(syn.HEAT_LASER, n)
+    p = wl.params
+    mesh = Mesh.uniform(ctx, n, wl.lo, wl.hi)
+    m = DofMap(mesh, 2, 1 << 4)
+    x = m.coords()
+    T_prev = syn.heat_initial_temperature(*x.T, p["laser"]["radius"], wl.hi[2])
+    op = Operator(ctx, "heat", [m], rhocp=p["rhocp"], dt=p["dt"], k0=p["k0"], t_boil=p["t_boil"], coef_mode=1)
+    op.set_field("t_prev", torch.tensor(T_prev, device="cuda"))
+    b = torch.tensor(syn.uniform_pm1(1, m.n_dofs), device="cuda")
+    b[torch.tensor(m.export(cell_map=False, constraints=False, coords=False)["dirichlet"], device="cuda")] = 0
+    out = {"workload": wl.name, "n_dofs": m.n_dofs, "tol": 1e-10}
+    for name, kw in (("fp64", dict(solver="cg", precond="chebyshev")),
+                     ("mixed", dict(solver="defect_correction", precond="chebyshev", inner_tol=1e-4,
+                                    inner_maxit=100))):
+        op.solve(b, tol=1e-10, use_graph=True, **kw)          # set-up + warm-up
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        _, info = op.solve(b, tol=1e-10, use_graph=True, **kw)
+        torch.cuda.synchronize()
+        out[name] = {"seconds": time.perf_counter() - t0, "iterations": info["iterations"],
+                     "outer": info["outer_iterations"], "rel_residual": info["rel_residual"],
+                     "status": info["status"]}
+    out["speedup_mixed_over_fp64"] = out["fp64"]["seconds"] / out["mixed"]["seconds"]
+    return out
+
+
+def cpu_oracle_apply(n_sample, budget_s=8.0):
+    """The oracle (assembled CSR from full-quadrature element matrices) applied on the host:
+    returns GDoF/s of its SpMV on an n_sample^3 instance of the same workload."""
+    import numpy as np
+    import synthetic as syn
+    from oracle import assemble as asm
+    from oracle import mesh as omesh
+    wl = syn.scaled(syn.OSEEN_INTERFACE, n_sample)
+    p = wl.params
+    dmu = omesh.uniform_dofmap(n_sample, wl.lo, wl.hi, 2, 0b011111)
+    dmp = omesh.uniform_dofmap(n_sample, wl.lo, wl.hi, 1, 0)
+    x = dmu.dof_coords()
+    t1, t2 = syn.wavy_plane_phases(wl.seed)
+    phi = syn.initial_level_set(syn.wavy_plane_distance(*x.T, t1, t2), wl.eps)
+    beta = np.array(syn.convection_field(*x.T, wl.seed, wl.lo, wl.hi))
+    A = asm.oseen_matrix(dmu, dmp, phi, beta, 1.0 / (p["dt_cfl"] * wl.h), p["rho_l"], p["rho_g"], p["mu_l"],
+                         p["mu_g"])
+    u = syn.uniform_pm1(1, A.shape[0])
+    A @ u
+    reps, t0 = 0, time.perf_counter()
+    while time.perf_counter() - t0 < budget_s:
+        A @ u
+        reps += 1
+    dt = time.perf_counter() - t0
+    return A.shape[0] * reps / dt / 1e9, A.shape[0], reps, dt
+
+
+def reference_arm(args, rank, world):
+    out = {"impl": "reference", "metric": METRIC, "unit": "GDoF/s", "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+           "dtype": "f64", "data": "synthetic"}
+    if rank != 0:
+        return None
+    import numpy as np
+    import synthetic as syn
+    from oracle import assemble as asm
+    from oracle import mesh as omesh
+    n_sample = 12
+    wl = syn.scaled(syn.OSEEN_INTERFACE, n_sample)
+    p = wl.params
+    dmu = omesh.uniform_dofmap(n_sample, wl.lo, wl.hi, 2, 0b011111)
+    dmp = omesh.uniform_dofmap(n_sample, wl.lo, wl.hi, 1, 0)
+    x = dmu.dof_coords()
+    t1, t2 = syn.wavy_plane_phases(wl.seed)
+    phi = syn.initial_level_set(syn.wavy_plane_distance(*x.T, t1, t2), wl.eps)
+    beta = np.array(syn.convection_field(*x.T, wl.seed, wl.lo, wl.hi))
+    A = asm.oseen_matrix(dmu, dmp, phi, beta, 1.0 / (p["dt_cfl"] * wl.h), p["rho_l"], p["rho_g"], p["mu_l"],
+                         p["mu_g"])
+    u = syn.uniform_pm1(1, A.shape[0])
+    for _ in range(args.warmup):
+        A @ u
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        A @ u
+    dt = time.perf_counter() - t0
+    val = A.shape[0] * args.steps / dt / 1e9
+    out.update(value=val, ms_per_step=dt / args.steps * 1e3,
+               config={"workload": wl.name, "n_dofs": int(A.shape[0]), "note": "oracle CSR SpMV (assembly untimed)"},
+               cpu_baseline={"value": val, "unit": "GDoF/s", "cores": 1, "kind": "oracle",
+                             "sample": f"{wl.name}: assembled CSR SpMV, {args.steps} steps"},
+               e2e={"value": val, "unit": "GDoF/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0})
+    return out
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-solve", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--n", type=int, default=64)
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        out = reference_arm(args, rank, world)
+        if out is not None:
+            print(json.dumps(out))
+        return
+
+    import torch
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    from paper_2501_18781_gb300 import Context, build_library
+    build_library()
+    ctx = Context(local)
+    op, mu, mp, mesh = build_oseen(ctx, args.n)
+    n = op.n
+    ncells = mu.n_cells
+    import synthetic as syn
+    src = torch.tensor(syn.uniform_pm1(1, n), device="cuda")
+    dst = torch.empty_like(src)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")   # > 129 MB L2
+
+    # warm-up and set-up (Gauss-point coefficient tables) outside the timed region
+    for _ in range(args.warmup):
+        op.apply(src, dst)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    l0 = ctx.launch_count()
+    with ClockSampler(local) as clocks:
+        times = time_apply(op, src, dst, args.steps, 0, flush)
+    launches = ctx.launch_count() - l0
+    total = sum(times)
+    if dist:
+        t = torch.tensor([total], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total = float(t.item())
+    value = n * args.steps * world / total / 1e9
+    mean = total / args.steps
+
+    # end to end through the public API: pinned host input -> device -> apply -> host output
+    hsrc = torch.empty(n, dtype=torch.float64, pin_memory=True)
+    hsrc.copy_(src.cpu())
+    hdst = torch.empty(n, dtype=torch.float64, pin_memory=True)
+    dsrc = torch.empty_like(src)
+    for _ in range(2):
+        dsrc.copy_(hsrc, non_blocking=True)
+        op.apply(dsrc, dst)
+        hdst.copy_(dst, non_blocking=True)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        dsrc.copy_(hsrc, non_blocking=True)
+        op.apply(dsrc, dst)
+        hdst.copy_(dst, non_blocking=True)
+    e1.record()
+    e1.synchronize()
+    e2e_t = e0.elapsed_time(e1) / 1e3
+    e2e = {"value": n * args.steps * world / e2e_t / 1e9, "unit": "GDoF/s",
+           "h2d_bytes_per_step": n * 8, "d2h_bytes_per_step": n * 8}
+
+    peaks = measured_peaks()
+    hbm = peaks.get("hbm_gbs", HBM_FALLBACK_GBS)
+    flops = OSEEN_FLOPS_PER_CELL * ncells
+    alg_bytes = 16 * n + OSEEN_BYTES_PER_VEL_NODE * mu.n_dofs
+    achieved = flops / mean / 1e12
+    out = {
+        "metric": METRIC, "value": value, "unit": "GDoF/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": mean * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"oseen_q2q1_interface_{args.n}", "n_dofs": n, "cells": ncells,
+                   "velocity": "Q2 x 3", "pressure": "Q1", "parallelism": "replicas" if world > 1 else "single",
+                   "l2": "flushed between timed steps (256 MB write)", "variant": op.variant},
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                     "frac": achieved / FP64_PEAK_TFLOPS, "traffic": ncu_traffic(f"oseen_q2q1_interface_{args.n}"),
+                     "flops_per_launch": flops, "peak_source": "GB300 FP64 rate of the profiling recipe"},
+        "hbm_roofline": {"achieved": alg_bytes / mean / 1e9, "peak": hbm, "unit": "GB/s",
+                         "frac": alg_bytes / mean / 1e9 / hbm, "bytes_per_launch": alg_bytes,
+                         "peak_source": "MEASURED_PEAKS.json" if "hbm_gbs" in peaks else "fallback"},
+        "e2e": e2e, "gpu_launches": launches, "clocks": clocks.summary(),
+    }
+    # the same apply in fp32 (context for the mixed-precision solver)
+    src32, dst32 = src.float(), torch.empty(n, dtype=torch.float32, device="cuda")
+    t32 = time_apply(op, src32, dst32, max(5, args.steps // 2), 3, flush)
+    out["fp32_apply"] = {"value": n / (sum(t32) / len(t32)) / 1e9, "unit": "GDoF/s",
+                         "ms_per_step": sum(t32) / len(t32) * 1e3}
+    if not args.no_solve and rank == 0:
+        out["solve"] = heat_solve_comparison(ctx)
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        v, nd, reps, dt = cpu_oracle_apply(16)
+        out["cpu_baseline"] = {"value": v, "unit": "GDoF/s", "cores": 1, "kind": "oracle",
+                               "sample": f"oseen_q2q1_interface_16 ({nd} DoFs): assembled-CSR SpMV x {reps} "
+                                         f"in {dt:.1f} s (assembly untimed)"}
+    if rank == 0:
+        print(json.dumps(out))
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()
