@@ -236,7 +236,8 @@ def reference_arm(args, rank, world):
     dt = time.perf_counter() - t0
     val = A.shape[0] * args.steps / dt / 1e9
     out.update(value=val, ms_per_step=dt / args.steps * 1e3,
-               config={"workload": wl.name, "n_dofs": int(A.shape[0]), "note": "oracle CSR SpMV (assembly untimed)"},
+               config={"workload": WORKLOAD, "sample": wl.name, "n_dofs": int(A.shape[0]),
+                       "note": "oracle: assembled-CSR SpMV of a 12^3 instance (assembly untimed)"},
                cpu_baseline={"value": val, "unit": "GDoF/s", "cores": 1, "kind": "oracle",
                              "sample": f"{wl.name}: assembled CSR SpMV, {args.steps} steps"},
                e2e={"value": val, "unit": "GDoF/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0})
