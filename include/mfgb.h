@@ -187,6 +187,15 @@ typedef struct {
   double seconds;          /* wall time of the call */
 } mf_solve_info;
 
+/* Inner products of the Krylov solvers (Appendix B: CG / GMRES): out[k] = sum_i x[k ld + i]
+ * y[k ld + i] for k < nvec (1 <= nvec <= 64), device vectors of dtype MF_F64 or MF_F32, fp64
+ * accumulation, out a device array of nvec doubles.  Partial sums go to the context's
+ * reduction workspace (allocated once with the context) over a fixed grid and are summed in a
+ * fixed order, so the result is bit-reproducible.  Asynchronous. */
+mf_status mf_dot(mf_ctx* ctx, const void* x, const void* y, int64_t n, int64_t ld, int nvec, int dtype,
+                 double* out);
+
+
 /* Solve A x = b for each of nrhs right-hand sides (stored n apart), x0 = 0, in fp64 (b, x
  * fp64 device vectors).  Synchronising.  Returns MF_ENOTCONV with info filled when the
  * tolerance is not reached within maxit. */

@@ -56,6 +56,14 @@ class Context:
         self.h = h
         self.device = device
 
+    def dot(self, x, y, nvec=1):
+        """Deterministic fp64-accumulated inner products of nvec vector pairs (device tensor out)."""
+        import torch
+        out = torch.empty(nvec, dtype=torch.float64, device="cuda")
+        n = x.numel() // nvec
+        check(_lib.load().mf_dot(self.h, _ptr(x), _ptr(y), n, n, nvec, _dtype_code(x), _ptr(out)))
+        return out
+
     def launch_count(self):
         return int(_lib.load().mf_context_launch_count(self.h))
 

@@ -558,6 +558,16 @@ mf_status mf_apply_transpose(mf_op* op, const void* src, void* dst, int nrhs, in
   MF_GUARD_END
 }
 
+mf_status mf_dot(mf_ctx* c, const void* x, const void* y, int64_t n, int64_t ld, int nvec, int dtype, double* out) {
+  MF_GUARD_BEGIN
+  if (!c || !x || !y || !out) return fail(MF_EINVAL, "NULL argument");
+  if (n < 0 || nvec < 1 || nvec > 64 || (nvec > 1 && ld < n)) return fail(MF_EINVAL, "need n >= 0, 1 <= nvec <= 64, ld >= n");
+  if (dtype == MF_F64) return dot_batched<double>(c, (const double*)x, (const double*)y, n, ld, nvec, out);
+  if (dtype == MF_F32) return dot_batched<float>(c, (const float*)x, (const float*)y, n, ld, nvec, out);
+  return fail(MF_EUNSUPPORTED, "dot precision must be MF_F64 or MF_F32");
+  MF_GUARD_END
+}
+
 mf_status mf_diagonal(mf_op* op, void* dst, int dtype) {
   MF_GUARD_BEGIN
   if (!op || !dst) return fail(MF_EINVAL, "NULL argument");

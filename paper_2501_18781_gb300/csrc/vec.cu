@@ -248,6 +248,19 @@ template <typename TX, typename TY> mf_status dot(mf_ctx* ctx, const TX* x, cons
 template mf_status dot<double, double>(mf_ctx*, const double*, const double*, int64_t, double*);
 template mf_status dot<float, float>(mf_ctx*, const float*, const float*, int64_t, double*);
 
+template <typename T>
+mf_status dot_batched(mf_ctx* ctx, const T* x, const T* y, int64_t n, int64_t ld, int nvec, double* out) {
+  double* part;
+  MF_TRY(scratch(ctx, 2 * kRedBlocks * size_t(nvec), &part));
+  k_dot2_partial<T, T><<<dim3(kRedBlocks, nvec), kRedThreads, 0, ctx->stream>>>(x, y, nullptr, nullptr, n, ld, part);
+  LAUNCH_CHECK();
+  k_finish<<<nvec, kRedThreads, 0, ctx->stream>>>(part, kRedBlocks, out, 0, nullptr);
+  LAUNCH_CHECK();
+  return MF_OK;
+}
+template mf_status dot_batched<double>(mf_ctx*, const double*, const double*, int64_t, int64_t, int, double*);
+template mf_status dot_batched<float>(mf_ctx*, const float*, const float*, int64_t, int64_t, int, double*);
+
 mf_status norm2_sq(mf_ctx* ctx, const double* x, int64_t n, double* out) { return dot<double, double>(ctx, x, x, n, out); }
 
 template <typename TX, typename TY> mf_status axpby(mf_ctx* ctx, int64_t n, double a, const TX* x, double b, TY* y) {

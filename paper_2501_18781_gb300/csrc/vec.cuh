@@ -14,6 +14,9 @@ constexpr size_t kScratchDoubles = size_t(2) * kRedBlocks * 64;  // up to 64 rig
 template <typename TX, typename TY>
 mf_status dot(mf_ctx* ctx, const TX* x, const TY* y, int64_t n, double* out);
 mf_status norm2_sq(mf_ctx* ctx, const double* x, int64_t n, double* out);
+// out[k] = x_k . y_k for nvec vector pairs ld apart (device out, fp64 accumulation)
+template <typename T>
+mf_status dot_batched(mf_ctx* ctx, const T* x, const T* y, int64_t n, int64_t ld, int nvec, double* out);
 
 // y = a x + b y (host scalars), mixed precisions allowed
 template <typename TX, typename TY>

@@ -130,3 +130,20 @@ def test_launch_count_increases(ctx):
     before = ctx.launch_count()
     P["op"].apply(torch.ones(P["n"], dtype=torch.float64, device="cuda"))
     assert ctx.launch_count() > before
+
+
+@pytest.mark.parametrize("dt", ["f64", "f32"])
+def test_dot_products_against_fp64_numpy(ctx, dt):
+    n, nvec = 1_000_003, 3
+    X = np.stack([syn.uniform_pm1(10 + k, n) for k in range(nvec)])
+    Y = np.stack([syn.uniform_pm1(20 + k, n) for k in range(nvec)])
+    tdt = torch.float64 if dt == "f64" else torch.float32
+    x = torch.tensor(X.ravel(), device="cuda", dtype=tdt)
+    y = torch.tensor(Y.ravel(), device="cuda", dtype=tdt)
+    out = ctx.dot(x, y, nvec).cpu().numpy()
+    Xs, Ys = x.cpu().double().numpy().reshape(nvec, n), y.cpu().double().numpy().reshape(nvec, n)
+    ref = np.array([np.dot(Xs[k], Ys[k]) for k in range(nvec)])
+    bound = np.array([np.dot(np.abs(Xs[k]), np.abs(Ys[k])) for k in range(nvec)])
+    assert np.all(np.abs(out - ref) <= 1e-13 * bound)
+    again = ctx.dot(x, y, nvec).cpu().numpy()
+    assert np.array_equal(out, again)     # fixed-grid reduction: bit-reproducible
