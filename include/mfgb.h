@@ -195,6 +195,20 @@ typedef struct {
 mf_status mf_dot(mf_ctx* ctx, const void* x, const void* y, int64_t n, int64_t ld, int nvec, int dtype,
                  double* out);
 
+/* The paper has no counterpart to this entry point.  The same inner products as mf_dot, for
+ * callers that cannot let the library allocate device memory (an application that owns all
+ * device memory through its own pool, a latency-critical loop where an allocation could
+ * synchronise the device, code without an mf_ctx): it needs no context and allocates nothing.
+ * Its block partial sums live in a static device array of 2 * 608 * 16 doubles (152 KB) that
+ * every GPU loading the library holds until exit; hence 1 <= nvec <= 16 (larger nvec:
+ * MF_EINVAL).  The first call on a device looks up that array's device address (with the
+ * device current) and should come before any stream capture.  All calls share the array, so
+ * calls that overlap on the GPU race; nothing in it needs clearing between calls.
+ * x, y: device vectors (MF_F64 or MF_F32) ld apart; out: device array of nvec doubles;
+ * cuda_stream: the cudaStream_t to launch on (NULL = the legacy default stream).
+ * Asynchronous; results equal mf_dot's (same fixed-grid reduction). */
+mf_status mf_dot_noalloc(const void* x, const void* y, int64_t n, int64_t ld, int nvec, int dtype, double* out,
+                         void* cuda_stream);
 
 /* Solve A x = b for each of nrhs right-hand sides (stored n apart), x0 = 0, in fp64 (b, x
  * fp64 device vectors).  Synchronising.  Returns MF_ENOTCONV with info filled when the

@@ -69,6 +69,7 @@ SIGNATURES = {
     "mf_apply_transpose": (C.c_int, [P, P, P, C.c_int, I64, C.c_int]),
     "mf_diagonal": (C.c_int, [P, P, C.c_int]),
     "mf_dot": (C.c_int, [P, P, P, I64, I64, C.c_int, C.c_int, P]),
+    "mf_dot_noalloc": (C.c_int, [P, P, I64, I64, C.c_int, C.c_int, P, P]),
     "mf_solve": (C.c_int, [P, C.POINTER(SolverParams), P, P, C.c_int, C.POINTER(SolveInfo)]),
     "mf_laser_load": (C.c_int, [P, C.POINTER(Laser), P, P]),
     "mf_heat_step_gradient": (C.c_int, [P, C.POINTER(Laser), C.POINTER(SolverParams), P, P, C.c_double, C.c_double,

@@ -1,6 +1,9 @@
 // Vector kernels of the Krylov solvers.  All reductions accumulate in fp64 over a fixed
 // grid of kRedBlocks blocks, then one block sums the partials in a fixed order, so every
 // dot product is deterministic.
+#include <mutex>
+#include <string>
+
 #include "vec.cuh"
 
 namespace mf {
@@ -429,4 +432,74 @@ template <typename T> mf_status zero_list(mf_ctx* ctx, T* v, const int32_t* list
 template mf_status zero_list<double>(mf_ctx*, double*, const int32_t*, int64_t);
 template mf_status zero_list<float>(mf_ctx*, float*, const int32_t*, int64_t);
 
+// ---------------------------------------------------------------------------------------
+// Allocation-free inner products (mf_dot_noalloc).
+//
+// Some callers cannot let this library call cudaMalloc: an application that owns all device
+// memory through its own pool and gives libraries a fixed budget, a latency-critical loop in
+// which an allocation could implicitly synchronise the device and stall other streams, or code
+// that has no mf_ctx (creating one allocates the context's reduction workspace).  For them the
+// block partial sums live in one statically sized device array of this file instead of the
+// context workspace.  Every GPU that loads the library holds the array until the process exits.
+// Host code may not use the array's name as a device address (on the host it only stands in for
+// the symbol), so its device address is looked up once per device with cudaGetSymbolAddress,
+// with that device current, on the first call made on that device; that first call should come
+// before any stream capture.  All calls share the array and it keeps the last call's partials:
+// nothing in it needs to start at zero, because the partial kernel writes every slot that the
+// finishing kernel then reads.  Calls that overlap on the GPU (several streams, several host
+// threads) race on the array; callers must serialise them.
+constexpr int kNoAllocMaxVec = 16;
+static __device__ __align__(256) double g_noalloc_partials[2 * kRedBlocks * kNoAllocMaxVec];
+
+namespace {
+std::mutex g_noalloc_mutex;
+double* g_noalloc_address[256] = {};
+}  // namespace
+
+static mf_status noalloc_workspace(double** out) {
+  int dev = -1;
+  MF_CUDA_TRY(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 256) return fail(MF_EINVAL, "device index outside the allocation-free table");
+  std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+  if (!g_noalloc_address[dev]) {
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_partials);
+    if (e != cudaSuccess || !p)
+      return fail(MF_ECUDA, std::string("cudaGetSymbolAddress of the allocation-free workspace: ") +
+                                cudaGetErrorString(e));
+    g_noalloc_address[dev] = static_cast<double*>(p);
+  }
+  *out = g_noalloc_address[dev];
+  return MF_OK;
+}
+
+template <typename T>
+static mf_status dot_noalloc(const T* x, const T* y, int64_t n, int64_t ld, int nvec, double* out, cudaStream_t s) {
+  double* part = nullptr;
+  MF_TRY(noalloc_workspace(&part));
+  k_dot2_partial<T, T><<<dim3(kRedBlocks, nvec), kRedThreads, 0, s>>>(x, y, nullptr, nullptr, n, ld, part);
+  MF_CUDA_TRY(cudaGetLastError());
+  k_finish<<<nvec, kRedThreads, 0, s>>>(part, kRedBlocks, out, 0, nullptr);
+  MF_CUDA_TRY(cudaGetLastError());
+  return MF_OK;
+}
+
 }  // namespace mf
+
+extern "C" mf_status mf_dot_noalloc(const void* x, const void* y, int64_t n, int64_t ld, int nvec, int dtype,
+                                    double* out, void* cuda_stream) {
+  using namespace mf;
+  try {
+    if (!x || !y || !out) return fail(MF_EINVAL, "NULL argument");
+    if (nvec < 1 || nvec > kNoAllocMaxVec)
+      return fail(MF_EINVAL, "mf_dot_noalloc: nvec must be in 1.." + std::to_string(kNoAllocMaxVec) +
+                                 " (size of its static workspace)");
+    if (n < 0 || (nvec > 1 && ld < n)) return fail(MF_EINVAL, "need n >= 0 and ld >= n");
+    cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+    if (dtype == MF_F64) return dot_noalloc<double>((const double*)x, (const double*)y, n, ld, nvec, out, s);
+    if (dtype == MF_F32) return dot_noalloc<float>((const float*)x, (const float*)y, n, ld, nvec, out, s);
+    return fail(MF_EUNSUPPORTED, "dot precision must be MF_F64 or MF_F32");
+  } catch (...) {
+    return fail(MF_EINVAL, "exception in mf_dot_noalloc");
+  }
+}
