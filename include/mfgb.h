@@ -47,7 +47,10 @@ typedef int mf_status;
 #define MF_ETIMEOUT (-5)      /* a device-side bounded wait ran out */
 #define MF_EUNSUPPORTED (-6)  /* valid request that this build does not implement */
 
-typedef enum { MF_F64 = 0, MF_F32 = 1, MF_F16 = 2, MF_BF16 = 3 } mf_dtype;
+/* MF_DF64: fp64 vectors, cell arithmetic in double-float (pairs of fp32 with error-free
+ * products and sums, 48-bit significand) on the fp32 pipes, which GB300 runs at ~62x its fp64
+ * rate; accurate to a few 1e-14 relative to |A||u| componentwise. */
+typedef enum { MF_F64 = 0, MF_F32 = 1, MF_F16 = 2, MF_BF16 = 3, MF_DF64 = 4 } mf_dtype;
 
 typedef struct mf_ctx mf_ctx;
 typedef struct mf_mesh mf_mesh;
@@ -176,7 +179,7 @@ typedef struct {
   double inner_tol;    /* defect correction: inner relative tolerance */
   double cheby_ratio;  /* Chebyshev interval [lambda_max/ratio, 1.1 lambda_max] */
   int lanczos_steps;   /* steps of the lambda_max estimate of D^-1 A */
-  int reserved;
+  int fp64_arith;      /* arithmetic of the fp64 operator applies: 0 fp64 pipes, 1 double-float */
 } mf_solver_params;
 
 typedef struct {

@@ -155,8 +155,10 @@ class DofMap:
 
 
 def solver_params(solver="cg", precond="jacobi", tol=1e-10, maxit=5000, restart=50, cheby_degree=4,
-                  inner_tol=1e-4, inner_maxit=100, use_graph=False, cheby_ratio=30.0, lanczos_steps=20):
+                  inner_tol=1e-4, inner_maxit=100, use_graph=False, cheby_ratio=30.0, lanczos_steps=20,
+                  fp64_arith="f64"):
     s = _lib.SolverParams()
+    s.fp64_arith = {"f64": 0, "df64": 1}[fp64_arith]
     s.solver = {"cg": MF_SOLVER_CG, "gmres": MF_SOLVER_GMRES, "defect_correction": MF_SOLVER_DEFECT_CORRECTION}[solver]
     s.precond = {"none": MF_PREC_NONE, "jacobi": MF_PREC_JACOBI, "chebyshev": MF_PREC_CHEBYSHEV,
                  "block_jacobi": MF_PREC_BLOCK_JACOBI}[precond]
@@ -193,12 +195,18 @@ class Operator:
         self._fields[name] = t
         check(_lib.load().mf_operator_set_field(self.h, self.FIELDS[name], _ptr(t), _dtype_code(t), t.numel()))
 
-    def apply(self, src, dst=None, nrhs=1, transpose=False):
+    def apply(self, src, dst=None, nrhs=1, transpose=False, arith=None):
+        """dst = A src; fp64 tensors may ask for arith="df64" (double-float cell arithmetic)."""
         import torch
         if dst is None:
             dst = torch.empty_like(src)
+        code = _dtype_code(src)
+        if arith == "df64":
+            if code != MF_F64:
+                raise TypeError("df64 arithmetic applies to fp64 tensors")
+            code = _lib.MF_DF64
         fn = _lib.load().mf_apply_transpose if transpose else _lib.load().mf_apply
-        check(fn(self.h, _ptr(src), _ptr(dst), nrhs, src.numel() // nrhs, _dtype_code(src)))
+        check(fn(self.h, _ptr(src), _ptr(dst), nrhs, src.numel() // nrhs, code))
         return dst
 
     def diagonal(self, dtype=None):

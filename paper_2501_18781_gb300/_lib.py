@@ -6,7 +6,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libmfgb.so")
 
 MF_OK, MF_EINVAL, MF_ENOMEM, MF_ECUDA, MF_ENOTCONV, MF_ETIMEOUT, MF_EUNSUPPORTED = 0, -1, -2, -3, -4, -5, -6
-MF_F64, MF_F32, MF_F16, MF_BF16 = 0, 1, 2, 3
+MF_F64, MF_F32, MF_F16, MF_BF16, MF_DF64 = 0, 1, 2, 3, 4
 MF_OP_HELMHOLTZ, MF_OP_HEAT, MF_OP_OSEEN, MF_OP_REINIT = 0, 1, 2, 3
 MF_HEAVISIDE_TANH, MF_HEAVISIDE_SINE = 0, 1
 MF_COEF_INKERNEL, MF_COEF_QPOINT = 0, 1
@@ -30,7 +30,7 @@ class SolverParams(C.Structure):
     _fields_ = [("solver", C.c_int), ("precond", C.c_int), ("inner_dtype", C.c_int), ("restart", C.c_int),
                 ("cheby_degree", C.c_int), ("maxit", C.c_int), ("inner_maxit", C.c_int), ("use_graph", C.c_int),
                 ("tol", C.c_double), ("inner_tol", C.c_double), ("cheby_ratio", C.c_double),
-                ("lanczos_steps", C.c_int), ("reserved", C.c_int)]
+                ("lanczos_steps", C.c_int), ("fp64_arith", C.c_int)]
 
 
 class SolveInfo(C.Structure):

@@ -471,26 +471,32 @@ template <typename T> OseenArgs<T> oseen_args(const mf_op* op, const T* src, T* 
 template OseenArgs<double> oseen_args<double>(const mf_op*, const double*, double*);
 
 // dst = A src (or A^T src), nrhs vectors ld apart, precision T.
-template <typename T> mf_status apply_impl(mf_op* op, const T* src, T* dst, int nrhs, int64_t ld, bool transpose) {
+// prec: PREC_F64 / PREC_DF64 for fp64 vectors (-1: the operator's fp64 arithmetic), PREC_F32 for fp32.
+template <typename T>
+mf_status apply_impl(mf_op* op, const T* src, T* dst, int nrhs, int64_t ld, bool transpose, int prec) {
   const bool f32 = sizeof(T) == 4;
+  if (f32) prec = PREC_F32;
+  else if (prec != PREC_F64 && prec != PREC_DF64) prec = op->f64_prec;
+  const bool df = prec == PREC_DF64;
   mf_ctx* c = op->ctx;
   MF_TRY(check_fields(op));
-  const int mode = f32 ? op->mode32 : op->mode64;
+  const int mode = df ? 1 : (f32 ? op->mode32 : op->mode64);
   const bool needs_tables = op->p.kind == MF_OP_OSEEN || mode == 1 || (op->p.kind == MF_OP_HEAT && (op->beta || op->kq_user));
   if (needs_tables) MF_TRY(ensure_tables(op));
   if (ld == op->n) MF_CUDA_TRY(cudaMemsetAsync(dst, 0, sizeof(T) * op->n * nrhs, c->stream));
   else
     for (int r = 0; r < nrhs; ++r) MF_CUDA_TRY(cudaMemsetAsync(dst + r * ld, 0, sizeof(T) * op->n, c->stream));
+  const char* pname = f32 ? "/f32" : (df ? "/df64" : "/f64");
   if (op->p.kind == MF_OP_OSEEN) {
     if (transpose) return fail(MF_EUNSUPPORTED, "transpose of the Oseen operator");
     const int64_t nu = op->map[0]->n_dofs;
     for (int r = 0; r < nrhs; ++r) {
       OseenArgs<T> a = oseen_args<T>(op, src + r * ld, dst + r * ld);
-      MF_TRY(launch_oseen_apply(c, op->map[0], f32, &a));
+      MF_TRY(launch_oseen_apply(c, op->map[0], prec, &a));
       for (int comp = 0; comp < 3; ++comp)
         MF_TRY(launch_dirichlet_copy(c, op->map[0], src + r * ld, dst + r * ld, 1, ld, comp * nu, f32));
     }
-    op->variant = std::string("oseen_q2q1/") + (f32 ? "f32" : "f64") + "/tabulated";
+    op->variant = std::string("oseen_q2q1") + pname + "/tabulated";
     return MF_OK;
   }
   const int kind = scalar_kind(op);
@@ -501,17 +507,16 @@ template <typename T> mf_status apply_impl(mf_op* op, const T* src, T* dst, int 
   }
   int m = mode;
   if (kind == K_HEAT && op->kq_user) m = 1;
-  if (!op->map[0]->uniform && !needs_tables && m == 1) MF_TRY(ensure_tables(op));
   ScalarArgs<T> a = scalar_args<T>(op, src, dst, nrhs, ld);
-  MF_TRY(launch_scalar_apply(c, op->map[0], kind, m, beta, transpose, f32, &a));
+  MF_TRY(launch_scalar_apply(c, op->map[0], kind, m, beta, transpose, prec, &a));
   MF_TRY(launch_dirichlet_copy(c, op->map[0], src, dst, nrhs, ld, 0, f32));
   op->variant = std::string(kind == K_HELM ? "helmholtz" : kind == K_HEAT ? "heat" : "reinit") +
-                (op->map[0]->uniform ? "/uniform" : "/octree") + (f32 ? "/f32" : "/f64") +
+                (op->map[0]->uniform ? "/uniform" : "/octree") + pname +
                 (m == 0 ? "/inkernel" : "/tabulated") + (beta ? (transpose ? "/conv-T" : "/conv") : "");
   return MF_OK;
 }
-template mf_status apply_impl<double>(mf_op*, const double*, double*, int, int64_t, bool);
-template mf_status apply_impl<float>(mf_op*, const float*, float*, int, int64_t, bool);
+template mf_status apply_impl<double>(mf_op*, const double*, double*, int, int64_t, bool, int);
+template mf_status apply_impl<float>(mf_op*, const float*, float*, int, int64_t, bool, int);
 
 mf_status diag64(mf_op* op, double** out) {
   if (!op->diag_ready) {
@@ -542,9 +547,10 @@ mf_status mf_apply(mf_op* op, const void* src, void* dst, int nrhs, int64_t ld, 
   MF_GUARD_BEGIN
   if (!op || !src || !dst) return fail(MF_EINVAL, "NULL argument");
   if (nrhs < 1 || ld < op->n) return fail(MF_EINVAL, "nrhs must be >= 1 and ld >= n");
-  if (dtype == MF_F64) return apply_impl<double>(op, (const double*)src, (double*)dst, nrhs, ld, false);
-  if (dtype == MF_F32) return apply_impl<float>(op, (const float*)src, (float*)dst, nrhs, ld, false);
-  return fail(MF_EUNSUPPORTED, "apply precision must be MF_F64 or MF_F32");
+  if (dtype == MF_F64) return apply_impl<double>(op, (const double*)src, (double*)dst, nrhs, ld, false, PREC_F64);
+  if (dtype == MF_DF64) return apply_impl<double>(op, (const double*)src, (double*)dst, nrhs, ld, false, PREC_DF64);
+  if (dtype == MF_F32) return apply_impl<float>(op, (const float*)src, (float*)dst, nrhs, ld, false, PREC_F32);
+  return fail(MF_EUNSUPPORTED, "apply precision must be MF_F64, MF_DF64 or MF_F32");
   MF_GUARD_END
 }
 
@@ -552,9 +558,10 @@ mf_status mf_apply_transpose(mf_op* op, const void* src, void* dst, int nrhs, in
   MF_GUARD_BEGIN
   if (!op || !src || !dst) return fail(MF_EINVAL, "NULL argument");
   if (nrhs < 1 || ld < op->n) return fail(MF_EINVAL, "nrhs must be >= 1 and ld >= n");
-  if (dtype == MF_F64) return apply_impl<double>(op, (const double*)src, (double*)dst, nrhs, ld, true);
-  if (dtype == MF_F32) return apply_impl<float>(op, (const float*)src, (float*)dst, nrhs, ld, true);
-  return fail(MF_EUNSUPPORTED, "apply precision must be MF_F64 or MF_F32");
+  if (dtype == MF_F64) return apply_impl<double>(op, (const double*)src, (double*)dst, nrhs, ld, true, PREC_F64);
+  if (dtype == MF_DF64) return apply_impl<double>(op, (const double*)src, (double*)dst, nrhs, ld, true, PREC_DF64);
+  if (dtype == MF_F32) return apply_impl<float>(op, (const float*)src, (float*)dst, nrhs, ld, true, PREC_F32);
+  return fail(MF_EUNSUPPORTED, "apply precision must be MF_F64, MF_DF64 or MF_F32");
   MF_GUARD_END
 }
 

@@ -13,6 +13,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "df64.cuh"
+
 namespace mf {
 
 // 1D tables, filled once per translation unit by upload_tables().
@@ -28,6 +30,8 @@ static __constant__ float cS32[9], cD32[9], cW32[3], cP32[6], cSp32[9], cW332[27
 static __constant__ double cSS64[9], cSSp64[9], cSpSp64[9], cPP64[6], cPpPp64[6];
 static __constant__ double cPW64[216], cG64[3];
 static __constant__ float cPW32[216];
+// double-float copies (hi, lo) for the df64 kernels
+static __constant__ float cSh[9], cSl[9], cDh[9], cDl[9], cW3h[27], cW3l[27], cPWh[216], cPWl[216];
 
 template <typename T> struct Tb;
 template <> struct Tb<double> {
@@ -49,6 +53,13 @@ template <> struct Tb<float> {
   static __device__ __forceinline__ float PW(int q, int n) { return cPW32[8 * q + n]; }
 };
 
+template <> struct Tb<df64> {
+  static __device__ __forceinline__ df64 S(int q, int a) { return df64(cSh[3 * q + a], cSl[3 * q + a]); }
+  static __device__ __forceinline__ df64 D(int q, int p) { return df64(cDh[3 * q + p], cDl[3 * q + p]); }
+  static __device__ __forceinline__ df64 W3(int q) { return df64(cW3h[q], cW3l[q]); }
+  static __device__ __forceinline__ df64 PW(int q, int n) { return df64(cPWh[8 * q + n], cPWl[8 * q + n]); }
+};
+
 Tables make_tables();           // host: closed forms (cellops_host.cpp)
 // upload_tables_here(): per translation unit, defined by MF_DEFINE_TABLE_UPLOAD
 
@@ -57,7 +68,7 @@ Tables make_tables();           // host: closed forms (cellops_host.cpp)
     static bool done = false;                                                             \
     if (done) return cudaSuccess;                                                         \
     Tables t = make_tables();                                                             \
-    float f[216];                                                                         \
+    float f[216], fl[216];                                                                \
     cudaError_t e = cudaSuccess;                                                          \
     auto up64 = [&](const void* sym, const double* src, int n) {                          \
       if (e == cudaSuccess) e = cudaMemcpyToSymbol(sym, src, n * sizeof(double));         \
@@ -73,6 +84,16 @@ Tables make_tables();           // host: closed forms (cellops_host.cpp)
     up32(cPW32, t.PW, 216);                                                               \
     up32(cS32, t.S, 9); up32(cD32, t.D, 9); up32(cW32, t.W, 3); up32(cP32, t.P, 6);       \
     up32(cSp32, t.Sp, 9); up32(cW332, t.W3, 27);                                          \
+    auto updf = [&](const void* sh, const void* sl, const double* src, int n) {           \
+      for (int i = 0; i < n; ++i) {                                                       \
+        f[i] = float(src[i]);                                                             \
+        fl[i] = float(src[i] - double(f[i]));                                             \
+      }                                                                                   \
+      if (e == cudaSuccess) e = cudaMemcpyToSymbol(sh, f, n * sizeof(float));             \
+      if (e == cudaSuccess) e = cudaMemcpyToSymbol(sl, fl, n * sizeof(float));            \
+    };                                                                                    \
+    updf(cSh, cSl, t.S, 9); updf(cDh, cDl, t.D, 9); updf(cW3h, cW3l, t.W3, 27);           \
+    updf(cPWh, cPWl, t.PW, 216);                                                          \
     if (e == cudaSuccess) done = true;                                                    \
     return e;                                                                             \
   }
@@ -177,6 +198,42 @@ __device__ __forceinline__ bool brick_cell(const UniformGeom& g, int& i, int& j,
 }
 inline int brick_blocks(int nx, int ny, int nz) { return ((nx + 7) / 8) * ((ny + 3) / 4) * ((nz + 3) / 4); }
 
+// Lattice nodes of one 8 x 4 x 4-cell brick: 17 x 9 x 9.
+constexpr int kBrickX = 17, kBrickY = 9, kBrickZ = 9, kBrickNodes = kBrickX * kBrickY * kBrickZ;
+
+// acc[brick node] += R[local node] for the calling thread's cell (shared-memory atomics).
+template <typename T>
+__device__ __forceinline__ void brick_accumulate(typename Store<T>::type* acc, const T* R) {
+  const int t = threadIdx.x;
+  const int base = 2 * (t & 7) + kBrickX * (2 * ((t >> 3) & 3) + kBrickY * (2 * (t >> 5)));
+#pragma unroll
+  for (int l = 0; l < 27; ++l) {
+    const int a = l % 3, b = (l / 3) % 3, c = l / 9;
+    atomicAdd(acc + base + a + kBrickX * (b + kBrickY * c), to_store<T>(R[l]));
+  }
+}
+
+// Write the brick's sums: nodes strictly inside the brick, or on a brick face that is the
+// domain boundary, are touched by this block only (plain store into the zeroed output);
+// nodes on a face shared with a neighbouring brick are added atomically.
+template <typename St>
+__device__ __forceinline__ void brick_flush(const UniformGeom& g, const St* acc, St* __restrict__ dst) {
+  const int nbx = (g.nx + 7) >> 3, nby = (g.ny + 3) >> 2;
+  const int b = blockIdx.x;
+  const int gx0 = 16 * (b % nbx), gy0 = 8 * ((b / nbx) % nby), gz0 = 8 * (b / (nbx * nby));
+  const int Rx = 2 * g.nx, Ry = 2 * g.ny, Rz = 2 * g.nz;
+  for (int i = threadIdx.x; i < kBrickNodes; i += blockDim.x) {
+    const int lx = i % kBrickX, ly = (i / kBrickX) % kBrickY, lz = i / (kBrickX * kBrickY);
+    const int gx = gx0 + lx, gy = gy0 + ly, gz = gz0 + lz;
+    if (gx > Rx || gy > Ry || gz > Rz) continue;
+    const bool shared = (lx == 0 && gx > 0) || (lx == kBrickX - 1 && gx < Rx) || (ly == 0 && gy > 0) ||
+                        (ly == kBrickY - 1 && gy < Ry) || (lz == 0 && gz > 0) || (lz == kBrickZ - 1 && gz < Rz);
+    St* p = dst + gx + g.sx * gy + g.sy * gz;
+    if (shared) atomicAdd(p, acc[i]);
+    else *p = acc[i];
+  }
+}
+
 // 27-bit mask of the cell's local nodes on Dirichlet faces.
 __device__ __forceinline__ uint32_t dirichlet_mask(const UniformGeom& g, int i, int j, int k) {
   if (!g.dir_faces) return 0u;
@@ -192,23 +249,29 @@ __device__ __forceinline__ uint32_t dirichlet_mask(const UniformGeom& g, int i, 
   return m;
 }
 
+// Vectors are stored in Store<T>::type (df64 values live in fp64 memory).
 template <typename T>
-__device__ __forceinline__ void gather_uniform(const T* __restrict__ src, int64_t base, int64_t sx, int64_t sy,
-                                               uint32_t dmask, T* U) {
+__device__ __forceinline__ void gather_uniform(const typename Store<T>::type* __restrict__ src, int64_t base,
+                                               int64_t sx, int64_t sy, uint32_t dmask, T* U) {
 #pragma unroll
   for (int l = 0; l < 27; ++l) {
     const int a = l % 3, b = (l / 3) % 3, c = l / 9;
-    T v = __ldg(src + base + a + sx * b + sy * c);
+    T v = from_store<T>(__ldg(src + base + a + sx * b + sy * c));
     U[l] = ((dmask >> l) & 1u) ? T(0) : v;
   }
 }
 template <typename T>
-__device__ __forceinline__ void scatter_uniform(T* __restrict__ dst, int64_t base, int64_t sx, int64_t sy,
-                                                uint32_t dmask, const T* R) {
+__device__ __forceinline__ void scatter_uniform(typename Store<T>::type* __restrict__ dst, int64_t base, int64_t sx,
+                                                int64_t sy, uint32_t dmask, const T* R) {
+  // Recompute the 27 addresses here instead of keeping the gather's 27 64-bit addresses
+  // alive across the whole cell computation (54 registers): the empty asm hides the
+  // equality of base/strides from the compiler.
+  asm volatile("" : "+l"(base), "+l"(sx), "+l"(sy));
+  typename Store<T>::type* __restrict__ d = dst + base;
 #pragma unroll
   for (int l = 0; l < 27; ++l) {
     const int a = l % 3, b = (l / 3) % 3, c = l / 9;
-    if (!((dmask >> l) & 1u)) atomicAdd(dst + base + a + sx * b + sy * c, R[l]);
+    if (!((dmask >> l) & 1u)) atomicAdd(d + a + sx * b + sy * c, to_store<T>(R[l]));
   }
 }
 
@@ -228,46 +291,50 @@ struct OctGeom {
   double h0;                          // edge of a level-0 cell
 };
 
-template <typename T> __device__ __forceinline__ const T* con_w(const OctGeom& g);
+template <typename T> __device__ __forceinline__ const typename Store<T>::type* con_w(const OctGeom& g);
 template <> __device__ __forceinline__ const double* con_w<double>(const OctGeom& g) { return g.w64; }
 template <> __device__ __forceinline__ const float* con_w<float>(const OctGeom& g) { return g.w32; }
+template <> __device__ __forceinline__ const double* con_w<df64>(const OctGeom& g) { return g.w64; }
 
 template <typename T, bool MASK = true>
-__device__ __forceinline__ void gather_oct(const OctGeom& g, const T* __restrict__ src, int64_t cell, T* U) {
+__device__ __forceinline__ void gather_oct(const OctGeom& g, const typename Store<T>::type* __restrict__ src,
+                                           int64_t cell, T* U) {
 #pragma unroll
   for (int l = 0; l < 27; ++l) {
     int32_t id = __ldg(g.cmap + l * g.ncp + cell);
     T v;
     if (id >= 0) {
-      v = __ldg(src + id);
+      v = from_store<T>(__ldg(src + id));
       if (MASK && g.dflag && __ldg(g.dflag + id)) v = T(0);
     } else {
       const int r = -1 - id;
-      const T* w = con_w<T>(g);
+      const auto* w = con_w<T>(g);
       v = T(0);
       for (int e = __ldg(g.rowptr + r); e < __ldg(g.rowptr + r + 1); ++e) {
         int32_t m = __ldg(g.cols + e);
-        T um = __ldg(src + m);
+        T um = from_store<T>(__ldg(src + m));
         if (MASK && g.dflag && __ldg(g.dflag + m)) um = T(0);
-        v += __ldg(w + e) * um;
+        v += from_store<T>(__ldg(w + e)) * um;
       }
     }
     U[l] = v;
   }
 }
 template <typename T, bool MASK = true>
-__device__ __forceinline__ void scatter_oct(const OctGeom& g, T* __restrict__ dst, int64_t cell, const T* R) {
+__device__ __forceinline__ void scatter_oct(const OctGeom& g, typename Store<T>::type* __restrict__ dst, int64_t cell,
+                                            const T* R) {
 #pragma unroll
   for (int l = 0; l < 27; ++l) {
     int32_t id = __ldg(g.cmap + l * g.ncp + cell);
     if (id >= 0) {
-      if (!(MASK && g.dflag && __ldg(g.dflag + id))) atomicAdd(dst + id, R[l]);
+      if (!(MASK && g.dflag && __ldg(g.dflag + id))) atomicAdd(dst + id, to_store<T>(R[l]));
     } else {
       const int r = -1 - id;
-      const T* w = con_w<T>(g);
+      const auto* w = con_w<T>(g);
+      const typename Store<T>::type rl = to_store<T>(R[l]);
       for (int e = __ldg(g.rowptr + r); e < __ldg(g.rowptr + r + 1); ++e) {
         int32_t m = __ldg(g.cols + e);
-        if (!(MASK && g.dflag && __ldg(g.dflag + m))) atomicAdd(dst + m, __ldg(w + e) * R[l]);
+        if (!(MASK && g.dflag && __ldg(g.dflag + m))) atomicAdd(dst + m, __ldg(w + e) * rl);
       }
     }
   }

@@ -7,6 +7,8 @@
 namespace mf {
 
 enum ScalarKind { K_HELM = 0, K_HEAT = 1, K_REINIT = 2, K_MASS = 3 };
+// arithmetic of an apply: fp64, fp32, or double-float (fp64 storage, pairs of fp32 in the kernel)
+enum ApplyPrec { PREC_F64 = 0, PREC_F32 = 1, PREC_DF64 = 2 };
 
 // Arguments of the scalar cell kernels.  Vector fields are in the apply precision T.
 template <typename T> struct ScalarArgs {
@@ -40,8 +42,8 @@ template <typename T> struct OseenArgs {
 
 // scalar apply: kind, coefficient mode (0 in-kernel, 1 tabulated), convection, transpose
 mf_status launch_scalar_apply(mf_ctx* ctx, const mf_dofmap* m, int kind, int mode, bool beta, bool transpose,
-                              bool f32, const void* args);
-mf_status launch_oseen_apply(mf_ctx* ctx, const mf_dofmap* mu, bool f32, const void* args);
+                              int prec, const void* args);
+mf_status launch_oseen_apply(mf_ctx* ctx, const mf_dofmap* mu, int prec, const void* args);
 // Gauss-point tables from nodal fp64 fields (always evaluated in fp64, stored in both precisions)
 mf_status launch_scalar_qtables(mf_ctx* ctx, const mf_dofmap* m, int kind, const double* field, const double* kq_user,
                                 const double* beta, double k0, double k_slope, double a_l, double a_g, int heaviside,
@@ -87,5 +89,6 @@ struct mf_op {
   bool tables_ready = false;
   bool diag_ready = false;
   int mode64 = 1, mode32 = 0;     // coefficient mode per precision (autotuned)
+  int f64_prec = 0;               // arithmetic of fp64 applies inside solvers (PREC_F64 or PREC_DF64)
   std::string variant;
 };

@@ -25,8 +25,9 @@ template <typename T> __device__ __forceinline__ T heaviside(T phi, int kind, T 
 // U: nodal values of the cell (overwritten); R: the cell's contribution, at the nodes.
 // C: scalar coefficient at the Gauss points (in-kernel phi for MODE 0 reinit).
 template <typename T, int KIND, int MODE, bool BETA, bool TR>
-__device__ __forceinline__ void scalar_local(const ScalarArgs<T>& A, int64_t cell, T h, T mh2, const T* C, T* U,
-                                             T* R) {
+__device__ __forceinline__ void scalar_local(const ScalarArgs<typename Store<T>::type>& A, int64_t cell, T h, T mh2,
+                                             const T* C, T* U, T* R) {
+  const T eps = T(A.eps);
   to_qpoints<T>(U);
 #pragma unroll
   for (int q = 0; q < 27; ++q) R[q] = T(0);
@@ -40,36 +41,36 @@ __device__ __forceinline__ void scalar_local(const ScalarArgs<T>& A, int64_t cel
         const T w = Tb<T>::W3(q);
         const T u = U[q];
         T fv = w * (mh2 * u);
-        if (KIND == K_MASS) {
+        if constexpr (KIND == K_MASS) {
           R[q] += fv;
           continue;
         }
         T gx, gy, gz;
         grad_at<T>(U, qa, qb, qc, gx, gy, gz);
         T Fx, Fy, Fz;
-        if (KIND == K_REINIT) {
+        if constexpr (KIND == K_REINIT) {
           T nx, ny, nz;
-          if (MODE == 0) {
+          if constexpr (MODE == 0) {
             grad_at<T>(C, qa, qb, qc, nx, ny, nz);
             T nn = sqrt(nx * nx + ny * ny + nz * nz);
             T inv = nn < T(1e-12) ? T(0) : T(1) / nn;
             nx *= inv; ny *= inv; nz *= inv;
           } else {
-            nx = __ldg(A.qvec + (0 * 27 + q) * A.ncp + cell);
-            ny = __ldg(A.qvec + (1 * 27 + q) * A.ncp + cell);
-            nz = __ldg(A.qvec + (2 * 27 + q) * A.ncp + cell);
+            nx = from_store<T>(__ldg(A.qvec + (0 * 27 + q) * A.ncp + cell));
+            ny = from_store<T>(__ldg(A.qvec + (1 * 27 + q) * A.ncp + cell));
+            nz = from_store<T>(__ldg(A.qvec + (2 * 27 + q) * A.ncp + cell));
           }
-          const T s = w * (A.eps * (nx * gx + ny * gy + nz * gz));
+          const T s = w * (eps * (nx * gx + ny * gy + nz * gz));
           Fx = s * nx; Fy = s * ny; Fz = s * nz;
         } else {
           const T c = w * C[q];
           Fx = c * gx; Fy = c * gy; Fz = c * gz;
         }
-        if (BETA) {
-          const T bx = __ldg(A.qvec + (0 * 27 + q) * A.ncp + cell);
-          const T by = __ldg(A.qvec + (1 * 27 + q) * A.ncp + cell);
-          const T bz = __ldg(A.qvec + (2 * 27 + q) * A.ncp + cell);
-          if (!TR) {
+        if constexpr (BETA) {
+          const T bx = from_store<T>(__ldg(A.qvec + (0 * 27 + q) * A.ncp + cell));
+          const T by = from_store<T>(__ldg(A.qvec + (1 * 27 + q) * A.ncp + cell));
+          const T bz = from_store<T>(__ldg(A.qvec + (2 * 27 + q) * A.ncp + cell));
+          if constexpr (!TR) {
             fv += w * (h * (bx * gx + by * gy + bz * gz));
           } else {
             const T s = w * (h * u);

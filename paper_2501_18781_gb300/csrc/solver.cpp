@@ -12,7 +12,8 @@
 
 namespace mf {
 
-template <typename T> mf_status apply_impl(mf_op* op, const T* src, T* dst, int nrhs, int64_t ld, bool transpose);
+template <typename T>
+mf_status apply_impl(mf_op* op, const T* src, T* dst, int nrhs, int64_t ld, bool transpose, int prec = -1);
 mf_status diag64(mf_op* op, double** out);
 mf_status check_fields(const mf_op* op);
 mf_status ensure_tables(mf_op* op);
@@ -481,6 +482,13 @@ mf_status solve_impl(mf_op* op, const mf_solver_params* sp, const double* b, dou
   mf_ctx* c = op->ctx;
   const int64_t n = op->n;
   MF_TRY(check_fields(op));
+  // fp64 applies of this solve run on the fp64 pipes or in double-float
+  struct Restore {
+    mf_op* op;
+    int prev;
+    ~Restore() { op->f64_prec = prev; }
+  } restore{op, op->f64_prec};
+  op->f64_prec = sp->fp64_arith == 1 ? PREC_DF64 : PREC_F64;
   mf_solve_info inf{};
   mf_status st = MF_OK;
   const double tol = sp->tol > 0 ? sp->tol : 1e-10;
@@ -641,7 +649,7 @@ mf_status mf_heat_step_gradient(mf_op* op, const mf_laser* lz, const mf_solver_p
     ScalarArgs<double> a = scalar_args<double>(op, theta_prev, bvec, 1, n);
     a.mass = op->p.rhocp / op->p.dt;
     MF_CUDA_TRY(cudaMemsetAsync(bvec, 0, sizeof(double) * n, c->stream));
-    MF_TRY(launch_scalar_apply(c, m, K_MASS, 1, false, false, false, &a));
+    MF_TRY(launch_scalar_apply(c, m, K_MASS, 1, false, false, PREC_F64, &a));
     MF_TRY(axpby<double, double>(c, n, 1.0, f, 1.0, bvec));
     MF_TRY(zero_list<double>(c, bvec, m->d_dir_list.as<int32_t>(), int64_t(m->dirichlet_list.size())));
     mf_solve_info inf;
@@ -657,7 +665,7 @@ mf_status mf_heat_step_gradient(mf_op* op, const mf_laser* lz, const mf_solver_p
     mb.box_zmin = m->mesh->hi[2] - box_depth;
     for (int d = 0; d < 3; ++d) mb.lo[d] = m->mesh->lo[d];
     MF_CUDA_TRY(cudaMemsetAsync(f, 0, sizeof(double) * n, c->stream));
-    MF_TRY(launch_scalar_apply(c, m, K_MASS, 1, false, false, false, &mb));
+    MF_TRY(launch_scalar_apply(c, m, K_MASS, 1, false, false, PREC_F64, &mb));
     double* ds = c->scalars.as<double>() + kScalarsHeat;
     MF_TRY(dot<double, double>(c, e, f, n, ds));
     MF_TRY(zero_list<double>(c, f, m->d_dir_list.as<int32_t>(), int64_t(m->dirichlet_list.size())));

@@ -27,20 +27,21 @@ def check_apply(P, seed=1, nrhs=1, rtol64=1e-12, rtol32=2e-5, transpose=False):
     n = P["n"]
     A = P["A"].T.tocsr() if transpose else P["A"]
     absA = abs(A)
-    for r in range(nrhs):
-        pass
     U = np.stack([syn.uniform_pm1(seed + r, n) for r in range(nrhs)])
     src = torch.tensor(U.ravel(), device="cuda")
     out64 = P["op"].apply(src, nrhs=nrhs, transpose=transpose).cpu().numpy().reshape(nrhs, n)
+    outdf = P["op"].apply(src, nrhs=nrhs, transpose=transpose, arith="df64").cpu().numpy().reshape(nrhs, n)
     out32 = P["op"].apply(src.float(), nrhs=nrhs, transpose=transpose).cpu().numpy().astype(np.float64).reshape(nrhs, n)
     for r in range(nrhs):
         ref = A @ U[r]
         bound = absA @ np.abs(U[r])
         ok, worst = componentwise_ok(out64[r], ref, bound, rtol64)
         assert ok, f"fp64 componentwise error {worst:.3e} (rhs {r})"
+        okd, worstd = componentwise_ok(outdf[r], ref, bound, rtol64)
+        assert okd, f"double-float componentwise error {worstd:.3e} (rhs {r})"
         ok32, worst32 = componentwise_ok(out32[r], ref, bound, rtol32)
         assert ok32, f"fp32 componentwise error {worst32:.3e} (rhs {r})"
-    return worst, worst32
+    return worst, worstd, worst32
 
 
 @pytest.mark.parametrize("n", [1, 3, 10])

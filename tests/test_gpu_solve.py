@@ -158,3 +158,12 @@ def test_heat_adjoint_gradient_matches_central_differences(ctx):
         P["op"].set_field("k_qpoint", torch.tensor(kq, device="cuda"))
         fd = (vals[0] - vals[1]) / (2 * hh)
         assert abs(gk[flat] - fd) <= 1e-6 * abs(fd), (flat, gk[flat], fd)
+
+
+def test_cg_with_double_float_applies_reaches_fp64_tolerance(ctx):
+    P = helmholtz(10, ctx)
+    solve_and_check(P, syn.uniform_pm1(6, P["n"]), solver="cg", precond="chebyshev", fp64_arith="df64")
+    Pg = heat(6, ctx, with_beta=True, kq=True)
+    b = syn.uniform_pm1(7, Pg["n"])
+    b[Pg["dm"].dirichlet] = 0.0
+    solve_and_check(Pg, b, solver="gmres", precond="jacobi", fp64_arith="df64")
