@@ -146,6 +146,115 @@ def time_apply(op, src, dst, steps, warmup, flush):
     return times
 
 
+def _event_ms(fn, reps=5, flush=None):
+    import torch
+    fn()
+    torch.cuda.synchronize()
+    ts = []
+    for _ in range(reps):
+        if flush is not None:
+            flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        fn()
+        e1.record()
+        e1.synchronize()
+        ts.append(e0.elapsed_time(e1))
+    return statistics.median(ts)
+
+
+def _apply_rates(op, n, nrhs, flush, reps=5):
+    """GDoF/s (DoF x RHS per second) of the fp64, double-float and fp32 applies."""
+    import torch
+    import synthetic as syn
+    u = torch.tensor(syn.uniform_pm1(1, n * nrhs), device="cuda")
+    u32 = u.float()
+    v, v32 = torch.empty_like(u), torch.empty_like(u32)
+    out = {}
+    for name, fn in (("f64", lambda: op.apply(u, v, nrhs=nrhs)),
+                     ("df64", lambda: op.apply(u, v, nrhs=nrhs, arith="df64")),
+                     ("f32", lambda: op.apply(u32, v32, nrhs=nrhs))):
+        ms = _event_ms(fn, reps, flush)
+        out[name] = {"ms": ms, "gdofs": n * nrhs / ms / 1e6, "variant": op.variant}
+    return out
+
+
+def workload_suite(ctx, flush):
+    """One bounded measurement per benchmark workload (the parity tests cover their numerics)."""
+    import numpy as np
+    import torch
+    import synthetic as syn
+    from paper_2501_18781_gb300 import DofMap, Mesh, Operator
+    res = {}
+    # Helmholtz 16^3 (L2-resident: launch-latency bound), Jacobi-CG in a CUDA graph
+    wl = syn.HELMHOLTZ_SPHERE
+    p = wl.params
+    m = DofMap(Mesh.uniform(ctx, wl.n, wl.lo, wl.hi), 2, 0)
+    x = m.coords()
+    phi = syn.initial_level_set(syn.sphere_distance(*x.T), wl.eps)
+    op = Operator(ctx, "helmholtz", [m], mass_coef=p["mass"], a_liquid=p["a_liquid"], a_gas=p["a_gas"])
+    op.set_field("phi", torch.tensor(phi, device="cuda"))
+    op.autotune()
+    b = torch.tensor(syn.uniform_pm1(1, m.n_dofs), device="cuda")
+    r = {"n_dofs": m.n_dofs, "apply": _apply_rates(op, m.n_dofs, 1, None, reps=20)}
+    for g in (False, True):
+        op.solve(b, solver="cg", precond="jacobi", use_graph=g)
+        t0 = time.perf_counter()
+        _, info = op.solve(b, solver="cg", precond="jacobi", use_graph=g)
+        r["cg_jacobi_graph" if g else "cg_jacobi"] = {"seconds": time.perf_counter() - t0, "iterations": info["iterations"],
+                                                      "rel_residual": info["rel_residual"]}
+    res[wl.name] = r
+    # heat-step adjoint on 64^3: forward + adjoint GMRES and both gradients
+    wl = syn.HEAT_ADJOINT
+    p = wl.params
+    m = DofMap(Mesh.uniform(ctx, wl.n, wl.lo, wl.hi), 2, 1 << 4)
+    x = m.coords()
+    beta = np.array(syn.convection_field(*x.T, wl.seed, wl.lo, wl.hi))
+    kq = syn.kq_field(m.n_cells * 27, wl.seed, p["k0"])
+    op = Operator(ctx, "heat", [m], rhocp=p["rhocp"], dt=p["dt"], k0=p["k0"], t_boil=p["t_boil"])
+    op.set_field("beta", torch.tensor(beta.ravel(), device="cuda"))
+    op.set_field("k_qpoint", torch.tensor(kq, device="cuda"))
+    ztop = wl.hi[2]
+    lz = p["laser"]
+    th_prev = syn.heat_initial_temperature(*x.T, lz["radius"], ztop) - p["t_ref"]
+    target = syn.heat_target_temperature(*x.T, ztop, wl.seed + 4) - p["t_ref"]
+    tp, tt = torch.tensor(th_prev, device="cuda"), torch.tensor(target, device="cuda")
+    lzt = (lz["power"], lz["radius"], lz["x0"], lz["y0"], lz["absorptivity"])
+    kw = dict(solver="gmres", precond="jacobi", tol=1e-10, restart=50)
+    op.heat_step_gradient(lzt, tp, tt, p["box_half"], p["box_depth"], **kw)
+    t0 = time.perf_counter()
+    J, g, gk, _, _ = op.heat_step_gradient(lzt, tp, tt, p["box_half"], p["box_depth"], **kw)
+    torch.cuda.synchronize()
+    res[wl.name] = {"n_dofs": m.n_dofs, "gradient_seconds": time.perf_counter() - t0, "J": J,
+                    "dJ_dlaser": g, "apply": _apply_rates(op, m.n_dofs, 1, flush)}
+    # adaptive octree reinitialisation, 8 right-hand sides batched per launch, mixed precision
+    wl = syn.REINIT_OCTREE
+    d = lambda X, Y, Z: syn.deformed_sphere_distance(X, Y, Z, wl.seed)
+    leaves = syn.refine_band_leaves(wl.n, wl.levels, d, wl.eps)
+    mesh = Mesh.octree(ctx, wl.n, wl.levels, leaves)
+    m = DofMap(mesh, 2, 0)
+    x = m.coords()
+    phi = syn.initial_level_set(syn.deformed_sphere_distance(*x.T, wl.seed), wl.eps)
+    hmin = 1.0 / (wl.n << wl.levels)
+    op = Operator(ctx, "reinit", [m], eps=wl.eps, dtau=0.5 * hmin)
+    op.set_field("phi", torch.tensor(phi, device="cuda"))
+    op.autotune()
+    B = torch.tensor(np.concatenate([syn.uniform_pm1(s, m.n_dofs) for s in range(1, wl.nrhs + 1)]), device="cuda")
+    r = {"n_dofs": m.n_dofs, "cells": m.n_cells, "hanging_nodes": m.n_constraints, "nrhs": wl.nrhs,
+         "apply_batched": _apply_rates(op, m.n_dofs, wl.nrhs, flush, reps=3),
+         "apply_single": _apply_rates(op, m.n_dofs, 1, flush, reps=3)}
+    kw = dict(solver="defect_correction", precond="chebyshev", tol=1e-10, use_graph=True)
+    op.solve(B, nrhs=wl.nrhs, **kw)
+    t0 = time.perf_counter()
+    _, info = op.solve(B, nrhs=wl.nrhs, **kw)
+    torch.cuda.synchronize()
+    r["mixed_solve_8rhs"] = {"seconds": time.perf_counter() - t0, "inner_iterations": info["iterations"],
+                             "outer": info["outer_iterations"], "rel_residual": info["rel_residual"],
+                             "status": info["status"]}
+    res[wl.name] = r
+    return res
+
+
 def heat_solve_comparison(ctx, n=128):
     """Implicit heat step on n^3 Q2 cells: fp64 CG with Chebyshev(4)-Jacobi vs fp32 inner CG
     (same preconditioner in fp32) inside fp64 defect correction, both to 1e-10."""
@@ -252,6 +361,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-solve", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--suite", action="store_true", help="also measure the other benchmark workloads")
     ap.add_argument("--n", type=int, default=64)
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
@@ -349,8 +459,12 @@ def main():
     t32 = time_apply(op, src32, dst32, max(5, args.steps // 2), 3, flush)
     out["fp32_apply"] = {"value": n / (sum(t32) / len(t32)) / 1e9, "unit": "GDoF/s",
                          "ms_per_step": sum(t32) / len(t32) * 1e3}
+    out["df64_apply"] = {"value": n / (_event_ms(lambda: op.apply(src, dst, arith="df64"), 5, flush) / 1e3) / 1e9,
+                         "unit": "GDoF/s", "note": "fp64 vectors, double-float cell arithmetic on the fp32 pipes"}
     if not args.no_solve and rank == 0:
         out["solve"] = heat_solve_comparison(ctx)
+    if args.suite and rank == 0:
+        out["workloads"] = workload_suite(ctx, flush)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         v, nd, reps, dt = cpu_oracle_apply(16)
         out["cpu_baseline"] = {"value": v, "unit": "GDoF/s", "cores": 1, "kind": "oracle",

@@ -1,0 +1,269 @@
+// Matrix-free operator apply kernels: gather -> values/gradients at Gauss points -> pointwise
+// physics -> integrate -> scatter-add (one thread per Q2 cell, registers only).  Included by one
+// translation unit per arithmetic (apply_f64.cu, apply_f32.cu, apply_df64.cu) so that the three
+// instantiations compile in parallel.
+#pragma once
+#include <type_traits>
+
+#include "scalar_local.cuh"
+
+namespace mf {
+
+MF_DEFINE_TABLE_UPLOAD
+
+UniformGeom uniform_geom(const mf_dofmap* m);
+OctGeom oct_geom(const mf_dofmap* m);
+
+namespace {
+
+struct CellLoc {
+  int64_t cell;
+  int64_t base;
+  uint32_t dmask;
+  double h;
+};
+
+template <bool OCT>
+__device__ __forceinline__ bool locate(const UniformGeom& ug, const OctGeom& og, int64_t t, CellLoc& L) {
+  if (OCT) {
+    if (t >= og.ncells) return false;
+    L.cell = __ldg(og.order + t);
+    L.h = og.h0 / double(1 << __ldg(og.level + L.cell));
+    L.base = 0;
+    L.dmask = 0;
+    return true;
+  } else {
+    int i, j, k;
+    if (!brick_cell(ug, i, j, k)) return false;
+    L.cell = i + int64_t(ug.nx) * (j + int64_t(ug.ny) * k);
+    L.base = 2 * int64_t(i) + ug.sx * (2 * int64_t(j)) + ug.sy * (2 * int64_t(k));
+    L.dmask = dirichlet_mask(ug, i, j, k);
+    L.h = ug.h;
+    return true;
+  }
+}
+
+template <typename T, bool OCT, bool MASK = true>
+__device__ __forceinline__ void gather(const UniformGeom& ug, const OctGeom& og, const CellLoc& L,
+                                       const typename Store<T>::type* src, T* U) {
+  if (OCT) gather_oct<T, MASK>(og, src, L.cell, U);
+  else gather_uniform<T>(src, L.base, ug.sx, ug.sy, L.dmask, U);
+}
+template <typename T, bool OCT, bool MASK = true>
+__device__ __forceinline__ void scatter(const UniformGeom& ug, const OctGeom& og, const CellLoc& L,
+                                        typename Store<T>::type* dst, const T* R) {
+  if (OCT) scatter_oct<T, MASK>(og, dst, L.cell, R);
+  else scatter_uniform<T>(dst, L.base, ug.sx, ug.sy, L.dmask, R);
+}
+
+// Scalar operators.  KIND: K_HELM, K_HEAT, K_REINIT, K_MASS; MODE 0 = coefficients from the
+// nodal field in the kernel, 1 = tabulated per Gauss point.
+template <typename T, int KIND, int MODE, bool BETA, bool TR, bool OCT>
+__global__ void __launch_bounds__(128) k_scalar(ScalarArgs<typename Store<T>::type> A, UniformGeom ug, OctGeom og) {
+  using St = typename Store<T>::type;
+  CellLoc L;
+  const int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  bool active = locate<OCT>(ug, og, t, L);
+  if constexpr (OCT) {
+    if (!active) return;
+  }
+  if (KIND == K_MASS) L.dmask = 0u;  // the plain mass matrix has no Dirichlet rows
+  const T h = T(OCT ? L.h : ug.h);
+  // every term carries at least one power of h: R = h * (...), with
+  // w h^3 m u = h (w (m h^2) u), w h k g = h (w k g), w h^2 beta.g = h (w h beta.g)
+  const T mh2 = T(A.mass) * h * h;
+  if (KIND == K_MASS && A.use_box && active) {
+    // centre of a uniform cell from its lattice base
+    const int64_t kk = L.base / ug.sy, jj = (L.base % ug.sy) / ug.sx, ii = L.base % ug.sx;
+    const double cx = A.lo[0] + (double(ii) * 0.5 + 0.5) * L.h, cy = A.lo[1] + (double(jj) * 0.5 + 0.5) * L.h,
+                 cz = A.lo[2] + (double(kk) * 0.5 + 0.5) * L.h;
+    if (!(fabs(cx) <= A.box_half && fabs(cy) <= A.box_half && cz >= A.box_zmin)) {
+      if constexpr (OCT) return;
+      active = false;
+    }
+  }
+  // scalar coefficient (or phi for in-kernel reinit) at the 27 Gauss points
+  T C[27];
+  if (active)
+  if constexpr (KIND == K_HELM || KIND == K_HEAT || KIND == K_REINIT) {
+    if constexpr (MODE == 0) {
+      gather<T, OCT, false>(ug, og, CellLoc{L.cell, L.base, 0u, L.h}, A.field, C);
+      to_qpoints<T>(C);
+      if constexpr (KIND == K_HELM) {
+#pragma unroll
+        for (int q = 0; q < 27; ++q) C[q] = A.a_g + (A.a_l - A.a_g) * heaviside<T>(C[q], A.heaviside, A.eps);
+      } else if constexpr (KIND == K_HEAT) {
+#pragma unroll
+        for (int q = 0; q < 27; ++q) C[q] = A.k0 + A.k_slope * C[q];
+      }
+    } else if constexpr (KIND != K_REINIT) {
+#pragma unroll
+      for (int q = 0; q < 27; ++q) C[q] = from_store<T>(__ldg(A.qcoef + q * A.ncp + L.cell));
+    }
+  }
+  if (!active) return;
+  for (int r = 0; r < A.nrhs; ++r) {
+    T U[27], R[27];
+    gather<T, OCT, KIND != K_MASS>(ug, og, L, A.src + r * A.ld, U);
+    scalar_local<T, KIND, MODE, BETA, TR>(A, L.cell, h, mh2, C, U, R);
+    scatter<T, OCT, KIND != K_MASS>(ug, og, L, A.dst + r * A.ld, R);
+  }
+}
+
+// Oseen operator, Q2 velocity / Q1 pressure on a uniform mesh, coefficients tabulated.
+// Pw[q][abc] = P[qa][a] P[qb][b] P[qc][c] (Q1 basis at the Gauss points).
+template <typename T> __device__ __forceinline__ T q1w(int q, int n) { return Tb<T>::PW(q, n); }
+
+template <typename T>
+__global__ void __launch_bounds__(128, 1) k_oseen(OseenArgs<typename Store<T>::type> A, UniformGeom ug) {
+  using St = typename Store<T>::type;
+  int i, j, k;
+  if (!brick_cell(ug, i, j, k)) return;
+  const int64_t cell = i + int64_t(ug.nx) * (j + int64_t(ug.ny) * k);
+  const int64_t nc = int64_t(ug.nx) * ug.ny * ug.nz;
+  const int64_t base = 2 * int64_t(i) + ug.sx * (2 * int64_t(j)) + ug.sy * (2 * int64_t(k));
+  const uint32_t dmask = dirichlet_mask(ug, i, j, k);
+  const int64_t px = ug.nx + 1, pxy = px * (ug.ny + 1);
+  const int64_t pbase = i + px * (j + (ug.ny + 1) * int64_t(k));
+  // every term carries a factor h (applied once before the scatter): w h^3 sigma rho u =
+  // h (w rho (sigma h^2) u), w h^2 rho beta.g = h (w rho (h beta.g)), w h mu g = h (w mu g)
+  const T h = T(ug.h), sh2 = T(A.sigma) * h * h;
+  const St* __restrict__ psrc = A.src + 3 * A.nu;
+
+  T R0[27], R1[27], R2[27];
+  {
+    T Pn[8];
+#pragma unroll
+    for (int n = 0; n < 8; ++n) Pn[n] = from_store<T>(__ldg(psrc + pbase + (n & 1) + px * ((n >> 1) & 1) + pxy * (n >> 2)));
+#pragma unroll
+    for (int q = 0; q < 27; ++q) { R0[q] = T(0); R1[q] = T(0); R2[q] = T(0); }
+#pragma unroll
+    for (int qc = 0; qc < 3; ++qc)
+#pragma unroll
+      for (int qb = 0; qb < 3; ++qb)
+#pragma unroll
+        for (int qa = 0; qa < 3; ++qa) {
+          const int q = qa + 3 * qb + 9 * qc;
+          T pq = T(0);
+#pragma unroll
+          for (int n = 0; n < 8; ++n) pq += q1w<T>(q, n) * Pn[n];
+          const T s = Tb<T>::W3(q) * (-h * pq);   // -int p div v
+          add_dir_test<T, 0>(R0, qa, qb, qc, s);
+          add_dir_test<T, 1>(R1, qa, qb, qc, s);
+          add_dir_test<T, 2>(R2, qa, qb, qc, s);
+        }
+  }
+  T Rp[8];
+#pragma unroll
+  for (int n = 0; n < 8; ++n) Rp[n] = T(0);
+
+#pragma unroll 1
+  for (int d = 0; d < 3; ++d) {
+    T U[27];
+    gather_uniform<T>(A.src + d * A.nu, base, ug.sx, ug.sy, dmask, U);
+    to_qpoints<T>(U);
+#pragma unroll
+    for (int qc = 0; qc < 3; ++qc)
+#pragma unroll
+      for (int qb = 0; qb < 3; ++qb)
+#pragma unroll
+        for (int qa = 0; qa < 3; ++qa) {
+          const int q = qa + 3 * qb + 9 * qc;
+          const T w = Tb<T>::W3(q);
+          T gx, gy, gz;
+          grad_at<T>(U, qa, qb, qc, gx, gy, gz);
+          const T rho = from_store<T>(__ldg(A.rho + q * nc + cell));
+          const T mu = from_store<T>(__ldg(A.mu + q * nc + cell));
+          const T bx = from_store<T>(__ldg(A.beta + (0 * 27 + q) * nc + cell));
+          const T by = from_store<T>(__ldg(A.beta + (1 * 27 + q) * nc + cell));
+          const T bz = from_store<T>(__ldg(A.beta + (2 * 27 + q) * nc + cell));
+          const T fv = w * (rho * (sh2 * U[q] + h * (bx * gx + by * gy + bz * gz)));
+          const T c1 = w * mu;
+          const T cx = c1 * gx, cy = c1 * gy, cz = c1 * gz;
+          const T gd = d == 0 ? gx : (d == 1 ? gy : gz);
+          // 2 mu eps(u):eps(v) = mu (grad u_d . grad v_d + d_c u_d d_d v_c), trial component d
+          if (d == 0) {
+            R0[q] += fv;
+            add_grad_test<T>(R0, qa, qb, qc, cx, cy, cz);
+            add_dir_test<T, 0>(R0, qa, qb, qc, cx);
+            add_dir_test<T, 0>(R1, qa, qb, qc, cy);
+            add_dir_test<T, 0>(R2, qa, qb, qc, cz);
+          } else if (d == 1) {
+            R1[q] += fv;
+            add_grad_test<T>(R1, qa, qb, qc, cx, cy, cz);
+            add_dir_test<T, 1>(R0, qa, qb, qc, cx);
+            add_dir_test<T, 1>(R1, qa, qb, qc, cy);
+            add_dir_test<T, 1>(R2, qa, qb, qc, cz);
+          } else {
+            R2[q] += fv;
+            add_grad_test<T>(R2, qa, qb, qc, cx, cy, cz);
+            add_dir_test<T, 2>(R0, qa, qb, qc, cx);
+            add_dir_test<T, 2>(R1, qa, qb, qc, cy);
+            add_dir_test<T, 2>(R2, qa, qb, qc, cz);
+          }
+          const T s = w * (-h * gd);  // -int q div u
+#pragma unroll
+          for (int n = 0; n < 8; ++n) Rp[n] += q1w<T>(q, n) * s;
+        }
+  }
+#pragma unroll
+  for (int q = 0; q < 27; ++q) { R0[q] *= h; R1[q] *= h; R2[q] *= h; }
+  to_nodes<T>(R0);
+  scatter_uniform<T>(A.dst, base, ug.sx, ug.sy, dmask, R0);
+  to_nodes<T>(R1);
+  scatter_uniform<T>(A.dst + A.nu, base, ug.sx, ug.sy, dmask, R1);
+  to_nodes<T>(R2);
+  scatter_uniform<T>(A.dst + 2 * A.nu, base, ug.sx, ug.sy, dmask, R2);
+  St* pdst = A.dst + 3 * A.nu;
+#pragma unroll
+  for (int n = 0; n < 8; ++n)
+    atomicAdd(pdst + pbase + (n & 1) + px * ((n >> 1) & 1) + pxy * (n >> 2), to_store<T>(h * Rp[n]));
+}
+
+}  // namespace
+
+template <typename T, int KIND, int MODE, bool BETA, bool TR>
+static inline mf_status launch_one(mf_ctx* ctx, const mf_dofmap* m, const ScalarArgs<typename Store<T>::type>& a) {
+  UniformGeom ug = m->uniform ? uniform_geom(m) : UniformGeom{};
+  OctGeom og = oct_geom(m);
+  if (m->uniform) {
+    int nb = brick_blocks(ug.nx, ug.ny, ug.nz);
+    k_scalar<T, KIND, MODE, BETA, TR, false><<<nb, 128, 0, ctx->stream>>>(a, ug, og);
+  } else {
+    int nb = int((m->n_cells + 127) / 128);
+    k_scalar<T, KIND, MODE, BETA, TR, true><<<nb, 128, 0, ctx->stream>>>(a, ug, og);
+  }
+  ctx->launches++;
+  MF_CUDA_TRY(cudaGetLastError());
+  return MF_OK;
+}
+
+// in-kernel coefficients exist for fp64 and fp32; double-float kernels read tabulated ones
+template <typename T, int KIND, bool BETA, bool TR>
+static inline mf_status launch_mode(mf_ctx* ctx, const mf_dofmap* m, int mode, const ScalarArgs<typename Store<T>::type>& a) {
+  if constexpr (!std::is_same<T, df64>::value) {
+    if (mode == 0) return launch_one<T, KIND, 0, BETA, TR>(ctx, m, a);
+  }
+  return launch_one<T, KIND, 1, BETA, TR>(ctx, m, a);
+}
+
+template <typename T>
+static inline mf_status dispatch_scalar(mf_ctx* ctx, const mf_dofmap* m, int kind, int mode, bool beta, bool tr,
+                                 const ScalarArgs<typename Store<T>::type>& a) {
+  MF_CUDA_TRY(upload_tables_here());
+  switch (kind) {
+    case K_HELM:
+      return launch_mode<T, K_HELM, false, false>(ctx, m, mode, a);
+    case K_HEAT:
+      if (!beta) return launch_mode<T, K_HEAT, false, false>(ctx, m, mode, a);
+      if (!tr) return launch_mode<T, K_HEAT, true, false>(ctx, m, mode, a);
+      return launch_mode<T, K_HEAT, true, true>(ctx, m, mode, a);
+    case K_REINIT:
+      return launch_mode<T, K_REINIT, false, false>(ctx, m, mode, a);
+    case K_MASS:
+      return launch_one<T, K_MASS, 1, false, false>(ctx, m, a);
+  }
+  return fail(MF_EINVAL, "unknown scalar operator kind");
+}
+
+}  // namespace mf

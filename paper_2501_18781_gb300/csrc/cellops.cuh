@@ -198,42 +198,6 @@ __device__ __forceinline__ bool brick_cell(const UniformGeom& g, int& i, int& j,
 }
 inline int brick_blocks(int nx, int ny, int nz) { return ((nx + 7) / 8) * ((ny + 3) / 4) * ((nz + 3) / 4); }
 
-// Lattice nodes of one 8 x 4 x 4-cell brick: 17 x 9 x 9.
-constexpr int kBrickX = 17, kBrickY = 9, kBrickZ = 9, kBrickNodes = kBrickX * kBrickY * kBrickZ;
-
-// acc[brick node] += R[local node] for the calling thread's cell (shared-memory atomics).
-template <typename T>
-__device__ __forceinline__ void brick_accumulate(typename Store<T>::type* acc, const T* R) {
-  const int t = threadIdx.x;
-  const int base = 2 * (t & 7) + kBrickX * (2 * ((t >> 3) & 3) + kBrickY * (2 * (t >> 5)));
-#pragma unroll
-  for (int l = 0; l < 27; ++l) {
-    const int a = l % 3, b = (l / 3) % 3, c = l / 9;
-    atomicAdd(acc + base + a + kBrickX * (b + kBrickY * c), to_store<T>(R[l]));
-  }
-}
-
-// Write the brick's sums: nodes strictly inside the brick, or on a brick face that is the
-// domain boundary, are touched by this block only (plain store into the zeroed output);
-// nodes on a face shared with a neighbouring brick are added atomically.
-template <typename St>
-__device__ __forceinline__ void brick_flush(const UniformGeom& g, const St* acc, St* __restrict__ dst) {
-  const int nbx = (g.nx + 7) >> 3, nby = (g.ny + 3) >> 2;
-  const int b = blockIdx.x;
-  const int gx0 = 16 * (b % nbx), gy0 = 8 * ((b / nbx) % nby), gz0 = 8 * (b / (nbx * nby));
-  const int Rx = 2 * g.nx, Ry = 2 * g.ny, Rz = 2 * g.nz;
-  for (int i = threadIdx.x; i < kBrickNodes; i += blockDim.x) {
-    const int lx = i % kBrickX, ly = (i / kBrickX) % kBrickY, lz = i / (kBrickX * kBrickY);
-    const int gx = gx0 + lx, gy = gy0 + ly, gz = gz0 + lz;
-    if (gx > Rx || gy > Ry || gz > Rz) continue;
-    const bool shared = (lx == 0 && gx > 0) || (lx == kBrickX - 1 && gx < Rx) || (ly == 0 && gy > 0) ||
-                        (ly == kBrickY - 1 && gy < Ry) || (lz == 0 && gz > 0) || (lz == kBrickZ - 1 && gz < Rz);
-    St* p = dst + gx + g.sx * gy + g.sy * gz;
-    if (shared) atomicAdd(p, acc[i]);
-    else *p = acc[i];
-  }
-}
-
 // 27-bit mask of the cell's local nodes on Dirichlet faces.
 __device__ __forceinline__ uint32_t dirichlet_mask(const UniformGeom& g, int i, int j, int k) {
   if (!g.dir_faces) return 0u;
