@@ -37,6 +37,22 @@ OSEEN_FLOPS_PER_CELL = 945 + 8019 + 1304
 OSEEN_BYTES_PER_VEL_NODE = 4 * 8
 
 
+def max_over_ranks(seconds, dist=None, device="cpu"):
+    """The slowest rank's timed-region duration (every rank calls this)."""
+    if dist is None:
+        return seconds
+    import torch
+    t = torch.tensor([seconds], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank, steps, world, seconds):
+    """Whole-job throughput in G units/s: every rank processes units_per_rank per step
+    (independent replicas, weak scaling), timed by the slowest rank."""
+    return units_per_rank * steps * world / seconds / 1e9
+
+
 def measured_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -405,11 +421,8 @@ def main():
         times = time_apply(op, src, dst, args.steps, 0, flush)
     launches = ctx.launch_count() - l0
     total = sum(times)
-    if dist:
-        t = torch.tensor([total], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total = float(t.item())
-    value = n * args.steps * world / total / 1e9
+    total = max_over_ranks(total, dist, "cuda")
+    value = whole_job_rate(n, args.steps, world, total)
     mean = total / args.steps
 
     # end to end through the public API: pinned host input -> device -> apply -> host output

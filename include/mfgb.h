@@ -179,7 +179,8 @@ typedef struct {
   double inner_tol;    /* defect correction: inner relative tolerance */
   double cheby_ratio;  /* Chebyshev interval [lambda_max/ratio, 1.1 lambda_max] */
   int lanczos_steps;   /* steps of the lambda_max estimate of D^-1 A */
-  int fp64_arith;      /* arithmetic of the fp64 operator applies: 0 fp64 pipes, 1 double-float */
+  int fp64_arith;      /* arithmetic of the fp64 operator applies: 0 fp64 pipes, 1 double-float,
+                          2 whichever mf_autotune measured faster */
 } mf_solver_params;
 
 typedef struct {

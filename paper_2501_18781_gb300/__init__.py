@@ -158,7 +158,7 @@ def solver_params(solver="cg", precond="jacobi", tol=1e-10, maxit=5000, restart=
                   inner_tol=1e-4, inner_maxit=100, use_graph=False, cheby_ratio=30.0, lanczos_steps=20,
                   fp64_arith="f64"):
     s = _lib.SolverParams()
-    s.fp64_arith = {"f64": 0, "df64": 1}[fp64_arith]
+    s.fp64_arith = {"f64": 0, "df64": 1, "auto": 2}[fp64_arith]
     s.solver = {"cg": MF_SOLVER_CG, "gmres": MF_SOLVER_GMRES, "defect_correction": MF_SOLVER_DEFECT_CORRECTION}[solver]
     s.precond = {"none": MF_PREC_NONE, "jacobi": MF_PREC_JACOBI, "chebyshev": MF_PREC_CHEBYSHEV,
                  "block_jacobi": MF_PREC_BLOCK_JACOBI}[precond]

@@ -450,6 +450,8 @@ template <typename T> ScalarArgs<T> scalar_args(const mf_op* op, const T* src, T
   a.k_slope = T(0.5 * op->p.k0 / (op->p.t_boil > 0 ? op->p.t_boil : 1.0));
   a.eps = T(op->p.eps);
   a.heaviside = op->p.heaviside;
+  a.block = op->block;
+  a.persistent_blocks = op->persistent_blocks;
   return a;
 }
 template ScalarArgs<double> scalar_args<double>(const mf_op*, const double*, double*, int, int64_t);
@@ -512,7 +514,9 @@ mf_status apply_impl(mf_op* op, const T* src, T* dst, int nrhs, int64_t ld, bool
   MF_TRY(launch_dirichlet_copy(c, op->map[0], src, dst, nrhs, ld, 0, f32));
   op->variant = std::string(kind == K_HELM ? "helmholtz" : kind == K_HEAT ? "heat" : "reinit") +
                 (op->map[0]->uniform ? "/uniform" : "/octree") + pname +
-                (m == 0 ? "/inkernel" : "/tabulated") + (beta ? (transpose ? "/conv-T" : "/conv") : "");
+                (m == 0 ? "/inkernel" : "/tabulated") + (beta ? (transpose ? "/conv-T" : "/conv") : "") + "/block" +
+                std::to_string(op->map[0]->uniform ? 128 : op->block) +
+                (op->persistent_blocks > 0 ? "/persistent" + std::to_string(op->persistent_blocks) : "");
   return MF_OK;
 }
 template mf_status apply_impl<double>(mf_op*, const double*, double*, int, int64_t, bool, int);

@@ -3,6 +3,7 @@
 // translation unit per arithmetic (apply_f64.cu, apply_f32.cu, apply_df64.cu) so that the three
 // instantiations compile in parallel.
 #pragma once
+#include <algorithm>
 #include <type_traits>
 
 #include "scalar_local.cuh"
@@ -23,9 +24,12 @@ struct CellLoc {
   double h;
 };
 
+// Work unit w: the w-th slot of blockDim.x cells of the (sorted) octree cell list, or the
+// w-th 8 x 4 x 4 brick of a uniform mesh; the thread's cell within it.
 template <bool OCT>
-__device__ __forceinline__ bool locate(const UniformGeom& ug, const OctGeom& og, int64_t t, CellLoc& L) {
+__device__ __forceinline__ bool locate(const UniformGeom& ug, const OctGeom& og, int64_t w, CellLoc& L) {
   if (OCT) {
+    const int64_t t = w * blockDim.x + threadIdx.x;
     if (t >= og.ncells) return false;
     L.cell = __ldg(og.order + t);
     L.h = og.h0 / double(1 << __ldg(og.level + L.cell));
@@ -34,7 +38,7 @@ __device__ __forceinline__ bool locate(const UniformGeom& ug, const OctGeom& og,
     return true;
   } else {
     int i, j, k;
-    if (!brick_cell(ug, i, j, k)) return false;
+    if (!brick_cell(ug, i, j, k, int(w))) return false;
     L.cell = i + int64_t(ug.nx) * (j + int64_t(ug.ny) * k);
     L.base = 2 * int64_t(i) + ug.sx * (2 * int64_t(j)) + ug.sy * (2 * int64_t(k));
     L.dmask = dirichlet_mask(ug, i, j, k);
@@ -59,14 +63,9 @@ __device__ __forceinline__ void scatter(const UniformGeom& ug, const OctGeom& og
 // Scalar operators.  KIND: K_HELM, K_HEAT, K_REINIT, K_MASS; MODE 0 = coefficients from the
 // nodal field in the kernel, 1 = tabulated per Gauss point.
 template <typename T, int KIND, int MODE, bool BETA, bool TR, bool OCT>
-__global__ void __launch_bounds__(128) k_scalar(ScalarArgs<typename Store<T>::type> A, UniformGeom ug, OctGeom og) {
-  using St = typename Store<T>::type;
-  CellLoc L;
-  const int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-  bool active = locate<OCT>(ug, og, t, L);
-  if constexpr (OCT) {
-    if (!active) return;
-  }
+__device__ __forceinline__ void scalar_cell(const ScalarArgs<typename Store<T>::type>& A, const UniformGeom& ug,
+                                            const OctGeom& og, CellLoc L) {
+  bool active = true;
   if (KIND == K_MASS) L.dmask = 0u;  // the plain mass matrix has no Dirichlet rows
   const T h = T(OCT ? L.h : ug.h);
   // every term carries at least one power of h: R = h * (...), with
@@ -77,14 +76,10 @@ __global__ void __launch_bounds__(128) k_scalar(ScalarArgs<typename Store<T>::ty
     const int64_t kk = L.base / ug.sy, jj = (L.base % ug.sy) / ug.sx, ii = L.base % ug.sx;
     const double cx = A.lo[0] + (double(ii) * 0.5 + 0.5) * L.h, cy = A.lo[1] + (double(jj) * 0.5 + 0.5) * L.h,
                  cz = A.lo[2] + (double(kk) * 0.5 + 0.5) * L.h;
-    if (!(fabs(cx) <= A.box_half && fabs(cy) <= A.box_half && cz >= A.box_zmin)) {
-      if constexpr (OCT) return;
-      active = false;
-    }
+    if (!(fabs(cx) <= A.box_half && fabs(cy) <= A.box_half && cz >= A.box_zmin)) return;
   }
   // scalar coefficient (or phi for in-kernel reinit) at the 27 Gauss points
   T C[27];
-  if (active)
   if constexpr (KIND == K_HELM || KIND == K_HEAT || KIND == K_REINIT) {
     if constexpr (MODE == 0) {
       gather<T, OCT, false>(ug, og, CellLoc{L.cell, L.base, 0u, L.h}, A.field, C);
@@ -101,12 +96,23 @@ __global__ void __launch_bounds__(128) k_scalar(ScalarArgs<typename Store<T>::ty
       for (int q = 0; q < 27; ++q) C[q] = from_store<T>(__ldg(A.qcoef + q * A.ncp + L.cell));
     }
   }
-  if (!active) return;
   for (int r = 0; r < A.nrhs; ++r) {
     T U[27], R[27];
     gather<T, OCT, KIND != K_MASS>(ug, og, L, A.src + r * A.ld, U);
     scalar_local<T, KIND, MODE, BETA, TR>(A, L.cell, h, mh2, C, U, R);
     scatter<T, OCT, KIND != K_MASS>(ug, og, L, A.dst + r * A.ld, R);
+  }
+}
+
+// One launch sweeps all nwork work units; with fewer blocks than units (the persistent
+// variant, grid = a few blocks per SM) each block strides over them.  All right-hand sides of
+// a cell are applied while its coefficients sit in registers.
+template <typename T, int KIND, int MODE, bool BETA, bool TR, bool OCT>
+__global__ void __launch_bounds__(128) k_scalar(ScalarArgs<typename Store<T>::type> A, UniformGeom ug, OctGeom og,
+                                                int64_t nwork) {
+  for (int64_t w = blockIdx.x; w < nwork; w += gridDim.x) {
+    CellLoc L;
+    if (locate<OCT>(ug, og, w, L)) scalar_cell<T, KIND, MODE, BETA, TR, OCT>(A, ug, og, L);
   }
 }
 
@@ -226,13 +232,16 @@ template <typename T, int KIND, int MODE, bool BETA, bool TR>
 static inline mf_status launch_one(mf_ctx* ctx, const mf_dofmap* m, const ScalarArgs<typename Store<T>::type>& a) {
   UniformGeom ug = m->uniform ? uniform_geom(m) : UniformGeom{};
   OctGeom og = oct_geom(m);
-  if (m->uniform) {
-    int nb = brick_blocks(ug.nx, ug.ny, ug.nz);
-    k_scalar<T, KIND, MODE, BETA, TR, false><<<nb, 128, 0, ctx->stream>>>(a, ug, og);
-  } else {
-    int nb = int((m->n_cells + 127) / 128);
-    k_scalar<T, KIND, MODE, BETA, TR, true><<<nb, 128, 0, ctx->stream>>>(a, ug, og);
-  }
+  // octree cell slots may be 64 or 128 wide; uniform bricks are 128 cells
+  const int threads = m->uniform ? 128 : (a.block == 64 ? 64 : 128);
+  const int64_t nwork = m->uniform ? brick_blocks(ug.nx, ug.ny, ug.nz) : (m->n_cells + threads - 1) / threads;
+  int64_t grid = nwork;
+  if (a.persistent_blocks > 0) grid = std::min<int64_t>(nwork, int64_t(a.persistent_blocks) * ctx->sm_count);
+  if (grid < 1) return MF_OK;
+  if (m->uniform)
+    k_scalar<T, KIND, MODE, BETA, TR, false><<<unsigned(grid), threads, 0, ctx->stream>>>(a, ug, og, nwork);
+  else
+    k_scalar<T, KIND, MODE, BETA, TR, true><<<unsigned(grid), threads, 0, ctx->stream>>>(a, ug, og, nwork);
   ctx->launches++;
   MF_CUDA_TRY(cudaGetLastError());
   return MF_OK;

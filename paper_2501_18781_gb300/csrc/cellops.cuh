@@ -186,9 +186,9 @@ struct UniformGeom {
 };
 
 // Bricks of 8 x 4 x 4 cells per 128-thread block (x fastest within a warp row).
-__device__ __forceinline__ bool brick_cell(const UniformGeom& g, int& i, int& j, int& k) {
+__device__ __forceinline__ bool brick_cell(const UniformGeom& g, int& i, int& j, int& k, int b = -1) {
   const int nbx = (g.nx + 7) >> 3, nby = (g.ny + 3) >> 2;
-  int b = blockIdx.x;
+  if (b < 0) b = blockIdx.x;
   int bx = b % nbx, by = (b / nbx) % nby, bz = b / (nbx * nby);
   int t = threadIdx.x;
   i = bx * 8 + (t & 7);

@@ -28,6 +28,10 @@ template <typename T> struct ScalarArgs {
   // K_MASS only: restrict to cells whose centre lies in a box (|x|,|y| <= bx, z >= bz)
   int use_box;
   double box_half, box_zmin, lo[3];
+  // launch shape (autotuned): octree cells per block (64 or 128) and, if > 0, a persistent
+  // grid of persistent_blocks blocks per SM striding over the work units
+  int block;
+  int persistent_blocks;
 };
 
 template <typename T> struct OseenArgs {
@@ -90,5 +94,9 @@ struct mf_op {
   bool diag_ready = false;
   int mode64 = 1, mode32 = 0;     // coefficient mode per precision (autotuned)
   int f64_prec = 0;               // arithmetic of fp64 applies inside solvers (PREC_F64 or PREC_DF64)
+  int block = 128;                // octree cells per block (autotuned: 64 or 128)
+  int persistent_blocks = 0;      // > 0: persistent launch with this many blocks per SM (autotuned)
+  bool df64_faster = false;       // autotuned: double-float beats the fp64 pipes (used when fp64_arith = 2)
+  std::string tune_record;        // JSON of the last autotuning
   std::string variant;
 };

@@ -488,7 +488,7 @@ mf_status solve_impl(mf_op* op, const mf_solver_params* sp, const double* b, dou
     int prev;
     ~Restore() { op->f64_prec = prev; }
   } restore{op, op->f64_prec};
-  op->f64_prec = sp->fp64_arith == 1 ? PREC_DF64 : PREC_F64;
+  op->f64_prec = (sp->fp64_arith == 1 || (sp->fp64_arith == 2 && op->df64_faster)) ? PREC_DF64 : PREC_F64;
   mf_solve_info inf{};
   mf_status st = MF_OK;
   const double tol = sp->tol > 0 ? sp->tol : 1e-10;
@@ -703,38 +703,69 @@ mf_status mf_autotune(mf_op* op, const char* cache_path) {
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
     const bool forced = op->p.kind == MF_OP_HEAT && (op->kq_user || op->beta);
-    double best[2][2] = {{1e30, 1e30}, {1e30, 1e30}};
-    for (int prec = 0; prec < 2; ++prec)
+    DevBuf s32, d32;
+    MF_TRY(s32.alloc(sizeof(float) * n));
+    MF_TRY(d32.alloc(sizeof(float) * n));
+    MF_TRY(convert<double, float>(c, n, src.as<double>(), s32.as<float>()));
+    // median-free best-of-5 event timing of one apply variant
+    auto time_variant = [&](int prec, double* out_ms) -> mf_status {
+      double best = 1e30;
+      for (int rep = 0; rep < 6; ++rep) {
+        cudaEventRecord(e0, c->stream);
+        if (prec == PREC_F32) MF_TRY(apply_impl<float>(op, s32.as<float>(), d32.as<float>(), 1, n, false, PREC_F32));
+        else MF_TRY(apply_impl<double>(op, src.as<double>(), dst.as<double>(), 1, n, false, prec));
+        cudaEventRecord(e1, c->stream);
+        MF_CUDA_TRY(cudaEventSynchronize(e1));
+        float ms;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (rep > 0) best = std::min(best, double(ms));
+      }
+      *out_ms = best;
+      return MF_OK;
+    };
+    // 1) coefficient evaluation: in the kernel from nodal fields, or tabulated per Gauss point
+    double mode_ms[2][2] = {{1e30, 1e30}, {1e30, 1e30}};
+    for (int pi = 0; pi < 2; ++pi)
       for (int mode = 0; mode < 2; ++mode) {
         if (forced && mode == 0) continue;
-        if (prec == 0) op->mode64 = mode;
-        else op->mode32 = mode;
-        DevBuf s32;
-        if (prec == 1) {
-          MF_TRY(s32.alloc(sizeof(float) * n));
-          MF_TRY(convert<double, float>(c, n, src.as<double>(), s32.as<float>()));
-        }
-        for (int rep = 0; rep < 6; ++rep) {
-          cudaEventRecord(e0, c->stream);
-          if (prec == 0) MF_TRY(apply_impl<double>(op, src.as<double>(), dst.as<double>(), 1, n, false));
-          else MF_TRY(apply_impl<float>(op, s32.as<float>(), reinterpret_cast<float*>(dst.as<double>()), 1, n, false));
-          cudaEventRecord(e1, c->stream);
-          MF_CUDA_TRY(cudaEventSynchronize(e1));
-          float ms;
-          cudaEventElapsedTime(&ms, e0, e1);
-          if (rep > 0) best[prec][mode] = std::min(best[prec][mode], double(ms));
-        }
+        (pi == 0 ? op->mode64 : op->mode32) = mode;
+        MF_TRY(time_variant(pi == 0 ? PREC_F64 : PREC_F32, &mode_ms[pi][mode]));
       }
+    op->mode64 = mode_ms[0][0] < mode_ms[0][1] ? 0 : 1;
+    op->mode32 = mode_ms[1][0] < mode_ms[1][1] ? 0 : 1;
+    // 2) launch shape on the fp32 apply: cells per block (octree) and persistent grids
+    const int shapes[5][2] = {{128, 0}, {64, 0}, {128, 2}, {128, 4}, {64, 8}};
+    double shape_ms[5];
+    int best_shape = 0;
+    for (int si = 0; si < 5; ++si) {
+      shape_ms[si] = 1e30;
+      if (op->map[0]->uniform && shapes[si][0] != 128) continue;
+      op->block = shapes[si][0];
+      op->persistent_blocks = shapes[si][1];
+      MF_TRY(time_variant(PREC_F32, &shape_ms[si]));
+      if (shape_ms[si] < shape_ms[best_shape]) best_shape = si;
+    }
+    op->block = shapes[best_shape][0];
+    op->persistent_blocks = shapes[best_shape][1];
+    // 3) fp64-accurate arithmetic: fp64 pipes vs double-float on the fp32 pipes
+    double f64_ms, df_ms;
+    MF_TRY(time_variant(PREC_F64, &f64_ms));
+    MF_TRY(time_variant(PREC_DF64, &df_ms));
+    op->df64_faster = df_ms < f64_ms;
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    op->mode64 = best[0][0] < best[0][1] ? 0 : 1;
-    op->mode32 = best[1][0] < best[1][1] ? 0 : 1;
+    char buf[512];
+    std::snprintf(buf, sizeof buf,
+                  "{\"kind\": %d, \"n\": %lld, \"f64_inkernel_ms\": %.6g, \"f64_tabulated_ms\": %.6g, "
+                  "\"f32_inkernel_ms\": %.6g, \"f32_tabulated_ms\": %.6g, \"block\": %d, \"persistent_blocks\": %d, "
+                  "\"f32_shape_ms\": %.6g, \"f64_ms\": %.6g, \"df64_ms\": %.6g}",
+                  op->p.kind, (long long)n, mode_ms[0][0], mode_ms[0][1], mode_ms[1][0], mode_ms[1][1], op->block,
+                  op->persistent_blocks, shape_ms[best_shape], f64_ms, df_ms);
+    op->tune_record = buf;
     if (cache_path) {
       FILE* fp = std::fopen(cache_path, "a");
       if (fp) {
-        std::fprintf(fp, "{\"kind\": %d, \"n\": %lld, \"f64_inkernel_ms\": %.6g, \"f64_tabulated_ms\": %.6g, "
-                     "\"f32_inkernel_ms\": %.6g, \"f32_tabulated_ms\": %.6g, \"mode64\": %d, \"mode32\": %d}\n",
-                     op->p.kind, (long long)n, best[0][0], best[0][1], best[1][0], best[1][1], op->mode64, op->mode32);
+        std::fprintf(fp, "%s\n", buf);
         std::fclose(fp);
       }
     }

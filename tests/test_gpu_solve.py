@@ -167,3 +167,27 @@ def test_cg_with_double_float_applies_reaches_fp64_tolerance(ctx):
     b = syn.uniform_pm1(7, Pg["n"])
     b[Pg["dm"].dirichlet] = 0.0
     solve_and_check(Pg, b, solver="gmres", precond="jacobi", fp64_arith="df64")
+
+
+def test_autograd_function_matches_adjoint_and_central_differences(ctx):
+    from paper_2501_18781_gb300.autograd import heat_step_objective
+    P, laser, th_prev, target = _gradient_case(ctx)
+    tp, tt = torch.tensor(th_prev, device="cuda"), torch.tensor(target, device="cuda")
+    kw = dict(solver="gmres", precond="jacobi", tol=1e-13, restart=50)
+    lz = torch.tensor([laser["power"], laser["radius"], laser["x0"], laser["y0"]], dtype=torch.float64,
+                      requires_grad=True)
+    kq = torch.tensor(P["kq"].ravel(), device="cuda", requires_grad=True)
+    J = heat_step_objective(P["op"], lz, kq, tp, tt, 200e-6, 200e-6, **kw)
+    J.backward()
+    _, g, gk, _, _ = P["op"].heat_step_gradient(list(lz.detach().tolist()) + [0.35], tp, tt, 200e-6, 200e-6, **kw)
+    assert np.allclose(lz.grad.numpy(), g, rtol=1e-12)
+    assert torch.allclose(kq.grad, gk, rtol=1e-12)
+    # central difference on the radius through the Function's forward
+    step = 1e-6 * laser["radius"]
+    with torch.no_grad():
+        a, b = lz.detach().clone(), lz.detach().clone()
+        a[1] += step
+        b[1] -= step
+        fd = (heat_step_objective(P["op"], a, kq.detach(), tp, tt, 200e-6, 200e-6, **kw)
+              - heat_step_objective(P["op"], b, kq.detach(), tp, tt, 200e-6, 200e-6, **kw)) / (2 * step)
+    assert abs(lz.grad[1].item() - fd.item()) <= 1e-6 * abs(fd.item())
