@@ -11,7 +11,8 @@ mf_status launch_scalar_apply_f32(mf_ctx* ctx, const mf_dofmap* m, int kind, int
 mf_status launch_oseen_apply_f32(mf_ctx* ctx, const mf_dofmap* mu, const OseenArgs<float>& a) {
   MF_CUDA_TRY(upload_tables_here());
   UniformGeom ug = uniform_geom(mu);
-  k_oseen<float><<<brick_blocks(ug.nx, ug.ny, ug.nz), 128, 0, ctx->stream>>>(a, ug);
+  // fp32: all three velocity components fit in registers (Gauss-point loop outside)
+  k_oseen_qouter<float><<<brick_blocks(ug.nx, ug.ny, ug.nz), 128, 0, ctx->stream>>>(a, ug);
   ctx->launches++;
   MF_CUDA_TRY(cudaGetLastError());
   return MF_OK;

@@ -226,6 +226,90 @@ __global__ void __launch_bounds__(128, 1) k_oseen(OseenArgs<typename Store<T>::t
     atomicAdd(pdst + pbase + (n & 1) + px * ((n >> 1) & 1) + pxy * (n >> 2), to_store<T>(h * Rp[n]));
 }
 
+// The same Oseen cell operator with the Gauss-point loop outside: all three velocity
+// components sit in registers at once (81 values + 81 accumulators), so each Gauss point's
+// rho, mu and beta are read once instead of once per component.  Fits the fp32 register file.
+template <typename T>
+__global__ void __launch_bounds__(128) k_oseen_qouter(OseenArgs<typename Store<T>::type> A, UniformGeom ug) {
+  using St = typename Store<T>::type;
+  int i, j, k;
+  if (!brick_cell(ug, i, j, k)) return;
+  const int64_t cell = i + int64_t(ug.nx) * (j + int64_t(ug.ny) * k);
+  const int64_t nc = int64_t(ug.nx) * ug.ny * ug.nz;
+  const int64_t base = 2 * int64_t(i) + ug.sx * (2 * int64_t(j)) + ug.sy * (2 * int64_t(k));
+  const uint32_t dmask = dirichlet_mask(ug, i, j, k);
+  const int64_t px = ug.nx + 1, pxy = px * (ug.ny + 1);
+  const int64_t pbase = i + px * (j + (ug.ny + 1) * int64_t(k));
+  const T h = T(ug.h), sh2 = T(A.sigma) * h * h;
+  T U0[27], U1[27], U2[27];
+  gather_uniform<T>(A.src, base, ug.sx, ug.sy, dmask, U0);
+  gather_uniform<T>(A.src + A.nu, base, ug.sx, ug.sy, dmask, U1);
+  gather_uniform<T>(A.src + 2 * A.nu, base, ug.sx, ug.sy, dmask, U2);
+  to_qpoints<T>(U0);
+  to_qpoints<T>(U1);
+  to_qpoints<T>(U2);
+  T Pn[8];
+  const St* __restrict__ psrc = A.src + 3 * A.nu;
+#pragma unroll
+  for (int n = 0; n < 8; ++n) Pn[n] = from_store<T>(__ldg(psrc + pbase + (n & 1) + px * ((n >> 1) & 1) + pxy * (n >> 2)));
+  T R0[27], R1[27], R2[27], Rp[8];
+#pragma unroll
+  for (int q = 0; q < 27; ++q) { R0[q] = T(0); R1[q] = T(0); R2[q] = T(0); }
+#pragma unroll
+  for (int n = 0; n < 8; ++n) Rp[n] = T(0);
+#pragma unroll
+  for (int qc = 0; qc < 3; ++qc)
+#pragma unroll
+    for (int qb = 0; qb < 3; ++qb)
+#pragma unroll
+      for (int qa = 0; qa < 3; ++qa) {
+        const int q = qa + 3 * qb + 9 * qc;
+        const T w = Tb<T>::W3(q);
+        const T rho = from_store<T>(__ldg(A.rho + q * nc + cell));
+        const T mu = from_store<T>(__ldg(A.mu + q * nc + cell));
+        const T bx = from_store<T>(__ldg(A.beta + (0 * 27 + q) * nc + cell));
+        const T by = from_store<T>(__ldg(A.beta + (1 * 27 + q) * nc + cell));
+        const T bz = from_store<T>(__ldg(A.beta + (2 * 27 + q) * nc + cell));
+        T pq = T(0);
+#pragma unroll
+        for (int n = 0; n < 8; ++n) pq += q1w<T>(q, n) * Pn[n];
+        T g[3][3];  // g[d][e] = d u_d / d x_e (reference)
+        grad_at<T>(U0, qa, qb, qc, g[0][0], g[0][1], g[0][2]);
+        grad_at<T>(U1, qa, qb, qc, g[1][0], g[1][1], g[1][2]);
+        grad_at<T>(U2, qa, qb, qc, g[2][0], g[2][1], g[2][2]);
+        const T c1 = w * mu;
+        // value test: sigma rho u_d + rho beta . grad u_d
+        const T rw = w * rho;
+        R0[q] += rw * (sh2 * U0[q] + h * (bx * g[0][0] + by * g[0][1] + bz * g[0][2]));
+        R1[q] += rw * (sh2 * U1[q] + h * (bx * g[1][0] + by * g[1][1] + bz * g[1][2]));
+        R2[q] += rw * (sh2 * U2[q] + h * (bx * g[2][0] + by * g[2][1] + bz * g[2][2]));
+        // gradient test: mu (grad u + grad u^T) - p I (both scaled by the weight)
+        const T pw = w * (-h * pq);
+        const T s00 = c1 * (g[0][0] + g[0][0]) + pw, s11 = c1 * (g[1][1] + g[1][1]) + pw,
+                s22 = c1 * (g[2][2] + g[2][2]) + pw;
+        const T s01 = c1 * (g[0][1] + g[1][0]), s02 = c1 * (g[0][2] + g[2][0]), s12 = c1 * (g[1][2] + g[2][1]);
+        add_grad_test<T>(R0, qa, qb, qc, s00, s01, s02);
+        add_grad_test<T>(R1, qa, qb, qc, s01, s11, s12);
+        add_grad_test<T>(R2, qa, qb, qc, s02, s12, s22);
+        // continuity test: -q div u
+        const T s = w * (-h * (g[0][0] + g[1][1] + g[2][2]));
+#pragma unroll
+        for (int n = 0; n < 8; ++n) Rp[n] += q1w<T>(q, n) * s;
+      }
+#pragma unroll
+  for (int q = 0; q < 27; ++q) { R0[q] *= h; R1[q] *= h; R2[q] *= h; }
+  to_nodes<T>(R0);
+  scatter_uniform<T>(A.dst, base, ug.sx, ug.sy, dmask, R0);
+  to_nodes<T>(R1);
+  scatter_uniform<T>(A.dst + A.nu, base, ug.sx, ug.sy, dmask, R1);
+  to_nodes<T>(R2);
+  scatter_uniform<T>(A.dst + 2 * A.nu, base, ug.sx, ug.sy, dmask, R2);
+  St* pdst = A.dst + 3 * A.nu;
+#pragma unroll
+  for (int n = 0; n < 8; ++n)
+    atomicAdd(pdst + pbase + (n & 1) + px * ((n >> 1) & 1) + pxy * (n >> 2), to_store<T>(h * Rp[n]));
+}
+
 }  // namespace
 
 template <typename T, int KIND, int MODE, bool BETA, bool TR>

@@ -263,35 +263,57 @@ template <> __device__ __forceinline__ const double* con_w<df64>(const OctGeom& 
 template <typename T, bool MASK = true>
 __device__ __forceinline__ void gather_oct(const OctGeom& g, const typename Store<T>::type* __restrict__ src,
                                            int64_t cell, T* U) {
+  // All 27 index loads, then all 27 value loads with no branch in between (constrained slots
+  // read entry 0 and are overwritten below), so a thread keeps 27 independent loads in flight.
+  int32_t id[27];
 #pragma unroll
-  for (int l = 0; l < 27; ++l) {
-    int32_t id = __ldg(g.cmap + l * g.ncp + cell);
-    T v;
-    if (id >= 0) {
-      v = from_store<T>(__ldg(src + id));
-      if (MASK && g.dflag && __ldg(g.dflag + id)) v = T(0);
-    } else {
-      const int r = -1 - id;
+  for (int l = 0; l < 27; ++l) id[l] = __ldg(g.cmap + l * g.ncp + cell);
+#pragma unroll
+  for (int l = 0; l < 27; ++l) U[l] = from_store<T>(__ldg(src + (id[l] >= 0 ? id[l] : 0)));
+  bool constrained = false, dirichlet = MASK && g.dflag;
+#pragma unroll
+  for (int l = 0; l < 27; ++l) constrained |= id[l] < 0;
+  if (dirichlet) {
+#pragma unroll
+    for (int l = 0; l < 27; ++l)
+      if (id[l] >= 0 && __ldg(g.dflag + id[l])) U[l] = T(0);
+  }
+  if (constrained) {
+#pragma unroll
+    for (int l = 0; l < 27; ++l) {
+      if (id[l] >= 0) continue;
+      const int r = -1 - id[l];
       const auto* w = con_w<T>(g);
-      v = T(0);
+      T v = T(0);
       for (int e = __ldg(g.rowptr + r); e < __ldg(g.rowptr + r + 1); ++e) {
         int32_t m = __ldg(g.cols + e);
         T um = from_store<T>(__ldg(src + m));
-        if (MASK && g.dflag && __ldg(g.dflag + m)) um = T(0);
+        if (dirichlet && __ldg(g.dflag + m)) um = T(0);
         v += from_store<T>(__ldg(w + e)) * um;
       }
+      U[l] = v;
     }
-    U[l] = v;
   }
 }
 template <typename T, bool MASK = true>
 __device__ __forceinline__ void scatter_oct(const OctGeom& g, typename Store<T>::type* __restrict__ dst, int64_t cell,
                                             const T* R) {
+  int32_t ids[27];
+#pragma unroll
+  for (int l = 0; l < 27; ++l) ids[l] = __ldg(g.cmap + l * g.ncp + cell);
+  bool constrained = false;
 #pragma unroll
   for (int l = 0; l < 27; ++l) {
-    int32_t id = __ldg(g.cmap + l * g.ncp + cell);
+    const int32_t id = ids[l];
+    constrained |= id < 0;
+    if (id >= 0 && !(MASK && g.dflag && __ldg(g.dflag + id))) atomicAdd(dst + id, to_store<T>(R[l]));
+  }
+  if (!constrained) return;
+#pragma unroll
+  for (int l = 0; l < 27; ++l) {
+    const int32_t id = ids[l];
     if (id >= 0) {
-      if (!(MASK && g.dflag && __ldg(g.dflag + id))) atomicAdd(dst + id, to_store<T>(R[l]));
+      continue;
     } else {
       const int r = -1 - id;
       const auto* w = con_w<T>(g);
