@@ -28,10 +28,13 @@ METRIC = "GDoF/s of matrix-free operator apply & %HBM roofline; CG solve time FP
 WORKLOAD = "oseen_q2q1_interface_64"
 HBM_FALLBACK_GBS = 6800.0
 FP64_PEAK_TFLOPS = 1.25      # GB300 FP64 (vector and tensor) rate of the profiling recipe's table
-# Algorithmic flops of one Oseen Q2/Q1 cell apply as the kernel performs it (FMA = 2 flops):
-# pressure at the Gauss points and its test terms 945, three velocity components x
-# (3 value sweeps 405 + 27 Gauss points x 84) = 8019, integration sweeps and scaling 1304.
-OSEEN_FLOPS_PER_CELL = 945 + 8019 + 1304
+# Algorithmic flops of one Oseen Q2/Q1 cell apply as each kernel variant performs it (FMA = 2):
+# component loop outside: pressure at the Gauss points and its test terms 945, three velocity
+# components x (3 value sweeps 405 + 27 Gauss points x 84) = 8019, integration sweeps and
+# scaling 1304.  Gauss-point loop outside: value sweeps 3 x 405, 27 points x 183 (pressure
+# 15, 9 gradients 45, value terms 30, symmetric stress 17, 3 test accumulations 54,
+# continuity 20, weights 2), scaling 89, integration sweeps 3 x 405.
+OSEEN_FLOPS_PER_CELL = {"component-outer": 945 + 8019 + 1304, "qpoint-outer": 1215 + 27 * 183 + 89 + 1215}
 # Algorithmic HBM bytes of one fp64 Oseen apply: read u, write v (16 B per DoF), the nodal
 # level set and convection field the coefficients come from (4 x 8 B per velocity node).
 OSEEN_BYTES_PER_VEL_NODE = 4 * 8
@@ -142,6 +145,7 @@ def build_oseen(ctx, n=64):
                   mu_g=p["mu_g"], eps=wl.eps)
     op.set_field("phi", torch.tensor(phi, device="cuda"))
     op.set_field("beta", torch.tensor(beta.ravel(), device="cuda"))
+    op.autotune()   # set-up: picks the fp64 kernel variant (component- or Gauss-point-outer)
     return op, mu, mp, mesh
 
 
@@ -449,7 +453,7 @@ def main():
 
     peaks = measured_peaks()
     hbm = peaks.get("hbm_gbs", HBM_FALLBACK_GBS)
-    flops = OSEEN_FLOPS_PER_CELL * ncells
+    flops = OSEEN_FLOPS_PER_CELL["qpoint-outer" if "qpoint-outer" in op.variant else "component-outer"] * ncells
     alg_bytes = 16 * n + OSEEN_BYTES_PER_VEL_NODE * mu.n_dofs
     achieved = flops / mean / 1e12
     out = {

@@ -468,6 +468,7 @@ template <typename T> OseenArgs<T> oseen_args(const mf_op* op, const T* src, T* 
   a.mu = f32 ? reinterpret_cast<const T*>(op->mu32.as<float>()) : reinterpret_cast<const T*>(op->mu64.as<double>());
   a.beta = f32 ? reinterpret_cast<const T*>(op->qvec32.as<float>()) : reinterpret_cast<const T*>(op->qvec64.as<double>());
   a.sigma = T(op->p.sigma);
+  a.qouter = op->oseen_qouter64;
   return a;
 }
 template OseenArgs<double> oseen_args<double>(const mf_op*, const double*, double*);
@@ -498,7 +499,8 @@ mf_status apply_impl(mf_op* op, const T* src, T* dst, int nrhs, int64_t ld, bool
       for (int comp = 0; comp < 3; ++comp)
         MF_TRY(launch_dirichlet_copy(c, op->map[0], src + r * ld, dst + r * ld, 1, ld, comp * nu, f32));
     }
-    op->variant = std::string("oseen_q2q1") + pname + "/tabulated";
+    op->variant = std::string("oseen_q2q1") + pname + "/tabulated" +
+                  ((f32 || op->oseen_qouter64) ? "/qpoint-outer" : "/component-outer");
     return MF_OK;
   }
   const int kind = scalar_kind(op);

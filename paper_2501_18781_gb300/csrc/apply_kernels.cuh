@@ -64,8 +64,9 @@ __device__ __forceinline__ void scatter(const UniformGeom& ug, const OctGeom& og
 // nodal field in the kernel, 1 = tabulated per Gauss point.
 template <typename T, int KIND, int MODE, bool BETA, bool TR, bool OCT>
 __device__ __forceinline__ void scalar_cell(const ScalarArgs<typename Store<T>::type>& A, const UniformGeom& ug,
-                                            const OctGeom& og, CellLoc L) {
-  bool active = true;
+                                            const OctGeom& og, CellLoc L, bool active) {
+  // On uniform meshes all 32 lanes of a warp take part in the warp-level scatter, so a lane
+  // without a cell stays (inactive, contributing zeros) instead of returning.
   if (KIND == K_MASS) L.dmask = 0u;  // the plain mass matrix has no Dirichlet rows
   const T h = T(OCT ? L.h : ug.h);
   // every term carries at least one power of h: R = h * (...), with
@@ -76,10 +77,14 @@ __device__ __forceinline__ void scalar_cell(const ScalarArgs<typename Store<T>::
     const int64_t kk = L.base / ug.sy, jj = (L.base % ug.sy) / ug.sx, ii = L.base % ug.sx;
     const double cx = A.lo[0] + (double(ii) * 0.5 + 0.5) * L.h, cy = A.lo[1] + (double(jj) * 0.5 + 0.5) * L.h,
                  cz = A.lo[2] + (double(kk) * 0.5 + 0.5) * L.h;
-    if (!(fabs(cx) <= A.box_half && fabs(cy) <= A.box_half && cz >= A.box_zmin)) return;
+    if (!(fabs(cx) <= A.box_half && fabs(cy) <= A.box_half && cz >= A.box_zmin)) active = false;
+  }
+  if constexpr (OCT) {
+    if (!active) return;
   }
   // scalar coefficient (or phi for in-kernel reinit) at the 27 Gauss points
   T C[27];
+  if (active)
   if constexpr (KIND == K_HELM || KIND == K_HEAT || KIND == K_REINIT) {
     if constexpr (MODE == 0) {
       gather<T, OCT, false>(ug, og, CellLoc{L.cell, L.base, 0u, L.h}, A.field, C);
@@ -98,9 +103,15 @@ __device__ __forceinline__ void scalar_cell(const ScalarArgs<typename Store<T>::
   }
   for (int r = 0; r < A.nrhs; ++r) {
     T U[27], R[27];
-    gather<T, OCT, KIND != K_MASS>(ug, og, L, A.src + r * A.ld, U);
-    scalar_local<T, KIND, MODE, BETA, TR>(A, L.cell, h, mh2, C, U, R);
-    scatter<T, OCT, KIND != K_MASS>(ug, og, L, A.dst + r * A.ld, R);
+    if (active) {
+      gather<T, OCT, KIND != K_MASS>(ug, og, L, A.src + r * A.ld, U);
+      scalar_local<T, KIND, MODE, BETA, TR>(A, L.cell, h, mh2, C, U, R);
+    } else {
+#pragma unroll
+      for (int q = 0; q < 27; ++q) R[q] = T(0);
+    }
+    if constexpr (OCT) scatter_oct<T, KIND != K_MASS>(og, A.dst + r * A.ld, L.cell, R);
+    else scatter_uniform_warp<T>(A.dst + r * A.ld, L.base, ug.sx, ug.sy, L.dmask, R, active);
   }
 }
 
@@ -112,7 +123,9 @@ __global__ void __launch_bounds__(128) k_scalar(ScalarArgs<typename Store<T>::ty
                                                 int64_t nwork) {
   for (int64_t w = blockIdx.x; w < nwork; w += gridDim.x) {
     CellLoc L;
-    if (locate<OCT>(ug, og, w, L)) scalar_cell<T, KIND, MODE, BETA, TR, OCT>(A, ug, og, L);
+    const bool active = locate<OCT>(ug, og, w, L);
+    if (OCT && !active) continue;
+    scalar_cell<T, KIND, MODE, BETA, TR, OCT>(A, ug, og, L, active);
   }
 }
 

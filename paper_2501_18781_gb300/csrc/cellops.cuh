@@ -239,6 +239,46 @@ __device__ __forceinline__ void scatter_uniform(typename Store<T>::type* __restr
   }
 }
 
+template <typename T> __device__ __forceinline__ T shfl_down_t(T v, int d) {
+  return __shfl_down_sync(0xffffffffu, v, d);
+}
+template <> __device__ __forceinline__ df64 shfl_down_t<df64>(df64 v, int d) {
+  return df64(__shfl_down_sync(0xffffffffu, v.hi, d), __shfl_down_sync(0xffffffffu, v.lo, d));
+}
+
+// Scatter-add of a warp of the 8 x 4 x 4 brick (lanes: 8 cells along x times 4 along y).  Cells
+// that are neighbours inside the warp share a face of 9 nodes: each lane first folds its x-low
+// face into the x-high face of the lane to its left, then its y-low face into the lane below,
+// both by register shuffles, so a node shared inside the warp is added to memory once; only
+// faces between warps (z) and bricks need atomics on more than one lane (about 14 atomics per
+// cell instead of 27).  Every lane of the warp must call this; inactive lanes pass zeros.
+template <typename T>
+__device__ __forceinline__ void scatter_uniform_warp(typename Store<T>::type* __restrict__ dst, int64_t base,
+                                                     int64_t sx, int64_t sy, uint32_t dmask, T* R, bool active) {
+  const int xl = threadIdx.x & 7, yl = (threadIdx.x >> 3) & 3;
+#pragma unroll
+  for (int bc = 0; bc < 9; ++bc) {
+    const int o = 3 * (bc % 3) + 9 * (bc / 3);
+    const T w = shfl_down_t<T>(R[o], 1);
+    if (xl < 7) R[o + 2] += w;
+  }
+#pragma unroll
+  for (int ac = 0; ac < 9; ++ac) {
+    const int a = ac % 3, o = a + 9 * (ac / 3);
+    const T w = shfl_down_t<T>((a == 0 && xl > 0) ? T(0) : R[o], 8);
+    if (yl < 3) R[o + 6] += w;
+  }
+  if (!active) return;
+  asm volatile("" : "+l"(base), "+l"(sx), "+l"(sy));
+  typename Store<T>::type* __restrict__ d = dst + base;
+#pragma unroll
+  for (int l = 0; l < 27; ++l) {
+    const int a = l % 3, b = (l / 3) % 3, c = l / 9;
+    if ((a == 0 && xl > 0) || (b == 0 && yl > 0) || ((dmask >> l) & 1u)) continue;
+    atomicAdd(d + a + sx * b + sy * c, to_store<T>(R[l]));
+  }
+}
+
 // Octree map: SoA cell map [27][ncp], negative entries -(1 + r) point at constraint row r.
 struct OctGeom {
   const int32_t* __restrict__ cmap;

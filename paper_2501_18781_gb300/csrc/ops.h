@@ -42,6 +42,7 @@ template <typename T> struct OseenArgs {
   const T* mu;      // [27][ncells]
   const T* beta;    // [3][27][ncells]
   T sigma;
+  int qouter;       // 1: Gauss-point loop outside the velocity components (autotuned variant)
 };
 
 // scalar apply: kind, coefficient mode (0 in-kernel, 1 tabulated), convection, transpose
@@ -97,6 +98,7 @@ struct mf_op {
   int block = 128;                // octree cells per block (autotuned: 64 or 128)
   int persistent_blocks = 0;      // > 0: persistent launch with this many blocks per SM (autotuned)
   bool df64_faster = false;       // autotuned: double-float beats the fp64 pipes (used when fp64_arith = 2)
+  int oseen_qouter64 = 0;         // Oseen fp64 kernel variant (autotuned)
   std::string tune_record;        // JSON of the last autotuning
   std::string variant;
 };

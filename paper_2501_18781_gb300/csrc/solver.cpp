@@ -693,7 +693,46 @@ mf_status mf_autotune(mf_op* op, const char* cache_path) {
     MF_TRY(check_fields(op));
     mf_ctx* c = op->ctx;
     const int64_t n = op->n;
-    if (op->p.kind == MF_OP_OSEEN) return MF_OK;  // one variant
+    if (op->p.kind == MF_OP_OSEEN) {
+      // fp64 kernel variant: component loop outside (fewer registers) or Gauss-point loop outside
+      // (fewer fp64 operations, spills)
+      MF_TRY(ensure_tables(op));
+      DevBuf s, d;
+      MF_TRY(s.alloc(sizeof(double) * n));
+      MF_TRY(d.alloc(sizeof(double) * n));
+      MF_TRY(fill_splitmix(c, 7, s.as<double>(), n));
+      cudaEvent_t a0, a1;
+      cudaEventCreate(&a0);
+      cudaEventCreate(&a1);
+      double ms[2] = {1e30, 1e30};
+      for (int v = 0; v < 2; ++v) {
+        op->oseen_qouter64 = v;
+        for (int rep = 0; rep < 4; ++rep) {
+          cudaEventRecord(a0, c->stream);
+          MF_TRY(apply_impl<double>(op, s.as<double>(), d.as<double>(), 1, n, false, PREC_F64));
+          cudaEventRecord(a1, c->stream);
+          MF_CUDA_TRY(cudaEventSynchronize(a1));
+          float t;
+          cudaEventElapsedTime(&t, a0, a1);
+          if (rep > 0) ms[v] = std::min(ms[v], double(t));
+        }
+      }
+      cudaEventDestroy(a0);
+      cudaEventDestroy(a1);
+      op->oseen_qouter64 = ms[1] < ms[0] ? 1 : 0;
+      char buf[256];
+      std::snprintf(buf, sizeof buf, "{\"kind\": %d, \"n\": %lld, \"component_outer_ms\": %.6g, \"qpoint_outer_ms\": %.6g}",
+                    op->p.kind, (long long)n, ms[0], ms[1]);
+      op->tune_record = buf;
+      if (cache_path) {
+        FILE* fp = std::fopen(cache_path, "a");
+        if (fp) {
+          std::fprintf(fp, "%s\n", buf);
+          std::fclose(fp);
+        }
+      }
+      return MF_OK;
+    }
     MF_TRY(ensure_tables(op));
     DevBuf src, dst;
     MF_TRY(src.alloc(sizeof(double) * n));
