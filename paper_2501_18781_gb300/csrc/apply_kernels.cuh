@@ -65,26 +65,29 @@ __device__ __forceinline__ void scatter(const UniformGeom& ug, const OctGeom& og
 template <typename T, int KIND, int MODE, bool BETA, bool TR, bool OCT>
 __device__ __forceinline__ void scalar_cell(const ScalarArgs<typename Store<T>::type>& A, const UniformGeom& ug,
                                             const OctGeom& og, CellLoc L, bool active) {
-  // On uniform meshes all 32 lanes of a warp take part in the warp-level scatter, so a lane
-  // without a cell stays (inactive, contributing zeros) instead of returning.
+  // On uniform meshes all 32 lanes of a warp take part in the warp-level scatter: a lane
+  // without a cell (active = false) stays and contributes zeros; a lane whose cell is in the
+  // mesh but outside the objective box (compute = false) contributes zeros but still writes the
+  // nodes it owns, which may hold its neighbours' folded contributions.
   if (KIND == K_MASS) L.dmask = 0u;  // the plain mass matrix has no Dirichlet rows
   const T h = T(OCT ? L.h : ug.h);
   // every term carries at least one power of h: R = h * (...), with
   // w h^3 m u = h (w (m h^2) u), w h k g = h (w k g), w h^2 beta.g = h (w h beta.g)
   const T mh2 = T(A.mass) * h * h;
+  bool compute = active;
   if (KIND == K_MASS && A.use_box && active) {
     // centre of a uniform cell from its lattice base
     const int64_t kk = L.base / ug.sy, jj = (L.base % ug.sy) / ug.sx, ii = L.base % ug.sx;
     const double cx = A.lo[0] + (double(ii) * 0.5 + 0.5) * L.h, cy = A.lo[1] + (double(jj) * 0.5 + 0.5) * L.h,
                  cz = A.lo[2] + (double(kk) * 0.5 + 0.5) * L.h;
-    if (!(fabs(cx) <= A.box_half && fabs(cy) <= A.box_half && cz >= A.box_zmin)) active = false;
+    if (!(fabs(cx) <= A.box_half && fabs(cy) <= A.box_half && cz >= A.box_zmin)) compute = false;
   }
   if constexpr (OCT) {
-    if (!active) return;
+    if (!compute) return;
   }
   // scalar coefficient (or phi for in-kernel reinit) at the 27 Gauss points
   T C[27];
-  if (active)
+  if (compute)
   if constexpr (KIND == K_HELM || KIND == K_HEAT || KIND == K_REINIT) {
     if constexpr (MODE == 0) {
       gather<T, OCT, false>(ug, og, CellLoc{L.cell, L.base, 0u, L.h}, A.field, C);
@@ -103,7 +106,7 @@ __device__ __forceinline__ void scalar_cell(const ScalarArgs<typename Store<T>::
   }
   for (int r = 0; r < A.nrhs; ++r) {
     T U[27], R[27];
-    if (active) {
+    if (compute) {
       gather<T, OCT, KIND != K_MASS>(ug, og, L, A.src + r * A.ld, U);
       scalar_local<T, KIND, MODE, BETA, TR>(A, L.cell, h, mh2, C, U, R);
     } else {
