@@ -20,6 +20,9 @@ mf_status ensure_tables(mf_op* op);
 int scalar_kind(const mf_op* op);
 double value_coef(const mf_op* op);
 template <typename T> ScalarArgs<T> scalar_args(const mf_op* op, const T* src, T* dst, int nrhs, int64_t ld);
+// small device helpers (solver_kernels.cu)
+template <typename T> mf_status dev_scale_mul(mf_ctx* c, const double* s, const double* v, T* out, int64_t n);
+template <typename T> mf_status dev_scale_mul_back(mf_ctx* c, const double* s, const T* v, double* out, int64_t n);
 
 namespace {
 
@@ -120,7 +123,9 @@ template <typename T> struct Prec {
 
   static mf_status invert_inplace(mf_ctx* c, double* v, int64_t n);
 
-  // lambda_max of D^-1 A (Lanczos on D^-1/2 A D^-1/2), applies in precision T
+  // lambda_max of D^-1 A (Lanczos on D^-1/2 A D^-1/2).  Only a preconditioner parameter (it is
+  // scaled by 1.1), so the operator applies run in fp32 whatever the solve precision; the
+  // Lanczos vectors and scalars are fp64.
   mf_status lanczos(const double* inv64, int steps, double* out) {
     mf_ctx* c = op->ctx;
     const int64_t n = op->n;
@@ -129,7 +134,7 @@ template <typename T> struct Prec {
     MF_TRY(v.alloc(n));
     MF_TRY(vp.alloc(n));
     MF_TRY(w.alloc(n));
-    Vec<T> tv, tw;
+    Vec<float> tv, tw;
     MF_TRY(tv.alloc(n));
     MF_TRY(tw.alloc(n));
     MF_TRY(sqrt_of(c, inv64, s.p, n));
@@ -143,9 +148,9 @@ template <typename T> struct Prec {
     std::vector<double> al, be;
     double beta = 0.0;
     for (int k = 0; k < steps; ++k) {
-      MF_TRY(scale_mul(c, s.p, v.p, tv.p, n));  // tv = s .* v (in T)
-      MF_TRY(apply_impl<T>(op, tv.p, tw.p, 1, n, false));
-      MF_TRY(scale_mul_back(c, s.p, tw.p, w.p, n));  // w = s .* tw
+      MF_TRY(dev_scale_mul<float>(c, s.p, v.p, tv.p, n));  // tv = s .* v (fp32)
+      MF_TRY(apply_impl<float>(op, tv.p, tw.p, 1, n, false));
+      MF_TRY(dev_scale_mul_back<float>(c, s.p, tw.p, w.p, n));  // w = s .* tw
       MF_TRY(axpby<double, double>(c, n, -beta, vp.p, 1.0, w.p));
       MF_TRY(dot<double, double>(c, w.p, v.p, n, ds));
       MF_TRY(sync_copy(c, hs, ds, 1));

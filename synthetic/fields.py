@@ -81,23 +81,34 @@ _WAVES = np.array([[1, 1, 1], [1, 2, 1], [2, 1, 1], [1, 1, 2]], dtype=np.float64
 
 
 def convection_field(x, y, z, seed, lo, hi, beta_max=None):
-    """Divergence-free field beta = curl A of a seeded trigonometric vector potential
-    A_c = sum_m a_cm sin(2 pi k_m . xi + t_cm), xi = (x - lo)/(hi - lo), scaled so that the
-    largest |beta| over the given points equals one (or over ``beta_max`` if given)."""
+    """Divergence-free field beta = curl(b A) of a seeded trigonometric vector potential
+    A_c = sum_m a_cm sin(2 pi k_m . xi + t_cm), xi = (x - lo)/(hi - lo), times the bubble
+    b = sin(pi xi_x) sin(pi xi_y) sin(pi xi_z). The bubble vanishes on every face of the box, so
+    beta . n = 0 there: no flow enters or leaves through any boundary, in particular not through
+    a natural (open) one, where inflow would make the convection form indefinite. The field is
+    scaled so that the largest |beta| over the given points equals one (or over ``beta_max``)."""
     a = uniform_pm1(seed, 12).reshape(3, 4)
     t = 2.0 * np.pi * uniform_01(seed + 1000, 12).reshape(3, 4)
     xi = [(x - lo[0]) / (hi[0] - lo[0]), (y - lo[1]) / (hi[1] - lo[1]), (z - lo[2]) / (hi[2] - lo[2])]
+    s = [np.sin(np.pi * v) for v in xi]
+    c = [np.cos(np.pi * v) for v in xi]
+    b = s[0] * s[1] * s[2]
+    db = [np.pi * c[0] * s[1] * s[2], np.pi * s[0] * c[1] * s[2], np.pi * s[0] * s[1] * c[2]]
+    A = np.zeros((3,) + np.shape(x))
     dA = np.zeros((3, 3) + np.shape(x))  # dA[c][d] = d A_c / d xi_d
     for m in range(4):
         k = _WAVES[m]
         arg = 2.0 * np.pi * (k[0] * xi[0] + k[1] * xi[1] + k[2] * xi[2])
-        for c in range(3):
-            cc = a[c, m] * np.cos(arg + t[c, m]) * 2.0 * np.pi
+        for cc in range(3):
+            A[cc] = A[cc] + a[cc, m] * np.sin(arg + t[cc, m])
+            g = a[cc, m] * np.cos(arg + t[cc, m]) * 2.0 * np.pi
             for d in range(3):
-                dA[c, d] = dA[c, d] + cc * k[d]
-    bx = dA[2, 1] - dA[1, 2]
-    by = dA[0, 2] - dA[2, 0]
-    bz = dA[1, 0] - dA[0, 1]
+                dA[cc, d] = dA[cc, d] + g * k[d]
+    # d(b A_c)/d xi_d = b dA_c/dxi_d + A_c db/dxi_d
+    dbA = [[b * dA[cc, d] + A[cc] * db[d] for d in range(3)] for cc in range(3)]
+    bx = dbA[2][1] - dbA[1][2]
+    by = dbA[0][2] - dbA[2][0]
+    bz = dbA[1][0] - dbA[0][1]
     if beta_max is None:
         beta_max = np.max(np.sqrt(bx * bx + by * by + bz * bz))
     return bx / beta_max, by / beta_max, bz / beta_max
