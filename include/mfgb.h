@@ -164,7 +164,21 @@ mf_status mf_apply_transpose(mf_op* op, const void* src, void* dst, int nrhs, in
 mf_status mf_diagonal(mf_op* op, void* dst, int dtype);
 
 typedef enum { MF_SOLVER_CG = 0, MF_SOLVER_GMRES = 1, MF_SOLVER_DEFECT_CORRECTION = 2 } mf_solver_kind;
-typedef enum { MF_PREC_NONE = 0, MF_PREC_JACOBI = 1, MF_PREC_CHEBYSHEV = 2, MF_PREC_BLOCK_JACOBI = 3 } mf_prec_kind;
+/* MF_PREC_BLOCK_TRIANGULAR (Oseen, GMRES only): right preconditioner built on the saddle-point
+ * block structure [[A_uu, B^T], [B, 0]] of Section 2 (eq. momentum_balance linearised, with the
+ * continuity constraint).  Per call: the pressure part solves S~ x_p = r_p with S~ = B D^-1 B^T
+ * (D = the 3x3 nodal blocks of A_uu, as in block Jacobi) by Jacobi-preconditioned CG to
+ * schur_tol or schur_maxit steps, z_p = -x_p; the velocity part runs velocity_steps GMRES steps
+ * on A_uu z_u = r_u - B^T z_p, right-preconditioned by D^-1.  All operator applications inside
+ * it are fp32; vectors and inner products fp64.  Its inner Krylov solves make it change from
+ * call to call, so the outer solver becomes flexible GMRES (Saad's FGMRES). */
+typedef enum {
+  MF_PREC_NONE = 0,
+  MF_PREC_JACOBI = 1,
+  MF_PREC_CHEBYSHEV = 2,
+  MF_PREC_BLOCK_JACOBI = 3,
+  MF_PREC_BLOCK_TRIANGULAR = 4
+} mf_prec_kind;
 
 typedef struct {
   int solver;          /* mf_solver_kind */
@@ -181,6 +195,9 @@ typedef struct {
   int lanczos_steps;   /* steps of the lambda_max estimate of D^-1 A */
   int fp64_arith;      /* arithmetic of the fp64 operator applies: 0 fp64 pipes, 1 double-float,
                           2 whichever mf_autotune measured faster */
+  int schur_maxit;     /* MF_PREC_BLOCK_TRIANGULAR: cap of the inner Schur CG (<= 0: 30) */
+  int velocity_steps;  /* MF_PREC_BLOCK_TRIANGULAR: GMRES steps on the velocity block, 1..60 (<= 0: 10) */
+  double schur_tol;    /* MF_PREC_BLOCK_TRIANGULAR: relative tolerance of the inner Schur CG (<= 0: 0.1) */
 } mf_solver_params;
 
 typedef struct {

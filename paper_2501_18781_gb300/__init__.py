@@ -11,7 +11,7 @@ from ._lib import (MF_F64, MF_F32, MF_OP_HELMHOLTZ, MF_OP_HEAT, MF_OP_OSEEN, MF_
                    MF_HEAVISIDE_TANH, MF_HEAVISIDE_SINE, MF_COEF_INKERNEL, MF_COEF_QPOINT,
                    MF_FIELD_PHI, MF_FIELD_T_PREV, MF_FIELD_BETA, MF_FIELD_K_QPOINT,
                    MF_SOLVER_CG, MF_SOLVER_GMRES, MF_SOLVER_DEFECT_CORRECTION,
-                   MF_PREC_NONE, MF_PREC_JACOBI, MF_PREC_CHEBYSHEV, MF_PREC_BLOCK_JACOBI,
+                   MF_PREC_NONE, MF_PREC_JACOBI, MF_PREC_CHEBYSHEV, MF_PREC_BLOCK_JACOBI, MF_PREC_BLOCK_TRIANGULAR,
                    MFError, check)
 
 __all__ = ["Context", "Mesh", "DofMap", "Operator", "MFError", "build_library", "load_library"]
@@ -156,12 +156,13 @@ class DofMap:
 
 def solver_params(solver="cg", precond="jacobi", tol=1e-10, maxit=5000, restart=50, cheby_degree=4,
                   inner_tol=1e-4, inner_maxit=100, use_graph=False, cheby_ratio=30.0, lanczos_steps=20,
-                  fp64_arith="f64"):
+                  fp64_arith="f64", schur_tol=0.1, schur_maxit=30, velocity_steps=10):
     s = _lib.SolverParams()
     s.fp64_arith = {"f64": 0, "df64": 1, "auto": 2}[fp64_arith]
     s.solver = {"cg": MF_SOLVER_CG, "gmres": MF_SOLVER_GMRES, "defect_correction": MF_SOLVER_DEFECT_CORRECTION}[solver]
     s.precond = {"none": MF_PREC_NONE, "jacobi": MF_PREC_JACOBI, "chebyshev": MF_PREC_CHEBYSHEV,
-                 "block_jacobi": MF_PREC_BLOCK_JACOBI}[precond]
+                 "block_jacobi": MF_PREC_BLOCK_JACOBI, "block_triangular": MF_PREC_BLOCK_TRIANGULAR}[precond]
+    s.schur_tol, s.schur_maxit, s.velocity_steps = schur_tol, schur_maxit, velocity_steps
     s.inner_dtype = MF_F32
     s.restart, s.cheby_degree, s.maxit, s.inner_maxit = restart, cheby_degree, maxit, inner_maxit
     s.use_graph = 1 if use_graph else 0

@@ -12,7 +12,7 @@ MF_HEAVISIDE_TANH, MF_HEAVISIDE_SINE = 0, 1
 MF_COEF_INKERNEL, MF_COEF_QPOINT = 0, 1
 MF_FIELD_PHI, MF_FIELD_T_PREV, MF_FIELD_BETA, MF_FIELD_K_QPOINT = 0, 1, 2, 3
 MF_SOLVER_CG, MF_SOLVER_GMRES, MF_SOLVER_DEFECT_CORRECTION = 0, 1, 2
-MF_PREC_NONE, MF_PREC_JACOBI, MF_PREC_CHEBYSHEV, MF_PREC_BLOCK_JACOBI = 0, 1, 2, 3
+MF_PREC_NONE, MF_PREC_JACOBI, MF_PREC_CHEBYSHEV, MF_PREC_BLOCK_JACOBI, MF_PREC_BLOCK_TRIANGULAR = 0, 1, 2, 3, 4
 
 STATUS_NAMES = {0: "MF_OK", -1: "MF_EINVAL", -2: "MF_ENOMEM", -3: "MF_ECUDA", -4: "MF_ENOTCONV",
                 -5: "MF_ETIMEOUT", -6: "MF_EUNSUPPORTED"}
@@ -30,7 +30,8 @@ class SolverParams(C.Structure):
     _fields_ = [("solver", C.c_int), ("precond", C.c_int), ("inner_dtype", C.c_int), ("restart", C.c_int),
                 ("cheby_degree", C.c_int), ("maxit", C.c_int), ("inner_maxit", C.c_int), ("use_graph", C.c_int),
                 ("tol", C.c_double), ("inner_tol", C.c_double), ("cheby_ratio", C.c_double),
-                ("lanczos_steps", C.c_int), ("fp64_arith", C.c_int)]
+                ("lanczos_steps", C.c_int), ("fp64_arith", C.c_int), ("schur_maxit", C.c_int),
+                ("velocity_steps", C.c_int), ("schur_tol", C.c_double)]
 
 
 class SolveInfo(C.Structure):

@@ -69,6 +69,7 @@ constexpr int kScalarsResid = 1024;  // 2 x 64
 constexpr int kScalarsGmres = 1536;  // 2 (m + 1) <= 128
 constexpr int kScalarsScale = 2048;  // 64
 constexpr int kScalarsHeat = 2560;   // 8
+constexpr int kScalarsTri = 3072;    // Oseen block-triangular inner solves: 2 (k + 1) + 8 <= 512
 constexpr int kScalarsTotal = 4096;
 }  // namespace mf
 

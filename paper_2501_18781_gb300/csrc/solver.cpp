@@ -5,6 +5,8 @@
 #include <chrono>
 #include <cmath>
 #include <cstdio>
+#include <memory>
+#include <type_traits>
 #include <vector>
 
 #include "ops.h"
@@ -71,8 +73,196 @@ double tridiag_max_eig(const std::vector<double>& a, const std::vector<double>& 
   return hi;
 }
 
-// Preconditioner in precision T for nrhs vectors: none, Jacobi, Chebyshev (on D^-1 A), or
-// the Oseen block Jacobi.
+// Givens rotation of column j of the (m+1) x m Hessenberg H (row-major, m columns) with the
+// previous rotations, then the new rotation that zeroes H[j+1][j]; updates g.
+void givens_column(std::vector<double>& H, int m, int j, std::vector<double>& cs, std::vector<double>& sn,
+                   std::vector<double>& g) {
+  for (int i = 0; i < j; ++i) {
+    const double tmp = cs[i] * H[i * m + j] + sn[i] * H[(i + 1) * m + j];
+    H[(i + 1) * m + j] = -sn[i] * H[i * m + j] + cs[i] * H[(i + 1) * m + j];
+    H[i * m + j] = tmp;
+  }
+  const double den = std::hypot(H[j * m + j], H[(j + 1) * m + j]);
+  cs[j] = den > 0 ? H[j * m + j] / den : 1.0;
+  sn[j] = den > 0 ? H[(j + 1) * m + j] / den : 0.0;
+  H[j * m + j] = den;
+  H[(j + 1) * m + j] = 0.0;
+  g[j + 1] = -sn[j] * g[j];
+  g[j] = cs[j] * g[j];
+}
+
+// y = R^-1 g for the leading j x j upper triangle of H (m columns)
+void back_substitute(const std::vector<double>& H, int m, int j, const std::vector<double>& g, std::vector<double>& y) {
+  for (int i = j - 1; i >= 0; --i) {
+    double s = g[i];
+    for (int k = i + 1; k < j; ++k) s -= H[i * m + k] * y[k];
+    y[i] = H[i * m + i] != 0.0 ? s / H[i * m + i] : 0.0;
+  }
+}
+
+// Block upper-triangular preconditioner of the Oseen saddle-point system [[A, B^T], [B, 0]]:
+//   P = [[A, B^T], [0, -S]],  P^-1 r:  z_p = -S^-1 r_p,  z_u = A^-1 (r_u - B^T z_p),
+// with S ~ S~ = B D^-1 B^T (D: the 3x3 nodal blocks of A) solved by Jacobi-CG (Jacobi from the
+// pressure scaling of the block-Jacobi setup) and A^-1 by a few D^-1-preconditioned GMRES
+// steps.  Every operator application here is an fp32 apply of the whole Oseen operator on a
+// vector whose other block is zero; B^T p is the velocity block of A [0; p], B u the pressure
+// block of A [u; 0].  Vectors and inner products stay fp64.
+struct OseenBlockTri {
+  mf_op* op = nullptr;
+  int64_t n = 0, nu = 0, nu3 = 0, np = 0;
+  int ku = 10, smax = 30;
+  double stol = 0.1;
+  Vec<float> f_in, f_out;
+  Vec<double> V, t, w, xp, rp, zp, pp, sp;
+  int64_t applies = 0;
+
+  mf_status setup(mf_op* o, int velocity_steps, int schur_maxit, double schur_tol) {
+    op = o;
+    n = op->n;
+    nu = op->map[0]->n_dofs;
+    nu3 = 3 * nu;
+    np = op->map[1]->n_dofs;
+    ku = velocity_steps > 0 ? velocity_steps : 10;
+    if (ku > 60) return fail(MF_EINVAL, "velocity_steps must be at most 60");
+    smax = schur_maxit > 0 ? schur_maxit : 30;
+    stol = schur_tol > 0 ? schur_tol : 0.1;
+    MF_TRY(diag64(op, nullptr));  // 3x3 block inverses and the pressure scaling
+    MF_TRY(f_in.alloc(n));
+    MF_TRY(f_out.alloc(n));
+    MF_TRY(V.alloc(n * (ku + 1)));
+    MF_TRY(t.alloc(n));
+    MF_TRY(w.alloc(n));
+    for (Vec<double>* v : {&xp, &rp, &zp, &pp, &sp}) MF_TRY(v->alloc(np));
+    return MF_OK;
+  }
+
+  const double* blk() const { return op->blk64.as<double>(); }
+  const double* pinv() const { return op->pdiag64.as<double>(); }
+
+  // out = A in (whole operator, fp32 arithmetic, fp64 vectors)
+  mf_status apply32(const double* in, double* out) {
+    mf_ctx* c = op->ctx;
+    MF_TRY((convert<double, float>(c, n, in, f_in.p)));
+    MF_TRY(apply_impl<float>(op, f_in.p, f_out.p, 1, n, false));
+    ++applies;
+    return convert<float, double>(c, n, f_out.p, out);
+  }
+
+  // out_p = S~ p = B D^-1 B^T p
+  mf_status schur(const double* p, double* out_p) {
+    mf_ctx* c = op->ctx;
+    MF_CUDA_TRY(cudaMemsetAsync(t.p, 0, sizeof(double) * nu3, c->stream));
+    MF_CUDA_TRY(cudaMemcpyAsync(t.p + nu3, p, sizeof(double) * np, cudaMemcpyDeviceToDevice, c->stream));
+    MF_TRY(apply32(t.p, w.p));  // w_u = B^T p (Dirichlet rows: 0), w_p = 0
+    MF_CUDA_TRY(cudaMemsetAsync(w.p + nu3, 0, sizeof(double) * np, c->stream));
+    MF_TRY(block_jacobi<double>(c, nu, np, blk(), pinv(), w.p, t.p));  // t = [D^-1 w_u; 0]
+    MF_TRY(apply32(t.p, w.p));  // w_p = B D^-1 B^T p
+    MF_CUDA_TRY(cudaMemcpyAsync(out_p, w.p + nu3, sizeof(double) * np, cudaMemcpyDeviceToDevice, c->stream));
+    return MF_OK;
+  }
+
+  // xp = S~^-1 r (Jacobi-PCG from 0 to stol relative or smax steps); r is not modified
+  mf_status schur_solve(const double* r) {
+    mf_ctx* c = op->ctx;
+    double* ds = c->scalars.as<double>() + kScalarsTri;
+    double* hs = c->host_scalars + kScalarsTri;
+    MF_CUDA_TRY(cudaMemsetAsync(xp.p, 0, sizeof(double) * np, c->stream));
+    MF_CUDA_TRY(cudaMemcpyAsync(rp.p, r, sizeof(double) * np, cudaMemcpyDeviceToDevice, c->stream));
+    MF_TRY(pointwise_mul<double>(c, np, pinv(), rp.p, zp.p));
+    MF_CUDA_TRY(cudaMemcpyAsync(pp.p, zp.p, sizeof(double) * np, cudaMemcpyDeviceToDevice, c->stream));
+    MF_TRY(norm2_sq(c, rp.p, np, ds));
+    MF_TRY((dot<double, double>(c, rp.p, zp.p, np, ds + 1)));
+    MF_TRY(sync_copy(c, hs, ds, 2));
+    const double r0 = std::sqrt(hs[0]);
+    double rz = hs[1];
+    if (r0 == 0.0) return MF_OK;
+    for (int k = 0; k < smax; ++k) {
+      MF_TRY(schur(pp.p, sp.p));
+      MF_TRY((dot<double, double>(c, pp.p, sp.p, np, ds)));
+      MF_TRY(sync_copy(c, hs, ds, 1));
+      if (!(hs[0] > 0.0)) break;  // S~ not positive along p: keep the iterate
+      const double alpha = rz / hs[0];
+      MF_TRY((axpby<double, double>(c, np, alpha, pp.p, 1.0, xp.p)));
+      MF_TRY((axpby<double, double>(c, np, -alpha, sp.p, 1.0, rp.p)));
+      MF_TRY(pointwise_mul<double>(c, np, pinv(), rp.p, zp.p));
+      MF_TRY(norm2_sq(c, rp.p, np, ds));
+      MF_TRY((dot<double, double>(c, rp.p, zp.p, np, ds + 1)));
+      MF_TRY(sync_copy(c, hs, ds, 2));
+      if (std::sqrt(hs[0]) <= stol * r0) break;
+      const double beta = hs[1] / rz;
+      rz = hs[1];
+      MF_TRY((axpby<double, double>(c, np, 1.0, zp.p, beta, pp.p)));
+    }
+    return MF_OK;
+  }
+
+  // z_u = A^-1 rhs_u by ku steps of GMRES from 0, right-preconditioned by D^-1.  rhs is a full
+  // length vector whose pressure block is zero and is read only before the first step (it may
+  // be w); z's pressure block is left untouched.
+  mf_status velocity_solve(const double* rhs, double* z) {
+    mf_ctx* c = op->ctx;
+    double* ds = c->scalars.as<double>() + kScalarsTri;
+    double* hs = c->host_scalars + kScalarsTri;
+    const int m = ku;
+    MF_TRY(norm2_sq(c, rhs, nu3, ds));
+    MF_TRY(sync_copy(c, hs, ds, 1));
+    const double beta = std::sqrt(hs[0]);
+    if (beta == 0.0) {
+      MF_CUDA_TRY(cudaMemsetAsync(z, 0, sizeof(double) * nu3, c->stream));
+      return MF_OK;
+    }
+    MF_TRY((axpby<double, double>(c, n, 1.0 / beta, rhs, 0.0, V.p)));
+    std::vector<double> H((m + 1) * m, 0.0), cs(m), sn(m), g(m + 1, 0.0), y(m);
+    g[0] = beta;
+    int j = 0;
+    for (; j < m; ++j) {
+      double* vj1 = V.p + (j + 1) * n;
+      MF_TRY(block_jacobi<double>(c, nu, np, blk(), pinv(), V.p + j * n, t.p));  // pressure block stays 0
+      MF_TRY(apply32(t.p, vj1));
+      MF_CUDA_TRY(cudaMemsetAsync(vj1 + nu3, 0, sizeof(double) * np, c->stream));
+      MF_TRY(multidot(c, V.p, n, j + 1, vj1, nu3, ds));
+      MF_TRY(multiaxpy(c, V.p, n, j + 1, ds, -1.0, vj1, nu3));
+      MF_TRY(multidot(c, V.p, n, j + 1, vj1, nu3, ds + (m + 1)));
+      MF_TRY(multiaxpy(c, V.p, n, j + 1, ds + (m + 1), -1.0, vj1, nu3));
+      MF_TRY(norm2_sq(c, vj1, nu3, ds + 2 * (m + 1)));
+      MF_TRY(sync_copy(c, hs, ds, 2 * (m + 1) + 1));
+      for (int i = 0; i <= j; ++i) H[i * m + j] = hs[i] + hs[(m + 1) + i];
+      const double hn = std::sqrt(hs[2 * (m + 1)]);
+      H[(j + 1) * m + j] = hn;
+      givens_column(H, m, j, cs, sn, g);
+      if (hn == 0.0) {
+        ++j;
+        break;
+      }
+      MF_TRY((axpby<double, double>(c, nu3, 1.0 / hn, vj1, 0.0, vj1)));
+    }
+    back_substitute(H, m, j, g, y);
+    for (int i = 0; i < j; ++i) hs[i] = y[i];
+    MF_CUDA_TRY(cudaMemcpyAsync(ds, hs, sizeof(double) * j, cudaMemcpyHostToDevice, c->stream));
+    MF_CUDA_TRY(cudaMemsetAsync(w.p, 0, sizeof(double) * n, c->stream));
+    MF_TRY(multiaxpy(c, V.p, n, j, ds, 1.0, w.p, nu3));
+    MF_TRY(block_jacobi<double>(c, nu, np, blk(), pinv(), w.p, t.p));
+    MF_CUDA_TRY(cudaMemcpyAsync(z, t.p, sizeof(double) * nu3, cudaMemcpyDeviceToDevice, c->stream));
+    return MF_OK;
+  }
+
+  // z = P^-1 r (fp64 vectors of length n)
+  mf_status apply(const double* r, double* z) {
+    mf_ctx* c = op->ctx;
+    MF_TRY(schur_solve(r + nu3));
+    // z_p = -x_p; velocity right-hand side r_u - B^T z_p = r_u + B^T x_p
+    MF_TRY((axpby<double, double>(c, np, -1.0, xp.p, 0.0, z + nu3)));
+    MF_CUDA_TRY(cudaMemsetAsync(t.p, 0, sizeof(double) * nu3, c->stream));
+    MF_CUDA_TRY(cudaMemcpyAsync(t.p + nu3, xp.p, sizeof(double) * np, cudaMemcpyDeviceToDevice, c->stream));
+    MF_TRY(apply32(t.p, w.p));
+    MF_TRY((axpby<double, double>(c, nu3, 1.0, r, 1.0, w.p)));
+    MF_CUDA_TRY(cudaMemsetAsync(w.p + nu3, 0, sizeof(double) * np, c->stream));
+    return velocity_solve(w.p, z);
+  }
+};
+
+// Preconditioner in precision T for nrhs vectors: none, Jacobi, Chebyshev (on D^-1 A), the
+// Oseen block Jacobi, or (fp64 only) the Oseen block-triangular preconditioner.
 template <typename T> struct Prec {
   mf_op* op = nullptr;
   int kind = MF_PREC_NONE;
@@ -80,6 +270,10 @@ template <typename T> struct Prec {
   double lmin = 0, lmax = 0;
   Vec<T> dinv, res, d, Ad;
   int nrhs = 1;
+  // block-triangular parameters (set before setup) and state
+  int tri_velocity_steps = 10, tri_schur_maxit = 30;
+  double tri_schur_tol = 0.1;
+  std::unique_ptr<OseenBlockTri> tri;
 
   mf_status setup(mf_op* o, int k, int deg, double ratio, int lanczos_steps, int nr) {
     op = o;
@@ -92,7 +286,14 @@ template <typename T> struct Prec {
       if (op->p.kind != MF_OP_OSEEN) return fail(MF_EINVAL, "block Jacobi is for the Oseen operator");
       return diag64(op, nullptr);
     }
-    if (op->p.kind == MF_OP_OSEEN) return fail(MF_EUNSUPPORTED, "Oseen: use block Jacobi");
+    if (kind == MF_PREC_BLOCK_TRIANGULAR) {
+      if (op->p.kind != MF_OP_OSEEN) return fail(MF_EINVAL, "the block-triangular preconditioner is for the Oseen operator");
+      if (!std::is_same<T, double>::value || nrhs != 1)
+        return fail(MF_EUNSUPPORTED, "the block-triangular preconditioner runs inside fp64 GMRES");
+      tri = std::make_unique<OseenBlockTri>();
+      return tri->setup(op, tri_velocity_steps, tri_schur_maxit, tri_schur_tol);
+    }
+    if (op->p.kind == MF_OP_OSEEN) return fail(MF_EUNSUPPORTED, "Oseen: use block Jacobi or block triangular");
     double* d64;
     MF_TRY(diag64(op, &d64));
     Vec<double> inv64;
@@ -193,6 +394,9 @@ template <typename T> struct Prec {
           MF_TRY(block_jacobi<T>(c, nu, np, op->blk64.as<double>(), op->pdiag64.as<double>(), r + k * n, z + k * n));
         return MF_OK;
       }
+      case MF_PREC_BLOCK_TRIANGULAR:
+        if constexpr (std::is_same<T, double>::value) return tri->apply(r, z);
+        return fail(MF_EUNSUPPORTED, "block-triangular preconditioner in fp32");
       case MF_PREC_CHEBYSHEV: {
         const double theta = 0.5 * (lmax + lmin), delta = 0.5 * (lmax - lmin), sigma = theta / delta;
         double rho = 1.0 / sigma;
@@ -393,10 +597,15 @@ mf_status gmres(mf_op* op, Prec<double>& P, const double* b, double* x, int m, d
                 int* iters, double* relres) {
   mf_ctx* c = op->ctx;
   const int64_t n = op->n;
-  Vec<double> V, t, r;
+  // a preconditioner that changes from call to call (inner Krylov solves) needs the flexible
+  // variant (FGMRES): keep Z_j = P^-1 V_j and update x with Z y
+  const bool flexible = P.kind == MF_PREC_BLOCK_TRIANGULAR;
+  if (flexible && transpose) return fail(MF_EUNSUPPORTED, "block-triangular preconditioner: forward operator only");
+  Vec<double> V, t, r, Z;
   MF_TRY(V.alloc(n * (m + 1)));
   MF_TRY(t.alloc(n));
   MF_TRY(r.alloc(n));
+  if (flexible) MF_TRY(Z.alloc(n * m));
   double* dh = c->scalars.as<double>() + kScalarsGmres;  // room for 2 (m+1) <= 128 values
   if (2 * (m + 1) > 128) return fail(MF_EINVAL, "GMRES restart too long (max 63)");
   double* hh = c->host_scalars + kScalarsGmres;
@@ -421,8 +630,9 @@ mf_status gmres(mf_op* op, Prec<double>& P, const double* b, double* x, int m, d
     bool conv = false;
     for (; j < m && it < maxit; ++j) {
       double* w = V.p + (j + 1) * n;
-      MF_TRY(P.apply(V.p + j * n, t.p));
-      MF_TRY(apply_impl<double>(op, t.p, w, 1, n, transpose));
+      double* zj = flexible ? Z.p + j * n : t.p;
+      MF_TRY(P.apply(V.p + j * n, zj));
+      MF_TRY(apply_impl<double>(op, zj, w, 1, n, transpose));
       MF_TRY(multidot(c, V.p, n, j + 1, w, n, dh));
       MF_TRY(multiaxpy(c, V.p, n, j + 1, dh, -1.0, w, n));
       MF_TRY(multidot(c, V.p, n, j + 1, w, n, dh + (m + 1)));
@@ -433,18 +643,7 @@ mf_status gmres(mf_op* op, Prec<double>& P, const double* b, double* x, int m, d
       double hn = std::sqrt(hh[2 * (m + 1) - 1]);
       H[(j + 1) * m + j] = hn;
       if (hn > 0) MF_TRY(axpby<double, double>(c, n, 1.0 / hn, w, 0.0, w));
-      for (int i = 0; i < j; ++i) {
-        double tmp = cs[i] * H[i * m + j] + sn[i] * H[(i + 1) * m + j];
-        H[(i + 1) * m + j] = -sn[i] * H[i * m + j] + cs[i] * H[(i + 1) * m + j];
-        H[i * m + j] = tmp;
-      }
-      double den = std::hypot(H[j * m + j], H[(j + 1) * m + j]);
-      cs[j] = H[j * m + j] / den;
-      sn[j] = H[(j + 1) * m + j] / den;
-      H[j * m + j] = den;
-      H[(j + 1) * m + j] = 0.0;
-      g[j + 1] = -sn[j] * g[j];
-      g[j] = cs[j] * g[j];
+      givens_column(H, m, j, cs, sn, g);
       ++it;
       if (std::fabs(g[j + 1]) <= tol * bn || hn == 0.0) {
         ++j;
@@ -452,18 +651,18 @@ mf_status gmres(mf_op* op, Prec<double>& P, const double* b, double* x, int m, d
         break;
       }
     }
-    // y = H^-1 g (upper triangular), x += M^-1 V y
-    for (int i = j - 1; i >= 0; --i) {
-      double s = g[i];
-      for (int k = i + 1; k < j; ++k) s -= H[i * m + k] * y[k];
-      y[i] = s / H[i * m + i];
-    }
+    // y = H^-1 g (upper triangular), x += M^-1 V y  (flexible: x += Z y)
+    back_substitute(H, m, j, g, y);
     for (int i = 0; i < j; ++i) hh[i] = y[i];
     MF_CUDA_TRY(cudaMemcpyAsync(dh, hh, sizeof(double) * j, cudaMemcpyHostToDevice, c->stream));
-    MF_CUDA_TRY(cudaMemsetAsync(r.p, 0, sizeof(double) * n, c->stream));
-    MF_TRY(multiaxpy(c, V.p, n, j, dh, 1.0, r.p, n));
-    MF_TRY(P.apply(r.p, t.p));
-    MF_TRY(axpby<double, double>(c, n, 1.0, t.p, 1.0, x));
+    if (flexible) {
+      MF_TRY(multiaxpy(c, Z.p, n, j, dh, 1.0, x, n));
+    } else {
+      MF_CUDA_TRY(cudaMemsetAsync(r.p, 0, sizeof(double) * n, c->stream));
+      MF_TRY(multiaxpy(c, V.p, n, j, dh, 1.0, r.p, n));
+      MF_TRY(P.apply(r.p, t.p));
+      MF_TRY(axpby<double, double>(c, n, 1.0, t.p, 1.0, x));
+    }
     // true residual
     MF_TRY(apply_impl<double>(op, x, r.p, 1, n, transpose));
     MF_TRY(axpby<double, double>(c, n, 1.0, b, -1.0, r.p));
@@ -502,6 +701,8 @@ mf_status solve_impl(mf_op* op, const mf_solver_params* sp, const double* b, dou
   const double ratio = sp->cheby_ratio > 0 ? sp->cheby_ratio : 30.0;
   const int deg = sp->cheby_degree > 0 ? sp->cheby_degree : 4;
   std::vector<double> rel;
+  if (sp->precond == MF_PREC_BLOCK_TRIANGULAR && sp->solver != MF_SOLVER_GMRES)
+    return fail(MF_EINVAL, "the block-triangular preconditioner needs the GMRES solver");
   if (sp->solver == MF_SOLVER_CG) {
     if (transpose && op->p.kind == MF_OP_HEAT && op->beta) return fail(MF_EINVAL, "CG on a nonsymmetric operator");
     Prec<double> P;
@@ -534,6 +735,9 @@ mf_status solve_impl(mf_op* op, const mf_solver_params* sp, const double* b, dou
     inf.iterations = total;
   } else if (sp->solver == MF_SOLVER_GMRES) {
     Prec<double> P;
+    P.tri_velocity_steps = sp->velocity_steps;
+    P.tri_schur_maxit = sp->schur_maxit;
+    P.tri_schur_tol = sp->schur_tol;
     MF_TRY(P.setup(op, sp->precond, deg, ratio, lsteps, 1));
     inf.lambda_max = P.lmax;
     const int m = sp->restart > 0 ? sp->restart : 50;

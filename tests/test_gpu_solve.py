@@ -76,6 +76,25 @@ def test_gmres_oseen_block_jacobi(ctx):
     solve_and_check(P, b, solver="gmres", precond="block_jacobi", restart=50, maxit=20000)
 
 
+@pytest.mark.parametrize("n", [4, 7])
+def test_fgmres_oseen_block_triangular(ctx, n):
+    P = oseen(n, ctx)
+    b = syn.uniform_pm1(2, P["n"])
+    mask = np.concatenate([np.tile(P["dmu"].dirichlet, 3), np.zeros(P["dmp"].n_dofs, bool)])
+    b[mask] = 0.0
+    info = solve_and_check(P, b, solver="gmres", precond="block_triangular", restart=50, maxit=400)
+    # the inner velocity GMRES and Schur CG make the outer iteration count nearly mesh independent
+    assert info["iterations"] <= 60, info
+
+
+def test_block_triangular_needs_gmres(ctx):
+    from paper_2501_18781_gb300._lib import MFError
+    P = oseen(3, ctx)
+    b = torch.ones(P["n"], dtype=torch.float64, device="cuda")
+    with pytest.raises(MFError):
+        P["op"].solve(b, solver="cg", precond="block_triangular")
+
+
 def test_defect_correction_mixed_precision_heat(ctx):
     P = heat(10, ctx)
     b = syn.uniform_pm1(4, P["n"])
