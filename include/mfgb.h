@@ -160,6 +160,19 @@ mf_status mf_operator_set_field(mf_op* op, int field, const void* dev_ptr, int d
 mf_status mf_apply(mf_op* op, const void* src, void* dst, int nrhs, int64_t ld, int dtype);
 /* dst = A^T src (Helmholtz, heat with convection, reinit).  Asynchronous. */
 mf_status mf_apply_transpose(mf_op* op, const void* src, void* dst, int nrhs, int64_t ld, int dtype);
+/* The coupling blocks of the Oseen operator on their own: the pressure-gradient term of the
+ * momentum balance and the continuity constraint (Section 2, eq. momentum_balance with
+ * div u = 0), in the weak form and quadrature of Appendix B, (B u, q) = -int q div u:
+ *   which = MF_COUPLING_GRAD (0): dst = B^T src; src = a pressure vector (n_p values), dst =
+ *           the three velocity blocks (3 n_u values), 0 in Dirichlet rows;
+ *   which = MF_COUPLING_DIV (1): dst = B src; src = the three velocity blocks (Dirichlet values
+ *           read as 0), dst = a pressure vector.
+ * These are the blocks of A [0; p] and A [u; 0] that mf_apply computes together with A_uu.
+ * Device vectors of dtype MF_F64 or MF_F32; dst is overwritten.  MF_EINVAL for other
+ * operator kinds or an unknown `which`.  Asynchronous. */
+enum { MF_COUPLING_GRAD = 0, MF_COUPLING_DIV = 1 };
+mf_status mf_oseen_coupling(mf_op* op, int which, const void* src, void* dst, int dtype);
+
 /* dst = diag(A) (Dirichlet rows 1).  Asynchronous. */
 mf_status mf_diagonal(mf_op* op, void* dst, int dtype);
 
@@ -209,8 +222,11 @@ typedef struct {
 } mf_solve_info;
 
 /* Inner products of the Krylov solvers (Appendix B: CG / GMRES): out[k] = sum_i x[k ld + i]
- * y[k ld + i] for k < nvec (1 <= nvec <= 64), device vectors of dtype MF_F64 or MF_F32, fp64
- * accumulation, out a device array of nvec doubles.  Partial sums go to the context's
+ * y[k ld + i] for k < nvec (1 <= nvec <= 64), device vectors of dtype MF_F64 or MF_F32, out a
+ * device array of nvec doubles.  MF_F64: fp64 accumulation.  MF_F32: each thread carries its
+ * products and sums as unevaluated pairs of floats (the compensated dot product of Ogita, Rump
+ * and Oishi, as accurate as evaluation in twice the fp32 precision; fp64 conversions would
+ * bound the kernel by the fp64 rate instead of HBM), partials are combined in fp64.  Partial sums go to the context's
  * reduction workspace (allocated once with the context) over a fixed grid and are summed in a
  * fixed order, so the result is bit-reproducible.  Asynchronous. */
 mf_status mf_dot(mf_ctx* ctx, const void* x, const void* y, int64_t n, int64_t ld, int nvec, int dtype,

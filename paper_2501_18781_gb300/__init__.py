@@ -228,6 +228,17 @@ class Operator:
         return x, {"status": st, "iterations": info.iterations, "outer_iterations": info.outer_iterations,
                    "rel_residual": info.rel_residual, "lambda_max": info.lambda_max, "seconds": info.seconds}
 
+    def coupling(self, which, src):
+        """Oseen coupling blocks alone: which="grad" gives B^T p (velocity blocks) from a pressure
+        vector, which="div" gives B u (pressure block) from the velocity blocks."""
+        import torch
+        nu, npr = self.maps[0].n_dofs, self.maps[1].n_dofs
+        w = {"grad": 0, "div": 1}[which]
+        src = src.contiguous()
+        dst = torch.empty(3 * nu if w == 0 else npr, dtype=src.dtype, device=src.device)
+        check(_lib.load().mf_oseen_coupling(self.h, w, _ptr(src), _ptr(dst), _dtype_code(src)))
+        return dst
+
     def laser_load(self, power, radius, x0, y0, absorptivity, derivatives=False):
         import torch
         lz = _lib.Laser(power, radius, x0, y0, absorptivity)

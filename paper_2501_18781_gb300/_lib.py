@@ -68,6 +68,7 @@ SIGNATURES = {
     "mf_operator_set_field": (C.c_int, [P, C.c_int, P, C.c_int, I64]),
     "mf_apply": (C.c_int, [P, P, P, C.c_int, I64, C.c_int]),
     "mf_apply_transpose": (C.c_int, [P, P, P, C.c_int, I64, C.c_int]),
+    "mf_oseen_coupling": (C.c_int, [P, C.c_int, P, P, C.c_int]),
     "mf_diagonal": (C.c_int, [P, P, C.c_int]),
     "mf_dot": (C.c_int, [P, P, P, I64, I64, C.c_int, C.c_int, P]),
     "mf_dot_noalloc": (C.c_int, [P, P, I64, I64, C.c_int, C.c_int, P, P]),

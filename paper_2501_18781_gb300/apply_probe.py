@@ -3,6 +3,7 @@
     python -m paper_2501_18781_gb300.apply_probe heat [n] [f32|f64|df64] [inkernel|tabulated]
     python -m paper_2501_18781_gb300.apply_probe oseen [n] [f32|f64|df64]
     python -m paper_2501_18781_gb300.apply_probe reinit [base] [levels] [f32|f64|df64] [nrhs]
+    python -m paper_2501_18781_gb300.apply_probe oseen_solve [n] [maxit]
 
 Inputs come from the seeded generators in ``synthetic``; every apply runs in libmfgb.
 """
@@ -46,9 +47,9 @@ def main(argv):
                       coef_mode=mode)
         op.set_field("t_prev", torch.tensor(T, device="cuda"))
         _apply(op, m.n_dofs, prec)
-    elif kind == "oseen":
+    elif kind in ("oseen", "oseen_solve"):
         n = int(argv[1]) if len(argv) > 1 else 64
-        prec = argv[2] if len(argv) > 2 else "f64"
+        prec = argv[2] if (len(argv) > 2 and kind == "oseen") else "f64"
         wl = syn.scaled(syn.OSEEN_INTERFACE, n)
         p = wl.params
         mesh = Mesh.uniform(ctx, n, wl.lo, wl.hi)
@@ -62,7 +63,19 @@ def main(argv):
         op.set_field("phi", torch.tensor(phi, device="cuda"))
         op.set_field("beta", torch.tensor(beta.ravel(), device="cuda"))
         op.autotune()
-        _apply(op, op.n, prec)
+        if kind == "oseen":
+            _apply(op, op.n, prec)
+        else:
+            # flexible GMRES with the block-triangular preconditioner, capped at maxit iterations
+            maxit = int(argv[2]) if len(argv) > 2 else 400
+            b = syn.uniform_pm1(1, op.n)
+            d = mu.export(cell_map=False, constraints=False, coords=False)["dirichlet"]
+            b[np.concatenate([np.tile(d, 3), np.zeros(mp.n_dofs, bool)])] = 0
+            bt = torch.tensor(b, device="cuda")
+            for _ in range(2):
+                _, info = op.solve(bt, solver="gmres", precond="block_triangular", maxit=maxit, tol=1e-10)
+            torch.cuda.synchronize()
+            print(op.variant, n, info)
     elif kind == "reinit":
         base = int(argv[1]) if len(argv) > 1 else 16
         levels = int(argv[2]) if len(argv) > 2 else 3

@@ -522,6 +522,18 @@ mf_status apply_impl(mf_op* op, const T* src, T* dst, int nrhs, int64_t ld, bool
   return MF_OK;
 }
 template mf_status apply_impl<double>(mf_op*, const double*, double*, int, int64_t, bool, int);
+
+// B^T p (which 0, into the three velocity blocks) or B u (which 1, into the pressure block)
+template <typename T> mf_status oseen_coupling(mf_op* op, int which, const T* src, T* dst) {
+  if (op->p.kind != MF_OP_OSEEN) return fail(MF_EINVAL, "coupling blocks exist for the Oseen operator only");
+  if (which != 0 && which != 1) return fail(MF_EINVAL, "which must be 0 (B^T p) or 1 (B u)");
+  const int64_t nu = op->map[0]->n_dofs, np = op->map[1]->n_dofs;
+  MF_CUDA_TRY(cudaMemsetAsync(dst, 0, sizeof(T) * size_t(which == 0 ? 3 * nu : np), op->ctx->stream));
+  if constexpr (sizeof(T) == 4) return launch_oseen_coupling_f32(op->ctx, op->map[0], which, src, dst);
+  else return launch_oseen_coupling_f64(op->ctx, op->map[0], which, src, dst);
+}
+template mf_status oseen_coupling<double>(mf_op*, int, const double*, double*);
+template mf_status oseen_coupling<float>(mf_op*, int, const float*, float*);
 template mf_status apply_impl<float>(mf_op*, const float*, float*, int, int64_t, bool, int);
 
 mf_status diag64(mf_op* op, double** out) {
@@ -557,6 +569,15 @@ mf_status mf_apply(mf_op* op, const void* src, void* dst, int nrhs, int64_t ld, 
   if (dtype == MF_DF64) return apply_impl<double>(op, (const double*)src, (double*)dst, nrhs, ld, false, PREC_DF64);
   if (dtype == MF_F32) return apply_impl<float>(op, (const float*)src, (float*)dst, nrhs, ld, false, PREC_F32);
   return fail(MF_EUNSUPPORTED, "apply precision must be MF_F64, MF_DF64 or MF_F32");
+  MF_GUARD_END
+}
+
+mf_status mf_oseen_coupling(mf_op* op, int which, const void* src, void* dst, int dtype) {
+  MF_GUARD_BEGIN
+  if (!op || !src || !dst) return fail(MF_EINVAL, "NULL argument");
+  if (dtype == MF_F64) return oseen_coupling<double>(op, which, (const double*)src, (double*)dst);
+  if (dtype == MF_F32) return oseen_coupling<float>(op, which, (const float*)src, (float*)dst);
+  return fail(MF_EUNSUPPORTED, "coupling precision must be MF_F64 or MF_F32");
   MF_GUARD_END
 }
 

@@ -326,6 +326,93 @@ __global__ void __launch_bounds__(128) k_oseen_qouter(OseenArgs<typename Store<T
     atomicAdd(pdst + pbase + (n & 1) + px * ((n >> 1) & 1) + pxy * (n >> 2), to_store<T>(h * Rp[n]));
 }
 
+// The two coupling blocks of the Oseen operator alone, for the Schur complement B D^-1 B^T of
+// the block preconditioner.  Same quadrature and scaling as k_oseen_qouter's pressure terms:
+//   (B^T p)_{v} = -int p div v   (velocity rows; Dirichlet rows receive nothing)
+//   (B u)_{q}  = -int q div u    (pressure rows; Dirichlet velocity values read as 0)
+// dst must be zero on entry (atomic scatter).
+template <typename T>
+__global__ void __launch_bounds__(128) k_oseen_bt(const typename Store<T>::type* __restrict__ p,
+                                                  typename Store<T>::type* __restrict__ dst_u, int64_t nu,
+                                                  UniformGeom ug) {
+  int i, j, k;
+  if (!brick_cell(ug, i, j, k)) return;
+  const int64_t base = 2 * int64_t(i) + ug.sx * (2 * int64_t(j)) + ug.sy * (2 * int64_t(k));
+  const uint32_t dmask = dirichlet_mask(ug, i, j, k);
+  const int64_t px = ug.nx + 1, pxy = px * (ug.ny + 1);
+  const int64_t pbase = i + px * (j + (ug.ny + 1) * int64_t(k));
+  const T h = T(ug.h);
+  T Pn[8];
+#pragma unroll
+  for (int n = 0; n < 8; ++n) Pn[n] = from_store<T>(__ldg(p + pbase + (n & 1) + px * ((n >> 1) & 1) + pxy * (n >> 2)));
+  T R0[27], R1[27], R2[27];
+#pragma unroll
+  for (int q = 0; q < 27; ++q) { R0[q] = T(0); R1[q] = T(0); R2[q] = T(0); }
+#pragma unroll
+  for (int qc = 0; qc < 3; ++qc)
+#pragma unroll
+    for (int qb = 0; qb < 3; ++qb)
+#pragma unroll
+      for (int qa = 0; qa < 3; ++qa) {
+        const int q = qa + 3 * qb + 9 * qc;
+        T pq = T(0);
+#pragma unroll
+        for (int n = 0; n < 8; ++n) pq += q1w<T>(q, n) * Pn[n];
+        const T pw = Tb<T>::W3(q) * (-h * pq);
+        add_grad_test<T>(R0, qa, qb, qc, pw, T(0), T(0));
+        add_grad_test<T>(R1, qa, qb, qc, T(0), pw, T(0));
+        add_grad_test<T>(R2, qa, qb, qc, T(0), T(0), pw);
+      }
+#pragma unroll
+  for (int q = 0; q < 27; ++q) { R0[q] *= h; R1[q] *= h; R2[q] *= h; }
+  to_nodes<T>(R0);
+  scatter_uniform<T>(dst_u, base, ug.sx, ug.sy, dmask, R0);
+  to_nodes<T>(R1);
+  scatter_uniform<T>(dst_u + nu, base, ug.sx, ug.sy, dmask, R1);
+  to_nodes<T>(R2);
+  scatter_uniform<T>(dst_u + 2 * nu, base, ug.sx, ug.sy, dmask, R2);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(128) k_oseen_div(const typename Store<T>::type* __restrict__ u, int64_t nu,
+                                                   typename Store<T>::type* __restrict__ dst_p, UniformGeom ug) {
+  int i, j, k;
+  if (!brick_cell(ug, i, j, k)) return;
+  const int64_t base = 2 * int64_t(i) + ug.sx * (2 * int64_t(j)) + ug.sy * (2 * int64_t(k));
+  const uint32_t dmask = dirichlet_mask(ug, i, j, k);
+  const int64_t px = ug.nx + 1, pxy = px * (ug.ny + 1);
+  const int64_t pbase = i + px * (j + (ug.ny + 1) * int64_t(k));
+  const T h = T(ug.h);
+  T U0[27], U1[27], U2[27];
+  gather_uniform<T>(u, base, ug.sx, ug.sy, dmask, U0);
+  gather_uniform<T>(u + nu, base, ug.sx, ug.sy, dmask, U1);
+  gather_uniform<T>(u + 2 * nu, base, ug.sx, ug.sy, dmask, U2);
+  to_qpoints<T>(U0);
+  to_qpoints<T>(U1);
+  to_qpoints<T>(U2);
+  T Rp[8];
+#pragma unroll
+  for (int n = 0; n < 8; ++n) Rp[n] = T(0);
+#pragma unroll
+  for (int qc = 0; qc < 3; ++qc)
+#pragma unroll
+    for (int qb = 0; qb < 3; ++qb)
+#pragma unroll
+      for (int qa = 0; qa < 3; ++qa) {
+        const int q = qa + 3 * qb + 9 * qc;
+        T gx0, gy0, gz0, gx1, gy1, gz1, gx2, gy2, gz2;
+        grad_at<T>(U0, qa, qb, qc, gx0, gy0, gz0);
+        grad_at<T>(U1, qa, qb, qc, gx1, gy1, gz1);
+        grad_at<T>(U2, qa, qb, qc, gx2, gy2, gz2);
+        const T s = Tb<T>::W3(q) * (-h * (gx0 + gy1 + gz2));
+#pragma unroll
+        for (int n = 0; n < 8; ++n) Rp[n] += q1w<T>(q, n) * s;
+      }
+#pragma unroll
+  for (int n = 0; n < 8; ++n)
+    atomicAdd(dst_p + pbase + (n & 1) + px * ((n >> 1) & 1) + pxy * (n >> 2), to_store<T>(h * Rp[n]));
+}
+
 }  // namespace
 
 template <typename T, int KIND, int MODE, bool BETA, bool TR>

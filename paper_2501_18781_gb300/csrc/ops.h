@@ -49,6 +49,9 @@ template <typename T> struct OseenArgs {
 mf_status launch_scalar_apply(mf_ctx* ctx, const mf_dofmap* m, int kind, int mode, bool beta, bool transpose,
                               int prec, const void* args);
 mf_status launch_oseen_apply(mf_ctx* ctx, const mf_dofmap* mu, int prec, const void* args);
+// Oseen coupling blocks alone: which 0 dst_u = B^T src_p, which 1 dst_p = B src_u (dst zeroed)
+mf_status launch_oseen_coupling_f64(mf_ctx* ctx, const mf_dofmap* mu, int which, const double* src, double* dst);
+mf_status launch_oseen_coupling_f32(mf_ctx* ctx, const mf_dofmap* mu, int which, const float* src, float* dst);
 // Gauss-point tables from nodal fp64 fields (always evaluated in fp64, stored in both precisions)
 mf_status launch_scalar_qtables(mf_ctx* ctx, const mf_dofmap* m, int kind, const double* field, const double* kq_user,
                                 const double* beta, double k0, double k_slope, double a_l, double a_g, int heaviside,

@@ -22,6 +22,14 @@ mf_status ensure_tables(mf_op* op);
 int scalar_kind(const mf_op* op);
 double value_coef(const mf_op* op);
 template <typename T> ScalarArgs<T> scalar_args(const mf_op* op, const T* src, T* dst, int nrhs, int64_t ld);
+template <typename T> mf_status oseen_coupling(mf_op* op, int which, const T* src, T* dst);
+// device-side stopping test and Givens kernels of the inner solves (solver_kernels.cu)
+mf_status dev_cg_tol_init(mf_ctx* c, double* S, double tol2);
+mf_status dev_cg_tol_check(mf_ctx* c, double* S);
+mf_status dev_gmres_begin(mf_ctx* c, const double* nrm2, double* G, int m);
+mf_status dev_gmres_column(mf_ctx* c, const double* h, double* G, int m, int j);
+mf_status dev_gmres_solve(mf_ctx* c, const double* G, int m, int j, double* y);
+template <typename T> mf_status dev_scale(mf_ctx* c, int64_t n, const double* s, T* v);
 // small device helpers (solver_kernels.cu)
 template <typename T> mf_status dev_scale_mul(mf_ctx* c, const double* s, const double* v, T* out, int64_t n);
 template <typename T> mf_status dev_scale_mul_back(mf_ctx* c, const double* s, const T* v, double* out, int64_t n);
@@ -104,20 +112,21 @@ void back_substitute(const std::vector<double>& H, int m, int j, const std::vect
 //   P = [[A, B^T], [0, -S]],  P^-1 r:  z_p = -S^-1 r_p,  z_u = A^-1 (r_u - B^T z_p),
 // with S ~ S~ = B D^-1 B^T (D: the 3x3 nodal blocks of A) solved by Jacobi-CG (Jacobi from the
 // pressure scaling of the block-Jacobi setup) and A^-1 by a few D^-1-preconditioned GMRES
-// steps.  Every operator application here is an fp32 apply of the whole Oseen operator on a
-// vector whose other block is zero; B^T p is the velocity block of A [0; p], B u the pressure
-// block of A [u; 0].  Vectors and inner products stay fp64.
+// steps.  Both inner solves keep fp32 vectors and fp32 operator arithmetic (the Schur CG on
+// the coupling kernels B^T p and B u alone, the velocity GMRES on the whole operator applied
+// to [v; 0]); inner products accumulate in fp64, and the stopping test, Givens rotations and
+// triangular solve run on the device, so a preconditioner call needs no host round trip.
 struct OseenBlockTri {
   mf_op* op = nullptr;
   int64_t n = 0, nu = 0, nu3 = 0, np = 0;
   int ku = 10, smax = 30;
   double stol = 0.1;
-  Vec<float> f_in, f_out;
-  Vec<double> V, t, w, xp, rp, zp, pp, sp;
-  int64_t applies = 0;
+  Vec<float> blk32, ua, ub, pinv32, xp, rp, zp, pp, sp, V, t, w;
+  Vec<double> gst, y;
 
   mf_status setup(mf_op* o, int velocity_steps, int schur_maxit, double schur_tol) {
     op = o;
+    mf_ctx* c = op->ctx;
     n = op->n;
     nu = op->map[0]->n_dofs;
     nu3 = 3 * nu;
@@ -127,123 +136,79 @@ struct OseenBlockTri {
     smax = schur_maxit > 0 ? schur_maxit : 30;
     stol = schur_tol > 0 ? schur_tol : 0.1;
     MF_TRY(diag64(op, nullptr));  // 3x3 block inverses and the pressure scaling
-    MF_TRY(f_in.alloc(n));
-    MF_TRY(f_out.alloc(n));
+    MF_TRY(blk32.alloc(9 * nu));
+    MF_TRY((convert<double, float>(c, 9 * nu, op->blk64.as<double>(), blk32.p)));
+    MF_TRY(ua.alloc(nu3));
+    MF_TRY(ub.alloc(nu3));
+    for (Vec<float>* v : {&pinv32, &xp, &rp, &zp, &pp, &sp}) MF_TRY(v->alloc(np));
+    MF_TRY((convert<double, float>(c, np, op->pdiag64.as<double>(), pinv32.p)));
     MF_TRY(V.alloc(n * (ku + 1)));
     MF_TRY(t.alloc(n));
     MF_TRY(w.alloc(n));
-    for (Vec<double>* v : {&xp, &rp, &zp, &pp, &sp}) MF_TRY(v->alloc(np));
+    MF_CUDA_TRY(cudaMemsetAsync(t.p, 0, sizeof(float) * n, c->stream));  // its pressure block stays 0
+    MF_TRY(gst.alloc(ku * ku + 3 * ku + 2));
+    MF_TRY(y.alloc(ku));
     return MF_OK;
   }
 
-  const double* blk() const { return op->blk64.as<double>(); }
-  const double* pinv() const { return op->pdiag64.as<double>(); }
-
-  // out = A in (whole operator, fp32 arithmetic, fp64 vectors)
-  mf_status apply32(const double* in, double* out) {
-    mf_ctx* c = op->ctx;
-    MF_TRY((convert<double, float>(c, n, in, f_in.p)));
-    MF_TRY(apply_impl<float>(op, f_in.p, f_out.p, 1, n, false));
-    ++applies;
-    return convert<float, double>(c, n, f_out.p, out);
+  // out = S~ p = B D^-1 B^T p
+  mf_status schur(const float* p, float* out) {
+    MF_TRY(oseen_coupling<float>(op, 0, p, ua.p));
+    MF_TRY(block_jacobi_u32(op->ctx, nu, blk32.p, ua.p, ub.p));
+    return oseen_coupling<float>(op, 1, ub.p, out);
   }
 
-  // out_p = S~ p = B D^-1 B^T p
-  mf_status schur(const double* p, double* out_p) {
-    mf_ctx* c = op->ctx;
-    MF_CUDA_TRY(cudaMemsetAsync(t.p, 0, sizeof(double) * nu3, c->stream));
-    MF_CUDA_TRY(cudaMemcpyAsync(t.p + nu3, p, sizeof(double) * np, cudaMemcpyDeviceToDevice, c->stream));
-    MF_TRY(apply32(t.p, w.p));  // w_u = B^T p (Dirichlet rows: 0), w_p = 0
-    MF_CUDA_TRY(cudaMemsetAsync(w.p + nu3, 0, sizeof(double) * np, c->stream));
-    MF_TRY(block_jacobi<double>(c, nu, np, blk(), pinv(), w.p, t.p));  // t = [D^-1 w_u; 0]
-    MF_TRY(apply32(t.p, w.p));  // w_p = B D^-1 B^T p
-    MF_CUDA_TRY(cudaMemcpyAsync(out_p, w.p + nu3, sizeof(double) * np, cudaMemcpyDeviceToDevice, c->stream));
-    return MF_OK;
-  }
-
-  // xp = S~^-1 r (Jacobi-PCG from 0 to stol relative or smax steps); r is not modified
+  // xp = S~^-1 r_p (r_p fp64): Jacobi-PCG from 0, smax steps; once ||r_k|| <= stol ||r_0|| (or
+  // p.S~p <= 0) the remaining steps leave x unchanged.
   mf_status schur_solve(const double* r) {
     mf_ctx* c = op->ctx;
-    double* ds = c->scalars.as<double>() + kScalarsTri;
-    double* hs = c->host_scalars + kScalarsTri;
-    MF_CUDA_TRY(cudaMemsetAsync(xp.p, 0, sizeof(double) * np, c->stream));
-    MF_CUDA_TRY(cudaMemcpyAsync(rp.p, r, sizeof(double) * np, cudaMemcpyDeviceToDevice, c->stream));
-    MF_TRY(pointwise_mul<double>(c, np, pinv(), rp.p, zp.p));
-    MF_CUDA_TRY(cudaMemcpyAsync(pp.p, zp.p, sizeof(double) * np, cudaMemcpyDeviceToDevice, c->stream));
-    MF_TRY(norm2_sq(c, rp.p, np, ds));
-    MF_TRY((dot<double, double>(c, rp.p, zp.p, np, ds + 1)));
-    MF_TRY(sync_copy(c, hs, ds, 2));
-    const double r0 = std::sqrt(hs[0]);
-    double rz = hs[1];
-    if (r0 == 0.0) return MF_OK;
+    double* S = c->scalars.as<double>() + kScalarsTri + 128;
+    MF_CUDA_TRY(cudaMemsetAsync(xp.p, 0, sizeof(float) * np, c->stream));
+    MF_TRY((convert<double, float>(c, np, r, rp.p)));
+    MF_TRY(pointwise_mul<float>(c, np, pinv32.p, rp.p, zp.p));
+    MF_CUDA_TRY(cudaMemcpyAsync(pp.p, zp.p, sizeof(float) * np, cudaMemcpyDeviceToDevice, c->stream));
+    MF_TRY(cg_init_scalars<float>(c, rp.p, zp.p, np, np, 1, S));
+    MF_TRY(dev_cg_tol_init(c, S, stol * stol));
     for (int k = 0; k < smax; ++k) {
       MF_TRY(schur(pp.p, sp.p));
-      MF_TRY((dot<double, double>(c, pp.p, sp.p, np, ds)));
-      MF_TRY(sync_copy(c, hs, ds, 1));
-      if (!(hs[0] > 0.0)) break;  // S~ not positive along p: keep the iterate
-      const double alpha = rz / hs[0];
-      MF_TRY((axpby<double, double>(c, np, alpha, pp.p, 1.0, xp.p)));
-      MF_TRY((axpby<double, double>(c, np, -alpha, sp.p, 1.0, rp.p)));
-      MF_TRY(pointwise_mul<double>(c, np, pinv(), rp.p, zp.p));
-      MF_TRY(norm2_sq(c, rp.p, np, ds));
-      MF_TRY((dot<double, double>(c, rp.p, zp.p, np, ds + 1)));
-      MF_TRY(sync_copy(c, hs, ds, 2));
-      if (std::sqrt(hs[0]) <= stol * r0) break;
-      const double beta = hs[1] / rz;
-      rz = hs[1];
-      MF_TRY((axpby<double, double>(c, np, 1.0, zp.p, beta, pp.p)));
+      MF_TRY(cg_alpha<float>(c, pp.p, sp.p, np, np, 1, S));
+      MF_TRY(cg_update_xr<float>(c, np, np, 1, xp.p, rp.p, pp.p, sp.p, pinv32.p, zp.p, 1, S));
+      MF_TRY(dev_cg_tol_check(c, S));
+      MF_TRY(cg_update_p<float>(c, np, np, 1, zp.p, pp.p, S));
     }
     return MF_OK;
   }
 
-  // z_u = A^-1 rhs_u by ku steps of GMRES from 0, right-preconditioned by D^-1.  rhs is a full
-  // length vector whose pressure block is zero and is read only before the first step (it may
-  // be w); z's pressure block is left untouched.
-  mf_status velocity_solve(const double* rhs, double* z) {
+  // z_u = A^-1 rhs_u (z fp64) by ku steps of GMRES from 0, right-preconditioned by D^-1.  rhs
+  // is w: a full-length vector whose pressure block is zero, read before the first step only.
+  mf_status velocity_solve(double* z) {
     mf_ctx* c = op->ctx;
-    double* ds = c->scalars.as<double>() + kScalarsTri;
-    double* hs = c->host_scalars + kScalarsTri;
+    double* ds = c->scalars.as<double>() + kScalarsTri;  // 2 (m + 1) + 1 CGS2 coefficients
     const int m = ku;
-    MF_TRY(norm2_sq(c, rhs, nu3, ds));
-    MF_TRY(sync_copy(c, hs, ds, 1));
-    const double beta = std::sqrt(hs[0]);
-    if (beta == 0.0) {
-      MF_CUDA_TRY(cudaMemsetAsync(z, 0, sizeof(double) * nu3, c->stream));
-      return MF_OK;
+    double* G = gst.p;
+    double* inv = G + 3 * m + 1;
+    MF_TRY((dot<float, float>(c, w.p, w.p, nu3, ds)));
+    MF_TRY(dev_gmres_begin(c, ds, G, m));
+    MF_CUDA_TRY(cudaMemcpyAsync(V.p, w.p, sizeof(float) * n, cudaMemcpyDeviceToDevice, c->stream));
+    MF_TRY(dev_scale<float>(c, nu3, inv, V.p));
+    for (int j = 0; j < m; ++j) {
+      float* vj1 = V.p + (j + 1) * n;
+      MF_TRY(block_jacobi_u32(c, nu, blk32.p, V.p + j * n, t.p));
+      MF_TRY(apply_impl<float>(op, t.p, vj1, 1, n, false));
+      MF_CUDA_TRY(cudaMemsetAsync(vj1 + nu3, 0, sizeof(float) * np, c->stream));
+      MF_TRY(multidot<float>(c, V.p, n, j + 1, vj1, nu3, ds));
+      MF_TRY(multiaxpy<float>(c, V.p, n, j + 1, ds, -1.0, vj1, nu3));
+      MF_TRY(multidot<float>(c, V.p, n, j + 1, vj1, nu3, ds + (m + 1)));
+      MF_TRY(multiaxpy<float>(c, V.p, n, j + 1, ds + (m + 1), -1.0, vj1, nu3));
+      MF_TRY((dot<float, float>(c, vj1, vj1, nu3, ds + 2 * (m + 1))));
+      MF_TRY(dev_gmres_column(c, ds, G, m, j));
+      MF_TRY(dev_scale<float>(c, nu3, inv, vj1));
     }
-    MF_TRY((axpby<double, double>(c, n, 1.0 / beta, rhs, 0.0, V.p)));
-    std::vector<double> H((m + 1) * m, 0.0), cs(m), sn(m), g(m + 1, 0.0), y(m);
-    g[0] = beta;
-    int j = 0;
-    for (; j < m; ++j) {
-      double* vj1 = V.p + (j + 1) * n;
-      MF_TRY(block_jacobi<double>(c, nu, np, blk(), pinv(), V.p + j * n, t.p));  // pressure block stays 0
-      MF_TRY(apply32(t.p, vj1));
-      MF_CUDA_TRY(cudaMemsetAsync(vj1 + nu3, 0, sizeof(double) * np, c->stream));
-      MF_TRY(multidot(c, V.p, n, j + 1, vj1, nu3, ds));
-      MF_TRY(multiaxpy(c, V.p, n, j + 1, ds, -1.0, vj1, nu3));
-      MF_TRY(multidot(c, V.p, n, j + 1, vj1, nu3, ds + (m + 1)));
-      MF_TRY(multiaxpy(c, V.p, n, j + 1, ds + (m + 1), -1.0, vj1, nu3));
-      MF_TRY(norm2_sq(c, vj1, nu3, ds + 2 * (m + 1)));
-      MF_TRY(sync_copy(c, hs, ds, 2 * (m + 1) + 1));
-      for (int i = 0; i <= j; ++i) H[i * m + j] = hs[i] + hs[(m + 1) + i];
-      const double hn = std::sqrt(hs[2 * (m + 1)]);
-      H[(j + 1) * m + j] = hn;
-      givens_column(H, m, j, cs, sn, g);
-      if (hn == 0.0) {
-        ++j;
-        break;
-      }
-      MF_TRY((axpby<double, double>(c, nu3, 1.0 / hn, vj1, 0.0, vj1)));
-    }
-    back_substitute(H, m, j, g, y);
-    for (int i = 0; i < j; ++i) hs[i] = y[i];
-    MF_CUDA_TRY(cudaMemcpyAsync(ds, hs, sizeof(double) * j, cudaMemcpyHostToDevice, c->stream));
-    MF_CUDA_TRY(cudaMemsetAsync(w.p, 0, sizeof(double) * n, c->stream));
-    MF_TRY(multiaxpy(c, V.p, n, j, ds, 1.0, w.p, nu3));
-    MF_TRY(block_jacobi<double>(c, nu, np, blk(), pinv(), w.p, t.p));
-    MF_CUDA_TRY(cudaMemcpyAsync(z, t.p, sizeof(double) * nu3, cudaMemcpyDeviceToDevice, c->stream));
-    return MF_OK;
+    MF_TRY(dev_gmres_solve(c, G, m, m, y.p));
+    MF_CUDA_TRY(cudaMemsetAsync(w.p, 0, sizeof(float) * nu3, c->stream));
+    MF_TRY(multiaxpy<float>(c, V.p, n, m, y.p, 1.0, w.p, nu3));
+    MF_TRY(block_jacobi_u32(c, nu, blk32.p, w.p, t.p));
+    return convert<float, double>(c, nu3, t.p, z);
   }
 
   // z = P^-1 r (fp64 vectors of length n)
@@ -251,13 +216,12 @@ struct OseenBlockTri {
     mf_ctx* c = op->ctx;
     MF_TRY(schur_solve(r + nu3));
     // z_p = -x_p; velocity right-hand side r_u - B^T z_p = r_u + B^T x_p
-    MF_TRY((axpby<double, double>(c, np, -1.0, xp.p, 0.0, z + nu3)));
-    MF_CUDA_TRY(cudaMemsetAsync(t.p, 0, sizeof(double) * nu3, c->stream));
-    MF_CUDA_TRY(cudaMemcpyAsync(t.p + nu3, xp.p, sizeof(double) * np, cudaMemcpyDeviceToDevice, c->stream));
-    MF_TRY(apply32(t.p, w.p));
-    MF_TRY((axpby<double, double>(c, nu3, 1.0, r, 1.0, w.p)));
-    MF_CUDA_TRY(cudaMemsetAsync(w.p + nu3, 0, sizeof(double) * np, c->stream));
-    return velocity_solve(w.p, z);
+    MF_TRY((axpby<float, double>(c, np, -1.0, xp.p, 0.0, z + nu3)));
+    MF_TRY(oseen_coupling<float>(op, 0, xp.p, ua.p));
+    MF_TRY((axpby<double, float>(c, nu3, 1.0, r, 0.0, w.p)));
+    MF_TRY((axpby<float, float>(c, nu3, 1.0, ua.p, 1.0, w.p)));
+    MF_CUDA_TRY(cudaMemsetAsync(w.p + nu3, 0, sizeof(float) * np, c->stream));
+    return velocity_solve(z);
   }
 };
 

@@ -39,6 +39,63 @@ __global__ void k_add_scaled(const float* d, double* x, const double* sc, int64_
     x[o + i] += s * double(d[o + i]);
 }
 
+// Inner solves of the Oseen block preconditioner without host round trips: the stopping test
+// of a CG and the Givens/back-substitution of a fixed-length GMRES run in one-thread kernels
+// on device scalars.
+__global__ void k_cg_tol_init(double* S, double tol2) {
+  S[S_ACTIVE] = S[S_RR] > 0.0 ? 1.0 : 0.0;
+  S[7] = tol2 * S[S_RR];
+}
+__global__ void k_cg_tol_check(double* S) {
+  if (S[S_RR] <= S[7] || !(S[S_PAP] > 0.0)) S[S_ACTIVE] = 0.0;
+}
+// G layout (m = restart): cs[m], sn[m], g[m + 1], inv (1/norm of the newest vector), R[m][m]
+__global__ void k_gmres_begin(const double* nrm2, double* G, int m) {
+  const double beta = sqrt(nrm2[0]);
+  double* g = G + 2 * m;
+  g[0] = beta;
+  for (int i = 1; i <= m; ++i) g[i] = 0.0;
+  G[3 * m + 1] = beta > 0.0 ? 1.0 / beta : 0.0;
+}
+// h: CGS2 coefficients h[0..j] and h[m+1..m+1+j] (two passes), h[2(m+1)] = |w|^2
+__global__ void k_gmres_column(const double* h, double* G, int m, int j) {
+  double* cs = G;
+  double* sn = G + m;
+  double* g = G + 2 * m;
+  double* R = G + 3 * m + 2;
+  double col[64];
+  for (int i = 0; i <= j; ++i) col[i] = h[i] + h[m + 1 + i];
+  const double hn = sqrt(h[2 * (m + 1)]);
+  col[j + 1] = hn;
+  for (int i = 0; i < j; ++i) {
+    const double t = cs[i] * col[i] + sn[i] * col[i + 1];
+    col[i + 1] = -sn[i] * col[i] + cs[i] * col[i + 1];
+    col[i] = t;
+  }
+  const double den = hypot(col[j], col[j + 1]);
+  cs[j] = den > 0.0 ? col[j] / den : 1.0;
+  sn[j] = den > 0.0 ? col[j + 1] / den : 0.0;
+  col[j] = den;
+  g[j + 1] = -sn[j] * g[j];
+  g[j] = cs[j] * g[j];
+  for (int i = 0; i <= j; ++i) R[i * m + j] = col[i];
+  G[3 * m + 1] = hn > 0.0 ? 1.0 / hn : 0.0;
+}
+__global__ void k_gmres_solve(const double* G, int m, int j, double* y) {
+  const double* g = G + 2 * m;
+  const double* R = G + 3 * m + 2;
+  for (int i = j - 1; i >= 0; --i) {
+    double s = g[i];
+    for (int k = i + 1; k < j; ++k) s -= R[i * m + k] * y[k];
+    y[i] = R[i * m + i] != 0.0 ? s / R[i * m + i] : 0.0;
+  }
+}
+template <typename T> __global__ void k_scale_dev(int64_t n, const double* s, T* v) {
+  const T a = T(s[0]);
+  for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x)
+    v[i] *= a;
+}
+
 }  // namespace
 
 #define LAUNCHED() \
@@ -73,5 +130,33 @@ mf_status dev_add_scaled(mf_ctx* c, const float* d, double* x, const double* sca
   k_add_scaled<<<dim3(grid(n), nrhs), 256, 0, c->stream>>>(d, x, scale, n);
   LAUNCHED();
 }
+
+mf_status dev_cg_tol_init(mf_ctx* c, double* S, double tol2) {
+  k_cg_tol_init<<<1, 1, 0, c->stream>>>(S, tol2);
+  LAUNCHED();
+}
+mf_status dev_cg_tol_check(mf_ctx* c, double* S) {
+  k_cg_tol_check<<<1, 1, 0, c->stream>>>(S);
+  LAUNCHED();
+}
+mf_status dev_gmres_begin(mf_ctx* c, const double* nrm2, double* G, int m) {
+  k_gmres_begin<<<1, 1, 0, c->stream>>>(nrm2, G, m);
+  LAUNCHED();
+}
+mf_status dev_gmres_column(mf_ctx* c, const double* h, double* G, int m, int j) {
+  if (m > 63) return fail(MF_EINVAL, "device GMRES: at most 63 steps");
+  k_gmres_column<<<1, 1, 0, c->stream>>>(h, G, m, j);
+  LAUNCHED();
+}
+mf_status dev_gmres_solve(mf_ctx* c, const double* G, int m, int j, double* y) {
+  k_gmres_solve<<<1, 1, 0, c->stream>>>(G, m, j, y);
+  LAUNCHED();
+}
+template <typename T> mf_status dev_scale(mf_ctx* c, int64_t n, const double* s, T* v) {
+  k_scale_dev<T><<<grid(n), 256, 0, c->stream>>>(n, s, v);
+  LAUNCHED();
+}
+template mf_status dev_scale<double>(mf_ctx*, int64_t, const double*, double*);
+template mf_status dev_scale<float>(mf_ctx*, int64_t, const double*, float*);
 
 }  // namespace mf

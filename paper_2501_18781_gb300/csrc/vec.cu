@@ -3,6 +3,7 @@
 // dot product is deterministic.
 #include <mutex>
 #include <string>
+#include <type_traits>
 
 #include "vec.cuh"
 
@@ -23,6 +24,27 @@ __device__ __forceinline__ double block_sum(double v) {
   __syncthreads();
   return s;  // valid in thread 0
 }
+
+// fp32 data: GB300's fp64 pipe (1/64 of the fp32 rate) cannot keep up with HBM if every
+// element is converted and accumulated in fp64 (a conversion and an fp64 FMA per 4-byte
+// element).  Within a thread, fp32 products and sums are therefore carried as unevaluated
+// pairs of floats: the product error by an FMA (a*b = p + e exactly) and the sum error by
+// Knuth's two-sum, i.e. the compensated dot product of Ogita, Rump and Oishi ("Accurate sum
+// and dot product", SIAM J. Sci. Comput. 26, 2005), whose result is as accurate as a dot
+// product evaluated in twice the working precision.  Partials leave the thread as
+// double(s) + double(c) and are reduced in fp64.
+struct Dot2f {
+  float s = 0.0f, c = 0.0f;
+  __device__ __forceinline__ void add(float a, float b) {
+    const float p = a * b;
+    const float e = fmaf(a, b, -p);
+    const float t = s + p;
+    const float z = t - s;
+    c += ((s - (t - z)) + (p - z)) + e;
+    s = t;
+  }
+  __device__ __forceinline__ double value() const { return double(s) + double(c); }
+};
 
 // out = sum(part); one block per right-hand side r (blockIdx.x), partial rows of g entries.
 // mode 0: out[r] = sum; 1: pAp and alpha; 2: rr, rz (second row), beta; 3: rz and beta; 4: rr and rz
@@ -58,18 +80,65 @@ __global__ void __launch_bounds__(kRedThreads) k_finish(const double* part, int 
   }
 }
 
+// Per-block partial sums of x.y (and x2.y2).  Each thread keeps four independent
+// accumulators over elements one grid stride apart, so four loads per vector are in flight
+// per thread (enough bytes in flight to approach HBM bandwidth with one block per warp slot);
+// the partition and the summation order are fixed, so results are reproducible bit for bit.
 template <typename TX, typename TY>
 __global__ void __launch_bounds__(kRedThreads) k_dot2_partial(const TX* x, const TY* y, const TX* x2, const TY* y2,
                                                              int64_t n, int64_t ld, double* part) {
   const int r = blockIdx.y;
   x += r * ld; y += r * ld;
-  double s = 0.0, s2 = 0.0;
-  for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x) {
-    s += double(x[i]) * double(y[i]);
-    if (x2) s2 += double(x2[r * ld + i]) * double(y2[r * ld + i]);
+  if (x2) { x2 += r * ld; y2 += r * ld; }
+  const int64_t st = int64_t(gridDim.x) * blockDim.x;
+  int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if constexpr (std::is_same<TX, float>::value && std::is_same<TY, float>::value) {
+    Dot2f a0, a1, a2, a3, b0, b1, b2, b3;
+    for (; i + 3 * st < n; i += 4 * st) {
+      const float p0 = x[i], p1 = x[i + st], p2 = x[i + 2 * st], p3 = x[i + 3 * st];
+      const float q0 = y[i], q1 = y[i + st], q2 = y[i + 2 * st], q3 = y[i + 3 * st];
+      a0.add(p0, q0); a1.add(p1, q1); a2.add(p2, q2); a3.add(p3, q3);
+      if (x2) {
+        b0.add(x2[i], y2[i]); b1.add(x2[i + st], y2[i + st]);
+        b2.add(x2[i + 2 * st], y2[i + 2 * st]); b3.add(x2[i + 3 * st], y2[i + 3 * st]);
+      }
+    }
+    for (; i < n; i += st) {
+      a0.add(x[i], y[i]);
+      if (x2) b0.add(x2[i], y2[i]);
+    }
+    const double s = block_sum((a0.value() + a1.value()) + (a2.value() + a3.value()));
+    const double s2 = x2 ? block_sum((b0.value() + b1.value()) + (b2.value() + b3.value())) : 0.0;
+    if (threadIdx.x == 0) {
+      part[int64_t(r) * 2 * gridDim.x + blockIdx.x] = s;
+      part[int64_t(r) * 2 * gridDim.x + gridDim.x + blockIdx.x] = s2;
+    }
+    return;
   }
-  s = block_sum(s);
-  if (x2) s2 = block_sum(s2);
+  double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0, b0 = 0.0, b1 = 0.0, b2 = 0.0, b3 = 0.0;
+  if (x2) {
+    for (; i + 3 * st < n; i += 4 * st) {
+      const double p0 = double(x[i]), p1 = double(x[i + st]), p2 = double(x[i + 2 * st]), p3 = double(x[i + 3 * st]);
+      const double q0 = double(y[i]), q1 = double(y[i + st]), q2 = double(y[i + 2 * st]), q3 = double(y[i + 3 * st]);
+      const double u0 = double(x2[i]), u1 = double(x2[i + st]), u2 = double(x2[i + 2 * st]), u3 = double(x2[i + 3 * st]);
+      const double v0 = double(y2[i]), v1 = double(y2[i + st]), v2 = double(y2[i + 2 * st]), v3 = double(y2[i + 3 * st]);
+      a0 += p0 * q0; a1 += p1 * q1; a2 += p2 * q2; a3 += p3 * q3;
+      b0 += u0 * v0; b1 += u1 * v1; b2 += u2 * v2; b3 += u3 * v3;
+    }
+    for (; i < n; i += st) {
+      a0 += double(x[i]) * double(y[i]);
+      b0 += double(x2[i]) * double(y2[i]);
+    }
+  } else {
+    for (; i + 3 * st < n; i += 4 * st) {
+      const double p0 = double(x[i]), p1 = double(x[i + st]), p2 = double(x[i + 2 * st]), p3 = double(x[i + 3 * st]);
+      const double q0 = double(y[i]), q1 = double(y[i + st]), q2 = double(y[i + 2 * st]), q3 = double(y[i + 3 * st]);
+      a0 += p0 * q0; a1 += p1 * q1; a2 += p2 * q2; a3 += p3 * q3;
+    }
+    for (; i < n; i += st) a0 += double(x[i]) * double(y[i]);
+  }
+  double s = block_sum((a0 + a1) + (a2 + a3));
+  double s2 = x2 ? block_sum((b0 + b1) + (b2 + b3)) : 0.0;
   if (threadIdx.x == 0) {
     part[int64_t(r) * 2 * gridDim.x + blockIdx.x] = s;
     part[int64_t(r) * 2 * gridDim.x + gridDim.x + blockIdx.x] = s2;
@@ -83,18 +152,38 @@ __global__ void __launch_bounds__(kRedThreads) k_cg_xr(int64_t n, int64_t ld, T*
   const double alpha = S[rh * S_NSCAL + S_ALPHA];
   const int64_t o = rh * ld;
   double rr = 0.0, rz = 0.0;
-  for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x) {
-    T xi = x[o + i] + T(alpha) * p[o + i];
-    T ri = r[o + i] - T(alpha) * Ap[o + i];
-    x[o + i] = xi;
-    r[o + i] = ri;
-    rr += double(ri) * double(ri);
-    if (zmode == 1) {
-      T zi = dinv[i] * ri;
-      z[o + i] = zi;
-      rz += double(ri) * double(zi);
-    } else if (zmode == 0) {
-      rz += double(ri) * double(ri);
+  if constexpr (std::is_same<T, float>::value) {
+    Dot2f crr, crz;
+    for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x) {
+      const float xi = x[o + i] + float(alpha) * p[o + i];
+      const float ri = r[o + i] - float(alpha) * Ap[o + i];
+      x[o + i] = xi;
+      r[o + i] = ri;
+      crr.add(ri, ri);
+      if (zmode == 1) {
+        const float zi = dinv[i] * ri;
+        z[o + i] = zi;
+        crz.add(ri, zi);
+      } else if (zmode == 0) {
+        crz.add(ri, ri);
+      }
+    }
+    rr = crr.value();
+    rz = crz.value();
+  } else {
+    for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x) {
+      T xi = x[o + i] + T(alpha) * p[o + i];
+      T ri = r[o + i] - T(alpha) * Ap[o + i];
+      x[o + i] = xi;
+      r[o + i] = ri;
+      rr += double(ri) * double(ri);
+      if (zmode == 1) {
+        T zi = dinv[i] * ri;
+        z[o + i] = zi;
+        rz += double(ri) * double(zi);
+      } else if (zmode == 0) {
+        rz += double(ri) * double(ri);
+      }
     }
   }
   rr = block_sum(rr);
@@ -124,12 +213,12 @@ template <typename T> __global__ void k_pmul(int64_t n, const T* d, const T* r, 
     z[i] = d ? d[i] * r[i] : r[i];
 }
 
-template <typename T>
-__global__ void k_block_jacobi(int64_t nu, int64_t np, const double* blk, const double* pinv, const T* r, T* z) {
+template <typename T, typename TB>
+__global__ void k_block_jacobi(int64_t nu, int64_t np, const TB* blk, const double* pinv, const T* r, T* z) {
   for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < nu + np; i += int64_t(gridDim.x) * blockDim.x) {
     if (i < nu) {
-      const double* B = blk + 9 * i;
-      double r0 = r[i], r1 = r[nu + i], r2 = r[2 * nu + i];
+      const TB* B = blk + 9 * i;
+      const TB r0 = TB(r[i]), r1 = TB(r[nu + i]), r2 = TB(r[2 * nu + i]);
       z[i] = T(B[0] * r0 + B[1] * r1 + B[2] * r2);
       z[nu + i] = T(B[3] * r0 + B[4] * r1 + B[5] * r2);
       z[2 * nu + i] = T(B[6] * r0 + B[7] * r1 + B[8] * r2);
@@ -175,15 +264,52 @@ template <typename T> __global__ void k_add_into(int64_t n, int64_t ld, const T*
 }
 
 // h partials: part[j * G + block] = sum over the block's slice of V_j . w
-__global__ void __launch_bounds__(kRedThreads) k_multidot(const double* V, int64_t ld, int k, const double* w, int64_t n,
+// h_j partials for V_j . w, eight vectors per sweep: every element of w is loaded once per
+// group of eight and the eight V_j loads are independent, so many loads are in flight per thread.
+template <typename T>
+__global__ void __launch_bounds__(kRedThreads) k_multidot(const T* V, int64_t ld, int k, const T* w, int64_t n,
                                                           double* part) {
-  for (int j = 0; j < k; ++j) {
-    double s = 0.0;
-    const double* v = V + j * ld;
-    for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x)
-      s += v[i] * w[i];
-    s = block_sum(s);
-    if (threadIdx.x == 0) part[j * gridDim.x + blockIdx.x] = s;
+  constexpr int G = 8;
+  const int64_t st = int64_t(gridDim.x) * blockDim.x;
+  for (int j0 = 0; j0 < k; j0 += G) {
+    double a[G];
+#pragma unroll
+    for (int g = 0; g < G; ++g) a[g] = 0.0;
+    const int kg = k - j0 < G ? k - j0 : G;
+    const T* V0 = V + j0 * ld;
+    if constexpr (std::is_same<T, float>::value) {
+      Dot2f c[G];
+      for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += st) {
+        const float wi = w[i];
+#pragma unroll
+        for (int g = 0; g < G; ++g)
+          if (g < kg) c[g].add(V0[g * ld + i], wi);
+      }
+#pragma unroll
+      for (int g = 0; g < G; ++g) a[g] = c[g].value();
+    } else if (kg == G) {
+      for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += st) {
+        const double wi = double(w[i]);
+        T v[G];
+#pragma unroll
+        for (int g = 0; g < G; ++g) v[g] = V0[g * ld + i];
+#pragma unroll
+        for (int g = 0; g < G; ++g) a[g] += double(v[g]) * wi;
+      }
+    } else {
+      for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += st) {
+        const double wi = double(w[i]);
+#pragma unroll
+        for (int g = 0; g < G; ++g)
+          if (g < kg) a[g] += double(V0[g * ld + i]) * wi;
+      }
+    }
+#pragma unroll
+    for (int g = 0; g < G; ++g) {
+      if (g >= kg) break;
+      const double sg = block_sum(a[g]);
+      if (threadIdx.x == 0) part[(j0 + g) * gridDim.x + blockIdx.x] = sg;
+    }
   }
 }
 __global__ void __launch_bounds__(kRedThreads) k_multidot_finish(const double* part, int g, double* h) {
@@ -193,11 +319,46 @@ __global__ void __launch_bounds__(kRedThreads) k_multidot_finish(const double* p
   if (threadIdx.x == 0) h[blockIdx.x] = s;
 }
 
-__global__ void k_multiaxpy(const double* V, int64_t ld, int k, const double* h, double sign, double* w, int64_t n) {
+// w += sign V h over k <= 64 vectors; h staged in shared memory, eight independent V loads
+// per step of the j loop.
+template <typename T>
+__global__ void k_multiaxpy(const T* V, int64_t ld, int k, const double* h, double sign, T* w, int64_t n) {
+  __shared__ double hs[64];
+  __shared__ float hf[64];
+  for (int j = threadIdx.x; j < k; j += blockDim.x) {
+    hs[j] = sign * h[j];
+    hf[j] = float(sign * h[j]);
+  }
+  __syncthreads();
+  if constexpr (std::is_same<T, float>::value) {
+    // fp32 result: fp32 FMAs (the fp64 pipe would bound this HBM-bound update)
+    for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x) {
+      float acc = w[i];
+      int j = 0;
+      for (; j + 8 <= k; j += 8) {
+        float v[8];
+#pragma unroll
+        for (int g = 0; g < 8; ++g) v[g] = V[(j + g) * ld + i];
+#pragma unroll
+        for (int g = 0; g < 8; ++g) acc = fmaf(hf[j + g], v[g], acc);
+      }
+      for (; j < k; ++j) acc = fmaf(hf[j], V[j * ld + i], acc);
+      w[i] = acc;
+    }
+    return;
+  }
   for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x) {
-    double acc = w[i];
-    for (int j = 0; j < k; ++j) acc += sign * h[j] * V[j * ld + i];
-    w[i] = acc;
+    double acc = double(w[i]);
+    int j = 0;
+    for (; j + 8 <= k; j += 8) {
+      T v[8];
+#pragma unroll
+      for (int g = 0; g < 8; ++g) v[g] = V[(j + g) * ld + i];
+#pragma unroll
+      for (int g = 0; g < 8; ++g) acc += hs[j + g] * double(v[g]);
+    }
+    for (; j < k; ++j) acc += hs[j] * double(V[j * ld + i]);
+    w[i] = T(acc);
   }
 }
 
@@ -286,7 +447,12 @@ template mf_status pointwise_mul<float>(mf_ctx*, int64_t, const float*, const fl
 
 template <typename T>
 mf_status block_jacobi(mf_ctx* ctx, int64_t nu, int64_t np, const double* blk, const double* pinv, const T* r, T* z) {
-  k_block_jacobi<T><<<grid_for(nu + np), 256, 0, ctx->stream>>>(nu, np, blk, pinv, r, z);
+  k_block_jacobi<T, double><<<grid_for(nu + np), 256, 0, ctx->stream>>>(nu, np, blk, pinv, r, z);
+  LAUNCH_CHECK();
+  return MF_OK;
+}
+mf_status block_jacobi_u32(mf_ctx* ctx, int64_t nu, const float* blk, const float* r, float* z) {
+  k_block_jacobi<float, float><<<grid_for(nu), 256, 0, ctx->stream>>>(nu, 0, blk, nullptr, r, z);
   LAUNCH_CHECK();
   return MF_OK;
 }
@@ -394,22 +560,30 @@ template <typename T> mf_status add_into(mf_ctx* ctx, int64_t n, int64_t ld, int
 template mf_status add_into<double>(mf_ctx*, int64_t, int64_t, int, const double*, double*);
 template mf_status add_into<float>(mf_ctx*, int64_t, int64_t, int, const float*, float*);
 
-mf_status multidot(mf_ctx* ctx, const double* V, int64_t ld, int k, const double* w, int64_t n, double* h) {
-  const int g = 152 * 2;
+template <typename T> mf_status multidot(mf_ctx* ctx, const T* V, int64_t ld, int k, const T* w, int64_t n, double* h) {
+  if (k > 64) return fail(MF_EINVAL, "multidot: at most 64 vectors");
+  const int g = kRedBlocks;
   double* part;
   MF_TRY(scratch(ctx, size_t(g) * (k + 1) + 64, &part));
-  k_multidot<<<g, kRedThreads, 0, ctx->stream>>>(V, ld, k, w, n, part);
+  k_multidot<T><<<g, kRedThreads, 0, ctx->stream>>>(V, ld, k, w, n, part);
   LAUNCH_CHECK();
   k_multidot_finish<<<k, kRedThreads, 0, ctx->stream>>>(part, g, h);
   LAUNCH_CHECK();
   return MF_OK;
 }
+template mf_status multidot<double>(mf_ctx*, const double*, int64_t, int, const double*, int64_t, double*);
+template mf_status multidot<float>(mf_ctx*, const float*, int64_t, int, const float*, int64_t, double*);
 
-mf_status multiaxpy(mf_ctx* ctx, double* V, int64_t ld, int k, const double* h, double sign, double* w, int64_t n) {
-  k_multiaxpy<<<grid_for(n), 256, 0, ctx->stream>>>(V, ld, k, h, sign, w, n);
+template <typename T>
+mf_status multiaxpy(mf_ctx* ctx, const T* V, int64_t ld, int k, const double* h, double sign, T* w, int64_t n) {
+  if (k > 64) return fail(MF_EINVAL, "multiaxpy: at most 64 vectors");
+  if (k < 1) return MF_OK;
+  k_multiaxpy<T><<<grid_for(n), 256, 0, ctx->stream>>>(V, ld, k, h, sign, w, n);
   LAUNCH_CHECK();
   return MF_OK;
 }
+template mf_status multiaxpy<double>(mf_ctx*, const double*, int64_t, int, const double*, double, double*, int64_t);
+template mf_status multiaxpy<float>(mf_ctx*, const float*, int64_t, int, const double*, double, float*, int64_t);
 
 mf_status fill_splitmix(mf_ctx* ctx, uint64_t seed, double* v, int64_t n) {
   k_splitmix<<<grid_for(n), 256, 0, ctx->stream>>>(seed, v, n);

@@ -14,7 +14,8 @@ constexpr size_t kScratchDoubles = size_t(2) * kRedBlocks * 64;  // up to 64 rig
 template <typename TX, typename TY>
 mf_status dot(mf_ctx* ctx, const TX* x, const TY* y, int64_t n, double* out);
 mf_status norm2_sq(mf_ctx* ctx, const double* x, int64_t n, double* out);
-// out[k] = x_k . y_k for nvec vector pairs ld apart (device out, fp64 accumulation)
+// out[k] = x_k . y_k for nvec vector pairs ld apart (device out; fp64 accumulation for fp64
+// data, compensated fp32 pairs within a thread for fp32 data, fp64 across threads)
 template <typename T>
 mf_status dot_batched(mf_ctx* ctx, const T* x, const T* y, int64_t n, int64_t ld, int nvec, double* out);
 
@@ -27,6 +28,8 @@ template <typename T> mf_status pointwise_mul(mf_ctx* ctx, int64_t n, const T* d
 template <typename T>
 mf_status block_jacobi(mf_ctx* ctx, int64_t nu, int64_t np, const double* blk, const double* pinv, const T* r, T* z);
 template <typename TS, typename TD> mf_status convert(mf_ctx* ctx, int64_t n, const TS* s, TD* d);
+// velocity part only, fp32 block inverses: z_u = B^-1 r_u per node
+mf_status block_jacobi_u32(mf_ctx* ctx, int64_t nu, const float* blk, const float* r, float* z);
 
 // Batched CG pieces: nrhs systems, vectors ld apart, device scalars S[r * S_NSCAL + k]:
 // 0 rz, 1 pAp, 2 alpha, 3 beta, 4 rr, 5 rz_new, 6 active (1 = still iterating)
@@ -55,10 +58,11 @@ mf_status cheb_step(mf_ctx* ctx, int64_t n, int64_t ld, int nrhs, T* z, T* res, 
                     double c1, double c2);
 template <typename T> mf_status add_into(mf_ctx* ctx, int64_t n, int64_t ld, int nrhs, const T* d, T* z);
 
-// GMRES: h[0..k) = V^T w (V: k vectors of length n, stride ld), into device h
-mf_status multidot(mf_ctx* ctx, const double* V, int64_t ld, int k, const double* w, int64_t n, double* h);
-// w -= V h (h device, k entries); or x += V y
-mf_status multiaxpy(mf_ctx* ctx, double* V, int64_t ld, int k, const double* h, double sign, double* w, int64_t n);
+// GMRES: h[0..k) = V^T w (V: k vectors of length n, stride ld), into device h (fp64 sums)
+template <typename T> mf_status multidot(mf_ctx* ctx, const T* V, int64_t ld, int k, const T* w, int64_t n, double* h);
+// w += sign V h (h device, k entries)
+template <typename T>
+mf_status multiaxpy(mf_ctx* ctx, const T* V, int64_t ld, int k, const double* h, double sign, T* w, int64_t n);
 // splitmix64 uniform [-1,1) vector (own implementation of the published generator)
 mf_status fill_splitmix(mf_ctx* ctx, uint64_t seed, double* v, int64_t n);
 // v[list[i]] = val

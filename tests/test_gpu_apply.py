@@ -85,6 +85,27 @@ def test_oseen_q2q1(ctx):
     check_apply(P, rtol32=5e-5)
 
 
+@pytest.mark.parametrize("dtype,rtol", [("f64", 1e-12), ("f32", 2e-5)])
+def test_oseen_coupling_blocks(ctx, dtype, rtol):
+    """B^T p and B u alone against the oracle's assembled off-diagonal blocks."""
+    P = oseen(5, ctx)
+    A = P["A"].tocsr()
+    N = 3 * P["dmu"].n_dofs
+    B, BT = A[N:, :N], A[:N, N:]
+    tdt = torch.float64 if dtype == "f64" else torch.float32
+    p = syn.uniform_pm1(3, A.shape[0] - N)
+    u = syn.uniform_pm1(4, N)
+    if dtype == "f32":
+        p, u = p.astype(np.float32).astype(np.float64), u.astype(np.float32).astype(np.float64)
+    g = P["op"].coupling("grad", torch.tensor(p, dtype=tdt, device="cuda")).cpu().double().numpy()
+    ok, worst = componentwise_ok(g, BT @ p, abs(BT) @ abs(p), rtol)
+    assert ok, worst
+    assert np.all(g[np.tile(P["dmu"].dirichlet, 3)] == 0.0)
+    d = P["op"].coupling("div", torch.tensor(u, dtype=tdt, device="cuda")).cpu().double().numpy()
+    ok, worst = componentwise_ok(d, B @ u, abs(B) @ abs(u), rtol)
+    assert ok, worst
+
+
 @pytest.mark.parametrize("mode", [0, 1])
 def test_helmholtz_octree_hanging_nodes(ctx, mode):
     P = helmholtz(0, ctx, octree=band_octree(), coef_mode=mode)
