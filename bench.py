@@ -28,13 +28,17 @@ METRIC = "GDoF/s of matrix-free operator apply & %HBM roofline; CG solve time FP
 WORKLOAD = "oseen_q2q1_interface_64"
 HBM_FALLBACK_GBS = 6800.0
 FP64_PEAK_TFLOPS = 1.25      # GB300 FP64 (vector and tensor) rate of the profiling recipe's table
-# Algorithmic flops of one Oseen Q2/Q1 cell apply as each kernel variant performs it (FMA = 2):
-# component loop outside: pressure at the Gauss points and its test terms 945, three velocity
-# components x (3 value sweeps 405 + 27 Gauss points x 84) = 8019, integration sweeps and
-# scaling 1304.  Gauss-point loop outside: value sweeps 3 x 405, 27 points x 183 (pressure
-# 15, 9 gradients 45, value terms 30, symmetric stress 17, 3 test accumulations 54,
-# continuity 20, weights 2), scaling 89, integration sweeps 3 x 405.
-OSEEN_FLOPS_PER_CELL = {"component-outer": 945 + 8019 + 1304, "qpoint-outer": 1215 + 27 * 183 + 89 + 1215}
+# Algorithmic flops of one Oseen Q2/Q1 cell apply as each kernel variant performs it (FMA = 2).
+# The 1D sweeps skip the exact zeros and ones of the tables (the middle Gauss point is the middle
+# node; D[1][1] = 0): a value sweep costs 9 lines x 2 points x 5 = 90, an integration sweep
+# 9 x 10 = 90, a collocation derivative 5 (3 at the middle point), a test accumulation along one
+# line 6 (4 at the middle point).
+# Gauss-point loop outside: value sweeps 3 x 270, 27 points x 171 (pressure 15, 9 gradients 39,
+# value terms 30, symmetric stress 17, 3 test accumulations 48, continuity 20, weights 2),
+# scaling 89, integration sweeps 3 x 270 = 6326 (ncu's DFMA/DMUL/DADD counters: 6285 per cell).
+# Component loop outside: pressure at the Gauss points and its test terms 891, three velocity
+# components x (value sweeps 270 + 27 points x 80) = 7290, integration sweeps and scaling 899.
+OSEEN_FLOPS_PER_CELL = {"component-outer": 891 + 7290 + 899, "qpoint-outer": 810 + 27 * 171 + 89 + 810}
 # Algorithmic HBM bytes of one fp64 Oseen apply: read u, write v (16 B per DoF), the nodal
 # level set and convection field the coefficients come from (4 x 8 B per velocity node).
 OSEEN_BYTES_PER_VEL_NODE = 4 * 8
@@ -107,7 +111,7 @@ class ClockSampler:
 
 def kernel_hash():
     h = hashlib.sha256()
-    for f in ("apply.cu", "cellops.cuh", "scalar_local.cuh", "ops.h"):
+    for f in ("apply.cu", "apply_f64.cu", "apply_kernels.cuh", "cellops.cuh", "scalar_local.cuh", "ops.h"):
         with open(os.path.join(ROOT, "paper_2501_18781_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]

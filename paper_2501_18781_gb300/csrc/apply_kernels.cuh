@@ -359,9 +359,9 @@ __global__ void __launch_bounds__(128) k_oseen_bt(const typename Store<T>::type*
 #pragma unroll
         for (int n = 0; n < 8; ++n) pq += q1w<T>(q, n) * Pn[n];
         const T pw = Tb<T>::W3(q) * (-h * pq);
-        add_grad_test<T>(R0, qa, qb, qc, pw, T(0), T(0));
-        add_grad_test<T>(R1, qa, qb, qc, T(0), pw, T(0));
-        add_grad_test<T>(R2, qa, qb, qc, T(0), T(0), pw);
+        add_dir_test<T, 0>(R0, qa, qb, qc, pw);
+        add_dir_test<T, 1>(R1, qa, qb, qc, pw);
+        add_dir_test<T, 2>(R2, qa, qb, qc, pw);
       }
 #pragma unroll
   for (int q = 0; q < 27; ++q) { R0[q] *= h; R1[q] *= h; R2[q] *= h; }
