@@ -131,3 +131,10 @@ def heat_target_temperature(x, y, z, z_top, seed, t_base=500.0, rise=2000.0,
 def kq_field(n_values, seed, k0):
     """Per-quadrature-point conductivity k0 * (1 + 0.25 (1 + U[-1,1))), values in [k0, 1.5 k0)."""
     return k0 * (1.0 + 0.25 * (1.0 + uniform_pm1(seed, n_values)))
+
+
+def interface_temperature(x, y, z, t_base=2000.0, t_peak=3600.0, centre=(0.5, 0.5, 0.5), radius=0.2):
+    """A hot spot across the interface region of the unit-cube workloads:
+    T = t_base + (t_peak - t_base) exp(-2 |x - c|^2 / r^2), above the boiling point near c."""
+    r2 = (x - centre[0]) ** 2 + (y - centre[1]) ** 2 + (z - centre[2]) ** 2
+    return t_base + (t_peak - t_base) * np.exp(-2.0 * r2 / radius ** 2)

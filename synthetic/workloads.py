@@ -13,7 +13,15 @@ TI64 = dict(
     cp_l=1130.0, cp_g=11.3,             # J/(kg K)
     k_l=28.63, k_g=0.02863,             # W/(m K)
     t_boil=3133.0,                      # K
+    molar_mass=4.78e-2,                 # kg/mol
+    h_v=8.84e6,                         # J/kg, latent heat of evaporation
+    sticking=1.0,                       # c_s
 )
+
+# Evaporation inputs of the interface source terms: the Ti-6Al-4V values above, atmospheric
+# ambient pressure, and a Tanasawa coefficient for the linear mass-flux law.
+EVAPORATION = dict(p_amb=101325.0, h_v=TI64["h_v"], molar_mass=TI64["molar_mass"], t_boil=TI64["t_boil"],
+                   sticking=TI64["sticking"], tanasawa=1e-3)
 
 
 @dataclass(frozen=True)
