@@ -69,7 +69,8 @@ def measured_peaks():
 
 
 class ClockSampler:
-    """Samples nvidia-smi SM clocks and throttle reasons every 200 ms while running."""
+    """Samples nvidia-smi SM clocks and throttle reasons every 100 ms while running (the timed
+    region starts after the first sample has arrived)."""
     Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
          "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
@@ -80,10 +81,13 @@ class ClockSampler:
     def __enter__(self):
         try:
             self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
+            t0 = time.time()
+            while not self.rows and time.time() - t0 < 3.0:
+                time.sleep(0.01)
         except Exception:
             self.proc = None
         return self
@@ -111,7 +115,7 @@ class ClockSampler:
 
 def kernel_hash():
     h = hashlib.sha256()
-    for f in ("apply.cu", "apply_f64.cu", "apply_kernels.cuh", "cellops.cuh", "scalar_local.cuh", "ops.h"):
+    for f in ("apply_f64.cu", "apply_kernels.cuh", "cellops.cuh", "scalar_local.cuh", "df64.cuh"):
         with open(os.path.join(ROOT, "paper_2501_18781_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -399,10 +403,24 @@ def oseen_solve(ctx, op, mu, mp):
             "tol": 1e-10}
 
 
+def interface_sources_timing(ctx, op, mu, flush, reps=10):
+    """The fused interface-source kernel (evaporative dilation, cooling and hybrid recoil loads)
+    on the Oseen mesh, Knight's mass flux, a hot spot across the interface."""
+    import torch
+    import synthetic as syn
+    ev, ti = syn.EVAPORATION, syn.TI64
+    T = torch.tensor(syn.interface_temperature(*mu.coords().T), device="cuda")
+    args = (T, ev["p_amb"], ev["h_v"], ev["molar_mass"], ev["t_boil"], ti["rho_l"] * ti["cp_l"], ti["rho_g"] * ti["cp_g"])
+    op.interface_sources(*args)
+    ms = _event_ms(lambda: op.interface_sources(*args), reps, flush)
+    return {"ms": ms, "cells_per_s": mu.n_cells / ms * 1e3, "gdofs": op.n / ms / 1e6,
+            "outputs": "recoil force (3 n_u), dilation (n_p), cooling (n_u)"}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-solve", action="store_true")
@@ -504,6 +522,8 @@ def main():
                          "ms_per_step": sum(t32) / len(t32) * 1e3}
     out["df64_apply"] = {"value": n / (_event_ms(lambda: op.apply(src, dst, arith="df64"), 5, flush) / 1e3) / 1e9,
                          "unit": "GDoF/s", "note": "fp64 vectors, double-float cell arithmetic on the fp32 pipes"}
+    if rank == 0:
+        out["interface_sources"] = interface_sources_timing(ctx, op, mu, flush)
     if not args.no_solve and rank == 0:
         out["solve"] = heat_solve_comparison(ctx)
         out["oseen_solve"] = oseen_solve(ctx, op, mu, mp)

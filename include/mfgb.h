@@ -257,6 +257,41 @@ typedef struct {
   double power, radius, x0, y0, absorptivity;
 } mf_laser;
 
+/* Evaporation model of the interface source terms (Section 2.4; Section 5.2 for the mass flux
+ * and the recoil pressure). */
+typedef enum { MF_MASS_FLUX_KNIGHT = 0, MF_MASS_FLUX_TANASAWA = 1 } mf_mass_flux;
+typedef struct {
+  int mass_flux;          /* MF_MASS_FLUX_KNIGHT: mdot = 0.82 c_s p_sat(T) sqrt(M / (2 pi R T)) (eq. mDotPSat),
+                             p_sat = p_amb exp(h_v M / (R T_v) (1 - T_v / T)) (Clausius-Clapeyron);
+                             MF_MASS_FLUX_TANASAWA: mdot = tanasawa_coef (T - T_v) (eq. mDotTanasawa) */
+  double p_ambient;       /* p_amb [Pa] */
+  double latent_heat;     /* h_v [J/kg] */
+  double molar_mass;      /* M [kg/mol] */
+  double t_boil;          /* T_v [K] */
+  double sticking;        /* c_s */
+  double tanasawa_coef;   /* h_e [kg/(m^2 s K)] */
+  double gas_constant;    /* R [J/(mol K)]; <= 0: 8.314 */
+  double rhocp_liquid;    /* (rho c_p)_l, (rho c_p)_g of the arithmetic (rho c_p)(phi) */
+  double rhocp_gas;
+} mf_evaporation;
+
+/* Interface source terms of Section 2.4 as load vectors on an Oseen operator's two maps, from the
+ * operator's level set (MF_FIELD_PHI, its Heaviside and eps, rho_l, rho_g) and a nodal
+ * temperature T (fp64 device, n_u values on the velocity map), all terms at the 27 Gauss points
+ * of every cell, with delta = ||grad H(phi_h)|| (eq. delta), delta_rho = delta rho(phi) c_rho,
+ * delta_rhocp = delta (rho c_p)(phi)^2 c_rhocp (the squared weight is the one c_rhocp of eq.
+ * deltaRhoCp normalises to unit integral), n_Gamma = grad phi_h / ||grad phi_h||:
+ *   f_p[n_p]   = int mdot (1/rho_l - 1/rho_g) delta psi_i          (eq. evaporDil, continuity)
+ *   f_T[n_u]   = int -mdot h_v delta_rhocp N_i                     (eq. vapor_heat_loss, energy)
+ *   f_u[3 n_u] = int (p_An(T) delta_rho - mdot^2 (1/rho_g - 1/rho_l) delta) n_Gamma N_i
+ *                with p_An = 0.54 p_amb exp(-h_v M / R (1/T - 1/T_v))  (eqs. anisimov,
+ *                recoilPressureEvaporDil, hybrid_recoil_pressure; momentum); Dirichlet rows 0.
+ * Outputs are fp64 device vectors, overwritten; any may be NULL (skipped).  f_p and f_T have no
+ * Dirichlet rows (natural loads).  Uniform maps only; MF_EINVAL for other operator kinds or a
+ * missing level set.  Asynchronous. */
+mf_status mf_interface_sources(mf_op* op, const mf_evaporation* evaporation, const double* T, double* f_u,
+                               double* f_p, double* f_T);
+
 /* Top-face load f_i = int_{z = hi_z} q(x, y) N_i dA of eq. (laser_gauss) (beam along -z,
  * so <-n . e_L> = 1), (k+1)^2 Gauss points per face, into fp64 device dst[n_dofs]
  * (overwritten; Dirichlet rows 0).  If d_params is not NULL it receives the four load

@@ -239,6 +239,29 @@ class Operator:
         check(_lib.load().mf_oseen_coupling(self.h, w, _ptr(src), _ptr(dst), _dtype_code(src)))
         return dst
 
+    def interface_sources(self, T, p_ambient, latent_heat, molar_mass, t_boil, rhocp_liquid, rhocp_gas,
+                          mass_flux="knight", sticking=1.0, tanasawa_coef=0.0, gas_constant=8.314,
+                          outputs=("u", "p", "T")):
+        """Interface source loads of an Oseen operator from the nodal temperature T (fp64 device,
+        n_u values): dict with "u" (hybrid recoil force, 3 n_u), "p" (evaporative dilation, n_p),
+        "T" (evaporative cooling, n_u) for the requested outputs."""
+        import torch
+        ev = _lib.Evaporation()
+        ev.mass_flux = {"knight": 0, "tanasawa": 1}[mass_flux]
+        ev.p_ambient, ev.latent_heat, ev.molar_mass, ev.t_boil = p_ambient, latent_heat, molar_mass, t_boil
+        ev.sticking, ev.tanasawa_coef, ev.gas_constant = sticking, tanasawa_coef, gas_constant
+        ev.rhocp_liquid, ev.rhocp_gas = rhocp_liquid, rhocp_gas
+        nu = self.maps[0].n_dofs
+        npr = self.maps[1].n_dofs if len(self.maps) > 1 else 0   # the library rejects non-Oseen operators
+        T = T.contiguous()
+        out = {}
+        for key, size in (("u", 3 * nu), ("p", npr), ("T", nu)):
+            if key in outputs:
+                out[key] = torch.empty(size, dtype=torch.float64, device=T.device)
+        ptr = lambda k: _ptr(out[k]) if k in out else None
+        check(_lib.load().mf_interface_sources(self.h, C.byref(ev), _ptr(T), ptr("u"), ptr("p"), ptr("T")))
+        return out
+
     def laser_load(self, power, radius, x0, y0, absorptivity, derivatives=False):
         import torch
         lz = _lib.Laser(power, radius, x0, y0, absorptivity)

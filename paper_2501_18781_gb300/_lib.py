@@ -39,6 +39,13 @@ class SolveInfo(C.Structure):
                 ("lambda_max", C.c_double), ("seconds", C.c_double)]
 
 
+class Evaporation(C.Structure):
+    _fields_ = [("mass_flux", C.c_int), ("p_ambient", C.c_double), ("latent_heat", C.c_double),
+                ("molar_mass", C.c_double), ("t_boil", C.c_double), ("sticking", C.c_double),
+                ("tanasawa_coef", C.c_double), ("gas_constant", C.c_double), ("rhocp_liquid", C.c_double),
+                ("rhocp_gas", C.c_double)]
+
+
 class Laser(C.Structure):
     _fields_ = [("power", C.c_double), ("radius", C.c_double), ("x0", C.c_double), ("y0", C.c_double),
                 ("absorptivity", C.c_double)]
@@ -69,6 +76,7 @@ SIGNATURES = {
     "mf_apply": (C.c_int, [P, P, P, C.c_int, I64, C.c_int]),
     "mf_apply_transpose": (C.c_int, [P, P, P, C.c_int, I64, C.c_int]),
     "mf_oseen_coupling": (C.c_int, [P, C.c_int, P, P, C.c_int]),
+    "mf_interface_sources": (C.c_int, [P, C.POINTER(Evaporation), P, P, P, P]),
     "mf_diagonal": (C.c_int, [P, P, C.c_int]),
     "mf_dot": (C.c_int, [P, P, P, I64, I64, C.c_int, C.c_int, P]),
     "mf_dot_noalloc": (C.c_int, [P, P, I64, I64, C.c_int, C.c_int, P, P]),

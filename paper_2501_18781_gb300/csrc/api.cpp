@@ -581,6 +581,25 @@ mf_status mf_oseen_coupling(mf_op* op, int which, const void* src, void* dst, in
   MF_GUARD_END
 }
 
+mf_status mf_interface_sources(mf_op* op, const mf_evaporation* ev, const double* T, double* f_u, double* f_p,
+                               double* f_T) {
+  MF_GUARD_BEGIN
+  if (!op || !ev || !T) return fail(MF_EINVAL, "NULL argument");
+  if (op->p.kind != MF_OP_OSEEN) return fail(MF_EINVAL, "interface sources live on an Oseen operator's maps");
+  if (!op->phi) return fail(MF_EINVAL, "interface sources need MF_FIELD_PHI");
+  if (!op->map[0]->uniform) return fail(MF_EUNSUPPORTED, "interface sources on octree maps");
+  if (ev->mass_flux != MF_MASS_FLUX_KNIGHT && ev->mass_flux != MF_MASS_FLUX_TANASAWA)
+    return fail(MF_EINVAL, "unknown mass-flux model");
+  if (!(op->p.rho_l > 0 && op->p.rho_g > 0 && op->p.rho_l != op->p.rho_g))
+    return fail(MF_EINVAL, "interface sources need distinct positive rho_l, rho_g");
+  if (!(ev->rhocp_liquid > 0 && ev->rhocp_gas > 0)) return fail(MF_EINVAL, "rho c_p must be positive");
+  if (ev->mass_flux == MF_MASS_FLUX_KNIGHT && !(ev->t_boil > 0 && ev->molar_mass > 0))
+    return fail(MF_EINVAL, "Knight's mass flux needs T_v > 0 and M > 0");
+  if (!f_u && !f_p && !f_T) return MF_OK;
+  return launch_interface_sources(op->ctx, op->map[0], op->map[1], op->p, op->phi, *ev, T, f_u, f_p, f_T);
+  MF_GUARD_END
+}
+
 mf_status mf_apply_transpose(mf_op* op, const void* src, void* dst, int nrhs, int64_t ld, int dtype) {
   MF_GUARD_BEGIN
   if (!op || !src || !dst) return fail(MF_EINVAL, "NULL argument");

@@ -68,6 +68,10 @@ mf_status launch_oseen_blockdiag(mf_ctx* ctx, const mf_dofmap* mu, const mf_dofm
 // dst[dir] = src[dir] for nrhs vectors (Dirichlet identity rows)
 mf_status launch_dirichlet_copy(mf_ctx* ctx, const mf_dofmap* m, const void* src, void* dst, int nrhs, int64_t ld,
                                 int64_t offset, bool f32);
+// interface source terms (evaporative dilation, cooling, hybrid recoil) on an Oseen mesh
+mf_status launch_interface_sources(mf_ctx* ctx, const mf_dofmap* mu, const mf_dofmap* mp, const mf_op_params& p,
+                                   const double* phi, const mf_evaporation& ev, const double* T, double* fu,
+                                   double* fp, double* fT);
 // laser top-face load and its parameter derivatives (uniform maps)
 mf_status launch_laser(mf_ctx* ctx, const mf_dofmap* m, const double lz[5], double* f, double* dF);
 // dJ/dk_q = -w_q h grad(lambda) . grad(theta), [cell][27]
