@@ -165,20 +165,42 @@ def mass_matrix(dm, cells=None):
     return (dm.C.T @ A_full @ dm.C).tocsr()
 
 
-def oseen_matrix(dmu, dmp, phi, beta, sigma, rho_l, rho_g, mu_l, mu_g):
+def oseen_matrix(dmu, dmp, phi, beta, sigma, rho_l, rho_g, mu_l, mu_g, T=None, solid=None, darcy=None,
+                 trace_correction=False):
     """Linearised incompressible Navier-Stokes (Oseen) operator of eq. (momentum_balance)
     and eq. (continuity) with Q2 velocity and Q1 pressure on one uniform mesh:
-        [[ sigma M_rho + C_rho(beta) + 2 mu eps(u):eps(v),  B^T ],
-         [ B,                                               0   ]],
-        (B u, q) = -int q div u,
-    rho(phi) by eq. (rhoEff) and mu(phi) by eq. (muEff) with the tanh Heaviside.  Velocity
-    Dirichlet DoFs (all three components) get identity rows/columns."""
+        [[ (sigma rho + K) M + C_rho(beta) + int tau(u):grad v,  B^T ],
+         [ B,                                                    0   ]],
+        (B u, q) = -int q div u,  tau = 2 mu (eps(u) - tr(eps(u)) n n)  (trace_correction)
+                                  or 2 mu eps(u),
+    rho(phi) by eq. (rhoEff) and mu(phi) by eq. (muEff) with the tanh Heaviside; with ``solid``
+    (dict rho_s, mu_s, t_solidus, t_liquidus) and the nodal temperature T, the three-phase laws
+    eqs. (solid_liquid_gas_density), (solid_liquid_gas_property) with H_s(f_s(T)); with ``darcy``
+    (dict C, b) the damping of eq. (darcy_damping_force) in the dense phase, K = H K_d(f_s(T)),
+    moved to the left-hand side.  n = grad phi_h / |grad phi_h| (0 where |grad phi_h| < 1e-12/h).
+    Velocity Dirichlet DoFs (all three components) get identity rows/columns."""
     N, G, w = tensor_tables(2, 3)
     P, _, _ = tensor_tables(1, 3)
-    ph, _ = field_at_qpoints(dmu, phi)
+    ph, gph = field_at_qpoints(dmu, phi)
     H = co.heaviside_tanh(ph)
-    rho = co.reciprocal_density(H, rho_l, rho_g)
-    mu = co.arithmetic_mix(H, mu_l, mu_g)
+    if T is not None and (solid is not None or darcy is not None):
+        Tq, _ = field_at_qpoints(dmu, T)
+    if solid is not None:
+        fs = co.solid_fraction(Tq, solid["t_solidus"], solid["t_liquidus"])
+        Hs = co.heaviside_solid(fs)
+        rho = co.three_phase_density(H, Hs, solid["rho_s"], rho_l, rho_g)
+        mu = co.three_phase_mix(H, Hs, solid["mu_s"], mu_l, mu_g)
+    else:
+        rho = co.reciprocal_density(H, rho_l, rho_g)
+        mu = co.arithmetic_mix(H, mu_l, mu_g)
+    mass = sigma * rho
+    if darcy is not None:
+        fs = co.solid_fraction(Tq, darcy["t_solidus"], darcy["t_liquidus"])
+        mass = mass + H * co.darcy_coefficient(fs, darcy["C"], darcy["b"])
+    if trace_correction:
+        gn = np.sqrt(np.sum(gph ** 2, axis=-1))
+        small = gn < 1e-12 / dmu.cell_h[:, None]
+        nrm = np.where(small[..., None], 0.0, gph / np.where(small, 1.0, gn)[..., None])
     bq = np.stack([field_at_qpoints(dmu, beta[c])[0] for c in range(3)], axis=-1)
     h = dmu.cell_h
     nu, nc = dmu.n_dofs, dmu.n_cells
@@ -186,7 +208,7 @@ def oseen_matrix(dmu, dmp, phi, beta, sigma, rho_l, rho_g, mu_l, mu_g):
     for s in range(0, nc, CHUNK):
         cs = np.arange(s, min(s + CHUNK, nc))
         hc = h[cs]
-        wm = sigma * rho[cs] * w * hc[:, None] ** 3
+        wm = mass[cs] * w * hc[:, None] ** 3
         wc = rho[cs] * w * hc[:, None] ** 2
         wv = mu[cs] * w * hc[:, None]
         Mss = np.einsum("cq,qi,qj->cij", wm, N, N)
@@ -195,11 +217,16 @@ def oseen_matrix(dmu, dmp, phi, beta, sigma, rho_l, rho_g, mu_l, mu_g):
         Lap = np.einsum("cq,qid,qjd->cij", wv, G, G)
         pu = dmu.cell_points[cs]
         pp = dmp.cell_points[cs]
+        if trace_correction:
+            nG = np.einsum("cqd,qid->cqi", nrm[cs], G)           # n . grad N_i (reference)
         for c in range(3):
             for d in range(3):
                 Ae = np.einsum("cq,qi,qj->cij", wv, G[:, :, d], G[:, :, c])
                 if c == d:
                     Ae = Ae + Mss + Conv + Lap
+                if trace_correction:
+                    # -2 mu (div u)(n . grad v . n): row comp c (test N_i e_c), column comp d (N_j e_d)
+                    Ae = Ae - 2.0 * np.einsum("cq,cq,cqi,qj->cij", wv, nrm[cs][:, :, c], nG, G[:, :, d])
                 rows.append(np.repeat(pu + c * nu, 27, axis=1).ravel())
                 cols.append(np.tile(pu + d * nu, (1, 27)).ravel())
                 vals.append(Ae.ravel())

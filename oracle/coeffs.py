@@ -8,6 +8,9 @@ Readings (stated once here, listed in the design notes):
   eq. (initial_phi): d = 2 eps atanh(phi), with phi clamped to +-(1 - 2^-52).
 * k(T) = k0 (1 + 0.5 T / T_b) is the temperature law of the heat workloads (the paper
   keeps properties temperature independent; it is a workload input, not a paper law).
+* Darcy damping acts in the dense phase only: K_eff = H_phi K(f_s(T)).  Eq. (darcy_damping_force)
+  computes f_s from T everywhere, but the solid fraction is defined "in the dense part of the
+  domain" (Section 3.1), and cold gas must not be frozen.
 """
 import numpy as np
 
@@ -57,3 +60,29 @@ def laser_flux_parameter_derivatives(x, y, power, radius, x0, y0, absorptivity):
                      q * (-2.0 / radius + 4.0 * r2 / radius ** 3),
                      4.0 * q * (x - x0) / radius ** 2,
                      4.0 * q * (y - y0) / radius ** 2])
+
+
+def solid_fraction(T, t_solidus, t_liquidus):
+    """Eq. (solid_fraction): 1 below T_s, 0 above T_l, linear (T_l - T)/(T_l - T_s) between."""
+    return np.clip((t_liquidus - T) / (t_liquidus - t_solidus), 0.0, 1.0)
+
+
+def heaviside_solid(fs):
+    """Eq. (heaviside_sl): H_s = 3 f_s^2 - 2 f_s^3."""
+    return 3.0 * fs * fs - 2.0 * fs * fs * fs
+
+
+def three_phase_mix(H, Hs, a_solid, a_liquid, a_gas):
+    """Eq. (solid_liquid_gas_property): H (H_s a_s + (1 - H_s) a_l) + (1 - H) a_g."""
+    return H * (Hs * a_solid + (1.0 - Hs) * a_liquid) + (1.0 - H) * a_gas
+
+
+def three_phase_density(H, Hs, rho_solid, rho_liquid, rho_gas):
+    """Eq. (solid_liquid_gas_density): 1/rho = H / rho_sl + (1 - H) / rho_g, rho_sl = H_s rho_s + (1 - H_s) rho_l."""
+    rho_sl = Hs * rho_solid + (1.0 - Hs) * rho_liquid
+    return 1.0 / (H / rho_sl + (1.0 - H) / rho_gas)
+
+
+def darcy_coefficient(fs, C, b):
+    """Magnitude of eq. (darcy_damping_force)'s K: C f_s^2 / ((1 - f_s)^3 + b) (the force is -that u)."""
+    return C * fs * fs / ((1.0 - fs) ** 3 + b)
