@@ -135,7 +135,23 @@ typedef struct {
   double rhocp, dt, k0, t_boil;                 /* heat */
   double sigma, rho_l, rho_g, mu_l, mu_g;       /* Oseen */
   double dtau;                                  /* reinit */
+  /* Oseen melt-pool extensions, switched on by oseen_flags (they need MF_FIELD_T_PREV, the nodal
+   * absolute temperature on the velocity map, for the solid fraction f_s(T) of eq. solid_fraction):
+   * MF_OSEEN_THREE_PHASE: rho and mu by eqs. (solid_liquid_gas_density), (solid_liquid_gas_property)
+   *   with H_s = 3 f_s^2 - 2 f_s^3 (eq. heaviside_sl) and the solid rho_s, mu_s;
+   * MF_OSEEN_DARCY: the damping force of eq. (darcy_damping_force) moved to the left-hand side,
+   *   + int H_phi C f_s^2 / ((1 - f_s)^3 + b) u . v (dense phase only);
+   * MF_OSEEN_TRACE_CORRECTION: viscous stress 2 mu (eps(u) - tr(eps(u)) n n) of Section 2.1,
+   *   n = grad phi_h / |grad phi_h| (0 where |grad phi_h| < 1e-12/h); the operator is then
+   *   nonsymmetric and its block-Jacobi blocks leave the correction out.
+   * Any flag selects the Gauss-point-outer kernel; double-float applies reject the flags. */
+  double rho_s, mu_s, t_solidus, t_liquidus;
+  double darcy_c, darcy_b;
+  int oseen_flags;
+  int reserved2;
 } mf_op_params;
+
+enum { MF_OSEEN_THREE_PHASE = 1, MF_OSEEN_DARCY = 2, MF_OSEEN_TRACE_CORRECTION = 4 };
 
 typedef enum {
   MF_FIELD_PHI = 0,      /* nodal level set on map 0 (n_dofs values) */

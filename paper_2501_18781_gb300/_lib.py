@@ -12,6 +12,7 @@ MF_HEAVISIDE_TANH, MF_HEAVISIDE_SINE = 0, 1
 MF_COEF_INKERNEL, MF_COEF_QPOINT = 0, 1
 MF_FIELD_PHI, MF_FIELD_T_PREV, MF_FIELD_BETA, MF_FIELD_K_QPOINT = 0, 1, 2, 3
 MF_SOLVER_CG, MF_SOLVER_GMRES, MF_SOLVER_DEFECT_CORRECTION = 0, 1, 2
+MF_OSEEN_THREE_PHASE, MF_OSEEN_DARCY, MF_OSEEN_TRACE_CORRECTION = 1, 2, 4
 MF_PREC_NONE, MF_PREC_JACOBI, MF_PREC_CHEBYSHEV, MF_PREC_BLOCK_JACOBI, MF_PREC_BLOCK_TRIANGULAR = 0, 1, 2, 3, 4
 
 STATUS_NAMES = {0: "MF_OK", -1: "MF_EINVAL", -2: "MF_ENOMEM", -3: "MF_ECUDA", -4: "MF_ENOTCONV",
@@ -23,7 +24,9 @@ class OpParams(C.Structure):
                 ("eps", C.c_double), ("mass_coef", C.c_double), ("a_liquid", C.c_double), ("a_gas", C.c_double),
                 ("rhocp", C.c_double), ("dt", C.c_double), ("k0", C.c_double), ("t_boil", C.c_double),
                 ("sigma", C.c_double), ("rho_l", C.c_double), ("rho_g", C.c_double), ("mu_l", C.c_double),
-                ("mu_g", C.c_double), ("dtau", C.c_double)]
+                ("mu_g", C.c_double), ("dtau", C.c_double), ("rho_s", C.c_double), ("mu_s", C.c_double),
+                ("t_solidus", C.c_double), ("t_liquidus", C.c_double), ("darcy_c", C.c_double),
+                ("darcy_b", C.c_double), ("oseen_flags", C.c_int), ("reserved2", C.c_int)]
 
 
 class SolverParams(C.Structure):

@@ -294,6 +294,17 @@ mf_status mf_operator_create(mf_ctx* c, const mf_op_params* p, const mf_dofmap* 
   } else {
     if (nmaps != 1 || !is_q2(maps[0])) return fail(MF_EINVAL, "scalar operators need one Q2 map");
   }
+  if (p->oseen_flags) {
+    if (p->kind != MF_OP_OSEEN) return fail(MF_EINVAL, "oseen_flags apply to the Oseen operator");
+    if (p->oseen_flags & ~(MF_OSEEN_THREE_PHASE | MF_OSEEN_DARCY | MF_OSEEN_TRACE_CORRECTION))
+      return fail(MF_EINVAL, "unknown oseen_flags bit");
+    if ((p->oseen_flags & (MF_OSEEN_THREE_PHASE | MF_OSEEN_DARCY)) && !(p->t_liquidus > p->t_solidus))
+      return fail(MF_EINVAL, "the solid fraction needs t_liquidus > t_solidus");
+    if ((p->oseen_flags & MF_OSEEN_THREE_PHASE) && !(p->rho_s > 0 && p->mu_s >= 0))
+      return fail(MF_EINVAL, "three-phase coefficients need rho_s > 0 and mu_s >= 0");
+    if ((p->oseen_flags & MF_OSEEN_DARCY) && !(p->darcy_b > 0 && p->darcy_c >= 0))
+      return fail(MF_EINVAL, "Darcy damping needs b > 0 and C >= 0");
+  }
   if (p->heaviside != 0 && p->heaviside != 1) return fail(MF_EINVAL, "heaviside must be 0 or 1");
   if (p->heaviside == 1 && !(p->eps > 0)) return fail(MF_EINVAL, "sine Heaviside needs eps > 0");
   auto* op = new mf_op();
@@ -389,6 +400,8 @@ mf_status check_fields(const mf_op* op) {
       break;
     case MF_OP_OSEEN:
       if (!op->phi || !op->beta) return fail(MF_EINVAL, "Oseen needs MF_FIELD_PHI and MF_FIELD_BETA");
+      if ((op->p.oseen_flags & (MF_OSEEN_THREE_PHASE | MF_OSEEN_DARCY)) && !op->tprev)
+        return fail(MF_EINVAL, "three-phase / Darcy terms need MF_FIELD_T_PREV (nodal temperature)");
       break;
     case MF_OP_REINIT:
       if (!op->phi) return fail(MF_EINVAL, "reinit needs MF_FIELD_PHI");
@@ -412,6 +425,16 @@ mf_status ensure_tables(mf_op* op) {
     MF_TRY(launch_oseen_qtables(op->ctx, op->map[0], op->phi, op->beta, p.rho_l, p.rho_g, p.mu_l, p.mu_g, p.heaviside,
                                 p.eps, op->rho64.as<double>(), op->rho32.as<float>(), op->mu64.as<double>(),
                                 op->mu32.as<float>(), op->qvec64.as<double>(), op->qvec32.as<float>()));
+    if (p.oseen_flags) {
+      MF_TRY(op->kd64.alloc(sizeof(double) * 27 * nc));
+      MF_TRY(op->kd32.alloc(sizeof(float) * 27 * nc));
+      MF_TRY(op->nrm64.alloc(sizeof(double) * 81 * nc));
+      MF_TRY(op->nrm32.alloc(sizeof(float) * 81 * nc));
+      MF_TRY(launch_oseen_ext_tables(op->ctx, op->map[0], p, op->phi, op->tprev, op->rho64.as<double>(),
+                                     op->rho32.as<float>(), op->mu64.as<double>(), op->mu32.as<float>(),
+                                     op->kd64.as<double>(), op->kd32.as<float>(), op->nrm64.as<double>(),
+                                     op->nrm32.as<float>()));
+    }
   } else {
     const int kind = scalar_kind(op);
     MF_TRY(op->qcoef64.alloc(sizeof(double) * 27 * nc));
@@ -468,7 +491,12 @@ template <typename T> OseenArgs<T> oseen_args(const mf_op* op, const T* src, T* 
   a.mu = f32 ? reinterpret_cast<const T*>(op->mu32.as<float>()) : reinterpret_cast<const T*>(op->mu64.as<double>());
   a.beta = f32 ? reinterpret_cast<const T*>(op->qvec32.as<float>()) : reinterpret_cast<const T*>(op->qvec64.as<double>());
   a.sigma = T(op->p.sigma);
-  a.qouter = op->oseen_qouter64;
+  a.ext = op->p.oseen_flags ? 1 : 0;
+  a.qouter = a.ext ? 1 : op->oseen_qouter64;  // the extensions exist in the Gauss-point-outer kernel
+  a.kd = a.ext ? (f32 ? reinterpret_cast<const T*>(op->kd32.as<float>()) : reinterpret_cast<const T*>(op->kd64.as<double>()))
+               : nullptr;
+  a.nrm = a.ext ? (f32 ? reinterpret_cast<const T*>(op->nrm32.as<float>()) : reinterpret_cast<const T*>(op->nrm64.as<double>()))
+                : nullptr;
   return a;
 }
 template OseenArgs<double> oseen_args<double>(const mf_op*, const double*, double*);
@@ -492,6 +520,7 @@ mf_status apply_impl(mf_op* op, const T* src, T* dst, int nrhs, int64_t ld, bool
   const char* pname = f32 ? "/f32" : (df ? "/df64" : "/f64");
   if (op->p.kind == MF_OP_OSEEN) {
     if (transpose) return fail(MF_EUNSUPPORTED, "transpose of the Oseen operator");
+    if (df && op->p.oseen_flags) return fail(MF_EUNSUPPORTED, "double-float Oseen applies without the melt-pool terms");
     const int64_t nu = op->map[0]->n_dofs;
     for (int r = 0; r < nrhs; ++r) {
       OseenArgs<T> a = oseen_args<T>(op, src + r * ld, dst + r * ld);
@@ -500,7 +529,8 @@ mf_status apply_impl(mf_op* op, const T* src, T* dst, int nrhs, int64_t ld, bool
         MF_TRY(launch_dirichlet_copy(c, op->map[0], src + r * ld, dst + r * ld, 1, ld, comp * nu, f32));
     }
     op->variant = std::string("oseen_q2q1") + pname + "/tabulated" +
-                  ((f32 || op->oseen_qouter64) ? "/qpoint-outer" : "/component-outer");
+                  ((f32 || op->oseen_qouter64 || op->p.oseen_flags) ? "/qpoint-outer" : "/component-outer") +
+                  (op->p.oseen_flags ? "/meltpool" : "");
     return MF_OK;
   }
   const int kind = scalar_kind(op);

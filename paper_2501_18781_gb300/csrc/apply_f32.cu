@@ -12,7 +12,10 @@ mf_status launch_oseen_apply_f32(mf_ctx* ctx, const mf_dofmap* mu, const OseenAr
   MF_CUDA_TRY(upload_tables_here());
   UniformGeom ug = uniform_geom(mu);
   // fp32: all three velocity components fit in registers (Gauss-point loop outside)
-  k_oseen_qouter<float><<<brick_blocks(ug.nx, ug.ny, ug.nz), 128, 0, ctx->stream>>>(a, ug);
+  if (a.ext)
+    k_oseen_qouter<float, true><<<brick_blocks(ug.nx, ug.ny, ug.nz), 128, 0, ctx->stream>>>(a, ug);
+  else
+    k_oseen_qouter<float><<<brick_blocks(ug.nx, ug.ny, ug.nz), 128, 0, ctx->stream>>>(a, ug);
   ctx->launches++;
   MF_CUDA_TRY(cudaGetLastError());
   return MF_OK;

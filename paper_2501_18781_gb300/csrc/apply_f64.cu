@@ -11,7 +11,9 @@ mf_status launch_scalar_apply_f64(mf_ctx* ctx, const mf_dofmap* m, int kind, int
 mf_status launch_oseen_apply_f64(mf_ctx* ctx, const mf_dofmap* mu, const OseenArgs<double>& a) {
   MF_CUDA_TRY(upload_tables_here());
   UniformGeom ug = uniform_geom(mu);
-  if (a.qouter)  // fewer fp64 operations per cell, at the price of register spills
+  if (a.ext)  // melt-pool terms (three-phase tables, Darcy, trace correction)
+    k_oseen_qouter<double, true><<<brick_blocks(ug.nx, ug.ny, ug.nz), 128, 0, ctx->stream>>>(a, ug);
+  else if (a.qouter)  // fewer fp64 operations per cell, at the price of register spills
     k_oseen_qouter<double><<<brick_blocks(ug.nx, ug.ny, ug.nz), 128, 0, ctx->stream>>>(a, ug);
   else
     k_oseen<double><<<brick_blocks(ug.nx, ug.ny, ug.nz), 128, 0, ctx->stream>>>(a, ug);

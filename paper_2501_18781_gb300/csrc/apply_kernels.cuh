@@ -245,7 +245,9 @@ __global__ void __launch_bounds__(128, 1) k_oseen(OseenArgs<typename Store<T>::t
 // The same Oseen cell operator with the Gauss-point loop outside: all three velocity
 // components sit in registers at once (81 values + 81 accumulators), so each Gauss point's
 // rho, mu and beta are read once instead of once per component.  Fits the fp32 register file.
-template <typename T>
+// EXT adds the melt-pool terms: the Darcy coefficient kd (a mass-like term kd u . v) and the
+// trace correction -2 mu tr(eps(u)) n n of the viscous stress, both read per Gauss point.
+template <typename T, bool EXT = false>
 __global__ void __launch_bounds__(128) k_oseen_qouter(OseenArgs<typename Store<T>::type> A, UniformGeom ug) {
   using St = typename Store<T>::type;
   int i, j, k;
@@ -301,9 +303,27 @@ __global__ void __launch_bounds__(128) k_oseen_qouter(OseenArgs<typename Store<T
         R2[q] += rw * (sh2 * U2[q] + h * (bx * g[2][0] + by * g[2][1] + bz * g[2][2]));
         // gradient test: mu (grad u + grad u^T) - p I (both scaled by the weight)
         const T pw = w * (-h * pq);
-        const T s00 = c1 * (g[0][0] + g[0][0]) + pw, s11 = c1 * (g[1][1] + g[1][1]) + pw,
-                s22 = c1 * (g[2][2] + g[2][2]) + pw;
-        const T s01 = c1 * (g[0][1] + g[1][0]), s02 = c1 * (g[0][2] + g[2][0]), s12 = c1 * (g[1][2] + g[2][1]);
+        T s00 = c1 * (g[0][0] + g[0][0]) + pw, s11 = c1 * (g[1][1] + g[1][1]) + pw, s22 = c1 * (g[2][2] + g[2][2]) + pw;
+        T s01 = c1 * (g[0][1] + g[1][0]), s02 = c1 * (g[0][2] + g[2][0]), s12 = c1 * (g[1][2] + g[2][1]);
+        if constexpr (EXT) {
+          // Darcy: w h^3 kd u = h (w kd h^2 u)
+          const T kw = w * from_store<T>(__ldg(A.kd + q * nc + cell)) * h * h;
+          R0[q] += kw * U0[q];
+          R1[q] += kw * U1[q];
+          R2[q] += kw * U2[q];
+          // trace correction: -2 mu (div u) n n (div in reference units, like g)
+          const T nx = from_store<T>(__ldg(A.nrm + q * nc + cell));
+          const T ny = from_store<T>(__ldg(A.nrm + (27 + q) * nc + cell));
+          const T nz = from_store<T>(__ldg(A.nrm + (54 + q) * nc + cell));
+          const T t = T(-2) * c1 * (g[0][0] + g[1][1] + g[2][2]);
+          const T tx = t * nx, ty = t * ny, tz = t * nz;
+          s00 += tx * nx;
+          s11 += ty * ny;
+          s22 += tz * nz;
+          s01 += tx * ny;
+          s02 += tx * nz;
+          s12 += ty * nz;
+        }
         add_grad_test<T>(R0, qa, qb, qc, s00, s01, s02);
         add_grad_test<T>(R1, qa, qb, qc, s01, s11, s12);
         add_grad_test<T>(R2, qa, qb, qc, s02, s12, s22);

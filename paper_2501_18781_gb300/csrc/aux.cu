@@ -142,6 +142,71 @@ __global__ void k_oseen_qtables(UniformGeom ug, const double* phi, const double*
   }
 }
 
+// Melt-pool extensions of the Oseen tables, evaluated in fp64 at the Gauss points from the nodal
+// phi and T: three-phase rho and mu (eqs. solid_liquid_gas_density, solid_liquid_gas_property with
+// H_s of eq. heaviside_sl), the Darcy coefficient H_phi C f_s^2 / ((1 - f_s)^3 + b) of eq.
+// (darcy_damping_force) and the unit normal grad phi_h / |grad phi_h| of the trace correction.
+__global__ void k_oseen_ext_tables(UniformGeom ug, const double* phi, const double* T, int hv, double eps, int flags,
+                                   double rho_l, double rho_g, double rho_s, double mu_l, double mu_g, double mu_s,
+                                   double t_sol, double t_liq, double dc, double db, double* r64, float* r32,
+                                   double* m64, float* m32, double* kd64, float* kd32, double* n64, float* n32) {
+  Loc L;
+  OctGeom og{};
+  const int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (!natural_cell<false>(ug, og, t, L)) return;
+  const int64_t nc = int64_t(ug.nx) * ug.ny * ug.nz;
+  const bool need_t = (flags & (MF_OSEEN_THREE_PHASE | MF_OSEEN_DARCY)) != 0;
+  double P[27], TT[27];
+  gather64<false, false>(ug, og, L, phi, P);
+  to_qpoints<double>(P);
+  if (need_t) {
+    gather64<false, false>(ug, og, L, T, TT);
+    to_qpoints<double>(TT);
+  }
+  for (int qc = 0; qc < 3; ++qc)
+    for (int qb = 0; qb < 3; ++qb)
+      for (int qa = 0; qa < 3; ++qa) {
+        const int q = qa + 3 * qb + 9 * qc;
+        const int64_t o = q * nc + L.cell;
+        const double H = heaviside<double>(P[q], hv, eps);
+        double fs = 0.0;
+        if (need_t) {
+          fs = (t_liq - TT[q]) / (t_liq - t_sol);
+          fs = fs < 0.0 ? 0.0 : (fs > 1.0 ? 1.0 : fs);
+        }
+        if (flags & MF_OSEEN_THREE_PHASE) {
+          const double Hs = 3.0 * fs * fs - 2.0 * fs * fs * fs;
+          const double rho_sl = Hs * rho_s + (1.0 - Hs) * rho_l;
+          const double rho = 1.0 / (H / rho_sl + (1.0 - H) / rho_g);
+          const double mu = H * (Hs * mu_s + (1.0 - Hs) * mu_l) + (1.0 - H) * mu_g;
+          r64[o] = rho;
+          r32[o] = float(rho);
+          m64[o] = mu;
+          m32[o] = float(mu);
+        }
+        const double kd = (flags & MF_OSEEN_DARCY) ? H * dc * fs * fs / ((1.0 - fs) * (1.0 - fs) * (1.0 - fs) + db) : 0.0;
+        kd64[o] = kd;
+        kd32[o] = float(kd);
+        double nx = 0.0, ny = 0.0, nz = 0.0;
+        if (flags & MF_OSEEN_TRACE_CORRECTION) {
+          double gx, gy, gz;
+          grad_at<double>(P, qa, qb, qc, gx, gy, gz);  // reference gradient = h grad phi_h
+          const double g = sqrt(gx * gx + gy * gy + gz * gz);
+          if (!(g < 1e-12)) {
+            nx = gx / g;
+            ny = gy / g;
+            nz = gz / g;
+          }
+        }
+        n64[o] = nx;
+        n64[27 * nc + o] = ny;
+        n64[54 * nc + o] = nz;
+        n32[o] = float(nx);
+        n32[27 * nc + o] = float(ny);
+        n32[54 * nc + o] = float(nz);
+      }
+}
+
 // ---------------------------------------------------------------- diagonals
 // out[l] += sum_q c[q] X[qa][a] Y[qb][b] Z[qc][c] with 1D tables X, Y, Z (3x3, [q][a]).
 __device__ __forceinline__ void separable_add(const double* c, const double* X, const double* Y, const double* Z,
@@ -291,7 +356,9 @@ __global__ void k_oseen_blocks(OseenArgs<double> A, UniformGeom ug, double* blk,
   double s[27], c[27];
   for (int i = 0; i < 27; ++i) s[i] = 0.0;
   // scalar part: sigma rho mass + rho convection + mu |grad|^2
-  for (int q = 0; q < 27; ++q) c[q] = cW364[q] * h * h * h * A.sigma * A.rho[q * nc + L.cell];
+  // mass-like part: sigma rho (+ the Darcy coefficient of the melt-pool extension)
+  for (int q = 0; q < 27; ++q)
+    c[q] = cW364[q] * h * h * h * (A.sigma * A.rho[q * nc + L.cell] + (A.ext ? A.kd[q * nc + L.cell] : 0.0));
   separable_add(c, cSS64, cSS64, cSS64, s);
   for (int d = 0; d < 3; ++d) {
     for (int q = 0; q < 27; ++q) c[q] = cW364[q] * h * h * A.rho[q * nc + L.cell] * A.beta[(d * 27 + q) * nc + L.cell];
@@ -332,7 +399,7 @@ __global__ void k_oseen_blocks(OseenArgs<double> A, UniformGeom ug, double* blk,
       const double psi = pa * pb * pc;
       const double g2 = pb * pb * pc * pc + pa * pa * pc * pc + pa * pa * pb * pb;  // |psi'|^2 with P' = -+1
       m += cW364[q] * h * h * h * psi * psi / A.mu[q * nc + L.cell];
-      kk += cW364[q] * h * g2 / (A.sigma * A.rho[q * nc + L.cell]);
+      kk += cW364[q] * h * g2 / (A.sigma * A.rho[q * nc + L.cell] + (A.ext ? A.kd[q * nc + L.cell] : 0.0));
     }
     const int64_t id = pbase + a + px * b + pxy * cc;
     atomicAdd(pm + id, m);
@@ -456,6 +523,19 @@ mf_status launch_oseen_qtables(mf_ctx* ctx, const mf_dofmap* mu, const double* p
   UniformGeom ug = uniform_geom(mu);
   k_oseen_qtables<<<blocks(mu->n_cells, 128), 128, 0, ctx->stream>>>(ug, phi, beta, rho_l, rho_g, mu_l, mu_g, hv, eps,
                                                                       r64, r32, m64, m32, b64, b32);
+  ctx->launches++;
+  MF_CUDA_TRY(cudaGetLastError());
+  return MF_OK;
+}
+
+mf_status launch_oseen_ext_tables(mf_ctx* ctx, const mf_dofmap* mu, const mf_op_params& p, const double* phi,
+                                  const double* T, double* rho64, float* rho32, double* muq64, float* muq32,
+                                  double* kd64, float* kd32, double* nrm64, float* nrm32) {
+  MF_CUDA_TRY(upload_tables_here());
+  UniformGeom ug = uniform_geom(mu);
+  k_oseen_ext_tables<<<blocks(mu->n_cells, 128), 128, 0, ctx->stream>>>(
+      ug, phi, T, p.heaviside, p.eps, p.oseen_flags, p.rho_l, p.rho_g, p.rho_s, p.mu_l, p.mu_g, p.mu_s, p.t_solidus,
+      p.t_liquidus, p.darcy_c, p.darcy_b, rho64, rho32, muq64, muq32, kd64, kd32, nrm64, nrm32);
   ctx->launches++;
   MF_CUDA_TRY(cudaGetLastError());
   return MF_OK;

@@ -43,6 +43,11 @@ template <typename T> struct OseenArgs {
   const T* beta;    // [3][27][ncells]
   T sigma;
   int qouter;       // 1: Gauss-point loop outside the velocity components (autotuned variant)
+  // melt-pool extensions (ext = 1): extra mass coefficient (Darcy) and interface normal per Gauss
+  // point; kd and nrm hold zeros for a term that is switched off
+  int ext;
+  const T* kd;      // [27][ncells]
+  const T* nrm;     // [3][27][ncells]
 };
 
 // scalar apply: kind, coefficient mode (0 in-kernel, 1 tabulated), convection, transpose
@@ -59,6 +64,10 @@ mf_status launch_scalar_qtables(mf_ctx* ctx, const mf_dofmap* m, int kind, const
 mf_status launch_oseen_qtables(mf_ctx* ctx, const mf_dofmap* mu, const double* phi, const double* beta, double rho_l,
                                double rho_g, double mu_l, double mu_g, int heaviside, double eps, double* rho64,
                                float* rho32, double* muq64, float* muq32, double* beta64, float* beta32);
+// melt-pool extension tables (three-phase rho/mu overwrite the two-phase ones; Darcy mass; normal)
+mf_status launch_oseen_ext_tables(mf_ctx* ctx, const mf_dofmap* mu, const mf_op_params& p, const double* phi,
+                                  const double* T, double* rho64, float* rho32, double* muq64, float* muq32,
+                                  double* kd64, float* kd32, double* nrm64, float* nrm32);
 // diagonal (scalar ops) in fp64 from tabulated coefficients
 mf_status launch_scalar_diag(mf_ctx* ctx, const mf_dofmap* m, int kind, bool beta, const ScalarArgs<double>& a,
                              double* diag);
@@ -96,6 +105,7 @@ struct mf_op {
   mf::DevBuf qcoef64, qcoef32;    // [27][ncells]
   mf::DevBuf qvec64, qvec32;      // [3][27][ncells]
   mf::DevBuf rho64, rho32, mu64, mu32;  // Oseen
+  mf::DevBuf kd64, kd32, nrm64, nrm32;  // Oseen melt-pool extensions
   mf::DevBuf diag64;              // cached diagonal (fp64)
   mf::DevBuf blk64, pdiag64;      // Oseen block Jacobi
   bool tables_ready = false;

@@ -1,0 +1,91 @@
+"""The Oseen operator with the melt-pool terms (three-phase density and viscosity, Darcy damping,
+trace-corrected viscous stress) on the GPU against the oracle's assembled matrix."""
+import numpy as np
+import pytest
+
+import synthetic as syn
+from oracle import assemble as asm
+from oracle import mesh as omesh
+from problems import OSEEN_FACES, componentwise_ok
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+TS, TL = 1933.0, 2200.0
+SOLID = dict(rho_s=5000.0, mu_s=2e-2, t_solidus=TS, t_liquidus=TL)
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_2501_18781_gb300 import Context, build_library
+    build_library()
+    return Context(0)
+
+
+def meltpool(n, ctx, flags, darcy_c=1e6):
+    from paper_2501_18781_gb300 import DofMap, Mesh, Operator
+    from paper_2501_18781_gb300._lib import MF_OSEEN_DARCY, MF_OSEEN_THREE_PHASE, MF_OSEEN_TRACE_CORRECTION
+    wl = syn.scaled(syn.OSEEN_INTERFACE, n)
+    p = wl.params
+    dmu = omesh.uniform_dofmap(n, wl.lo, wl.hi, 2, OSEEN_FACES)
+    dmp = omesh.uniform_dofmap(n, wl.lo, wl.hi, 1, 0)
+    x = dmu.dof_coords()
+    t1, t2 = syn.wavy_plane_phases(wl.seed)
+    phi = syn.initial_level_set(syn.wavy_plane_distance(*x.T, t1, t2), wl.eps)
+    beta = np.array(syn.convection_field(*x.T, wl.seed, wl.lo, wl.hi))
+    T = syn.interface_temperature(*x.T, t_base=1500.0)   # solid far away, melt and vapour near the spot
+    sigma = 1.0 / (p["dt_cfl"] * wl.h)
+    darcy = dict(C=darcy_c, b=1.0, t_solidus=TS, t_liquidus=TL)
+    A = asm.oseen_matrix(dmu, dmp, phi, beta, sigma, p["rho_l"], p["rho_g"], p["mu_l"], p["mu_g"], T=T,
+                         solid=SOLID if "three" in flags else None, darcy=darcy if "darcy" in flags else None,
+                         trace_correction="trace" in flags)
+    bits = (MF_OSEEN_THREE_PHASE if "three" in flags else 0) | (MF_OSEEN_DARCY if "darcy" in flags else 0) | \
+        (MF_OSEEN_TRACE_CORRECTION if "trace" in flags else 0)
+    mesh = Mesh.uniform(ctx, n, wl.lo, wl.hi)
+    mu_, mp_ = DofMap(mesh, 2, OSEEN_FACES), DofMap(mesh, 1, 0)
+    op = Operator(ctx, "oseen", [mu_, mp_], sigma=sigma, rho_l=p["rho_l"], rho_g=p["rho_g"], mu_l=p["mu_l"],
+                  mu_g=p["mu_g"], eps=wl.eps, rho_s=SOLID["rho_s"], mu_s=SOLID["mu_s"], t_solidus=TS, t_liquidus=TL,
+                  darcy_c=darcy_c, darcy_b=1.0, oseen_flags=bits)
+    op.set_field("phi", torch.tensor(phi, device="cuda"))
+    op.set_field("beta", torch.tensor(beta.ravel(), device="cuda"))
+    op.set_field("t_prev", torch.tensor(T, device="cuda"))
+    return dict(A=A, op=op, n=A.shape[0], dmu=dmu, dmp=dmp)
+
+
+@pytest.mark.parametrize("flags", [("three",), ("darcy",), ("trace",), ("three", "darcy", "trace")])
+def test_meltpool_oseen_apply_matches_oracle(ctx, flags):
+    P = meltpool(5, ctx, flags)
+    u = syn.uniform_pm1(5, P["n"])
+    ref = P["A"] @ u
+    bound = abs(P["A"]) @ np.abs(u)
+    v = P["op"].apply(torch.tensor(u, device="cuda")).cpu().numpy()
+    ok, worst = componentwise_ok(v, ref, bound, 1e-12)
+    assert ok, (flags, worst)
+    u32 = u.astype(np.float32)
+    v32 = P["op"].apply(torch.tensor(u32, device="cuda")).cpu().numpy().astype(np.float64)
+    ok, worst = componentwise_ok(v32, P["A"] @ u32.astype(np.float64), abs(P["A"]) @ np.abs(u32.astype(np.float64)),
+                                 5e-5)
+    assert ok, (flags, "fp32", worst)
+    assert "meltpool" in P["op"].variant
+
+
+def test_meltpool_oseen_solve_with_block_preconditioner(ctx):
+    P = meltpool(6, ctx, ("three", "darcy", "trace"))
+    b = syn.uniform_pm1(6, P["n"])
+    b[np.concatenate([np.tile(P["dmu"].dirichlet, 3), np.zeros(P["dmp"].n_dofs, bool)])] = 0.0
+    x, info = P["op"].solve(torch.tensor(b, device="cuda"), solver="gmres", precond="block_triangular", restart=50,
+                            maxit=600, tol=1e-10)
+    assert info["status"] == 0, info
+    res = np.linalg.norm(b - P["A"] @ x.cpu().numpy()) / np.linalg.norm(b)
+    assert res <= 1e-10 * (1 + 1e-3), (res, info)
+
+
+def test_meltpool_rejects_double_float_and_missing_temperature(ctx):
+    from paper_2501_18781_gb300._lib import MFError
+    P = meltpool(3, ctx, ("darcy",))
+    u = torch.tensor(syn.uniform_pm1(1, P["n"]), device="cuda")
+    with pytest.raises(MFError):
+        P["op"].apply(u, arith="df64")
