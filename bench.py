@@ -403,6 +403,62 @@ def oseen_solve(ctx, op, mu, mp):
             "tol": 1e-10}
 
 
+def meltpool_oseen(ctx, n, flush, darcy_c=None):
+    """The Oseen workload with the melt-pool terms switched on (three-phase rho/mu, Darcy damping,
+    trace-corrected stress) and a hot spot across the interface.  The paper damps with C = 1e12
+    kg/(m^3 s) at a time step of 0.01 us (rho_l / dt = 4.1e11): C / (rho_l sigma) = 2.45.  The
+    unit-cube workload has sigma = 1/dt = 2n, so C is scaled to keep that ratio (C = 1e12 * 1e-8 *
+    sigma); the unscaled 1e12 makes even a direct solve stall at a 1e-7 relative residual here.
+    Solid below T_s far from the spot.  fp64 and fp32 apply rates and the FGMRES solve to 1e-10 with
+    the interface source loads as right-hand side."""
+    import numpy as np
+    import torch
+    import synthetic as syn
+    from paper_2501_18781_gb300 import DofMap, Mesh, Operator
+    from paper_2501_18781_gb300._lib import MF_OSEEN_DARCY, MF_OSEEN_THREE_PHASE, MF_OSEEN_TRACE_CORRECTION
+    wl = syn.scaled(syn.OSEEN_INTERFACE, n)
+    p = wl.params
+    mesh = Mesh.uniform(ctx, n, wl.lo, wl.hi)
+    mu, mp = DofMap(mesh, 2, 0b011111), DofMap(mesh, 1, 0)
+    x = mu.coords()
+    t1, t2 = syn.wavy_plane_phases(wl.seed)
+    phi = syn.initial_level_set(syn.wavy_plane_distance(*x.T, t1, t2), wl.eps)
+    beta = np.array(syn.convection_field(*x.T, wl.seed, wl.lo, wl.hi))
+    T = syn.interface_temperature(*x.T, t_base=1500.0)
+    sigma = 1.0 / (p["dt_cfl"] * wl.h)
+    if darcy_c is None:
+        darcy_c = 1e12 * 1e-8 * sigma
+    op = Operator(ctx, "oseen", [mu, mp], sigma=sigma, rho_l=p["rho_l"], rho_g=p["rho_g"],
+                  mu_l=p["mu_l"], mu_g=p["mu_g"], eps=wl.eps, rho_s=p["rho_l"], mu_s=p["mu_l"], t_solidus=1933.0,
+                  t_liquidus=2200.0, darcy_c=darcy_c, darcy_b=1.0,
+                  oseen_flags=MF_OSEEN_THREE_PHASE | MF_OSEEN_DARCY | MF_OSEEN_TRACE_CORRECTION)
+    fields = [torch.tensor(phi, device="cuda"), torch.tensor(beta.ravel(), device="cuda"), torch.tensor(T, device="cuda")]
+    op.set_field("phi", fields[0])
+    op.set_field("beta", fields[1])
+    op.set_field("t_prev", fields[2])
+    u = torch.tensor(syn.uniform_pm1(1, op.n), device="cuda")
+    v = torch.empty_like(u)
+    u32, v32 = u.float(), torch.empty(op.n, dtype=torch.float32, device="cuda")
+    ms64 = _event_ms(lambda: op.apply(u, v), 10, flush)
+    ms32 = _event_ms(lambda: op.apply(u32, v32), 10, flush)
+    # right-hand side: the interface loads of this temperature field (hybrid recoil force in the
+    # momentum rows, evaporative dilation in the continuity rows)
+    ev, ti = syn.EVAPORATION, syn.TI64
+    src = op.interface_sources(fields[2], ev["p_amb"], ev["h_v"], ev["molar_mass"], ev["t_boil"],
+                               ti["rho_l"] * ti["cp_l"], ti["rho_g"] * ti["cp_g"], outputs=("u", "p"))
+    bt = torch.cat([src["u"], src["p"]])
+    kw = dict(solver="gmres", precond="block_triangular", restart=50, maxit=400, tol=1e-10)
+    op.solve(bt, **kw)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    _, info = op.solve(bt, **kw)
+    torch.cuda.synchronize()
+    return {"workload": f"oseen_meltpool_{n}", "variant": op.variant, "darcy_c": darcy_c,
+            "apply_f64": {"ms": ms64, "gdofs": op.n / ms64 / 1e6}, "apply_f32": {"ms": ms32, "gdofs": op.n / ms32 / 1e6},
+            "solve": {"seconds": time.perf_counter() - t0, "iterations": info["iterations"],
+                      "rel_residual": info["rel_residual"], "status": info["status"]}}
+
+
 def interface_sources_timing(ctx, op, mu, flush, reps=10):
     """The fused interface-source kernel (evaporative dilation, cooling and hybrid recoil loads)
     on the Oseen mesh, Knight's mass flux, a hot spot across the interface."""
@@ -529,6 +585,7 @@ def main():
         out["oseen_solve"] = oseen_solve(ctx, op, mu, mp)
     if args.suite and rank == 0:
         out["workloads"] = workload_suite(ctx, flush)
+        out["workloads"]["oseen_meltpool"] = meltpool_oseen(ctx, args.n, flush)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         v, nd, reps, dt = cpu_oracle_apply(16)
         out["cpu_baseline"] = {"value": v, "unit": "GDoF/s", "cores": 1, "kind": "oracle",
