@@ -207,6 +207,19 @@ def _apply_rates(op, n, nrhs, flush, reps=5):
     return out
 
 
+def _packed_rates(op, n, nrhs, flush, reps=5):
+    """G DoF.RHS/s of the packed 16-bit applies (fp32 vectors, pairs of right-hand sides per thread)."""
+    import torch
+    import synthetic as syn
+    u = torch.tensor(syn.uniform_pm1(1, n * nrhs), device="cuda").float()
+    v = torch.empty_like(u)
+    out = {}
+    for arith in ("f16", "bf16"):
+        ms = _event_ms(lambda: op.apply(u, v, nrhs=nrhs, arith=arith), reps, flush)
+        out[arith] = {"ms": ms, "gdofs": n * nrhs / ms / 1e6, "variant": op.variant}
+    return out
+
+
 def workload_suite(ctx, flush):
     """One bounded measurement per benchmark workload (the parity tests cover their numerics)."""
     import numpy as np
@@ -270,7 +283,8 @@ def workload_suite(ctx, flush):
     B = torch.tensor(np.concatenate([syn.uniform_pm1(s, m.n_dofs) for s in range(1, wl.nrhs + 1)]), device="cuda")
     r = {"n_dofs": m.n_dofs, "cells": m.n_cells, "hanging_nodes": m.n_constraints, "nrhs": wl.nrhs,
          "apply_batched": _apply_rates(op, m.n_dofs, wl.nrhs, flush, reps=3),
-         "apply_single": _apply_rates(op, m.n_dofs, 1, flush, reps=3)}
+         "apply_single": _apply_rates(op, m.n_dofs, 1, flush, reps=3),
+         "apply_batched_packed16": _packed_rates(op, m.n_dofs, wl.nrhs, flush, reps=3)}
     kw = dict(solver="defect_correction", precond="chebyshev", tol=1e-10, use_graph=True)
     op.solve(B, nrhs=wl.nrhs, **kw)
     t0 = time.perf_counter()
@@ -279,6 +293,15 @@ def workload_suite(ctx, flush):
     r["mixed_solve_8rhs"] = {"seconds": time.perf_counter() - t0, "inner_iterations": info["iterations"],
                              "outer": info["outer_iterations"], "rel_residual": info["rel_residual"],
                              "status": info["status"]}
+    for arith in ("bf16", "f16"):
+        op.solve(B, nrhs=wl.nrhs, inner_arith=arith, **kw)
+        t0 = time.perf_counter()
+        _, info = op.solve(B, nrhs=wl.nrhs, inner_arith=arith, **kw)
+        torch.cuda.synchronize()
+        r[f"mixed_solve_8rhs_inner_{arith}"] = {"seconds": time.perf_counter() - t0,
+                                                "inner_iterations": info["iterations"],
+                                                "outer": info["outer_iterations"], "rel_residual": info["rel_residual"],
+                                                "status": info["status"]}
     res[wl.name] = r
     return res
 

@@ -174,6 +174,15 @@ mf_status mf_operator_set_field(mf_op* op, int field, const void* dev_ptr, int d
 /* dst = A src for nrhs vectors stored ld apart (dtype MF_F64 or MF_F32: the arithmetic
  * precision of the apply).  Dirichlet rows return src.  Asynchronous. */
 mf_status mf_apply(mf_op* op, const void* src, void* dst, int nrhs, int64_t ld, int dtype);
+/* dst = A src with fp32 vectors and packed 16-bit arithmetic (format MF_F16 or MF_BF16): two
+ * right-hand sides share every instruction (lanes of an fp16x2 / bf16x2 register), so an odd nrhs
+ * leaves one lane idle.  Helmholtz, heat without convection and reinit, coefficients from the
+ * fp32 Gauss-point tables; values are scaled by a power of two near sqrt(n) and the coefficients
+ * by one at or above their maximum before packing (fp16's range), and the result is unscaled in
+ * fp32.  About 3 (fp16) or 2 (bf16) significant digits per operation: meant for smoothers inside a
+ * higher-precision iteration.  The first call after a field change measures the coefficient
+ * maximum (synchronising).  MF_EUNSUPPORTED for the Oseen operator or convection. */
+mf_status mf_apply_packed16(mf_op* op, const float* src, float* dst, int nrhs, int64_t ld, int format);
 /* dst = A^T src (Helmholtz, heat with convection, reinit).  Asynchronous. */
 mf_status mf_apply_transpose(mf_op* op, const void* src, void* dst, int nrhs, int64_t ld, int dtype);
 /* The coupling blocks of the Oseen operator on their own: the pressure-gradient term of the
@@ -227,6 +236,10 @@ typedef struct {
   int schur_maxit;     /* MF_PREC_BLOCK_TRIANGULAR: cap of the inner Schur CG (<= 0: 30) */
   int velocity_steps;  /* MF_PREC_BLOCK_TRIANGULAR: GMRES steps on the velocity block, 1..60 (<= 0: 10) */
   double schur_tol;    /* MF_PREC_BLOCK_TRIANGULAR: relative tolerance of the inner Schur CG (<= 0: 0.1) */
+  int inner_arith;     /* defect correction: arithmetic of the inner fp32 operator applies (CG and
+                          Chebyshev): MF_F32 (default, also 0), MF_F16 or MF_BF16 (packed pairs of
+                          right-hand sides, see mf_apply_packed16) */
+  int reserved3;
 } mf_solver_params;
 
 typedef struct {

@@ -7,7 +7,7 @@ provide device memory: pass CUDA tensors, their data pointers go to the library.
 import ctypes as C
 
 from . import _lib
-from ._lib import (MF_F64, MF_F32, MF_OP_HELMHOLTZ, MF_OP_HEAT, MF_OP_OSEEN, MF_OP_REINIT,
+from ._lib import (MF_F64, MF_F32, MF_F16, MF_BF16, MF_OP_HELMHOLTZ, MF_OP_HEAT, MF_OP_OSEEN, MF_OP_REINIT,
                    MF_HEAVISIDE_TANH, MF_HEAVISIDE_SINE, MF_COEF_INKERNEL, MF_COEF_QPOINT,
                    MF_FIELD_PHI, MF_FIELD_T_PREV, MF_FIELD_BETA, MF_FIELD_K_QPOINT,
                    MF_SOLVER_CG, MF_SOLVER_GMRES, MF_SOLVER_DEFECT_CORRECTION,
@@ -156,13 +156,14 @@ class DofMap:
 
 def solver_params(solver="cg", precond="jacobi", tol=1e-10, maxit=5000, restart=50, cheby_degree=4,
                   inner_tol=1e-4, inner_maxit=100, use_graph=False, cheby_ratio=30.0, lanczos_steps=20,
-                  fp64_arith="f64", schur_tol=0.1, schur_maxit=30, velocity_steps=10):
+                  fp64_arith="f64", schur_tol=0.1, schur_maxit=30, velocity_steps=10, inner_arith="f32"):
     s = _lib.SolverParams()
     s.fp64_arith = {"f64": 0, "df64": 1, "auto": 2}[fp64_arith]
     s.solver = {"cg": MF_SOLVER_CG, "gmres": MF_SOLVER_GMRES, "defect_correction": MF_SOLVER_DEFECT_CORRECTION}[solver]
     s.precond = {"none": MF_PREC_NONE, "jacobi": MF_PREC_JACOBI, "chebyshev": MF_PREC_CHEBYSHEV,
                  "block_jacobi": MF_PREC_BLOCK_JACOBI, "block_triangular": MF_PREC_BLOCK_TRIANGULAR}[precond]
     s.schur_tol, s.schur_maxit, s.velocity_steps = schur_tol, schur_maxit, velocity_steps
+    s.inner_arith = {"f32": MF_F32, "f16": MF_F16, "bf16": MF_BF16}[inner_arith]
     s.inner_dtype = MF_F32
     s.restart, s.cheby_degree, s.maxit, s.inner_maxit = restart, cheby_degree, maxit, inner_maxit
     s.use_graph = 1 if use_graph else 0
@@ -197,11 +198,18 @@ class Operator:
         check(_lib.load().mf_operator_set_field(self.h, self.FIELDS[name], _ptr(t), _dtype_code(t), t.numel()))
 
     def apply(self, src, dst=None, nrhs=1, transpose=False, arith=None):
-        """dst = A src; fp64 tensors may ask for arith="df64" (double-float cell arithmetic)."""
+        """dst = A src; fp64 tensors may ask for arith="df64" (double-float cell arithmetic), fp32
+        tensors for arith="f16" or "bf16" (packed 16-bit arithmetic, pairs of right-hand sides)."""
         import torch
         if dst is None:
             dst = torch.empty_like(src)
         code = _dtype_code(src)
+        if arith in ("f16", "bf16"):
+            if code != MF_F32 or transpose:
+                raise TypeError("16-bit arithmetic applies to fp32 tensors, forward only")
+            check(_lib.load().mf_apply_packed16(self.h, _ptr(src), _ptr(dst), nrhs, src.numel() // nrhs,
+                                                MF_F16 if arith == "f16" else MF_BF16))
+            return dst
         if arith == "df64":
             if code != MF_F64:
                 raise TypeError("df64 arithmetic applies to fp64 tensors")

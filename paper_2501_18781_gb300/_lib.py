@@ -34,7 +34,8 @@ class SolverParams(C.Structure):
                 ("cheby_degree", C.c_int), ("maxit", C.c_int), ("inner_maxit", C.c_int), ("use_graph", C.c_int),
                 ("tol", C.c_double), ("inner_tol", C.c_double), ("cheby_ratio", C.c_double),
                 ("lanczos_steps", C.c_int), ("fp64_arith", C.c_int), ("schur_maxit", C.c_int),
-                ("velocity_steps", C.c_int), ("schur_tol", C.c_double)]
+                ("velocity_steps", C.c_int), ("schur_tol", C.c_double), ("inner_arith", C.c_int),
+                ("reserved3", C.c_int)]
 
 
 class SolveInfo(C.Structure):
@@ -78,6 +79,7 @@ SIGNATURES = {
     "mf_operator_set_field": (C.c_int, [P, C.c_int, P, C.c_int, I64]),
     "mf_apply": (C.c_int, [P, P, P, C.c_int, I64, C.c_int]),
     "mf_apply_transpose": (C.c_int, [P, P, P, C.c_int, I64, C.c_int]),
+    "mf_apply_packed16": (C.c_int, [P, P, P, C.c_int, I64, C.c_int]),
     "mf_oseen_coupling": (C.c_int, [P, C.c_int, P, P, C.c_int]),
     "mf_interface_sources": (C.c_int, [P, C.POINTER(Evaporation), P, P, P, P]),
     "mf_diagonal": (C.c_int, [P, P, C.c_int]),

@@ -358,6 +358,7 @@ mf_status mf_operator_set_field(mf_op* op, int field, const void* ptr, int dtype
   }
   op->tables_ready = false;
   op->diag_ready = false;
+  op->h16_cnorm = 0.0f;
   // float copy of the in-kernel nodal field
   const double* f = op->p.kind == MF_OP_HEAT ? op->tprev : op->phi;
   if (f && (field == MF_FIELD_PHI || field == MF_FIELD_T_PREV)) {
@@ -501,13 +502,53 @@ template <typename T> OseenArgs<T> oseen_args(const mf_op* op, const T* src, T* 
 }
 template OseenArgs<double> oseen_args<double>(const mf_op*, const double*, double*);
 
+// Packed 16-bit arithmetic (two right-hand sides per thread) on fp32 vectors: scalar operators
+// with tabulated coefficients and no convection.
+mf_status apply_h16(mf_op* op, const float* src, float* dst, int nrhs, int64_t ld, bool transpose, int prec) {
+  mf_ctx* c = op->ctx;
+  MF_TRY(check_fields(op));
+  if (op->p.kind == MF_OP_OSEEN) return fail(MF_EUNSUPPORTED, "16-bit arithmetic for the Oseen operator");
+  const int kind = scalar_kind(op);
+  if (kind == K_HEAT && op->beta) return fail(MF_EUNSUPPORTED, "16-bit arithmetic with convection");
+  (void)transpose;  // the supported operators are symmetric
+  MF_TRY(ensure_tables(op));
+  if (ld == op->n) MF_CUDA_TRY(cudaMemsetAsync(dst, 0, sizeof(float) * op->n * nrhs, c->stream));
+  else
+    for (int r = 0; r < nrhs; ++r) MF_CUDA_TRY(cudaMemsetAsync(dst + r * ld, 0, sizeof(float) * op->n, c->stream));
+  ScalarArgs<float> a = scalar_args<float>(op, src, dst, nrhs, ld);
+  // power of two near sqrt(n): unit-norm vectors get O(1) entries (inside fp16's range)
+  const float scale = std::ldexp(1.0f, int(std::lround(0.5 * std::log2(double(std::max<int64_t>(op->n, 1))))));
+  if (op->h16_cnorm <= 0.0f) {
+    // every coefficient the packed kernel multiplies: the value term mass h^2 (largest h), eps
+    // (reinit) and the Gauss-point table (a or k)
+    double big = std::fabs(double(a.mass)) * op->map[0]->mesh->h0 * op->map[0]->mesh->h0;
+    if (kind == K_REINIT) {
+      big = std::max(big, std::fabs(double(a.eps)));
+    } else {
+      float qmax = 0.0f;
+      MF_TRY(abs_max_f32(c, op->qcoef32.as<float>(), int64_t(27) * op->ncells, &qmax));
+      big = std::max(big, double(qmax));
+    }
+    op->h16_cnorm = std::ldexp(1.0f, std::max(0, int(std::ceil(std::log2(std::max(big, 1e-30))))));
+  }
+  MF_TRY(launch_scalar_apply_h16(c, op->map[0], kind, prec, a, scale, op->h16_cnorm));
+  MF_TRY(launch_dirichlet_copy(c, op->map[0], src, dst, nrhs, ld, 0, true));
+  op->variant = std::string(kind == K_HELM ? "helmholtz" : kind == K_HEAT ? "heat" : "reinit") +
+                (op->map[0]->uniform ? "/uniform" : "/octree") + (prec == PREC_F16 ? "/f16x2" : "/bf16x2") +
+                "/tabulated/pairs-of-rhs";
+  return MF_OK;
+}
+
 // dst = A src (or A^T src), nrhs vectors ld apart, precision T.
 // prec: PREC_F64 / PREC_DF64 for fp64 vectors (-1: the operator's fp64 arithmetic), PREC_F32 for fp32.
 template <typename T>
 mf_status apply_impl(mf_op* op, const T* src, T* dst, int nrhs, int64_t ld, bool transpose, int prec) {
   const bool f32 = sizeof(T) == 4;
-  if (f32) prec = PREC_F32;
+  if (f32) prec = (prec == PREC_F16 || prec == PREC_BF16 || prec == PREC_F32) ? prec : op->f32_prec;
   else if (prec != PREC_F64 && prec != PREC_DF64) prec = op->f64_prec;
+  if constexpr (sizeof(T) == 4) {
+    if (prec == PREC_F16 || prec == PREC_BF16) return apply_h16(op, src, dst, nrhs, ld, transpose, prec);
+  }
   const bool df = prec == PREC_DF64;
   mf_ctx* c = op->ctx;
   MF_TRY(check_fields(op));
@@ -627,6 +668,15 @@ mf_status mf_interface_sources(mf_op* op, const mf_evaporation* ev, const double
     return fail(MF_EINVAL, "Knight's mass flux needs T_v > 0 and M > 0");
   if (!f_u && !f_p && !f_T) return MF_OK;
   return launch_interface_sources(op->ctx, op->map[0], op->map[1], op->p, op->phi, *ev, T, f_u, f_p, f_T);
+  MF_GUARD_END
+}
+
+mf_status mf_apply_packed16(mf_op* op, const float* src, float* dst, int nrhs, int64_t ld, int format) {
+  MF_GUARD_BEGIN
+  if (!op || !src || !dst) return fail(MF_EINVAL, "NULL argument");
+  if (nrhs < 1 || ld < op->n) return fail(MF_EINVAL, "nrhs must be >= 1 and ld >= n");
+  if (format != MF_F16 && format != MF_BF16) return fail(MF_EINVAL, "format must be MF_F16 or MF_BF16");
+  return apply_impl<float>(op, src, dst, nrhs, ld, false, format == MF_F16 ? PREC_F16 : PREC_BF16);
   MF_GUARD_END
 }
 

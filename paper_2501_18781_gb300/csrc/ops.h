@@ -8,7 +8,7 @@ namespace mf {
 
 enum ScalarKind { K_HELM = 0, K_HEAT = 1, K_REINIT = 2, K_MASS = 3 };
 // arithmetic of an apply: fp64, fp32, or double-float (fp64 storage, pairs of fp32 in the kernel)
-enum ApplyPrec { PREC_F64 = 0, PREC_F32 = 1, PREC_DF64 = 2 };
+enum ApplyPrec { PREC_F64 = 0, PREC_F32 = 1, PREC_DF64 = 2, PREC_F16 = 3, PREC_BF16 = 4 };
 
 // Arguments of the scalar cell kernels.  Vector fields are in the apply precision T.
 template <typename T> struct ScalarArgs {
@@ -77,6 +77,10 @@ mf_status launch_oseen_blockdiag(mf_ctx* ctx, const mf_dofmap* mu, const mf_dofm
 // dst[dir] = src[dir] for nrhs vectors (Dirichlet identity rows)
 mf_status launch_dirichlet_copy(mf_ctx* ctx, const mf_dofmap* m, const void* src, void* dst, int nrhs, int64_t ld,
                                 int64_t offset, bool f32);
+// scalar operators in packed 16-bit arithmetic on fp32 vectors (prec PREC_F16 / PREC_BF16)
+mf_status launch_scalar_apply_h16(mf_ctx* ctx, const mf_dofmap* m, int kind, int prec, const ScalarArgs<float>& a,
+                                  float scale, float cnorm);
+mf_status abs_max_f32(mf_ctx* ctx, const float* x, int64_t n, float* out);
 // interface source terms (evaporative dilation, cooling, hybrid recoil) on an Oseen mesh
 mf_status launch_interface_sources(mf_ctx* ctx, const mf_dofmap* mu, const mf_dofmap* mp, const mf_op_params& p,
                                    const double* phi, const mf_evaporation& ev, const double* T, double* fu,
@@ -112,6 +116,8 @@ struct mf_op {
   bool diag_ready = false;
   int mode64 = 1, mode32 = 0;     // coefficient mode per precision (autotuned)
   int f64_prec = 0;               // arithmetic of fp64 applies inside solvers (PREC_F64 or PREC_DF64)
+  int f32_prec = 1;               // arithmetic of fp32 applies inside solvers (PREC_F32, PREC_F16, PREC_BF16)
+  float h16_cnorm = 0.0f;         // 16-bit applies: power of two >= every coefficient (0: not computed)
   int block = 128;                // octree cells per block (autotuned: 64 or 128)
   int persistent_blocks = 0;      // > 0: persistent launch with this many blocks per SM (autotuned)
   bool df64_faster = false;       // autotuned: double-float beats the fp64 pipes (used when fp64_arith = 2)

@@ -657,6 +657,18 @@ mf_status solve_impl(mf_op* op, const mf_solver_params* sp, const double* b, dou
     ~Restore() { op->f64_prec = prev; }
   } restore{op, op->f64_prec};
   op->f64_prec = (sp->fp64_arith == 1 || (sp->fp64_arith == 2 && op->df64_faster)) ? PREC_DF64 : PREC_F64;
+  // fp32 applies of the inner solve in fp32 or packed 16-bit arithmetic
+  struct Restore32 {
+    mf_op* op;
+    ~Restore32() { op->f32_prec = PREC_F32; }
+  } restore32{op};
+  if (sp->inner_arith == MF_F16 || sp->inner_arith == MF_BF16) {
+    if (sp->solver != MF_SOLVER_DEFECT_CORRECTION)
+      return fail(MF_EINVAL, "16-bit inner arithmetic belongs to defect correction");
+    op->f32_prec = sp->inner_arith == MF_F16 ? PREC_F16 : PREC_BF16;
+  } else if (sp->inner_arith != 0 && sp->inner_arith != MF_F32) {
+    return fail(MF_EINVAL, "inner_arith must be MF_F32, MF_F16 or MF_BF16");
+  }
   mf_solve_info inf{};
   mf_status st = MF_OK;
   const double tol = sp->tol > 0 ? sp->tol : 1e-10;
