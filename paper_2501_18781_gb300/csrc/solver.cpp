@@ -772,6 +772,13 @@ mf_status solve_impl(mf_op* op, const mf_solver_params* sp, const double* b, dou
       MF_TRY(dev_add_scaled(c, d32.p, x, dscale, n, nrhs));
       ++outer;
       MF_TRY(true_residual(op, b, x, r.p, nrhs, rel));
+      for (double v : rel)
+        if (!std::isfinite(v)) {
+          inf.outer_iterations = outer;
+          inf.rel_residual = v;
+          if (info) *info = inf;
+          return fail(MF_ENOTCONV, "defect correction broke down (non-finite residual)");
+        }
     }
     inf.outer_iterations = outer;
     if (*std::max_element(rel.begin(), rel.end()) > tol) st = MF_ENOTCONV;
