@@ -436,6 +436,12 @@ mf_status ensure_tables(mf_op* op) {
                                      op->kd64.as<double>(), op->kd32.as<float>(), op->nrm64.as<double>(),
                                      op->nrm32.as<float>()));
     }
+    for (mf::DevBuf* b : {&op->cm64, &op->cc64, &op->cv64}) MF_TRY(b->alloc(sizeof(double) * 27 * nc));
+    for (mf::DevBuf* b : {&op->cm32, &op->cc32, &op->cv32}) MF_TRY(b->alloc(sizeof(float) * 27 * nc));
+    MF_TRY(launch_oseen_fold(op->ctx, op->map[0], p.sigma, op->rho64.as<double>(), op->mu64.as<double>(),
+                             p.oseen_flags ? op->kd64.as<double>() : nullptr, op->cm64.as<double>(),
+                             op->cm32.as<float>(), op->cc64.as<double>(), op->cc32.as<float>(), op->cv64.as<double>(),
+                             op->cv32.as<float>()));
   } else {
     const int kind = scalar_kind(op);
     MF_TRY(op->qcoef64.alloc(sizeof(double) * 27 * nc));
@@ -498,6 +504,12 @@ template <typename T> OseenArgs<T> oseen_args(const mf_op* op, const T* src, T* 
                : nullptr;
   a.nrm = a.ext ? (f32 ? reinterpret_cast<const T*>(op->nrm32.as<float>()) : reinterpret_cast<const T*>(op->nrm64.as<double>()))
                 : nullptr;
+  auto pick = [&](const mf::DevBuf& b64, const mf::DevBuf& b32) {
+    return f32 ? reinterpret_cast<const T*>(b32.as<float>()) : reinterpret_cast<const T*>(b64.as<double>());
+  };
+  a.cm = pick(op->cm64, op->cm32);
+  a.cc = pick(op->cc64, op->cc32);
+  a.cv = pick(op->cv64, op->cv32);
   return a;
 }
 template OseenArgs<double> oseen_args<double>(const mf_op*, const double*, double*);

@@ -258,7 +258,7 @@ __global__ void __launch_bounds__(128) k_oseen_qouter(OseenArgs<typename Store<T
   const uint32_t dmask = dirichlet_mask(ug, i, j, k);
   const int64_t px = ug.nx + 1, pxy = px * (ug.ny + 1);
   const int64_t pbase = i + px * (j + (ug.ny + 1) * int64_t(k));
-  const T h = T(ug.h), sh2 = T(A.sigma) * h * h;
+  const T h = T(ug.h), mh2 = -(h * h);
   T U0[27], U1[27], U2[27];
   gather_uniform<T>(A.src, base, ug.sx, ug.sy, dmask, U0);
   gather_uniform<T>(A.src + A.nu, base, ug.sx, ug.sy, dmask, U1);
@@ -266,10 +266,12 @@ __global__ void __launch_bounds__(128) k_oseen_qouter(OseenArgs<typename Store<T
   to_qpoints<T>(U0);
   to_qpoints<T>(U1);
   to_qpoints<T>(U2);
+  // nodal pressure times -h^2: the pressure test term -w h^3 p div v = (w psi . (-h^2 p)) g_ref(v)
   T Pn[8];
   const St* __restrict__ psrc = A.src + 3 * A.nu;
 #pragma unroll
-  for (int n = 0; n < 8; ++n) Pn[n] = from_store<T>(__ldg(psrc + pbase + (n & 1) + px * ((n >> 1) & 1) + pxy * (n >> 2)));
+  for (int n = 0; n < 8; ++n)
+    Pn[n] = mh2 * from_store<T>(__ldg(psrc + pbase + (n & 1) + px * ((n >> 1) & 1) + pxy * (n >> 2)));
   T R0[27], R1[27], R2[27], Rp[8];
 #pragma unroll
   for (int q = 0; q < 27; ++q) { R0[q] = T(0); R1[q] = T(0); R2[q] = T(0); }
@@ -282,40 +284,35 @@ __global__ void __launch_bounds__(128) k_oseen_qouter(OseenArgs<typename Store<T
 #pragma unroll
       for (int qa = 0; qa < 3; ++qa) {
         const int q = qa + 3 * qb + 9 * qc;
-        const T w = Tb<T>::W3(q);
-        const T rho = from_store<T>(__ldg(A.rho + q * nc + cell));
-        const T mu = from_store<T>(__ldg(A.mu + q * nc + cell));
+        // Gauss-point coefficients with weight and powers of h folded in (tabulated once per
+        // operator): cm = w h^3 (sigma rho [+ Darcy]), cc = w h^2 rho, cv = w h mu
+        const T cm = from_store<T>(__ldg(A.cm + q * nc + cell));
+        const T cc = from_store<T>(__ldg(A.cc + q * nc + cell));
+        const T cv = from_store<T>(__ldg(A.cv + q * nc + cell));
         const T bx = from_store<T>(__ldg(A.beta + (0 * 27 + q) * nc + cell));
         const T by = from_store<T>(__ldg(A.beta + (1 * 27 + q) * nc + cell));
         const T bz = from_store<T>(__ldg(A.beta + (2 * 27 + q) * nc + cell));
-        T pq = T(0);
+        T pw = T(0);
 #pragma unroll
-        for (int n = 0; n < 8; ++n) pq += q1w<T>(q, n) * Pn[n];
+        for (int n = 0; n < 8; ++n) pw += Tb<T>::PWW(q, n) * Pn[n];
         T g[3][3];  // g[d][e] = d u_d / d x_e (reference)
         grad_at<T>(U0, qa, qb, qc, g[0][0], g[0][1], g[0][2]);
         grad_at<T>(U1, qa, qb, qc, g[1][0], g[1][1], g[1][2]);
         grad_at<T>(U2, qa, qb, qc, g[2][0], g[2][1], g[2][2]);
-        const T c1 = w * mu;
         // value test: sigma rho u_d + rho beta . grad u_d
-        const T rw = w * rho;
-        R0[q] += rw * (sh2 * U0[q] + h * (bx * g[0][0] + by * g[0][1] + bz * g[0][2]));
-        R1[q] += rw * (sh2 * U1[q] + h * (bx * g[1][0] + by * g[1][1] + bz * g[1][2]));
-        R2[q] += rw * (sh2 * U2[q] + h * (bx * g[2][0] + by * g[2][1] + bz * g[2][2]));
-        // gradient test: mu (grad u + grad u^T) - p I (both scaled by the weight)
-        const T pw = w * (-h * pq);
-        T s00 = c1 * (g[0][0] + g[0][0]) + pw, s11 = c1 * (g[1][1] + g[1][1]) + pw, s22 = c1 * (g[2][2] + g[2][2]) + pw;
-        T s01 = c1 * (g[0][1] + g[1][0]), s02 = c1 * (g[0][2] + g[2][0]), s12 = c1 * (g[1][2] + g[2][1]);
+        R0[q] += cm * U0[q] + cc * (bx * g[0][0] + by * g[0][1] + bz * g[0][2]);
+        R1[q] += cm * U1[q] + cc * (bx * g[1][0] + by * g[1][1] + bz * g[1][2]);
+        R2[q] += cm * U2[q] + cc * (bx * g[2][0] + by * g[2][1] + bz * g[2][2]);
+        // gradient test: mu (grad u + grad u^T) - p I
+        T s00 = cv * (g[0][0] + g[0][0]) + pw, s11 = cv * (g[1][1] + g[1][1]) + pw, s22 = cv * (g[2][2] + g[2][2]) + pw;
+        T s01 = cv * (g[0][1] + g[1][0]), s02 = cv * (g[0][2] + g[2][0]), s12 = cv * (g[1][2] + g[2][1]);
+        const T div = g[0][0] + g[1][1] + g[2][2];
         if constexpr (EXT) {
-          // Darcy: w h^3 kd u = h (w kd h^2 u)
-          const T kw = w * from_store<T>(__ldg(A.kd + q * nc + cell)) * h * h;
-          R0[q] += kw * U0[q];
-          R1[q] += kw * U1[q];
-          R2[q] += kw * U2[q];
-          // trace correction: -2 mu (div u) n n (div in reference units, like g)
+          // trace correction: -2 mu (div u) n n (the Darcy term sits in cm)
           const T nx = from_store<T>(__ldg(A.nrm + q * nc + cell));
           const T ny = from_store<T>(__ldg(A.nrm + (27 + q) * nc + cell));
           const T nz = from_store<T>(__ldg(A.nrm + (54 + q) * nc + cell));
-          const T t = T(-2) * c1 * (g[0][0] + g[1][1] + g[2][2]);
+          const T t = T(-2) * cv * div;
           const T tx = t * nx, ty = t * ny, tz = t * nz;
           s00 += tx * nx;
           s11 += ty * ny;
@@ -327,13 +324,10 @@ __global__ void __launch_bounds__(128) k_oseen_qouter(OseenArgs<typename Store<T
         add_grad_test<T>(R0, qa, qb, qc, s00, s01, s02);
         add_grad_test<T>(R1, qa, qb, qc, s01, s11, s12);
         add_grad_test<T>(R2, qa, qb, qc, s02, s12, s22);
-        // continuity test: -q div u
-        const T s = w * (-h * (g[0][0] + g[1][1] + g[2][2]));
+        // continuity test: -q div u (the factor -h^2 is applied at the scatter)
 #pragma unroll
-        for (int n = 0; n < 8; ++n) Rp[n] += q1w<T>(q, n) * s;
+        for (int n = 0; n < 8; ++n) Rp[n] += Tb<T>::PWW(q, n) * div;
       }
-#pragma unroll
-  for (int q = 0; q < 27; ++q) { R0[q] *= h; R1[q] *= h; R2[q] *= h; }
   to_nodes<T>(R0);
   scatter_uniform<T>(A.dst, base, ug.sx, ug.sy, dmask, R0);
   to_nodes<T>(R1);
@@ -343,7 +337,7 @@ __global__ void __launch_bounds__(128) k_oseen_qouter(OseenArgs<typename Store<T
   St* pdst = A.dst + 3 * A.nu;
 #pragma unroll
   for (int n = 0; n < 8; ++n)
-    atomicAdd(pdst + pbase + (n & 1) + px * ((n >> 1) & 1) + pxy * (n >> 2), to_store<T>(h * Rp[n]));
+    atomicAdd(pdst + pbase + (n & 1) + px * ((n >> 1) & 1) + pxy * (n >> 2), to_store<T>(mh2 * Rp[n]));
 }
 
 // The two coupling blocks of the Oseen operator alone, for the Schur complement B D^-1 B^T of

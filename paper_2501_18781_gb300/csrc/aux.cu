@@ -207,6 +207,25 @@ __global__ void k_oseen_ext_tables(UniformGeom ug, const double* phi, const doub
       }
 }
 
+// cm = w h^3 (sigma rho + kd), cc = w h^2 rho, cv = w h mu per (Gauss point, cell), in fp64 and fp32
+__global__ void k_oseen_fold(int64_t nc, double h, double sigma, const double* rho, const double* mu,
+                             const double* kd, double* cm64, float* cm32, double* cc64, float* cc32, double* cv64,
+                             float* cv32) {
+  const int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (t >= 27 * nc) return;
+  const int q = int(t / nc);
+  const double w = cW364[q];
+  const double m = w * h * h * h * (sigma * rho[t] + (kd ? kd[t] : 0.0));
+  const double c = w * h * h * rho[t];
+  const double v = w * h * mu[t];
+  cm64[t] = m;
+  cm32[t] = float(m);
+  cc64[t] = c;
+  cc32[t] = float(c);
+  cv64[t] = v;
+  cv32[t] = float(v);
+}
+
 // ---------------------------------------------------------------- diagonals
 // out[l] += sum_q c[q] X[qa][a] Y[qb][b] Z[qc][c] with 1D tables X, Y, Z (3x3, [q][a]).
 __device__ __forceinline__ void separable_add(const double* c, const double* X, const double* Y, const double* Z,
@@ -523,6 +542,18 @@ mf_status launch_oseen_qtables(mf_ctx* ctx, const mf_dofmap* mu, const double* p
   UniformGeom ug = uniform_geom(mu);
   k_oseen_qtables<<<blocks(mu->n_cells, 128), 128, 0, ctx->stream>>>(ug, phi, beta, rho_l, rho_g, mu_l, mu_g, hv, eps,
                                                                       r64, r32, m64, m32, b64, b32);
+  ctx->launches++;
+  MF_CUDA_TRY(cudaGetLastError());
+  return MF_OK;
+}
+
+mf_status launch_oseen_fold(mf_ctx* ctx, const mf_dofmap* mu, double sigma, const double* rho, const double* muq,
+                            const double* kd, double* cm64, float* cm32, double* cc64, float* cc32, double* cv64,
+                            float* cv32) {
+  MF_CUDA_TRY(upload_tables_here());
+  const int64_t nc = mu->n_cells;
+  k_oseen_fold<<<blocks(27 * nc, 256), 256, 0, ctx->stream>>>(nc, mu->mesh->h0, sigma, rho, muq, kd, cm64, cm32, cc64,
+                                                              cc32, cv64, cv32);
   ctx->launches++;
   MF_CUDA_TRY(cudaGetLastError());
   return MF_OK;

@@ -23,13 +23,14 @@ struct Tables {
   double SS[9], SSp[9], SpSp[9], PP[6], PpPp[6];
   double G[3];     // Gauss points on [0, 1]
   double PW[216];  // PW[8 q + n] = Q1 basis function n at Gauss point q (n: x fastest)
+  double PWW[216]; // PWW[8 q + n] = W3[q] PW[8 q + n]
 };
 
 static __constant__ double cS64[9], cD64[9], cW64[3], cP64[6], cSp64[9], cW364[27];
 static __constant__ float cS32[9], cD32[9], cW32[3], cP32[6], cSp32[9], cW332[27];
 static __constant__ double cSS64[9], cSSp64[9], cSpSp64[9], cPP64[6], cPpPp64[6];
-static __constant__ double cPW64[216], cG64[3];
-static __constant__ float cPW32[216];
+static __constant__ double cPW64[216], cG64[3], cPWW64[216];
+static __constant__ float cPW32[216], cPWW32[216];
 // double-float copies (hi, lo) for the df64 kernels
 static __constant__ float cSh[9], cSl[9], cDh[9], cDl[9], cW3h[27], cW3l[27], cPWh[216], cPWl[216];
 
@@ -42,6 +43,7 @@ template <> struct Tb<double> {
   static __device__ __forceinline__ double P(int q, int a) { return cP64[2 * q + a]; }
   static __device__ __forceinline__ double Sp(int q, int a) { return cSp64[3 * q + a]; }
   static __device__ __forceinline__ double PW(int q, int n) { return cPW64[8 * q + n]; }
+  static __device__ __forceinline__ double PWW(int q, int n) { return cPWW64[8 * q + n]; }
 };
 template <> struct Tb<float> {
   static __device__ __forceinline__ float S(int q, int a) { return cS32[3 * q + a]; }
@@ -51,6 +53,7 @@ template <> struct Tb<float> {
   static __device__ __forceinline__ float P(int q, int a) { return cP32[2 * q + a]; }
   static __device__ __forceinline__ float Sp(int q, int a) { return cSp32[3 * q + a]; }
   static __device__ __forceinline__ float PW(int q, int n) { return cPW32[8 * q + n]; }
+  static __device__ __forceinline__ float PWW(int q, int n) { return cPWW32[8 * q + n]; }
 };
 
 template <> struct Tb<df64> {
@@ -81,7 +84,7 @@ Tables make_tables();           // host: closed forms (cellops_host.cpp)
     up64(cSp64, t.Sp, 9); up64(cW364, t.W3, 27);                                          \
     up64(cSS64, t.SS, 9); up64(cSSp64, t.SSp, 9); up64(cSpSp64, t.SpSp, 9);               \
     up64(cPP64, t.PP, 6); up64(cPpPp64, t.PpPp, 6); up64(cPW64, t.PW, 216); up64(cG64, t.G, 3);\
-    up32(cPW32, t.PW, 216);                                                               \
+    up32(cPW32, t.PW, 216); up64(cPWW64, t.PWW, 216); up32(cPWW32, t.PWW, 216);           \
     up32(cS32, t.S, 9); up32(cD32, t.D, 9); up32(cW32, t.W, 3); up32(cP32, t.P, 6);       \
     up32(cSp32, t.Sp, 9); up32(cW332, t.W3, 27);                                          \
     auto updf = [&](const void* sh, const void* sl, const double* src, int n) {           \

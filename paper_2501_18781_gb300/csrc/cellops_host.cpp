@@ -50,6 +50,7 @@ Tables make_tables() {
         t.W3[q] = w[a] * w[b] * w[c];
         for (int n = 0; n < 8; ++n)
           t.PW[8 * q + n] = t.P[2 * a + (n & 1)] * t.P[2 * b + ((n >> 1) & 1)] * t.P[2 * c + (n >> 2)];
+        for (int n = 0; n < 8; ++n) t.PWW[8 * q + n] = t.W3[q] * t.PW[8 * q + n];
       }
   return t;
 }
