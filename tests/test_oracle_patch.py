@@ -1,0 +1,57 @@
+"""The oracle's patch rows (one row of a full-size operator from a 2x2x2-cell patch) reproduce the
+rows of the fully assembled oracle matrices: heat with Dirichlet rows, per-Gauss-point k and the
+convection transpose, and the Oseen saddle-point operator (velocity and pressure rows)."""
+import numpy as np
+
+import synthetic as syn
+from oracle import assemble as asm
+from oracle import mesh as omesh
+from oracle import patch
+
+from problems import DIRICHLET_BOTTOM, OSEEN_FACES
+
+
+def test_heat_rows_with_dirichlet_kq_and_transpose():
+    n = 4
+    wl = syn.scaled(syn.HEAT_ADJOINT, n)
+    p = wl.params
+    dm = omesh.uniform_dofmap(n, wl.lo, wl.hi, 2, DIRICHLET_BOTTOM)
+    x = dm.dof_coords()
+    beta = np.array(syn.convection_field(*x.T, wl.seed, wl.lo, wl.hi))
+    kq = syn.kq_field(dm.n_cells * 27, wl.seed, p["k0"]).reshape(dm.n_cells, 27)
+    A = asm.heat_matrix(dm, p["rhocp"], p["dt"], kq=kq, beta=beta).tocsr()
+    u = syn.uniform_pm1(3, dm.n_dofs)
+    free = np.random.default_rng(0).choice(np.nonzero(~dm.dirichlet)[0], 150, replace=False)
+    build = lambda d, nod, cw: asm.heat_matrix(d, p["rhocp"], p["dt"], kq=cw["kq"], beta=nod["beta"])
+    for tr in (False, True):
+        got = patch.scalar_rows(n, wl.lo, wl.hi, free, build, {"beta": beta}, u, dm.dirichlet,
+                                cellwise={"kq": kq}, transpose=tr)
+        ref = ((A.T if tr else A) @ np.where(dm.dirichlet, 0.0, u))[free]
+        assert np.abs(got - ref).max() <= 1e-13 * np.abs(ref).max()
+
+
+def test_oseen_rows_velocity_and_pressure():
+    n = 4
+    wl = syn.scaled(syn.OSEEN_INTERFACE, n)
+    p = wl.params
+    dmu = omesh.uniform_dofmap(n, wl.lo, wl.hi, 2, OSEEN_FACES)
+    dmp = omesh.uniform_dofmap(n, wl.lo, wl.hi, 1, 0)
+    x = dmu.dof_coords()
+    t1, t2 = syn.wavy_plane_phases(wl.seed)
+    phi = syn.initial_level_set(syn.wavy_plane_distance(*x.T, t1, t2), wl.eps)
+    beta = np.array(syn.convection_field(*x.T, wl.seed, wl.lo, wl.hi))
+    sigma = 1.0 / (p["dt_cfl"] * wl.h)
+    args = (sigma, p["rho_l"], p["rho_g"], p["mu_l"], p["mu_g"])
+    A = asm.oseen_matrix(dmu, dmp, phi, beta, *args).tocsr()
+    nu = dmu.n_dofs
+    u = syn.uniform_pm1(4, A.shape[0])
+    mask = np.concatenate([np.tile(dmu.dirichlet, 3), np.zeros(dmp.n_dofs, bool)])
+    rows = np.sort(np.concatenate([np.random.default_rng(1).choice(np.nonzero(~mask[:3 * nu])[0], 120, replace=False),
+                                   3 * nu + np.arange(dmp.n_dofs)[::4]]))
+    build = lambda du, dp, nod: asm.oseen_matrix(du, dp, nod["phi"], nod["beta"], *args)
+    got = patch.oseen_rows(n, wl.lo, wl.hi, rows, build, {"phi": phi, "beta": beta}, u, dmu.dirichlet)
+    ref = (A @ np.where(mask, 0.0, u))[rows]
+    assert np.abs(got - ref).max() <= 1e-13 * np.abs(ref).max()
+    bound = patch.oseen_rows(n, wl.lo, wl.hi, rows[:20], build, {"phi": phi, "beta": beta}, u, dmu.dirichlet,
+                             absolute=True)
+    assert np.allclose(bound, (abs(A) @ np.abs(np.where(mask, 0.0, u)))[rows[:20]], rtol=1e-13)
