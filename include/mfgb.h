@@ -123,7 +123,7 @@ typedef enum {
 typedef enum {
   MF_COEF_INKERNEL = 0,  /* coefficients re-evaluated from the nodal fields in every apply */
   MF_COEF_QPOINT = 1     /* coefficients tabulated per Gauss point when fields are set */
-} mf_coef_mode;
+} mf_coef_mode;           /* reinit: fp32 applies always use the table (normals evaluated in fp64) */
 
 typedef struct {
   int kind;        /* mf_op_kind */

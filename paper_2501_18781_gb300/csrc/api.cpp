@@ -315,7 +315,9 @@ mf_status mf_operator_create(mf_ctx* c, const mf_op_params* p, const mf_dofmap* 
   op->n = maps[0]->n_dofs * (p->kind == MF_OP_OSEEN ? 3 : 1) + (nmaps == 2 ? maps[1]->n_dofs : 0);
   op->ncells = maps[0]->n_cells;
   op->mode64 = p->kind == MF_OP_OSEEN ? 1 : (p->coef_mode == MF_COEF_INKERNEL ? 0 : 1);
-  op->mode32 = op->mode64;
+  // reinit: fp32 applies always read the normal evaluated in fp64 (far from the interface phi_h is
+  // flat to within fp32 rounding, and a normal computed there in fp32 points anywhere)
+  op->mode32 = p->kind == MF_OP_REINIT ? 1 : op->mode64;
   *out = op;
   return MF_OK;
   MF_GUARD_END

@@ -959,11 +959,12 @@ mf_status mf_autotune(mf_op* op, const char* cache_path) {
     for (int pi = 0; pi < 2; ++pi)
       for (int mode = 0; mode < 2; ++mode) {
         if (forced && mode == 0) continue;
+        if (pi == 1 && mode == 0 && op->p.kind == MF_OP_REINIT) continue;  // fp64-evaluated normals only
         (pi == 0 ? op->mode64 : op->mode32) = mode;
         MF_TRY(time_variant(pi == 0 ? PREC_F64 : PREC_F32, &mode_ms[pi][mode]));
       }
     op->mode64 = mode_ms[0][0] < mode_ms[0][1] ? 0 : 1;
-    op->mode32 = mode_ms[1][0] < mode_ms[1][1] ? 0 : 1;
+    op->mode32 = (op->p.kind != MF_OP_REINIT && mode_ms[1][0] < mode_ms[1][1]) ? 0 : 1;
     // 2) launch shape on the fp32 apply: cells per block (octree) and persistent grids
     const int shapes[5][2] = {{128, 0}, {64, 0}, {128, 2}, {128, 4}, {64, 8}};
     double shape_ms[5];
