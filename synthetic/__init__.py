@@ -15,16 +15,17 @@ counter-based generator: output i of stream ``seed`` is mix(seed + (i+1)*gamma).
 from .rng import splitmix64, uniform_pm1, uniform_01
 from .fields import (sphere_distance, wavy_plane_distance, deformed_sphere_distance,
                      initial_level_set, convection_field, heat_initial_temperature,
-                     heat_target_temperature, kq_field, wavy_plane_phases, interface_temperature)
+                     heat_target_temperature, kq_field, wavy_plane_phases, interface_temperature,
+                     meltpool_state)
 from .octree import refine_band_leaves, is_two_to_one_balanced
 from .workloads import (TI64, EVAPORATION, HELMHOLTZ_SPHERE, OSEEN_INTERFACE, HEAT_LASER, HEAT_ADJOINT,
-                        REINIT_OCTREE, Workload, scaled)
+                        REINIT_OCTREE, MELTPOOL_STEP, Workload, scaled)
 
 __all__ = [
     "splitmix64", "uniform_pm1", "uniform_01", "sphere_distance", "wavy_plane_distance",
     "deformed_sphere_distance", "initial_level_set", "convection_field",
     "heat_initial_temperature", "heat_target_temperature", "kq_field", "wavy_plane_phases",
-    "interface_temperature", "EVAPORATION",
+    "interface_temperature", "meltpool_state", "EVAPORATION", "MELTPOOL_STEP",
     "refine_band_leaves", "is_two_to_one_balanced", "TI64", "HELMHOLTZ_SPHERE",
     "OSEEN_INTERFACE", "HEAT_LASER", "HEAT_ADJOINT", "REINIT_OCTREE", "Workload", "scaled",
 ]

@@ -138,3 +138,24 @@ def interface_temperature(x, y, z, t_base=2000.0, t_peak=3600.0, centre=(0.5, 0.
     T = t_base + (t_peak - t_base) exp(-2 |x - c|^2 / r^2), above the boiling point near c."""
     r2 = (x - centre[0]) ** 2 + (y - centre[1]) ** 2 + (z - centre[2]) ** 2
     return t_base + (t_peak - t_base) * np.exp(-2.0 * r2 / radius ** 2)
+
+
+def meltpool_state(x, y, z, seed, lo, hi, eps, u_max=1.0, r_hot=50e-6, t_base=500.0, t_peak=3600.0,
+                   surface=0.6, amplitude=0.03):
+    """Two time levels (n and n-1) of the fields of one melt-pool step on the box [lo, hi]:
+    a wavy melt surface z_s = lo_z + L_z (surface + amplitude sin(2 pi xi_x + t1) sin(2 pi xi_y + t2))
+    with the dense phase below (phi = tanh(d / (2 eps)), d = z_s - z; one step earlier the surface
+    stood eps/4 higher), a hot spot T = t_base + (t_peak - t_base) exp(-2 rho^2/r^2 - 2 (z - z_s)^2/r^2)
+    under the box centre (3 % cooler one step earlier), and the divergence-free, wall-tangential
+    convection field scaled to u_max (10 % slower one step earlier)."""
+    t1, t2 = wavy_plane_phases(seed)
+    L = [hi[i] - lo[i] for i in range(3)]
+    xi, eta = (x - lo[0]) / L[0], (y - lo[1]) / L[1]
+    zs = lo[2] + L[2] * (surface + amplitude * np.sin(2.0 * np.pi * xi + t1) * np.sin(2.0 * np.pi * eta + t2))
+    d = zs - z
+    xc, yc = 0.5 * (lo[0] + hi[0]), 0.5 * (lo[1] + hi[1])
+    g = np.exp(-2.0 * ((x - xc) ** 2 + (y - yc) ** 2) / r_hot ** 2 - 2.0 * ((z - zs) / r_hot) ** 2)
+    T = t_base + (t_peak - t_base) * g
+    u = u_max * np.array(convection_field(x, y, z, seed, lo, hi))
+    return dict(u=u, u_prev=0.9 * u, T=T, T_prev=t_base + 0.97 * (T - t_base),
+                phi=initial_level_set(d, eps), phi_prev=initial_level_set(d + 0.25 * eps, eps))

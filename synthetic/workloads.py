@@ -74,6 +74,18 @@ REINIT_OCTREE = Workload(
     params=dict(sphere_radius=0.3, amplitude=0.05, lmax=6, tol=1e-10))
 
 
+MELTPOOL_STEP = Workload(
+    "meltpool_step_q2q1_64", "meltpool_step", 64, lo=(-3e-4, -3e-4, -3e-4), hi=(3e-4, 3e-4, 3e-4),
+    params=dict(dt=5e-7, u_max=1.0, reinit_steps=2, dtau_cells=0.5,
+                laser=dict(power=200.0, radius=50e-6, absorptivity=0.35, focus=(0.0, 0.0, 0.0),
+                           direction=(0.0, 0.0, -1.0)),
+                surface_tension=dict(alpha0=1.493, alpha1=5.5e-4, t_alpha=1928.0, alpha_res=0.01),
+                gravity=(0.0, 0.0, -9.81),
+                solid=dict(rho_s=TI64["rho_l"], mu_s=TI64["mu_l"], t_solidus=1933.0, t_liquidus=2200.0),
+                darcy=dict(C=1e12, b=1.0, t_solidus=1933.0, t_liquidus=2200.0),
+                trace_correction=True, tol=1e-10, flow_tol=1e-10))
+
+
 def scaled(wl, n, levels=None, nrhs=None):
     """The same workload recipe on a smaller (or larger) mesh."""
     kw = dict(n=n, name=f"{wl.name}@n{n}")
