@@ -483,6 +483,53 @@ def meltpool_oseen(ctx, n, flush, darcy_c=None):
                       "rel_residual": info["rel_residual"], "status": info["status"]}}
 
 
+def meltpool_step(ctx, n=64, reps=3):
+    """One step of the melt-pool algorithm on the 600 um box (64^3 cells: 2.1M Q2 nodes per field,
+    6.7M velocity-pressure DoFs): predictors, level-set advection (GMRES) with the variant-1
+    transport velocity, 2 reinitialisation steps (CG), two-phase heat with laser and evaporative
+    cooling (GMRES), melt-pool Navier-Stokes with surface tension, recoil and Darcy damping
+    (FGMRES, block-triangular).  The same state is advanced reps times after one warm-up step."""
+    import numpy as np
+    import torch
+    import synthetic as syn
+    from paper_2501_18781_gb300 import DofMap, MeltPoolStep, Mesh
+    from paper_2501_18781_gb300._lib import MF_OSEEN_DARCY, MF_OSEEN_THREE_PHASE, MF_OSEEN_TRACE_CORRECTION
+    wl = syn.scaled(syn.MELTPOOL_STEP, n)
+    p, ti, ev = wl.params, syn.TI64, syn.EVAPORATION
+    mesh = Mesh.uniform(ctx, n, wl.lo, wl.hi)
+    maps = [DofMap(mesh, 2, 0b011111), DofMap(mesh, 1, 0), DofMap(mesh, 2, 0), DofMap(mesh, 2, 1 << 4)]
+    x = maps[0].coords()
+    state = {k: torch.tensor(np.ascontiguousarray(v.ravel()), device="cuda")
+             for k, v in syn.meltpool_state(*x.T, wl.seed, wl.lo, wl.hi, wl.eps, u_max=p["u_max"]).items()}
+    sol, dar, st = p["solid"], p["darcy"], p["surface_tension"]
+    step = MeltPoolStep(
+        ctx, maps,
+        evaporation=dict(mass_flux="knight", p_ambient=ev["p_amb"], latent_heat=ev["h_v"], molar_mass=ev["molar_mass"],
+                         t_boil=ev["t_boil"], sticking=ev["sticking"], gas_constant=8.314),
+        laser=p["laser"], gravity=p["gravity"], dt=p["dt"], eps=wl.eps, rho_l=ti["rho_l"], rho_g=ti["rho_g"],
+        mu_l=ti["mu_l"], mu_g=ti["mu_g"], rhocp_l=ti["rho_l"] * ti["cp_l"], rhocp_g=ti["rho_g"] * ti["cp_g"],
+        k_l=ti["k_l"], k_g=ti["k_g"], oseen_flags=MF_OSEEN_THREE_PHASE | MF_OSEEN_DARCY | MF_OSEEN_TRACE_CORRECTION,
+        rho_s=sol["rho_s"], mu_s=sol["mu_s"], t_solidus=sol["t_solidus"], t_liquidus=sol["t_liquidus"],
+        darcy_c=dar["C"], darcy_b=dar["b"], alpha0=st["alpha0"], alpha1=st["alpha1"], t_alpha=st["t_alpha"],
+        alpha_res=st["alpha_res"], reinit_steps=p["reinit_steps"], dtau=p["dtau_cells"] * wl.h, tol=p["tol"],
+        flow_tol=p["flow_tol"], maxit=2000)
+    step.advance(state)
+    torch.cuda.synchronize()
+    runs = []
+    for _ in range(reps):
+        t0 = time.perf_counter()
+        _, info = step.advance(state)
+        torch.cuda.synchronize()
+        runs.append((time.perf_counter() - t0, info))
+    wall, info = sorted(runs, key=lambda r: r[0])[len(runs) // 2]
+    nu, npr = maps[0].n_dofs, maps[1].n_dofs
+    return {"workload": wl.name, "n_u": nu, "n_p": npr, "unknowns_per_step": 5 * nu + npr, "ms_per_step": wall * 1e3,
+            "stage_seconds": dict(zip(("advection", "reinit", "heat", "flow", "total"), info["seconds"])),
+            "iterations": {k: info[k + "_iterations"] for k in ("advection", "reinit", "heat", "flow")},
+            "rel_residuals": {k: info[k + "_residual"] for k in ("advection", "reinit", "heat", "flow")},
+            "status": info["status"], "tol": p["tol"], "flow_tol": p["flow_tol"]}
+
+
 def interface_sources_timing(ctx, op, mu, flush, reps=10):
     """The fused interface-source kernel (evaporative dilation, cooling and hybrid recoil loads)
     on the Oseen mesh, Knight's mass flux, a hot spot across the interface."""
@@ -506,6 +553,7 @@ def main():
     ap.add_argument("--no-solve", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--suite", action="store_true", help="also measure the other benchmark workloads")
+    ap.add_argument("--meltpool-step", action="store_true", help="also time one melt-pool algorithm step")
     ap.add_argument("--n", type=int, default=64)
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
@@ -610,6 +658,8 @@ def main():
     if args.suite and rank == 0:
         out["workloads"] = workload_suite(ctx, flush)
         out["workloads"]["oseen_meltpool"] = meltpool_oseen(ctx, args.n, flush)
+    if (args.suite or args.meltpool_step) and rank == 0:
+        out.setdefault("workloads", {})["meltpool_step"] = meltpool_step(ctx, args.n)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         v, nd, reps, dt = cpu_oracle_apply(16)
         out["cpu_baseline"] = {"value": v, "unit": "GDoF/s", "cores": 1, "kind": "oracle",

@@ -157,7 +157,15 @@ typedef enum {
   MF_FIELD_PHI = 0,      /* nodal level set on map 0 (n_dofs values) */
   MF_FIELD_T_PREV = 1,   /* nodal absolute temperature T^n on map 0 */
   MF_FIELD_BETA = 2,     /* nodal convection field, 3 blocks of n_dofs (x, y, z) */
-  MF_FIELD_K_QPOINT = 3  /* conductivity per Gauss point, n_cells*27, cell-major, x fastest */
+  MF_FIELD_K_QPOINT = 3, /* conductivity per Gauss point, n_cells*27, cell-major, x fastest */
+  /* heat operators only, for the two-phase energy equation (eq. heat_transfer with eq. muEff):
+   * the volumetric heat capacity per Gauss point (n_cells*27, layout of K_QPOINT) replaces
+   * rho_cp in both the value term (rho_cp,q / dt) and the convection term (rho_cp,q beta), and a
+   * convection velocity per Gauss point (n_cells*27*3, cell-major, point, then x/y/z) replaces the
+   * interpolated nodal MF_FIELD_BETA (the level-set transport velocity lives at Gauss points).
+   * Either one makes the operator tabulated; 16-bit applies and the heat-step gradient reject it. */
+  MF_FIELD_RHOCP_QPOINT = 4,
+  MF_FIELD_BETA_QPOINT = 5
 } mf_field;
 
 /* Operator on `maps` (one map; Oseen: the Q2 velocity map then the Q1 pressure map on the
@@ -348,6 +356,80 @@ const char* mf_operator_variant(const mf_op* op);
 
 /* Number of kernel launches the library has issued on this context so far. */
 int64_t mf_context_launch_count(const mf_ctx* ctx);
+
+/* ---------------------------------------------------------------------------------------------
+ * One time step of the overall solution algorithm (Algorithm algo:meltpooldg) on one uniform
+ * mesh: velocity on a Q2 map (its Dirichlet faces are the walls, u = 0 there), pressure on a Q1
+ * map, level set phi on a Q2 map without Dirichlet faces, temperature on a Q2 map whose Dirichlet
+ * faces keep T^n.  With x* = 2 x^n - x^(n-1) (step 1):
+ *  2. u_G = u*_h + mdot(T*_h) / rho(phi*_h) n_G(phi*_h) at the Gauss points (variant 1, eq.
+ *     transport_vel_local_continuous); (M/dt + C(u_G)) phi_a = M phi^n / dt (eq. transport, backward
+ *     Euler, GMRES); reinit_steps pseudo-time steps (M/dtau + eps N_n) psi' = M psi / dtau + F(psi),
+ *     F_i = int (1 - psi_h^2)/2 n . grad N_i, n the unit normal of phi_a (Olsson's conservative
+ *     reinitialisation for phi in [-1, 1], CG), phi^(n+1) = the last psi;
+ *  3. heat (eq. heat_transfer, GMRES): (M_{rho_cp/dt} + K_k + C_{rho_cp}(u*)) T^(n+1) =
+ *     M_{rho_cp/dt} T^n + s with rho_cp, k of phi^(n+1) (eq. muEff) and s = evaporative cooling
+ *     (mdot of T*, eq. vapor_heat_loss) + laser (eq. laser_gauss with <n_G . e_L>, n_G pointing into
+ *     the dense phase, e_L the beam direction); solved for T^(n+1) - T^n;
+ *  4. flow (FGMRES(50) with the block-triangular preconditioner, fp32 inner solves): the melt-pool
+ *     Oseen operator about u* with sigma = 1/dt, phi^(n+1), T^(n+1), velocity load sigma M_rho u^n
+ *     + rho g + surface tension (eq. surface_tension, kappa = -div n_G from the Hessian of phi_h) +
+ *     hybrid recoil force, pressure rows -int q sdot (eq. evaporDil).
+ * The tanh Heaviside throughout (mf_op_params heaviside 0).  Every value in fp64. */
+typedef struct mf_meltpool_step mf_meltpool_step;
+
+typedef struct {
+  double dt;                                /* time step */
+  double eps;                               /* interface thickness parameter */
+  double rho_l, rho_g, mu_l, mu_g;          /* eqs. (rhoEff), (muEff) */
+  double rhocp_l, rhocp_g, k_l, k_g;        /* eq. (muEff) for rho c_p and k */
+  int oseen_flags;                          /* MF_OSEEN_* terms of the flow operator */
+  int laser_on;                             /* 0: no laser flux */
+  double rho_s, mu_s, t_solidus, t_liquidus, darcy_c, darcy_b;  /* as in mf_op_params */
+  mf_evaporation evaporation;               /* mass flux and recoil (its rhocp_* are ignored) */
+  double alpha0, alpha1, t_alpha, alpha_res;  /* eq. (surface_tension) */
+  double gravity[3];
+  double laser_power, laser_radius, laser_absorptivity;
+  double laser_focus[3], laser_direction[3];  /* a point of the beam axis and its direction */
+  int reinit_steps;                         /* >= 0 */
+  int maxit;                                /* iteration limit of every solve (<= 0: 5000) */
+  double dtau;                              /* pseudo-time step (reinit_steps > 0) */
+  double tol;                               /* relative tolerance of the level-set and heat solves */
+  double flow_tol;                          /* relative tolerance of the flow solve */
+} mf_meltpool_params;
+
+typedef struct {
+  int advection_iterations, reinit_iterations, heat_iterations, flow_iterations;
+  double advection_residual, reinit_residual, heat_residual, flow_residual;  /* relative, last solve */
+  double seconds[5];  /* level-set advection (incl. predictors), reinitialisation, heat, flow, total */
+} mf_meltpool_info;
+
+/* Optional device copies of intermediate quantities (any pointer may be NULL). */
+typedef struct {
+  double* u_star;        /* 3 n_u */
+  double* T_star;        /* n_u */
+  double* phi_star;      /* n_u */
+  double* u_gamma;       /* n_cells * 27 * 3 */
+  double* b_advection;   /* n_u: M phi^n / dt */
+  double* phi_advected;  /* n_u */
+  double* r_heat;        /* n_u: s + M_{rho_cp/dt} T^n - A T^n, Dirichlet rows 0 */
+  double* b_flow;        /* 3 n_u + n_p */
+} mf_meltpool_trace;
+
+/* maps: velocity (Q2), pressure (Q1), level set (Q2, no Dirichlet faces), temperature (Q2), one
+ * uniform mesh.  The step owns its operators and work vectors (about 40 n_u doubles plus
+ * 7 n_cells * 27 for the Gauss-point tables).  MF_EINVAL on inconsistent maps or parameters. */
+mf_status mf_meltpool_create(mf_ctx* ctx, const mf_meltpool_params* params, const mf_dofmap* u_map,
+                             const mf_dofmap* p_map, const mf_dofmap* phi_map, const mf_dofmap* T_map,
+                             mf_meltpool_step** out);
+void mf_meltpool_destroy(mf_meltpool_step* step);
+/* Advance one step.  Inputs (device, fp64): u^(n-1), u^n (3 n_u each), T^(n-1), T^n, phi^(n-1),
+ * phi^n (n_u each); pass the same pointer twice for a first step (x* = x^n).  Outputs (device,
+ * may not alias the inputs): up = [u^(n+1); p^(n+1)] (3 n_u + n_p), T^(n+1), phi^(n+1).
+ * Synchronising; MF_ENOTCONV (outputs and info filled) if a solve stops at maxit. */
+mf_status mf_meltpool_advance(mf_meltpool_step* step, const double* u_prev, const double* u, const double* T_prev,
+                              const double* T, const double* phi_prev, const double* phi, double* up, double* T_out,
+                              double* phi_out, mf_meltpool_trace* trace, mf_meltpool_info* info);
 
 #ifdef __cplusplus
 }

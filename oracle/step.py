@@ -224,8 +224,8 @@ def reinitialise(dmphi, phi_a, prm):
 
 def heat_system(maps, T_n, u_s, T_s, phi_new, prm):
     """Step 3: the heat matrix A_T (Dirichlet rows identity), the right-hand side with the
-    Dirichlet columns lifted, and r = s + M_{rho c_p/dt} T^n - A_all T^n (Dirichlet rows 0), the
-    right-hand side of the update T^(n+1) - T^n."""
+    Dirichlet columns lifted, r = s + M_{rho c_p/dt} T^n - A_all T^n (Dirichlet rows 0), the
+    right-hand side of the update T^(n+1) - T^n, and A_all (the form without Dirichlet rows)."""
     dmu, dmp, dmphi, dmT = maps
     dt = prm["dt"]
     ph, gph = asm.field_at_qpoints(dmT, phi_new)
@@ -248,7 +248,7 @@ def heat_system(maps, T_n, u_s, T_s, phi_new, prm):
     rhs[D] = T_n[D]
     r = b - A_all @ T_n
     r[D] = 0.0
-    return A_T, rhs, r
+    return A_T, rhs, r, A_all
 
 
 def flow_system(maps, u_n, u_s, phi_new, T_new, prm):
@@ -294,7 +294,7 @@ def step(maps, state, prm, keep=False):
     A_adv, b_adv, uG = advection_system(dmphi, state["phi"], u_s, T_s, phi_s, prm)
     phi_a = sla.spsolve(A_adv.tocsc(), b_adv)
     phi_new, A_re = reinitialise(dmphi, phi_a, prm)
-    A_T, rhs_T, r_T = heat_system(maps, state["T"], u_s, T_s, phi_new, prm)
+    A_T, rhs_T, r_T, _ = heat_system(maps, state["T"], u_s, T_s, phi_new, prm)
     T_new = sla.spsolve(A_T.tocsc(), rhs_T)
     A_ns, rhs = flow_system(maps, state["u"], u_s, phi_new, T_new, prm)
     x = sla.spsolve(A_ns.tocsc(), rhs)

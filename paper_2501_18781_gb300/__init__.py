@@ -175,7 +175,8 @@ class Operator:
     """A matrix-free operator; ``params`` are the fields of mf_op_params (kind given by name)."""
 
     KINDS = {"helmholtz": MF_OP_HELMHOLTZ, "heat": MF_OP_HEAT, "oseen": MF_OP_OSEEN, "reinit": MF_OP_REINIT}
-    FIELDS = {"phi": MF_FIELD_PHI, "t_prev": MF_FIELD_T_PREV, "beta": MF_FIELD_BETA, "k_qpoint": MF_FIELD_K_QPOINT}
+    FIELDS = {"phi": MF_FIELD_PHI, "t_prev": MF_FIELD_T_PREV, "beta": MF_FIELD_BETA, "k_qpoint": MF_FIELD_K_QPOINT,
+              "rhocp_qpoint": _lib.MF_FIELD_RHOCP_QPOINT, "beta_qpoint": _lib.MF_FIELD_BETA_QPOINT}
 
     def __init__(self, ctx, kind, maps, **params):
         p = _lib.OpParams()
@@ -305,5 +306,73 @@ class Operator:
         try:
             if self.h:
                 _lib.load().mf_operator_destroy(self.h)
+        except Exception:
+            pass
+
+
+class MeltPoolStep:
+    """One time step of the melt-pool algorithm (mf_meltpool_create / mf_meltpool_advance) on the
+    maps (velocity Q2, pressure Q1, level set Q2 without Dirichlet faces, temperature Q2).
+    ``params`` are the fields of mf_meltpool_params; ``evaporation`` a dict of mf_evaporation
+    fields (mass_flux "knight" | "tanasawa"), ``laser`` a dict (power, radius, absorptivity, focus,
+    direction) or None."""
+
+    TRACE = ("u_star", "T_star", "phi_star", "u_gamma", "b_advection", "phi_advected", "r_heat", "b_flow")
+
+    def __init__(self, ctx, maps, evaporation, laser=None, gravity=(0.0, 0.0, 0.0), **params):
+        p = _lib.MeltPoolParams()
+        ev = dict(evaporation)
+        ev["mass_flux"] = {"knight": 0, "tanasawa": 1}[ev.get("mass_flux", "knight")]
+        for k, v in ev.items():
+            setattr(p.evaporation, k, v)
+        if p.evaporation.gas_constant == 0:
+            p.evaporation.gas_constant = 8.314
+        for k, v in params.items():
+            setattr(p, k, v)
+        p.gravity[:] = list(gravity)
+        if laser is not None:
+            p.laser_on = 1
+            p.laser_power, p.laser_radius = laser["power"], laser["radius"]
+            p.laser_absorptivity = laser["absorptivity"]
+            p.laser_focus[:] = list(laser["focus"])
+            p.laser_direction[:] = list(laser["direction"])
+        h = C.c_void_p()
+        check(_lib.load().mf_meltpool_create(ctx.h, C.byref(p), *[m.h for m in maps], C.byref(h)))
+        self.ctx, self.h, self.maps, self.params = ctx, h, maps, p
+
+    def advance(self, state, trace=False):
+        """state: dict of fp64 CUDA tensors u, u_prev (3 n_u), T, T_prev, phi, phi_prev (n_u).
+        Returns (dict u (3, n_u), p, T, phi [, trace tensors]), info dict."""
+        import torch
+        mu, mp = self.maps[0], self.maps[1]
+        nu, npr, nc = mu.n_dofs, mp.n_dofs, mu.n_cells
+        kw = dict(dtype=torch.float64, device="cuda")
+        up = torch.empty(3 * nu + npr, **kw)
+        T = torch.empty(nu, **kw)
+        phi = torch.empty(nu, **kw)
+        tr, trp = {}, None
+        if trace:
+            sizes = dict(u_star=3 * nu, T_star=nu, phi_star=nu, u_gamma=81 * nc, b_advection=nu,
+                         phi_advected=nu, r_heat=nu, b_flow=3 * nu + npr)
+            tr = {k: torch.empty(sizes[k], **kw) for k in self.TRACE}
+            trp = _lib.MeltPoolTrace(*[tr[k].data_ptr() for k in self.TRACE])
+        inf = _lib.MeltPoolInfo()
+        s = {k: state[k].contiguous() for k in ("u_prev", "u", "T_prev", "T", "phi_prev", "phi")}
+        st = _lib.load().mf_meltpool_advance(self.h, *[_ptr(s[k]) for k in ("u_prev", "u", "T_prev", "T",
+                                                                             "phi_prev", "phi")],
+                                             _ptr(up), _ptr(T), _ptr(phi), C.byref(trp) if trp else None,
+                                             C.byref(inf))
+        if st not in (_lib.MF_OK, _lib.MF_ENOTCONV):
+            check(st)
+        out = dict(u=up[:3 * nu].view(3, nu), p=up[3 * nu:], T=T, phi=phi, **tr)
+        info = {k: getattr(inf, k) for k, _ in _lib.MeltPoolInfo._fields_ if k != "seconds"}
+        info["seconds"] = list(inf.seconds)
+        info["status"] = st
+        return out, info
+
+    def __del__(self):
+        try:
+            if self.h:
+                _lib.load().mf_meltpool_destroy(self.h)
         except Exception:
             pass

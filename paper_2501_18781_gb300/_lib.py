@@ -11,6 +11,7 @@ MF_OP_HELMHOLTZ, MF_OP_HEAT, MF_OP_OSEEN, MF_OP_REINIT = 0, 1, 2, 3
 MF_HEAVISIDE_TANH, MF_HEAVISIDE_SINE = 0, 1
 MF_COEF_INKERNEL, MF_COEF_QPOINT = 0, 1
 MF_FIELD_PHI, MF_FIELD_T_PREV, MF_FIELD_BETA, MF_FIELD_K_QPOINT = 0, 1, 2, 3
+MF_FIELD_RHOCP_QPOINT, MF_FIELD_BETA_QPOINT = 4, 5
 MF_SOLVER_CG, MF_SOLVER_GMRES, MF_SOLVER_DEFECT_CORRECTION = 0, 1, 2
 MF_OSEEN_THREE_PHASE, MF_OSEEN_DARCY, MF_OSEEN_TRACE_CORRECTION = 1, 2, 4
 MF_PREC_NONE, MF_PREC_JACOBI, MF_PREC_CHEBYSHEV, MF_PREC_BLOCK_JACOBI, MF_PREC_BLOCK_TRIANGULAR = 0, 1, 2, 3, 4
@@ -55,6 +56,30 @@ class Laser(C.Structure):
                 ("absorptivity", C.c_double)]
 
 
+class MeltPoolParams(C.Structure):
+    _fields_ = [("dt", C.c_double), ("eps", C.c_double), ("rho_l", C.c_double), ("rho_g", C.c_double),
+                ("mu_l", C.c_double), ("mu_g", C.c_double), ("rhocp_l", C.c_double), ("rhocp_g", C.c_double),
+                ("k_l", C.c_double), ("k_g", C.c_double), ("oseen_flags", C.c_int), ("laser_on", C.c_int),
+                ("rho_s", C.c_double), ("mu_s", C.c_double), ("t_solidus", C.c_double), ("t_liquidus", C.c_double),
+                ("darcy_c", C.c_double), ("darcy_b", C.c_double), ("evaporation", Evaporation),
+                ("alpha0", C.c_double), ("alpha1", C.c_double), ("t_alpha", C.c_double), ("alpha_res", C.c_double),
+                ("gravity", C.c_double * 3), ("laser_power", C.c_double), ("laser_radius", C.c_double),
+                ("laser_absorptivity", C.c_double), ("laser_focus", C.c_double * 3),
+                ("laser_direction", C.c_double * 3), ("reinit_steps", C.c_int), ("maxit", C.c_int),
+                ("dtau", C.c_double), ("tol", C.c_double), ("flow_tol", C.c_double)]
+
+
+class MeltPoolInfo(C.Structure):
+    _fields_ = [("advection_iterations", C.c_int), ("reinit_iterations", C.c_int), ("heat_iterations", C.c_int),
+                ("flow_iterations", C.c_int), ("advection_residual", C.c_double), ("reinit_residual", C.c_double),
+                ("heat_residual", C.c_double), ("flow_residual", C.c_double), ("seconds", C.c_double * 5)]
+
+
+class MeltPoolTrace(C.Structure):
+    _fields_ = [(k, C.c_void_p) for k in ("u_star", "T_star", "phi_star", "u_gamma", "b_advection",
+                                          "phi_advected", "r_heat", "b_flow")]
+
+
 P = C.c_void_p
 I64 = C.c_int64
 DP = C.POINTER(C.c_double)
@@ -92,6 +117,10 @@ SIGNATURES = {
     "mf_autotune": (C.c_int, [P, C.c_char_p]),
     "mf_operator_variant": (C.c_char_p, [P]),
     "mf_context_launch_count": (I64, [P]),
+    "mf_meltpool_create": (C.c_int, [P, C.POINTER(MeltPoolParams), P, P, P, P, C.POINTER(P)]),
+    "mf_meltpool_destroy": (None, [P]),
+    "mf_meltpool_advance": (C.c_int, [P, P, P, P, P, P, P, P, P, P, C.POINTER(MeltPoolTrace),
+                                      C.POINTER(MeltPoolInfo)]),
 }
 
 _lib = None

@@ -355,6 +355,16 @@ mf_status mf_operator_set_field(mf_op* op, int field, const void* ptr, int dtype
       if (n != op->ncells * 27) return fail(MF_EINVAL, "K_QPOINT must have n_cells * 27 values");
       op->kq_user = static_cast<const double*>(ptr);
       break;
+    case MF_FIELD_RHOCP_QPOINT:
+      if (op->p.kind != MF_OP_HEAT) return fail(MF_EINVAL, "RHOCP_QPOINT belongs to heat operators");
+      if (n != op->ncells * 27) return fail(MF_EINVAL, "RHOCP_QPOINT must have n_cells * 27 values");
+      op->rhocp_user = static_cast<const double*>(ptr);
+      break;
+    case MF_FIELD_BETA_QPOINT:
+      if (op->p.kind != MF_OP_HEAT) return fail(MF_EINVAL, "BETA_QPOINT belongs to heat operators");
+      if (n != op->ncells * 81) return fail(MF_EINVAL, "BETA_QPOINT must have n_cells * 27 * 3 values");
+      op->betaq_user = static_cast<const double*>(ptr);
+      break;
     default:
       return fail(MF_EINVAL, "unknown field");
   }
@@ -391,6 +401,14 @@ double value_coef(const mf_op* op) {
     case MF_OP_REINIT: return 1.0 / op->p.dtau;
   }
   return 0.0;
+}
+
+// heat operator with a convection term (nodal or per Gauss point)
+bool heat_convection(const mf_op* op) { return op->p.kind == MF_OP_HEAT && (op->beta || op->betaq_user); }
+
+// heat operator whose coefficients must come from the Gauss-point tables
+bool heat_tabulated(const mf_op* op) {
+  return op->p.kind == MF_OP_HEAT && (op->beta || op->kq_user || op->rhocp_user || op->betaq_user);
 }
 
 mf_status check_fields(const mf_op* op) {
@@ -448,16 +466,23 @@ mf_status ensure_tables(mf_op* op) {
     const int kind = scalar_kind(op);
     MF_TRY(op->qcoef64.alloc(sizeof(double) * 27 * nc));
     MF_TRY(op->qcoef32.alloc(sizeof(float) * 27 * nc));
-    const bool vec = (kind == K_REINIT) || (kind == K_HEAT && op->beta);
+    const bool vec = (kind == K_REINIT) || heat_convection(op);
     if (vec) {
       MF_TRY(op->qvec64.alloc(sizeof(double) * 81 * nc));
       MF_TRY(op->qvec32.alloc(sizeof(float) * 81 * nc));
+    }
+    const bool qm = kind == K_HEAT && op->rhocp_user;
+    if (qm) {
+      MF_TRY(op->qmass64.alloc(sizeof(double) * 27 * nc));
+      MF_TRY(op->qmass32.alloc(sizeof(float) * 27 * nc));
     }
     const double* field = kind == K_HEAT ? op->tprev : op->phi;
     MF_TRY(launch_scalar_qtables(op->ctx, op->map[0], kind, field, op->kq_user, kind == K_HEAT ? op->beta : nullptr,
                                  p.k0, 0.5 * p.k0 / (p.t_boil > 0 ? p.t_boil : 1.0), p.a_liquid, p.a_gas, p.heaviside,
                                  p.eps, p.rhocp, op->qcoef64.as<double>(), op->qcoef32.as<float>(),
-                                 vec ? op->qvec64.as<double>() : nullptr, vec ? op->qvec32.as<float>() : nullptr));
+                                 vec ? op->qvec64.as<double>() : nullptr, vec ? op->qvec32.as<float>() : nullptr,
+                                 kind == K_HEAT ? op->rhocp_user : nullptr, kind == K_HEAT ? op->betaq_user : nullptr,
+                                 p.dt, qm ? op->qmass64.as<double>() : nullptr, qm ? op->qmass32.as<float>() : nullptr));
   }
   op->tables_ready = true;
   return MF_OK;
@@ -474,6 +499,9 @@ template <typename T> ScalarArgs<T> scalar_args(const mf_op* op, const T* src, T
                 : reinterpret_cast<const T*>(op->p.kind == MF_OP_HEAT ? op->tprev : op->phi);
   a.qcoef = f32 ? reinterpret_cast<const T*>(op->qcoef32.as<float>()) : reinterpret_cast<const T*>(op->qcoef64.as<double>());
   a.qvec = f32 ? reinterpret_cast<const T*>(op->qvec32.as<float>()) : reinterpret_cast<const T*>(op->qvec64.as<double>());
+  a.qmass = !(op->p.kind == MF_OP_HEAT && op->rhocp_user) ? nullptr
+            : f32 ? reinterpret_cast<const T*>(op->qmass32.as<float>())
+                  : reinterpret_cast<const T*>(op->qmass64.as<double>());
   a.ncp = op->ncells;
   a.mass = T(value_coef(op));
   a.a_l = T(op->p.a_liquid);
@@ -523,7 +551,8 @@ mf_status apply_h16(mf_op* op, const float* src, float* dst, int nrhs, int64_t l
   MF_TRY(check_fields(op));
   if (op->p.kind == MF_OP_OSEEN) return fail(MF_EUNSUPPORTED, "16-bit arithmetic for the Oseen operator");
   const int kind = scalar_kind(op);
-  if (kind == K_HEAT && op->beta) return fail(MF_EUNSUPPORTED, "16-bit arithmetic with convection");
+  if (heat_convection(op)) return fail(MF_EUNSUPPORTED, "16-bit arithmetic with convection");
+  if (kind == K_HEAT && op->rhocp_user) return fail(MF_EUNSUPPORTED, "16-bit arithmetic with rho_cp per Gauss point");
   (void)transpose;  // the supported operators are symmetric
   MF_TRY(ensure_tables(op));
   if (ld == op->n) MF_CUDA_TRY(cudaMemsetAsync(dst, 0, sizeof(float) * op->n * nrhs, c->stream));
@@ -567,7 +596,7 @@ mf_status apply_impl(mf_op* op, const T* src, T* dst, int nrhs, int64_t ld, bool
   mf_ctx* c = op->ctx;
   MF_TRY(check_fields(op));
   const int mode = df ? 1 : (f32 ? op->mode32 : op->mode64);
-  const bool needs_tables = op->p.kind == MF_OP_OSEEN || mode == 1 || (op->p.kind == MF_OP_HEAT && (op->beta || op->kq_user));
+  const bool needs_tables = op->p.kind == MF_OP_OSEEN || mode == 1 || heat_tabulated(op);
   if (needs_tables) MF_TRY(ensure_tables(op));
   if (ld == op->n) MF_CUDA_TRY(cudaMemsetAsync(dst, 0, sizeof(T) * op->n * nrhs, c->stream));
   else
@@ -589,13 +618,13 @@ mf_status apply_impl(mf_op* op, const T* src, T* dst, int nrhs, int64_t ld, bool
     return MF_OK;
   }
   const int kind = scalar_kind(op);
-  const bool beta = kind == K_HEAT && op->beta;
+  const bool beta = heat_convection(op);
   if (transpose && !(kind == K_HEAT && beta)) {
     // symmetric operators: A^T = A
     transpose = false;
   }
   int m = mode;
-  if (kind == K_HEAT && op->kq_user) m = 1;
+  if (heat_tabulated(op) && (op->kq_user || op->rhocp_user || op->betaq_user)) m = 1;
   ScalarArgs<T> a = scalar_args<T>(op, src, dst, nrhs, ld);
   MF_TRY(launch_scalar_apply(c, op->map[0], kind, m, beta, transpose, prec, &a));
   MF_TRY(launch_dirichlet_copy(c, op->map[0], src, dst, nrhs, ld, 0, f32));
@@ -634,7 +663,7 @@ mf_status diag64(mf_op* op, double** out) {
       MF_TRY(op->diag64.alloc(sizeof(double) * op->n));
       ScalarArgs<double> a = scalar_args<double>(op, nullptr, nullptr, 1, op->n);
       const int kind = scalar_kind(op);
-      MF_TRY(launch_scalar_diag(op->ctx, op->map[0], kind, kind == K_HEAT && op->beta, a, op->diag64.as<double>()));
+      MF_TRY(launch_scalar_diag(op->ctx, op->map[0], kind, heat_convection(op), a, op->diag64.as<double>()));
     }
     op->diag_ready = true;
   }

@@ -57,7 +57,8 @@ template <bool OCT>
 __global__ void k_scalar_qtables(UniformGeom ug, OctGeom og, int kind, const double* field, const double* kq_user,
                                  const double* beta, int64_t nd, double k0, double kslope, double a_l, double a_g,
                                  int hv, double eps, double rhocp, int64_t ncp, double* qc64, float* qc32,
-                                 double* qv64, float* qv32) {
+                                 double* qv64, float* qv32, const double* rhocp_q, const double* beta_q, double dt,
+                                 double* qm64, float* qm32) {
   Loc L;
   const int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (!natural_cell<OCT>(ug, og, t, L)) return;
@@ -80,14 +81,26 @@ __global__ void k_scalar_qtables(UniformGeom ug, OctGeom og, int kind, const dou
       qc64[q * ncp + L.cell] = k;
       qc32[q * ncp + L.cell] = float(k);
     }
-    if (beta) {
+    if (rhocp_q) {
+      for (int q = 0; q < 27; ++q) {
+        const double m = rhocp_q[L.cell * 27 + q] / dt;
+        qm64[q * ncp + L.cell] = m;
+        qm32[q * ncp + L.cell] = float(m);
+      }
+    }
+    if (beta || beta_q) {
       for (int d = 0; d < 3; ++d) {
         double B[27];
-        gather64<OCT, false>(ug, og, L, beta + d * nd, B);
-        to_qpoints<double>(B);
+        if (beta_q) {
+          for (int q = 0; q < 27; ++q) B[q] = beta_q[(L.cell * 27 + q) * 3 + d];
+        } else {
+          gather64<OCT, false>(ug, og, L, beta + d * nd, B);
+          to_qpoints<double>(B);
+        }
         for (int q = 0; q < 27; ++q) {
-          qv64[(d * 27 + q) * ncp + L.cell] = rhocp * B[q];
-          qv32[(d * 27 + q) * ncp + L.cell] = float(rhocp * B[q]);
+          const double v = (rhocp_q ? rhocp_q[L.cell * 27 + q] : rhocp) * B[q];
+          qv64[(d * 27 + q) * ncp + L.cell] = v;
+          qv32[(d * 27 + q) * ncp + L.cell] = float(v);
         }
       }
     }
@@ -273,7 +286,7 @@ __global__ void k_scalar_diag(ScalarArgs<double> A, int kind, bool beta, Uniform
   double out[27], c[27];
   for (int i = 0; i < 27; ++i) out[i] = 0.0;
   // mass
-  for (int q = 0; q < 27; ++q) c[q] = cW364[q] * h * h * h * A.mass;
+  for (int q = 0; q < 27; ++q) c[q] = cW364[q] * h * h * h * (A.qmass ? A.qmass[q * A.ncp + L.cell] : A.mass);
   separable_add(c, cSS64, cSS64, cSS64, out);
   if (kind == K_HELM || kind == K_HEAT) {
     for (int q = 0; q < 27; ++q) c[q] = cW364[q] * h * A.qcoef[q * A.ncp + L.cell];
@@ -519,17 +532,20 @@ inline int blocks(int64_t n, int b) { return int((n + b - 1) / b); }
 
 mf_status launch_scalar_qtables(mf_ctx* ctx, const mf_dofmap* m, int kind, const double* field, const double* kq_user,
                                 const double* beta, double k0, double k_slope, double a_l, double a_g, int hv,
-                                double eps, double rhocp, double* qc64, float* qc32, double* qv64, float* qv32) {
+                                double eps, double rhocp, double* qc64, float* qc32, double* qv64, float* qv32,
+                                const double* rhocp_q, const double* beta_q, double dt, double* qm64, float* qm32) {
   MF_CUDA_TRY(upload_tables_here());
   UniformGeom ug = m->uniform ? uniform_geom(m) : UniformGeom{};
   OctGeom og = oct_geom(m);
   const int64_t ncp = m->n_cells;
   if (m->uniform)
     k_scalar_qtables<false><<<blocks(m->n_cells, 128), 128, 0, ctx->stream>>>(
-        ug, og, kind, field, kq_user, beta, m->n_dofs, k0, k_slope, a_l, a_g, hv, eps, rhocp, ncp, qc64, qc32, qv64, qv32);
+        ug, og, kind, field, kq_user, beta, m->n_dofs, k0, k_slope, a_l, a_g, hv, eps, rhocp, ncp, qc64, qc32, qv64, qv32,
+        rhocp_q, beta_q, dt, qm64, qm32);
   else
     k_scalar_qtables<true><<<blocks(m->n_cells, 128), 128, 0, ctx->stream>>>(
-        ug, og, kind, field, kq_user, beta, m->n_dofs, k0, k_slope, a_l, a_g, hv, eps, rhocp, ncp, qc64, qc32, qv64, qv32);
+        ug, og, kind, field, kq_user, beta, m->n_dofs, k0, k_slope, a_l, a_g, hv, eps, rhocp, ncp, qc64, qc32, qv64, qv32,
+        rhocp_q, beta_q, dt, qm64, qm32);
   ctx->launches++;
   MF_CUDA_TRY(cudaGetLastError());
   return MF_OK;

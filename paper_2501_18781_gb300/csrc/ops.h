@@ -19,6 +19,7 @@ template <typename T> struct ScalarArgs {
   const T* field;   // nodal phi (Helmholtz, reinit) or T^n (heat) for in-kernel coefficients
   const T* qcoef;   // [27][ncp] scalar coefficient per Gauss point (a, k) when tabulated
   const T* qvec;    // [3][27][ncp] rho_cp beta (heat) or n (reinit) per Gauss point
+  const T* qmass;   // [27][ncp] value-term coefficient per Gauss point (heat with rho_cp,q), or NULL
   int64_t ncp;      // stride of the Gauss-point tables (number of cells)
   T mass;           // value-term coefficient
   T a_l, a_g;       // Helmholtz: a = a_g + (a_l - a_g) H
@@ -63,9 +64,12 @@ mf_status launch_oseen_apply(mf_ctx* ctx, const mf_dofmap* mu, int prec, const v
 mf_status launch_oseen_coupling_f64(mf_ctx* ctx, const mf_dofmap* mu, int which, const double* src, double* dst);
 mf_status launch_oseen_coupling_f32(mf_ctx* ctx, const mf_dofmap* mu, int which, const float* src, float* dst);
 // Gauss-point tables from nodal fp64 fields (always evaluated in fp64, stored in both precisions)
+// (heat: rhocp_q / beta_q are the optional per-Gauss-point fields; qmass gets rhocp_q / dt)
 mf_status launch_scalar_qtables(mf_ctx* ctx, const mf_dofmap* m, int kind, const double* field, const double* kq_user,
                                 const double* beta, double k0, double k_slope, double a_l, double a_g, int heaviside,
-                                double eps, double rhocp, double* qcoef64, float* qcoef32, double* qvec64, float* qvec32);
+                                double eps, double rhocp, double* qcoef64, float* qcoef32, double* qvec64, float* qvec32,
+                                const double* rhocp_q = nullptr, const double* beta_q = nullptr, double dt = 1.0,
+                                double* qmass64 = nullptr, float* qmass32 = nullptr);
 mf_status launch_oseen_qtables(mf_ctx* ctx, const mf_dofmap* mu, const double* phi, const double* beta, double rho_l,
                                double rho_g, double mu_l, double mu_g, int heaviside, double eps, double* rho64,
                                float* rho32, double* muq64, float* muq32, double* beta64, float* beta32);
@@ -113,10 +117,13 @@ struct mf_op {
   const double* tprev = nullptr;
   const double* beta = nullptr;
   const double* kq_user = nullptr;
+  const double* rhocp_user = nullptr;   // heat: rho_cp per Gauss point [cell][27]
+  const double* betaq_user = nullptr;   // heat: convection velocity per Gauss point [cell][27][3]
   // owned copies / tables
   mf::DevBuf field32;             // float copy of the in-kernel nodal field
   mf::DevBuf qcoef64, qcoef32;    // [27][ncells]
   mf::DevBuf qvec64, qvec32;      // [3][27][ncells]
+  mf::DevBuf qmass64, qmass32;    // [27][ncells] heat value term rho_cp,q / dt
   mf::DevBuf rho64, rho32, mu64, mu32;  // Oseen
   mf::DevBuf kd64, kd32, nrm64, nrm32;  // Oseen melt-pool extensions
   mf::DevBuf cm64, cm32, cc64, cc32, cv64, cv32;  // Oseen folded Gauss-point coefficients

@@ -40,7 +40,12 @@ __device__ __forceinline__ void scalar_local(const ScalarArgs<typename Store<T>:
         const int q = qa + 3 * qb + 9 * qc;
         const T w = Tb<T>::W3(q);
         const T u = U[q];
-        T fv = w * (mh2 * u);
+        T fv;
+        if constexpr (KIND == K_HEAT) {  // rho_cp / dt per Gauss point when the heat capacity varies
+          fv = A.qmass ? w * ((from_store<T>(__ldg(A.qmass + q * A.ncp + cell)) * (h * h)) * u) : w * (mh2 * u);
+        } else {
+          fv = w * (mh2 * u);
+        }
         if constexpr (KIND == K_MASS) {
           R[q] += fv;
           continue;

@@ -18,6 +18,8 @@ template <typename T>
 mf_status apply_impl(mf_op* op, const T* src, T* dst, int nrhs, int64_t ld, bool transpose, int prec = -1);
 mf_status diag64(mf_op* op, double** out);
 mf_status check_fields(const mf_op* op);
+bool heat_convection(const mf_op* op);
+bool heat_tabulated(const mf_op* op);
 mf_status ensure_tables(mf_op* op);
 int scalar_kind(const mf_op* op);
 double value_coef(const mf_op* op);
@@ -680,7 +682,7 @@ mf_status solve_impl(mf_op* op, const mf_solver_params* sp, const double* b, dou
   if (sp->precond == MF_PREC_BLOCK_TRIANGULAR && sp->solver != MF_SOLVER_GMRES)
     return fail(MF_EINVAL, "the block-triangular preconditioner needs the GMRES solver");
   if (sp->solver == MF_SOLVER_CG) {
-    if (transpose && op->p.kind == MF_OP_HEAT && op->beta) return fail(MF_EINVAL, "CG on a nonsymmetric operator");
+    if (transpose && heat_convection(op)) return fail(MF_EINVAL, "CG on a nonsymmetric operator");
     Prec<double> P;
     MF_TRY(P.setup(op, sp->precond, deg, ratio, lsteps, nrhs));
     inf.lambda_max = P.lmax;
@@ -824,6 +826,7 @@ mf_status mf_heat_step_gradient(mf_op* op, const mf_laser* lz, const mf_solver_p
     if (!op || !lz || !sp || !theta_prev || !theta_target || !J || !dJ_dlaser) return fail(MF_EINVAL, "NULL argument");
     if (op->p.kind != MF_OP_HEAT) return fail(MF_EINVAL, "heat operators only");
     if (dJ_dkq && !op->kq_user) return fail(MF_EINVAL, "dJ/dk_q needs MF_FIELD_K_QPOINT");
+    if (op->rhocp_user || op->betaq_user) return fail(MF_EUNSUPPORTED, "heat-step gradient with Gauss-point rho_cp / beta");
     mf_ctx* c = op->ctx;
     const mf_dofmap* m = op->map[0];
     if (!m->uniform) return fail(MF_EUNSUPPORTED, "heat-step gradient on octree maps");
@@ -933,7 +936,7 @@ mf_status mf_autotune(mf_op* op, const char* cache_path) {
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
-    const bool forced = op->p.kind == MF_OP_HEAT && (op->kq_user || op->beta);
+    const bool forced = heat_tabulated(op);
     DevBuf s32, d32;
     MF_TRY(s32.alloc(sizeof(float) * n));
     MF_TRY(d32.alloc(sizeof(float) * n));

@@ -9,7 +9,7 @@
 // Every value is evaluated in fp64 at the 27 Gauss points of a cell from the nodal phi and T.
 #include <cmath>
 
-#include "scalar_local.cuh"
+#include "interface.cuh"
 
 namespace mf {
 
@@ -31,20 +31,6 @@ struct SourceArgs {
   double c_rho, c_rhocp;
   double kappa, inv_t_boil, knight_coef;  // h_v M / R, 1 / T_v, 0.82 c_s p_amb sqrt(M / (2 pi R))
 };
-
-// eq. (delta) at a Gauss point from phi_h and its physical gradient
-__device__ __forceinline__ double delta_at(double phi, double g, int kind, double eps) {
-  if (kind == 0) {
-    const double H = 0.5 * (1.0 + phi);
-    return (H > 0.0 && H < 1.0) ? 0.5 * g : 0.0;
-  }
-  const double lim = 1.0 - 2.220446049250313e-16;
-  const double p = phi > lim ? lim : (phi < -lim ? -lim : phi);
-  const double d = 2.0 * eps * atanh(p);
-  if (!(fabs(d) < 3.0 * eps)) return 0.0;
-  const double pi = 3.141592653589793;
-  return (1.0 + cos(pi * d / (3.0 * eps))) / (6.0 * eps) * 2.0 * eps * g / (1.0 - p * p);
-}
 
 template <bool RECOIL>
 __global__ void __launch_bounds__(128) k_interface_sources(SourceArgs A, UniformGeom ug) {

@@ -269,7 +269,7 @@ def test_update_form_of_the_heat_solve_equals_the_lifted_form():
     phi = np.tanh((0.6 - X[:, 2]) / 0.3)
     u = np.stack([X[:, 1] - 0.5, 0.5 - X[:, 0], 0.2 + 0 * X[:, 2]])
     prm = _params(dt=0.05)
-    A, rhs, r = st.heat_system(maps, T, u, T, phi, prm)
+    A, rhs, r, _ = st.heat_system(maps, T, u, T, phi, prm)
     lifted = sla.spsolve(A.tocsc(), rhs)
     assert np.array_equal(lifted[maps[3].dirichlet], T[maps[3].dirichlet])
     assert np.abs(T + sla.spsolve(A.tocsc(), r) - lifted).max() <= 1e-12 * np.abs(T).max()
