@@ -414,6 +414,7 @@ typedef struct {
   double* phi_advected;  /* n_u */
   double* r_heat;        /* n_u: s + M_{rho_cp/dt} T^n - A T^n, Dirichlet rows 0 */
   double* b_flow;        /* 3 n_u + n_p */
+  double* T_update;      /* n_u: the solved T^(n+1) - T^n */
 } mf_meltpool_trace;
 
 /* maps: velocity (Q2), pressure (Q1), level set (Q2, no Dirichlet faces), temperature (Q2), one

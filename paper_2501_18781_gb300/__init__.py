@@ -317,7 +317,8 @@ class MeltPoolStep:
     fields (mass_flux "knight" | "tanasawa"), ``laser`` a dict (power, radius, absorptivity, focus,
     direction) or None."""
 
-    TRACE = ("u_star", "T_star", "phi_star", "u_gamma", "b_advection", "phi_advected", "r_heat", "b_flow")
+    TRACE = ("u_star", "T_star", "phi_star", "u_gamma", "b_advection", "phi_advected", "r_heat", "b_flow",
+             "T_update")
 
     def __init__(self, ctx, maps, evaporation, laser=None, gravity=(0.0, 0.0, 0.0), **params):
         p = _lib.MeltPoolParams()
@@ -353,7 +354,7 @@ class MeltPoolStep:
         tr, trp = {}, None
         if trace:
             sizes = dict(u_star=3 * nu, T_star=nu, phi_star=nu, u_gamma=81 * nc, b_advection=nu,
-                         phi_advected=nu, r_heat=nu, b_flow=3 * nu + npr)
+                         phi_advected=nu, r_heat=nu, b_flow=3 * nu + npr, T_update=nu)
             tr = {k: torch.empty(sizes[k], **kw) for k in self.TRACE}
             trp = _lib.MeltPoolTrace(*[tr[k].data_ptr() for k in self.TRACE])
         inf = _lib.MeltPoolInfo()

@@ -77,7 +77,7 @@ class MeltPoolInfo(C.Structure):
 
 class MeltPoolTrace(C.Structure):
     _fields_ = [(k, C.c_void_p) for k in ("u_star", "T_star", "phi_star", "u_gamma", "b_advection",
-                                          "phi_advected", "r_heat", "b_flow")]
+                                          "phi_advected", "r_heat", "b_flow", "T_update")]
 
 
 P = C.c_void_p

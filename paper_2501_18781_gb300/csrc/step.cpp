@@ -290,6 +290,7 @@ mf_status mf_meltpool_advance(mf_meltpool_step* step, const double* u_prev, cons
     if (trace) MF_TRY(copy_out(c, trace->r_heat, r, nu));
     MF_TRY(run_solve(S.heat, scalar_solver(MF_SOLVER_GMRES, p.tol, maxit), r, S.d.as<double>(),
                      &inf.heat_iterations, &inf.heat_residual, &worst));
+    if (trace) MF_TRY(copy_out(c, trace->T_update, S.d.as<double>(), nu));
     MF_CUDA_TRY(cudaMemcpyAsync(T_out, T, sizeof(double) * nu, cudaMemcpyDeviceToDevice, c->stream));
     MF_TRY(mf::axpby<double, double>(c, nu, 1.0, S.d.as<double>(), 1.0, T_out));
     MF_TRY(lap(2, t));
