@@ -1,4 +1,4 @@
-"""Q_k Lagrange bases on equispaced nodes and tensor Gauss rules (Appendix B).
+"""Q_k Lagrange bases and tensor Gauss rules (Appendix B).
 
 Everything is evaluated directly from its definition: a 1D Lagrange polynomial as a
 product over the other nodes, a 3D shape function as the product of three 1D ones.
@@ -14,8 +14,13 @@ def gauss_rule_01(npts):
 
 
 def lagrange_nodes(k):
-    """Equispaced nodes on [0, 1]: {0, 1} for k = 1 and {0, 1/2, 1} for k = 2."""
-    return np.linspace(0.0, 1.0, k + 1)
+    """Support points on [0, 1]: {0, 1} for k = 1, {0, 1/2, 1} for k = 2 (equispaced and
+    Gauss-Lobatto coincide), and the Gauss-Lobatto points for k >= 3: the ends and the roots of
+    P_k', the derivative of the Legendre polynomial of degree k (numpy's root finder)."""
+    if k <= 2:
+        return np.linspace(0.0, 1.0, k + 1)
+    inner = np.sort(np.polynomial.legendre.Legendre.basis(k).deriv().roots().real)
+    return np.concatenate([[0.0], 0.5 * (inner + 1.0), [1.0]])
 
 
 def lagrange_1d(k, x):

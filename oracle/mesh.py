@@ -44,11 +44,17 @@ class DofMap:
         return self.cell_points.shape[0]
 
     def dof_coords(self):
-        """Physical coordinates of the free DoFs, in DoF order."""
+        """Physical coordinates of the free DoFs, in DoF order (for k >= 3, uniform meshes: lattice
+        coordinate k c + a sits at the support point xi_a of cell c)."""
         free = np.nonzero(self.free_of_point >= 0)[0]
         order = np.argsort(self.free_of_point[free])
-        p = self.points[free[order]].astype(np.float64)
-        return self.lo + p * (self.hspan / self.R)
+        p = self.points[free[order]]
+        if self.degree <= 2:
+            return self.lo + p.astype(np.float64) * (self.hspan / self.R)
+        from .basis import lagrange_nodes
+        k, n = self.degree, self.R // self.degree
+        c = np.minimum(p // k, n - 1)
+        return self.lo + (c + lagrange_nodes(k)[p - k * c]) * (self.hspan / n)
 
     def export(self):
         """Integer cell map (free index, or -(1 + hanging rank)) and the constraint rows
