@@ -530,6 +530,41 @@ def meltpool_step(ctx, n=64, reps=3):
             "status": info["status"], "tol": p["tol"], "flow_tol": p["flow_tol"]}
 
 
+def qk_flops_per_cell(k):
+    """Sum-factorised Q_k Helmholtz apply, P = k + 1: 3 interpolation sweeps, 3 collocation
+    derivatives, 3 transposed derivatives and 3 transposed sweeps of P^4 multiply-adds each, and
+    about 10 flops per Gauss point for the pointwise work."""
+    P = k + 1
+    return 2 * 12 * P ** 4 + 10 * P ** 3
+
+
+def helmholtz_qk(ctx, flush):
+    """Q3 on 64^3 and Q4 on 48^3 cells (193^3 = 7,189,057 DoFs each), the sphere coefficient
+    a = 1 + 999 H(phi): fp64 and fp32 applies with the L2 flushed."""
+    import torch
+    import synthetic as syn
+    from paper_2501_18781_gb300 import DofMap, Mesh, Operator
+    out = {}
+    for k, n in ((3, 64), (4, 48)):
+        m = DofMap(Mesh.uniform(ctx, n), k, 0)
+        eps = 1.0 / (2 * n)
+        phi = torch.tensor(syn.initial_level_set(syn.sphere_distance(*m.coords().T), eps), device="cuda")
+        op = Operator(ctx, "helmholtz", [m], mass_coef=1.0, a_liquid=1000.0, a_gas=1.0, eps=eps)
+        op.set_field("phi", phi)
+        fl = qk_flops_per_cell(k) * m.n_cells
+        r = {"cells": m.n_cells, "n_dofs": m.n_dofs, "flops_per_cell": qk_flops_per_cell(k)}
+        for dt in (torch.float64, torch.float32):
+            u = torch.tensor(syn.uniform_pm1(1, m.n_dofs), device="cuda").to(dt)
+            v = torch.empty_like(u)
+            op.apply(u, v)
+            ms = _event_ms(lambda: op.apply(u, v), 10, flush)
+            r["f64" if dt == torch.float64 else "f32"] = {"ms": ms, "gdofs": m.n_dofs / ms / 1e6,
+                                                          "tflops": fl / ms / 1e9, "variant": op.variant}
+        r["f64"]["frac_of_fp64_peak"] = r["f64"]["tflops"] / FP64_PEAK_TFLOPS
+        out[f"q{k}"] = r
+    return out
+
+
 def interface_sources_timing(ctx, op, mu, flush, reps=10):
     """The fused interface-source kernel (evaporative dilation, cooling and hybrid recoil loads)
     on the Oseen mesh, Knight's mass flux, a hot spot across the interface."""
@@ -554,6 +589,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--suite", action="store_true", help="also measure the other benchmark workloads")
     ap.add_argument("--meltpool-step", action="store_true", help="also time one melt-pool algorithm step")
+    ap.add_argument("--qk", action="store_true", help="also time the Q3 / Q4 Helmholtz applies")
     ap.add_argument("--n", type=int, default=64)
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
@@ -658,6 +694,8 @@ def main():
     if args.suite and rank == 0:
         out["workloads"] = workload_suite(ctx, flush)
         out["workloads"]["oseen_meltpool"] = meltpool_oseen(ctx, args.n, flush)
+    if (args.suite or args.qk) and rank == 0:
+        out.setdefault("workloads", {})["helmholtz_qk"] = helmholtz_qk(ctx, flush)
     if (args.suite or args.meltpool_step) and rank == 0:
         out.setdefault("workloads", {})["meltpool_step"] = meltpool_step(ctx, args.n)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

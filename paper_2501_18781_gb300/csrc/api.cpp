@@ -198,7 +198,8 @@ mf_status mf_dofmap_create(mf_mesh* mesh, int degree, uint32_t faces, mf_dofmap*
   MF_GUARD_BEGIN
   if (!mesh || !out) return fail(MF_EINVAL, "NULL argument");
   *out = nullptr;
-  if (degree != 1 && degree != 2) return fail(MF_EUNSUPPORTED, "degree must be 1 or 2");
+  if (degree < 1 || degree > 4) return fail(MF_EUNSUPPORTED, "degree must be 1 to 4");
+  if (degree > 2 && mesh->octree) return fail(MF_EUNSUPPORTED, "degrees 3 and 4 on uniform meshes only");
   if (faces >> 6) return fail(MF_EINVAL, "dirichlet_faces has bits above 5");
   auto* m = new mf_dofmap();
   m->mesh = mesh;
@@ -264,10 +265,31 @@ mf_status mf_dofmap_export(const mf_dofmap* m, int32_t* cell_map, int64_t* con_r
       span[d] = (me->hi[d] - me->lo[d]) / double(m->R[d]);
       lo[d] = me->lo[d];
     }
+    // degrees 3 and 4: lattice coordinate k c + a sits at the Gauss-Lobatto point xi_a of cell c
+    double xi[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+    if (k == 3) {
+      const double r = 1.0 / std::sqrt(5.0);
+      xi[1] = 0.5 * (1.0 - r);
+      xi[2] = 0.5 * (1.0 + r);
+      xi[3] = 1.0;
+    } else if (k == 4) {
+      const double r = std::sqrt(3.0 / 7.0);
+      xi[1] = 0.5 * (1.0 - r);
+      xi[2] = 0.5;
+      xi[3] = 0.5 * (1.0 + r);
+      xi[4] = 1.0;
+    }
     for (int64_t d = 0; d < m->n_dofs; ++d) {
       const int64_t key = m->uniform ? d : m->free_keys[d];
       const int64_t p[3] = {key % Rx, (key / Rx) % Ry, key / (Rx * Ry)};
-      for (int a = 0; a < 3; ++a) coords[3 * d + a] = lo[a] + double(p[a]) * span[a];
+      for (int a = 0; a < 3; ++a) {
+        if (k <= 2) {
+          coords[3 * d + a] = lo[a] + double(p[a]) * span[a];
+        } else {
+          const int64_t n = m->R[a] / k, c = std::min<int64_t>(p[a] / k, n - 1);
+          coords[3 * d + a] = lo[a] + (double(c) + xi[p[a] - k * c]) * ((me->hi[a] - me->lo[a]) / double(n));
+        }
+      }
     }
   }
   if (dirichlet) std::memcpy(dirichlet, m->dirichlet.data(), m->dirichlet.size());
@@ -291,6 +313,9 @@ mf_status mf_operator_create(mf_ctx* c, const mf_op_params* p, const mf_dofmap* 
         !maps[0]->uniform)
       return fail(MF_EINVAL, "Oseen needs a Q2 and a Q1 map on the same uniform mesh");
     if (maps[1]->dirichlet_faces) return fail(MF_EUNSUPPORTED, "Dirichlet pressure DoFs");
+  } else if (nmaps == 1 && maps[0] && maps[0]->degree >= 3) {
+    if (p->kind != MF_OP_HELMHOLTZ) return fail(MF_EUNSUPPORTED, "degrees 3 and 4: the Helmholtz operator only");
+    if (maps[0]->dirichlet_faces) return fail(MF_EUNSUPPORTED, "degrees 3 and 4: no Dirichlet faces");
   } else {
     if (nmaps != 1 || !is_q2(maps[0])) return fail(MF_EINVAL, "scalar operators need one Q2 map");
   }
@@ -411,6 +436,9 @@ bool heat_tabulated(const mf_op* op) {
   return op->p.kind == MF_OP_HEAT && (op->beta || op->kq_user || op->rhocp_user || op->betaq_user);
 }
 
+// 3 or 4 for the Q3/Q4 Helmholtz operators, else 0
+int qk_degree(const mf_op* op) { return op->map[0] && op->map[0]->degree >= 3 ? op->map[0]->degree : 0; }
+
 mf_status check_fields(const mf_op* op) {
   switch (op->p.kind) {
     case MF_OP_HELMHOLTZ:
@@ -462,6 +490,12 @@ mf_status ensure_tables(mf_op* op) {
                              p.oseen_flags ? op->kd64.as<double>() : nullptr, op->cm64.as<double>(),
                              op->cm32.as<float>(), op->cc64.as<double>(), op->cc32.as<float>(), op->cv64.as<double>(),
                              op->cv32.as<float>()));
+  } else if (qk_degree(op)) {
+    const int64_t P3 = int64_t(qk_degree(op) + 1) * (qk_degree(op) + 1) * (qk_degree(op) + 1);
+    MF_TRY(op->qcoef64.alloc(sizeof(double) * P3 * nc));
+    MF_TRY(op->qcoef32.alloc(sizeof(float) * P3 * nc));
+    MF_TRY(launch_qk_coef(op->ctx, op->map[0], op->phi, p.a_liquid, p.a_gas, p.heaviside, p.eps,
+                          op->qcoef64.as<double>(), op->qcoef32.as<float>()));
   } else {
     const int kind = scalar_kind(op);
     MF_TRY(op->qcoef64.alloc(sizeof(double) * 27 * nc));
@@ -589,6 +623,20 @@ mf_status apply_impl(mf_op* op, const T* src, T* dst, int nrhs, int64_t ld, bool
   const bool f32 = sizeof(T) == 4;
   if (f32) prec = (prec == PREC_F16 || prec == PREC_BF16 || prec == PREC_F32) ? prec : op->f32_prec;
   else if (prec != PREC_F64 && prec != PREC_DF64) prec = op->f64_prec;
+  if (qk_degree(op)) {  // Q3 / Q4 Helmholtz: symmetric, fp64 or fp32 arithmetic
+    if (prec != PREC_F64 && prec != PREC_F32) return fail(MF_EUNSUPPORTED, "degrees 3 and 4: fp64 or fp32 applies");
+    MF_TRY(check_fields(op));
+    MF_TRY(ensure_tables(op));
+    const T* coef = f32 ? reinterpret_cast<const T*>(op->qcoef32.as<float>())
+                        : reinterpret_cast<const T*>(op->qcoef64.as<double>());
+    for (int r = 0; r < nrhs; ++r) {
+      MF_CUDA_TRY(cudaMemsetAsync(dst + r * ld, 0, sizeof(T) * op->n, op->ctx->stream));
+      MF_TRY(launch_helmholtz_qk<T>(op->ctx, op->map[0], src + r * ld, dst + r * ld, coef, op->p.mass_coef));
+    }
+    op->variant = std::string("helmholtz_q") + std::to_string(qk_degree(op)) + "/uniform" + (f32 ? "/f32" : "/f64") +
+                  "/tabulated/line-per-thread";
+    return MF_OK;
+  }
   if constexpr (sizeof(T) == 4) {
     if (prec == PREC_F16 || prec == PREC_BF16) return apply_h16(op, src, dst, nrhs, ld, transpose, prec);
   }
@@ -653,7 +701,10 @@ template mf_status apply_impl<float>(mf_op*, const float*, float*, int, int64_t,
 mf_status diag64(mf_op* op, double** out) {
   if (!op->diag_ready) {
     MF_TRY(ensure_tables(op));
-    if (op->p.kind == MF_OP_OSEEN) {
+    if (qk_degree(op)) {
+      MF_TRY(op->diag64.alloc(sizeof(double) * op->n));
+      MF_TRY(launch_qk_diag(op->ctx, op->map[0], op->qcoef64.as<double>(), op->p.mass_coef, op->diag64.as<double>()));
+    } else if (op->p.kind == MF_OP_OSEEN) {
       const int64_t nu = op->map[0]->n_dofs, np = op->map[1]->n_dofs;
       MF_TRY(op->blk64.alloc(sizeof(double) * 9 * nu));
       MF_TRY(op->pdiag64.alloc(sizeof(double) * np));

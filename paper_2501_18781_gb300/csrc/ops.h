@@ -98,6 +98,12 @@ mf_status abs_max_f32(mf_ctx* ctx, const float* x, int64_t n, float* out);
 mf_status launch_interface_sources(mf_ctx* ctx, const mf_dofmap* mu, const mf_dofmap* mp, const mf_op_params& p,
                                    const double* phi, const mf_evaporation& ev, const double* T, double* fu,
                                    double* fp, double* fT);
+// Q3 / Q4 Helmholtz (uniform maps): Gauss-point coefficient table [cell][q], apply, diagonal
+mf_status launch_qk_coef(mf_ctx* ctx, const mf_dofmap* m, const double* phi, double a_l, double a_g, int heaviside,
+                         double eps, double* c64, float* c32);
+template <typename T>
+mf_status launch_helmholtz_qk(mf_ctx* ctx, const mf_dofmap* m, const T* src, T* dst, const T* coef, double mass);
+mf_status launch_qk_diag(mf_ctx* ctx, const mf_dofmap* m, const double* coef, double mass, double* diag);
 // laser top-face load and its parameter derivatives (uniform maps)
 mf_status launch_laser(mf_ctx* ctx, const mf_dofmap* m, const double lz[5], double* f, double* dF);
 // dJ/dk_q = -w_q h grad(lambda) . grad(theta), [cell][27]

@@ -19,6 +19,7 @@ mf_status apply_impl(mf_op* op, const T* src, T* dst, int nrhs, int64_t ld, bool
 mf_status diag64(mf_op* op, double** out);
 mf_status check_fields(const mf_op* op);
 bool heat_convection(const mf_op* op);
+int qk_degree(const mf_op* op);
 bool heat_tabulated(const mf_op* op);
 mf_status ensure_tables(mf_op* op);
 int scalar_kind(const mf_op* op);
@@ -888,6 +889,10 @@ mf_status mf_autotune(mf_op* op, const char* cache_path) {
     MF_TRY(check_fields(op));
     mf_ctx* c = op->ctx;
     const int64_t n = op->n;
+    if (qk_degree(op)) {  // Q3 / Q4: one kernel variant per precision, nothing to choose
+      op->tune_record = "{\"variants\": \"helmholtz_q" + std::to_string(qk_degree(op)) + ": one\"}";
+      return MF_OK;
+    }
     if (op->p.kind == MF_OP_OSEEN) {
       // fp64 kernel variant: component loop outside (fewer registers) or Gauss-point loop outside
       // (fewer fp64 operations, spills)

@@ -63,6 +63,20 @@ def test_uniform_maps_match_oracle(n, deg, faces):
     _compare_maps(ours, omesh.uniform_dofmap(n, lo, hi, deg, faces))
 
 
+@pytest.mark.parametrize("n,deg", [(1, 3), (3, 3), (2, 4), (3, 4)])
+def test_q3_q4_maps_match_oracle(n, deg):
+    """Degrees 3 and 4 (Gauss-Lobatto support points): integer maps bit for bit, coordinates to the
+    rounding of the closed-form Lobatto points against the oracle's root finder."""
+    lo, hi = (-3e-4,) * 3, (3e-4,) * 3
+    ours = DofMap(Mesh.uniform(None, n, lo, hi), deg, 0)
+    theirs = omesh.uniform_dofmap(n, lo, hi, deg, 0)
+    e = ours.export()
+    cm, _, _, _ = theirs.export()
+    assert ours.n_dofs == theirs.n_dofs and np.array_equal(e["cell_map"], cm)
+    assert np.abs(e["coords"] - theirs.dof_coords()).max() <= 1e-15 * 6e-4
+    assert not e["dirichlet"].any()
+
+
 def _leaves_small():
     L = [[0, i, j, k] for k in range(2) for j in range(2) for i in range(2) if (i, j, k) != (0, 0, 0)]
     L += [[1, i, j, k] for k in range(2) for j in range(2) for i in range(2)]

@@ -1,0 +1,97 @@
+"""Q3/Q4 Helmholtz operators (Gauss-Lobatto support points, (k+1)^3 Gauss points) on the GPU against
+the oracle's assembled matrices: applies componentwise (fp64 1e-12, fp32 5e-5 of (|A||u|)_i), the
+diagonal, Jacobi- and Chebyshev-preconditioned CG by the oracle's true residual, and the
+combinations the boundary rejects."""
+import numpy as np
+import pytest
+
+import synthetic as syn
+from oracle import assemble as asm
+from oracle import mesh as omesh
+from problems import componentwise_ok
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_2501_18781_gb300 import Context, build_library
+    build_library()
+    return Context(0)
+
+
+def _problem(ctx, k, n, heaviside="tanh"):
+    from paper_2501_18781_gb300 import DofMap, Mesh, Operator
+    dm = omesh.uniform_dofmap(n, (0, 0, 0), (1, 1, 1), k)
+    eps = 1.0 / (2 * n)
+    phi = syn.initial_level_set(syn.sphere_distance(*dm.dof_coords().T), eps)
+    A = asm.helmholtz_matrix(dm, phi, 1.0, 1000.0, 1.0, heaviside, eps)
+    m = DofMap(Mesh.uniform(ctx, n), k, 0)
+    op = Operator(ctx, "helmholtz", [m], mass_coef=1.0, a_liquid=1000.0, a_gas=1.0, eps=eps,
+                  heaviside=0 if heaviside == "tanh" else 1)
+    op.set_field("phi", torch.tensor(phi, device="cuda"))
+    assert m.n_dofs == dm.n_dofs
+    return dm, A, op
+
+
+@pytest.mark.parametrize("k", [3, 4])
+@pytest.mark.parametrize("n", [1, 3, 4])
+def test_qk_apply_matches_oracle(ctx, k, n):
+    dm, A, op = _problem(ctx, k, n)
+    u = syn.uniform_pm1(k + n, dm.n_dofs)
+    ref, bound = A @ u, abs(A) @ np.abs(u)
+    v = op.apply(torch.tensor(u, device="cuda")).cpu().numpy()
+    ok, worst = componentwise_ok(v, ref, bound, 1e-12)
+    assert ok, worst
+    v32 = op.apply(torch.tensor(u, device="cuda").float()).cpu().double().numpy()
+    ok, worst = componentwise_ok(v32, ref, bound, 5e-5)
+    assert ok, worst
+    assert op.variant.startswith(f"helmholtz_q{k}/")
+
+
+def test_qk_sine_heaviside_and_strided_batch(ctx):
+    dm, A, op = _problem(ctx, 3, 3, heaviside="sine")
+    n, ld = dm.n_dofs, dm.n_dofs + 11
+    U = np.zeros((2, ld))
+    U[0, :n], U[1, :n] = syn.uniform_pm1(1, n), syn.uniform_pm1(2, n)
+    out = op.apply(torch.tensor(U.ravel(), device="cuda"), nrhs=2).cpu().numpy().reshape(2, ld)
+    for r in range(2):
+        ok, worst = componentwise_ok(out[r, :n], A @ U[r, :n], abs(A) @ np.abs(U[r, :n]), 1e-12)
+        assert ok, (r, worst)
+
+
+@pytest.mark.parametrize("k", [3, 4])
+def test_qk_diagonal(ctx, k):
+    dm, A, op = _problem(ctx, k, 3)
+    d = op.diagonal().cpu().numpy()
+    assert np.abs(d - A.diagonal()).max() <= 1e-12 * np.abs(A.diagonal()).max()
+
+
+@pytest.mark.parametrize("k,precond", [(3, "jacobi"), (4, "jacobi"), (3, "chebyshev")])
+def test_qk_cg_reaches_tolerance_on_the_oracle_matrix(ctx, k, precond):
+    dm, A, op = _problem(ctx, k, 4)
+    b = syn.uniform_pm1(7, dm.n_dofs)
+    x, info = op.solve(torch.tensor(b, device="cuda"), solver="cg", precond=precond, tol=1e-10)
+    assert info["status"] == 0, info
+    res = np.linalg.norm(b - A @ x.cpu().numpy()) / np.linalg.norm(b)
+    assert res <= 1e-10 * (1 + 1e-3), (res, info)
+
+
+def test_qk_rejections(ctx):
+    from paper_2501_18781_gb300 import DofMap, Mesh, Operator
+    from paper_2501_18781_gb300._lib import MFError
+    mesh = Mesh.uniform(ctx, 2)
+    with pytest.raises(MFError):
+        Operator(ctx, "helmholtz", [DofMap(mesh, 3, 1 << 4)], mass_coef=1.0, a_liquid=2.0, a_gas=1.0)
+    with pytest.raises(MFError):
+        Operator(ctx, "heat", [DofMap(mesh, 4, 0)], rhocp=1.0, dt=1.0, k0=1.0, t_boil=1.0)
+    _, _, op = _problem(ctx, 3, 2)
+    with pytest.raises(MFError):
+        op.apply(torch.zeros(op.n, dtype=torch.float64, device="cuda"), arith="df64")
+    with pytest.raises(MFError):
+        DofMap(Mesh.octree(ctx, 2, 0, np.array([[0, i, j, k] for k in range(2) for j in range(2) for i in range(2)],
+                                                np.int32)), 3, 0)
