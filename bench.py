@@ -561,6 +561,15 @@ def helmholtz_qk(ctx, flush):
             r["f64" if dt == torch.float64 else "f32"] = {"ms": ms, "gdofs": m.n_dofs / ms / 1e6,
                                                           "tflops": fl / ms / 1e9, "variant": op.variant}
         r["f64"]["frac_of_fp64_peak"] = r["f64"]["tflops"] / FP64_PEAK_TFLOPS
+        if k == 3:
+            # the tensor-core kernel: 2 dense products of 2 x 64 x 256 flops per cell, three split terms
+            u = torch.tensor(syn.uniform_pm1(1, m.n_dofs), device="cuda").float()
+            v = torch.empty_like(u)
+            op.apply(u, v, arith="tc")
+            ms = _event_ms(lambda: op.apply(u, v, arith="tc"), 10, flush)
+            dense = 3 * 2 * 2 * 64 * 256 * m.n_cells
+            r["tc_bf16x3"] = {"ms": ms, "gdofs": m.n_dofs / ms / 1e6, "tensor_tflops": dense / ms / 1e9,
+                              "sum_factorised_tflops_equiv": fl / ms / 1e9, "variant": op.variant}
         out[f"q{k}"] = r
     return out
 

@@ -193,6 +193,17 @@ mf_status mf_apply(mf_op* op, const void* src, void* dst, int nrhs, int64_t ld, 
 mf_status mf_apply_packed16(mf_op* op, const float* src, float* dst, int nrhs, int64_t ld, int format);
 /* dst = A^T src (Helmholtz, heat with convection, reinit).  Asynchronous. */
 mf_status mf_apply_transpose(mf_op* op, const void* src, void* dst, int nrhs, int64_t ld, int dtype);
+
+/* Q3 Helmholtz operators (degree-3 uniform maps) only: dst = A src for fp32 vectors on the fifth-
+ * generation tensor cores.  The cell operator is applied in its dense form: U (128 cells x 64 nodal
+ * values) times the 64 x 256 matrix of the shape functions and their reference derivatives at the
+ * 64 Gauss points, the Gauss-point weights and a(phi) applied per row, then the transposed matrix
+ * (tcgen05.mma kind::f16 with fp32 accumulation in tensor memory, operands split into bf16 hi + lo
+ * parts and three products per contraction: fp32-class accuracy, about 29 times the flops of the
+ * sum-factorised kernel).  nrhs vectors ld apart.  MF_EUNSUPPORTED for other operators;
+ * MF_ETIMEOUT if an earlier tensor-core apply stopped at its one-second wait limit (the kernel
+ * then frees its tensor memory and returns; the device stays usable).  Asynchronous. */
+mf_status mf_apply_tc(mf_op* op, const float* src, float* dst, int nrhs, int64_t ld);
 /* The coupling blocks of the Oseen operator on their own: the pressure-gradient term of the
  * momentum balance and the continuity constraint (Section 2, eq. momentum_balance with
  * div u = 0), in the weak form and quadrature of Appendix B, (B u, q) = -int q div u:

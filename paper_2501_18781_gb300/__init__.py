@@ -200,11 +200,17 @@ class Operator:
 
     def apply(self, src, dst=None, nrhs=1, transpose=False, arith=None):
         """dst = A src; fp64 tensors may ask for arith="df64" (double-float cell arithmetic), fp32
-        tensors for arith="f16" or "bf16" (packed 16-bit arithmetic, pairs of right-hand sides)."""
+        tensors for arith="f16" or "bf16" (packed 16-bit arithmetic, pairs of right-hand sides) or,
+        on Q3 Helmholtz operators, arith="tc" (the tensor-core kernel)."""
         import torch
         if dst is None:
             dst = torch.empty_like(src)
         code = _dtype_code(src)
+        if arith == "tc":
+            if code != MF_F32 or transpose:
+                raise TypeError("tensor-core applies take fp32 tensors, forward (the operator is symmetric)")
+            check(_lib.load().mf_apply_tc(self.h, _ptr(src), _ptr(dst), nrhs, src.numel() // nrhs))
+            return dst
         if arith in ("f16", "bf16"):
             if code != MF_F32 or transpose:
                 raise TypeError("16-bit arithmetic applies to fp32 tensors, forward only")

@@ -105,6 +105,7 @@ SIGNATURES = {
     "mf_apply": (C.c_int, [P, P, P, C.c_int, I64, C.c_int]),
     "mf_apply_transpose": (C.c_int, [P, P, P, C.c_int, I64, C.c_int]),
     "mf_apply_packed16": (C.c_int, [P, P, P, C.c_int, I64, C.c_int]),
+    "mf_apply_tc": (C.c_int, [P, P, P, C.c_int, I64]),
     "mf_oseen_coupling": (C.c_int, [P, C.c_int, P, P, C.c_int]),
     "mf_interface_sources": (C.c_int, [P, C.POINTER(Evaporation), P, P, P, P]),
     "mf_diagonal": (C.c_int, [P, P, C.c_int]),

@@ -20,7 +20,7 @@ COMMON = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler",
           "-I", CSRC, "-I", INCLUDE]
 SOURCES = ["mesh.cpp", "cellops_host.cpp", "api.cpp", "solver.cpp",
            "apply.cu", "apply_f64.cu", "apply_f32.cu", "apply_df64.cu", "aux.cu", "vec.cu",
-           "solver_kernels.cu", "sources.cu", "apply_h16.cu", "step.cu", "step.cpp", "apply_qk.cu"]
+           "solver_kernels.cu", "sources.cu", "apply_h16.cu", "step.cu", "step.cpp", "apply_qk.cu", "apply_qk_tc.cu"]
 
 
 def _digest():

@@ -774,6 +774,23 @@ mf_status mf_apply_packed16(mf_op* op, const float* src, float* dst, int nrhs, i
   MF_GUARD_END
 }
 
+mf_status mf_apply_tc(mf_op* op, const float* src, float* dst, int nrhs, int64_t ld) {
+  MF_GUARD_BEGIN
+  if (!op || !src || !dst) return fail(MF_EINVAL, "NULL argument");
+  if (nrhs < 1 || ld < op->n) return fail(MF_EINVAL, "nrhs must be >= 1 and ld >= n");
+  if (qk_degree(op) != 3) return fail(MF_EUNSUPPORTED, "tensor-core applies: Q3 Helmholtz operators");
+  MF_TRY(check_fields(op));
+  MF_TRY(ensure_tables(op));
+  for (int r = 0; r < nrhs; ++r) {
+    MF_CUDA_TRY(cudaMemsetAsync(dst + r * ld, 0, sizeof(float) * op->n, op->ctx->stream));
+    MF_TRY(launch_helmholtz_q3_tc(op->ctx, op->map[0], src + r * ld, dst + r * ld, op->qcoef32.as<float>(),
+                                  op->p.mass_coef, nullptr));
+  }
+  op->variant = "helmholtz_q3/uniform/f32/tcgen05-bf16x3/dense";
+  return MF_OK;
+  MF_GUARD_END
+}
+
 mf_status mf_apply_transpose(mf_op* op, const void* src, void* dst, int nrhs, int64_t ld, int dtype) {
   MF_GUARD_BEGIN
   if (!op || !src || !dst) return fail(MF_EINVAL, "NULL argument");

@@ -343,6 +343,21 @@ __global__ void k_qk_diag(QkGeom g, const double* coef, double mass, double* dia
   atomicAdd(diag + (K * cx + la) + g.sx * (K * cy + lb) + g.sy * (K * cz + lc), acc);
 }
 
+}  // namespace
+
+// host copies of the degree-k 1D tables (S, Sp: (k+1) x (k+1), W: k+1)
+void qk_host_tables(int k, double* S, double* Sp, double* W) {
+  const Tables1D t = make_qk_tables(k);
+  const int n = (k + 1) * (k + 1);
+  for (int i = 0; i < n; ++i) {
+    S[i] = t.S[i];
+    Sp[i] = t.Sp[i];
+  }
+  for (int i = 0; i <= k; ++i) W[i] = t.W[i];
+}
+
+namespace {
+
 QkGeom qk_geom(const mf_dofmap* m) {
   QkGeom g{};
   g.nx = m->mesh->n[0];

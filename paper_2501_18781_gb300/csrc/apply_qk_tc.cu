@@ -1,0 +1,332 @@
+// Q3 Helmholtz apply on the fifth-generation tensor cores (tcgen05 with the accumulators in tensor
+// memory), for fp32 vectors.  The cell operator of the sum-factorised kernel, written densely: with
+// G the 256 x 64 matrix of the 64 Q3 shape functions and their three reference derivatives at the
+// 64 Gauss points,
+//   D1 = U G^T        (128 cells x 256: values and reference gradients at the Gauss points)
+//   P  = pointwise(D1) (w c h^3 on the values, w a_q h on the gradients)
+//   V  = P G          (128 cells x 64: the cell contributions at the nodes)
+// are two dense products per tile of 128 cells.  To keep fp32-class accuracy on the bf16 tensor
+// cores every operand x is split into x_hi = bf16(x) and x_lo = bf16(x - x_hi) and each product is
+// x_hi y_hi + x_hi y_lo + x_lo y_hi with fp32 accumulation.  One CTA per SM (192 KB of operand
+// images in shared memory, 320 of the 512 tensor-memory columns), persistent over the tiles; one
+// thread per cell gathers, applies the coefficients and scatters; thread 0 issues the MMAs.
+#include <cuda_bf16.h>
+
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "ops.h"
+
+namespace mf {
+
+void qk_host_tables(int k, double* S, double* Sp, double* W);
+
+namespace {
+
+constexpr int kM = 128;   // cells per tile (rows of the MMA)
+constexpr int kNb = 64;   // Q3 nodes per cell
+constexpr int kNq = 256;  // 64 values + 3 x 64 reference gradients
+// shared memory image (bytes); every operand in the K-major layout without swizzle
+constexpr uint32_t kB1H = 0, kB1L = 32768, kB2H = 65536, kB2L = 98304;  // G as B of product 1 and 2
+constexpr uint32_t kA1H = 131072, kA1L = 147456;                          // 128 x 64 nodal values
+constexpr uint32_t kA2H = 163840, kA2L = 180224;                          // 128 x 64 chunk of P
+constexpr uint32_t kBar = 196608, kSlot = 196624, kSmem = 196640;
+constexpr uint32_t kImage = 131072;  // the two G images, copied from global memory once per CTA
+constexpr uint32_t kTmemCols = 512;
+
+// byte offset of element (r, c) of a K-major tile with K columns: 8 x 16-byte core matrices,
+// adjacent along K (leading offset 128 B), row groups of 8 after all K columns (stride K/8 * 128 B)
+__host__ __device__ constexpr uint32_t kmajor(int r, int c, int K) {
+  return uint32_t((r & 7) * 16 + (r >> 3) * (K / 8) * 128 + (c & 7) * 2 + (c >> 3) * 128);
+}
+
+// shared memory matrix descriptor (no swizzle): start, leading offset 128 B, stride sbo
+__device__ __forceinline__ uint64_t sdesc(uint32_t addr, uint32_t sbo) {
+  return uint64_t((addr >> 4) & 0x3FFF) | (uint64_t(128 >> 4) << 16) | (uint64_t((sbo >> 4) & 0x3FFF) << 32) |
+         (uint64_t(1) << 46);
+}
+
+// instruction descriptor of kind::f16: bf16 A and B (K-major), fp32 D, M x N
+__host__ __device__ constexpr uint32_t idesc(int M, int N) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | (uint32_t(N >> 3) << 17) | (uint32_t(M >> 4) << 24);
+}
+
+__constant__ float cTcW[64];  // Gauss weights w_q of the 64 points (x fastest)
+
+struct TcArgs {
+  const float* src;
+  float* dst;
+  const float* coef;  // a per Gauss point, [cell][64]
+  const uint4* image; // the G images (kImage bytes)
+  int* err;           // host-mapped error flag
+  int nx, ny;
+  int64_t sx, sy, ncells;
+  float mass_h3, h;
+};
+
+__device__ __forceinline__ void mma_bf16(uint32_t d, uint64_t a, uint64_t b, uint32_t id, uint32_t acc) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d),
+      "l"(a), "l"(b), "r"(id), "r"(acc));
+}
+
+__device__ __forceinline__ void commit(uint32_t bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
+}
+
+// wait for the phase of an mbarrier, at most one second (global timer); false on timeout
+__device__ __forceinline__ bool wait_phase(uint32_t bar, uint32_t phase) {
+  uint64_t t0, t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t0));
+  while (true) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.b32 %0, 1, 0, p;\n\t}\n"
+        : "=r"(ok)
+        : "r"(bar), "r"(phase)
+        : "memory");
+    if (ok) return true;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    if (t - t0 > 1000000000ull) return false;
+  }
+}
+
+__device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+// 16 consecutive fp32 columns of this thread's tensor-memory lane
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+      "%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+__device__ __forceinline__ void put_split(unsigned char* sm, uint32_t hi, uint32_t lo, uint32_t off, float x) {
+  const __nv_bfloat16 h = __float2bfloat16_rn(x);
+  const __nv_bfloat16 l = __float2bfloat16_rn(x - __bfloat162float(h));
+  *reinterpret_cast<__nv_bfloat16*>(sm + hi + off) = h;
+  *reinterpret_cast<__nv_bfloat16*>(sm + lo + off) = l;
+}
+
+__global__ void __launch_bounds__(128, 1) k_helmholtz_q3_tc(TcArgs A) {
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  unsigned char* sm = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  const uint32_t sb = static_cast<uint32_t>(__cvta_generic_to_shared(sm));
+  const int tid = threadIdx.x, warp = tid >> 5;
+  __shared__ int s_abort;
+  // the G images (once per CTA), the barriers, tensor memory
+  for (uint32_t i = tid; i < kImage / 16; i += blockDim.x) reinterpret_cast<uint4*>(sm)[i] = A.image[i];
+  if (tid == 0) {
+    s_abort = 0;
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(sb + kBar));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(sb + kBar + 8));
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(sb + kSlot),
+                 "r"(kTmemCols));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  fence_async_smem();
+  fence_before();
+  __syncthreads();
+  fence_after();
+  const uint32_t tmem = *reinterpret_cast<volatile uint32_t*>(sm + kSlot);
+  const uint32_t d1 = tmem, d2 = tmem + 256;
+  const uint32_t lane_base = uint32_t(warp * 32) << 16;
+  const uint32_t bar1 = sb + kBar, bar2 = sb + kBar + 8;
+  uint32_t ph1 = 0, ph2 = 0;
+  const uint32_t id1 = idesc(kM, kNq), id2 = idesc(kM, kNb);
+  const int64_t ntiles = (A.ncells + kM - 1) / kM;
+  int pending = 0;  // 1: product 1 in flight, 2: product 2 in flight
+  for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const int64_t cell = tile * kM + tid;
+    const bool on = cell < A.ncells;
+    int64_t base = 0;
+    if (on) {
+      const int64_t cx = cell % A.nx, cy = (cell / A.nx) % A.ny, cz = cell / (int64_t(A.nx) * A.ny);
+      base = 3 * cx + A.sx * (3 * cy) + A.sy * (3 * cz);
+    }
+    // 1. nodal values of this thread's cell -> row tid of U (hi, lo)
+#pragma unroll 4
+    for (int l = 0; l < kNb; ++l) {
+      const float x = on ? __ldg(A.src + base + (l & 3) + A.sx * ((l >> 2) & 3) + A.sy * (l >> 4)) : 0.0f;
+      put_split(sm, kA1H, kA1L, kmajor(tid, l, kNb), x);
+    }
+    fence_async_smem();
+    fence_before();
+    __syncthreads();
+    // 2. D1 = U G^T: three split products, four K-steps of 16 each
+    if (tid == 0) {
+      fence_after();
+      for (int t = 0; t < 3; ++t) {
+        const uint32_t a = sb + (t == 2 ? kA1L : kA1H), b = sb + (t == 1 ? kB1L : kB1H);
+        for (int s = 0; s < 4; ++s) mma_bf16(d1, sdesc(a + s * 256, 1024), sdesc(b + s * 256, 1024), id1, (t | s) != 0);
+      }
+      commit(bar1);
+    }
+    pending = 1;
+    if (!wait_phase(bar1, ph1)) s_abort = 1;
+    ph1 ^= 1;
+    pending = 0;
+    __syncthreads();
+    if (s_abort) break;
+    fence_after();
+    // 3. per 64-column chunk: coefficients, then V += P_chunk G_chunk
+    const float* coef = A.coef + (on ? cell : 0) * 64;
+    for (int j = 0; j < 4; ++j) {
+      if (j > 0) {
+        if (!wait_phase(bar2, ph2)) s_abort = 1;
+        ph2 ^= 1;
+        pending = 0;
+        __syncthreads();
+        if (s_abort) break;
+        fence_after();
+      }
+      for (int c16 = 0; c16 < 4; ++c16) {
+        float v[16];
+        tmem_ld16(d1 + lane_base + j * 64 + c16 * 16, v);
+#pragma unroll
+        for (int i = 0; i < 16; ++i) {
+          const int q = c16 * 16 + i;
+          const float s = j == 0 ? cTcW[q] * A.mass_h3 : cTcW[q] * (on ? __ldg(coef + q) : 0.0f) * A.h;
+          put_split(sm, kA2H, kA2L, kmajor(tid, q, 64), v[i] * s);
+        }
+      }
+      fence_async_smem();
+      fence_before();
+      __syncthreads();
+      if (tid == 0) {
+        fence_after();
+        for (int t = 0; t < 3; ++t) {
+          const uint32_t a = sb + (t == 2 ? kA2L : kA2H), b = sb + (t == 1 ? kB2L : kB2H);
+          for (int s = 0; s < 4; ++s)
+            mma_bf16(d2, sdesc(a + s * 256, 1024), sdesc(b + j * 1024 + s * 256, 4096), id2, (j | t | s) != 0);
+        }
+        commit(bar2);
+      }
+      pending = 2;
+    }
+    if (s_abort) break;
+    if (!wait_phase(bar2, ph2)) s_abort = 1;
+    ph2 ^= 1;
+    pending = 0;
+    __syncthreads();
+    if (s_abort) break;
+    fence_after();
+    // 4. scatter the 64 nodal contributions of this cell
+    for (int c16 = 0; c16 < 4; ++c16) {
+      float v[16];
+      tmem_ld16(d2 + lane_base + c16 * 16, v);
+      if (on)
+#pragma unroll
+        for (int i = 0; i < 16; ++i) {
+          const int l = c16 * 16 + i;
+          atomicAdd(A.dst + base + (l & 3) + A.sx * ((l >> 2) & 3) + A.sy * (l >> 4), v[i]);
+        }
+    }
+    fence_before();
+    __syncthreads();
+  }
+  if (s_abort) {
+    // report, give the products still in flight their time, then free the tensor memory
+    if (tid == 0) atomicExch(A.err, 1);
+    if (pending == 1) wait_phase(bar1, ph1);
+    if (pending == 2) wait_phase(bar2, ph2);
+  }
+  fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols));
+  }
+}
+
+// the two G images: B of product 1 (256 rows x K = 64) and of product 2 (64 rows x K = 256), hi, lo
+std::vector<uint16_t> make_image() {
+  double S[16], Sp[16], W[4];
+  qk_host_tables(3, S, Sp, W);
+  std::vector<uint16_t> img(kImage / 2, 0);
+  auto put = [&](uint32_t region, uint32_t off, float x) {
+    const __nv_bfloat16 h = __float2bfloat16_rn(x);
+    const __nv_bfloat16 l = __float2bfloat16_rn(x - __bfloat162float(h));
+    uint16_t hb, lb;
+    std::memcpy(&hb, &h, 2);
+    std::memcpy(&lb, &l, 2);
+    img[(region + off) / 2] = hb;
+    img[(region + 32768 + off) / 2] = lb;
+  };
+  for (int col = 0; col < kNq; ++col) {
+    const int part = col / 64, q = col % 64, qa = q % 4, qb = (q / 4) % 4, qc = q / 16;
+    for (int l = 0; l < kNb; ++l) {
+      const int a = l % 4, b = (l / 4) % 4, c = l / 16;
+      const double fa = part == 1 ? Sp[4 * qa + a] : S[4 * qa + a];
+      const double fb = part == 2 ? Sp[4 * qb + b] : S[4 * qb + b];
+      const double fc = part == 3 ? Sp[4 * qc + c] : S[4 * qc + c];
+      const float g = float(fa * fb * fc);
+      put(kB1H, kmajor(col, l, kNb), g);   // product 1: B[n = col][k = l]
+      put(kB2H, kmajor(l, col, kNq), g);   // product 2: B[n = l][k = col]
+    }
+  }
+  return img;
+}
+
+}  // namespace
+
+mf_status launch_helmholtz_q3_tc(mf_ctx* ctx, const mf_dofmap* m, const float* src, float* dst, const float* coef,
+                                 double mass, int* host_err_out) {
+  static DevBuf image;
+  static int* h_err = nullptr;
+  static int* d_err = nullptr;
+  static bool ready = false;
+  if (!ready) {
+    const std::vector<uint16_t> img = make_image();
+    MF_TRY(image.alloc(kImage));
+    MF_CUDA_TRY(cudaMemcpy(image.p, img.data(), kImage, cudaMemcpyHostToDevice));
+    double S[16], Sp[16], W[4];
+    qk_host_tables(3, S, Sp, W);
+    float w[64];
+    for (int q = 0; q < 64; ++q) w[q] = float(W[q % 4] * W[(q / 4) % 4] * W[q / 16]);
+    MF_CUDA_TRY(cudaMemcpyToSymbol(cTcW, w, sizeof(w)));
+    MF_CUDA_TRY(cudaHostAlloc(reinterpret_cast<void**>(&h_err), sizeof(int), cudaHostAllocMapped));
+    *h_err = 0;
+    MF_CUDA_TRY(cudaHostGetDevicePointer(reinterpret_cast<void**>(&d_err), h_err, 0));
+    MF_CUDA_TRY(cudaFuncSetAttribute(k_helmholtz_q3_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, int(kSmem + 1024)));
+    ready = true;
+  }
+  if (*reinterpret_cast<volatile int*>(h_err)) return fail(MF_ETIMEOUT, "a tensor-core apply timed out waiting on its MMAs");
+  TcArgs a{};
+  a.src = src;
+  a.dst = dst;
+  a.coef = coef;
+  a.image = image.as<const uint4>();
+  a.err = d_err;
+  a.nx = m->mesh->n[0];
+  a.ny = m->mesh->n[1];
+  a.sx = m->R[0] + 1;
+  a.sy = a.sx * (m->R[1] + 1);
+  a.ncells = m->n_cells;
+  const double h = m->mesh->h0;
+  a.mass_h3 = float(mass * h * h * h);
+  a.h = float(h);
+  const int64_t ntiles = (m->n_cells + kM - 1) / kM;
+  const int grid = int(std::min<int64_t>(ntiles, ctx->sm_count > 0 ? ctx->sm_count : 152));
+  k_helmholtz_q3_tc<<<grid, 128, kSmem + 1024, ctx->stream>>>(a);
+  ctx->launches++;
+  MF_CUDA_TRY(cudaGetLastError());
+  if (host_err_out) *host_err_out = *reinterpret_cast<volatile int*>(h_err);
+  return MF_OK;
+}
+
+}  // namespace mf

@@ -104,6 +104,10 @@ mf_status launch_qk_coef(mf_ctx* ctx, const mf_dofmap* m, const double* phi, dou
 template <typename T>
 mf_status launch_helmholtz_qk(mf_ctx* ctx, const mf_dofmap* m, const T* src, T* dst, const T* coef, double mass);
 mf_status launch_qk_diag(mf_ctx* ctx, const mf_dofmap* m, const double* coef, double mass, double* diag);
+// Q3 Helmholtz on the tensor cores (fp32 vectors, dst accumulated); host_err_out: the error flag
+// left by earlier launches (may be NULL)
+mf_status launch_helmholtz_q3_tc(mf_ctx* ctx, const mf_dofmap* m, const float* src, float* dst, const float* coef,
+                                 double mass, int* host_err_out);
 // laser top-face load and its parameter derivatives (uniform maps)
 mf_status launch_laser(mf_ctx* ctx, const mf_dofmap* m, const double lz[5], double* f, double* dF);
 // dJ/dk_q = -w_q h grad(lambda) . grad(theta), [cell][27]

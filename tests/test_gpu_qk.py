@@ -95,3 +95,31 @@ def test_qk_rejections(ctx):
     with pytest.raises(MFError):
         DofMap(Mesh.octree(ctx, 2, 0, np.array([[0, i, j, k] for k in range(2) for j in range(2) for i in range(2)],
                                                 np.int32)), 3, 0)
+
+
+@pytest.mark.parametrize("n", [1, 3, 6])
+def test_q3_tensor_core_apply_matches_oracle(ctx, n):
+    """tcgen05 dense form with bf16 hi/lo operands (three products, fp32 accumulation): tiles of 128
+    cells, here 1 cell, one partial tile (27 cells) and two tiles with a ragged tail (216 cells)."""
+    dm, A, op = _problem(ctx, 3, n)
+    u = syn.uniform_pm1(11 + n, dm.n_dofs).astype(np.float32).astype(np.float64)
+    ref, bound = A @ u, abs(A) @ np.abs(u)
+    v = op.apply(torch.tensor(u, device="cuda").float(), arith="tc").cpu().double().numpy()
+    ok, worst = componentwise_ok(v, ref, bound, 5e-5)
+    assert ok, worst
+    assert op.variant == "helmholtz_q3/uniform/f32/tcgen05-bf16x3/dense"
+    # a strided batch of two
+    ld = dm.n_dofs + 5
+    U = np.zeros((2, ld), np.float32)
+    U[0, :dm.n_dofs], U[1, :dm.n_dofs] = u, -0.5 * u
+    out = op.apply(torch.tensor(U.ravel(), device="cuda"), nrhs=2, arith="tc").cpu().double().numpy().reshape(2, ld)
+    for r, s in ((0, 1.0), (1, -0.5)):
+        ok, worst = componentwise_ok(out[r, :dm.n_dofs], s * ref, abs(s) * bound, 5e-5)
+        assert ok, (r, worst)
+
+
+def test_tensor_core_apply_rejects_q4(ctx):
+    from paper_2501_18781_gb300._lib import MFError
+    _, _, op = _problem(ctx, 4, 2)
+    with pytest.raises(MFError):
+        op.apply(torch.zeros(op.n, dtype=torch.float32, device="cuda"), arith="tc")
