@@ -4,6 +4,7 @@
     python -m paper_2501_18781_gb300.apply_probe oseen [n] [f32|f64|df64]
     python -m paper_2501_18781_gb300.apply_probe reinit [base] [levels] [f32|f64|df64] [nrhs]
     python -m paper_2501_18781_gb300.apply_probe oseen_solve [n] [maxit]
+    python -m paper_2501_18781_gb300.apply_probe helmholtz_qk [k] [n] [f32|f64|tc]
 
 Inputs come from the seeded generators in ``synthetic``; every apply runs in libmfgb.
 """
@@ -76,6 +77,23 @@ def main(argv):
                 _, info = op.solve(bt, solver="gmres", precond="block_triangular", maxit=maxit, tol=1e-10)
             torch.cuda.synchronize()
             print(op.variant, n, info)
+    elif kind == "helmholtz_qk":
+        k = int(argv[1]) if len(argv) > 1 else 3
+        n = int(argv[2]) if len(argv) > 2 else 64
+        prec = argv[3] if len(argv) > 3 else "f32"
+        m = DofMap(Mesh.uniform(ctx, n), k, 0)
+        eps = 1.0 / (2 * n)
+        phi = syn.initial_level_set(syn.sphere_distance(*m.coords().T), eps)
+        op = Operator(ctx, "helmholtz", [m], mass_coef=1.0, a_liquid=1000.0, a_gas=1.0, eps=eps)
+        op.set_field("phi", torch.tensor(phi, device="cuda"))
+        u = torch.tensor(syn.uniform_pm1(1, m.n_dofs), device="cuda")
+        if prec != "f64":
+            u = u.float()
+        v = torch.empty_like(u)
+        for _ in range(4):
+            op.apply(u, v, arith="tc" if prec == "tc" else None)
+        torch.cuda.synchronize()
+        print(op.variant, m.n_dofs)
     elif kind == "reinit":
         base = int(argv[1]) if len(argv) > 1 else 16
         levels = int(argv[2]) if len(argv) > 2 else 3

@@ -7,9 +7,9 @@
 //   V  = P G          (128 cells x 64: the cell contributions at the nodes)
 // are two dense products per tile of 128 cells.  To keep fp32-class accuracy on the bf16 tensor
 // cores every operand x is split into x_hi = bf16(x) and x_lo = bf16(x - x_hi) and each product is
-// x_hi y_hi + x_hi y_lo + x_lo y_hi with fp32 accumulation.  One CTA per SM (192 KB of operand
-// images in shared memory, 320 of the 512 tensor-memory columns), persistent over the tiles; one
-// thread per cell gathers, applies the coefficients and scatters; thread 0 issues the MMAs.
+// x_hi y_hi + x_hi y_lo + x_lo y_hi with fp32 accumulation.  One CTA per SM (224 KB of operand
+// images and coefficients in shared memory, 320 of the 512 tensor-memory columns), persistent over the tiles; two
+// threads per cell gather, apply the coefficients and scatter; thread 0 issues the MMAs.
 #include <cuda_bf16.h>
 
 #include <cmath>
@@ -31,7 +31,8 @@ constexpr int kNq = 256;  // 64 values + 3 x 64 reference gradients
 constexpr uint32_t kB1H = 0, kB1L = 32768, kB2H = 65536, kB2L = 98304;  // G as B of product 1 and 2
 constexpr uint32_t kA1H = 131072, kA1L = 147456;                          // 128 x 64 nodal values
 constexpr uint32_t kA2H = 163840, kA2L = 180224;                          // 128 x 64 chunk of P
-constexpr uint32_t kBar = 196608, kSlot = 196624, kSmem = 196640;
+constexpr uint32_t kStage = 196608;                                       // 128 x 64 fp32 coefficients
+constexpr uint32_t kBar = 229376, kSlot = 229392, kSmem = 229408;
 constexpr uint32_t kImage = 131072;  // the two G images, copied from global memory once per CTA
 constexpr uint32_t kTmemCols = 512;
 
@@ -112,18 +113,48 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
   for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
-__device__ __forceinline__ void put_split(unsigned char* sm, uint32_t hi, uint32_t lo, uint32_t off, float x) {
-  const __nv_bfloat16 h = __float2bfloat16_rn(x);
-  const __nv_bfloat16 l = __float2bfloat16_rn(x - __bfloat162float(h));
-  *reinterpret_cast<__nv_bfloat16*>(sm + hi + off) = h;
-  *reinterpret_cast<__nv_bfloat16*>(sm + lo + off) = l;
+// 8 consecutive K-elements of one row as bf16 hi and lo parts: two 16-byte stores into the core
+// matrices of the hi and lo images
+__device__ __forceinline__ void put_split8(unsigned char* sm, uint32_t hi, uint32_t lo, uint32_t off, const float* x) {
+  uint32_t h[4], l[4];
+#pragma unroll
+  for (int e = 0; e < 4; ++e) {
+    const __nv_bfloat162 a = __floats2bfloat162_rn(x[2 * e], x[2 * e + 1]);
+    const __nv_bfloat162 b = __floats2bfloat162_rn(x[2 * e] - __low2float(a), x[2 * e + 1] - __high2float(a));
+    h[e] = *reinterpret_cast<const uint32_t*>(&a);
+    l[e] = *reinterpret_cast<const uint32_t*>(&b);
+  }
+  *reinterpret_cast<uint4*>(sm + hi + off) = make_uint4(h[0], h[1], h[2], h[3]);
+  *reinterpret_cast<uint4*>(sm + lo + off) = make_uint4(l[0], l[1], l[2], l[3]);
 }
 
-__global__ void __launch_bounds__(128, 1) k_helmholtz_q3_tc(TcArgs A) {
+// nodes 32 half .. 32 half + 31 of a cell (zeros for a cell past the end)
+__device__ __forceinline__ void gather32(const TcArgs& A, bool on, int64_t base, int half, float* x) {
+#pragma unroll
+  for (int e = 0; e < 32; ++e) {
+    const int l = 32 * half + e;
+    x[e] = on ? __ldg(A.src + base + (l & 3) + A.sx * ((l >> 2) & 3) + A.sy * (l >> 4)) : 0.0f;
+  }
+}
+
+__device__ __forceinline__ bool tile_cell(const TcArgs& A, int64_t tile, int row, int64_t& base) {
+  const int64_t cell = tile * kM + row;
+  base = 0;
+  if (cell >= A.ncells) return false;
+  const int64_t cx = cell % A.nx, cy = (cell / A.nx) % A.ny, cz = cell / (int64_t(A.nx) * A.ny);
+  base = 3 * cx + A.sx * (3 * cy) + A.sy * (3 * cz);
+  return true;
+}
+
+// Two threads per cell: thread t works on row t % 128 of the tile and on half t / 128 of its
+// columns (warps w and w + 4 read the same tensor-memory lanes).  Software-pipelined over the
+// CTA's tiles: the next tile's nodal values are loaded while the coefficients of the current one
+// are applied, and its first product runs while the current tile is scattered.
+__global__ void __launch_bounds__(256, 1) k_helmholtz_q3_tc(TcArgs A) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* sm = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   const uint32_t sb = static_cast<uint32_t>(__cvta_generic_to_shared(sm));
-  const int tid = threadIdx.x, warp = tid >> 5;
+  const int tid = threadIdx.x, warp = tid >> 5, row = tid & 127, half = tid >> 7;
   __shared__ int s_abort;
   // the G images (once per CTA), the barriers, tensor memory
   for (uint32_t i = tid; i < kImage / 16; i += blockDim.x) reinterpret_cast<uint4*>(sm)[i] = A.image[i];
@@ -138,71 +169,96 @@ __global__ void __launch_bounds__(128, 1) k_helmholtz_q3_tc(TcArgs A) {
                  "r"(kTmemCols));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
+  const uint32_t tmem_slot = sb + kSlot;
+  const uint32_t lane_base = uint32_t((warp & 3) * 32) << 16;
+  const uint32_t bar1 = sb + kBar, bar2 = sb + kBar + 8;
+  uint32_t ph1 = 0, ph2 = 0;
+  const uint32_t id1 = idesc(kM, kNq), id2 = idesc(kM, kNb);
+  const int64_t ntiles = (A.ncells + kM - 1) / kM;
+  // coefficients of the current tile: row r, column q at r * 64 + (q ^ (r & 31)) (a warp's 32 rows
+  // read one column from 32 banks)
+  float* stage = reinterpret_cast<float*>(sm + kStage);
+  const uint32_t rowoff = uint32_t((row & 7) * 16 + (row >> 3) * 1024);  // row's place in a 64-column tile
+  // products committed to bar1 / bar2 and not yet waited for; a wait clears its flag and advances
+  // its phase only when it succeeds, so a timed-out product is waited for again before the exit
+  int pend1 = 0, pend2 = 0;
+  auto wait1 = [&]() {
+    if (wait_phase(bar1, ph1)) { ph1 ^= 1; pend1 = 0; } else { s_abort = 1; }
+  };
+  auto wait2 = [&]() {
+    if (wait_phase(bar2, ph2)) { ph2 ^= 1; pend2 = 0; } else { s_abort = 1; }
+  };
+  int64_t tile = blockIdx.x;
+  int64_t base = 0;
+  bool on = tile < ntiles ? tile_cell(A, tile, row, base) : false;
+  // prologue: the first tile's nodal values
+  if (tile < ntiles) {
+    float x[32];
+    gather32(A, on, base, half, x);
+#pragma unroll
+    for (int g = 0; g < 4; ++g) put_split8(sm, kA1H, kA1L, rowoff + (4 * half + g) * 128, x + 8 * g);
+  }
   fence_async_smem();
   fence_before();
   __syncthreads();
   fence_after();
   const uint32_t tmem = *reinterpret_cast<volatile uint32_t*>(sm + kSlot);
+  (void)tmem_slot;
   const uint32_t d1 = tmem, d2 = tmem + 256;
-  const uint32_t lane_base = uint32_t(warp * 32) << 16;
-  const uint32_t bar1 = sb + kBar, bar2 = sb + kBar + 8;
-  uint32_t ph1 = 0, ph2 = 0;
-  const uint32_t id1 = idesc(kM, kNq), id2 = idesc(kM, kNb);
-  const int64_t ntiles = (A.ncells + kM - 1) / kM;
-  int pending = 0;  // 1: product 1 in flight, 2: product 2 in flight
-  for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-    const int64_t cell = tile * kM + tid;
-    const bool on = cell < A.ncells;
-    int64_t base = 0;
-    if (on) {
-      const int64_t cx = cell % A.nx, cy = (cell / A.nx) % A.ny, cz = cell / (int64_t(A.nx) * A.ny);
-      base = 3 * cx + A.sx * (3 * cy) + A.sy * (3 * cz);
+  auto issue_product1 = [&]() {
+    for (int t = 0; t < 3; ++t) {
+      const uint32_t a = sb + (t == 2 ? kA1L : kA1H), b = sb + (t == 1 ? kB1L : kB1H);
+      for (int s = 0; s < 4; ++s) mma_bf16(d1, sdesc(a + s * 256, 1024), sdesc(b + s * 256, 1024), id1, (t | s) != 0);
     }
-    // 1. nodal values of this thread's cell -> row tid of U (hi, lo)
-#pragma unroll 4
-    for (int l = 0; l < kNb; ++l) {
-      const float x = on ? __ldg(A.src + base + (l & 3) + A.sx * ((l >> 2) & 3) + A.sy * (l >> 4)) : 0.0f;
-      put_split(sm, kA1H, kA1L, kmajor(tid, l, kNb), x);
-    }
-    fence_async_smem();
-    fence_before();
-    __syncthreads();
-    // 2. D1 = U G^T: three split products, four K-steps of 16 each
-    if (tid == 0) {
-      fence_after();
-      for (int t = 0; t < 3; ++t) {
-        const uint32_t a = sb + (t == 2 ? kA1L : kA1H), b = sb + (t == 1 ? kB1L : kB1H);
-        for (int s = 0; s < 4; ++s) mma_bf16(d1, sdesc(a + s * 256, 1024), sdesc(b + s * 256, 1024), id1, (t | s) != 0);
-      }
-      commit(bar1);
-    }
-    pending = 1;
-    if (!wait_phase(bar1, ph1)) s_abort = 1;
-    ph1 ^= 1;
-    pending = 0;
+    commit(bar1);
+  };
+  if (tile < ntiles && tid == 0) issue_product1();
+  pend1 = tile < ntiles ? 1 : 0;
+  for (; tile < ntiles; tile += gridDim.x) {
+    const int64_t next = tile + gridDim.x;
+    // 1. D1 of this tile is ready
+    wait1();
     __syncthreads();
     if (s_abort) break;
     fence_after();
+    // 2. coefficients of the tile (contiguous [cell][64] in global memory), coalesced; the next
+    //    tile's nodal values into registers
+    {
+      const float4* cg = reinterpret_cast<const float4*>(A.coef + tile * kM * 64);
+      for (int i = tid; i < kM * 16; i += blockDim.x) {
+        const int r = i >> 4, q4 = (i & 15) * 4;
+        const float4 v = (tile * kM + r < A.ncells) ? __ldg(cg + i) : make_float4(0.f, 0.f, 0.f, 0.f);
+        stage[r * 64 + ((q4 + 0) ^ (r & 31))] = v.x;
+        stage[r * 64 + ((q4 + 1) ^ (r & 31))] = v.y;
+        stage[r * 64 + ((q4 + 2) ^ (r & 31))] = v.z;
+        stage[r * 64 + ((q4 + 3) ^ (r & 31))] = v.w;
+      }
+    }
+    int64_t nbase = 0;
+    const bool non = next < ntiles ? tile_cell(A, next, row, nbase) : false;
+    float xn[32];
+    gather32(A, non, nbase, half, xn);
+    __syncthreads();
     // 3. per 64-column chunk: coefficients, then V += P_chunk G_chunk
-    const float* coef = A.coef + (on ? cell : 0) * 64;
     for (int j = 0; j < 4; ++j) {
       if (j > 0) {
-        if (!wait_phase(bar2, ph2)) s_abort = 1;
-        ph2 ^= 1;
-        pending = 0;
+        wait2();
         __syncthreads();
         if (s_abort) break;
         fence_after();
       }
-      for (int c16 = 0; c16 < 4; ++c16) {
+#pragma unroll
+      for (int c16 = 0; c16 < 2; ++c16) {
         float v[16];
-        tmem_ld16(d1 + lane_base + j * 64 + c16 * 16, v);
+        const int q0 = half * 32 + c16 * 16;
+        tmem_ld16(d1 + lane_base + j * 64 + q0, v);
 #pragma unroll
         for (int i = 0; i < 16; ++i) {
-          const int q = c16 * 16 + i;
-          const float s = j == 0 ? cTcW[q] * A.mass_h3 : cTcW[q] * (on ? __ldg(coef + q) : 0.0f) * A.h;
-          put_split(sm, kA2H, kA2L, kmajor(tid, q, 64), v[i] * s);
+          const int q = q0 + i;
+          v[i] *= j == 0 ? cTcW[q] * A.mass_h3 : cTcW[q] * stage[row * 64 + (q ^ (row & 31))] * A.h;
         }
+        put_split8(sm, kA2H, kA2L, rowoff + (q0 >> 3) * 128, v);
+        put_split8(sm, kA2H, kA2L, rowoff + ((q0 >> 3) + 1) * 128, v + 8);
       }
       fence_async_smem();
       fence_before();
@@ -216,34 +272,49 @@ __global__ void __launch_bounds__(128, 1) k_helmholtz_q3_tc(TcArgs A) {
         }
         commit(bar2);
       }
-      pending = 2;
+      pend2 = 1;
     }
     if (s_abort) break;
-    if (!wait_phase(bar2, ph2)) s_abort = 1;
-    ph2 ^= 1;
-    pending = 0;
+    // 4. the next tile's U (its first product reads it while this tile is scattered); D1 of this
+    //    tile has been read in full
+    if (next < ntiles) {
+#pragma unroll
+      for (int g = 0; g < 4; ++g) put_split8(sm, kA1H, kA1L, rowoff + (4 * half + g) * 128, xn + 8 * g);
+    }
+    fence_async_smem();
+    fence_before();
+    __syncthreads();
+    if (next < ntiles && tid == 0) {
+      fence_after();
+      issue_product1();
+    }
+    if (next < ntiles) pend1 = 1;
+    // 5. this tile's V, scattered
+    wait2();
     __syncthreads();
     if (s_abort) break;
     fence_after();
-    // 4. scatter the 64 nodal contributions of this cell
-    for (int c16 = 0; c16 < 4; ++c16) {
+#pragma unroll
+    for (int c16 = 0; c16 < 2; ++c16) {
       float v[16];
-      tmem_ld16(d2 + lane_base + c16 * 16, v);
+      tmem_ld16(d2 + lane_base + half * 32 + c16 * 16, v);
       if (on)
 #pragma unroll
         for (int i = 0; i < 16; ++i) {
-          const int l = c16 * 16 + i;
+          const int l = half * 32 + c16 * 16 + i;
           atomicAdd(A.dst + base + (l & 3) + A.sx * ((l >> 2) & 3) + A.sy * (l >> 4), v[i]);
         }
     }
+    on = non;
+    base = nbase;
     fence_before();
     __syncthreads();
   }
   if (s_abort) {
     // report, give the products still in flight their time, then free the tensor memory
     if (tid == 0) atomicExch(A.err, 1);
-    if (pending == 1) wait_phase(bar1, ph1);
-    if (pending == 2) wait_phase(bar2, ph2);
+    if (pend1) wait_phase(bar1, ph1);
+    if (pend2) wait_phase(bar2, ph2);
   }
   fence_before();
   __syncthreads();
@@ -322,7 +393,7 @@ mf_status launch_helmholtz_q3_tc(mf_ctx* ctx, const mf_dofmap* m, const float* s
   a.h = float(h);
   const int64_t ntiles = (m->n_cells + kM - 1) / kM;
   const int grid = int(std::min<int64_t>(ntiles, ctx->sm_count > 0 ? ctx->sm_count : 152));
-  k_helmholtz_q3_tc<<<grid, 128, kSmem + 1024, ctx->stream>>>(a);
+  k_helmholtz_q3_tc<<<grid, 256, kSmem + 1024, ctx->stream>>>(a);
   ctx->launches++;
   MF_CUDA_TRY(cudaGetLastError());
   if (host_err_out) *host_err_out = *reinterpret_cast<volatile int*>(h_err);
