@@ -394,6 +394,7 @@ mf_status mf_operator_set_field(mf_op* op, int field, const void* ptr, int dtype
       return fail(MF_EINVAL, "unknown field");
   }
   op->tables_ready = false;
+  op->tc_ready = false;
   op->diag_ready = false;
   op->h16_cnorm = 0.0f;
   // float copy of the in-kernel nodal field
@@ -781,9 +782,15 @@ mf_status mf_apply_tc(mf_op* op, const float* src, float* dst, int nrhs, int64_t
   if (qk_degree(op) != 3) return fail(MF_EUNSUPPORTED, "tensor-core applies: Q3 Helmholtz operators");
   MF_TRY(check_fields(op));
   MF_TRY(ensure_tables(op));
+  if (!op->tc_ready) {
+    const int64_t ntiles = (op->ncells + 127) / 128;
+    MF_TRY(op->qcoef_tc.alloc(sizeof(float) * ntiles * 128 * 64));
+    MF_TRY(launch_tc_coef_layout(op->ctx, op->map[0], op->qcoef32.as<float>(), op->qcoef_tc.as<float>()));
+    op->tc_ready = true;
+  }
   for (int r = 0; r < nrhs; ++r) {
     MF_CUDA_TRY(cudaMemsetAsync(dst + r * ld, 0, sizeof(float) * op->n, op->ctx->stream));
-    MF_TRY(launch_helmholtz_q3_tc(op->ctx, op->map[0], src + r * ld, dst + r * ld, op->qcoef32.as<float>(),
+    MF_TRY(launch_helmholtz_q3_tc(op->ctx, op->map[0], src + r * ld, dst + r * ld, op->qcoef_tc.as<float>(),
                                   op->p.mass_coef, nullptr));
   }
   op->variant = "helmholtz_q3/uniform/f32/tcgen05-bf16x3/dense";

@@ -27,14 +27,15 @@ namespace {
 constexpr int kM = 128;   // cells per tile (rows of the MMA)
 constexpr int kNb = 64;   // Q3 nodes per cell
 constexpr int kNq = 256;  // 64 values + 3 x 64 reference gradients
-// shared memory image (bytes); every operand in the K-major layout without swizzle
-constexpr uint32_t kB1H = 0, kB1L = 32768, kB2H = 65536, kB2L = 98304;  // G as B of product 1 and 2
-constexpr uint32_t kA1H = 131072, kA1L = 147456;                          // 128 x 64 nodal values
-constexpr uint32_t kA2H = 163840, kA2L = 180224;                          // 128 x 64 chunk of P
-constexpr uint32_t kStage = 196608;                                       // 128 x 64 fp32 coefficients
-constexpr uint32_t kBar = 229376, kSlot = 229392, kSmem = 229408;
-constexpr uint32_t kImage = 131072;  // the two G images, copied from global memory once per CTA
+// shared memory image (bytes); the operands in the no-swizzle layouts
+constexpr uint32_t kB1H = 0, kB1L = 32768;          // G: B of product 1 (K-major) and of product 2 (MN-major)
+constexpr uint32_t kA1H = 65536, kA1L = 81920;      // 128 x 64 nodal values
+constexpr uint32_t kA2H = 98304, kA2L = 114688;     // 128 x 64 chunk of P
+constexpr uint32_t kStage = 131072;                 // two 128 x 64 fp32 coefficient tiles (TMA)
+constexpr uint32_t kBar = 196608, kSlot = 196640, kSmem = 196656;
+constexpr uint32_t kImage = 65536;  // the G image, copied from global memory once per CTA
 constexpr uint32_t kTmemCols = 512;
+constexpr uint32_t kStageBytes = 32768;
 
 // byte offset of element (r, c) of a K-major tile with K columns: 8 x 16-byte core matrices,
 // adjacent along K (leading offset 128 B), row groups of 8 after all K columns (stride K/8 * 128 B)
@@ -48,9 +49,17 @@ __device__ __forceinline__ uint64_t sdesc(uint32_t addr, uint32_t sbo) {
          (uint64_t(1) << 46);
 }
 
-// instruction descriptor of kind::f16: bf16 A and B (K-major), fp32 D, M x N
-__host__ __device__ constexpr uint32_t idesc(int M, int N) {
-  return (1u << 4) | (1u << 7) | (1u << 10) | (uint32_t(N >> 3) << 17) | (uint32_t(M >> 4) << 24);
+// shared memory matrix descriptor (no swizzle) with explicit leading and stride offsets
+__device__ __forceinline__ uint64_t sdesc2(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+  return uint64_t((addr >> 4) & 0x3FFF) | (uint64_t((lbo >> 4) & 0x3FFF) << 16) | (uint64_t((sbo >> 4) & 0x3FFF) << 32) |
+         (uint64_t(1) << 46);
+}
+
+// instruction descriptor of kind::f16: bf16 A (K-major) and B (K-major, or MN-major with b_mn),
+// fp32 D, M x N
+__host__ __device__ constexpr uint32_t idesc(int M, int N, bool b_mn = false) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | (b_mn ? (1u << 16) : 0u) | (uint32_t(N >> 3) << 17) |
+         (uint32_t(M >> 4) << 24);
 }
 
 __constant__ float cTcW[64];  // Gauss weights w_q of the 64 points (x fastest)
@@ -58,7 +67,7 @@ __constant__ float cTcW[64];  // Gauss weights w_q of the 64 points (x fastest)
 struct TcArgs {
   const float* src;
   float* dst;
-  const float* coef;  // a per Gauss point, [cell][64]
+  const float* coef;  // a per Gauss point, per tile of 128 cells: [tile][q][row]
   const uint4* image; // the G images (kImage bytes)
   int* err;           // host-mapped error flag
   int nx, ny;
@@ -148,20 +157,21 @@ __device__ __forceinline__ bool tile_cell(const TcArgs& A, int64_t tile, int row
 
 // Two threads per cell: thread t works on row t % 128 of the tile and on half t / 128 of its
 // columns (warps w and w + 4 read the same tensor-memory lanes).  Software-pipelined over the
-// CTA's tiles: the next tile's nodal values are loaded while the coefficients of the current one
-// are applied, and its first product runs while the current tile is scattered.
+// CTA's tiles: the next tile's coefficients arrive by a TMA bulk copy and its nodal values are
+// loaded while the coefficients of the current one are applied, and its first product runs while
+// the current tile is scattered.  Product 2 reads the same G image as product 1, as an MN-major B.
 __global__ void __launch_bounds__(256, 1) k_helmholtz_q3_tc(TcArgs A) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* sm = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   const uint32_t sb = static_cast<uint32_t>(__cvta_generic_to_shared(sm));
   const int tid = threadIdx.x, warp = tid >> 5, row = tid & 127, half = tid >> 7;
   __shared__ int s_abort;
-  // the G images (once per CTA), the barriers, tensor memory
+  const uint32_t bar1 = sb + kBar, bar2 = sb + kBar + 8, bars = sb + kBar + 16;  // bars: 2 stage barriers
+  // the G image (once per CTA), the barriers, tensor memory
   for (uint32_t i = tid; i < kImage / 16; i += blockDim.x) reinterpret_cast<uint4*>(sm)[i] = A.image[i];
   if (tid == 0) {
     s_abort = 0;
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(sb + kBar));
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(sb + kBar + 8));
+    for (int b = 0; b < 4; ++b) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(sb + kBar + 8 * b));
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 0) {
@@ -169,29 +179,38 @@ __global__ void __launch_bounds__(256, 1) k_helmholtz_q3_tc(TcArgs A) {
                  "r"(kTmemCols));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
-  const uint32_t tmem_slot = sb + kSlot;
   const uint32_t lane_base = uint32_t((warp & 3) * 32) << 16;
-  const uint32_t bar1 = sb + kBar, bar2 = sb + kBar + 8;
-  uint32_t ph1 = 0, ph2 = 0;
-  const uint32_t id1 = idesc(kM, kNq), id2 = idesc(kM, kNb);
+  uint32_t ph1 = 0, ph2 = 0, phs[2] = {0, 0};
+  const uint32_t id1 = idesc(kM, kNq), id2 = idesc(kM, kNb, true);
   const int64_t ntiles = (A.ncells + kM - 1) / kM;
-  // coefficients of the current tile: row r, column q at r * 64 + (q ^ (r & 31)) (a warp's 32 rows
-  // read one column from 32 banks)
-  float* stage = reinterpret_cast<float*>(sm + kStage);
   const uint32_t rowoff = uint32_t((row & 7) * 16 + (row >> 3) * 1024);  // row's place in a 64-column tile
-  // products committed to bar1 / bar2 and not yet waited for; a wait clears its flag and advances
-  // its phase only when it succeeds, so a timed-out product is waited for again before the exit
-  int pend1 = 0, pend2 = 0;
+  // asynchronous work committed and not yet waited for; a wait clears its flag and advances its
+  // phase only when it succeeds, so timed-out work is waited for again before the exit
+  int pend1 = 0, pend2 = 0, pends[2] = {0, 0};
   auto wait1 = [&]() {
     if (wait_phase(bar1, ph1)) { ph1 ^= 1; pend1 = 0; } else { s_abort = 1; }
   };
   auto wait2 = [&]() {
     if (wait_phase(bar2, ph2)) { ph2 ^= 1; pend2 = 0; } else { s_abort = 1; }
   };
+  auto waits = [&](int b) {
+    if (wait_phase(bars + 8 * b, phs[b])) { phs[b] ^= 1; pends[b] = 0; } else { s_abort = 1; }
+  };
+  // thread 0: the coefficient tile t into stage buffer b by one bulk copy
+  auto fetch_coef = [&](int64_t t, int b) {
+    const uint32_t dst = sb + kStage + b * kStageBytes, bar = bars + 8 * b;
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(kStageBytes) : "memory");
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+                 "l"(A.coef + t * (kM * 64)), "r"(kStageBytes), "r"(bar)
+                 : "memory");
+  };
   int64_t tile = blockIdx.x;
   int64_t base = 0;
   bool on = tile < ntiles ? tile_cell(A, tile, row, base) : false;
-  // prologue: the first tile's nodal values
+  // prologue: the first tile's coefficients and nodal values
+  if (tile < ntiles && tid == 0) fetch_coef(tile, 0);
+  if (tile < ntiles) pends[0] = 1;
   if (tile < ntiles) {
     float x[32];
     gather32(A, on, base, half, x);
@@ -203,7 +222,6 @@ __global__ void __launch_bounds__(256, 1) k_helmholtz_q3_tc(TcArgs A) {
   __syncthreads();
   fence_after();
   const uint32_t tmem = *reinterpret_cast<volatile uint32_t*>(sm + kSlot);
-  (void)tmem_slot;
   const uint32_t d1 = tmem, d2 = tmem + 256;
   auto issue_product1 = [&]() {
     for (int t = 0; t < 3; ++t) {
@@ -214,32 +232,24 @@ __global__ void __launch_bounds__(256, 1) k_helmholtz_q3_tc(TcArgs A) {
   };
   if (tile < ntiles && tid == 0) issue_product1();
   pend1 = tile < ntiles ? 1 : 0;
-  for (; tile < ntiles; tile += gridDim.x) {
+  int sbuf = 0;  // stage buffer of the current tile
+  for (; tile < ntiles; tile += gridDim.x, sbuf ^= 1) {
     const int64_t next = tile + gridDim.x;
-    // 1. D1 of this tile is ready
+    // 1. D1 of this tile and its coefficients are ready; the next tile's coefficients are fetched
     wait1();
+    waits(sbuf);
     __syncthreads();
     if (s_abort) break;
     fence_after();
-    // 2. coefficients of the tile (contiguous [cell][64] in global memory), coalesced; the next
-    //    tile's nodal values into registers
-    {
-      const float4* cg = reinterpret_cast<const float4*>(A.coef + tile * kM * 64);
-      for (int i = tid; i < kM * 16; i += blockDim.x) {
-        const int r = i >> 4, q4 = (i & 15) * 4;
-        const float4 v = (tile * kM + r < A.ncells) ? __ldg(cg + i) : make_float4(0.f, 0.f, 0.f, 0.f);
-        stage[r * 64 + ((q4 + 0) ^ (r & 31))] = v.x;
-        stage[r * 64 + ((q4 + 1) ^ (r & 31))] = v.y;
-        stage[r * 64 + ((q4 + 2) ^ (r & 31))] = v.z;
-        stage[r * 64 + ((q4 + 3) ^ (r & 31))] = v.w;
-      }
-    }
+    if (next < ntiles && tid == 0) fetch_coef(next, sbuf ^ 1);
+    if (next < ntiles) pends[sbuf ^ 1] = 1;
+    const float* stage = reinterpret_cast<const float*>(sm + kStage + sbuf * kStageBytes);
+    // the next tile's nodal values into registers
     int64_t nbase = 0;
     const bool non = next < ntiles ? tile_cell(A, next, row, nbase) : false;
     float xn[32];
     gather32(A, non, nbase, half, xn);
-    __syncthreads();
-    // 3. per 64-column chunk: coefficients, then V += P_chunk G_chunk
+    // 2. per 64-column chunk: coefficients, then V += P_chunk G_chunk
     for (int j = 0; j < 4; ++j) {
       if (j > 0) {
         wait2();
@@ -255,7 +265,7 @@ __global__ void __launch_bounds__(256, 1) k_helmholtz_q3_tc(TcArgs A) {
 #pragma unroll
         for (int i = 0; i < 16; ++i) {
           const int q = q0 + i;
-          v[i] *= j == 0 ? cTcW[q] * A.mass_h3 : cTcW[q] * stage[row * 64 + (q ^ (row & 31))] * A.h;
+          v[i] *= j == 0 ? cTcW[q] * A.mass_h3 : cTcW[q] * stage[q * kM + row] * A.h;
         }
         put_split8(sm, kA2H, kA2L, rowoff + (q0 >> 3) * 128, v);
         put_split8(sm, kA2H, kA2L, rowoff + ((q0 >> 3) + 1) * 128, v + 8);
@@ -266,16 +276,19 @@ __global__ void __launch_bounds__(256, 1) k_helmholtz_q3_tc(TcArgs A) {
       if (tid == 0) {
         fence_after();
         for (int t = 0; t < 3; ++t) {
-          const uint32_t a = sb + (t == 2 ? kA2L : kA2H), b = sb + (t == 1 ? kB2L : kB2H);
+          const uint32_t a = sb + (t == 2 ? kA2L : kA2H), b = sb + (t == 1 ? kB1L : kB1H);
+          // B = G^T read from the product-1 image as MN-major without swizzle: 8 nodes contiguous
+          // (16 B), node groups 128 B apart (the stride offset in this mode), Gauss-point groups of
+          // 8 rows 1024 B apart (the leading offset)
           for (int s = 0; s < 4; ++s)
-            mma_bf16(d2, sdesc(a + s * 256, 1024), sdesc(b + j * 1024 + s * 256, 4096), id2, (j | t | s) != 0);
+            mma_bf16(d2, sdesc(a + s * 256, 1024), sdesc2(b + (8 * j + 2 * s) * 1024, 1024, 128), id2, (j | t | s) != 0);
         }
         commit(bar2);
       }
       pend2 = 1;
     }
     if (s_abort) break;
-    // 4. the next tile's U (its first product reads it while this tile is scattered); D1 of this
+    // 3. the next tile's U (its first product reads it while this tile is scattered); D1 of this
     //    tile has been read in full
     if (next < ntiles) {
 #pragma unroll
@@ -289,7 +302,7 @@ __global__ void __launch_bounds__(256, 1) k_helmholtz_q3_tc(TcArgs A) {
       issue_product1();
     }
     if (next < ntiles) pend1 = 1;
-    // 5. this tile's V, scattered
+    // 4. this tile's V, scattered
     wait2();
     __syncthreads();
     if (s_abort) break;
@@ -311,10 +324,12 @@ __global__ void __launch_bounds__(256, 1) k_helmholtz_q3_tc(TcArgs A) {
     __syncthreads();
   }
   if (s_abort) {
-    // report, give the products still in flight their time, then free the tensor memory
+    // report, give the work still in flight its time, then free the tensor memory
     if (tid == 0) atomicExch(A.err, 1);
     if (pend1) wait_phase(bar1, ph1);
     if (pend2) wait_phase(bar2, ph2);
+    for (int b = 0; b < 2; ++b)
+      if (pends[b]) wait_phase(bars + 8 * b, phs[b]);
   }
   fence_before();
   __syncthreads();
@@ -324,20 +339,21 @@ __global__ void __launch_bounds__(256, 1) k_helmholtz_q3_tc(TcArgs A) {
   }
 }
 
-// the two G images: B of product 1 (256 rows x K = 64) and of product 2 (64 rows x K = 256), hi, lo
+// coefficients [cell][64] -> per tile of 128 cells [tile][q][row] (rows past the end: 0)
+__global__ void k_tc_coef_layout(const float* __restrict__ in, float* __restrict__ out, int64_t ncells, int64_t ntiles) {
+  const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i >= ntiles * kM * 64) return;
+  const int64_t t = i / (kM * 64);
+  const int q = int((i / kM) % 64), r = int(i % kM);
+  const int64_t cell = t * kM + r;
+  out[i] = cell < ncells ? in[cell * 64 + q] : 0.0f;
+}
+
+// the G image: B of product 1 (256 rows x K = 64, K-major), hi then lo
 std::vector<uint16_t> make_image() {
   double S[16], Sp[16], W[4];
   qk_host_tables(3, S, Sp, W);
   std::vector<uint16_t> img(kImage / 2, 0);
-  auto put = [&](uint32_t region, uint32_t off, float x) {
-    const __nv_bfloat16 h = __float2bfloat16_rn(x);
-    const __nv_bfloat16 l = __float2bfloat16_rn(x - __bfloat162float(h));
-    uint16_t hb, lb;
-    std::memcpy(&hb, &h, 2);
-    std::memcpy(&lb, &l, 2);
-    img[(region + off) / 2] = hb;
-    img[(region + 32768 + off) / 2] = lb;
-  };
   for (int col = 0; col < kNq; ++col) {
     const int part = col / 64, q = col % 64, qa = q % 4, qb = (q / 4) % 4, qc = q / 16;
     for (int l = 0; l < kNb; ++l) {
@@ -346,14 +362,25 @@ std::vector<uint16_t> make_image() {
       const double fb = part == 2 ? Sp[4 * qb + b] : S[4 * qb + b];
       const double fc = part == 3 ? Sp[4 * qc + c] : S[4 * qc + c];
       const float g = float(fa * fb * fc);
-      put(kB1H, kmajor(col, l, kNb), g);   // product 1: B[n = col][k = l]
-      put(kB2H, kmajor(l, col, kNq), g);   // product 2: B[n = l][k = col]
+      const __nv_bfloat16 h = __float2bfloat16_rn(g);
+      const __nv_bfloat16 lo = __float2bfloat16_rn(g - __bfloat162float(h));
+      const uint32_t off = kmajor(col, l, kNb);
+      std::memcpy(&img[(kB1H + off) / 2], &h, 2);
+      std::memcpy(&img[(kB1L + off) / 2], &lo, 2);
     }
   }
   return img;
 }
 
 }  // namespace
+
+mf_status launch_tc_coef_layout(mf_ctx* ctx, const mf_dofmap* m, const float* in, float* out) {
+  const int64_t ntiles = (m->n_cells + kM - 1) / kM, n = ntiles * kM * 64;
+  k_tc_coef_layout<<<int((n + 255) / 256), 256, 0, ctx->stream>>>(in, out, m->n_cells, ntiles);
+  ctx->launches++;
+  MF_CUDA_TRY(cudaGetLastError());
+  return MF_OK;
+}
 
 mf_status launch_helmholtz_q3_tc(mf_ctx* ctx, const mf_dofmap* m, const float* src, float* dst, const float* coef,
                                  double mass, int* host_err_out) {

@@ -104,8 +104,10 @@ mf_status launch_qk_coef(mf_ctx* ctx, const mf_dofmap* m, const double* phi, dou
 template <typename T>
 mf_status launch_helmholtz_qk(mf_ctx* ctx, const mf_dofmap* m, const T* src, T* dst, const T* coef, double mass);
 mf_status launch_qk_diag(mf_ctx* ctx, const mf_dofmap* m, const double* coef, double mass, double* diag);
-// Q3 Helmholtz on the tensor cores (fp32 vectors, dst accumulated); host_err_out: the error flag
-// left by earlier launches (may be NULL)
+// Q3 Helmholtz on the tensor cores (fp32 vectors, dst accumulated; coef per tile of 128 cells,
+// [tile][q][row], from launch_tc_coef_layout); host_err_out: the error flag left by earlier
+// launches (may be NULL)
+mf_status launch_tc_coef_layout(mf_ctx* ctx, const mf_dofmap* m, const float* in, float* out);
 mf_status launch_helmholtz_q3_tc(mf_ctx* ctx, const mf_dofmap* m, const float* src, float* dst, const float* coef,
                                  double mass, int* host_err_out);
 // laser top-face load and its parameter derivatives (uniform maps)
@@ -134,6 +136,8 @@ struct mf_op {
   mf::DevBuf qcoef64, qcoef32;    // [27][ncells]
   mf::DevBuf qvec64, qvec32;      // [3][27][ncells]
   mf::DevBuf qmass64, qmass32;    // [27][ncells] heat value term rho_cp,q / dt
+  mf::DevBuf qcoef_tc;            // Q3 tensor-core apply: fp32 coefficients [tile of 128 cells][q][row]
+  bool tc_ready = false;
   mf::DevBuf rho64, rho32, mu64, mu32;  // Oseen
   mf::DevBuf kd64, kd32, nrm64, nrm32;  // Oseen melt-pool extensions
   mf::DevBuf cm64, cm32, cc64, cc32, cv64, cv32;  // Oseen folded Gauss-point coefficients
