@@ -8,7 +8,7 @@
 // are two dense products per tile of 128 cells.  To keep fp32-class accuracy on the bf16 tensor
 // cores every operand x is split into x_hi = bf16(x) and x_lo = bf16(x - x_hi) and each product is
 // x_hi y_hi + x_hi y_lo + x_lo y_hi with fp32 accumulation.  One CTA per SM (224 KB of operand
-// images and coefficients in shared memory, 320 of the 512 tensor-memory columns), persistent over the tiles; two
+// images and coefficients in shared memory, 320 of the 512 tensor-memory columns), persistent over the tiles; four
 // threads per cell gather, apply the coefficients and scatter; thread 0 issues the MMAs.
 #include <cuda_bf16.h>
 
@@ -137,11 +137,11 @@ __device__ __forceinline__ void put_split8(unsigned char* sm, uint32_t hi, uint3
   *reinterpret_cast<uint4*>(sm + lo + off) = make_uint4(l[0], l[1], l[2], l[3]);
 }
 
-// nodes 32 half .. 32 half + 31 of a cell (zeros for a cell past the end)
-__device__ __forceinline__ void gather32(const TcArgs& A, bool on, int64_t base, int half, float* x) {
+// nodes 16 quarter .. 16 quarter + 15 of a cell (zeros for a cell past the end)
+__device__ __forceinline__ void gather16(const TcArgs& A, bool on, int64_t base, int quarter, float* x) {
 #pragma unroll
-  for (int e = 0; e < 32; ++e) {
-    const int l = 32 * half + e;
+  for (int e = 0; e < 16; ++e) {
+    const int l = 16 * quarter + e;
     x[e] = on ? __ldg(A.src + base + (l & 3) + A.sx * ((l >> 2) & 3) + A.sy * (l >> 4)) : 0.0f;
   }
 }
@@ -155,16 +155,16 @@ __device__ __forceinline__ bool tile_cell(const TcArgs& A, int64_t tile, int row
   return true;
 }
 
-// Two threads per cell: thread t works on row t % 128 of the tile and on half t / 128 of its
-// columns (warps w and w + 4 read the same tensor-memory lanes).  Software-pipelined over the
+// Four threads per cell: thread t works on row t % 128 of the tile and on quarter t / 128 of its
+// columns (warps w, w + 4, w + 8 and w + 12 read the same tensor-memory lanes).  Software-pipelined over the
 // CTA's tiles: the next tile's coefficients arrive by a TMA bulk copy and its nodal values are
 // loaded while the coefficients of the current one are applied, and its first product runs while
 // the current tile is scattered.  Product 2 reads the same G image as product 1, as an MN-major B.
-__global__ void __launch_bounds__(256, 1) k_helmholtz_q3_tc(TcArgs A) {
+__global__ void __launch_bounds__(512, 1) k_helmholtz_q3_tc(TcArgs A) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* sm = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   const uint32_t sb = static_cast<uint32_t>(__cvta_generic_to_shared(sm));
-  const int tid = threadIdx.x, warp = tid >> 5, row = tid & 127, half = tid >> 7;
+  const int tid = threadIdx.x, warp = tid >> 5, row = tid & 127, quarter = tid >> 7;
   __shared__ int s_abort;
   const uint32_t bar1 = sb + kBar, bar2 = sb + kBar + 8, bars = sb + kBar + 16;  // bars: 2 stage barriers
   // the G image (once per CTA), the barriers, tensor memory
@@ -212,10 +212,10 @@ __global__ void __launch_bounds__(256, 1) k_helmholtz_q3_tc(TcArgs A) {
   if (tile < ntiles && tid == 0) fetch_coef(tile, 0);
   if (tile < ntiles) pends[0] = 1;
   if (tile < ntiles) {
-    float x[32];
-    gather32(A, on, base, half, x);
+    float x[16];
+    gather16(A, on, base, quarter, x);
 #pragma unroll
-    for (int g = 0; g < 4; ++g) put_split8(sm, kA1H, kA1L, rowoff + (4 * half + g) * 128, x + 8 * g);
+    for (int g = 0; g < 2; ++g) put_split8(sm, kA1H, kA1L, rowoff + (2 * quarter + g) * 128, x + 8 * g);
   }
   fence_async_smem();
   fence_before();
@@ -247,8 +247,8 @@ __global__ void __launch_bounds__(256, 1) k_helmholtz_q3_tc(TcArgs A) {
     // the next tile's nodal values into registers
     int64_t nbase = 0;
     const bool non = next < ntiles ? tile_cell(A, next, row, nbase) : false;
-    float xn[32];
-    gather32(A, non, nbase, half, xn);
+    float xn[16];
+    gather16(A, non, nbase, quarter, xn);
     // 2. per 64-column chunk: coefficients, then V += P_chunk G_chunk
     for (int j = 0; j < 4; ++j) {
       if (j > 0) {
@@ -257,10 +257,9 @@ __global__ void __launch_bounds__(256, 1) k_helmholtz_q3_tc(TcArgs A) {
         if (s_abort) break;
         fence_after();
       }
-#pragma unroll
-      for (int c16 = 0; c16 < 2; ++c16) {
+      {
         float v[16];
-        const int q0 = half * 32 + c16 * 16;
+        const int q0 = quarter * 16;
         tmem_ld16(d1 + lane_base + j * 64 + q0, v);
 #pragma unroll
         for (int i = 0; i < 16; ++i) {
@@ -292,7 +291,7 @@ __global__ void __launch_bounds__(256, 1) k_helmholtz_q3_tc(TcArgs A) {
     //    tile has been read in full
     if (next < ntiles) {
 #pragma unroll
-      for (int g = 0; g < 4; ++g) put_split8(sm, kA1H, kA1L, rowoff + (4 * half + g) * 128, xn + 8 * g);
+      for (int g = 0; g < 2; ++g) put_split8(sm, kA1H, kA1L, rowoff + (2 * quarter + g) * 128, xn + 8 * g);
     }
     fence_async_smem();
     fence_before();
@@ -307,14 +306,13 @@ __global__ void __launch_bounds__(256, 1) k_helmholtz_q3_tc(TcArgs A) {
     __syncthreads();
     if (s_abort) break;
     fence_after();
-#pragma unroll
-    for (int c16 = 0; c16 < 2; ++c16) {
+    {
       float v[16];
-      tmem_ld16(d2 + lane_base + half * 32 + c16 * 16, v);
+      tmem_ld16(d2 + lane_base + quarter * 16, v);
       if (on)
 #pragma unroll
         for (int i = 0; i < 16; ++i) {
-          const int l = half * 32 + c16 * 16 + i;
+          const int l = quarter * 16 + i;
           atomicAdd(A.dst + base + (l & 3) + A.sx * ((l >> 2) & 3) + A.sy * (l >> 4), v[i]);
         }
     }
@@ -420,7 +418,7 @@ mf_status launch_helmholtz_q3_tc(mf_ctx* ctx, const mf_dofmap* m, const float* s
   a.h = float(h);
   const int64_t ntiles = (m->n_cells + kM - 1) / kM;
   const int grid = int(std::min<int64_t>(ntiles, ctx->sm_count > 0 ? ctx->sm_count : 152));
-  k_helmholtz_q3_tc<<<grid, 256, kSmem + 1024, ctx->stream>>>(a);
+  k_helmholtz_q3_tc<<<grid, 512, kSmem + 1024, ctx->stream>>>(a);
   ctx->launches++;
   MF_CUDA_TRY(cudaGetLastError());
   if (host_err_out) *host_err_out = *reinterpret_cast<volatile int*>(h_err);
