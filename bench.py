@@ -483,12 +483,9 @@ def meltpool_oseen(ctx, n, flush, darcy_c=None):
                       "rel_residual": info["rel_residual"], "status": info["status"]}}
 
 
-def meltpool_step(ctx, n=64, reps=3):
-    """One step of the melt-pool algorithm on the 600 um box (64^3 cells: 2.1M Q2 nodes per field,
-    6.7M velocity-pressure DoFs): predictors, level-set advection (GMRES) with the variant-1
-    transport velocity, 2 reinitialisation steps (CG), two-phase heat with laser and evaporative
-    cooling (GMRES), melt-pool Navier-Stokes with surface tension, recoil and Darcy damping
-    (FGMRES, block-triangular).  The same state is advanced reps times after one warm-up step."""
+def build_meltpool_step(ctx, n=64):
+    """The melt-pool step workload on the 600 um box (n^3 cells): maps, the seeded state (fp64
+    device tensors) and the MeltPoolStep with every term switched on."""
     import numpy as np
     import torch
     import synthetic as syn
@@ -513,6 +510,18 @@ def meltpool_step(ctx, n=64, reps=3):
         darcy_c=dar["C"], darcy_b=dar["b"], alpha0=st["alpha0"], alpha1=st["alpha1"], t_alpha=st["t_alpha"],
         alpha_res=st["alpha_res"], reinit_steps=p["reinit_steps"], dtau=p["dtau_cells"] * wl.h, tol=p["tol"],
         flow_tol=p["flow_tol"], maxit=500)
+    return wl, maps, state, step
+
+
+def meltpool_step(ctx, n=64, reps=3):
+    """One step of the melt-pool algorithm on the 600 um box (64^3 cells: 2.1M Q2 nodes per field,
+    6.7M velocity-pressure DoFs): predictors, level-set advection (GMRES) with the variant-1
+    transport velocity, 2 reinitialisation steps (CG), two-phase heat with laser and evaporative
+    cooling (GMRES), melt-pool Navier-Stokes with surface tension, recoil and Darcy damping
+    (FGMRES, block-triangular).  The same state is advanced reps times after one warm-up step."""
+    import torch
+    wl, maps, state, step = build_meltpool_step(ctx, n)
+    p = wl.params
     step.advance(state)
     torch.cuda.synchronize()
     runs = []
@@ -570,6 +579,26 @@ def helmholtz_qk(ctx, flush):
             dense = 3 * 2 * 2 * 64 * 256 * m.n_cells
             r["tc_bf16x3"] = {"ms": ms, "gdofs": m.n_dofs / ms / 1e6, "tensor_tflops": dense / ms / 1e9,
                               "sum_factorised_tflops_equiv": fl / ms / 1e9, "variant": op.variant}
+            # solves to 1e-10: fp64 Jacobi-CG; defect correction with fp32 Chebyshev-CG inner solves on
+            # the CUDA cores or on the tensor cores
+            b = torch.tensor(syn.uniform_pm1(2, m.n_dofs), device="cuda")
+            # (this contrast-1000 problem needs ~1750 Jacobi-CG iterations in fp64: the inner solves get
+            # room to reach their 1e-4)
+            runs = {"fp64_cg_jacobi": dict(solver="cg", precond="jacobi"),
+                    "mixed_inner_f32": dict(solver="defect_correction", precond="chebyshev", inner_arith="f32",
+                                            inner_maxit=3000),
+                    "mixed_inner_tensor_cores": dict(solver="defect_correction", precond="chebyshev",
+                                                     inner_arith="tc", inner_maxit=3000)}
+            r["solve"] = {}
+            for name, kw in runs.items():
+                op.solve(b, tol=1e-10, **kw)
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                _, info = op.solve(b, tol=1e-10, **kw)
+                torch.cuda.synchronize()
+                r["solve"][name] = {"seconds": time.perf_counter() - t0, "iterations": info["iterations"],
+                                    "outer": info["outer_iterations"], "rel_residual": info["rel_residual"],
+                                    "status": info["status"]}
         out[f"q{k}"] = r
     return out
 

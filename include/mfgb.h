@@ -51,6 +51,8 @@ typedef int mf_status;
  * products and sums, 48-bit significand) on the fp32 pipes, which GB300 runs at ~62x its fp64
  * rate; accurate to a few 1e-14 relative to |A||u| componentwise. */
 typedef enum { MF_F64 = 0, MF_F32 = 1, MF_F16 = 2, MF_BF16 = 3, MF_DF64 = 4 } mf_dtype;
+/* mf_solver_params.inner_arith value beside the dtypes: fp32 inner applies on the tensor cores */
+enum { MF_INNER_TENSOR_CORES = 16 };
 
 typedef struct mf_ctx mf_ctx;
 typedef struct mf_mesh mf_mesh;
@@ -257,7 +259,8 @@ typedef struct {
   double schur_tol;    /* MF_PREC_BLOCK_TRIANGULAR: relative tolerance of the inner Schur CG (<= 0: 0.1) */
   int inner_arith;     /* defect correction: arithmetic of the inner fp32 operator applies (CG and
                           Chebyshev): MF_F32 (default, also 0), MF_F16 or MF_BF16 (packed pairs of
-                          right-hand sides, see mf_apply_packed16) */
+                          right-hand sides, see mf_apply_packed16), or MF_INNER_TENSOR_CORES (Q3
+                          Helmholtz operators: the applies of mf_apply_tc) */
   int reserved3;
 } mf_solver_params;
 

@@ -163,7 +163,7 @@ def solver_params(solver="cg", precond="jacobi", tol=1e-10, maxit=5000, restart=
     s.precond = {"none": MF_PREC_NONE, "jacobi": MF_PREC_JACOBI, "chebyshev": MF_PREC_CHEBYSHEV,
                  "block_jacobi": MF_PREC_BLOCK_JACOBI, "block_triangular": MF_PREC_BLOCK_TRIANGULAR}[precond]
     s.schur_tol, s.schur_maxit, s.velocity_steps = schur_tol, schur_maxit, velocity_steps
-    s.inner_arith = {"f32": MF_F32, "f16": MF_F16, "bf16": MF_BF16}[inner_arith]
+    s.inner_arith = {"f32": MF_F32, "f16": MF_F16, "bf16": MF_BF16, "tc": _lib.MF_INNER_TENSOR_CORES}[inner_arith]
     s.inner_dtype = MF_F32
     s.restart, s.cheby_degree, s.maxit, s.inner_maxit = restart, cheby_degree, maxit, inner_maxit
     s.use_graph = 1 if use_graph else 0

@@ -7,6 +7,7 @@ LIB_PATH = os.path.join(_HERE, "libmfgb.so")
 
 MF_OK, MF_EINVAL, MF_ENOMEM, MF_ECUDA, MF_ENOTCONV, MF_ETIMEOUT, MF_EUNSUPPORTED = 0, -1, -2, -3, -4, -5, -6
 MF_F64, MF_F32, MF_F16, MF_BF16, MF_DF64 = 0, 1, 2, 3, 4
+MF_INNER_TENSOR_CORES = 16
 MF_OP_HELMHOLTZ, MF_OP_HEAT, MF_OP_OSEEN, MF_OP_REINIT = 0, 1, 2, 3
 MF_HEAVISIDE_TANH, MF_HEAVISIDE_SINE = 0, 1
 MF_COEF_INKERNEL, MF_COEF_QPOINT = 0, 1

@@ -437,6 +437,8 @@ bool heat_tabulated(const mf_op* op) {
   return op->p.kind == MF_OP_HEAT && (op->beta || op->kq_user || op->rhocp_user || op->betaq_user);
 }
 
+mf_status apply_tc(mf_op* op, const float* src, float* dst, int nrhs, int64_t ld);
+
 // 3 or 4 for the Q3/Q4 Helmholtz operators, else 0
 int qk_degree(const mf_op* op) { return op->map[0] && op->map[0]->degree >= 3 ? op->map[0]->degree : 0; }
 
@@ -622,9 +624,12 @@ mf_status apply_h16(mf_op* op, const float* src, float* dst, int nrhs, int64_t l
 template <typename T>
 mf_status apply_impl(mf_op* op, const T* src, T* dst, int nrhs, int64_t ld, bool transpose, int prec) {
   const bool f32 = sizeof(T) == 4;
-  if (f32) prec = (prec == PREC_F16 || prec == PREC_BF16 || prec == PREC_F32) ? prec : op->f32_prec;
+  if (f32) prec = (prec == PREC_F16 || prec == PREC_BF16 || prec == PREC_F32 || prec == PREC_TC) ? prec : op->f32_prec;
   else if (prec != PREC_F64 && prec != PREC_DF64) prec = op->f64_prec;
-  if (qk_degree(op)) {  // Q3 / Q4 Helmholtz: symmetric, fp64 or fp32 arithmetic
+  if (qk_degree(op)) {  // Q3 / Q4 Helmholtz: symmetric, fp64 or fp32 arithmetic (Q3 fp32: or the tensor cores)
+    if constexpr (sizeof(T) == 4) {
+      if (prec == PREC_TC) return apply_tc(op, src, dst, nrhs, ld);
+    }
     if (prec != PREC_F64 && prec != PREC_F32) return fail(MF_EUNSUPPORTED, "degrees 3 and 4: fp64 or fp32 applies");
     MF_TRY(check_fields(op));
     MF_TRY(ensure_tables(op));
@@ -779,6 +784,15 @@ mf_status mf_apply_tc(mf_op* op, const float* src, float* dst, int nrhs, int64_t
   MF_GUARD_BEGIN
   if (!op || !src || !dst) return fail(MF_EINVAL, "NULL argument");
   if (nrhs < 1 || ld < op->n) return fail(MF_EINVAL, "nrhs must be >= 1 and ld >= n");
+  return apply_tc(op, src, dst, nrhs, ld);
+  MF_GUARD_END
+}
+
+}  // extern "C"
+
+namespace mf {
+
+mf_status apply_tc(mf_op* op, const float* src, float* dst, int nrhs, int64_t ld) {
   if (qk_degree(op) != 3) return fail(MF_EUNSUPPORTED, "tensor-core applies: Q3 Helmholtz operators");
   MF_TRY(check_fields(op));
   MF_TRY(ensure_tables(op));
@@ -795,8 +809,11 @@ mf_status mf_apply_tc(mf_op* op, const float* src, float* dst, int nrhs, int64_t
   }
   op->variant = "helmholtz_q3/uniform/f32/tcgen05-bf16x3/dense";
   return MF_OK;
-  MF_GUARD_END
 }
+
+}  // namespace mf
+
+extern "C" {
 
 mf_status mf_apply_transpose(mf_op* op, const void* src, void* dst, int nrhs, int64_t ld, int dtype) {
   MF_GUARD_BEGIN

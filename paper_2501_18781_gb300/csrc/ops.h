@@ -8,7 +8,7 @@ namespace mf {
 
 enum ScalarKind { K_HELM = 0, K_HEAT = 1, K_REINIT = 2, K_MASS = 3 };
 // arithmetic of an apply: fp64, fp32, or double-float (fp64 storage, pairs of fp32 in the kernel)
-enum ApplyPrec { PREC_F64 = 0, PREC_F32 = 1, PREC_DF64 = 2, PREC_F16 = 3, PREC_BF16 = 4 };
+enum ApplyPrec { PREC_F64 = 0, PREC_F32 = 1, PREC_DF64 = 2, PREC_F16 = 3, PREC_BF16 = 4, PREC_TC = 5 };
 
 // Arguments of the scalar cell kernels.  Vector fields are in the apply precision T.
 template <typename T> struct ScalarArgs {
@@ -147,7 +147,7 @@ struct mf_op {
   bool diag_ready = false;
   int mode64 = 1, mode32 = 0;     // coefficient mode per precision (autotuned)
   int f64_prec = 0;               // arithmetic of fp64 applies inside solvers (PREC_F64 or PREC_DF64)
-  int f32_prec = 1;               // arithmetic of fp32 applies inside solvers (PREC_F32, PREC_F16, PREC_BF16)
+  int f32_prec = 1;               // arithmetic of fp32 applies inside solvers (PREC_F32, PREC_F16, PREC_BF16, PREC_TC)
   float h16_cnorm = 0.0f;         // 16-bit applies: power of two >= every coefficient (0: not computed)
   int block = 128;                // octree cells per block (autotuned: 64 or 128)
   int persistent_blocks = 0;      // > 0: persistent launch with this many blocks per SM (autotuned)

@@ -669,8 +669,13 @@ mf_status solve_impl(mf_op* op, const mf_solver_params* sp, const double* b, dou
     if (sp->solver != MF_SOLVER_DEFECT_CORRECTION)
       return fail(MF_EINVAL, "16-bit inner arithmetic belongs to defect correction");
     op->f32_prec = sp->inner_arith == MF_F16 ? PREC_F16 : PREC_BF16;
+  } else if (sp->inner_arith == MF_INNER_TENSOR_CORES) {
+    if (sp->solver != MF_SOLVER_DEFECT_CORRECTION)
+      return fail(MF_EINVAL, "tensor-core inner arithmetic belongs to defect correction");
+    if (qk_degree(op) != 3) return fail(MF_EUNSUPPORTED, "tensor-core inner applies: Q3 Helmholtz operators");
+    op->f32_prec = PREC_TC;
   } else if (sp->inner_arith != 0 && sp->inner_arith != MF_F32) {
-    return fail(MF_EINVAL, "inner_arith must be MF_F32, MF_F16 or MF_BF16");
+    return fail(MF_EINVAL, "inner_arith must be MF_F32, MF_F16, MF_BF16 or MF_INNER_TENSOR_CORES");
   }
   mf_solve_info inf{};
   mf_status st = MF_OK;

@@ -123,3 +123,29 @@ def test_tensor_core_apply_rejects_q4(ctx):
     _, _, op = _problem(ctx, 4, 2)
     with pytest.raises(MFError):
         op.apply(torch.zeros(op.n, dtype=torch.float32, device="cuda"), arith="tc")
+
+
+@pytest.mark.parametrize("inner", ["f32", "tc"])
+def test_q3_defect_correction_with_cuda_core_or_tensor_core_inner_applies(ctx, inner):
+    """fp64 outer residual, fp32 Chebyshev-CG inner solve whose applies run on the CUDA cores or on
+    the tensor cores: the oracle's true residual reaches 1e-10."""
+    dm, A, op = _problem(ctx, 3, 4)
+    b = syn.uniform_pm1(9, dm.n_dofs)
+    x, info = op.solve(torch.tensor(b, device="cuda"), solver="defect_correction", precond="chebyshev",
+                       inner_arith=inner, tol=1e-10)
+    assert info["status"] == 0, info
+    res = np.linalg.norm(b - A @ x.cpu().numpy()) / np.linalg.norm(b)
+    assert res <= 1e-10 * (1 + 1e-3), (res, info)
+    assert info["outer_iterations"] >= 2
+
+
+def test_tensor_core_inner_arithmetic_needs_q3_and_defect_correction(ctx):
+    from paper_2501_18781_gb300._lib import MFError
+    dm, A, op = _problem(ctx, 3, 2)
+    b = torch.ones(dm.n_dofs, dtype=torch.float64, device="cuda")
+    with pytest.raises(MFError):
+        op.solve(b, solver="cg", precond="jacobi", inner_arith="tc")
+    _, _, op4 = _problem(ctx, 4, 2)
+    with pytest.raises(MFError):
+        op4.solve(torch.ones(op4.n, dtype=torch.float64, device="cuda"), solver="defect_correction",
+                  precond="chebyshev", inner_arith="tc")
