@@ -41,18 +41,19 @@ def _cells(n, c0):
     return (ci + n * (cj + n * ck)).transpose(2, 1, 0).ravel()     # patch cell order: i fastest
 
 
-def scalar_rows(n, lo, hi, dofs, build, nodal, u, dirichlet, cellwise=None, transpose=False, absolute=False):
-    """(A u)_i (or (A^T u)_i) for the Q2 DoFs ``dofs`` of a uniform n^3 mesh of [lo, hi].
+def scalar_rows(n, lo, hi, dofs, build, nodal, u, dirichlet, cellwise=None, transpose=False, absolute=False,
+                degree=2):
+    """(A u)_i (or (A^T u)_i) for the Q_k DoFs ``dofs`` (k = ``degree``) of a uniform n^3 mesh of [lo, hi].
     ``build(dm, nodal, cellwise)`` assembles the operator on a patch from the nodal fields (dict of
     arrays over the patch DoFs) and the per-cell fields (dict of (8, ...) arrays); ``dirichlet`` is
     the full problem's Dirichlet mask (nodal arrays are indexed on their last axis).  With
     ``absolute``, (|A| |u|)_i instead."""
-    L = 2 * n + 1
+    L = degree * n + 1
     out = np.empty(len(dofs))
     for s, d in enumerate(dofs):
         coord = (d % L, (d // L) % L, d // (L * L))
-        c0 = [_first_cell(c, 2, n) for c in coord]
-        dm, idx = _patch(n, lo, hi, c0, 2)
+        c0 = [_first_cell(c, degree, n) for c in coord]
+        dm, idx = _patch(n, lo, hi, c0, degree)
         cells = _cells(n, c0)
         A = build(dm, {k: v[..., idx] for k, v in nodal.items()},
                   {k: v[cells] for k, v in (cellwise or {}).items()}).tocsr()

@@ -201,3 +201,36 @@ def test_meltpool_step_64_properties(ctx):
     i_adv, i_new = (w * out["phi_advected"]).sum().item(), (w * out["phi"]).sum().item()
     assert abs(i_new - i_adv) <= 1e-8 * (w * out["phi_advected"].abs()).sum().item()
     assert out["phi"].abs().max().item() <= 1.05
+
+
+@pytest.mark.parametrize("k,n", [(3, 64), (4, 48)])
+def test_qk_bench_size_sampled_rows(ctx, k, n):
+    """Q3 on 64^3 and Q4 on 48^3 cells (7,189,057 DoFs each, as bench.py builds them): sampled rows
+    against the oracle's degree-k patch rows, fp64 1e-12, fp32 5e-5, and Q3 on the tensor cores 5e-5."""
+    import torch
+    from paper_2501_18781_gb300 import DofMap, Mesh, Operator
+    m = DofMap(Mesh.uniform(ctx, n), k, 0)
+    eps = 1.0 / (2 * n)
+    phi = syn.initial_level_set(syn.sphere_distance(*m.coords().T), eps)
+    op = Operator(ctx, "helmholtz", [m], mass_coef=1.0, a_liquid=1000.0, a_gas=1.0, eps=eps)
+    op.set_field("phi", torch.tensor(phi, device="cuda"))
+    L = k * n + 1
+    rng = np.random.default_rng(20 + k)
+    rows = list(rng.choice(m.n_dofs, 50, replace=False))
+    for x in (0, 1, L // 2, L - 2, L - 1):
+        for y in (0, k, L - 1):
+            for z in (0, 1, L - 1):
+                rows.append(x + L * (y + L * z))
+    rows = np.unique(np.array(rows))
+    uu = syn.uniform_pm1(30 + k, m.n_dofs).astype(np.float32).astype(np.float64)
+    build = lambda d, nod, cw: asm.helmholtz_matrix(d, nod["phi"], 1.0, 1000.0, 1.0, "tanh", eps)
+    none = np.zeros(m.n_dofs, bool)
+    ref = patch.scalar_rows(n, (0, 0, 0), (1, 1, 1), rows, build, {"phi": phi}, uu, none, degree=k)
+    bound = patch.scalar_rows(n, (0, 0, 0), (1, 1, 1), rows, build, {"phi": phi}, uu, none, degree=k, absolute=True)
+    cases = [("f64", torch.float64, None, 1e-12), ("f32", torch.float32, None, 5e-5)]
+    if k == 3:
+        cases.append(("tc", torch.float32, "tc", 5e-5))
+    for name, dt, arith, rtol in cases:
+        v = op.apply(torch.tensor(uu, device="cuda", dtype=dt), arith=arith).cpu().double().numpy()
+        ok, worst = componentwise_ok(v[rows], ref, bound, rtol)
+        assert ok, (name, worst)

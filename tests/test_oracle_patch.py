@@ -55,3 +55,21 @@ def test_oseen_rows_velocity_and_pressure():
     bound = patch.oseen_rows(n, wl.lo, wl.hi, rows[:20], build, {"phi": phi, "beta": beta}, u, dmu.dirichlet,
                              absolute=True)
     assert np.allclose(bound, (abs(A) @ np.abs(np.where(mask, 0.0, u)))[rows[:20]], rtol=1e-13)
+
+
+def test_q3_q4_helmholtz_rows():
+    """Degree-k patches (Gauss-Lobatto nodes): Q3 and Q4 Helmholtz rows against the assembled matrix,
+    including every corner, edge and face class of the lattice."""
+    for k in (3, 4):
+        n = 3
+        dm = omesh.uniform_dofmap(n, (0, 0, 0), (1, 1, 1), k)
+        phi = syn.initial_level_set(syn.sphere_distance(*dm.dof_coords().T), 1.0 / 6)
+        A = asm.helmholtz_matrix(dm, phi, 1.0, 1000.0, 1.0, "tanh", 1.0 / 6).tocsr()
+        u = syn.uniform_pm1(4 + k, dm.n_dofs)
+        L = k * n + 1
+        rows = np.unique(np.concatenate([np.random.default_rng(k).choice(dm.n_dofs, 60, replace=False),
+                                         [0, L - 1, L * L - 1, dm.n_dofs - 1, L // 2 + L * (L // 2)]]))
+        build = lambda d, nod, cw: asm.helmholtz_matrix(d, nod["phi"], 1.0, 1000.0, 1.0, "tanh", 1.0 / 6)
+        got = patch.scalar_rows(n, (0, 0, 0), (1, 1, 1), rows, build, {"phi": phi}, u, dm.dirichlet, degree=k)
+        ref = (A @ u)[rows]
+        assert np.abs(got - ref).max() <= 1e-13 * np.abs(ref).max(), k
