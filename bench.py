@@ -509,7 +509,8 @@ def build_meltpool_step(ctx, n=64):
         rho_s=sol["rho_s"], mu_s=sol["mu_s"], t_solidus=sol["t_solidus"], t_liquidus=sol["t_liquidus"],
         darcy_c=dar["C"], darcy_b=dar["b"], alpha0=st["alpha0"], alpha1=st["alpha1"], t_alpha=st["t_alpha"],
         alpha_res=st["alpha_res"], reinit_steps=p["reinit_steps"], dtau=p["dtau_cells"] * wl.h, tol=p["tol"],
-        flow_tol=p["flow_tol"], maxit=500)
+        flow_tol=p["flow_tol"], maxit=500, reinit_mixed=p["reinit_mixed"], flow_velocity_steps=p["flow_velocity_steps"],
+        flow_schur_maxit=p["flow_schur_maxit"], flow_schur_tol=p["flow_schur_tol"])
     return wl, maps, state, step
 
 

@@ -410,6 +410,12 @@ typedef struct {
   double dtau;                              /* pseudo-time step (reinit_steps > 0) */
   double tol;                               /* relative tolerance of the level-set and heat solves */
   double flow_tol;                          /* relative tolerance of the flow solve */
+  int flow_velocity_steps;                  /* block-triangular preconditioner of the flow solve: GMRES */
+  int flow_schur_maxit;                     /*   steps on the velocity block, Schur CG cap, Schur CG */
+  double flow_schur_tol;                    /*   tolerance (<= 0: the defaults of mf_solver_params) */
+  int reinit_mixed;                         /* 1: reinitialisation by fp32-inner defect correction
+                                               (Chebyshev), 0: fp64 Jacobi-CG */
+  int reserved;
 } mf_meltpool_params;
 
 typedef struct {

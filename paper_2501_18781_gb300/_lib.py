@@ -67,7 +67,9 @@ class MeltPoolParams(C.Structure):
                 ("gravity", C.c_double * 3), ("laser_power", C.c_double), ("laser_radius", C.c_double),
                 ("laser_absorptivity", C.c_double), ("laser_focus", C.c_double * 3),
                 ("laser_direction", C.c_double * 3), ("reinit_steps", C.c_int), ("maxit", C.c_int),
-                ("dtau", C.c_double), ("tol", C.c_double), ("flow_tol", C.c_double)]
+                ("dtau", C.c_double), ("tol", C.c_double), ("flow_tol", C.c_double),
+                ("flow_velocity_steps", C.c_int), ("flow_schur_maxit", C.c_int), ("flow_schur_tol", C.c_double),
+                ("reinit_mixed", C.c_int), ("reserved", C.c_int)]
 
 
 class MeltPoolInfo(C.Structure):

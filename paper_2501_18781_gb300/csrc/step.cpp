@@ -262,8 +262,14 @@ mf_status mf_meltpool_advance(mf_meltpool_step* step, const double* u_prev, cons
       MF_CUDA_TRY(cudaMemsetAsync(b, 0, sizeof(double) * nu, c->stream));
       MF_TRY(mf::launch_mass_load(c, S.mphi, S.psi.as<double>(), nullptr, 0, 0, 1.0 / p.dtau, false, b));
       MF_TRY(mf::launch_compressive_flux(c, S.mphi, S.psi.as<double>(), phia, b));
-      MF_TRY(run_solve(S.re, scalar_solver(MF_SOLVER_CG, p.tol, maxit), b, S.psi2.as<double>(),
-                       &inf.reinit_iterations, &inf.reinit_residual, &worst));
+      mf_solver_params rs = scalar_solver(MF_SOLVER_CG, p.tol, maxit);
+      if (p.reinit_mixed) {  // fp32 Chebyshev-CG inner solves, fp64 residuals
+        rs.solver = MF_SOLVER_DEFECT_CORRECTION;
+        rs.precond = MF_PREC_CHEBYSHEV;
+        rs.inner_dtype = MF_F32;
+        rs.maxit = 100;
+      }
+      MF_TRY(run_solve(S.re, rs, b, S.psi2.as<double>(), &inf.reinit_iterations, &inf.reinit_residual, &worst));
       std::swap(S.psi.p, S.psi2.p);
     }
     MF_CUDA_TRY(cudaMemcpyAsync(phi_out, S.psi.p, sizeof(double) * nu, cudaMemcpyDeviceToDevice, c->stream));
@@ -317,6 +323,9 @@ mf_status mf_meltpool_advance(mf_meltpool_step* step, const double* u_prev, cons
     fs.restart = 50;
     fs.maxit = maxit;
     fs.tol = p.flow_tol;
+    fs.velocity_steps = p.flow_velocity_steps;
+    fs.schur_maxit = p.flow_schur_maxit;
+    fs.schur_tol = p.flow_schur_tol;
     MF_TRY(run_solve(S.flow, fs, bf, up, &inf.flow_iterations, &inf.flow_residual, &worst));
     MF_TRY(lap(3, t));
     inf.seconds[4] = std::chrono::duration<double>(clk::now() - t0).count();
