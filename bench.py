@@ -34,12 +34,13 @@ FP64_PEAK_TFLOPS = 1.25      # GB300 FP64 (vector and tensor) rate of the profil
 # 9 x 10 = 90, a collocation derivative 5 (3 at the middle point), a test accumulation along one
 # line 6 (4 at the middle point).
 # Gauss-point loop outside, on Gauss-point coefficients with the weight and the powers of h folded
-# in: value sweeps 3 x 270, 27 points x 161 (pressure 15, 9 gradients 39, value terms 24, symmetric
-# stress 17, 3 test accumulations 48, continuity 18), nodal pressure and continuity scaling 16,
-# integration sweeps 3 x 270 = 5983.
+# in (w h^2 rho beta tabulated, so the value terms are multiply-adds only): value sweeps 3 x 270,
+# 27 points x 159 (pressure 15, 9 gradients 39, value terms 24, symmetric stress 15 with 2 mu formed
+# once, 3 test accumulations 48, continuity 18), nodal pressure and continuity scaling 16,
+# integration sweeps 3 x 270 = 5929.
 # Component loop outside: pressure at the Gauss points and its test terms 891, three velocity
 # components x (value sweeps 270 + 27 points x 80) = 7290, integration sweeps and scaling 899.
-OSEEN_FLOPS_PER_CELL = {"component-outer": 891 + 7290 + 899, "qpoint-outer": 810 + 27 * 161 + 16 + 810}
+OSEEN_FLOPS_PER_CELL = {"component-outer": 891 + 7290 + 899, "qpoint-outer": 810 + 27 * 159 + 16 + 810}
 # Algorithmic HBM bytes of one fp64 Oseen apply: read u, write v (16 B per DoF), the nodal
 # level set and convection field the coefficients come from (4 x 8 B per velocity node).
 OSEEN_BYTES_PER_VEL_NODE = 4 * 8

@@ -487,12 +487,14 @@ mf_status ensure_tables(mf_op* op) {
                                      op->kd64.as<double>(), op->kd32.as<float>(), op->nrm64.as<double>(),
                                      op->nrm32.as<float>()));
     }
-    for (mf::DevBuf* b : {&op->cm64, &op->cc64, &op->cv64}) MF_TRY(b->alloc(sizeof(double) * 27 * nc));
-    for (mf::DevBuf* b : {&op->cm32, &op->cc32, &op->cv32}) MF_TRY(b->alloc(sizeof(float) * 27 * nc));
+    for (mf::DevBuf* b : {&op->cm64, &op->cv64}) MF_TRY(b->alloc(sizeof(double) * 27 * nc));
+    for (mf::DevBuf* b : {&op->cm32, &op->cv32}) MF_TRY(b->alloc(sizeof(float) * 27 * nc));
+    MF_TRY(op->cb64.alloc(sizeof(double) * 81 * nc));
+    MF_TRY(op->cb32.alloc(sizeof(float) * 81 * nc));
     MF_TRY(launch_oseen_fold(op->ctx, op->map[0], p.sigma, op->rho64.as<double>(), op->mu64.as<double>(),
-                             p.oseen_flags ? op->kd64.as<double>() : nullptr, op->cm64.as<double>(),
-                             op->cm32.as<float>(), op->cc64.as<double>(), op->cc32.as<float>(), op->cv64.as<double>(),
-                             op->cv32.as<float>()));
+                             p.oseen_flags ? op->kd64.as<double>() : nullptr, op->qvec64.as<double>(),
+                             op->cm64.as<double>(), op->cm32.as<float>(), op->cb64.as<double>(), op->cb32.as<float>(),
+                             op->cv64.as<double>(), op->cv32.as<float>()));
   } else if (qk_degree(op)) {
     const int64_t P3 = int64_t(qk_degree(op) + 1) * (qk_degree(op) + 1) * (qk_degree(op) + 1);
     MF_TRY(op->qcoef64.alloc(sizeof(double) * P3 * nc));
@@ -575,7 +577,7 @@ template <typename T> OseenArgs<T> oseen_args(const mf_op* op, const T* src, T* 
     return f32 ? reinterpret_cast<const T*>(b32.as<float>()) : reinterpret_cast<const T*>(b64.as<double>());
   };
   a.cm = pick(op->cm64, op->cm32);
-  a.cc = pick(op->cc64, op->cc32);
+  a.cb = pick(op->cb64, op->cb32);
   a.cv = pick(op->cv64, op->cv32);
   return a;
 }

@@ -285,13 +285,12 @@ __global__ void __launch_bounds__(128) k_oseen_qouter(OseenArgs<typename Store<T
       for (int qa = 0; qa < 3; ++qa) {
         const int q = qa + 3 * qb + 9 * qc;
         // Gauss-point coefficients with weight and powers of h folded in (tabulated once per
-        // operator): cm = w h^3 (sigma rho [+ Darcy]), cc = w h^2 rho, cv = w h mu
+        // operator): cm = w h^3 (sigma rho [+ Darcy]), cv = w h mu, (bx, by, bz) = w h^2 rho beta
         const T cm = from_store<T>(__ldg(A.cm + q * nc + cell));
-        const T cc = from_store<T>(__ldg(A.cc + q * nc + cell));
         const T cv = from_store<T>(__ldg(A.cv + q * nc + cell));
-        const T bx = from_store<T>(__ldg(A.beta + (0 * 27 + q) * nc + cell));
-        const T by = from_store<T>(__ldg(A.beta + (1 * 27 + q) * nc + cell));
-        const T bz = from_store<T>(__ldg(A.beta + (2 * 27 + q) * nc + cell));
+        const T bx = from_store<T>(__ldg(A.cb + (0 * 27 + q) * nc + cell));
+        const T by = from_store<T>(__ldg(A.cb + (1 * 27 + q) * nc + cell));
+        const T bz = from_store<T>(__ldg(A.cb + (2 * 27 + q) * nc + cell));
         T pw = T(0);
 #pragma unroll
         for (int n = 0; n < 8; ++n) pw += Tb<T>::PWW(q, n) * Pn[n];
@@ -299,12 +298,13 @@ __global__ void __launch_bounds__(128) k_oseen_qouter(OseenArgs<typename Store<T
         grad_at<T>(U0, qa, qb, qc, g[0][0], g[0][1], g[0][2]);
         grad_at<T>(U1, qa, qb, qc, g[1][0], g[1][1], g[1][2]);
         grad_at<T>(U2, qa, qb, qc, g[2][0], g[2][1], g[2][2]);
-        // value test: sigma rho u_d + rho beta . grad u_d
-        R0[q] += cm * U0[q] + cc * (bx * g[0][0] + by * g[0][1] + bz * g[0][2]);
-        R1[q] += cm * U1[q] + cc * (bx * g[1][0] + by * g[1][1] + bz * g[1][2]);
-        R2[q] += cm * U2[q] + cc * (bx * g[2][0] + by * g[2][1] + bz * g[2][2]);
+        // value test: sigma rho u_d + rho beta . grad u_d, accumulated by multiply-adds only
+        R0[q] = fma(bz, g[0][2], fma(by, g[0][1], fma(bx, g[0][0], fma(cm, U0[q], R0[q]))));
+        R1[q] = fma(bz, g[1][2], fma(by, g[1][1], fma(bx, g[1][0], fma(cm, U1[q], R1[q]))));
+        R2[q] = fma(bz, g[2][2], fma(by, g[2][1], fma(bx, g[2][0], fma(cm, U2[q], R2[q]))));
         // gradient test: mu (grad u + grad u^T) - p I
-        T s00 = cv * (g[0][0] + g[0][0]) + pw, s11 = cv * (g[1][1] + g[1][1]) + pw, s22 = cv * (g[2][2] + g[2][2]) + pw;
+        const T cv2 = cv + cv;
+        T s00 = fma(cv2, g[0][0], pw), s11 = fma(cv2, g[1][1], pw), s22 = fma(cv2, g[2][2], pw);
         T s01 = cv * (g[0][1] + g[1][0]), s02 = cv * (g[0][2] + g[2][0]), s12 = cv * (g[1][2] + g[2][1]);
         const T div = g[0][0] + g[1][1] + g[2][2];
         if constexpr (EXT) {
@@ -312,7 +312,7 @@ __global__ void __launch_bounds__(128) k_oseen_qouter(OseenArgs<typename Store<T
           const T nx = from_store<T>(__ldg(A.nrm + q * nc + cell));
           const T ny = from_store<T>(__ldg(A.nrm + (27 + q) * nc + cell));
           const T nz = from_store<T>(__ldg(A.nrm + (54 + q) * nc + cell));
-          const T t = T(-2) * cv * div;
+          const T t = -(cv2 * div);
           const T tx = t * nx, ty = t * ny, tz = t * nz;
           s00 += tx * nx;
           s11 += ty * ny;

@@ -220,10 +220,11 @@ __global__ void k_oseen_ext_tables(UniformGeom ug, const double* phi, const doub
       }
 }
 
-// cm = w h^3 (sigma rho + kd), cc = w h^2 rho, cv = w h mu per (Gauss point, cell), in fp64 and fp32
+// cm = w h^3 (sigma rho + kd), cv = w h mu and cb_d = w h^2 rho beta_d per (Gauss point, cell), in
+// fp64 and fp32
 __global__ void k_oseen_fold(int64_t nc, double h, double sigma, const double* rho, const double* mu,
-                             const double* kd, double* cm64, float* cm32, double* cc64, float* cc32, double* cv64,
-                             float* cv32) {
+                             const double* kd, const double* beta, double* cm64, float* cm32, double* cb64,
+                             float* cb32, double* cv64, float* cv32) {
   const int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (t >= 27 * nc) return;
   const int q = int(t / nc);
@@ -233,8 +234,11 @@ __global__ void k_oseen_fold(int64_t nc, double h, double sigma, const double* r
   const double v = w * h * mu[t];
   cm64[t] = m;
   cm32[t] = float(m);
-  cc64[t] = c;
-  cc32[t] = float(c);
+  for (int d = 0; d < 3; ++d) {
+    const double b = c * beta[d * 27 * nc + t];
+    cb64[d * 27 * nc + t] = b;
+    cb32[d * 27 * nc + t] = float(b);
+  }
   cv64[t] = v;
   cv32[t] = float(v);
 }
@@ -564,12 +568,12 @@ mf_status launch_oseen_qtables(mf_ctx* ctx, const mf_dofmap* mu, const double* p
 }
 
 mf_status launch_oseen_fold(mf_ctx* ctx, const mf_dofmap* mu, double sigma, const double* rho, const double* muq,
-                            const double* kd, double* cm64, float* cm32, double* cc64, float* cc32, double* cv64,
-                            float* cv32) {
+                            const double* kd, const double* beta, double* cm64, float* cm32, double* cb64,
+                            float* cb32, double* cv64, float* cv32) {
   MF_CUDA_TRY(upload_tables_here());
   const int64_t nc = mu->n_cells;
-  k_oseen_fold<<<blocks(27 * nc, 256), 256, 0, ctx->stream>>>(nc, mu->mesh->h0, sigma, rho, muq, kd, cm64, cm32, cc64,
-                                                              cc32, cv64, cv32);
+  k_oseen_fold<<<blocks(27 * nc, 256), 256, 0, ctx->stream>>>(nc, mu->mesh->h0, sigma, rho, muq, kd, beta, cm64, cm32,
+                                                              cb64, cb32, cv64, cv32);
   ctx->launches++;
   MF_CUDA_TRY(cudaGetLastError());
   return MF_OK;

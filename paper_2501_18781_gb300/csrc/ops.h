@@ -50,9 +50,10 @@ template <typename T> struct OseenArgs {
   const T* kd;      // [27][ncells]
   const T* nrm;     // [3][27][ncells]
   // Gauss-point coefficients with the weight and the powers of h folded in (Gauss-point-outer
-  // kernel): cm = w h^3 (sigma rho + Darcy), cc = w h^2 rho, cv = w h mu, each [27][ncells]
+  // kernel): cm = w h^3 (sigma rho + Darcy), cv = w h mu, each [27][ncells], and the convection
+  // velocity times w h^2 rho, cb [3][27][ncells]
   const T* cm;
-  const T* cc;
+  const T* cb;
   const T* cv;
 };
 
@@ -73,9 +74,10 @@ mf_status launch_scalar_qtables(mf_ctx* ctx, const mf_dofmap* m, int kind, const
 mf_status launch_oseen_qtables(mf_ctx* ctx, const mf_dofmap* mu, const double* phi, const double* beta, double rho_l,
                                double rho_g, double mu_l, double mu_g, int heaviside, double eps, double* rho64,
                                float* rho32, double* muq64, float* muq32, double* beta64, float* beta32);
-// folded coefficients cm, cc, cv of the Gauss-point-outer Oseen kernel from rho, mu (and kd)
+// folded coefficients cm, cv, cb of the Gauss-point-outer Oseen kernel from rho, mu, beta (and kd)
 mf_status launch_oseen_fold(mf_ctx* ctx, const mf_dofmap* mu, double sigma, const double* rho, const double* muq,
-                            const double* kd, double* cm64, float* cm32, double* cc64, float* cc32, double* cv64,
+                            const double* kd, const double* beta, double* cm64, float* cm32, double* cb64, float* cb32,
+                            double* cv64,
                             float* cv32);
 // melt-pool extension tables (three-phase rho/mu overwrite the two-phase ones; Darcy mass; normal)
 mf_status launch_oseen_ext_tables(mf_ctx* ctx, const mf_dofmap* mu, const mf_op_params& p, const double* phi,
@@ -140,7 +142,7 @@ struct mf_op {
   bool tc_ready = false;
   mf::DevBuf rho64, rho32, mu64, mu32;  // Oseen
   mf::DevBuf kd64, kd32, nrm64, nrm32;  // Oseen melt-pool extensions
-  mf::DevBuf cm64, cm32, cc64, cc32, cv64, cv32;  // Oseen folded Gauss-point coefficients
+  mf::DevBuf cm64, cm32, cb64, cb32, cv64, cv32;  // Oseen folded Gauss-point coefficients
   mf::DevBuf diag64;              // cached diagonal (fp64)
   mf::DevBuf blk64, pdiag64;      // Oseen block Jacobi
   bool tables_ready = false;
