@@ -361,8 +361,10 @@ mf_status mf_heat_step_gradient(mf_op* op, const mf_laser* laser, const mf_solve
                                 double box_half, double box_depth, double* J, double* dJ_dlaser,
                                 double* dJ_dkq, double* theta, double* lambda);
 
-/* Time the apply variants of this operator (cells per block, coefficient mode) and keep
- * the fastest; results are appended to cache_path (may be NULL).  Synchronising. */
+/* Time the apply variants of this operator (cells per block, coefficient mode; Oseen: the fp64
+ * loop order; Q3 Helmholtz: the CUDA-core or the tensor-core kernel for fp32 applies, which then
+ * also serves the fp32 applies inside solvers) and keep the fastest; results are appended to
+ * cache_path (may be NULL).  Synchronising. */
 mf_status mf_autotune(mf_op* op, const char* cache_path);
 
 /* Describe the variant the next apply will launch (host string, owned by the library). */

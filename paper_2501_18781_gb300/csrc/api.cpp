@@ -630,7 +630,8 @@ mf_status apply_impl(mf_op* op, const T* src, T* dst, int nrhs, int64_t ld, bool
   else if (prec != PREC_F64 && prec != PREC_DF64) prec = op->f64_prec;
   if (qk_degree(op)) {  // Q3 / Q4 Helmholtz: symmetric, fp64 or fp32 arithmetic (Q3 fp32: or the tensor cores)
     if constexpr (sizeof(T) == 4) {
-      if (prec == PREC_TC) return apply_tc(op, src, dst, nrhs, ld);
+      if (prec == PREC_TC || (prec == PREC_F32 && op->qk_f32_tc))
+        return apply_tc(op, src, dst, nrhs, ld);
     }
     if (prec != PREC_F64 && prec != PREC_F32) return fail(MF_EUNSUPPORTED, "degrees 3 and 4: fp64 or fp32 applies");
     MF_TRY(check_fields(op));

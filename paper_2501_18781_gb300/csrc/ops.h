@@ -140,6 +140,7 @@ struct mf_op {
   mf::DevBuf qmass64, qmass32;    // [27][ncells] heat value term rho_cp,q / dt
   mf::DevBuf qcoef_tc;            // Q3 tensor-core apply: fp32 coefficients [tile of 128 cells][q][row]
   bool tc_ready = false;
+  int qk_f32_tc = 0;              // Q3: plain fp32 applies run on the tensor cores (autotuned)
   mf::DevBuf rho64, rho32, mu64, mu32;  // Oseen
   mf::DevBuf kd64, kd32, nrm64, nrm32;  // Oseen melt-pool extensions
   mf::DevBuf cm64, cm32, cb64, cb32, cv64, cv32;  // Oseen folded Gauss-point coefficients

@@ -894,8 +894,46 @@ mf_status mf_autotune(mf_op* op, const char* cache_path) {
     MF_TRY(check_fields(op));
     mf_ctx* c = op->ctx;
     const int64_t n = op->n;
-    if (qk_degree(op)) {  // Q3 / Q4: one kernel variant per precision, nothing to choose
-      op->tune_record = "{\"variants\": \"helmholtz_q" + std::to_string(qk_degree(op)) + ": one\"}";
+    if (qk_degree(op) == 4) {  // Q4: one kernel variant per precision, nothing to choose
+      op->tune_record = "{\"variants\": \"helmholtz_q4: one\"}";
+      return MF_OK;
+    }
+    if (qk_degree(op) == 3) {
+      // fp32 applies: the sum-factorised CUDA-core kernel or the dense tensor-core kernel
+      op->qk_f32_tc = 0;
+      DevBuf s, d;
+      MF_TRY(s.alloc(sizeof(float) * n));
+      MF_TRY(d.alloc(sizeof(float) * n));
+      MF_CUDA_TRY(cudaMemsetAsync(s.p, 0, sizeof(float) * n, c->stream));
+      cudaEvent_t a0, a1;
+      cudaEventCreate(&a0);
+      cudaEventCreate(&a1);
+      double ms[2] = {1e30, 1e30};
+      for (int v = 0; v < 2; ++v) {
+        for (int rep = 0; rep < 4; ++rep) {
+          cudaEventRecord(a0, c->stream);
+          MF_TRY(apply_impl<float>(op, s.as<float>(), d.as<float>(), 1, n, false, v ? PREC_TC : PREC_F32));
+          cudaEventRecord(a1, c->stream);
+          MF_CUDA_TRY(cudaEventSynchronize(a1));
+          float t;
+          cudaEventElapsedTime(&t, a0, a1);
+          if (rep > 0) ms[v] = std::min(ms[v], double(t));
+        }
+      }
+      cudaEventDestroy(a0);
+      cudaEventDestroy(a1);
+      op->qk_f32_tc = ms[1] < ms[0] ? 1 : 0;
+      char buf[256];
+      std::snprintf(buf, sizeof buf, "{\"kind\": %d, \"n\": %lld, \"q3_f32_cuda_core_ms\": %.6g, \"q3_f32_tensor_core_ms\": %.6g}",
+                    op->p.kind, (long long)n, ms[0], ms[1]);
+      op->tune_record = buf;
+      if (cache_path) {
+        FILE* fp = std::fopen(cache_path, "a");
+        if (fp) {
+          std::fprintf(fp, "%s\n", buf);
+          std::fclose(fp);
+        }
+      }
       return MF_OK;
     }
     if (op->p.kind == MF_OP_OSEEN) {

@@ -149,3 +149,15 @@ def test_tensor_core_inner_arithmetic_needs_q3_and_defect_correction(ctx):
     with pytest.raises(MFError):
         op4.solve(torch.ones(op4.n, dtype=torch.float64, device="cuda"), solver="defect_correction",
                   precond="chebyshev", inner_arith="tc")
+
+
+def test_q3_autotune_picks_an_fp32_kernel_and_keeps_parity(ctx):
+    """After mf_autotune the plain fp32 apply runs whichever Q3 kernel was faster; either passes."""
+    dm, A, op = _problem(ctx, 3, 6)
+    op.autotune()
+    u = syn.uniform_pm1(5, dm.n_dofs).astype(np.float32).astype(np.float64)
+    v = op.apply(torch.tensor(u, device="cuda").float()).cpu().double().numpy()
+    ok, worst = componentwise_ok(v, A @ u, abs(A) @ np.abs(u), 5e-5)
+    assert ok, worst
+    assert op.variant in ("helmholtz_q3/uniform/f32/tabulated/line-per-thread",
+                          "helmholtz_q3/uniform/f32/tcgen05-bf16x3/dense")
