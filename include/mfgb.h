@@ -45,7 +45,7 @@ typedef int mf_status;
 #define MF_ECUDA (-3)         /* a CUDA runtime call failed */
 #define MF_ENOTCONV (-4)      /* a solver stopped at maxit above its tolerance */
 #define MF_ETIMEOUT (-5)      /* a device-side bounded wait ran out */
-#define MF_EUNSUPPORTED (-6)  /* valid request that this build does not implement */
+#define MF_EUNSUPPORTED (-6)  /* valid request that the library does not implement */
 
 /* MF_DF64: fp64 vectors, cell arithmetic in double-float (pairs of fp32 with error-free
  * products and sums, 48-bit significand) on the fp32 pipes, which GB300 runs at ~62x its fp64
