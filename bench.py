@@ -368,6 +368,36 @@ def cpu_oracle_apply(n_sample, budget_s=8.0):
     return A.shape[0] * reps / dt / 1e9, A.shape[0], reps, dt
 
 
+def cpu_oracle_workloads():
+    """The oracle as it stands on the host (one core, scipy CSR): assembly, SpMV and Jacobi-CG to
+    1e-10 on the Helmholtz 16^3 workload (35,937 DoFs) -- the CPU side of the solve comparison."""
+    import numpy as np
+    import synthetic as syn
+    from oracle import assemble as asm
+    from oracle import krylov
+    from oracle import mesh as omesh
+    wl = syn.HELMHOLTZ_SPHERE
+    p = wl.params
+    t0 = time.perf_counter()
+    dm = omesh.uniform_dofmap(wl.n, wl.lo, wl.hi, 2)
+    phi = syn.initial_level_set(syn.sphere_distance(*dm.dof_coords().T), wl.eps)
+    A = asm.helmholtz_matrix(dm, phi, p["mass"], p["a_liquid"], p["a_gas"])
+    t_asm = time.perf_counter() - t0
+    b = syn.uniform_pm1(1, dm.n_dofs)
+    A @ b
+    reps, t0 = 0, time.perf_counter()
+    while time.perf_counter() - t0 < 2.0:
+        A @ b
+        reps += 1
+    t_spmv = (time.perf_counter() - t0) / reps
+    t0 = time.perf_counter()
+    _, its, res = krylov.cg(lambda v: A @ v, b, krylov.jacobi(A.diagonal()), tol=1e-10)
+    t_cg = time.perf_counter() - t0
+    return {"workload": wl.name, "n_dofs": dm.n_dofs, "cores": 1, "assembly_seconds": t_asm,
+            "spmv_gdofs": dm.n_dofs / t_spmv / 1e9, "cg_jacobi_seconds": t_cg, "cg_iterations": its,
+            "rel_residual": res}
+
+
 def reference_arm(args, rank, world):
     out = {"impl": "reference", "metric": METRIC, "unit": "GDoF/s", "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -734,6 +764,8 @@ def main():
     if args.suite and rank == 0:
         out["workloads"] = workload_suite(ctx, flush)
         out["workloads"]["oseen_meltpool"] = meltpool_oseen(ctx, args.n, flush)
+    if args.suite and rank == 0 and world == 1:
+        out.setdefault("workloads", {})["cpu_oracle_helmholtz_16"] = cpu_oracle_workloads()
     if (args.suite or args.qk) and rank == 0:
         out.setdefault("workloads", {})["helmholtz_qk"] = helmholtz_qk(ctx, flush)
     if (args.suite or args.meltpool_step) and rank == 0:
