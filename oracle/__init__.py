@@ -24,5 +24,12 @@ element integrals with the same Gauss rule.  So the oracle *is* that definition:
                Chebyshev and Lanczos (Appendix B: CG for symmetric and GMRES
                for nonsymmetric systems);
 * ``heat``     one implicit heat step, the box objective and its adjoint
-               gradients with respect to the laser parameters and k_q.
+               gradients with respect to the laser parameters and k_q;
+* ``interface`` the interface source terms of Section 2.4 (smoothed delta,
+               mass flux, dilation, cooling, hybrid recoil) as load vectors;
+* ``patch``    single rows of full-size operators from 2 x 2 x 2-cell patches
+               (parity of the benchmark-size applies);
+* ``step``     one step of Algorithm algo:meltpooldg (predictors, level-set
+               advection and reinitialisation, heat, Navier-Stokes) by direct
+               sparse solves, in stage functions.
 """
