@@ -212,11 +212,15 @@ mf_status mf_apply_tc(mf_op* op, const float* src, float* dst, int nrhs, int64_t
  *   which = MF_COUPLING_GRAD (0): dst = B^T src; src = a pressure vector (n_p values), dst =
  *           the three velocity blocks (3 n_u values), 0 in Dirichlet rows;
  *   which = MF_COUPLING_DIV (1): dst = B src; src = the three velocity blocks (Dirichlet values
- *           read as 0), dst = a pressure vector.
+ *           read as 0), dst = a pressure vector;
+ *   which = MF_COUPLING_SCHUR (2): dst = B D^-1 B^T src, pressure to pressure, with D the 3 x 3
+ *           nodal blocks of A_uu (the Schur complement approximation that MF_PREC_BLOCK_TRIANGULAR
+ *           inverts; its fp32 form is the preconditioner's own node-by-node kernel).  Needs the
+ *           operator's fields; allocates work vectors and returns after the result is written.
  * These are the blocks of A [0; p] and A [u; 0] that mf_apply computes together with A_uu.
  * Device vectors of dtype MF_F64 or MF_F32; dst is overwritten.  MF_EINVAL for other
- * operator kinds or an unknown `which`.  Asynchronous. */
-enum { MF_COUPLING_GRAD = 0, MF_COUPLING_DIV = 1 };
+ * operator kinds or an unknown `which`.  Asynchronous for which 0 and 1. */
+enum { MF_COUPLING_GRAD = 0, MF_COUPLING_DIV = 1, MF_COUPLING_SCHUR = 2 };
 mf_status mf_oseen_coupling(mf_op* op, int which, const void* src, void* dst, int dtype);
 
 /* dst = diag(A) (Dirichlet rows 1).  Asynchronous. */
@@ -247,7 +251,8 @@ typedef struct {
   int cheby_degree;    /* operator applications per Chebyshev preconditioner call */
   int maxit;           /* iteration cap (outer steps for defect correction) */
   int inner_maxit;     /* defect correction: inner CG cap */
-  int use_graph;       /* capture the CG iteration body in a CUDA graph */
+  int use_graph;       /* replay recorded CUDA graphs: the CG iteration body, and each call of
+                          MF_PREC_BLOCK_TRIANGULAR (recorded at its second call) */
   double tol;          /* stop when ||b - A x||_2 <= tol ||b||_2 (x0 = 0) */
   double inner_tol;    /* defect correction: inner relative tolerance */
   double cheby_ratio;  /* Chebyshev interval [lambda_max/ratio, 1.1 lambda_max] */
@@ -270,6 +275,10 @@ typedef struct {
   double rel_residual;     /* final ||b - A x|| / ||b|| in fp64 */
   double lambda_max;       /* Chebyshev estimate used (0 if none) */
   double seconds;          /* wall time of the call */
+  int inner_steps;         /* MF_PREC_BLOCK_TRIANGULAR: Schur CG steps taken before its stopping
+                              test held, summed over the preconditioner calls (the steps after
+                              it leave the iterate unchanged) */
+  int reserved;
 } mf_solve_info;
 
 /* Inner products of the Krylov solvers (Appendix B: CG / GMRES): out[k] = sum_i x[k ld + i]

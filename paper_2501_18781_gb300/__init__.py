@@ -241,14 +241,16 @@ class Operator:
         if st not in (_lib.MF_OK, _lib.MF_ENOTCONV):
             check(st)
         return x, {"status": st, "iterations": info.iterations, "outer_iterations": info.outer_iterations,
-                   "rel_residual": info.rel_residual, "lambda_max": info.lambda_max, "seconds": info.seconds}
+                   "rel_residual": info.rel_residual, "lambda_max": info.lambda_max, "seconds": info.seconds,
+                   "inner_steps": info.inner_steps}
 
     def coupling(self, which, src):
         """Oseen coupling blocks alone: which="grad" gives B^T p (velocity blocks) from a pressure
-        vector, which="div" gives B u (pressure block) from the velocity blocks."""
+        vector, which="div" gives B u (pressure block) from the velocity blocks, which="schur"
+        gives B D^-1 B^T p (D: the 3 x 3 nodal blocks of A_uu) from a pressure vector."""
         import torch
         nu, npr = self.maps[0].n_dofs, self.maps[1].n_dofs
-        w = {"grad": 0, "div": 1}[which]
+        w = {"grad": 0, "div": 1, "schur": 2}[which]
         src = src.contiguous()
         dst = torch.empty(3 * nu if w == 0 else npr, dtype=src.dtype, device=src.device)
         check(_lib.load().mf_oseen_coupling(self.h, w, _ptr(src), _ptr(dst), _dtype_code(src)))

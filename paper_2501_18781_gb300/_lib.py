@@ -42,7 +42,8 @@ class SolverParams(C.Structure):
 
 class SolveInfo(C.Structure):
     _fields_ = [("iterations", C.c_int), ("outer_iterations", C.c_int), ("rel_residual", C.c_double),
-                ("lambda_max", C.c_double), ("seconds", C.c_double)]
+                ("lambda_max", C.c_double), ("seconds", C.c_double), ("inner_steps", C.c_int),
+                ("reserved", C.c_int)]
 
 
 class Evaporation(C.Structure):

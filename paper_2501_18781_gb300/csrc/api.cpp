@@ -56,6 +56,11 @@ mf_status mf_context_create(int device, void* cuda_stream, mf_ctx** out) {
   cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, device);
   mf_status st = c->scratch.alloc(kScratchDoubles * sizeof(double));
   if (st == MF_OK) st = c->scalars.alloc(sizeof(double) * kScalarsTotal);
+  if (st == MF_OK) st = c->counters.alloc(sizeof(unsigned) * 64);
+  // zeroed on the context's stream (a non-blocking stream is not ordered after the legacy one)
+  if (st == MF_OK && (cudaMemsetAsync(c->counters.p, 0, sizeof(unsigned) * 64, c->stream) != cudaSuccess ||
+                      cudaStreamSynchronize(c->stream) != cudaSuccess))
+    st = fail(MF_ECUDA, "zeroing the reduction counters failed");
   if (st == MF_OK && cudaMallocHost(&c->host_scalars, sizeof(double) * kScalarsTotal) != cudaSuccess)
     st = fail(MF_ENOMEM, "pinned host allocation failed");
   if (st != MF_OK) {
@@ -694,11 +699,33 @@ mf_status apply_impl(mf_op* op, const T* src, T* dst, int nrhs, int64_t ld, bool
 }
 template mf_status apply_impl<double>(mf_op*, const double*, double*, int, int64_t, bool, int);
 
-// B^T p (which 0, into the three velocity blocks) or B u (which 1, into the pressure block)
+mf_status diag64(mf_op* op, double** out);
+
+// B^T p (which 0, into the three velocity blocks), B u (which 1, into the pressure block) or the
+// approximate Schur complement B D^-1 B^T p (which 2, pressure to pressure; D the 3 x 3 nodal
+// blocks of A_uu; work vectors allocated per call)
 template <typename T> mf_status oseen_coupling(mf_op* op, int which, const T* src, T* dst) {
   if (op->p.kind != MF_OP_OSEEN) return fail(MF_EINVAL, "coupling blocks exist for the Oseen operator only");
-  if (which != 0 && which != 1) return fail(MF_EINVAL, "which must be 0 (B^T p) or 1 (B u)");
+  if (which < 0 || which > 2) return fail(MF_EINVAL, "which must be 0 (B^T p), 1 (B u) or 2 (B D^-1 B^T p)");
   const int64_t nu = op->map[0]->n_dofs, np = op->map[1]->n_dofs;
+  if (which == 2) {
+    MF_TRY(check_fields(op));
+    MF_TRY(diag64(op, nullptr));
+    DevBuf ua, ub;
+    MF_TRY(ub.alloc(sizeof(T) * 3 * size_t(nu)));
+    if constexpr (sizeof(T) == 4) {
+      MF_TRY(ua.alloc(sizeof(float) * 9 * size_t(nu)));  // the fp32 block inverses, entry-major
+      MF_TRY(blocks_soa32(op->ctx, nu, op->blk64.as<double>(), ua.as<float>()));
+      MF_TRY(launch_oseen_bt_dinv_f32(op->ctx, op->map[0], src, ua.as<float>(), ub.as<float>()));
+    } else {
+      MF_TRY(ua.alloc(sizeof(T) * 3 * size_t(nu)));
+      MF_TRY(oseen_coupling<T>(op, 0, src, ua.as<T>()));
+      MF_TRY(block_jacobi<T>(op->ctx, nu, 0, op->blk64.as<double>(), nullptr, ua.as<T>(), ub.as<T>()));
+    }
+    MF_TRY(oseen_coupling<T>(op, 1, ub.as<T>(), dst));
+    MF_CUDA_TRY(cudaStreamSynchronize(op->ctx->stream));  // before the work vectors are freed
+    return MF_OK;
+  }
   MF_CUDA_TRY(cudaMemsetAsync(dst, 0, sizeof(T) * size_t(which == 0 ? 3 * nu : np), op->ctx->stream));
   if constexpr (sizeof(T) == 4) return launch_oseen_coupling_f32(op->ctx, op->map[0], which, src, dst);
   else return launch_oseen_coupling_f64(op->ctx, op->map[0], which, src, dst);

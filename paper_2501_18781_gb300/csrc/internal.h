@@ -80,6 +80,7 @@ struct mf_ctx {
   int64_t launches = 0;
   int sm_count = 0;
   mf::DevBuf scratch;   // reduction partials (fixed size, allocated with the context)
+  mf::DevBuf counters;  // 64 arrival counters of the reductions (zero between launches)
   mf::DevBuf scalars;   // device scalars of the solvers
   double* host_scalars = nullptr;  // pinned
   // CUDA graphs are captured on a private stream (the legacy default stream cannot be

@@ -28,7 +28,7 @@ template <typename T> ScalarArgs<T> scalar_args(const mf_op* op, const T* src, T
 template <typename T> mf_status oseen_coupling(mf_op* op, int which, const T* src, T* dst);
 // device-side stopping test and Givens kernels of the inner solves (solver_kernels.cu)
 mf_status dev_cg_tol_init(mf_ctx* c, double* S, double tol2);
-mf_status dev_cg_tol_check(mf_ctx* c, double* S);
+mf_status dev_cg_tol_check(mf_ctx* c, double* S, double* steps);
 mf_status dev_gmres_begin(mf_ctx* c, const double* nrm2, double* G, int m);
 mf_status dev_gmres_column(mf_ctx* c, const double* h, double* G, int m, int j);
 mf_status dev_gmres_solve(mf_ctx* c, const double* G, int m, int j, double* y);
@@ -54,6 +54,40 @@ template <typename T> struct Vec {
 mf_status sync_copy(mf_ctx* c, double* host, const double* dev, size_t n) {
   MF_CUDA_TRY(cudaMemcpyAsync(host, dev, n * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
   MF_CUDA_TRY(cudaStreamSynchronize(c->stream));
+  return MF_OK;
+}
+
+// Krylov basis vectors are stored this many elements apart: n rounded up to 64, so that every
+// vector starts on a 256-byte boundary and the CGS2 kernels move 16-byte words.
+inline int64_t basis_stride(int64_t n) { return (n + 63) / 64 * 64; }
+
+// Records what fn launches on the context's stream into an executable graph.  The capture runs
+// on a private stream (nothing executes during a capture, so the work queued on the context's
+// stream needs no fence); *kernels = the kernel launches the graph holds, which each replay adds
+// to the context's launch count.
+template <typename F> mf_status capture_graph(mf_ctx* c, F&& fn, cudaGraphExec_t* exec, int64_t* kernels) {
+  if (!c->capture_stream) {
+    MF_CUDA_TRY(cudaStreamCreateWithFlags(&c->capture_stream, cudaStreamNonBlocking));
+    MF_CUDA_TRY(cudaEventCreateWithFlags(&c->fence, cudaEventDisableTiming));
+  }
+  cudaGraph_t g;
+  cudaStream_t orig = c->stream;
+  const int64_t before = c->launches;
+  c->stream = c->capture_stream;
+  MF_CUDA_TRY(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
+  mf_status st = fn();
+  cudaError_t e = cudaStreamEndCapture(c->stream, &g);
+  c->stream = orig;
+  *kernels = c->launches - before;
+  c->launches = before;
+  if (st != MF_OK) {
+    if (e == cudaSuccess) cudaGraphDestroy(g);
+    return st;
+  }
+  if (e != cudaSuccess) return fail(MF_ECUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+  e = cudaGraphInstantiate(exec, g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) return fail(MF_ECUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
   return MF_OK;
 }
 
@@ -125,7 +159,19 @@ struct OseenBlockTri {
   int ku = 10, smax = 30;
   double stol = 0.1;
   Vec<float> blk32, ua, ub, pinv32, xp, rp, zp, pp, sp, V, t, w;
+  int64_t ldv = 0;  // stride of the basis vectors in V
   Vec<double> gst, y;
+  // graph replay: a call launches the same sequence every time (several hundred small kernels),
+  // so it is recorded once, between fixed input and output vectors, and replayed
+  bool use_graph = false;
+  int calls = 0;
+  cudaGraphExec_t exec = nullptr;
+  int64_t graph_kernels = 0;
+  Vec<double> rin, zout;
+
+  ~OseenBlockTri() {
+    if (exec) cudaGraphExecDestroy(exec);
+  }
 
   mf_status setup(mf_op* o, int velocity_steps, int schur_maxit, double schur_tol) {
     op = o;
@@ -140,24 +186,28 @@ struct OseenBlockTri {
     stol = schur_tol > 0 ? schur_tol : 0.1;
     MF_TRY(diag64(op, nullptr));  // 3x3 block inverses and the pressure scaling
     MF_TRY(blk32.alloc(9 * nu));
-    MF_TRY((convert<double, float>(c, 9 * nu, op->blk64.as<double>(), blk32.p)));
+    MF_TRY(blocks_soa32(c, nu, op->blk64.as<double>(), blk32.p));
     MF_TRY(ua.alloc(nu3));
     MF_TRY(ub.alloc(nu3));
     for (Vec<float>* v : {&pinv32, &xp, &rp, &zp, &pp, &sp}) MF_TRY(v->alloc(np));
     MF_TRY((convert<double, float>(c, np, op->pdiag64.as<double>(), pinv32.p)));
-    MF_TRY(V.alloc(n * (ku + 1)));
+    ldv = basis_stride(n);
+    MF_TRY(V.alloc(ldv * (ku + 1)));
     MF_TRY(t.alloc(n));
     MF_TRY(w.alloc(n));
     MF_CUDA_TRY(cudaMemsetAsync(t.p, 0, sizeof(float) * n, c->stream));  // its pressure block stays 0
+    MF_CUDA_TRY(cudaMemsetAsync(schur_steps(), 0, sizeof(double), c->stream));
     MF_TRY(gst.alloc(ku * ku + 3 * ku + 2));
     MF_TRY(y.alloc(ku));
     return MF_OK;
   }
 
-  // out = S~ p = B D^-1 B^T p
+  // device counter of the Schur CG steps taken while still iterating, over all calls
+  double* schur_steps() { return op->ctx->scalars.as<double>() + kScalarsTri + 144; }
+
+  // out = S~ p = B D^-1 B^T p (D^-1 B^T p node by node, then B cell by cell)
   mf_status schur(const float* p, float* out) {
-    MF_TRY(oseen_coupling<float>(op, 0, p, ua.p));
-    MF_TRY(block_jacobi_u32(op->ctx, nu, blk32.p, ua.p, ub.p));
+    MF_TRY(launch_oseen_bt_dinv_f32(op->ctx, op->map[0], p, blk32.p, ub.p));
     return oseen_coupling<float>(op, 1, ub.p, out);
   }
 
@@ -176,7 +226,7 @@ struct OseenBlockTri {
       MF_TRY(schur(pp.p, sp.p));
       MF_TRY(cg_alpha<float>(c, pp.p, sp.p, np, np, 1, S));
       MF_TRY(cg_update_xr<float>(c, np, np, 1, xp.p, rp.p, pp.p, sp.p, pinv32.p, zp.p, 1, S));
-      MF_TRY(dev_cg_tol_check(c, S));
+      MF_TRY(dev_cg_tol_check(c, S, schur_steps()));
       MF_TRY(cg_update_p<float>(c, np, np, 1, zp.p, pp.p, S));
     }
     return MF_OK;
@@ -195,23 +245,40 @@ struct OseenBlockTri {
     MF_CUDA_TRY(cudaMemcpyAsync(V.p, w.p, sizeof(float) * n, cudaMemcpyDeviceToDevice, c->stream));
     MF_TRY(dev_scale<float>(c, nu3, inv, V.p));
     for (int j = 0; j < m; ++j) {
-      float* vj1 = V.p + (j + 1) * n;
-      MF_TRY(block_jacobi_u32(c, nu, blk32.p, V.p + j * n, t.p));
+      float* vj1 = V.p + (j + 1) * ldv;
+      MF_TRY(block_jacobi_u32(c, nu, blk32.p, V.p + j * ldv, t.p));
       MF_TRY(apply_impl<float>(op, t.p, vj1, 1, n, false));
       MF_CUDA_TRY(cudaMemsetAsync(vj1 + nu3, 0, sizeof(float) * np, c->stream));
-      MF_TRY(multidot<float>(c, V.p, n, j + 1, vj1, nu3, ds));
-      MF_TRY(multiaxpy<float>(c, V.p, n, j + 1, ds, -1.0, vj1, nu3));
-      MF_TRY(multidot<float>(c, V.p, n, j + 1, vj1, nu3, ds + (m + 1)));
-      MF_TRY(multiaxpy<float>(c, V.p, n, j + 1, ds + (m + 1), -1.0, vj1, nu3));
+      MF_TRY(multidot<float>(c, V.p, ldv, j + 1, vj1, nu3, ds));
+      MF_TRY(multiaxpy<float>(c, V.p, ldv, j + 1, ds, -1.0, vj1, nu3));
+      MF_TRY(multidot<float>(c, V.p, ldv, j + 1, vj1, nu3, ds + (m + 1)));
+      MF_TRY(multiaxpy<float>(c, V.p, ldv, j + 1, ds + (m + 1), -1.0, vj1, nu3));
       MF_TRY((dot<float, float>(c, vj1, vj1, nu3, ds + 2 * (m + 1))));
       MF_TRY(dev_gmres_column(c, ds, G, m, j));
       MF_TRY(dev_scale<float>(c, nu3, inv, vj1));
     }
     MF_TRY(dev_gmres_solve(c, G, m, m, y.p));
     MF_CUDA_TRY(cudaMemsetAsync(w.p, 0, sizeof(float) * nu3, c->stream));
-    MF_TRY(multiaxpy<float>(c, V.p, n, m, y.p, 1.0, w.p, nu3));
+    MF_TRY(multiaxpy<float>(c, V.p, ldv, m, y.p, 1.0, w.p, nu3));
     MF_TRY(block_jacobi_u32(c, nu, blk32.p, w.p, t.p));
     return convert<float, double>(c, nu3, t.p, z);
+  }
+
+  // z = P^-1 r through the recorded graph.  The first call runs directly, which also leaves every
+  // lazily built table of the operator in place before the capture.
+  mf_status apply_replayed(const double* r, double* z) {
+    mf_ctx* c = op->ctx;
+    if (!use_graph || calls++ == 0) return apply(r, z);
+    if (!exec) {
+      MF_TRY(rin.alloc(n));
+      MF_TRY(zout.alloc(n));
+      MF_TRY(capture_graph(c, [&]() { return apply(rin.p, zout.p); }, &exec, &graph_kernels));
+    }
+    MF_CUDA_TRY(cudaMemcpyAsync(rin.p, r, sizeof(double) * n, cudaMemcpyDeviceToDevice, c->stream));
+    MF_CUDA_TRY(cudaGraphLaunch(exec, c->stream));
+    c->launches += graph_kernels;
+    MF_CUDA_TRY(cudaMemcpyAsync(z, zout.p, sizeof(double) * n, cudaMemcpyDeviceToDevice, c->stream));
+    return MF_OK;
   }
 
   // z = P^-1 r (fp64 vectors of length n)
@@ -240,6 +307,7 @@ template <typename T> struct Prec {
   // block-triangular parameters (set before setup) and state
   int tri_velocity_steps = 10, tri_schur_maxit = 30;
   double tri_schur_tol = 0.1;
+  bool tri_graph = false;
   std::unique_ptr<OseenBlockTri> tri;
 
   mf_status setup(mf_op* o, int k, int deg, double ratio, int lanczos_steps, int nr) {
@@ -258,6 +326,7 @@ template <typename T> struct Prec {
       if (!std::is_same<T, double>::value || nrhs != 1)
         return fail(MF_EUNSUPPORTED, "the block-triangular preconditioner runs inside fp64 GMRES");
       tri = std::make_unique<OseenBlockTri>();
+      tri->use_graph = tri_graph;
       return tri->setup(op, tri_velocity_steps, tri_schur_maxit, tri_schur_tol);
     }
     if (op->p.kind == MF_OP_OSEEN) return fail(MF_EUNSUPPORTED, "Oseen: use block Jacobi or block triangular");
@@ -362,7 +431,7 @@ template <typename T> struct Prec {
         return MF_OK;
       }
       case MF_PREC_BLOCK_TRIANGULAR:
-        if constexpr (std::is_same<T, double>::value) return tri->apply(r, z);
+        if constexpr (std::is_same<T, double>::value) return tri->apply_replayed(r, z);
         return fail(MF_EUNSUPPORTED, "block-triangular preconditioner in fp32");
       case MF_PREC_CHEBYSHEV: {
         const double theta = 0.5 * (lmax + lmin), delta = 0.5 * (lmax - lmin), sigma = theta / delta;
@@ -416,6 +485,7 @@ template <typename T> struct CG {
   int check_every = 1;
   bool use_graph = false;
   cudaGraphExec_t exec = nullptr;
+  int64_t graph_kernels = 0;
 
   ~CG() {
     if (exec) cudaGraphExecDestroy(exec);
@@ -486,30 +556,15 @@ template <typename T> struct CG {
       }
     }
     int it = 0;
-    if (use_graph && !exec) {
-      cudaGraph_t g;
-      if (!c->capture_stream) {
-        MF_CUDA_TRY(cudaStreamCreateWithFlags(&c->capture_stream, cudaStreamNonBlocking));
-        MF_CUDA_TRY(cudaEventCreateWithFlags(&c->fence, cudaEventDisableTiming));
-      }
-      // capture on the private stream; nothing runs during capture, so no fence is needed here
-      cudaStream_t orig = c->stream;
-      c->stream = c->capture_stream;
-      MF_CUDA_TRY(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
-      mf_status st = MF_OK;
-      for (int k = 0; k < check_every && st == MF_OK; ++k) st = iteration(x, S);
-      cudaError_t e = cudaStreamEndCapture(c->stream, &g);
-      c->stream = orig;
-      if (st != MF_OK) return st;
-      if (e != cudaSuccess) return fail(MF_ECUDA, std::string("graph capture: ") + cudaGetErrorString(e));
-      e = cudaGraphInstantiate(&exec, g, 0);
-      cudaGraphDestroy(g);
-      if (e != cudaSuccess) return fail(MF_ECUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
-    }
+    if (use_graph && !exec)
+      MF_TRY(capture_graph(c, [&]() {
+        for (int k = 0; k < check_every; ++k) MF_TRY(iteration(x, S));
+        return MF_OK;
+      }, &exec, &graph_kernels));
     while (ndone < nrhs && it < maxit) {
       if (exec) {
         MF_CUDA_TRY(cudaGraphLaunch(exec, c->stream));
-        c->launches++;
+        c->launches += graph_kernels;
       } else {
         for (int k = 0; k < check_every; ++k) MF_TRY(iteration(x, S));
       }
@@ -569,10 +624,11 @@ mf_status gmres(mf_op* op, Prec<double>& P, const double* b, double* x, int m, d
   const bool flexible = P.kind == MF_PREC_BLOCK_TRIANGULAR;
   if (flexible && transpose) return fail(MF_EUNSUPPORTED, "block-triangular preconditioner: forward operator only");
   Vec<double> V, t, r, Z;
-  MF_TRY(V.alloc(n * (m + 1)));
+  const int64_t ldv = basis_stride(n);
+  MF_TRY(V.alloc(ldv * (m + 1)));
   MF_TRY(t.alloc(n));
   MF_TRY(r.alloc(n));
-  if (flexible) MF_TRY(Z.alloc(n * m));
+  if (flexible) MF_TRY(Z.alloc(ldv * m));
   double* dh = c->scalars.as<double>() + kScalarsGmres;  // room for 2 (m+1) <= 128 values
   if (2 * (m + 1) > 128) return fail(MF_EINVAL, "GMRES restart too long (max 63)");
   double* hh = c->host_scalars + kScalarsGmres;
@@ -596,14 +652,14 @@ mf_status gmres(mf_op* op, Prec<double>& P, const double* b, double* x, int m, d
     int j = 0;
     bool conv = false;
     for (; j < m && it < maxit; ++j) {
-      double* w = V.p + (j + 1) * n;
-      double* zj = flexible ? Z.p + j * n : t.p;
-      MF_TRY(P.apply(V.p + j * n, zj));
+      double* w = V.p + (j + 1) * ldv;
+      double* zj = flexible ? Z.p + j * ldv : t.p;
+      MF_TRY(P.apply(V.p + j * ldv, zj));
       MF_TRY(apply_impl<double>(op, zj, w, 1, n, transpose));
-      MF_TRY(multidot(c, V.p, n, j + 1, w, n, dh));
-      MF_TRY(multiaxpy(c, V.p, n, j + 1, dh, -1.0, w, n));
-      MF_TRY(multidot(c, V.p, n, j + 1, w, n, dh + (m + 1)));
-      MF_TRY(multiaxpy(c, V.p, n, j + 1, dh + (m + 1), -1.0, w, n));
+      MF_TRY(multidot(c, V.p, ldv, j + 1, w, n, dh));
+      MF_TRY(multiaxpy(c, V.p, ldv, j + 1, dh, -1.0, w, n));
+      MF_TRY(multidot(c, V.p, ldv, j + 1, w, n, dh + (m + 1)));
+      MF_TRY(multiaxpy(c, V.p, ldv, j + 1, dh + (m + 1), -1.0, w, n));
       MF_TRY(norm2_sq(c, w, n, dh + 2 * (m + 1) - 1));
       MF_TRY(sync_copy(c, hh, dh, 2 * (m + 1)));
       for (int i = 0; i <= j; ++i) H[i * m + j] = hh[i] + hh[(m + 1) + i];
@@ -623,10 +679,10 @@ mf_status gmres(mf_op* op, Prec<double>& P, const double* b, double* x, int m, d
     for (int i = 0; i < j; ++i) hh[i] = y[i];
     MF_CUDA_TRY(cudaMemcpyAsync(dh, hh, sizeof(double) * j, cudaMemcpyHostToDevice, c->stream));
     if (flexible) {
-      MF_TRY(multiaxpy(c, Z.p, n, j, dh, 1.0, x, n));
+      MF_TRY(multiaxpy(c, Z.p, ldv, j, dh, 1.0, x, n));
     } else {
       MF_CUDA_TRY(cudaMemsetAsync(r.p, 0, sizeof(double) * n, c->stream));
-      MF_TRY(multiaxpy(c, V.p, n, j, dh, 1.0, r.p, n));
+      MF_TRY(multiaxpy(c, V.p, ldv, j, dh, 1.0, r.p, n));
       MF_TRY(P.apply(r.p, t.p));
       MF_TRY(axpby<double, double>(c, n, 1.0, t.p, 1.0, x));
     }
@@ -722,6 +778,7 @@ mf_status solve_impl(mf_op* op, const mf_solver_params* sp, const double* b, dou
     P.tri_velocity_steps = sp->velocity_steps;
     P.tri_schur_maxit = sp->schur_maxit;
     P.tri_schur_tol = sp->schur_tol;
+    P.tri_graph = sp->use_graph != 0;
     MF_TRY(P.setup(op, sp->precond, deg, ratio, lsteps, 1));
     inf.lambda_max = P.lmax;
     const int m = sp->restart > 0 ? sp->restart : 50;
@@ -734,6 +791,10 @@ mf_status solve_impl(mf_op* op, const mf_solver_params* sp, const double* b, dou
       if (s2 == MF_ENOTCONV) st = s2;
       inf.iterations += its;
       rel[k] = rr;
+    }
+    if (P.tri) {
+      MF_TRY(sync_copy(c, c->host_scalars + kScalarsTri + 144, P.tri->schur_steps(), 1));
+      inf.inner_steps = int(c->host_scalars[kScalarsTri + 144]);
     }
   } else if (sp->solver == MF_SOLVER_DEFECT_CORRECTION) {
     if (sp->inner_dtype != MF_F32) return fail(MF_EUNSUPPORTED, "inner precision must be MF_F32");

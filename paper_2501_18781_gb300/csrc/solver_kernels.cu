@@ -46,7 +46,9 @@ __global__ void k_cg_tol_init(double* S, double tol2) {
   S[S_ACTIVE] = S[S_RR] > 0.0 ? 1.0 : 0.0;
   S[7] = tol2 * S[S_RR];
 }
-__global__ void k_cg_tol_check(double* S) {
+// steps: counts the steps that ran while the CG was still iterating (may be NULL)
+__global__ void k_cg_tol_check(double* S, double* steps) {
+  if (steps && S[S_ACTIVE] != 0.0) steps[0] += 1.0;
   if (S[S_RR] <= S[7] || !(S[S_PAP] > 0.0)) S[S_ACTIVE] = 0.0;
 }
 // G layout (m = restart): cs[m], sn[m], g[m + 1], inv (1/norm of the newest vector), R[m][m]
@@ -135,8 +137,8 @@ mf_status dev_cg_tol_init(mf_ctx* c, double* S, double tol2) {
   k_cg_tol_init<<<1, 1, 0, c->stream>>>(S, tol2);
   LAUNCHED();
 }
-mf_status dev_cg_tol_check(mf_ctx* c, double* S) {
-  k_cg_tol_check<<<1, 1, 0, c->stream>>>(S);
+mf_status dev_cg_tol_check(mf_ctx* c, double* S, double* steps) {
+  k_cg_tol_check<<<1, 1, 0, c->stream>>>(S, steps);
   LAUNCHED();
 }
 mf_status dev_gmres_begin(mf_ctx* c, const double* nrm2, double* G, int m) {

@@ -326,6 +326,7 @@ mf_status mf_meltpool_advance(mf_meltpool_step* step, const double* u_prev, cons
     fs.velocity_steps = p.flow_velocity_steps;
     fs.schur_maxit = p.flow_schur_maxit;
     fs.schur_tol = p.flow_schur_tol;
+    fs.use_graph = 1;
     MF_TRY(run_solve(S.flow, fs, bf, up, &inf.flow_iterations, &inf.flow_residual, &worst));
     MF_TRY(lap(3, t));
     inf.seconds[4] = std::chrono::duration<double>(clk::now() - t0).count();

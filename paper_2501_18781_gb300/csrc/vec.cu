@@ -46,38 +46,67 @@ struct Dot2f {
   __device__ __forceinline__ double value() const { return double(s) + double(c); }
 };
 
-// out = sum(part); one block per right-hand side r (blockIdx.x), partial rows of g entries.
-// mode 0: out[r] = sum; 1: pAp and alpha; 2: rr, rz (second row), beta; 3: rz and beta; 4: rr and rz
-__global__ void __launch_bounds__(kRedThreads) k_finish(const double* part, int g, double* out, int mode, double* S) {
-  const int r = blockIdx.x;
+// What the sum of a row of g partials feeds (row r; mode 0: out[r] = sum; 1: pAp and alpha;
+// 2: rr, rz (second row), beta; 3: rz and beta; 4: rr and rz; 5: rr).  count: one arrival
+// counter per row (zero between launches); NULL when a separate k_finish launch does the sum.
+struct Finish {
+  double* out;
+  int mode;
+  double* S;
+  unsigned* count;
+};
+
+// Sums row r of the partials in a fixed order (so results are reproducible bit for bit) and
+// applies the mode.  The loads go to L2: in the fused form other blocks of the same launch
+// wrote the partials.
+__device__ void finish_row(const double* part, int g, int r, const Finish& f) {
   const double* pr = part + int64_t(r) * 2 * g;
   double s = 0.0;
-  for (int i = threadIdx.x; i < g; i += blockDim.x) s += pr[i];
+  for (int i = threadIdx.x; i < g; i += blockDim.x) s += __ldcg(pr + i);
   s = block_sum(s);
   double s2 = 0.0;
-  if (mode == 2 || mode == 4) {
-    for (int i = threadIdx.x; i < g; i += blockDim.x) s2 += pr[g + i];
+  if (f.mode == 2 || f.mode == 4) {
+    for (int i = threadIdx.x; i < g; i += blockDim.x) s2 += __ldcg(pr + g + i);
     s2 = block_sum(s2);
   }
   if (threadIdx.x == 0) {
-    double* Sr = S ? S + r * S_NSCAL : nullptr;
-    if (mode == 0) out[r] = s;
-    else if (mode == 1) {
+    double* Sr = f.S ? f.S + r * S_NSCAL : nullptr;
+    if (f.mode == 0) f.out[r] = s;
+    else if (f.mode == 1) {
       Sr[S_PAP] = s;
       Sr[S_ALPHA] = (Sr[S_ACTIVE] != 0.0 && s != 0.0) ? Sr[S_RZ] / s : 0.0;
-    } else if (mode == 2 || mode == 3) {
-      const double rz = mode == 2 ? s2 : s;
-      if (mode == 2) Sr[S_RR] = s;
+    } else if (f.mode == 2 || f.mode == 3) {
+      const double rz = f.mode == 2 ? s2 : s;
+      if (f.mode == 2) Sr[S_RR] = s;
       Sr[S_RZN] = rz;
       Sr[S_BETA] = (Sr[S_ACTIVE] != 0.0 && Sr[S_RZ] != 0.0) ? rz / Sr[S_RZ] : 0.0;
       Sr[S_RZ] = rz;
-    } else if (mode == 4) {
+    } else if (f.mode == 4) {
       Sr[S_RR] = s;
       Sr[S_RZ] = s2;
-    } else if (mode == 5) {
+    } else if (f.mode == 5) {
       Sr[S_RR] = s;
     }
   }
+}
+
+__global__ void __launch_bounds__(kRedThreads) k_finish(const double* part, int g, double* out, int mode, double* S) {
+  finish_row(part, g, blockIdx.x, Finish{out, mode, S, nullptr});
+}
+
+// Called by every thread after thread 0 stored the block's partials of row blockIdx.y: the last
+// block of the row to arrive sums the row (finish_row) and resets the counter for the next launch.
+__device__ __forceinline__ void finish_if_last(const double* part, const Finish& f) {
+  if (!f.count) return;
+  __shared__ unsigned last;
+  __threadfence();  // this block's partials are visible device-wide before it is counted
+  __syncthreads();
+  if (threadIdx.x == 0) last = atomicAdd(f.count + blockIdx.y, 1u) == gridDim.x - 1 ? 1u : 0u;
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  finish_row(part, gridDim.x, blockIdx.y, f);
+  if (threadIdx.x == 0) f.count[blockIdx.y] = 0u;
 }
 
 // Per-block partial sums of x.y (and x2.y2).  Each thread keeps four independent
@@ -86,7 +115,7 @@ __global__ void __launch_bounds__(kRedThreads) k_finish(const double* part, int 
 // the partition and the summation order are fixed, so results are reproducible bit for bit.
 template <typename TX, typename TY>
 __global__ void __launch_bounds__(kRedThreads) k_dot2_partial(const TX* x, const TY* y, const TX* x2, const TY* y2,
-                                                             int64_t n, int64_t ld, double* part) {
+                                                             int64_t n, int64_t ld, double* part, Finish fin) {
   const int r = blockIdx.y;
   x += r * ld; y += r * ld;
   if (x2) { x2 += r * ld; y2 += r * ld; }
@@ -113,6 +142,7 @@ __global__ void __launch_bounds__(kRedThreads) k_dot2_partial(const TX* x, const
       part[int64_t(r) * 2 * gridDim.x + blockIdx.x] = s;
       part[int64_t(r) * 2 * gridDim.x + gridDim.x + blockIdx.x] = s2;
     }
+    finish_if_last(part, fin);
     return;
   }
   double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0, b0 = 0.0, b1 = 0.0, b2 = 0.0, b3 = 0.0;
@@ -143,11 +173,13 @@ __global__ void __launch_bounds__(kRedThreads) k_dot2_partial(const TX* x, const
     part[int64_t(r) * 2 * gridDim.x + blockIdx.x] = s;
     part[int64_t(r) * 2 * gridDim.x + gridDim.x + blockIdx.x] = s2;
   }
+  finish_if_last(part, fin);
 }
 
 template <typename T>
 __global__ void __launch_bounds__(kRedThreads) k_cg_xr(int64_t n, int64_t ld, T* x, T* r, const T* p, const T* Ap,
-                                                       const T* dinv, T* z, int zmode, const double* S, double* part) {
+                                                       const T* dinv, T* z, int zmode, const double* S, double* part,
+                                                       Finish fin) {
   const int rh = blockIdx.y;
   const double alpha = S[rh * S_NSCAL + S_ALPHA];
   const int64_t o = rh * ld;
@@ -192,6 +224,7 @@ __global__ void __launch_bounds__(kRedThreads) k_cg_xr(int64_t n, int64_t ld, T*
     part[int64_t(rh) * 2 * gridDim.x + blockIdx.x] = rr;
     part[int64_t(rh) * 2 * gridDim.x + gridDim.x + blockIdx.x] = rz;
   }
+  finish_if_last(part, fin);
 }
 
 template <typename T> __global__ void k_cg_p(int64_t n, int64_t ld, const T* z, T* p, const double* S) {
@@ -229,6 +262,23 @@ __global__ void k_block_jacobi(int64_t nu, int64_t np, const TB* blk, const doub
   }
 }
 
+// fp32 block inverses stored entry-major (entry e of node i at e * nu + i), so that each of a
+// warp's nine loads is one coalesced run
+__global__ void k_block_jacobi_soa32(int64_t nu, const float* __restrict__ blk, const float* __restrict__ r,
+                                     float* __restrict__ z) {
+  for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < nu; i += int64_t(gridDim.x) * blockDim.x) {
+    const float r0 = r[i], r1 = r[nu + i], r2 = r[2 * nu + i];
+    z[i] = blk[i] * r0 + blk[nu + i] * r1 + blk[2 * nu + i] * r2;
+    z[nu + i] = blk[3 * nu + i] * r0 + blk[4 * nu + i] * r1 + blk[5 * nu + i] * r2;
+    z[2 * nu + i] = blk[6 * nu + i] * r0 + blk[7 * nu + i] * r1 + blk[8 * nu + i] * r2;
+  }
+}
+__global__ void k_blocks_soa32(int64_t nu, const double* __restrict__ blk, float* __restrict__ out) {
+  for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < nu; i += int64_t(gridDim.x) * blockDim.x)
+#pragma unroll
+    for (int e = 0; e < 9; ++e) out[e * nu + i] = float(blk[9 * i + e]);
+}
+
 template <typename TS, typename TD> __global__ void k_convert(int64_t n, const TS* s, TD* d) {
   for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x)
     d[i] = TD(s[i]);
@@ -263,53 +313,71 @@ template <typename T> __global__ void k_add_into(int64_t n, int64_t ld, const T*
     z[o + i] += d[o + i];
 }
 
-// h partials: part[j * G + block] = sum over the block's slice of V_j . w
-// h_j partials for V_j . w, eight vectors per sweep: every element of w is loaded once per
-// group of eight and the eight V_j loads are independent, so many loads are in flight per thread.
-template <typename T>
-__global__ void __launch_bounds__(kRedThreads) k_multidot(const T* V, int64_t ld, int k, const T* w, int64_t n,
-                                                          double* part) {
-  constexpr int G = 8;
-  const int64_t st = int64_t(gridDim.x) * blockDim.x;
-  for (int j0 = 0; j0 < k; j0 += G) {
-    double a[G];
+// CGS2 pieces of the GMRES solvers.  V holds k basis vectors ld apart.  Where V and w start on
+// 16-byte boundaries and ld * sizeof(T) is a multiple of 16 (the solvers pad their bases so),
+// every thread moves 16-byte words (four floats or two doubles), so each step of a thread has
+// KG + 1 independent 16-byte loads in flight; otherwise the same code runs on single elements.
+template <typename T, int W> struct alignas(sizeof(T) * W) Word {
+  T c[W];
+};
+
+template <typename T> struct DotAcc;
+template <> struct DotAcc<float> : Dot2f {};
+template <> struct DotAcc<double> {
+  double s = 0.0;
+  __device__ __forceinline__ void add(double a, double b) { s = fma(a, b, s); }
+  __device__ __forceinline__ double value() const { return s; }
+};
+
+// part[(j0 + g) * gridDim.x + block] = the block's share of V_g . w for g < KG (V already offset
+// to vector j0): one sweep over w for KG vectors.
+template <typename T, int KG, int W>
+__device__ __forceinline__ void multidot_group(const T* V, int64_t ld, const T* w, int64_t n, double* part, int j0) {
+  using Wd = Word<T, W>;
+  DotAcc<T> acc[KG];
+  const int64_t t0 = int64_t(blockIdx.x) * blockDim.x + threadIdx.x, st = int64_t(gridDim.x) * blockDim.x;
+  const int64_t nw = n / W, ldw = ld / W;
+  const Wd* Vw = reinterpret_cast<const Wd*>(V);
+  const Wd* ww = reinterpret_cast<const Wd*>(w);
+  for (int64_t i = t0; i < nw; i += st) {
+    const Wd y = ww[i];
+    Wd x[KG];
 #pragma unroll
-    for (int g = 0; g < G; ++g) a[g] = 0.0;
-    const int kg = k - j0 < G ? k - j0 : G;
-    const T* V0 = V + j0 * ld;
-    if constexpr (std::is_same<T, float>::value) {
-      Dot2f c[G];
-      for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += st) {
-        const float wi = w[i];
+    for (int g = 0; g < KG; ++g) x[g] = Vw[g * ldw + i];
 #pragma unroll
-        for (int g = 0; g < G; ++g)
-          if (g < kg) c[g].add(V0[g * ld + i], wi);
-      }
+    for (int g = 0; g < KG; ++g)
 #pragma unroll
-      for (int g = 0; g < G; ++g) a[g] = c[g].value();
-    } else if (kg == G) {
-      for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += st) {
-        const double wi = double(w[i]);
-        T v[G];
+      for (int c = 0; c < W; ++c) acc[g].add(x[g].c[c], y.c[c]);
+  }
+  if (W > 1)  // the last n mod W elements
+    for (int64_t i = nw * W + t0; i < n; i += st) {
+      const T y = w[i];
 #pragma unroll
-        for (int g = 0; g < G; ++g) v[g] = V0[g * ld + i];
-#pragma unroll
-        for (int g = 0; g < G; ++g) a[g] += double(v[g]) * wi;
-      }
-    } else {
-      for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += st) {
-        const double wi = double(w[i]);
-#pragma unroll
-        for (int g = 0; g < G; ++g)
-          if (g < kg) a[g] += double(V0[g * ld + i]) * wi;
-      }
+      for (int g = 0; g < KG; ++g) acc[g].add(V[g * ld + i], y);
     }
 #pragma unroll
-    for (int g = 0; g < G; ++g) {
-      if (g >= kg) break;
-      const double sg = block_sum(a[g]);
-      if (threadIdx.x == 0) part[(j0 + g) * gridDim.x + blockIdx.x] = sg;
-    }
+  for (int g = 0; g < KG; ++g) {
+    const double sg = block_sum(acc[g].value());
+    if (threadIdx.x == 0) part[int64_t(j0 + g) * gridDim.x + blockIdx.x] = sg;
+  }
+}
+
+// h_j partials of V_j . w for j < k: groups of eight vectors, then one group of the rest
+template <typename T, int W>
+__global__ void __launch_bounds__(kRedThreads, 4) k_multidot(const T* V, int64_t ld, int k, const T* w, int64_t n,
+                                                             double* part) {
+  int j0 = 0;
+  for (; j0 + 8 <= k; j0 += 8) multidot_group<T, 8, W>(V + j0 * ld, ld, w, n, part, j0);
+  const T* Vr = V + j0 * ld;
+  switch (k - j0) {
+    case 1: multidot_group<T, 1, W>(Vr, ld, w, n, part, j0); break;
+    case 2: multidot_group<T, 2, W>(Vr, ld, w, n, part, j0); break;
+    case 3: multidot_group<T, 3, W>(Vr, ld, w, n, part, j0); break;
+    case 4: multidot_group<T, 4, W>(Vr, ld, w, n, part, j0); break;
+    case 5: multidot_group<T, 5, W>(Vr, ld, w, n, part, j0); break;
+    case 6: multidot_group<T, 6, W>(Vr, ld, w, n, part, j0); break;
+    case 7: multidot_group<T, 7, W>(Vr, ld, w, n, part, j0); break;
+    default: break;
   }
 }
 __global__ void __launch_bounds__(kRedThreads) k_multidot_finish(const double* part, int g, double* h) {
@@ -319,47 +387,45 @@ __global__ void __launch_bounds__(kRedThreads) k_multidot_finish(const double* p
   if (threadIdx.x == 0) h[blockIdx.x] = s;
 }
 
-// w += sign V h over k <= 64 vectors; h staged in shared memory, eight independent V loads
+// w += sign V h over k <= 64 vectors, h staged in shared memory (in T: fp32 data takes fp32
+// FMAs, since the fp64 pipe would bound this HBM-bound update); eight independent word loads
 // per step of the j loop.
-template <typename T>
-__global__ void k_multiaxpy(const T* V, int64_t ld, int k, const double* h, double sign, T* w, int64_t n) {
-  __shared__ double hs[64];
-  __shared__ float hf[64];
-  for (int j = threadIdx.x; j < k; j += blockDim.x) {
-    hs[j] = sign * h[j];
-    hf[j] = float(sign * h[j]);
-  }
+template <typename T, int W>
+__global__ void __launch_bounds__(256) k_multiaxpy(const T* V, int64_t ld, int k, const double* h, double sign, T* w,
+                                                   int64_t n) {
+  using Wd = Word<T, W>;
+  __shared__ T hs[64];
+  for (int j = threadIdx.x; j < k; j += blockDim.x) hs[j] = T(sign * h[j]);
   __syncthreads();
-  if constexpr (std::is_same<T, float>::value) {
-    // fp32 result: fp32 FMAs (the fp64 pipe would bound this HBM-bound update)
-    for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x) {
-      float acc = w[i];
-      int j = 0;
-      for (; j + 8 <= k; j += 8) {
-        float v[8];
-#pragma unroll
-        for (int g = 0; g < 8; ++g) v[g] = V[(j + g) * ld + i];
-#pragma unroll
-        for (int g = 0; g < 8; ++g) acc = fmaf(hf[j + g], v[g], acc);
-      }
-      for (; j < k; ++j) acc = fmaf(hf[j], V[j * ld + i], acc);
-      w[i] = acc;
-    }
-    return;
-  }
-  for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x) {
-    double acc = double(w[i]);
+  const int64_t t0 = int64_t(blockIdx.x) * blockDim.x + threadIdx.x, st = int64_t(gridDim.x) * blockDim.x;
+  const int64_t nw = n / W, ldw = ld / W;
+  const Wd* Vw = reinterpret_cast<const Wd*>(V);
+  Wd* ww = reinterpret_cast<Wd*>(w);
+  for (int64_t i = t0; i < nw; i += st) {
+    Wd acc = ww[i];
     int j = 0;
     for (; j + 8 <= k; j += 8) {
-      T v[8];
+      Wd x[8];
 #pragma unroll
-      for (int g = 0; g < 8; ++g) v[g] = V[(j + g) * ld + i];
+      for (int g = 0; g < 8; ++g) x[g] = Vw[(j + g) * ldw + i];
 #pragma unroll
-      for (int g = 0; g < 8; ++g) acc += hs[j + g] * double(v[g]);
+      for (int g = 0; g < 8; ++g)
+#pragma unroll
+        for (int c = 0; c < W; ++c) acc.c[c] = fma(hs[j + g], x[g].c[c], acc.c[c]);
     }
-    for (; j < k; ++j) acc += hs[j] * double(V[j * ld + i]);
-    w[i] = T(acc);
+    for (; j < k; ++j) {
+      const Wd x = Vw[j * ldw + i];
+#pragma unroll
+      for (int c = 0; c < W; ++c) acc.c[c] = fma(hs[j], x.c[c], acc.c[c]);
+    }
+    ww[i] = acc;
   }
+  if (W > 1)
+    for (int64_t i = nw * W + t0; i < n; i += st) {
+      T acc = w[i];
+      for (int j = 0; j < k; ++j) acc = fma(hs[j], V[j * ld + i], acc);
+      w[i] = acc;
+    }
 }
 
 __global__ void k_splitmix(uint64_t seed, double* v, int64_t n) {
@@ -388,6 +454,9 @@ inline int grid_for(int64_t n) {
 
 // The reduction scratch is allocated with the context (kScratchDoubles) and never grown, so
 // that solver iterations can be captured in CUDA graphs.
+// one arrival counter per right-hand side for the reductions that sum their own partials
+unsigned* counters(mf_ctx* ctx) { return ctx->counters.as<unsigned>(); }
+
 mf_status scratch(mf_ctx* ctx, size_t doubles, double** p) {
   if (ctx->scratch.bytes < doubles * sizeof(double))
     return fail(MF_EINVAL, "reduction scratch too small for this many right-hand sides");
@@ -403,9 +472,8 @@ mf_status scratch(mf_ctx* ctx, size_t doubles, double** p) {
 template <typename TX, typename TY> mf_status dot(mf_ctx* ctx, const TX* x, const TY* y, int64_t n, double* out) {
   double* part;
   MF_TRY(scratch(ctx, 2 * kRedBlocks, &part));
-  k_dot2_partial<TX, TY><<<dim3(kRedBlocks, 1), kRedThreads, 0, ctx->stream>>>(x, y, nullptr, nullptr, n, 0, part);
-  LAUNCH_CHECK();
-  k_finish<<<1, kRedThreads, 0, ctx->stream>>>(part, kRedBlocks, out, 0, nullptr);
+  k_dot2_partial<TX, TY><<<dim3(kRedBlocks, 1), kRedThreads, 0, ctx->stream>>>(x, y, nullptr, nullptr, n, 0, part,
+                                                                                Finish{out, 0, nullptr, counters(ctx)});
   LAUNCH_CHECK();
   return MF_OK;
 }
@@ -416,9 +484,8 @@ template <typename T>
 mf_status dot_batched(mf_ctx* ctx, const T* x, const T* y, int64_t n, int64_t ld, int nvec, double* out) {
   double* part;
   MF_TRY(scratch(ctx, 2 * kRedBlocks * size_t(nvec), &part));
-  k_dot2_partial<T, T><<<dim3(kRedBlocks, nvec), kRedThreads, 0, ctx->stream>>>(x, y, nullptr, nullptr, n, ld, part);
-  LAUNCH_CHECK();
-  k_finish<<<nvec, kRedThreads, 0, ctx->stream>>>(part, kRedBlocks, out, 0, nullptr);
+  k_dot2_partial<T, T><<<dim3(kRedBlocks, nvec), kRedThreads, 0, ctx->stream>>>(x, y, nullptr, nullptr, n, ld, part,
+                                                                                 Finish{out, 0, nullptr, counters(ctx)});
   LAUNCH_CHECK();
   return MF_OK;
 }
@@ -452,7 +519,12 @@ mf_status block_jacobi(mf_ctx* ctx, int64_t nu, int64_t np, const double* blk, c
   return MF_OK;
 }
 mf_status block_jacobi_u32(mf_ctx* ctx, int64_t nu, const float* blk, const float* r, float* z) {
-  k_block_jacobi<float, float><<<grid_for(nu), 256, 0, ctx->stream>>>(nu, 0, blk, nullptr, r, z);
+  k_block_jacobi_soa32<<<grid_for(nu), 256, 0, ctx->stream>>>(nu, blk, r, z);
+  LAUNCH_CHECK();
+  return MF_OK;
+}
+mf_status blocks_soa32(mf_ctx* ctx, int64_t nu, const double* blk, float* out) {
+  k_blocks_soa32<<<grid_for(nu), 256, 0, ctx->stream>>>(nu, blk, out);
   LAUNCH_CHECK();
   return MF_OK;
 }
@@ -470,9 +542,8 @@ template mf_status convert<float, double>(mf_ctx*, int64_t, const float*, double
 template <typename T> mf_status cg_alpha(mf_ctx* ctx, const T* p, const T* Ap, int64_t n, int64_t ld, int nrhs, double* S) {
   double* part;
   MF_TRY(scratch(ctx, 2 * kRedBlocks * size_t(nrhs), &part));
-  k_dot2_partial<T, T><<<dim3(kRedBlocks, nrhs), kRedThreads, 0, ctx->stream>>>(p, Ap, nullptr, nullptr, n, ld, part);
-  LAUNCH_CHECK();
-  k_finish<<<nrhs, kRedThreads, 0, ctx->stream>>>(part, kRedBlocks, nullptr, 1, S);
+  k_dot2_partial<T, T><<<dim3(kRedBlocks, nrhs), kRedThreads, 0, ctx->stream>>>(p, Ap, nullptr, nullptr, n, ld, part,
+                                                                                 Finish{nullptr, 1, S, counters(ctx)});
   LAUNCH_CHECK();
   return MF_OK;
 }
@@ -484,9 +555,8 @@ mf_status cg_update_xr(mf_ctx* ctx, int64_t n, int64_t ld, int nrhs, T* x, T* r,
                        const T* dinv, T* z, int zmode, double* S) {
   double* part;
   MF_TRY(scratch(ctx, 2 * kRedBlocks * size_t(nrhs), &part));
-  k_cg_xr<T><<<dim3(kRedBlocks, nrhs), kRedThreads, 0, ctx->stream>>>(n, ld, x, r, p, Ap, dinv, z, zmode, S, part);
-  LAUNCH_CHECK();
-  k_finish<<<nrhs, kRedThreads, 0, ctx->stream>>>(part, kRedBlocks, nullptr, zmode == 2 ? 5 : 2, S);
+  k_cg_xr<T><<<dim3(kRedBlocks, nrhs), kRedThreads, 0, ctx->stream>>>(
+      n, ld, x, r, p, Ap, dinv, z, zmode, S, part, Finish{nullptr, zmode == 2 ? 5 : 2, S, counters(ctx)});
   LAUNCH_CHECK();
   return MF_OK;
 }
@@ -498,9 +568,8 @@ template mf_status cg_update_xr<float>(mf_ctx*, int64_t, int64_t, int, float*, f
 template <typename T> mf_status cg_rz(mf_ctx* ctx, const T* r, const T* z, int64_t n, int64_t ld, int nrhs, double* S) {
   double* part;
   MF_TRY(scratch(ctx, 2 * kRedBlocks * size_t(nrhs), &part));
-  k_dot2_partial<T, T><<<dim3(kRedBlocks, nrhs), kRedThreads, 0, ctx->stream>>>(r, z, nullptr, nullptr, n, ld, part);
-  LAUNCH_CHECK();
-  k_finish<<<nrhs, kRedThreads, 0, ctx->stream>>>(part, kRedBlocks, nullptr, 3, S);
+  k_dot2_partial<T, T><<<dim3(kRedBlocks, nrhs), kRedThreads, 0, ctx->stream>>>(r, z, nullptr, nullptr, n, ld, part,
+                                                                                 Finish{nullptr, 3, S, counters(ctx)});
   LAUNCH_CHECK();
   return MF_OK;
 }
@@ -511,9 +580,8 @@ template <typename T>
 mf_status cg_init_scalars(mf_ctx* ctx, const T* r, const T* z, int64_t n, int64_t ld, int nrhs, double* S) {
   double* part;
   MF_TRY(scratch(ctx, 2 * kRedBlocks * size_t(nrhs), &part));
-  k_dot2_partial<T, T><<<dim3(kRedBlocks, nrhs), kRedThreads, 0, ctx->stream>>>(r, r, r, z, n, ld, part);
-  LAUNCH_CHECK();
-  k_finish<<<nrhs, kRedThreads, 0, ctx->stream>>>(part, kRedBlocks, nullptr, 4, S);
+  k_dot2_partial<T, T><<<dim3(kRedBlocks, nrhs), kRedThreads, 0, ctx->stream>>>(r, r, r, z, n, ld, part,
+                                                                                 Finish{nullptr, 4, S, counters(ctx)});
   LAUNCH_CHECK();
   return MF_OK;
 }
@@ -560,12 +628,20 @@ template <typename T> mf_status add_into(mf_ctx* ctx, int64_t n, int64_t ld, int
 template mf_status add_into<double>(mf_ctx*, int64_t, int64_t, int, const double*, double*);
 template mf_status add_into<float>(mf_ctx*, int64_t, int64_t, int, const float*, float*);
 
+// p starts on a 16-byte boundary and so does every vector ld elements further on
+template <typename T> bool words16(const T* p, int64_t ld) {
+  return reinterpret_cast<uintptr_t>(p) % 16 == 0 && (ld * int64_t(sizeof(T))) % 16 == 0;
+}
+
 template <typename T> mf_status multidot(mf_ctx* ctx, const T* V, int64_t ld, int k, const T* w, int64_t n, double* h) {
   if (k > 64) return fail(MF_EINVAL, "multidot: at most 64 vectors");
   const int g = kRedBlocks;
   double* part;
   MF_TRY(scratch(ctx, size_t(g) * (k + 1) + 64, &part));
-  k_multidot<T><<<g, kRedThreads, 0, ctx->stream>>>(V, ld, k, w, n, part);
+  if (words16(V, ld) && words16(w, 0))
+    k_multidot<T, 16 / sizeof(T)><<<g, kRedThreads, 0, ctx->stream>>>(V, ld, k, w, n, part);
+  else
+    k_multidot<T, 1><<<g, kRedThreads, 0, ctx->stream>>>(V, ld, k, w, n, part);
   LAUNCH_CHECK();
   k_multidot_finish<<<k, kRedThreads, 0, ctx->stream>>>(part, g, h);
   LAUNCH_CHECK();
@@ -578,7 +654,10 @@ template <typename T>
 mf_status multiaxpy(mf_ctx* ctx, const T* V, int64_t ld, int k, const double* h, double sign, T* w, int64_t n) {
   if (k > 64) return fail(MF_EINVAL, "multiaxpy: at most 64 vectors");
   if (k < 1) return MF_OK;
-  k_multiaxpy<T><<<grid_for(n), 256, 0, ctx->stream>>>(V, ld, k, h, sign, w, n);
+  if (words16(V, ld) && words16(w, 0))
+    k_multiaxpy<T, 16 / sizeof(T)><<<grid_for(n), 256, 0, ctx->stream>>>(V, ld, k, h, sign, w, n);
+  else
+    k_multiaxpy<T, 1><<<grid_for(n), 256, 0, ctx->stream>>>(V, ld, k, h, sign, w, n);
   LAUNCH_CHECK();
   return MF_OK;
 }
@@ -651,7 +730,8 @@ template <typename T>
 static mf_status dot_noalloc(const T* x, const T* y, int64_t n, int64_t ld, int nvec, double* out, cudaStream_t s) {
   double* part = nullptr;
   MF_TRY(noalloc_workspace(&part));
-  k_dot2_partial<T, T><<<dim3(kRedBlocks, nvec), kRedThreads, 0, s>>>(x, y, nullptr, nullptr, n, ld, part);
+  k_dot2_partial<T, T><<<dim3(kRedBlocks, nvec), kRedThreads, 0, s>>>(x, y, nullptr, nullptr, n, ld, part,
+                                                                       Finish{nullptr, 0, nullptr, nullptr});
   MF_CUDA_TRY(cudaGetLastError());
   k_finish<<<nvec, kRedThreads, 0, s>>>(part, kRedBlocks, out, 0, nullptr);
   MF_CUDA_TRY(cudaGetLastError());

@@ -28,8 +28,11 @@ template <typename T> mf_status pointwise_mul(mf_ctx* ctx, int64_t n, const T* d
 template <typename T>
 mf_status block_jacobi(mf_ctx* ctx, int64_t nu, int64_t np, const double* blk, const double* pinv, const T* r, T* z);
 template <typename TS, typename TD> mf_status convert(mf_ctx* ctx, int64_t n, const TS* s, TD* d);
-// velocity part only, fp32 block inverses: z_u = B^-1 r_u per node
+// velocity part only, fp32 block inverses stored entry-major (entry e of node i at e nu + i):
+// z_u = B^-1 r_u per node
 mf_status block_jacobi_u32(mf_ctx* ctx, int64_t nu, const float* blk, const float* r, float* z);
+// the fp64 block inverses (9 per node, row major) as entry-major fp32
+mf_status blocks_soa32(mf_ctx* ctx, int64_t nu, const double* blk, float* out);
 
 // Batched CG pieces: nrhs systems, vectors ld apart, device scalars S[r * S_NSCAL + k]:
 // 0 rz, 1 pAp, 2 alpha, 3 beta, 4 rr, 5 rz_new, 6 active (1 = still iterating)

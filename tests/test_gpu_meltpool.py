@@ -73,12 +73,17 @@ def test_meltpool_oseen_apply_matches_oracle(ctx, flags):
 
 
 def test_meltpool_oseen_solve_with_block_preconditioner(ctx):
+    """The Darcy-damped velocity block needs more inner GMRES steps than the defaults: with 10,
+    restarted FGMRES(50) takes about 300 iterations in exact arithmetic, and the run-to-run
+    rounding of the atomic scatter moves the count between 300 and past 600; with 20 steps and
+    the Schur CG to 0.05 it converges within the first restart cycle (34 iterations in fp64)."""
     P = meltpool(6, ctx, ("three", "darcy", "trace"))
     b = syn.uniform_pm1(6, P["n"])
     b[np.concatenate([np.tile(P["dmu"].dirichlet, 3), np.zeros(P["dmp"].n_dofs, bool)])] = 0.0
     x, info = P["op"].solve(torch.tensor(b, device="cuda"), solver="gmres", precond="block_triangular", restart=50,
-                            maxit=600, tol=1e-10)
+                            maxit=400, tol=1e-10, velocity_steps=20, schur_maxit=50, schur_tol=0.05)
     assert info["status"] == 0, info
+    assert info["iterations"] <= 100, info
     res = np.linalg.norm(b - P["A"] @ x.cpu().numpy()) / np.linalg.norm(b)
     assert res <= 1e-10 * (1 + 1e-3), (res, info)
 

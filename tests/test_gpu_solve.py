@@ -87,6 +87,25 @@ def test_fgmres_oseen_block_triangular(ctx, n):
     assert info["iterations"] <= 60, info
 
 
+def test_fgmres_oseen_block_triangular_replayed_as_a_graph(ctx):
+    """use_graph records the preconditioner call once and replays it: the same solution to the
+    oracle's tolerance, the same outer iteration count, and the launch count of the replayed
+    kernels equal to that of the direct calls."""
+    P = oseen(7, ctx)
+    b = syn.uniform_pm1(3, P["n"])
+    mask = np.concatenate([np.tile(P["dmu"].dirichlet, 3), np.zeros(P["dmp"].n_dofs, bool)])
+    b[mask] = 0.0
+    kw = dict(solver="gmres", precond="block_triangular", restart=50, maxit=400)
+    solve_and_check(P, b, **kw)  # builds the operator's fp32 tables, once
+    l0 = ctx.launch_count()
+    direct = solve_and_check(P, b, **kw)
+    l1 = ctx.launch_count()
+    replayed = solve_and_check(P, b, use_graph=True, **kw)
+    l2 = ctx.launch_count()
+    assert replayed["iterations"] == direct["iterations"], (direct, replayed)
+    assert l2 - l1 == l1 - l0
+
+
 def test_block_triangular_needs_gmres(ctx):
     from paper_2501_18781_gb300._lib import MFError
     P = oseen(3, ctx)
