@@ -671,8 +671,8 @@ mf_status apply_impl(mf_op* op, const T* src, T* dst, int nrhs, int64_t ld, bool
     for (int r = 0; r < nrhs; ++r) {
       OseenArgs<T> a = oseen_args<T>(op, src + r * ld, dst + r * ld);
       MF_TRY(launch_oseen_apply(c, op->map[0], prec, &a));
-      for (int comp = 0; comp < 3; ++comp)
-        MF_TRY(launch_dirichlet_copy(c, op->map[0], src + r * ld, dst + r * ld, 1, ld, comp * nu, f32));
+      // the three velocity components' Dirichlet rows, as three vectors nu apart
+      MF_TRY(launch_dirichlet_copy(c, op->map[0], src + r * ld, dst + r * ld, 3, nu, 0, f32));
     }
     op->variant = std::string("oseen_q2q1") + pname + "/tabulated" +
                   ((f32 || op->oseen_qouter64 || op->p.oseen_flags) ? "/qpoint-outer" : "/component-outer") +
@@ -712,17 +712,24 @@ template <typename T> mf_status oseen_coupling(mf_op* op, int which, const T* sr
     MF_TRY(check_fields(op));
     MF_TRY(diag64(op, nullptr));
     DevBuf ua, ub;
-    MF_TRY(ub.alloc(sizeof(T) * 3 * size_t(nu)));
     if constexpr (sizeof(T) == 4) {
-      MF_TRY(ua.alloc(sizeof(float) * 9 * size_t(nu)));  // the fp32 block inverses, entry-major
+      // the preconditioner's form: the assembled 125-point stencil from the fp32 block inverses
+      const int* gn = op->map[0]->mesh->n;
+      DevBuf sc;
+      MF_TRY(ua.alloc(sizeof(float) * 9 * size_t(nu)));
+      MF_TRY(ub.alloc(2 * size_t(stencil_halves(np))));
+      MF_TRY(sc.alloc(sizeof(float) * size_t(np)));
       MF_TRY(blocks_soa32(op->ctx, nu, op->blk64.as<double>(), ua.as<float>()));
-      MF_TRY(launch_oseen_bt_dinv_f32(op->ctx, op->map[0], src, ua.as<float>(), ub.as<float>()));
+      MF_TRY(launch_schur_assemble_f32(op->ctx, op->map[0], ua.as<float>(), ub.p, sc.as<float>()));
+      MF_TRY(stencil125_apply(op->ctx, ub.p, sc.as<float>(), src, dst, gn[0], gn[1], gn[2], nullptr));
+      MF_CUDA_TRY(cudaStreamSynchronize(op->ctx->stream));  // before sc is freed
     } else {
       MF_TRY(ua.alloc(sizeof(T) * 3 * size_t(nu)));
+      MF_TRY(ub.alloc(sizeof(T) * 3 * size_t(nu)));
       MF_TRY(oseen_coupling<T>(op, 0, src, ua.as<T>()));
       MF_TRY(block_jacobi<T>(op->ctx, nu, 0, op->blk64.as<double>(), nullptr, ua.as<T>(), ub.as<T>()));
+      MF_TRY(oseen_coupling<T>(op, 1, ub.as<T>(), dst));
     }
-    MF_TRY(oseen_coupling<T>(op, 1, ub.as<T>(), dst));
     MF_CUDA_TRY(cudaStreamSynchronize(op->ctx->stream));  // before the work vectors are freed
     return MF_OK;
   }

@@ -1,5 +1,8 @@
 // float instantiation of the apply kernels.
 #include "apply_kernels.cuh"
+#include <cuda_fp16.h>
+
+#include "vec.cuh"
 
 namespace mf {
 
@@ -66,84 +69,86 @@ __device__ __forceinline__ void hat_couplings(int a, int n, int& lo, float M[3],
   }
 }
 
-// ub = D^-1 B^T p at every velocity node, node by node (no scatter, no atomics): on a uniform
-// mesh the coupling factors into 1D couplings, (B^T p)_{v,x} = -h^2 sum_ijk D_a,i M_b,j M_c,k
-// p_ijk (and likewise along y and z), which the cellwise Gauss quadrature evaluates exactly;
-// here it is summed dimension by dimension over the 3 x 3 x 3 pressure nodes around the node.
-// One grid row per lattice plane c (blockIdx.y), so the index arithmetic stays in 32 bits.
-// blk: the fp32 inverses of the 3 x 3 nodal blocks of A_uu, entry-major (e * nu + node).
-// Dirichlet nodes receive 0.
-__global__ void __launch_bounds__(256) k_oseen_bt_dinv(const float* __restrict__ p, const float* __restrict__ blk,
-                                                       float* __restrict__ ub, int64_t nu, UniformGeom ug) {
-  const uint32_t sx = uint32_t(ug.sx), plane = uint32_t(ug.sy);
-  const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= plane) return;
-  const int a = int(t % sx), b = int(t / sx), c = int(blockIdx.y);
-  const int64_t v = int64_t(c) * plane + t;
+constexpr int kSchurRows = 64;  // pressure rows per block of the assembly
+
+// S~ = B D^-1 B^T on the pressure grid as a 5 x 5 x 5 stencil (the scaled fp16 tiled layout of
+// stencil_at; scale[i] = the row's largest magnitude, 1 for an empty row):
+// entry o of row i couples pressure node i with node i + (ox, oy, oz), o = (ox + 2) + 5 (oy + 2) +
+// 25 (oz + 2), 0 where that node lies outside the grid.  With b(v, i) the column of B^T of pressure node i at velocity
+// node v (on a uniform mesh, (B^T)_{v,x; i} = -h^2 D_{a,ix} M_{b,iy} M_{c,iz} and likewise along y
+// and z, from the 1D couplings above), S~_{i,i'} = sum over the non-Dirichlet velocity nodes v
+// within two lattice steps of i of b(v, i)^T D_v^-1 b(v, i').  One thread per pressure row; its
+// 125 sums live in shared memory as [o][thread].  blk: the fp32 nodal block inverses,
+// entry-major (e nu + v, e = 3 row + column); fp32 arithmetic (the result is the operator of an
+// inner preconditioner solve).
+__global__ void __launch_bounds__(kSchurRows) k_schur_assemble(const float* __restrict__ blk, __half* __restrict__ S,
+                                                               float* __restrict__ scale, int64_t nu, UniformGeom ug) {
+  __shared__ float acc[125 * kSchurRows];
+  const int px = ug.nx + 1, py = ug.ny + 1;
+  const int64_t np = int64_t(px) * py * (ug.nz + 1);
+  const int64_t row = int64_t(blockIdx.x) * kSchurRows + threadIdx.x;
+  for (int o = 0; o < 125; ++o) acc[o * kSchurRows + threadIdx.x] = 0.0f;
+  if (row >= np) return;
+  const int ix = int(row % px), iy = int((row / px) % py), iz = int(row / (int64_t(px) * py));
+  const float sc = -float(ug.h * ug.h);
   const uint32_t f = ug.dir_faces;
-  if (((f & 1u) && a == 0) || ((f & 2u) && a == 2 * ug.nx) || ((f & 4u) && b == 0) ||
-      ((f & 8u) && b == 2 * ug.ny) || ((f & 16u) && c == 0) || ((f & 32u) && c == 2 * ug.nz)) {
-    ub[v] = 0.0f;
-    ub[nu + v] = 0.0f;
-    ub[2 * nu + v] = 0.0f;
-    return;
-  }
-  int lx, ly, lz;
-  float Mx[3], Dx[3], My[3], Dy[3], Mz[3], Dz[3];
-  hat_couplings(a, ug.nx, lx, Mx, Dx);
-  hat_couplings(b, ug.ny, ly, My, Dy);
-  hat_couplings(c, ug.nz, lz, Mz, Dz);
-  const int px = ug.nx + 1, pxy = px * (ug.ny + 1);
-  int oi[3], oj[3], ok[3];
+  for (int c = max(0, 2 * iz - 2); c <= min(2 * ug.nz, 2 * iz + 2); ++c) {
+    int lz;
+    float Mz[3], Dz[3];
+    hat_couplings(c, ug.nz, lz, Mz, Dz);
+    const int qz = iz - lz;  // the slot of row i in node c's couplings: 0..2
+    if (((f & 16u) && c == 0) || ((f & 32u) && c == 2 * ug.nz)) continue;
+    for (int b = max(0, 2 * iy - 2); b <= min(2 * ug.ny, 2 * iy + 2); ++b) {
+      int ly;
+      float My[3], Dy[3];
+      hat_couplings(b, ug.ny, ly, My, Dy);
+      const int qy = iy - ly;
+      if (((f & 4u) && b == 0) || ((f & 8u) && b == 2 * ug.ny)) continue;
+      for (int a = max(0, 2 * ix - 2); a <= min(2 * ug.nx, 2 * ix + 2); ++a) {
+        if (((f & 1u) && a == 0) || ((f & 2u) && a == 2 * ug.nx)) continue;
+        int lx;
+        float Mx[3], Dx[3];
+        hat_couplings(a, ug.nx, lx, Mx, Dx);
+        const int qx = ix - lx;
+        const float bx = sc * Dx[qx] * My[qy] * Mz[qz];
+        const float by = sc * Mx[qx] * Dy[qy] * Mz[qz];
+        const float bz = sc * Mx[qx] * My[qy] * Dz[qz];
+        if (bx == 0.0f && by == 0.0f && bz == 0.0f) continue;
+        const int64_t v = a + ug.sx * b + ug.sy * c;
+        // w^T = b(v, i)^T D_v^-1
+        const float w0 = bx * blk[v] + by * blk[3 * nu + v] + bz * blk[6 * nu + v];
+        const float w1 = bx * blk[nu + v] + by * blk[4 * nu + v] + bz * blk[7 * nu + v];
+        const float w2 = bx * blk[2 * nu + v] + by * blk[5 * nu + v] + bz * blk[8 * nu + v];
 #pragma unroll
-  for (int s = 0; s < 3; ++s) {
-    oi[s] = min(max(lx + s, 0), ug.nx);
-    oj[s] = px * min(max(ly + s, 0), ug.ny);
-    ok[s] = pxy * min(max(lz + s, 0), ug.nz);
-  }
-  float Qmm[3], Qdm[3], Qmd[3];
+        for (int u = 0; u < 3; ++u)
 #pragma unroll
-  for (int si = 0; si < 3; ++si) {
-    Qmm[si] = 0.0f, Qdm[si] = 0.0f, Qmd[si] = 0.0f;
+          for (int t = 0; t < 3; ++t) {
+            const float myz = My[t] * Mz[u], dyz = Dy[t] * Mz[u], mdz = My[t] * Dz[u];
+            const int oyz = 5 * (ly + t - iy + 2) + 25 * (lz + u - iz + 2);
 #pragma unroll
-    for (int sj = 0; sj < 3; ++sj) {
-      float pm = 0.0f, pd = 0.0f;
-#pragma unroll
-      for (int sk = 0; sk < 3; ++sk) {
-        const float pv = __ldg(p + (oi[si] + oj[sj] + ok[sk]));
-        pm = fmaf(Mz[sk], pv, pm);
-        pd = fmaf(Dz[sk], pv, pd);
+            for (int s2 = 0; s2 < 3; ++s2) {
+              const float val = sc * (w0 * (Dx[s2] * myz) + w1 * (Mx[s2] * dyz) + w2 * (Mx[s2] * mdz));
+              acc[(oyz + lx + s2 - ix + 2) * kSchurRows + threadIdx.x] += val;
+            }
+          }
       }
-      Qmm[si] = fmaf(My[sj], pm, Qmm[si]);
-      Qdm[si] = fmaf(Dy[sj], pm, Qdm[si]);
-      Qmd[si] = fmaf(My[sj], pd, Qmd[si]);
     }
   }
-  const float sc = -float(ug.h * ug.h);
-  float gx = 0.0f, gy = 0.0f, gz = 0.0f;
-#pragma unroll
-  for (int si = 0; si < 3; ++si) {
-    gx = fmaf(Dx[si], Qmm[si], gx);
-    gy = fmaf(Mx[si], Qdm[si], gy);
-    gz = fmaf(Mx[si], Qmd[si], gz);
-  }
-  gx *= sc, gy *= sc, gz *= sc;
-  ub[v] = blk[v] * gx + blk[nu + v] * gy + blk[2 * nu + v] * gz;
-  ub[nu + v] = blk[3 * nu + v] * gx + blk[4 * nu + v] * gy + blk[5 * nu + v] * gz;
-  ub[2 * nu + v] = blk[6 * nu + v] * gx + blk[7 * nu + v] * gy + blk[8 * nu + v] * gz;
+  float big = 0.0f;
+  for (int o = 0; o < 125; ++o) big = fmaxf(big, fabsf(acc[o * kSchurRows + threadIdx.x]));
+  const float sr = big > 0.0f ? big : 1.0f;
+  scale[row] = sr;
+  for (int o = 0; o < 125; ++o) S[stencil_at(o, row)] = __float2half_rn(acc[o * kSchurRows + threadIdx.x] / sr);
+  for (int o = 125; o < 128; ++o) S[stencil_at(o, row)] = __float2half_rn(0.0f);
 }
 
 }  // namespace
 
-mf_status launch_oseen_bt_dinv_f32(mf_ctx* ctx, const mf_dofmap* mu, const float* p, const float* blk, float* ub) {
+mf_status launch_schur_assemble_f32(mf_ctx* ctx, const mf_dofmap* mu, const float* blk, void* S, float* scale) {
   UniformGeom ug = uniform_geom(mu);
-  const int64_t nu = mu->n_dofs;
-  // 32-bit plane and pressure indices; the grid's y extent is limited to 65535 planes
-  if (ug.sy >= (int64_t(1) << 31) || int64_t(ug.nx + 1) * (ug.ny + 1) * (ug.nz + 1) >= (int64_t(1) << 31) ||
-      2 * ug.nz + 1 > 65535)
-    return fail(MF_EUNSUPPORTED, "node-wise coupling kernel: mesh too large for 32-bit plane indices");
-  const dim3 grid(unsigned((ug.sy + 255) / 256), unsigned(2 * ug.nz + 1));
-  k_oseen_bt_dinv<<<grid, 256, 0, ctx->stream>>>(p, blk, ub, nu, ug);
+  const int64_t np = int64_t(ug.nx + 1) * (ug.ny + 1) * (ug.nz + 1);
+  k_schur_assemble<<<unsigned((np + kSchurRows - 1) / kSchurRows), kSchurRows, 0, ctx->stream>>>(
+      blk, static_cast<__half*>(S), scale, mu->n_dofs, ug);
   ctx->launches++;
   MF_CUDA_TRY(cudaGetLastError());
   return MF_OK;

@@ -421,6 +421,26 @@ __global__ void k_oseen_blocks(OseenArgs<double> A, UniformGeom ug, double* blk,
     double B[9] = {s[l] + lap + X[0][l], X[3][l], X[4][l],
                    X[3][l], s[l] + lap + X[1][l], X[5][l],
                    X[4][l], X[5][l], s[l] + lap + X[2][l]};
+    if (A.ext) {
+      // trace correction -2 mu (div u) n n (n = 0 where it is switched off): with u = N e_e,
+      // B[d][e] += sum_q -2 w h mu n_d (n . grad N) d_e N, not symmetric in (d, e)
+      for (int q = 0; q < 27; ++q) {
+        const int qa = q % 3, qb = (q / 3) % 3, qc = q / 9;
+        const double n0 = A.nrm[q * nc + L.cell], n1 = A.nrm[(27 + q) * nc + L.cell];
+        const double n2 = A.nrm[(54 + q) * nc + L.cell];
+        if (n0 == 0.0 && n1 == 0.0 && n2 == 0.0) continue;
+        const double g0 = cSp64[3 * qa + a] * cS64[3 * qb + b] * cS64[3 * qc + cc];
+        const double g1 = cS64[3 * qa + a] * cSp64[3 * qb + b] * cS64[3 * qc + cc];
+        const double g2 = cS64[3 * qa + a] * cS64[3 * qb + b] * cSp64[3 * qc + cc];
+        const double t = -2.0 * cW364[q] * h * A.mu[q * nc + L.cell] * (n0 * g0 + n1 * g1 + n2 * g2);
+        const double tn[3] = {t * n0, t * n1, t * n2};
+        for (int d = 0; d < 3; ++d) {
+          B[3 * d] += tn[d] * g0;
+          B[3 * d + 1] += tn[d] * g1;
+          B[3 * d + 2] += tn[d] * g2;
+        }
+      }
+    }
     for (int e = 0; e < 9; ++e) atomicAdd(blk + id * 9 + e, B[e]);
   }
   // pressure: sum_q w h^3 psi_i^2 / mu and sum_q w h |grad psi_i|^2 / (sigma rho)

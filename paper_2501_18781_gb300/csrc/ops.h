@@ -64,9 +64,10 @@ mf_status launch_oseen_apply(mf_ctx* ctx, const mf_dofmap* mu, int prec, const v
 // Oseen coupling blocks alone: which 0 dst_u = B^T src_p, which 1 dst_p = B src_u (dst zeroed)
 mf_status launch_oseen_coupling_f64(mf_ctx* ctx, const mf_dofmap* mu, int which, const double* src, double* dst);
 mf_status launch_oseen_coupling_f32(mf_ctx* ctx, const mf_dofmap* mu, int which, const float* src, float* dst);
-// ub = D^-1 B^T p node by node (uniform Q2 velocity map; blk: fp32 inverses of the 3 x 3 nodal
-// blocks, 9 per node; ub: the three velocity blocks, overwritten, 0 in Dirichlet rows)
-mf_status launch_oseen_bt_dinv_f32(mf_ctx* ctx, const mf_dofmap* mu, const float* p, const float* blk, float* ub);
+// S~ = B D^-1 B^T as a 125-point stencil on the pressure grid (uniform Q2 velocity map; blk: fp32
+// inverses of the 3 x 3 nodal blocks, entry-major; S: stencil_halves(n_p) fp16 entries in the
+// scaled tiled layout of stencil_at, scale: n_p row factors; both overwritten)
+mf_status launch_schur_assemble_f32(mf_ctx* ctx, const mf_dofmap* mu, const float* blk, void* S, float* scale);
 // Gauss-point tables from nodal fp64 fields (always evaluated in fp64, stored in both precisions)
 // (heat: rhocp_q / beta_q are the optional per-Gauss-point fields; qmass gets rhocp_q / dt)
 mf_status launch_scalar_qtables(mf_ctx* ctx, const mf_dofmap* m, int kind, const double* field, const double* kq_user,

@@ -158,7 +158,10 @@ struct OseenBlockTri {
   int64_t n = 0, nu = 0, nu3 = 0, np = 0;
   int ku = 10, smax = 30;
   double stol = 0.1;
-  Vec<float> blk32, ua, ub, pinv32, xp, rp, zp, pp, sp, V, t, w;
+  Vec<float> blk32, ua, pinv32, xp, rp, zp, pp, sp, V, t, w;
+  DevBuf stil;        // S~ = B D^-1 B^T as a 125-point stencil on the pressure grid (fp16 entries)
+  Vec<float> stscale;  // and its row factors
+  int gn[3] = {0, 0, 0};  // cells per axis
   int64_t ldv = 0;  // stride of the basis vectors in V
   Vec<double> gst, y;
   // graph replay: a call launches the same sequence every time (several hundred small kernels),
@@ -187,8 +190,11 @@ struct OseenBlockTri {
     MF_TRY(diag64(op, nullptr));  // 3x3 block inverses and the pressure scaling
     MF_TRY(blk32.alloc(9 * nu));
     MF_TRY(blocks_soa32(c, nu, op->blk64.as<double>(), blk32.p));
+    for (int d = 0; d < 3; ++d) gn[d] = op->map[0]->mesh->n[d];
+    MF_TRY(stil.alloc(2 * size_t(stencil_halves(np))));
+    MF_TRY(stscale.alloc(np));
+    MF_TRY(launch_schur_assemble_f32(c, op->map[0], blk32.p, stil.p, stscale.p));
     MF_TRY(ua.alloc(nu3));
-    MF_TRY(ub.alloc(nu3));
     for (Vec<float>* v : {&pinv32, &xp, &rp, &zp, &pp, &sp}) MF_TRY(v->alloc(np));
     MF_TRY((convert<double, float>(c, np, op->pdiag64.as<double>(), pinv32.p)));
     ldv = basis_stride(n);
@@ -205,12 +211,6 @@ struct OseenBlockTri {
   // device counter of the Schur CG steps taken while still iterating, over all calls
   double* schur_steps() { return op->ctx->scalars.as<double>() + kScalarsTri + 144; }
 
-  // out = S~ p = B D^-1 B^T p (D^-1 B^T p node by node, then B cell by cell)
-  mf_status schur(const float* p, float* out) {
-    MF_TRY(launch_oseen_bt_dinv_f32(op->ctx, op->map[0], p, blk32.p, ub.p));
-    return oseen_coupling<float>(op, 1, ub.p, out);
-  }
-
   // xp = S~^-1 r_p (r_p fp64): Jacobi-PCG from 0, smax steps; once ||r_k|| <= stol ||r_0|| (or
   // p.S~p <= 0) the remaining steps leave x unchanged.
   mf_status schur_solve(const double* r) {
@@ -223,8 +223,8 @@ struct OseenBlockTri {
     MF_TRY(cg_init_scalars<float>(c, rp.p, zp.p, np, np, 1, S));
     MF_TRY(dev_cg_tol_init(c, S, stol * stol));
     for (int k = 0; k < smax; ++k) {
-      MF_TRY(schur(pp.p, sp.p));
-      MF_TRY(cg_alpha<float>(c, pp.p, sp.p, np, np, 1, S));
+      // sp = S~ pp and alpha in one launch
+      MF_TRY(stencil125_apply(c, stil.p, stscale.p, pp.p, sp.p, gn[0], gn[1], gn[2], S));
       MF_TRY(cg_update_xr<float>(c, np, np, 1, xp.p, rp.p, pp.p, sp.p, pinv32.p, zp.p, 1, S));
       MF_TRY(dev_cg_tol_check(c, S, schur_steps()));
       MF_TRY(cg_update_p<float>(c, np, np, 1, zp.p, pp.p, S));

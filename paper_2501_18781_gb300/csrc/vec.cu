@@ -1,112 +1,21 @@
 // Vector kernels of the Krylov solvers.  All reductions accumulate in fp64 over a fixed
-// grid of kRedBlocks blocks, then one block sums the partials in a fixed order, so every
-// dot product is deterministic.
+// grid of kRedBlocks blocks, then the last block to finish sums the partials in a fixed order,
+// so every dot product is deterministic.
+#include <algorithm>
 #include <mutex>
 #include <string>
 #include <type_traits>
 
-#include "vec.cuh"
+#include <cuda_fp16.h>
+
+#include "reduce.cuh"
 
 namespace mf {
 
 namespace {
 
-__device__ __forceinline__ double block_sum(double v) {
-  __shared__ double sh[kRedThreads / 32];
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
-  __syncthreads();
-  double s = 0.0;
-  if (threadIdx.x < 32) {
-    s = threadIdx.x < kRedThreads / 32 ? sh[threadIdx.x] : 0.0;
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
-  }
-  __syncthreads();
-  return s;  // valid in thread 0
-}
-
-// fp32 data: GB300's fp64 pipe (1/64 of the fp32 rate) cannot keep up with HBM if every
-// element is converted and accumulated in fp64 (a conversion and an fp64 FMA per 4-byte
-// element).  Within a thread, fp32 products and sums are therefore carried as unevaluated
-// pairs of floats: the product error by an FMA (a*b = p + e exactly) and the sum error by
-// Knuth's two-sum, i.e. the compensated dot product of Ogita, Rump and Oishi ("Accurate sum
-// and dot product", SIAM J. Sci. Comput. 26, 2005), whose result is as accurate as a dot
-// product evaluated in twice the working precision.  Partials leave the thread as
-// double(s) + double(c) and are reduced in fp64.
-struct Dot2f {
-  float s = 0.0f, c = 0.0f;
-  __device__ __forceinline__ void add(float a, float b) {
-    const float p = a * b;
-    const float e = fmaf(a, b, -p);
-    const float t = s + p;
-    const float z = t - s;
-    c += ((s - (t - z)) + (p - z)) + e;
-    s = t;
-  }
-  __device__ __forceinline__ double value() const { return double(s) + double(c); }
-};
-
-// What the sum of a row of g partials feeds (row r; mode 0: out[r] = sum; 1: pAp and alpha;
-// 2: rr, rz (second row), beta; 3: rz and beta; 4: rr and rz; 5: rr).  count: one arrival
-// counter per row (zero between launches); NULL when a separate k_finish launch does the sum.
-struct Finish {
-  double* out;
-  int mode;
-  double* S;
-  unsigned* count;
-};
-
-// Sums row r of the partials in a fixed order (so results are reproducible bit for bit) and
-// applies the mode.  The loads go to L2: in the fused form other blocks of the same launch
-// wrote the partials.
-__device__ void finish_row(const double* part, int g, int r, const Finish& f) {
-  const double* pr = part + int64_t(r) * 2 * g;
-  double s = 0.0;
-  for (int i = threadIdx.x; i < g; i += blockDim.x) s += __ldcg(pr + i);
-  s = block_sum(s);
-  double s2 = 0.0;
-  if (f.mode == 2 || f.mode == 4) {
-    for (int i = threadIdx.x; i < g; i += blockDim.x) s2 += __ldcg(pr + g + i);
-    s2 = block_sum(s2);
-  }
-  if (threadIdx.x == 0) {
-    double* Sr = f.S ? f.S + r * S_NSCAL : nullptr;
-    if (f.mode == 0) f.out[r] = s;
-    else if (f.mode == 1) {
-      Sr[S_PAP] = s;
-      Sr[S_ALPHA] = (Sr[S_ACTIVE] != 0.0 && s != 0.0) ? Sr[S_RZ] / s : 0.0;
-    } else if (f.mode == 2 || f.mode == 3) {
-      const double rz = f.mode == 2 ? s2 : s;
-      if (f.mode == 2) Sr[S_RR] = s;
-      Sr[S_RZN] = rz;
-      Sr[S_BETA] = (Sr[S_ACTIVE] != 0.0 && Sr[S_RZ] != 0.0) ? rz / Sr[S_RZ] : 0.0;
-      Sr[S_RZ] = rz;
-    } else if (f.mode == 4) {
-      Sr[S_RR] = s;
-      Sr[S_RZ] = s2;
-    } else if (f.mode == 5) {
-      Sr[S_RR] = s;
-    }
-  }
-}
-
 __global__ void __launch_bounds__(kRedThreads) k_finish(const double* part, int g, double* out, int mode, double* S) {
   finish_row(part, g, blockIdx.x, Finish{out, mode, S, nullptr});
-}
-
-// Called by every thread after thread 0 stored the block's partials of row blockIdx.y: the last
-// block of the row to arrive sums the row (finish_row) and resets the counter for the next launch.
-__device__ __forceinline__ void finish_if_last(const double* part, const Finish& f) {
-  if (!f.count) return;
-  __shared__ unsigned last;
-  __threadfence();  // this block's partials are visible device-wide before it is counted
-  __syncthreads();
-  if (threadIdx.x == 0) last = atomicAdd(f.count + blockIdx.y, 1u) == gridDim.x - 1 ? 1u : 0u;
-  __syncthreads();
-  if (!last) return;
-  __threadfence();
-  finish_row(part, gridDim.x, blockIdx.y, f);
-  if (threadIdx.x == 0) f.count[blockIdx.y] = 0u;
 }
 
 // Per-block partial sums of x.y (and x2.y2).  Each thread keeps four independent
@@ -225,6 +134,61 @@ __global__ void __launch_bounds__(kRedThreads) k_cg_xr(int64_t n, int64_t ld, T*
     part[int64_t(rh) * 2 * gridDim.x + gridDim.x + blockIdx.x] = rz;
   }
   finish_if_last(part, fin);
+}
+
+// y = S p for a 125-point stencil on an (nx + 1) x (ny + 1) x (nz + 1) grid (the scaled fp16
+// tiled layout of stencil_at; entries toward nodes outside the grid are 0, and their loads are
+// clamped into it).  All sixteen 16-byte words of a row are loaded before the first is used.  DOT: also p.y, reduced like cg_alpha (Finish mode 1), so one launch
+// is a CG step's operator application and its alpha.  Fixed grid of at most kRedBlocks blocks.
+template <bool DOT>
+__global__ void __launch_bounds__(kRedThreads) k_stencil125(const __half* __restrict__ S,
+                                                            const float* __restrict__ scale,
+                                                            const float* __restrict__ p, float* __restrict__ y,
+                                                            int nx, int ny, int nz, double* part, Finish fin) {
+  const int px = nx + 1, pxy = px * (ny + 1), np = pxy * (nz + 1);
+  Dot2f acc;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < np; i += gridDim.x * blockDim.x) {
+    const int ix = i % px, iy = (i / px) % (ny + 1), iz = i / pxy;
+    int ox[5], oy[5], oz[5];
+#pragma unroll
+    for (int d = 0; d < 5; ++d) {
+      ox[d] = min(max(ix + d - 2, 0), nx);
+      oy[d] = px * min(max(iy + d - 2, 0), ny);
+      oz[d] = pxy * min(max(iz + d - 2, 0), nz);
+    }
+    const uint4* Si = reinterpret_cast<const uint4*>(S + stencil_at(0, i));
+    uint4 w[16];
+#pragma unroll
+    for (int k = 0; k < 16; ++k) w[k] = __ldcs(Si + 32 * k);
+    float sz[5] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f};  // one running sum per z plane
+#pragma unroll
+    for (int k = 0; k < 16; ++k) {
+      const uint32_t pair[4] = {w[k].x, w[k].y, w[k].z, w[k].w};
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        __half2 h2;
+        memcpy(&h2, &pair[j], 4);
+        const float2 c = __half22float2(h2);
+        const float cv[2] = {c.x, c.y};
+#pragma unroll
+        for (int e = 0; e < 2; ++e) {
+          const int o = 8 * k + 2 * j + e;
+          if (o < 125) {
+            const int dx = o % 5, dy = (o / 5) % 5, dz = o / 25;
+            sz[dz] = fmaf(cv[e], __ldg(p + (ox[dx] + oy[dy] + oz[dz])), sz[dz]);
+          }
+        }
+      }
+    }
+    const float s = scale[i] * (((sz[0] + sz[1]) + (sz[2] + sz[3])) + sz[4]);
+    y[i] = s;
+    if (DOT) acc.add(p[i], s);
+  }
+  if constexpr (DOT) {
+    const double t = block_sum(acc.value());
+    if (threadIdx.x == 0) part[blockIdx.x] = t;
+    finish_if_last(part, fin);
+  }
 }
 
 template <typename T> __global__ void k_cg_p(int64_t n, int64_t ld, const T* z, T* p, const double* S) {
@@ -587,6 +551,24 @@ mf_status cg_init_scalars(mf_ctx* ctx, const T* r, const T* z, int64_t n, int64_
 }
 template mf_status cg_init_scalars<double>(mf_ctx*, const double*, const double*, int64_t, int64_t, int, double*);
 template mf_status cg_init_scalars<float>(mf_ctx*, const float*, const float*, int64_t, int64_t, int, double*);
+
+mf_status stencil125_apply(mf_ctx* ctx, const void* Sv, const float* scale, const float* p, float* y, int nx, int ny,
+                           int nz, double* Scg) {
+  const __half* S = static_cast<const __half*>(Sv);
+  const int64_t np = int64_t(nx + 1) * (ny + 1) * (nz + 1);
+  if (np >= (int64_t(1) << 30)) return fail(MF_EUNSUPPORTED, "stencil grid too large for 32-bit indices");
+  const int g = int(std::min<int64_t>((np + kRedThreads - 1) / kRedThreads, kRedBlocks));
+  if (Scg) {
+    double* part;
+    MF_TRY(scratch(ctx, 2 * kRedBlocks, &part));
+    k_stencil125<true><<<g, kRedThreads, 0, ctx->stream>>>(S, scale, p, y, nx, ny, nz, part,
+                                                         Finish{nullptr, 1, Scg, counters(ctx)});
+  } else {
+    k_stencil125<false><<<g, kRedThreads, 0, ctx->stream>>>(S, scale, p, y, nx, ny, nz, nullptr, Finish{});
+  }
+  LAUNCH_CHECK();
+  return MF_OK;
+}
 
 template <typename T> mf_status cg_update_p(mf_ctx* ctx, int64_t n, int64_t ld, int nrhs, const T* z, T* p, double* S) {
   k_cg_p<T><<<dim3(grid_for(n), nrhs), 256, 0, ctx->stream>>>(n, ld, z, p, S);

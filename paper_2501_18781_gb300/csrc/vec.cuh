@@ -46,6 +46,22 @@ mf_status cg_update_xr(mf_ctx* ctx, int64_t n, int64_t ld, int nrhs, T* x, T* r,
                        const T* dinv, T* z, int zmode, double* S);
 // S[rz] = r.z and beta (preconditioner applied separately)
 template <typename T> mf_status cg_rz(mf_ctx* ctx, const T* r, const T* z, int64_t n, int64_t ld, int nrhs, double* S);
+// 125-point stencils on a grid of n nodes (offsets o = (ox + 2) + 5 (oy + 2) + 25 (oz + 2)) are
+// stored as fp16 entries scaled by a per-row fp32 factor (the row's largest magnitude, so every
+// entry lies in [-1, 1] and keeps 11 bits relative to the row's largest), rows padded to 128
+// entries (the last three 0), in tiles of 32 rows: within a tile, entry group o / 8 of all 32 rows,
+// then the next group, each row's eight entries one 16-byte word.  A warp's 16 coefficient loads
+// are then 16 consecutive 512-byte runs.  stencil_at: where entry o of row i lives (in halves);
+// stencil_halves: the size; the scales are a separate array of n floats.
+__host__ __device__ inline int64_t stencil_at(int o, int64_t i) {
+  return (i >> 5) * (128 * 32) + (o >> 3) * 256 + (i & 31) * 8 + (o & 7);
+}
+inline int64_t stencil_halves(int64_t n) { return (n + 31) / 32 * (128 * 32); }
+// y = S p for a 125-point stencil on the (nx + 1) x (ny + 1) x (nz + 1) grid (S: the fp16 entries,
+// scale: the row factors); with Scg non-NULL also Scg[pAp] = p.y and Scg[alpha] as cg_alpha sets
+// them, in the same launch
+mf_status stencil125_apply(mf_ctx* ctx, const void* S, const float* scale, const float* p, float* y, int nx, int ny,
+                           int nz, double* Scg);
 // p = z + beta p (z = r when z is NULL)
 template <typename T> mf_status cg_update_p(mf_ctx* ctx, int64_t n, int64_t ld, int nrhs, const T* z, T* p, double* S);
 // S[rr] = r.r, S[rz] = r.z (initial)

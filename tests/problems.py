@@ -19,6 +19,45 @@ def componentwise_ok(v, ref, bound, rtol):
     return worst <= rtol, worst
 
 
+def schur_reference(A, nu):
+    """The oracle's B D^-1 B^T (D: the 3 x 3 nodal blocks of A_uu) from an assembled Oseen matrix
+    with 3 nu velocity unknowns first: returns (S, |B| |D^-1| |B^T|) as sparse matrices."""
+    import scipy.sparse as sp
+    A = A.tocsr()
+    N = 3 * nu
+    B, BT, Auu = A[N:, :N], A[:N, N:], A[:N, :N]
+    i = np.arange(nu)
+    D = np.empty((nu, 3, 3))
+    for d in range(3):
+        for e in range(3):
+            D[:, d, e] = np.asarray(Auu[d * nu + i, e * nu + i]).ravel()
+    Dinv = np.linalg.inv(D)
+    rows = np.concatenate([d * nu + i for d in range(3) for e in range(3)])
+    cols = np.concatenate([e * nu + i for d in range(3) for e in range(3)])
+    Dsp = sp.csr_matrix((np.concatenate([Dinv[:, d, e] for d in range(3) for e in range(3)]), (rows, cols)),
+                        shape=(N, N))
+    return (B @ Dsp @ BT).tocsr(), (abs(B) @ abs(Dsp) @ abs(BT)).tocsr()
+
+
+def schur_fp16_bound(S, p, n):
+    """Error bound of the fp32 Schur stencil whose entries are stored as fp16 scaled by their row's
+    largest magnitude: per entry at most half an fp16 unit of 1, 2^-12 of the row maximum, so per
+    row 2^-12 max_o |S_io| times the sum of |p| over the 5 x 5 x 5 box of grid nodes (n + 1 per
+    axis) around the row's node."""
+    m = n + 1
+    P = np.abs(p).reshape(m, m, m)
+    box = np.zeros_like(P)
+    for dz in range(-2, 3):
+        for dy in range(-2, 3):
+            for dx in range(-2, 3):
+                sh = np.zeros_like(P)
+                sh[max(0, -dz):m - max(0, dz), max(0, -dy):m - max(0, dy), max(0, -dx):m - max(0, dx)] = \
+                    P[max(0, dz):m - max(0, -dz), max(0, dy):m - max(0, -dy), max(0, dx):m - max(0, -dx)]
+                box += sh
+    rowmax = np.asarray(abs(S).max(axis=1).todense()).ravel()
+    return 2.0 ** -12 * rowmax * box.ravel()
+
+
 def helmholtz(n, ctx=None, heaviside="tanh", coef_mode=0, octree=None):
     wl = syn.scaled(syn.HELMHOLTZ_SPHERE, n)
     if octree is None:

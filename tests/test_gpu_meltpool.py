@@ -6,7 +6,7 @@ import pytest
 import synthetic as syn
 from oracle import assemble as asm
 from oracle import mesh as omesh
-from problems import OSEEN_FACES, componentwise_ok
+from problems import OSEEN_FACES, componentwise_ok, schur_fp16_bound, schur_reference
 
 pytestmark = pytest.mark.gpu
 
@@ -70,6 +70,31 @@ def test_meltpool_oseen_apply_matches_oracle(ctx, flags):
                                  5e-5)
     assert ok, (flags, "fp32", worst)
     assert "meltpool" in P["op"].variant
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+def test_meltpool_schur_complement_approximation(ctx, dtype):
+    """B D^-1 B^T p with the melt-pool terms (the trace correction makes the nodal blocks D
+    nonsymmetric) against the oracle's assembled blocks; fp32 is the preconditioner's row-scaled
+    fp16 stencil, whose bound adds the storage error."""
+    P = meltpool(3, ctx, ("three", "darcy", "trace"))
+    nu = P["dmu"].n_dofs
+    Auu = P["A"].tocsr()[:3 * nu, :3 * nu]
+    i = np.arange(nu)
+    d01 = np.asarray(Auu[i, nu + i]).ravel() - np.asarray(Auu[nu + i, i]).ravel()
+    assert np.abs(d01).max() > 0  # the nodal blocks are nonsymmetric
+    S, Sabs = schur_reference(P["A"], nu)
+    p = syn.uniform_pm1(12, S.shape[0])
+    if dtype == "f32":
+        p = p.astype(np.float32).astype(np.float64)
+    tdt = torch.float64 if dtype == "f64" else torch.float32
+    got = P["op"].coupling("schur", torch.tensor(p, dtype=tdt, device="cuda")).cpu().double().numpy()
+    ref, bound = S @ p, Sabs @ np.abs(p)
+    if dtype == "f64":
+        ok, worst = componentwise_ok(got, ref, bound, 1e-12)
+    else:
+        ok, worst = componentwise_ok(got, ref, 5e-5 * bound + schur_fp16_bound(S, p, 3), 1.0)
+    assert ok, worst
 
 
 def test_meltpool_oseen_solve_with_block_preconditioner(ctx):
