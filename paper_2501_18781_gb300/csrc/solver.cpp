@@ -147,12 +147,13 @@ void back_substitute(const std::vector<double>& H, int m, int j, const std::vect
 
 // Block upper-triangular preconditioner of the Oseen saddle-point system [[A, B^T], [B, 0]]:
 //   P = [[A, B^T], [0, -S]],  P^-1 r:  z_p = -S^-1 r_p,  z_u = A^-1 (r_u - B^T z_p),
-// with S ~ S~ = B D^-1 B^T (D: the 3x3 nodal blocks of A) solved by Jacobi-CG (Jacobi from the
-// pressure scaling of the block-Jacobi setup) and A^-1 by a few D^-1-preconditioned GMRES
-// steps.  Both inner solves keep fp32 vectors and fp32 operator arithmetic (the Schur CG on
-// the coupling kernels B^T p and B u alone, the velocity GMRES on the whole operator applied
-// to [v; 0]); inner products accumulate in fp64, and the stopping test, Givens rotations and
-// triangular solve run on the device, so a preconditioner call needs no host round trip.
+// with S ~ S~ = B D^-1 B^T (D: the 3x3 nodal blocks of A), assembled once as a 125-point stencil
+// on the pressure grid and solved by Jacobi-CG (Jacobi: its inverse diagonal), and A^-1 by a few
+// D^-1-preconditioned GMRES steps.  Both inner solves keep fp32 vectors and fp32 operator
+// arithmetic (the Schur CG on the stencil, stored as row-scaled fp16; the velocity GMRES on the
+// whole operator applied to [v; 0]); inner products accumulate in fp64, and the stopping test,
+// Givens rotations and triangular solve run on the device, so a preconditioner call needs no host
+// round trip.
 struct OseenBlockTri {
   mf_op* op = nullptr;
   int64_t n = 0, nu = 0, nu3 = 0, np = 0;
@@ -197,6 +198,8 @@ struct OseenBlockTri {
     MF_TRY(ua.alloc(nu3));
     for (Vec<float>* v : {&pinv32, &xp, &rp, &zp, &pp, &sp}) MF_TRY(v->alloc(np));
     MF_TRY((convert<double, float>(c, np, op->pdiag64.as<double>(), pinv32.p)));
+    // Jacobi of the Schur CG: diag(S~)^-1 (the pressure scaling above where it is not positive)
+    MF_TRY(stencil_diag_inverse(c, stil.p, stscale.p, np, pinv32.p));
     ldv = basis_stride(n);
     MF_TRY(V.alloc(ldv * (ku + 1)));
     MF_TRY(t.alloc(n));
@@ -212,7 +215,7 @@ struct OseenBlockTri {
   double* schur_steps() { return op->ctx->scalars.as<double>() + kScalarsTri + 144; }
 
   // xp = S~^-1 r_p (r_p fp64): Jacobi-PCG from 0, smax steps; once ||r_k|| <= stol ||r_0|| (or
-  // p.S~p <= 0) the remaining steps leave x unchanged.
+  // p.S~p <= 0) the remaining steps' kernels return at once and x stays as it is.
   mf_status schur_solve(const double* r) {
     mf_ctx* c = op->ctx;
     double* S = c->scalars.as<double>() + kScalarsTri + 128;
@@ -225,9 +228,9 @@ struct OseenBlockTri {
     for (int k = 0; k < smax; ++k) {
       // sp = S~ pp and alpha in one launch
       MF_TRY(stencil125_apply(c, stil.p, stscale.p, pp.p, sp.p, gn[0], gn[1], gn[2], S));
-      MF_TRY(cg_update_xr<float>(c, np, np, 1, xp.p, rp.p, pp.p, sp.p, pinv32.p, zp.p, 1, S));
+      MF_TRY(cg_update_xr<float>(c, np, np, 1, xp.p, rp.p, pp.p, sp.p, pinv32.p, zp.p, 1, S, true));
       MF_TRY(dev_cg_tol_check(c, S, schur_steps()));
-      MF_TRY(cg_update_p<float>(c, np, np, 1, zp.p, pp.p, S));
+      MF_TRY(cg_update_p<float>(c, np, np, 1, zp.p, pp.p, S, true));
     }
     return MF_OK;
   }
@@ -242,20 +245,18 @@ struct OseenBlockTri {
     double* inv = G + 3 * m + 1;
     MF_TRY((dot<float, float>(c, w.p, w.p, nu3, ds)));
     MF_TRY(dev_gmres_begin(c, ds, G, m));
-    MF_CUDA_TRY(cudaMemcpyAsync(V.p, w.p, sizeof(float) * n, cudaMemcpyDeviceToDevice, c->stream));
-    MF_TRY(dev_scale<float>(c, nu3, inv, V.p));
     for (int j = 0; j < m; ++j) {
+      float* vj = V.p + j * ldv;
       float* vj1 = V.p + (j + 1) * ldv;
-      MF_TRY(block_jacobi_u32(c, nu, blk32.p, V.p + j * ldv, t.p));
+      // V_j = inv * (w or the previous step's unnormalised vector), t = D^-1 V_j, in one pass;
+      // only the velocity blocks of the basis are ever read
+      MF_TRY(block_jacobi_u32_scaled(c, nu, blk32.p, inv, j == 0 ? w.p : vj, vj, t.p));
       MF_TRY(apply_impl<float>(op, t.p, vj1, 1, n, false));
-      MF_CUDA_TRY(cudaMemsetAsync(vj1 + nu3, 0, sizeof(float) * np, c->stream));
       MF_TRY(multidot<float>(c, V.p, ldv, j + 1, vj1, nu3, ds));
       MF_TRY(multiaxpy<float>(c, V.p, ldv, j + 1, ds, -1.0, vj1, nu3));
       MF_TRY(multidot<float>(c, V.p, ldv, j + 1, vj1, nu3, ds + (m + 1)));
-      MF_TRY(multiaxpy<float>(c, V.p, ldv, j + 1, ds + (m + 1), -1.0, vj1, nu3));
-      MF_TRY((dot<float, float>(c, vj1, vj1, nu3, ds + 2 * (m + 1))));
-      MF_TRY(dev_gmres_column(c, ds, G, m, j));
-      MF_TRY(dev_scale<float>(c, nu3, inv, vj1));
+      MF_TRY(multiaxpy<float>(c, V.p, ldv, j + 1, ds + (m + 1), -1.0, vj1, nu3, ds + 2 * (m + 1)));
+      MF_TRY(dev_gmres_column(c, ds, G, m, j));  // sets inv = 1 / |V_{j+1}|
     }
     MF_TRY(dev_gmres_solve(c, G, m, m, y.p));
     MF_CUDA_TRY(cudaMemsetAsync(w.p, 0, sizeof(float) * nu3, c->stream));
@@ -659,8 +660,7 @@ mf_status gmres(mf_op* op, Prec<double>& P, const double* b, double* x, int m, d
       MF_TRY(multidot(c, V.p, ldv, j + 1, w, n, dh));
       MF_TRY(multiaxpy(c, V.p, ldv, j + 1, dh, -1.0, w, n));
       MF_TRY(multidot(c, V.p, ldv, j + 1, w, n, dh + (m + 1)));
-      MF_TRY(multiaxpy(c, V.p, ldv, j + 1, dh + (m + 1), -1.0, w, n));
-      MF_TRY(norm2_sq(c, w, n, dh + 2 * (m + 1) - 1));
+      MF_TRY(multiaxpy(c, V.p, ldv, j + 1, dh + (m + 1), -1.0, w, n, dh + 2 * (m + 1) - 1));  // and |w|^2
       MF_TRY(sync_copy(c, hh, dh, 2 * (m + 1)));
       for (int i = 0; i <= j; ++i) H[i * m + j] = hh[i] + hh[(m + 1) + i];
       double hn = std::sqrt(hh[2 * (m + 1) - 1]);

@@ -88,8 +88,9 @@ __global__ void __launch_bounds__(kRedThreads) k_dot2_partial(const TX* x, const
 template <typename T>
 __global__ void __launch_bounds__(kRedThreads) k_cg_xr(int64_t n, int64_t ld, T* x, T* r, const T* p, const T* Ap,
                                                        const T* dinv, T* z, int zmode, const double* S, double* part,
-                                                       Finish fin) {
+                                                       Finish fin, bool skip_inactive) {
   const int rh = blockIdx.y;
+  if (skip_inactive && S[rh * S_NSCAL + S_ACTIVE] == 0.0) return;  // this system has stopped
   const double alpha = S[rh * S_NSCAL + S_ALPHA];
   const int64_t o = rh * ld;
   double rr = 0.0, rz = 0.0;
@@ -145,6 +146,7 @@ __global__ void __launch_bounds__(kRedThreads) k_stencil125(const __half* __rest
                                                             const float* __restrict__ scale,
                                                             const float* __restrict__ p, float* __restrict__ y,
                                                             int nx, int ny, int nz, double* part, Finish fin) {
+  if (DOT && fin.S[S_ACTIVE] == 0.0) return;  // the CG this step belongs to has stopped
   const int px = nx + 1, pxy = px * (ny + 1), np = pxy * (nz + 1);
   Dot2f acc;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < np; i += gridDim.x * blockDim.x) {
@@ -191,8 +193,19 @@ __global__ void __launch_bounds__(kRedThreads) k_stencil125(const __half* __rest
   }
 }
 
-template <typename T> __global__ void k_cg_p(int64_t n, int64_t ld, const T* z, T* p, const double* S) {
+// pinv[i] = 1 / (row i's centre entry, o = 62) where that is positive; other entries unchanged
+__global__ void k_stencil_diag_inverse(const __half* __restrict__ S, const float* __restrict__ scale, int64_t n,
+                                       float* pinv) {
+  const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const float d = scale[i] * __half2float(S[stencil_at(62, i)]);
+  if (d > 0.0f) pinv[i] = 1.0f / d;
+}
+
+template <typename T>
+__global__ void k_cg_p(int64_t n, int64_t ld, const T* z, T* p, const double* S, bool skip_inactive) {
   const int rh = blockIdx.y;
+  if (skip_inactive && S[rh * S_NSCAL + S_ACTIVE] == 0.0) return;
   const T beta = T(S[rh * S_NSCAL + S_BETA]);
   const int64_t o = rh * ld;
   for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x)
@@ -232,6 +245,20 @@ __global__ void k_block_jacobi_soa32(int64_t nu, const float* __restrict__ blk, 
                                      float* __restrict__ z) {
   for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < nu; i += int64_t(gridDim.x) * blockDim.x) {
     const float r0 = r[i], r1 = r[nu + i], r2 = r[2 * nu + i];
+    z[i] = blk[i] * r0 + blk[nu + i] * r1 + blk[2 * nu + i] * r2;
+    z[nu + i] = blk[3 * nu + i] * r0 + blk[4 * nu + i] * r1 + blk[5 * nu + i] * r2;
+    z[2 * nu + i] = blk[6 * nu + i] * r0 + blk[7 * nu + i] * r1 + blk[8 * nu + i] * r2;
+  }
+}
+// dst = s[0] src (velocity blocks; dst may be src) and z = B^-1 dst per node, in one pass
+__global__ void k_block_jacobi_scaled32(int64_t nu, const float* __restrict__ blk, const double* s, const float* src,
+                                        float* dst, float* __restrict__ z) {
+  const float a = float(s[0]);
+  for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < nu; i += int64_t(gridDim.x) * blockDim.x) {
+    const float r0 = a * src[i], r1 = a * src[nu + i], r2 = a * src[2 * nu + i];
+    dst[i] = r0;
+    dst[nu + i] = r1;
+    dst[2 * nu + i] = r2;
     z[i] = blk[i] * r0 + blk[nu + i] * r1 + blk[2 * nu + i] * r2;
     z[nu + i] = blk[3 * nu + i] * r0 + blk[4 * nu + i] * r1 + blk[5 * nu + i] * r2;
     z[2 * nu + i] = blk[6 * nu + i] * r0 + blk[7 * nu + i] * r1 + blk[8 * nu + i] * r2;
@@ -353,10 +380,11 @@ __global__ void __launch_bounds__(kRedThreads) k_multidot_finish(const double* p
 
 // w += sign V h over k <= 64 vectors, h staged in shared memory (in T: fp32 data takes fp32
 // FMAs, since the fp64 pipe would bound this HBM-bound update); eight independent word loads
-// per step of the j loop.
-template <typename T, int W>
+// per step of the j loop.  NORM: also |w|^2 of the result, reduced into fin.out (Finish mode 0)
+// by the last block, which saves the separate norm pass of Gram-Schmidt.
+template <typename T, int W, bool NORM>
 __global__ void __launch_bounds__(256) k_multiaxpy(const T* V, int64_t ld, int k, const double* h, double sign, T* w,
-                                                   int64_t n) {
+                                                   int64_t n, double* part, Finish fin) {
   using Wd = Word<T, W>;
   __shared__ T hs[64];
   for (int j = threadIdx.x; j < k; j += blockDim.x) hs[j] = T(sign * h[j]);
@@ -365,6 +393,7 @@ __global__ void __launch_bounds__(256) k_multiaxpy(const T* V, int64_t ld, int k
   const int64_t nw = n / W, ldw = ld / W;
   const Wd* Vw = reinterpret_cast<const Wd*>(V);
   Wd* ww = reinterpret_cast<Wd*>(w);
+  DotAcc<T> nrm;
   for (int64_t i = t0; i < nw; i += st) {
     Wd acc = ww[i];
     int j = 0;
@@ -383,13 +412,22 @@ __global__ void __launch_bounds__(256) k_multiaxpy(const T* V, int64_t ld, int k
       for (int c = 0; c < W; ++c) acc.c[c] = fma(hs[j], x.c[c], acc.c[c]);
     }
     ww[i] = acc;
+    if (NORM)
+#pragma unroll
+      for (int c = 0; c < W; ++c) nrm.add(acc.c[c], acc.c[c]);
   }
   if (W > 1)
     for (int64_t i = nw * W + t0; i < n; i += st) {
       T acc = w[i];
       for (int j = 0; j < k; ++j) acc = fma(hs[j], V[j * ld + i], acc);
       w[i] = acc;
+      if (NORM) nrm.add(acc, acc);
     }
+  if constexpr (NORM) {
+    const double s = block_sum(nrm.value());
+    if (threadIdx.x == 0) part[blockIdx.x] = s;
+    finish_if_last(part, fin);
+  }
 }
 
 __global__ void k_splitmix(uint64_t seed, double* v, int64_t n) {
@@ -482,6 +520,12 @@ mf_status block_jacobi(mf_ctx* ctx, int64_t nu, int64_t np, const double* blk, c
   LAUNCH_CHECK();
   return MF_OK;
 }
+mf_status block_jacobi_u32_scaled(mf_ctx* ctx, int64_t nu, const float* blk, const double* s, const float* src,
+                                  float* dst, float* z) {
+  k_block_jacobi_scaled32<<<grid_for(nu), 256, 0, ctx->stream>>>(nu, blk, s, src, dst, z);
+  LAUNCH_CHECK();
+  return MF_OK;
+}
 mf_status block_jacobi_u32(mf_ctx* ctx, int64_t nu, const float* blk, const float* r, float* z) {
   k_block_jacobi_soa32<<<grid_for(nu), 256, 0, ctx->stream>>>(nu, blk, r, z);
   LAUNCH_CHECK();
@@ -516,18 +560,19 @@ template mf_status cg_alpha<float>(mf_ctx*, const float*, const float*, int64_t,
 
 template <typename T>
 mf_status cg_update_xr(mf_ctx* ctx, int64_t n, int64_t ld, int nrhs, T* x, T* r, const T* p, const T* Ap,
-                       const T* dinv, T* z, int zmode, double* S) {
+                       const T* dinv, T* z, int zmode, double* S, bool skip_inactive) {
   double* part;
   MF_TRY(scratch(ctx, 2 * kRedBlocks * size_t(nrhs), &part));
   k_cg_xr<T><<<dim3(kRedBlocks, nrhs), kRedThreads, 0, ctx->stream>>>(
-      n, ld, x, r, p, Ap, dinv, z, zmode, S, part, Finish{nullptr, zmode == 2 ? 5 : 2, S, counters(ctx)});
+      n, ld, x, r, p, Ap, dinv, z, zmode, S, part, Finish{nullptr, zmode == 2 ? 5 : 2, S, counters(ctx)},
+      skip_inactive);
   LAUNCH_CHECK();
   return MF_OK;
 }
 template mf_status cg_update_xr<double>(mf_ctx*, int64_t, int64_t, int, double*, double*, const double*, const double*,
-                                        const double*, double*, int, double*);
+                                        const double*, double*, int, double*, bool);
 template mf_status cg_update_xr<float>(mf_ctx*, int64_t, int64_t, int, float*, float*, const float*, const float*,
-                                       const float*, float*, int, double*);
+                                       const float*, float*, int, double*, bool);
 
 template <typename T> mf_status cg_rz(mf_ctx* ctx, const T* r, const T* z, int64_t n, int64_t ld, int nrhs, double* S) {
   double* part;
@@ -570,13 +615,21 @@ mf_status stencil125_apply(mf_ctx* ctx, const void* Sv, const float* scale, cons
   return MF_OK;
 }
 
-template <typename T> mf_status cg_update_p(mf_ctx* ctx, int64_t n, int64_t ld, int nrhs, const T* z, T* p, double* S) {
-  k_cg_p<T><<<dim3(grid_for(n), nrhs), 256, 0, ctx->stream>>>(n, ld, z, p, S);
+mf_status stencil_diag_inverse(mf_ctx* ctx, const void* S, const float* scale, int64_t n, float* pinv) {
+  k_stencil_diag_inverse<<<unsigned((n + 255) / 256), 256, 0, ctx->stream>>>(static_cast<const __half*>(S), scale, n,
+                                                                             pinv);
   LAUNCH_CHECK();
   return MF_OK;
 }
-template mf_status cg_update_p<double>(mf_ctx*, int64_t, int64_t, int, const double*, double*, double*);
-template mf_status cg_update_p<float>(mf_ctx*, int64_t, int64_t, int, const float*, float*, double*);
+
+template <typename T>
+mf_status cg_update_p(mf_ctx* ctx, int64_t n, int64_t ld, int nrhs, const T* z, T* p, double* S, bool skip_inactive) {
+  k_cg_p<T><<<dim3(grid_for(n), nrhs), 256, 0, ctx->stream>>>(n, ld, z, p, S, skip_inactive);
+  LAUNCH_CHECK();
+  return MF_OK;
+}
+template mf_status cg_update_p<double>(mf_ctx*, int64_t, int64_t, int, const double*, double*, double*, bool);
+template mf_status cg_update_p<float>(mf_ctx*, int64_t, int64_t, int, const float*, float*, double*, bool);
 
 template <typename T>
 mf_status cheb_init(mf_ctx* ctx, int64_t n, int64_t ld, int nrhs, const T* r, const T* dinv, double inv_theta, T* res,
@@ -633,18 +686,32 @@ template mf_status multidot<double>(mf_ctx*, const double*, int64_t, int, const 
 template mf_status multidot<float>(mf_ctx*, const float*, int64_t, int, const float*, int64_t, double*);
 
 template <typename T>
-mf_status multiaxpy(mf_ctx* ctx, const T* V, int64_t ld, int k, const double* h, double sign, T* w, int64_t n) {
+mf_status multiaxpy(mf_ctx* ctx, const T* V, int64_t ld, int k, const double* h, double sign, T* w, int64_t n,
+                    double* norm2) {
   if (k > 64) return fail(MF_EINVAL, "multiaxpy: at most 64 vectors");
-  if (k < 1) return MF_OK;
-  if (words16(V, ld) && words16(w, 0))
-    k_multiaxpy<T, 16 / sizeof(T)><<<grid_for(n), 256, 0, ctx->stream>>>(V, ld, k, h, sign, w, n);
-  else
-    k_multiaxpy<T, 1><<<grid_for(n), 256, 0, ctx->stream>>>(V, ld, k, h, sign, w, n);
+  if (k < 1 && !norm2) return MF_OK;
+  const bool words = words16(V, ld) && words16(w, 0);
+  const int g = grid_for(n);
+  if (norm2) {
+    double* part;
+    MF_TRY(scratch(ctx, size_t(g), &part));
+    const Finish fin{norm2, 0, nullptr, counters(ctx)};
+    if (words)
+      k_multiaxpy<T, 16 / sizeof(T), true><<<g, 256, 0, ctx->stream>>>(V, ld, k, h, sign, w, n, part, fin);
+    else
+      k_multiaxpy<T, 1, true><<<g, 256, 0, ctx->stream>>>(V, ld, k, h, sign, w, n, part, fin);
+  } else if (words) {
+    k_multiaxpy<T, 16 / sizeof(T), false><<<g, 256, 0, ctx->stream>>>(V, ld, k, h, sign, w, n, nullptr, Finish{});
+  } else {
+    k_multiaxpy<T, 1, false><<<g, 256, 0, ctx->stream>>>(V, ld, k, h, sign, w, n, nullptr, Finish{});
+  }
   LAUNCH_CHECK();
   return MF_OK;
 }
-template mf_status multiaxpy<double>(mf_ctx*, const double*, int64_t, int, const double*, double, double*, int64_t);
-template mf_status multiaxpy<float>(mf_ctx*, const float*, int64_t, int, const double*, double, float*, int64_t);
+template mf_status multiaxpy<double>(mf_ctx*, const double*, int64_t, int, const double*, double, double*, int64_t,
+                                     double*);
+template mf_status multiaxpy<float>(mf_ctx*, const float*, int64_t, int, const double*, double, float*, int64_t,
+                                    double*);
 
 mf_status fill_splitmix(mf_ctx* ctx, uint64_t seed, double* v, int64_t n) {
   k_splitmix<<<grid_for(n), 256, 0, ctx->stream>>>(seed, v, n);

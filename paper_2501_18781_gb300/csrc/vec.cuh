@@ -31,6 +31,9 @@ template <typename TS, typename TD> mf_status convert(mf_ctx* ctx, int64_t n, co
 // velocity part only, fp32 block inverses stored entry-major (entry e of node i at e nu + i):
 // z_u = B^-1 r_u per node
 mf_status block_jacobi_u32(mf_ctx* ctx, int64_t nu, const float* blk, const float* r, float* z);
+// velocity part only: dst = s[0] src (s device; dst may equal src), then z_u = B^-1 dst per node
+mf_status block_jacobi_u32_scaled(mf_ctx* ctx, int64_t nu, const float* blk, const double* s, const float* src,
+                                  float* dst, float* z);
 // the fp64 block inverses (9 per node, row major) as entry-major fp32
 mf_status blocks_soa32(mf_ctx* ctx, int64_t nu, const double* blk, float* out);
 
@@ -40,10 +43,11 @@ enum { S_RZ = 0, S_PAP = 1, S_ALPHA = 2, S_BETA = 3, S_RR = 4, S_RZN = 5, S_ACTI
 // S[pAp] = p.Ap, S[alpha] = active ? rz / pAp : 0
 template <typename T> mf_status cg_alpha(mf_ctx* ctx, const T* p, const T* Ap, int64_t n, int64_t ld, int nrhs, double* S);
 // x += alpha p; r -= alpha Ap; then (zmode 1) z = dinv .* r, S[rz] = r.z, beta; (zmode 0) z := r
-// implicitly (S[rz] = r.r); (zmode 2) only S[rr]
+// implicitly (S[rz] = r.r); (zmode 2) only S[rr].  skip_inactive: systems whose active flag is 0
+// are left untouched (an inner CG with an on-device stopping test)
 template <typename T>
 mf_status cg_update_xr(mf_ctx* ctx, int64_t n, int64_t ld, int nrhs, T* x, T* r, const T* p, const T* Ap,
-                       const T* dinv, T* z, int zmode, double* S);
+                       const T* dinv, T* z, int zmode, double* S, bool skip_inactive = false);
 // S[rz] = r.z and beta (preconditioner applied separately)
 template <typename T> mf_status cg_rz(mf_ctx* ctx, const T* r, const T* z, int64_t n, int64_t ld, int nrhs, double* S);
 // 125-point stencils on a grid of n nodes (offsets o = (ox + 2) + 5 (oy + 2) + 25 (oz + 2)) are
@@ -59,11 +63,15 @@ __host__ __device__ inline int64_t stencil_at(int o, int64_t i) {
 inline int64_t stencil_halves(int64_t n) { return (n + 31) / 32 * (128 * 32); }
 // y = S p for a 125-point stencil on the (nx + 1) x (ny + 1) x (nz + 1) grid (S: the fp16 entries,
 // scale: the row factors); with Scg non-NULL also Scg[pAp] = p.y and Scg[alpha] as cg_alpha sets
-// them, in the same launch
+// them, in the same launch, and nothing at all once Scg's active flag is 0
 mf_status stencil125_apply(mf_ctx* ctx, const void* S, const float* scale, const float* p, float* y, int nx, int ny,
                            int nz, double* Scg);
-// p = z + beta p (z = r when z is NULL)
-template <typename T> mf_status cg_update_p(mf_ctx* ctx, int64_t n, int64_t ld, int nrhs, const T* z, T* p, double* S);
+// pinv[i] = 1 / (the stencil's diagonal entry of row i) where that is positive, else unchanged
+mf_status stencil_diag_inverse(mf_ctx* ctx, const void* S, const float* scale, int64_t n, float* pinv);
+// p = z + beta p (z = r when z is NULL); skip_inactive as for cg_update_xr
+template <typename T>
+mf_status cg_update_p(mf_ctx* ctx, int64_t n, int64_t ld, int nrhs, const T* z, T* p, double* S,
+                      bool skip_inactive = false);
 // S[rr] = r.r, S[rz] = r.z (initial)
 template <typename T> mf_status cg_init_scalars(mf_ctx* ctx, const T* r, const T* z, int64_t n, int64_t ld, int nrhs, double* S);
 
@@ -79,9 +87,11 @@ template <typename T> mf_status add_into(mf_ctx* ctx, int64_t n, int64_t ld, int
 
 // GMRES: h[0..k) = V^T w (V: k vectors of length n, stride ld), into device h (fp64 sums)
 template <typename T> mf_status multidot(mf_ctx* ctx, const T* V, int64_t ld, int k, const T* w, int64_t n, double* h);
-// w += sign V h (h device, k entries)
+// w += sign V h (h device, k entries); with norm2 non-NULL also *norm2 = |w|^2 of the result
+// (device, fp64 sum), in the same launch
 template <typename T>
-mf_status multiaxpy(mf_ctx* ctx, const T* V, int64_t ld, int k, const double* h, double sign, T* w, int64_t n);
+mf_status multiaxpy(mf_ctx* ctx, const T* V, int64_t ld, int k, const double* h, double sign, T* w, int64_t n,
+                    double* norm2 = nullptr);
 // splitmix64 uniform [-1,1) vector (own implementation of the published generator)
 mf_status fill_splitmix(mf_ctx* ctx, uint64_t seed, double* v, int64_t n);
 // v[list[i]] = val

@@ -88,8 +88,8 @@ MELTPOOL_STEP = Workload(
                 darcy=dict(C=1e12, b=1.0, t_solidus=1933.0, t_liquidus=2200.0),
                 trace_correction=True, tol=1e-10, flow_tol=1e-10,
                 # solver settings measured best on the 64^3 step (reinit by fp32-inner defect
-                # correction; flow preconditioner: 5 velocity GMRES steps, Schur CG to 0.05 or 50 steps)
-                reinit_mixed=1, flow_velocity_steps=5, flow_schur_maxit=50, flow_schur_tol=0.05))
+                # correction; flow preconditioner: 5 velocity GMRES steps, Schur CG to 0.1 or 30 steps)
+                reinit_mixed=1, flow_velocity_steps=5, flow_schur_maxit=30, flow_schur_tol=0.1))
 
 
 def scaled(wl, n, levels=None, nrhs=None):
