@@ -32,7 +32,6 @@ mf_status dev_cg_tol_check(mf_ctx* c, double* S, double* steps);
 mf_status dev_gmres_begin(mf_ctx* c, const double* nrm2, double* G, int m);
 mf_status dev_gmres_column(mf_ctx* c, const double* h, double* G, int m, int j);
 mf_status dev_gmres_solve(mf_ctx* c, const double* G, int m, int j, double* y);
-template <typename T> mf_status dev_scale(mf_ctx* c, int64_t n, const double* s, T* v);
 // small device helpers (solver_kernels.cu)
 template <typename T> mf_status dev_scale_mul(mf_ctx* c, const double* s, const double* v, T* out, int64_t n);
 template <typename T> mf_status dev_scale_mul_back(mf_ctx* c, const double* s, const T* v, double* out, int64_t n);

@@ -92,11 +92,6 @@ __global__ void k_gmres_solve(const double* G, int m, int j, double* y) {
     y[i] = R[i * m + i] != 0.0 ? s / R[i * m + i] : 0.0;
   }
 }
-template <typename T> __global__ void k_scale_dev(int64_t n, const double* s, T* v) {
-  const T a = T(s[0]);
-  for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x)
-    v[i] *= a;
-}
 
 }  // namespace
 
@@ -154,11 +149,5 @@ mf_status dev_gmres_solve(mf_ctx* c, const double* G, int m, int j, double* y) {
   k_gmres_solve<<<1, 1, 0, c->stream>>>(G, m, j, y);
   LAUNCHED();
 }
-template <typename T> mf_status dev_scale(mf_ctx* c, int64_t n, const double* s, T* v) {
-  k_scale_dev<T><<<grid(n), 256, 0, c->stream>>>(n, s, v);
-  LAUNCHED();
-}
-template mf_status dev_scale<double>(mf_ctx*, int64_t, const double*, double*);
-template mf_status dev_scale<float>(mf_ctx*, int64_t, const double*, float*);
 
 }  // namespace mf
