@@ -252,8 +252,7 @@ struct OseenBlockTri {
       MF_TRY(block_jacobi_u32_scaled(c, nu, blk32.p, inv, j == 0 ? w.p : vj, vj, t.p));
       MF_TRY(apply_impl<float>(op, t.p, vj1, 1, n, false));
       MF_TRY(multidot<float>(c, V.p, ldv, j + 1, vj1, nu3, ds));
-      MF_TRY(multiaxpy<float>(c, V.p, ldv, j + 1, ds, -1.0, vj1, nu3));
-      MF_TRY(multidot<float>(c, V.p, ldv, j + 1, vj1, nu3, ds + (m + 1)));
+      MF_TRY(axpy_multidot<float>(c, V.p, ldv, j + 1, ds, -1.0, vj1, nu3, ds + (m + 1)));
       MF_TRY(multiaxpy<float>(c, V.p, ldv, j + 1, ds + (m + 1), -1.0, vj1, nu3, ds + 2 * (m + 1)));
       MF_TRY(dev_gmres_column(c, ds, G, m, j));  // sets inv = 1 / |V_{j+1}|
     }
@@ -657,8 +656,7 @@ mf_status gmres(mf_op* op, Prec<double>& P, const double* b, double* x, int m, d
       MF_TRY(P.apply(V.p + j * ldv, zj));
       MF_TRY(apply_impl<double>(op, zj, w, 1, n, transpose));
       MF_TRY(multidot(c, V.p, ldv, j + 1, w, n, dh));
-      MF_TRY(multiaxpy(c, V.p, ldv, j + 1, dh, -1.0, w, n));
-      MF_TRY(multidot(c, V.p, ldv, j + 1, w, n, dh + (m + 1)));
+      MF_TRY(axpy_multidot(c, V.p, ldv, j + 1, dh, -1.0, w, n, dh + (m + 1)));
       MF_TRY(multiaxpy(c, V.p, ldv, j + 1, dh + (m + 1), -1.0, w, n, dh + 2 * (m + 1) - 1));  // and |w|^2
       MF_TRY(sync_copy(c, hh, dh, 2 * (m + 1)));
       for (int i = 0; i <= j; ++i) H[i * m + j] = hh[i] + hh[(m + 1) + i];

@@ -371,6 +371,53 @@ __global__ void __launch_bounds__(kRedThreads, 4) k_multidot(const T* V, int64_t
     default: break;
   }
 }
+// The first pass's update and the second pass's products of classical Gram-Schmidt in one sweep,
+// for KG <= 8 vectors: w <- w + sign V h (T arithmetic, as k_multiaxpy), then part[g] = the
+// block's share of V_g . w (as k_multidot, same grid and per-thread order, so the results equal
+// the two separate launches bit for bit).
+template <typename T, int KG, int W>
+__global__ void __launch_bounds__(kRedThreads, 4) k_axpy_multidot(const T* V, int64_t ld, const double* h, double sign,
+                                                                  T* w, int64_t n, double* part) {
+  using Wd = Word<T, W>;
+  __shared__ T hs[KG];
+  if (threadIdx.x < KG) hs[threadIdx.x] = T(sign * h[threadIdx.x]);
+  __syncthreads();
+  DotAcc<T> acc[KG];
+  const int64_t t0 = int64_t(blockIdx.x) * blockDim.x + threadIdx.x, st = int64_t(gridDim.x) * blockDim.x;
+  const int64_t nw = n / W, ldw = ld / W;
+  const Wd* Vw = reinterpret_cast<const Wd*>(V);
+  Wd* ww = reinterpret_cast<Wd*>(w);
+  for (int64_t i = t0; i < nw; i += st) {
+    Wd y = ww[i];
+    Wd x[KG];
+#pragma unroll
+    for (int g = 0; g < KG; ++g) x[g] = Vw[g * ldw + i];
+#pragma unroll
+    for (int g = 0; g < KG; ++g)
+#pragma unroll
+      for (int c = 0; c < W; ++c) y.c[c] = fma(hs[g], x[g].c[c], y.c[c]);
+    ww[i] = y;
+#pragma unroll
+    for (int g = 0; g < KG; ++g)
+#pragma unroll
+      for (int c = 0; c < W; ++c) acc[g].add(x[g].c[c], y.c[c]);
+  }
+  if (W > 1)
+    for (int64_t i = nw * W + t0; i < n; i += st) {
+      T y = w[i];
+#pragma unroll
+      for (int g = 0; g < KG; ++g) y = fma(hs[g], V[g * ld + i], y);
+      w[i] = y;
+#pragma unroll
+      for (int g = 0; g < KG; ++g) acc[g].add(V[g * ld + i], y);
+    }
+#pragma unroll
+  for (int g = 0; g < KG; ++g) {
+    const double sg = block_sum(acc[g].value());
+    if (threadIdx.x == 0) part[int64_t(g) * gridDim.x + blockIdx.x] = sg;
+  }
+}
+
 __global__ void __launch_bounds__(kRedThreads) k_multidot_finish(const double* part, int g, double* h) {
   double s = 0.0;
   for (int i = threadIdx.x; i < g; i += blockDim.x) s += part[blockIdx.x * g + i];
@@ -685,6 +732,57 @@ template <typename T> mf_status multidot(mf_ctx* ctx, const T* V, int64_t ld, in
 template mf_status multidot<double>(mf_ctx*, const double*, int64_t, int, const double*, int64_t, double*);
 template mf_status multidot<float>(mf_ctx*, const float*, int64_t, int, const float*, int64_t, double*);
 
+// groups up to 6 fp32 or 2 fp64 vectors: within the 64 registers of 4 blocks per SM (larger groups
+// spill, and go to the two separate kernels)
+template <typename T> constexpr int kAxpyDotMax = sizeof(T) == 4 ? 6 : 2;
+
+template <typename T, int W>
+static void launch_axpy_multidot(mf_ctx* ctx, const T* V, int64_t ld, int k, const double* h, double sign, T* w,
+                                 int64_t n, double* part) {
+  const int g = kRedBlocks;
+  switch (k) {
+    case 1: k_axpy_multidot<T, 1, W><<<g, kRedThreads, 0, ctx->stream>>>(V, ld, h, sign, w, n, part); break;
+    case 2: k_axpy_multidot<T, 2, W><<<g, kRedThreads, 0, ctx->stream>>>(V, ld, h, sign, w, n, part); break;
+    case 3:
+      if constexpr (kAxpyDotMax<T> >= 3)
+        k_axpy_multidot<T, 3, W><<<g, kRedThreads, 0, ctx->stream>>>(V, ld, h, sign, w, n, part);
+      break;
+    case 4:
+      if constexpr (kAxpyDotMax<T> >= 4)
+        k_axpy_multidot<T, 4, W><<<g, kRedThreads, 0, ctx->stream>>>(V, ld, h, sign, w, n, part);
+      break;
+    case 5:
+      if constexpr (kAxpyDotMax<T> >= 5)
+        k_axpy_multidot<T, 5, W><<<g, kRedThreads, 0, ctx->stream>>>(V, ld, h, sign, w, n, part);
+      break;
+    default:
+      if constexpr (kAxpyDotMax<T> >= 6)
+        k_axpy_multidot<T, 6, W><<<g, kRedThreads, 0, ctx->stream>>>(V, ld, h, sign, w, n, part);
+      break;
+  }
+}
+
+template <typename T>
+mf_status axpy_multidot(mf_ctx* ctx, const T* V, int64_t ld, int k, const double* h, double sign, T* w, int64_t n,
+                        double* h2) {
+  if (k > kAxpyDotMax<T>) {
+    MF_TRY(multiaxpy<T>(ctx, V, ld, k, h, sign, w, n));
+    return multidot<T>(ctx, V, ld, k, w, n, h2);
+  }
+  if (k < 1) return MF_OK;
+  const int g = kRedBlocks;
+  double* part;
+  MF_TRY(scratch(ctx, size_t(g) * (k + 1) + 64, &part));
+  if (words16(V, ld) && words16(w, 0))
+    launch_axpy_multidot<T, 16 / sizeof(T)>(ctx, V, ld, k, h, sign, w, n, part);
+  else
+    launch_axpy_multidot<T, 1>(ctx, V, ld, k, h, sign, w, n, part);
+  LAUNCH_CHECK();
+  k_multidot_finish<<<k, kRedThreads, 0, ctx->stream>>>(part, g, h2);
+  LAUNCH_CHECK();
+  return MF_OK;
+}
+
 template <typename T>
 mf_status multiaxpy(mf_ctx* ctx, const T* V, int64_t ld, int k, const double* h, double sign, T* w, int64_t n,
                     double* norm2) {
@@ -712,6 +810,10 @@ template mf_status multiaxpy<double>(mf_ctx*, const double*, int64_t, int, const
                                      double*);
 template mf_status multiaxpy<float>(mf_ctx*, const float*, int64_t, int, const double*, double, float*, int64_t,
                                     double*);
+template mf_status axpy_multidot<double>(mf_ctx*, const double*, int64_t, int, const double*, double, double*, int64_t,
+                                         double*);
+template mf_status axpy_multidot<float>(mf_ctx*, const float*, int64_t, int, const double*, double, float*, int64_t,
+                                        double*);
 
 mf_status fill_splitmix(mf_ctx* ctx, uint64_t seed, double* v, int64_t n) {
   k_splitmix<<<grid_for(n), 256, 0, ctx->stream>>>(seed, v, n);

@@ -92,6 +92,12 @@ template <typename T> mf_status multidot(mf_ctx* ctx, const T* V, int64_t ld, in
 template <typename T>
 mf_status multiaxpy(mf_ctx* ctx, const T* V, int64_t ld, int k, const double* h, double sign, T* w, int64_t n,
                     double* norm2 = nullptr);
+// w += sign V h, then h2[0..k) = V^T w: the first Gram-Schmidt pass's update and the second
+// pass's products, in one sweep over V for up to 6 fp32 / 2 fp64 vectors (the same results as
+// multiaxpy then multidot, which it calls for more)
+template <typename T>
+mf_status axpy_multidot(mf_ctx* ctx, const T* V, int64_t ld, int k, const double* h, double sign, T* w, int64_t n,
+                        double* h2);
 // splitmix64 uniform [-1,1) vector (own implementation of the published generator)
 mf_status fill_splitmix(mf_ctx* ctx, uint64_t seed, double* v, int64_t n);
 // v[list[i]] = val
