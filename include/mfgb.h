@@ -66,7 +66,12 @@ const char* mf_last_error(void);
  * handles cudaStreamLegacy and cudaStreamPerThread; NULL asks for a non-blocking stream that
  * the library creates and owns (its work is then unordered with the legacy default stream).
  * A borrowed stream must outlive the context.  CUDA graphs are captured on a private stream
- * and launched on this one. */
+ * and launched on this one.
+ * One device per process: the first call with a device index that is valid (or made while no
+ * device is visible) binds the process to that device, because the operator tables and error
+ * flags are set up once per process; a later call naming another device returns
+ * MF_EUNSUPPORTED without touching the GPU.  Calls on a context must be made with its device
+ * current (cudaSetDevice / torch.cuda.set_device). */
 mf_status mf_context_create(int device, void* cuda_stream, mf_ctx** out);
 void mf_context_destroy(mf_ctx* ctx);
 /* Replace the context's stream (borrowed). */
@@ -202,9 +207,11 @@ mf_status mf_apply_transpose(mf_op* op, const void* src, void* dst, int nrhs, in
  * 64 Gauss points, the Gauss-point weights and a(phi) applied per row, then the transposed matrix
  * (tcgen05.mma kind::f16 with fp32 accumulation in tensor memory, operands split into bf16 hi + lo
  * parts and three products per contraction: fp32-class accuracy, about 29 times the flops of the
- * sum-factorised kernel).  nrhs vectors ld apart.  MF_EUNSUPPORTED for other operators;
- * MF_ETIMEOUT if an earlier tensor-core apply stopped at its one-second wait limit (the kernel
- * then frees its tensor memory and returns; the device stays usable).  Asynchronous. */
+ * sum-factorised kernel).  nrhs vectors ld apart.  MF_EUNSUPPORTED for other operators.
+ * A launch whose one-second wait limit runs out frees its tensor memory and returns (the device
+ * stays usable) and sets a flag: the next mf_apply_tc call returns MF_ETIMEOUT (the call is
+ * asynchronous, so it cannot see its own launch), and so does an mf_solve whose inner applies
+ * timed out; each timeout is reported once and the flag is cleared.  Asynchronous. */
 mf_status mf_apply_tc(mf_op* op, const float* src, float* dst, int nrhs, int64_t ld);
 /* The coupling blocks of the Oseen operator on their own: the pressure-gradient term of the
  * momentum balance and the continuity constraint (Section 2, eq. momentum_balance with
@@ -300,11 +307,13 @@ mf_status mf_dot(mf_ctx* ctx, const void* x, const void* y, int64_t n, int64_t l
  * Its block partial sums live in a static device array of 2 * 608 * 16 doubles (152 KB) that
  * every GPU loading the library holds until exit; hence 1 <= nvec <= 16 (larger nvec:
  * MF_EINVAL).  The first call on a device looks up that array's device address (with the
- * device current) and should come before any stream capture.  All calls share the array, so
- * calls that overlap on the GPU race; nothing in it needs clearing between calls.
+ * device current) and should come before any stream capture; the address is kept for the life
+ * of the process and does not survive cudaDeviceReset (make no call on a device after resetting
+ * it).  All calls share the array, so calls that overlap on the GPU race; nothing in it needs
+ * clearing between calls.
  * x, y: device vectors (MF_F64 or MF_F32) ld apart; out: device array of nvec doubles;
  * cuda_stream: the cudaStream_t to launch on (NULL = the legacy default stream).
- * Asynchronous; results equal mf_dot's (same fixed-grid reduction). */
+ * Asynchronous; results equal mf_dot's bit for bit (same fixed grid, same summation order). */
 mf_status mf_dot_noalloc(const void* x, const void* y, int64_t n, int64_t ld, int nvec, int dtype, double* out,
                          void* cuda_stream);
 

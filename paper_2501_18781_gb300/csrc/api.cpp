@@ -1,5 +1,6 @@
 // C ABI of libmfgb: contexts, meshes, DoF maps, operators, apply / transpose / diagonal.
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstring>
 #include <new>
@@ -11,6 +12,11 @@
 namespace mf {
 
 static thread_local std::string g_error;
+
+// The device this process is bound to (-1: none yet).  Constant tables, the tensor-core operand
+// image and the host-mapped error flags are uploaded once per process, so every context must
+// live on the same device.
+static std::atomic<int> g_bound_device{-1};
 
 void set_error(const std::string& msg) { g_error = msg; }
 mf_status fail(mf_status st, const std::string& msg) {
@@ -36,12 +42,27 @@ mf_status mf_context_create(int device, void* cuda_stream, mf_ctx** out) {
   MF_GUARD_BEGIN
   if (!out) return fail(MF_EINVAL, "out is NULL");
   *out = nullptr;
+  if (device < 0) return fail(MF_EINVAL, "device index out of range");
+  {
+    const int bound = g_bound_device.load();
+    if (bound >= 0 && bound != device)
+      return fail(MF_EUNSUPPORTED, "this process is bound to CUDA device " + std::to_string(bound) +
+                                       ": the library serves one device per process");
+  }
   int ndev = 0;
   if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
     cudaGetLastError();
+    int expect = -1;   // nothing can run without a device; the first request still fixes the binding
+    g_bound_device.compare_exchange_strong(expect, device);
     return fail(MF_ECUDA, "no CUDA device visible");
   }
-  if (device < 0 || device >= ndev) return fail(MF_EINVAL, "device index out of range");
+  if (device >= ndev) return fail(MF_EINVAL, "device index out of range");
+  {
+    int expect = -1;
+    if (!g_bound_device.compare_exchange_strong(expect, device) && expect != device)
+      return fail(MF_EUNSUPPORTED, "this process is bound to CUDA device " + std::to_string(expect) +
+                                       ": the library serves one device per process");
+  }
   MF_CUDA_TRY(cudaSetDevice(device));
   auto* c = new mf_ctx();
   c->device = device;
@@ -842,7 +863,7 @@ mf_status apply_tc(mf_op* op, const float* src, float* dst, int nrhs, int64_t ld
   for (int r = 0; r < nrhs; ++r) {
     MF_CUDA_TRY(cudaMemsetAsync(dst + r * ld, 0, sizeof(float) * op->n, op->ctx->stream));
     MF_TRY(launch_helmholtz_q3_tc(op->ctx, op->map[0], src + r * ld, dst + r * ld, op->qcoef_tc.as<float>(),
-                                  op->p.mass_coef, nullptr));
+                                  op->p.mass_coef));
   }
   op->variant = "helmholtz_q3/uniform/f32/tcgen05-bf16x3/dense";
   return MF_OK;

@@ -380,12 +380,21 @@ mf_status launch_tc_coef_layout(mf_ctx* ctx, const mf_dofmap* m, const float* in
   return MF_OK;
 }
 
+// Host-mapped error flag of the tensor-core kernel: set by a launch whose bounded wait ran out.
+static int* g_tc_h_err = nullptr;
+
+mf_status tc_take_error() {
+  if (!g_tc_h_err || !*reinterpret_cast<volatile int*>(g_tc_h_err)) return MF_OK;
+  *reinterpret_cast<volatile int*>(g_tc_h_err) = 0;   // reported once
+  return fail(MF_ETIMEOUT, "a tensor-core apply timed out waiting on its MMAs");
+}
+
 mf_status launch_helmholtz_q3_tc(mf_ctx* ctx, const mf_dofmap* m, const float* src, float* dst, const float* coef,
-                                 double mass, int* host_err_out) {
+                                 double mass) {
   static DevBuf image;
-  static int* h_err = nullptr;
   static int* d_err = nullptr;
   static bool ready = false;
+  int*& h_err = g_tc_h_err;
   if (!ready) {
     const std::vector<uint16_t> img = make_image();
     MF_TRY(image.alloc(kImage));
@@ -401,7 +410,7 @@ mf_status launch_helmholtz_q3_tc(mf_ctx* ctx, const mf_dofmap* m, const float* s
     MF_CUDA_TRY(cudaFuncSetAttribute(k_helmholtz_q3_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, int(kSmem + 1024)));
     ready = true;
   }
-  if (*reinterpret_cast<volatile int*>(h_err)) return fail(MF_ETIMEOUT, "a tensor-core apply timed out waiting on its MMAs");
+  MF_TRY(tc_take_error());   // a launch issued earlier on this process timed out
   TcArgs a{};
   a.src = src;
   a.dst = dst;
@@ -421,7 +430,6 @@ mf_status launch_helmholtz_q3_tc(mf_ctx* ctx, const mf_dofmap* m, const float* s
   k_helmholtz_q3_tc<<<grid, 512, kSmem + 1024, ctx->stream>>>(a);
   ctx->launches++;
   MF_CUDA_TRY(cudaGetLastError());
-  if (host_err_out) *host_err_out = *reinterpret_cast<volatile int*>(h_err);
   return MF_OK;
 }
 

@@ -111,11 +111,14 @@ template <typename T>
 mf_status launch_helmholtz_qk(mf_ctx* ctx, const mf_dofmap* m, const T* src, T* dst, const T* coef, double mass);
 mf_status launch_qk_diag(mf_ctx* ctx, const mf_dofmap* m, const double* coef, double mass, double* diag);
 // Q3 Helmholtz on the tensor cores (fp32 vectors, dst accumulated; coef per tile of 128 cells,
-// [tile][q][row], from launch_tc_coef_layout); host_err_out: the error flag left by earlier
-// launches (may be NULL)
+// [tile][q][row], from launch_tc_coef_layout).  A launch returns MF_ETIMEOUT when an earlier one
+// stopped at its bounded wait.
 mf_status launch_tc_coef_layout(mf_ctx* ctx, const mf_dofmap* m, const float* in, float* out);
 mf_status launch_helmholtz_q3_tc(mf_ctx* ctx, const mf_dofmap* m, const float* src, float* dst, const float* coef,
-                                 double mass, int* host_err_out);
+                                 double mass);
+// MF_ETIMEOUT (once, then the flag is cleared) if a tensor-core launch timed out; read it after
+// the stream has synchronised to cover the launches of the last call
+mf_status tc_take_error();
 // laser top-face load and its parameter derivatives (uniform maps)
 mf_status launch_laser(mf_ctx* ctx, const mf_dofmap* m, const double lz[5], double* f, double* dF);
 // dJ/dk_q = -w_q h grad(lambda) . grad(theta), [cell][27]

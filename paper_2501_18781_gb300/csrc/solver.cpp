@@ -869,7 +869,10 @@ mf_status mf_solve(mf_op* op, const mf_solver_params* sp, const double* b, doubl
   try {
     if (!op || !sp || !b || !x) return fail(MF_EINVAL, "NULL argument");
     if (nrhs < 1 || nrhs > 64) return fail(MF_EINVAL, "nrhs must be in 1..64");
-    return solve_impl(op, sp, b, x, nrhs, info, false);
+    const mf_status st = solve_impl(op, sp, b, x, nrhs, info, false);
+    // the solve has synchronised: a tensor-core apply inside it that timed out is reported here
+    const mf_status tc = tc_take_error();
+    return tc != MF_OK ? tc : st;
   } catch (...) {
     return fail(MF_ENOMEM, "exception in mf_solve");
   }

@@ -44,6 +44,34 @@ def test_context_without_gpu_fails_cleanly(lib):
     assert b"CUDA" in lib.mf_last_error()
 
 
+def test_second_device_is_rejected_before_any_cuda_call():
+    """The library serves one device per process: after a context request for device 0 (which
+    succeeds with a GPU and fails with MF_ECUDA without one), a request for device 1 is refused with
+    MF_EUNSUPPORTED, and device 0 is still accepted.  Runs in a fresh process because the binding is
+    process-wide."""
+    import subprocess
+    import sys
+    code = (
+        "import ctypes as C, sys\n"
+        f"sys.path.insert(0, {ROOT!r})\n"
+        "from paper_2501_18781_gb300 import _lib\n"
+        "lib = _lib.load()\n"
+        "h = C.c_void_p()\n"
+        "a = lib.mf_context_create(0, None, C.byref(h))\n"
+        "if a == 0: lib.mf_context_destroy(h)\n"
+        "g = C.c_void_p()\n"
+        "b = lib.mf_context_create(1, None, C.byref(g))\n"
+        "msg = lib.mf_last_error().decode()\n"
+        "c = lib.mf_context_create(0, None, C.byref(h))\n"
+        "if c == 0: lib.mf_context_destroy(h)\n"
+        "print(a, b, c, 'device 0' in msg and 'one device per process' in msg, bool(g.value))\n")
+    out = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, timeout=300)
+    assert out.returncode == 0, out.stderr
+    a, b, c, msg_ok, handle = out.stdout.split()
+    assert int(a) in (_lib.MF_OK, _lib.MF_ECUDA) and int(c) == int(a)
+    assert int(b) == _lib.MF_EUNSUPPORTED and msg_ok == "True" and handle == "False"
+
+
 def _compare_maps(ours, theirs):
     cm, rp, cols, w = theirs.export()
     e = ours.export()
