@@ -1,14 +1,22 @@
 #!/usr/bin/env python
-"""Benchmark: matrix-free operator apply throughput (GDoF/s) with its roofline, and the
-time of an implicit heat-step solve in fp64 vs mixed fp32/fp64 precision.
+"""Benchmark: matrix-free operator apply throughput (GDoF/s) with its roofline, and the time of the
+implicit heat-step solve in fp64 vs mixed fp32/fp64 precision.
 
-One step = one application of the linearised incompressible Navier-Stokes (Oseen) operator,
-Q2 velocity / Q1 pressure on a uniform 64^3 mesh (6,714,692 DoFs), fp64, with density and
-viscosity from a tanh-smoothed level set (1000:1, 100:1) and a seeded convection field: gather,
-Gauss-point values and gradients, pointwise physics, integration and scatter-add, all in the
-library's CUDA kernels.  Inputs are resident in HBM; L2 is flushed between timed steps.
+One step = one application of the implicit heat-step operator (rho c_p / dt) M + K(k(T^n)) with
+k(T) = k0 (1 + 0.5 T / T_b), Q2 on a uniform 128^3 mesh of the 600 um box (257^3 = 16,974,593
+DoFs, Dirichlet bottom face), in fp64: gather, Gauss-point values and gradients, conductivity from
+the interpolated previous temperature, integration and scatter-add, all in the library's CUDA
+kernels.  Inputs are resident in HBM; L2 is flushed between timed steps.
 
-    python bench.py [--steps K] [--warmup W] [--impl ours|reference] [--no-solve]
+The same JSON line carries the other workloads of the run (each measured once, bounded): the fp32
+and double-float applies and the laser-driven heat-step solve (fp64 CG vs fp32-inner defect
+correction) on the same mesh; the Oseen Q2/Q1 operator on 64^3 (applies, FGMRES solve, interface
+source loads); the adaptive-octree reinitialisation with 8 right-hand sides per launch; the 16^3
+Helmholtz Jacobi-CG in a CUDA graph; the heat-step adjoint gradient on 64^3; the Q3/Q4 applies;
+one melt-pool algorithm step; and the oracle on the host cores.
+
+    python bench.py [--steps K] [--warmup W] [--impl ours|reference] [--quick] [--suite]
+    python bench.py --probe WORKLOAD [ARGS...]     build one workload, apply it a few times (for ncu)
 Under torchrun (N > 1) every rank runs an independent replica on its own GPU.
 """
 import argparse
@@ -25,14 +33,22 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "GDoF/s of matrix-free operator apply & %HBM roofline; CG solve time FP64 vs mixed"
-WORKLOAD = "oseen_q2q1_interface_64"
+WORKLOAD = "heat_laser_q2_128"
 HBM_FALLBACK_GBS = 6800.0
 FP64_PEAK_TFLOPS = 1.25      # GB300 FP64 (vector and tensor) rate of the profiling recipe's table
-# Algorithmic flops of one Oseen Q2/Q1 cell apply as each kernel variant performs it (FMA = 2).
-# The 1D sweeps skip the exact zeros and ones of the tables (the middle Gauss point is the middle
-# node; D[1][1] = 0): a value sweep costs 9 lines x 2 points x 5 = 90, an integration sweep
-# 9 x 10 = 90, a collocation derivative 5 (3 at the middle point), a test accumulation along one
-# line 6 (4 at the middle point).
+# Algorithmic flops of one scalar Q2 heat-cell apply as the kernel performs it (FMA = 2).  The 1D
+# sweeps skip the exact zeros and ones of the 3-point tables (the middle Gauss point is the middle
+# node; D[1][1] = 0): a value sweep costs 9 lines x 2 points x 5 = 90 (three sweeps 270), an
+# integration sweep 9 x 10 = 90 (three sweeps 270); the reference gradient at the 27 points costs
+# 3 x (9 x 3 + 18 x 5) = 351 and its transposed test accumulation 3 x (9 x 4 + 18 x 6) = 432; per
+# point the mass term w (m h^2) u (2), the conductivity factor w k and its three products (4) and the
+# value accumulation (1) make 27 x 7 = 189; the final h scaling 27: 1539 with k tabulated per Gauss
+# point.  With k evaluated in the kernel, the nodal T^n is swept to the Gauss points (270) and
+# k0 + s T applied (27 x 2): 1863.
+HEAT_FLOPS_PER_CELL = {"tabulated": 1539, "inkernel": 1863}
+# Algorithmic HBM bytes of one heat apply: read u, write v, read the nodal T^n (3 words per DoF).
+HEAT_WORDS_PER_DOF = 3
+# Algorithmic flops of one Oseen Q2/Q1 cell apply as each kernel variant performs it.
 # Gauss-point loop outside, on Gauss-point coefficients with the weight and the powers of h folded
 # in (w h^2 rho beta tabulated, so the value terms are multiply-adds only): value sweeps 3 x 270,
 # 27 points x 159 (pressure 15, 9 gradients 39, value terms 24, symmetric stress 15 with 2 mu formed
@@ -115,26 +131,70 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(self.rows)}
 
 
+KERNEL_SOURCES = ("apply_f64.cu", "apply_f32.cu", "apply_df64.cu", "apply_kernels.cuh", "cellops.cuh",
+                  "scalar_local.cuh", "df64.cuh")
+
+
 def kernel_hash():
     h = hashlib.sha256()
-    for f in ("apply_f64.cu", "apply_kernels.cuh", "cellops.cuh", "scalar_local.cuh", "df64.cuh"):
+    for f in KERNEL_SOURCES:
         with open(os.path.join(ROOT, "paper_2501_18781_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
 
 
-def ncu_traffic(workload):
+def ncu_traffic(key):
     """DRAM bytes per launch of the dominant kernel from the committed ncu summary, if it was
-    taken on the current kernel source (else None)."""
+    taken on the current kernel source (else None).  key: workload/arithmetic."""
     p = os.path.join(ROOT, "profiles", "dram_traffic.txt")
     if not os.path.exists(p):
         return None
     kh = kernel_hash()
     for line in open(p):
         parts = line.split()
-        if len(parts) >= 3 and not line.startswith("#") and parts[0] == workload and parts[1] == kh:
+        if len(parts) >= 3 and not line.startswith("#") and parts[0] == key and parts[1] == kh:
             return float(parts[2])
     return None
+
+
+# ----------------------------------------------------------------------------- workload builders
+
+def build_heat(ctx, n=128, autotune=True, coef_mode=None):
+    """The implicit heat-step operator of the 128^3 laser workload: Q2 on the 600 um box, Dirichlet
+    bottom face, k(T^n) from the seeded hot-spot temperature.  Returns (op, map, T^n tensor)."""
+    import torch
+    import synthetic as syn
+    from paper_2501_18781_gb300 import DofMap, Mesh, Operator
+    wl = syn.scaled(syn.HEAT_LASER, n)
+    p = wl.params
+    m = DofMap(Mesh.uniform(ctx, n, wl.lo, wl.hi), 2, 1 << 4)
+    x = m.coords()
+    T_prev = torch.tensor(syn.heat_initial_temperature(*x.T, p["laser"]["radius"], wl.hi[2]), device="cuda")
+    kw = {} if coef_mode is None else {"coef_mode": coef_mode}
+    op = Operator(ctx, "heat", [m], rhocp=p["rhocp"], dt=p["dt"], k0=p["k0"], t_boil=p["t_boil"], **kw)
+    op.set_field("t_prev", T_prev)
+    if autotune:
+        op.autotune()   # set-up: coefficient mode, launch shape, fp64 vs double-float
+    return op, m, T_prev
+
+
+def heat_step_rhs(ctx, m, T_prev, n=128):
+    """Right-hand side of the laser-driven heat step for theta = T - T_ref: (rho c_p / dt) M theta^n +
+    the top-face load of eq. (laser_gauss) (200 W, 50 um), Dirichlet rows 0.  The mass term is the
+    library's apply of the same map's heat operator with k0 = 0, the laser load its mf_laser_load."""
+    import torch
+    import synthetic as syn
+    from paper_2501_18781_gb300 import Operator
+    wl = syn.scaled(syn.HEAT_LASER, n)
+    p = wl.params
+    mass = Operator(ctx, "heat", [m], rhocp=p["rhocp"], dt=p["dt"], k0=0.0, t_boil=p["t_boil"], coef_mode=1)
+    mass.set_field("t_prev", T_prev)
+    theta = T_prev - p["t_ref"]
+    lz = p["laser"]
+    b = mass.apply(theta) + mass.laser_load(lz["power"], lz["radius"], lz["x0"], lz["y0"], lz["absorptivity"])
+    d = torch.tensor(m.export(cell_map=False, constraints=False, coords=False)["dirichlet"], device="cuda")
+    b[d] = 0.0
+    return b
 
 
 def build_oseen(ctx, n=64):
@@ -159,17 +219,42 @@ def build_oseen(ctx, n=64):
     return op, mu, mp, mesh
 
 
-def time_apply(op, src, dst, steps, warmup, flush):
+def build_reinit_octree(ctx, base=None, levels=None, autotune=True):
+    """The adaptive-octree reinitialisation workload: base^3 + levels band refinement around the
+    seeded deformed sphere, Q2 with hanging-node constraints."""
+    import torch
+    import synthetic as syn
+    from paper_2501_18781_gb300 import DofMap, Mesh, Operator
+    wl = syn.REINIT_OCTREE
+    base = base or wl.n
+    levels = wl.levels if levels is None else levels
+    eps = 2.0 / (base << levels)
+    d = lambda X, Y, Z: syn.deformed_sphere_distance(X, Y, Z, wl.seed)
+    leaves = syn.refine_band_leaves(base, levels, d, eps)
+    m = DofMap(Mesh.octree(ctx, base, levels, leaves), 2, 0)
+    x = m.coords()
+    phi = torch.tensor(syn.initial_level_set(syn.deformed_sphere_distance(*x.T, wl.seed), eps), device="cuda")
+    op = Operator(ctx, "reinit", [m], eps=eps, dtau=0.5 / (base << levels))
+    op.set_field("phi", phi)
+    op._keep = phi
+    if autotune:
+        op.autotune()
+    return op, m
+
+
+# ----------------------------------------------------------------------------- timing helpers
+
+def time_apply(op, src, dst, steps, warmup, flush, arith=None):
     import torch
     for _ in range(warmup):
-        op.apply(src, dst)
+        op.apply(src, dst, arith=arith)
     torch.cuda.synchronize()
     times = []
     for _ in range(steps):
         flush.zero_()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record()
-        op.apply(src, dst)
+        op.apply(src, dst, arith=arith)
         e1.record()
         e1.synchronize()
         times.append(e0.elapsed_time(e1) / 1e3)
@@ -193,19 +278,25 @@ def _event_ms(fn, reps=5, flush=None):
     return statistics.median(ts)
 
 
-def _apply_rates(op, n, nrhs, flush, reps=5):
-    """GDoF/s (DoF x RHS per second) of the fp64, double-float and fp32 applies."""
+def _apply_rates(op, n, nrhs, flush, reps=5, words=None):
+    """G DoF.RHS/s of the fp64, double-float and fp32 applies; with ``words`` (vector words per DoF
+    and right-hand side, fields per DoF) also the fraction of the measured HBM peak."""
     import torch
     import synthetic as syn
     u = torch.tensor(syn.uniform_pm1(1, n * nrhs), device="cuda")
     u32 = u.float()
     v, v32 = torch.empty_like(u), torch.empty_like(u32)
+    hbm = measured_peaks().get("hbm_gbs", HBM_FALLBACK_GBS)
     out = {}
-    for name, fn in (("f64", lambda: op.apply(u, v, nrhs=nrhs)),
-                     ("df64", lambda: op.apply(u, v, nrhs=nrhs, arith="df64")),
-                     ("f32", lambda: op.apply(u32, v32, nrhs=nrhs))):
+    for name, fn, wb in (("f64", lambda: op.apply(u, v, nrhs=nrhs), 8),
+                         ("df64", lambda: op.apply(u, v, nrhs=nrhs, arith="df64"), 8),
+                         ("f32", lambda: op.apply(u32, v32, nrhs=nrhs), 4)):
         ms = _event_ms(fn, reps, flush)
         out[name] = {"ms": ms, "gdofs": n * nrhs / ms / 1e6, "variant": op.variant}
+        if words is not None:
+            b = (words[0] * nrhs + words[1]) * wb * n
+            out[name]["hbm_frac"] = b / (ms * 1e-3) / 1e9 / hbm
+            out[name]["bytes_per_launch"] = b
     return out
 
 
@@ -222,14 +313,98 @@ def _packed_rates(op, n, nrhs, flush, reps=5):
     return out
 
 
-def workload_suite(ctx, flush):
-    """One bounded measurement per benchmark workload (the parity tests cover their numerics)."""
+def _timed_solve(op, b, reps=1, **kw):
+    """Set-up + warm-up solve, then the median of reps timed solves (host clock, synchronised)."""
+    import torch
+    op.solve(b, **kw)
+    torch.cuda.synchronize()
+    runs = []
+    for _ in range(reps):
+        t0 = time.perf_counter()
+        _, info = op.solve(b, **kw)
+        torch.cuda.synchronize()
+        runs.append((time.perf_counter() - t0, info))
+    sec, info = sorted(runs, key=lambda r: r[0])[len(runs) // 2]
+    return {"seconds": sec, "iterations": info["iterations"], "outer": info["outer_iterations"],
+            "rel_residual": info["rel_residual"], "status": info["status"]}
+
+
+# ----------------------------------------------------------------------------- sub-measurements
+
+HEAT_SOLVERS = {"fp64": dict(solver="cg", precond="chebyshev"),
+                "mixed": dict(solver="defect_correction", precond="chebyshev", inner_tol=1e-4, inner_maxit=100)}
+
+
+def heat_solve_comparison(ctx, op, m, T_prev, n=128):
+    """The implicit heat step on n^3 Q2 cells to 1e-10: fp64 CG with Chebyshev(4)-Jacobi vs fp32 inner
+    CG (same preconditioner in fp32) inside fp64 defect correction.  Right-hand side: the laser load
+    and (rho c_p / dt) M theta^n; also a seeded uniform right-hand side as a second case."""
+    import torch
+    import synthetic as syn
+    out = {"workload": f"heat_laser_q2_{n}", "n_dofs": m.n_dofs, "tol": 1e-10}
+    b = heat_step_rhs(ctx, m, T_prev, n)
+    for name, kw in HEAT_SOLVERS.items():
+        out[name] = _timed_solve(op, b, tol=1e-10, use_graph=True, **kw)
+    out["speedup_mixed_over_fp64"] = out["fp64"]["seconds"] / out["mixed"]["seconds"]
+    br = torch.tensor(syn.uniform_pm1(1, m.n_dofs), device="cuda")
+    br[torch.tensor(m.export(cell_map=False, constraints=False, coords=False)["dirichlet"], device="cuda")] = 0
+    rnd = {name: _timed_solve(op, br, tol=1e-10, use_graph=True, **kw) for name, kw in HEAT_SOLVERS.items()}
+    rnd["speedup_mixed_over_fp64"] = rnd["fp64"]["seconds"] / rnd["mixed"]["seconds"]
+    out["random_rhs"] = rnd
+    return out
+
+
+def oseen_workload(ctx, flush, n=64, solve=True):
+    """The Oseen Q2/Q1 operator on n^3: fp64 / double-float / fp32 applies with the FP64-pipe and HBM
+    rooflines of the fp64 kernel, the FGMRES solve, and the interface source loads."""
+    op, mu, mp, mesh = build_oseen(ctx, n)
+    rates = _apply_rates(op, op.n, 1, flush, reps=10)
+    ncells = mu.n_cells
+    flops = OSEEN_FLOPS_PER_CELL["qpoint-outer" if "qpoint-outer" in rates["f64"]["variant"] else "component-outer"] * ncells
+    hbm = measured_peaks().get("hbm_gbs", HBM_FALLBACK_GBS)
+    alg = 16 * op.n + OSEEN_BYTES_PER_VEL_NODE * mu.n_dofs
+    s64 = rates["f64"]["ms"] * 1e-3
+    out = {"workload": f"oseen_q2q1_interface_{n}", "n_dofs": op.n, "cells": ncells, "apply": rates,
+           "roofline_f64": {"bound": "alu", "achieved": flops / s64 / 1e12, "peak": FP64_PEAK_TFLOPS,
+                            "unit": "TFLOP/s", "frac": flops / s64 / 1e12 / FP64_PEAK_TFLOPS,
+                            "flops_per_launch": flops},
+           "hbm_f64": {"achieved": alg / s64 / 1e9, "peak": hbm, "unit": "GB/s", "frac": alg / s64 / 1e9 / hbm,
+                       "bytes_per_launch": alg},
+           "hbm_f32": {"bytes_per_launch": alg // 2,
+                       "frac": alg / 2 / (rates["f32"]["ms"] * 1e-3) / 1e9 / hbm}}
+    out["interface_sources"] = interface_sources_timing(ctx, op, mu, flush)
+    if solve:
+        out["solve"] = oseen_solve(ctx, op, mu, mp)
+    return out
+
+
+def reinit_octree_workload(ctx, flush, solves=True):
+    """Adaptive octree (base 32^3 + 3 levels, ~12.3M Q2 DoFs with hanging nodes), 8 right-hand sides
+    per launch: fp64 / double-float / fp32 batched and single applies with the fraction of HBM of the
+    algorithmic bytes (per right-hand side u read and v written, plus the nodal level set once:
+    136N bytes in fp64, 72N in fp32), and the 8-RHS mixed-precision solve to 1e-10."""
     import numpy as np
     import torch
     import synthetic as syn
+    wl = syn.REINIT_OCTREE
+    op, m = build_reinit_octree(ctx)
+    r = {"workload": wl.name, "n_dofs": m.n_dofs, "cells": m.n_cells, "hanging_nodes": m.n_constraints,
+         "nrhs": wl.nrhs,
+         "apply_batched": _apply_rates(op, m.n_dofs, wl.nrhs, flush, reps=3, words=(2, 1)),
+         "apply_single": _apply_rates(op, m.n_dofs, 1, flush, reps=3, words=(2, 1))}
+    if solves:
+        B = torch.tensor(np.concatenate([syn.uniform_pm1(s, m.n_dofs) for s in range(1, wl.nrhs + 1)]), device="cuda")
+        r["mixed_solve_8rhs"] = _timed_solve(op, B, nrhs=wl.nrhs, solver="defect_correction", precond="chebyshev",
+                                             tol=1e-10, use_graph=True)
+    return r
+
+
+def helmholtz_workload(ctx):
+    """Helmholtz 16^3 (35,937 DoFs, L2-resident: launch-latency bound): apply rates and the Jacobi-CG
+    solve to 1e-10, launched directly and with the iteration body replayed as a CUDA graph."""
+    import torch
+    import synthetic as syn
     from paper_2501_18781_gb300 import DofMap, Mesh, Operator
-    res = {}
-    # Helmholtz 16^3 (L2-resident: launch-latency bound), Jacobi-CG in a CUDA graph
     wl = syn.HELMHOLTZ_SPHERE
     p = wl.params
     m = DofMap(Mesh.uniform(ctx, wl.n, wl.lo, wl.hi), 2, 0)
@@ -239,15 +414,20 @@ def workload_suite(ctx, flush):
     op.set_field("phi", torch.tensor(phi, device="cuda"))
     op.autotune()
     b = torch.tensor(syn.uniform_pm1(1, m.n_dofs), device="cuda")
-    r = {"n_dofs": m.n_dofs, "apply": _apply_rates(op, m.n_dofs, 1, None, reps=20)}
+    r = {"workload": wl.name, "n_dofs": m.n_dofs, "apply": _apply_rates(op, m.n_dofs, 1, None, reps=20)}
     for g in (False, True):
-        op.solve(b, solver="cg", precond="jacobi", use_graph=g)
-        t0 = time.perf_counter()
-        _, info = op.solve(b, solver="cg", precond="jacobi", use_graph=g)
-        r["cg_jacobi_graph" if g else "cg_jacobi"] = {"seconds": time.perf_counter() - t0, "iterations": info["iterations"],
-                                                      "rel_residual": info["rel_residual"]}
-    res[wl.name] = r
-    # heat-step adjoint on 64^3: forward + adjoint GMRES and both gradients
+        r["cg_jacobi_graph" if g else "cg_jacobi"] = _timed_solve(op, b, reps=3, solver="cg", precond="jacobi",
+                                                                  tol=1e-10, use_graph=g)
+    return r
+
+
+def heat_adjoint_workload(ctx, flush):
+    """Heat-step adjoint on 64^3 (2,146,689 DoFs): forward GMRES, adjoint GMRES with the transposed
+    convection, the four laser-parameter gradients and dJ/dk_q; fp64 to 1e-10."""
+    import numpy as np
+    import torch
+    import synthetic as syn
+    from paper_2501_18781_gb300 import DofMap, Mesh, Operator
     wl = syn.HEAT_ADJOINT
     p = wl.params
     m = DofMap(Mesh.uniform(ctx, wl.n, wl.lo, wl.hi), 2, 1 << 4)
@@ -255,8 +435,9 @@ def workload_suite(ctx, flush):
     beta = np.array(syn.convection_field(*x.T, wl.seed, wl.lo, wl.hi))
     kq = syn.kq_field(m.n_cells * 27, wl.seed, p["k0"])
     op = Operator(ctx, "heat", [m], rhocp=p["rhocp"], dt=p["dt"], k0=p["k0"], t_boil=p["t_boil"])
-    op.set_field("beta", torch.tensor(beta.ravel(), device="cuda"))
-    op.set_field("k_qpoint", torch.tensor(kq, device="cuda"))
+    keep = [torch.tensor(beta.ravel(), device="cuda"), torch.tensor(kq, device="cuda")]
+    op.set_field("beta", keep[0])
+    op.set_field("k_qpoint", keep[1])
     ztop = wl.hi[2]
     lz = p["laser"]
     th_prev = syn.heat_initial_temperature(*x.T, lz["radius"], ztop) - p["t_ref"]
@@ -265,175 +446,12 @@ def workload_suite(ctx, flush):
     lzt = (lz["power"], lz["radius"], lz["x0"], lz["y0"], lz["absorptivity"])
     kw = dict(solver="gmres", precond="jacobi", tol=1e-10, restart=50)
     op.heat_step_gradient(lzt, tp, tt, p["box_half"], p["box_depth"], **kw)
+    torch.cuda.synchronize()
     t0 = time.perf_counter()
     J, g, gk, _, _ = op.heat_step_gradient(lzt, tp, tt, p["box_half"], p["box_depth"], **kw)
     torch.cuda.synchronize()
-    res[wl.name] = {"n_dofs": m.n_dofs, "gradient_seconds": time.perf_counter() - t0, "J": J,
-                    "dJ_dlaser": g, "apply": _apply_rates(op, m.n_dofs, 1, flush)}
-    # adaptive octree reinitialisation, 8 right-hand sides batched per launch, mixed precision
-    wl = syn.REINIT_OCTREE
-    d = lambda X, Y, Z: syn.deformed_sphere_distance(X, Y, Z, wl.seed)
-    leaves = syn.refine_band_leaves(wl.n, wl.levels, d, wl.eps)
-    mesh = Mesh.octree(ctx, wl.n, wl.levels, leaves)
-    m = DofMap(mesh, 2, 0)
-    x = m.coords()
-    phi = syn.initial_level_set(syn.deformed_sphere_distance(*x.T, wl.seed), wl.eps)
-    hmin = 1.0 / (wl.n << wl.levels)
-    op = Operator(ctx, "reinit", [m], eps=wl.eps, dtau=0.5 * hmin)
-    op.set_field("phi", torch.tensor(phi, device="cuda"))
-    op.autotune()
-    B = torch.tensor(np.concatenate([syn.uniform_pm1(s, m.n_dofs) for s in range(1, wl.nrhs + 1)]), device="cuda")
-    r = {"n_dofs": m.n_dofs, "cells": m.n_cells, "hanging_nodes": m.n_constraints, "nrhs": wl.nrhs,
-         "apply_batched": _apply_rates(op, m.n_dofs, wl.nrhs, flush, reps=3),
-         "apply_single": _apply_rates(op, m.n_dofs, 1, flush, reps=3),
-         "apply_batched_packed16": _packed_rates(op, m.n_dofs, wl.nrhs, flush, reps=3)}
-    kw = dict(solver="defect_correction", precond="chebyshev", tol=1e-10, use_graph=True)
-    op.solve(B, nrhs=wl.nrhs, **kw)
-    t0 = time.perf_counter()
-    _, info = op.solve(B, nrhs=wl.nrhs, **kw)
-    torch.cuda.synchronize()
-    r["mixed_solve_8rhs"] = {"seconds": time.perf_counter() - t0, "inner_iterations": info["iterations"],
-                             "outer": info["outer_iterations"], "rel_residual": info["rel_residual"],
-                             "status": info["status"]}
-    for arith in ("bf16", "f16"):
-        op.solve(B, nrhs=wl.nrhs, inner_arith=arith, **kw)
-        t0 = time.perf_counter()
-        _, info = op.solve(B, nrhs=wl.nrhs, inner_arith=arith, **kw)
-        torch.cuda.synchronize()
-        r[f"mixed_solve_8rhs_inner_{arith}"] = {"seconds": time.perf_counter() - t0,
-                                                "inner_iterations": info["iterations"],
-                                                "outer": info["outer_iterations"], "rel_residual": info["rel_residual"],
-                                                "status": info["status"]}
-    res[wl.name] = r
-    return res
-
-
-def heat_solve_comparison(ctx, n=128):
-    """Implicit heat step on n^3 Q2 cells: fp64 CG with Chebyshev(4)-Jacobi vs fp32 inner CG
-    (same preconditioner in fp32) inside fp64 defect correction, both to 1e-10."""
-    import numpy as np
-    import torch
-    import synthetic as syn
-    from paper_2501_18781_gb300 import DofMap, Mesh, Operator
-    wl = syn.scaled(syn.HEAT_LASER, n)
-    p = wl.params
-    mesh = Mesh.uniform(ctx, n, wl.lo, wl.hi)
-    m = DofMap(mesh, 2, 1 << 4)
-    x = m.coords()
-    T_prev = syn.heat_initial_temperature(*x.T, p["laser"]["radius"], wl.hi[2])
-    op = Operator(ctx, "heat", [m], rhocp=p["rhocp"], dt=p["dt"], k0=p["k0"], t_boil=p["t_boil"], coef_mode=1)
-    op.set_field("t_prev", torch.tensor(T_prev, device="cuda"))
-    b = torch.tensor(syn.uniform_pm1(1, m.n_dofs), device="cuda")
-    b[torch.tensor(m.export(cell_map=False, constraints=False, coords=False)["dirichlet"], device="cuda")] = 0
-    out = {"workload": wl.name, "n_dofs": m.n_dofs, "tol": 1e-10}
-    for name, kw in (("fp64", dict(solver="cg", precond="chebyshev")),
-                     ("mixed", dict(solver="defect_correction", precond="chebyshev", inner_tol=1e-4,
-                                    inner_maxit=100))):
-        op.solve(b, tol=1e-10, use_graph=True, **kw)          # set-up + warm-up
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        _, info = op.solve(b, tol=1e-10, use_graph=True, **kw)
-        torch.cuda.synchronize()
-        out[name] = {"seconds": time.perf_counter() - t0, "iterations": info["iterations"],
-                     "outer": info["outer_iterations"], "rel_residual": info["rel_residual"],
-                     "status": info["status"]}
-    out["speedup_mixed_over_fp64"] = out["fp64"]["seconds"] / out["mixed"]["seconds"]
-    return out
-
-
-def cpu_oracle_apply(n_sample, budget_s=8.0):
-    """The oracle (assembled CSR from full-quadrature element matrices) applied on the host:
-    returns GDoF/s of its SpMV on an n_sample^3 instance of the same workload."""
-    import numpy as np
-    import synthetic as syn
-    from oracle import assemble as asm
-    from oracle import mesh as omesh
-    wl = syn.scaled(syn.OSEEN_INTERFACE, n_sample)
-    p = wl.params
-    dmu = omesh.uniform_dofmap(n_sample, wl.lo, wl.hi, 2, 0b011111)
-    dmp = omesh.uniform_dofmap(n_sample, wl.lo, wl.hi, 1, 0)
-    x = dmu.dof_coords()
-    t1, t2 = syn.wavy_plane_phases(wl.seed)
-    phi = syn.initial_level_set(syn.wavy_plane_distance(*x.T, t1, t2), wl.eps)
-    beta = np.array(syn.convection_field(*x.T, wl.seed, wl.lo, wl.hi))
-    A = asm.oseen_matrix(dmu, dmp, phi, beta, 1.0 / (p["dt_cfl"] * wl.h), p["rho_l"], p["rho_g"], p["mu_l"],
-                         p["mu_g"])
-    u = syn.uniform_pm1(1, A.shape[0])
-    A @ u
-    reps, t0 = 0, time.perf_counter()
-    while time.perf_counter() - t0 < budget_s:
-        A @ u
-        reps += 1
-    dt = time.perf_counter() - t0
-    return A.shape[0] * reps / dt / 1e9, A.shape[0], reps, dt
-
-
-def cpu_oracle_workloads():
-    """The oracle as it stands on the host (one core, scipy CSR): assembly, SpMV and Jacobi-CG to
-    1e-10 on the Helmholtz 16^3 workload (35,937 DoFs) -- the CPU side of the solve comparison."""
-    import numpy as np
-    import synthetic as syn
-    from oracle import assemble as asm
-    from oracle import krylov
-    from oracle import mesh as omesh
-    wl = syn.HELMHOLTZ_SPHERE
-    p = wl.params
-    t0 = time.perf_counter()
-    dm = omesh.uniform_dofmap(wl.n, wl.lo, wl.hi, 2)
-    phi = syn.initial_level_set(syn.sphere_distance(*dm.dof_coords().T), wl.eps)
-    A = asm.helmholtz_matrix(dm, phi, p["mass"], p["a_liquid"], p["a_gas"])
-    t_asm = time.perf_counter() - t0
-    b = syn.uniform_pm1(1, dm.n_dofs)
-    A @ b
-    reps, t0 = 0, time.perf_counter()
-    while time.perf_counter() - t0 < 2.0:
-        A @ b
-        reps += 1
-    t_spmv = (time.perf_counter() - t0) / reps
-    t0 = time.perf_counter()
-    _, its, res = krylov.cg(lambda v: A @ v, b, krylov.jacobi(A.diagonal()), tol=1e-10)
-    t_cg = time.perf_counter() - t0
-    return {"workload": wl.name, "n_dofs": dm.n_dofs, "cores": 1, "assembly_seconds": t_asm,
-            "spmv_gdofs": dm.n_dofs / t_spmv / 1e9, "cg_jacobi_seconds": t_cg, "cg_iterations": its,
-            "rel_residual": res}
-
-
-def reference_arm(args, rank, world):
-    out = {"impl": "reference", "metric": METRIC, "unit": "GDoF/s", "n_gpus": world, "steps": args.steps,
-           "warmup": args.warmup, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-           "dtype": "f64", "data": "synthetic"}
-    if rank != 0:
-        return None
-    import numpy as np
-    import synthetic as syn
-    from oracle import assemble as asm
-    from oracle import mesh as omesh
-    n_sample = 12
-    wl = syn.scaled(syn.OSEEN_INTERFACE, n_sample)
-    p = wl.params
-    dmu = omesh.uniform_dofmap(n_sample, wl.lo, wl.hi, 2, 0b011111)
-    dmp = omesh.uniform_dofmap(n_sample, wl.lo, wl.hi, 1, 0)
-    x = dmu.dof_coords()
-    t1, t2 = syn.wavy_plane_phases(wl.seed)
-    phi = syn.initial_level_set(syn.wavy_plane_distance(*x.T, t1, t2), wl.eps)
-    beta = np.array(syn.convection_field(*x.T, wl.seed, wl.lo, wl.hi))
-    A = asm.oseen_matrix(dmu, dmp, phi, beta, 1.0 / (p["dt_cfl"] * wl.h), p["rho_l"], p["rho_g"], p["mu_l"],
-                         p["mu_g"])
-    u = syn.uniform_pm1(1, A.shape[0])
-    for _ in range(args.warmup):
-        A @ u
-    t0 = time.perf_counter()
-    for _ in range(args.steps):
-        A @ u
-    dt = time.perf_counter() - t0
-    val = A.shape[0] * args.steps / dt / 1e9
-    out.update(value=val, ms_per_step=dt / args.steps * 1e3,
-               config={"workload": WORKLOAD, "sample": wl.name, "n_dofs": int(A.shape[0]),
-                       "note": "oracle: assembled-CSR SpMV of a 12^3 instance (assembly untimed)"},
-               cpu_baseline={"value": val, "unit": "GDoF/s", "cores": 1, "kind": "oracle",
-                             "sample": f"{wl.name}: assembled CSR SpMV, {args.steps} steps"},
-               e2e={"value": val, "unit": "GDoF/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0})
-    return out
+    return {"workload": wl.name, "n_dofs": m.n_dofs, "gradient_seconds": time.perf_counter() - t0, "J": J,
+            "dJ_dlaser": g, "apply": _apply_rates(op, m.n_dofs, 1, flush)}
 
 
 def oseen_solve(ctx, op, mu, mp):
@@ -582,9 +600,10 @@ def qk_flops_per_cell(k):
     return 2 * 12 * P ** 4 + 10 * P ** 3
 
 
-def helmholtz_qk(ctx, flush):
+def helmholtz_qk(ctx, flush, solves=False):
     """Q3 on 64^3 and Q4 on 48^3 cells (193^3 = 7,189,057 DoFs each), the sphere coefficient
-    a = 1 + 999 H(phi): fp64 and fp32 applies with the L2 flushed."""
+    a = 1 + 999 H(phi): fp64 and fp32 applies with the L2 flushed; with ``solves`` also the Q3
+    solve comparison."""
     import torch
     import synthetic as syn
     from paper_2501_18781_gb300 import DofMap, Mesh, Operator
@@ -614,6 +633,7 @@ def helmholtz_qk(ctx, flush):
             dense = 3 * 2 * 2 * 64 * 256 * m.n_cells
             r["tc_bf16x3"] = {"ms": ms, "gdofs": m.n_dofs / ms / 1e6, "tensor_tflops": dense / ms / 1e9,
                               "sum_factorised_tflops_equiv": fl / ms / 1e9, "variant": op.variant}
+        if k == 3 and solves:
             # solves to 1e-10: fp64 Jacobi-CG; defect correction with fp32 Chebyshev-CG inner solves on
             # the CUDA cores or on the tensor cores
             b = torch.tensor(syn.uniform_pm1(2, m.n_dofs), device="cuda")
@@ -652,18 +672,214 @@ def interface_sources_timing(ctx, op, mu, flush, reps=10):
             "outputs": "recoil force (3 n_u), dilation (n_p), cooling (n_u)"}
 
 
+
+
+# ----------------------------------------------------------------------------- the oracle on the host
+
+CPU_SAMPLE_N = 32   # 32^3 cells of the heat workload: 274,625 DoFs, 16.6M nonzeros (past the host caches)
+
+
+def _oracle_heat_matrix(n):
+    """The oracle's assembled heat-step matrix of the headline workload on an n^3 mesh (the same
+    recipe: 600 um box, Dirichlet bottom, k(T^n) from the seeded hot spot)."""
+    import synthetic as syn
+    from oracle import assemble as asm
+    from oracle import mesh as omesh
+    wl = syn.scaled(syn.HEAT_LASER, n)
+    p = wl.params
+    dm = omesh.uniform_dofmap(n, wl.lo, wl.hi, 2, 1 << 4)
+    T = syn.heat_initial_temperature(*dm.dof_coords().T, p["laser"]["radius"], wl.hi[2])
+    return asm.heat_matrix(dm, p["rhocp"], p["dt"], p["k0"], p["t_boil"], T_prev=T), wl.name
+
+
+def _spmv_worker(args):
+    """One host process: the rows [r0, r1) of the oracle's CSR matrix applied repeatedly for a fixed
+    wall-clock window; returns the rows processed."""
+    import numpy as np
+    import scipy.sparse as sp
+    data, indices, indptr, shape, u, window = args
+    A = sp.csr_matrix((data, indices, indptr), shape=shape)
+    u = np.asarray(u)
+    A @ u
+    reps, t0 = 0, time.perf_counter()
+    while time.perf_counter() - t0 < window:
+        A @ u
+        reps += 1
+    return shape[0] * reps, time.perf_counter() - t0
+
+
+def _host_cpu():
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except Exception:
+        pass
+    return {"os_cpu_count": os.cpu_count(), "model": model}
+
+
+def cpu_oracle_baseline(n=CPU_SAMPLE_N, window=4.0):
+    """The oracle as it stands (assembled CSR from full-quadrature element matrices, scipy's
+    one-thread CSR product) applying the headline operator on an n^3 sample: one host core, and all
+    host cores as row blocks in a pool of spawned processes (each applies its block for the same
+    wall-clock window; the rate is the rows processed by all over the window)."""
+    import multiprocessing as mp
+    import numpy as np
+    import synthetic as syn
+    t0 = time.perf_counter()
+    A, name = _oracle_heat_matrix(n)
+    t_asm = time.perf_counter() - t0
+    u = syn.uniform_pm1(1, A.shape[0])
+    one = _spmv_worker((A.data, A.indices, A.indptr, A.shape, u, window))
+    cores = os.cpu_count() or 1
+    bounds = np.linspace(0, A.shape[0], cores + 1).astype(np.int64)
+    jobs = []
+    for i in range(cores):
+        B = A[bounds[i]:bounds[i + 1]]
+        jobs.append((B.data, B.indices, B.indptr, B.shape, u, window))
+    with mp.get_context("spawn").Pool(cores) as pool:
+        res = pool.map(_spmv_worker, jobs)
+    all_rate = sum(r[0] for r in res) / max(r[1] for r in res) / 1e9
+    return {"value": all_rate, "unit": "GDoF/s", "cores": cores, "kind": "oracle",
+            "sample": f"{name} ({A.shape[0]} DoFs, {A.nnz} nonzeros): assembled-CSR SpMV, {cores} processes x "
+                      f"{window:.0f} s row blocks (assembly {t_asm:.1f} s untimed)",
+            "value_1core": one[0] / one[1] / 1e9, "host": _host_cpu()}
+
+
+def cpu_oracle_helmholtz_cg():
+    """The oracle's Jacobi-CG to 1e-10 on the Helmholtz 16^3 workload (35,937 DoFs, one core): the
+    CPU side of the graph-CG measurement."""
+    import synthetic as syn
+    from oracle import assemble as asm
+    from oracle import krylov
+    from oracle import mesh as omesh
+    wl = syn.HELMHOLTZ_SPHERE
+    p = wl.params
+    t0 = time.perf_counter()
+    dm = omesh.uniform_dofmap(wl.n, wl.lo, wl.hi, 2)
+    phi = syn.initial_level_set(syn.sphere_distance(*dm.dof_coords().T), wl.eps)
+    A = asm.helmholtz_matrix(dm, phi, p["mass"], p["a_liquid"], p["a_gas"])
+    t_asm = time.perf_counter() - t0
+    b = syn.uniform_pm1(1, dm.n_dofs)
+    t0 = time.perf_counter()
+    _, its, res = krylov.cg(lambda v: A @ v, b, krylov.jacobi(A.diagonal()), tol=1e-10)
+    return {"workload": wl.name, "n_dofs": dm.n_dofs, "cores": 1, "assembly_seconds": t_asm,
+            "cg_jacobi_seconds": time.perf_counter() - t0, "cg_iterations": its, "rel_residual": res}
+
+
+def reference_arm(args, rank, world):
+    """The oracle timed on the host cores on this arm's metric: each step one assembled-CSR product
+    of the headline heat operator on a 32^3 sample (assembly untimed), as the oracle stands (one core)."""
+    out = {"impl": "reference", "metric": METRIC, "unit": "GDoF/s", "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+           "dtype": "f64", "data": "synthetic"}
+    if rank != 0:
+        return None
+    import synthetic as syn
+    A, name = _oracle_heat_matrix(CPU_SAMPLE_N)
+    u = syn.uniform_pm1(1, A.shape[0])
+    for _ in range(args.warmup):
+        A @ u
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        A @ u
+    dt = time.perf_counter() - t0
+    val = A.shape[0] * args.steps / dt / 1e9
+    out.update(value=val, ms_per_step=dt / args.steps * 1e3,
+               config={"workload": WORKLOAD, "sample": name, "n_dofs": int(A.shape[0]),
+                       "note": f"oracle: assembled-CSR SpMV of a {CPU_SAMPLE_N}^3 instance (assembly untimed)"},
+               cpu_baseline={"value": val, "unit": "GDoF/s", "cores": 1, "kind": "oracle",
+                             "sample": f"{name}: assembled CSR SpMV, {args.steps} steps", "host": _host_cpu()},
+               e2e={"value": val, "unit": "GDoF/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0})
+    return out
+
+
+# ----------------------------------------------------------------------------- profiler probe
+
+def probe(argv):
+    """Build one workload and apply its operator a few times, for profilers such as ncu:
+        heat [n] [f32|f64|df64] [inkernel|tabulated]
+        oseen [n] [f32|f64|df64]
+        reinit [base] [levels] [f32|f64|df64] [nrhs]
+        oseen_solve [n] [maxit]
+        helmholtz_qk [k] [n] [f32|f64|tc]
+    Inputs come from the seeded generators; every apply runs in libmfgb."""
+    import numpy as np
+    import torch
+    import synthetic as syn
+    from paper_2501_18781_gb300 import Context, DofMap, Mesh, Operator, build_library
+    build_library()
+    ctx = Context(0)
+    kind = argv[0] if argv else "heat"
+
+    def run(op, n, prec, nrhs=1, reps=4):
+        u = torch.tensor(syn.uniform_pm1(1, n * nrhs), device="cuda")
+        if prec in ("f32", "tc"):
+            u = u.float()
+        v = torch.empty_like(u)
+        for _ in range(reps):
+            op.apply(u, v, nrhs=nrhs, arith=prec if prec in ("df64", "tc") else None)
+        torch.cuda.synchronize()
+        print(op.variant, n, "x", nrhs)
+
+    if kind == "heat":
+        n = int(argv[1]) if len(argv) > 1 else 128
+        prec = argv[2] if len(argv) > 2 else "f32"
+        mode = None if len(argv) <= 3 else (0 if argv[3] == "inkernel" else 1)
+        op, m, _ = build_heat(ctx, n, autotune=mode is None, coef_mode=mode)
+        run(op, m.n_dofs, prec)
+    elif kind in ("oseen", "oseen_solve"):
+        n = int(argv[1]) if len(argv) > 1 else 64
+        op, mu, mp, _ = build_oseen(ctx, n)
+        if kind == "oseen":
+            run(op, op.n, argv[2] if len(argv) > 2 else "f64")
+        else:
+            # flexible GMRES with the block-triangular preconditioner, capped at maxit iterations
+            maxit = int(argv[2]) if len(argv) > 2 else 400
+            b = syn.uniform_pm1(1, op.n)
+            d = mu.export(cell_map=False, constraints=False, coords=False)["dirichlet"]
+            b[np.concatenate([np.tile(d, 3), np.zeros(mp.n_dofs, bool)])] = 0
+            bt = torch.tensor(b, device="cuda")
+            for _ in range(2):
+                _, info = op.solve(bt, solver="gmres", precond="block_triangular", maxit=maxit, tol=1e-10)
+            torch.cuda.synchronize()
+            print(op.variant, n, info)
+    elif kind == "helmholtz_qk":
+        k = int(argv[1]) if len(argv) > 1 else 3
+        n = int(argv[2]) if len(argv) > 2 else 64
+        m = DofMap(Mesh.uniform(ctx, n), k, 0)
+        eps = 1.0 / (2 * n)
+        phi = syn.initial_level_set(syn.sphere_distance(*m.coords().T), eps)
+        op = Operator(ctx, "helmholtz", [m], mass_coef=1.0, a_liquid=1000.0, a_gas=1.0, eps=eps)
+        op.set_field("phi", torch.tensor(phi, device="cuda"))
+        run(op, m.n_dofs, argv[3] if len(argv) > 3 else "f32")
+    elif kind == "reinit":
+        base = int(argv[1]) if len(argv) > 1 else 16
+        levels = int(argv[2]) if len(argv) > 2 else 3
+        op, m = build_reinit_octree(ctx, base, levels, autotune=False)
+        run(op, m.n_dofs, argv[3] if len(argv) > 3 else "f32", int(argv[4]) if len(argv) > 4 else 1)
+    else:
+        raise SystemExit(f"unknown workload {kind}")
+
+
+# ----------------------------------------------------------------------------- main
+
 def main():
+    if len(sys.argv) > 1 and sys.argv[1] == "--probe":
+        probe(sys.argv[2:])
+        return
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--no-solve", action="store_true")
+    ap.add_argument("--quick", action="store_true", help="the headline workload only")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--suite", action="store_true", help="also measure the other benchmark workloads")
-    ap.add_argument("--meltpool-step", action="store_true", help="also time one melt-pool algorithm step")
-    ap.add_argument("--qk", action="store_true", help="also time the Q3 / Q4 Helmholtz applies")
-    ap.add_argument("--n", type=int, default=64)
+    ap.add_argument("--suite", action="store_true", help="also the melt-pool Oseen operator and the Q3 solves")
+    ap.add_argument("--n", type=int, default=128)
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -676,6 +892,12 @@ def main():
             print(json.dumps(out))
         return
 
+    # the oracle's host baseline first: its process pool is spawned before any GPU work
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and not args.quick:
+        cpu = cpu_oracle_baseline()
+        cpu["helmholtz_16_cg"] = cpu_oracle_helmholtz_cg()
+
     import torch
     torch.cuda.set_device(local)
     dist = None
@@ -684,12 +906,11 @@ def main():
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
 
     from paper_2501_18781_gb300 import Context, build_library
+    import synthetic as syn
     build_library()
     ctx = Context(local)
-    op, mu, mp, mesh = build_oseen(ctx, args.n)
-    n = op.n
-    ncells = mu.n_cells
-    import synthetic as syn
+    op, m, T_prev = build_heat(ctx, args.n)
+    n, ncells = op.n, m.n_cells
     src = torch.tensor(syn.uniform_pm1(1, n), device="cuda")
     dst = torch.empty_like(src)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")   # > 129 MB L2
@@ -705,8 +926,8 @@ def main():
     with ClockSampler(local) as clocks:
         times = time_apply(op, src, dst, args.steps, 0, flush)
     launches = ctx.launch_count() - l0
-    total = sum(times)
-    total = max_over_ranks(total, dist, "cuda")
+    variant = op.variant
+    total = max_over_ranks(sum(times), dist, "cuda")
     value = whole_job_rate(n, args.steps, world, total)
     mean = total / args.steps
 
@@ -728,56 +949,60 @@ def main():
         hdst.copy_(dst, non_blocking=True)
     e1.record()
     e1.synchronize()
-    e2e_t = e0.elapsed_time(e1) / 1e3
+    e2e_t = max_over_ranks(e0.elapsed_time(e1) / 1e3, dist, "cuda")
     e2e = {"value": n * args.steps * world / e2e_t / 1e9, "unit": "GDoF/s",
            "h2d_bytes_per_step": n * 8, "d2h_bytes_per_step": n * 8}
 
     peaks = measured_peaks()
     hbm = peaks.get("hbm_gbs", HBM_FALLBACK_GBS)
-    flops = OSEEN_FLOPS_PER_CELL["qpoint-outer" if "qpoint-outer" in op.variant else "component-outer"] * ncells
-    alg_bytes = 16 * n + OSEEN_BYTES_PER_VEL_NODE * mu.n_dofs
+    flops = HEAT_FLOPS_PER_CELL["inkernel" if "/inkernel" in variant else "tabulated"] * ncells
+    alg_bytes = HEAT_WORDS_PER_DOF * 8 * n
     achieved = flops / mean / 1e12
     out = {
         "metric": METRIC, "value": value, "unit": "GDoF/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": mean * 1e3, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": f"oseen_q2q1_interface_{args.n}", "n_dofs": n, "cells": ncells,
-                   "velocity": "Q2 x 3", "pressure": "Q1", "parallelism": "replicas" if world > 1 else "single",
-                   "l2": "flushed between timed steps (256 MB write)", "variant": op.variant},
+        "config": {"workload": f"heat_laser_q2_{args.n}", "n_dofs": n, "cells": ncells, "element": "Q2",
+                   "operator": "(rho c_p / dt) M + K(k(T^n)), k = k0 (1 + 0.5 T / T_b), Dirichlet bottom",
+                   "parallelism": "replicas" if world > 1 else "single",
+                   "l2": "flushed between timed steps (256 MB write); vectors of 136 MB exceed L2",
+                   "variant": variant},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                     "frac": achieved / FP64_PEAK_TFLOPS, "traffic": ncu_traffic(f"oseen_q2q1_interface_{args.n}"),
+                     "frac": achieved / FP64_PEAK_TFLOPS, "traffic": ncu_traffic(f"heat_laser_q2_{args.n}/f64"),
                      "flops_per_launch": flops, "peak_source": "GB300 FP64 rate of the profiling recipe"},
         "hbm_roofline": {"achieved": alg_bytes / mean / 1e9, "peak": hbm, "unit": "GB/s",
                          "frac": alg_bytes / mean / 1e9 / hbm, "bytes_per_launch": alg_bytes,
-                         "peak_source": "MEASURED_PEAKS.json" if "hbm_gbs" in peaks else "fallback"},
+                         "peak_source": "MEASURED_PEAKS.json (of measured)" if "hbm_gbs" in peaks else "fallback"},
         "e2e": e2e, "gpu_launches": launches, "clocks": clocks.summary(),
     }
-    # the same apply in fp32 (context for the mixed-precision solver)
+    # the same operator in fp32 (the arithmetic of the mixed solver's inner applies) and in
+    # double-float, with their HBM fractions
     src32, dst32 = src.float(), torch.empty(n, dtype=torch.float32, device="cuda")
     t32 = time_apply(op, src32, dst32, max(5, args.steps // 2), 3, flush)
-    out["fp32_apply"] = {"value": n / (sum(t32) / len(t32)) / 1e9, "unit": "GDoF/s",
-                         "ms_per_step": sum(t32) / len(t32) * 1e3}
-    out["df64_apply"] = {"value": n / (_event_ms(lambda: op.apply(src, dst, arith="df64"), 5, flush) / 1e3) / 1e9,
-                         "unit": "GDoF/s", "note": "fp64 vectors, double-float cell arithmetic on the fp32 pipes"}
-    if rank == 0:
-        out["interface_sources"] = interface_sources_timing(ctx, op, mu, flush)
-    if not args.no_solve and rank == 0:
-        out["solve"] = heat_solve_comparison(ctx)
-        out["oseen_solve"] = oseen_solve(ctx, op, mu, mp)
-    if args.suite and rank == 0:
-        out["workloads"] = workload_suite(ctx, flush)
-        out["workloads"]["oseen_meltpool"] = meltpool_oseen(ctx, args.n, flush)
-    if args.suite and rank == 0 and world == 1:
-        out.setdefault("workloads", {})["cpu_oracle_helmholtz_16"] = cpu_oracle_workloads()
-    if (args.suite or args.qk) and rank == 0:
-        out.setdefault("workloads", {})["helmholtz_qk"] = helmholtz_qk(ctx, flush)
-    if (args.suite or args.meltpool_step) and rank == 0:
-        out.setdefault("workloads", {})["meltpool_step"] = meltpool_step(ctx, args.n)
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        v, nd, reps, dt = cpu_oracle_apply(16)
-        out["cpu_baseline"] = {"value": v, "unit": "GDoF/s", "cores": 1, "kind": "oracle",
-                               "sample": f"oseen_q2q1_interface_16 ({nd} DoFs): assembled-CSR SpMV x {reps} "
-                                         f"in {dt:.1f} s (assembly untimed)"}
+    ms32 = sum(t32) / len(t32) * 1e3
+    out["fp32_apply"] = {"value": n / ms32 / 1e6, "unit": "GDoF/s", "ms_per_step": ms32, "variant": op.variant,
+                         "hbm_roofline": {"bytes_per_launch": alg_bytes // 2,
+                                          "frac": alg_bytes / 2 / (ms32 * 1e-3) / 1e9 / hbm, "peak": hbm},
+                         "traffic": ncu_traffic(f"heat_laser_q2_{args.n}/f32")}
+    tdf = time_apply(op, src, dst, max(5, args.steps // 2), 3, flush, arith="df64")
+    msdf = sum(tdf) / len(tdf) * 1e3
+    out["df64_apply"] = {"value": n / msdf / 1e6, "unit": "GDoF/s", "ms_per_step": msdf, "variant": op.variant,
+                         "note": "fp64 vectors, double-float cell arithmetic on the fp32 pipes"}
+    if rank == 0 and not args.quick:
+        out["solve"] = heat_solve_comparison(ctx, op, m, T_prev, args.n)
+        del op, m, T_prev, src, dst, src32, dst32, hsrc, hdst, dsrc
+        torch.cuda.empty_cache()
+        w = out["workloads"] = {}
+        w["oseen_q2q1_interface_64"] = oseen_workload(ctx, flush)
+        w["reinit_octree_q2_32_l3"] = reinit_octree_workload(ctx, flush)
+        w["helmholtz_sphere_q2_16"] = helmholtz_workload(ctx)
+        w["heat_adjoint_q2_64"] = heat_adjoint_workload(ctx, flush)
+        w["helmholtz_qk"] = helmholtz_qk(ctx, flush, solves=args.suite)
+        w["meltpool_step"] = meltpool_step(ctx, 64, reps=2)
+        if args.suite:
+            w["oseen_meltpool"] = meltpool_oseen(ctx, 64, flush)
+    if cpu is not None:
+        out["cpu_baseline"] = cpu
     if rank == 0:
         print(json.dumps(out))
     if dist:

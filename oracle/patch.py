@@ -92,3 +92,39 @@ def oseen_rows(n, lo, hi, rows, build, nodal, u, dirichlet_u, absolute=False):
         row = A[local]
         out[s] = np.ravel(abs(row) @ np.abs(us) if absolute else row @ us)[0]
     return out
+
+
+def constrained_rows(dm, dofs, element_matrices, u, absolute=False):
+    """(C^T A C u)_i for the free DoFs ``dofs`` of an octree (or uniform) DoF map ``dm`` without
+    assembling the whole operator.  Row i of C^T A C u is sum_p C[p, i] (A C u)_p over the lattice
+    points p whose constraint row holds DoF i (i itself, and the hanging points that interpolate from
+    it); (A C u)_p sums the element contributions of the cells that contain p.  So only those cells'
+    element matrices are formed, by ``element_matrices(cells)`` -> (len(cells), nb, nb) (the plain
+    full-quadrature routines of ``assemble``).  Dirichlet columns are removed by zeroing u there;
+    Dirichlet rows are identities and are not computed here.  With ``absolute``, (|C|^T |A| |C| |u|)_i,
+    an upper bound of (|C^T A C| |u|)_i."""
+    import scipy.sparse as sp
+    M = dm.points.shape[0]
+    nc, nb = dm.cell_points.shape  # incidence of lattice points in cells
+    incid = sp.csr_matrix((np.ones(nc * nb), (dm.cell_points.ravel(), np.repeat(np.arange(nc), nb))),
+                          shape=(M, nc))
+    CT = dm.C.T.tocsr()
+    us = np.where(dm.dirichlet, 0.0, u)
+    Cu = (abs(dm.C) @ np.abs(us)) if absolute else dm.C @ us
+    out = np.empty(len(dofs))
+    for s, i in enumerate(dofs):
+        pts = CT.indices[CT.indptr[i]:CT.indptr[i + 1]]
+        wts = CT.data[CT.indptr[i]:CT.indptr[i + 1]]
+        order = np.argsort(pts)
+        pts, wts = pts[order], (np.abs(wts) if absolute else wts)[order]
+        cells = np.unique(incid[pts].indices)
+        Ae = element_matrices(cells)
+        cp = dm.cell_points[cells]
+        ul = Cu[cp]                                             # (ncells, nb)
+        pos = np.minimum(np.searchsorted(pts, cp), len(pts) - 1)
+        wl = np.where(pts[pos] == cp, wts[pos], 0.0)            # C[p_a(e), i] per local row
+        if absolute:
+            out[s] = np.einsum("ea,eab,eb->", wl, np.abs(Ae), ul)
+        else:
+            out[s] = np.einsum("ea,eab,eb->", wl, Ae, ul)
+    return out

@@ -258,3 +258,198 @@ def test_qk_bench_size_sampled_rows(ctx, k, n):
         v = op.apply(torch.tensor(uu, device="cuda", dtype=dt), arith=arith).cpu().double().numpy()
         ok, worst = componentwise_ok(v[rows], ref, bound, rtol)
         assert ok, (name, worst)
+
+
+def _true_residual(op, b, x, nrhs=1):
+    """Per right-hand side ||b - A x|| / ||b|| with A the fp64 apply that the sampled-row tests pin
+    against the oracle, reduced by torch."""
+    r = (b - op.apply(x, nrhs=nrhs)).view(nrhs, -1)
+    return (torch.linalg.vector_norm(r, dim=1) / torch.linalg.vector_norm(b.view(nrhs, -1), dim=1)).cpu().numpy()
+
+
+def test_heat_128_step_solves_true_residual(ctx):
+    """The 128^3 heat-step solves exactly as bench.py times them (laser load plus (rho c_p/dt) M theta^n
+    as right-hand side; fp64 CG with Chebyshev(4) and fp32-inner defect correction, graph-replayed):
+    the residual recomputed with the pinned fp64 apply is at most 1e-10 |b|, agrees with the reported
+    one, and the Dirichlet rows of x are exactly 0.  Also the seeded uniform right-hand side."""
+    import bench
+    op, m, T_prev = bench.build_heat(ctx, 128)
+    d = torch.tensor(m.export(cell_map=False, constraints=False, coords=False)["dirichlet"], device="cuda")
+    b = bench.heat_step_rhs(ctx, m, T_prev, 128)
+    assert torch.all(b[d] == 0) and b.abs().max().item() > 0
+    br = torch.tensor(syn.uniform_pm1(1, m.n_dofs), device="cuda")
+    br[d] = 0
+    for rhs in (b, br):
+        for name, kw in bench.HEAT_SOLVERS.items():
+            x, info = op.solve(rhs, tol=1e-10, use_graph=True, **kw)
+            assert info["status"] == 0, (name, info)
+            rel = _true_residual(op, rhs, x)[0]
+            assert rel <= 1e-10 * (1 + 1e-3), (name, rel, info)
+            assert abs(rel - info["rel_residual"]) <= 1e-2 * max(rel, info["rel_residual"]), (name, rel, info)
+            assert torch.all(x[d] == 0)
+
+
+def test_heat_128_laser_rhs_sampled_rows(ctx):
+    """The heat-step right-hand side the bench solves, checked at sampled rows against the oracle:
+    (rho c_p / dt) (M theta^n)_i from the patch rows of the oracle's mass form plus the oracle's laser
+    load (its top-face rows, computed on the 2 x 2 x 2-cell patch with the same Gauss face rule)."""
+    import bench
+    from oracle import mesh as omesh
+    n = 128
+    wl = syn.scaled(syn.HEAT_LASER, n)
+    p = wl.params
+    op, m, T_prev = bench.build_heat(ctx, n, autotune=False)
+    b = bench.heat_step_rhs(ctx, m, T_prev, n).cpu().numpy()
+    dirichlet = m.export(cell_map=False, constraints=False, coords=False)["dirichlet"].astype(bool)
+    theta = T_prev.cpu().numpy() - p["t_ref"]
+    free, _ = _lattice_sample(n, 40, 9, dirichlet)
+    L = 2 * n + 1
+    top = free[free // (L * L) >= L - 2]
+    rng = np.random.default_rng(3)
+    rows = np.unique(np.concatenate([free, top, L * L * (L - 1) + rng.choice(L * L, 30, replace=False)]))
+    rows = rows[~dirichlet[rows]]
+    mass = lambda d, nod, cw: asm.assemble_scalar(d, np.full((d.n_cells, 27), p["rhocp"] / p["dt"]))
+    ref = patch.scalar_rows(n, wl.lo, wl.hi, rows, mass, {}, theta, dirichlet)
+    bound = patch.scalar_rows(n, wl.lo, wl.hi, rows, mass, {}, theta, dirichlet, absolute=True)
+    lz = p["laser"]
+    # the laser load of a row from the top cells of its patch (only top-face rows are nonzero)
+    for s, r in enumerate(rows):
+        coord = (r % L, (r // L) % L, r // (L * L))
+        if coord[2] != L - 1:
+            continue
+        c0 = [patch._first_cell(c, 2, n) for c in coord]
+        dm, idx = patch._patch(n, wl.lo, wl.hi, c0, 2)
+        f = asm.laser_rhs(dm, lz["power"], lz["radius"], lz["x0"], lz["y0"], lz["absorptivity"])
+        loc = int(np.nonzero(idx == r)[0][0])
+        ref[s] += f[loc]
+        bound[s] += abs(f[loc])
+    ok, worst = componentwise_ok(b[rows], ref, bound, 1e-12)
+    assert ok, worst
+
+
+def test_reinit_octree_8rhs_mixed_solve_true_residual(ctx):
+    """The 8-right-hand-side mixed-precision solve of the 12.3M-DoF octree as bench.py times it
+    (fp32-inner defect correction, Chebyshev, graph-replayed): every column's residual, recomputed with
+    the fp64 batched apply and reduced by torch, is at most 1e-10 of its right-hand side."""
+    import bench
+    op, m = bench.build_reinit_octree(ctx)
+    R = syn.REINIT_OCTREE.nrhs
+    B = torch.tensor(np.concatenate([syn.uniform_pm1(s, m.n_dofs) for s in range(1, R + 1)]), device="cuda")
+    X, info = op.solve(B, nrhs=R, solver="defect_correction", precond="chebyshev", tol=1e-10, use_graph=True)
+    assert info["status"] == 0, info
+    rel = _true_residual(op, B, X, nrhs=R)
+    assert np.all(rel <= 1e-10 * (1 + 1e-3)), rel
+
+
+def test_heat_adjoint_64_gradients_match_central_differences(ctx):
+    """The gradient workload at its own size (Q2 on 64^3, 2,146,689 DoFs, convection and a
+    per-Gauss-point k_q, the 200 W / 50 um beam, the 100 um objective box): the adjoint gradients with
+    respect to the four laser parameters and to the largest-magnitude k_q entries agree with central
+    differences of the objective at step 1e-6 (relative to the parameter) to 1e-6."""
+    import bench
+    from paper_2501_18781_gb300 import DofMap, Mesh, Operator
+    wl = syn.HEAT_ADJOINT
+    p = wl.params
+    m = DofMap(Mesh.uniform(ctx, wl.n, wl.lo, wl.hi), 2, DIRICHLET_BOTTOM)
+    x = m.coords()
+    beta = np.array(syn.convection_field(*x.T, wl.seed, wl.lo, wl.hi))
+    kq = syn.kq_field(m.n_cells * 27, wl.seed, p["k0"])
+    op = Operator(ctx, "heat", [m], rhocp=p["rhocp"], dt=p["dt"], k0=p["k0"], t_boil=p["t_boil"])
+    bt = torch.tensor(beta.ravel(), device="cuda")
+    op.set_field("beta", bt)
+    op.set_field("k_qpoint", torch.tensor(kq, device="cuda"))
+    lz = p["laser"]
+    th_prev = syn.heat_initial_temperature(*x.T, lz["radius"], wl.hi[2]) - p["t_ref"]
+    target = syn.heat_target_temperature(*x.T, wl.hi[2], wl.seed + 4) - p["t_ref"]
+    tp, tt = torch.tensor(th_prev, device="cuda"), torch.tensor(target, device="cuda")
+    kw = dict(solver="gmres", precond="jacobi", tol=1e-13, restart=50)
+    names = ["power", "radius", "x0", "y0"]
+    lzl = [lz[k] for k in names] + [lz["absorptivity"]]
+    box = (p["box_half"], p["box_depth"])
+    J0, g, gk, _, _ = op.heat_step_gradient(lzl, tp, tt, *box, **kw)
+    assert J0 > 0
+    for i, k in enumerate(names):
+        step = p["fd_step"] * (abs(lzl[i]) if k in ("power", "radius") else lz["radius"])
+        a, b = list(lzl), list(lzl)
+        a[i] += step
+        b[i] -= step
+        Ja = op.heat_step_gradient(a, tp, tt, *box, with_kq=False, **kw)[0]
+        Jb = op.heat_step_gradient(b, tp, tt, *box, with_kq=False, **kw)[0]
+        fd = (Ja - Jb) / (2 * step)
+        assert abs(g[i] - fd) <= 1e-6 * max(abs(fd), 1e-3 * max(abs(v) for v in g)), (k, g[i], fd)
+    gk = gk.cpu().numpy()
+    for flat in np.argsort(-np.abs(gk))[:3]:
+        hh = p["fd_step"] * kq[flat]
+        vals = []
+        for sgn in (1, -1):
+            k2 = kq.copy()
+            k2[flat] += sgn * hh
+            op.set_field("k_qpoint", torch.tensor(k2, device="cuda"))
+            vals.append(op.heat_step_gradient(lzl, tp, tt, *box, with_kq=False, **kw)[0])
+        fd = (vals[0] - vals[1]) / (2 * hh)
+        assert abs(gk[flat] - fd) <= 1e-6 * abs(fd), (flat, gk[flat], fd)
+
+
+def test_reinit_octree_full_size_maps_and_sampled_rows(ctx):
+    """The 12.3M-DoF octree of the batched reinitialisation (base 32^3 + 3 levels) against the
+    oracle's own construction from the same leaf list: the integer cell map, the constraint rows and
+    the DoF coordinates bit for bit, then rows of the 8-right-hand-side launch as bench.py times it
+    (fp64 1e-12, fp32 5e-5 componentwise) at DoFs on leaves of every level and at the masters of
+    every class of hanging node (edge, face, chained), each row of C^T A C formed from the cells
+    around it by the oracle's full-quadrature element matrices."""
+    import dataclasses
+    import bench
+    from oracle import mesh as omesh
+    wl = syn.REINIT_OCTREE
+    eps = 2.0 / (wl.n << wl.levels)
+    dtau = 0.5 / (wl.n << wl.levels)
+    d = lambda X, Y, Z: syn.deformed_sphere_distance(X, Y, Z, wl.seed)
+    leaves = syn.refine_band_leaves(wl.n, wl.levels, d, eps)
+    dm = omesh.octree_dofmap(leaves, wl.n, wl.levels)
+    op, m = bench.build_reinit_octree(ctx)
+    # integer maps, bit for bit
+    e = m.export()
+    cm, rp, cols, w = dm.export()
+    assert m.n_dofs == dm.n_dofs and m.n_cells == dm.n_cells
+    assert np.array_equal(e["cell_map"], cm) and np.array_equal(e["con_rowptr"], rp)
+    assert np.array_equal(e["con_cols"], cols) and np.array_equal(e["con_w"], w)
+    x = dm.dof_coords()
+    assert np.array_equal(e["coords"], x)
+    del e, cm
+    phi = syn.initial_level_set(syn.deformed_sphere_distance(*x.T, wl.seed), eps)
+    # sampled rows: DoFs on leaves of each level, masters of each class of hanging node
+    rng = np.random.default_rng(17)
+    rows = []
+    for lev in range(wl.levels + 1):
+        cells = np.nonzero(dm.cell_level == lev)[0]
+        pts = dm.cell_points[rng.choice(cells, 12)].ravel()
+        free = dm.free_of_point[pts]
+        rows.append(rng.choice(free[free >= 0], 8, replace=False))
+    hang = np.nonzero(dm.hang_of_point >= 0)[0]
+    Ch = dm.C[hang].tocsr()
+    nm = np.diff(Ch.indptr)
+    for cls in np.unique(nm):
+        sel = np.nonzero(nm == cls)[0]
+        for t in rng.choice(sel, min(3, sel.size), replace=False):
+            rows.append(Ch.indices[Ch.indptr[t]:Ch.indptr[t + 1]][:3])
+    rows = np.unique(np.concatenate(rows))
+
+    def emat(cells):
+        sub = dataclasses.replace(dm, cell_points=dm.cell_points[cells], cell_h=dm.cell_h[cells],
+                                  cell_origin=dm.cell_origin[cells], cell_level=dm.cell_level[cells])
+        mq, D = asm.reinit_coefficients(sub, phi, eps, dtau)
+        return asm.scalar_element_matrices(sub, mq, diff_tensor=D)
+
+    R = wl.nrhs
+    U = np.concatenate([syn.uniform_pm1(s, dm.n_dofs) for s in range(1, R + 1)])
+    U = U.astype(np.float32).astype(np.float64)         # exact in both arithmetics
+    refs = {}
+    for r in (0, R - 1):
+        u = U[r * dm.n_dofs:(r + 1) * dm.n_dofs]
+        refs[r] = (patch.constrained_rows(dm, rows, emat, u), patch.constrained_rows(dm, rows, emat, u, absolute=True))
+    for arith, rtol in (("f64", 1e-12), ("f32", 5e-5)):
+        t = torch.tensor(U, device="cuda", dtype=torch.float32 if arith == "f32" else torch.float64)
+        V = op.apply(t, nrhs=R).cpu().double().numpy()
+        for r, (ref, bound) in refs.items():
+            ok, worst = componentwise_ok(V[r * dm.n_dofs + rows], ref, bound, rtol)
+            assert ok, (arith, r, worst)

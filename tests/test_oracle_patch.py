@@ -73,3 +73,27 @@ def test_q3_q4_helmholtz_rows():
         got = patch.scalar_rows(n, (0, 0, 0), (1, 1, 1), rows, build, {"phi": phi}, u, dm.dirichlet, degree=k)
         ref = (A @ u)[rows]
         assert np.abs(got - ref).max() <= 1e-13 * np.abs(ref).max(), k
+
+
+def test_constrained_rows_match_the_assembled_octree_operator():
+    """Rows of C^T A C from the cells around each row (octree with hanging nodes on two levels)
+    equal the rows of the fully assembled and condensed oracle matrix, for free DoFs next to
+    hanging nodes, on coarse and fine leaves; the absolute form bounds |C^T A C| |u|."""
+    d = lambda x, y, z: syn.deformed_sphere_distance(x, y, z, 3)
+    leaves = syn.refine_band_leaves(4, 2, d, 1.0 / 64)
+    dm = omesh.octree_dofmap(leaves, 4, 2)
+    eps = 1.0 / 64
+    phi = syn.initial_level_set(syn.deformed_sphere_distance(*dm.dof_coords().T, 3), eps)
+    m, D = asm.reinit_coefficients(dm, phi, eps, 0.5 / 16)
+    A = asm.assemble_scalar(dm, m, diff_tensor=D).tocsr()
+    u = syn.uniform_pm1(5, dm.n_dofs)
+    # DoFs that master some hanging node, plus random ones
+    masters = np.unique(dm.C[dm.hang_of_point >= 0].indices)
+    rng = np.random.default_rng(2)
+    rows = np.unique(np.concatenate([rng.choice(masters, 60, replace=False), rng.choice(dm.n_dofs, 60, replace=False)]))
+    emat = lambda cells: asm.scalar_element_matrices(dm, m, diff_tensor=D, cells=cells)
+    got = patch.constrained_rows(dm, rows, emat, u)
+    ref = (A @ u)[rows]
+    assert np.abs(got - ref).max() <= 1e-13 * np.abs(ref).max()
+    bound = patch.constrained_rows(dm, rows, emat, u, absolute=True)
+    assert np.all(bound >= (abs(A) @ np.abs(u))[rows] * (1 - 1e-13))
