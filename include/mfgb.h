@@ -382,8 +382,11 @@ mf_status mf_heat_step_gradient(mf_op* op, const mf_laser* laser, const mf_solve
 
 /* Time the apply variants of this operator (cells per block, coefficient mode; Oseen: the fp64
  * loop order; Q3 Helmholtz: the CUDA-core or the tensor-core kernel for fp32 applies, which then
- * also serves the fp32 applies inside solvers) and keep the fastest; results are appended to
- * cache_path (may be NULL).  Synchronising. */
+ * also serves the fp32 applies inside solvers) and keep the fastest.  cache_path (may be NULL) is a
+ * text file of one JSON record per line, keyed by the operator's configuration (kind, degree, mesh
+ * type and sizes, optional fields, melt-pool flags, the device's SM count): if it holds a record with
+ * this operator's key, the last such record's choice is applied and nothing is timed; otherwise the
+ * variants are timed and the record (key, choice, timings) is appended.  Synchronising when it times. */
 mf_status mf_autotune(mf_op* op, const char* cache_path);
 
 /* Describe the variant the next apply will launch (host string, owned by the library). */

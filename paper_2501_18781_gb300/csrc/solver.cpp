@@ -949,9 +949,70 @@ mf_status mf_heat_step_gradient(mf_op* op, const mf_laser* lz, const mf_solver_p
   }
 }
 
-mf_status mf_autotune(mf_op* op, const char* cache_path) {
+}  // extern "C"
+
+namespace {
+
+// The configuration that decides which variant is fastest: operator kind and degree, mesh type
+// and sizes, the optional fields, the melt-pool flags and the device's SM count.
+std::string tune_key(const mf_op* op) {
+  const mf_dofmap* m = op->map[0];
+  char buf[320];
+  std::snprintf(buf, sizeof buf, "kind=%d deg=%d %s dofs=%lld cells=%lld con=%lld beta=%d kq=%d rhocp=%d betaq=%d "
+                "mode=%d flags=%d sms=%d", op->p.kind, m->degree, m->uniform ? "uniform" : "octree",
+                (long long)op->n, (long long)op->ncells, (long long)(m->con_rowptr.empty() ? 0 : m->con_rowptr.size() - 1), op->beta ? 1 : 0,
+                op->kq_user ? 1 : 0, op->rhocp_user ? 1 : 0, op->betaq_user ? 1 : 0, op->p.coef_mode,
+                op->p.oseen_flags, op->ctx->sm_count);
+  return buf;
+}
+
+std::string tune_choice(const mf_op* op) {
+  char buf[256];
+  std::snprintf(buf, sizeof buf, "\"mode64\": %d, \"mode32\": %d, \"block\": %d, \"persistent_blocks\": %d, "
+                "\"df64_faster\": %d, \"oseen_qouter64\": %d, \"qk_f32_tc\": %d", op->mode64, op->mode32, op->block,
+                op->persistent_blocks, op->df64_faster ? 1 : 0, op->oseen_qouter64, op->qk_f32_tc);
+  return buf;
+}
+
+bool read_int(const std::string& line, const char* name, int* out) {
+  const std::string tag = std::string("\"") + name + "\": ";
+  const size_t at = line.find(tag);
+  return at != std::string::npos && std::sscanf(line.c_str() + at + tag.size(), "%d", out) == 1;
+}
+
+// The last record of cache_path whose key matches this operator, applied to it; false if none.
+bool apply_cached_choice(mf_op* op, const char* cache_path) {
+  FILE* fp = std::fopen(cache_path, "r");
+  if (!fp) return false;
+  const std::string want = "\"key\": \"" + tune_key(op) + "\"";
+  std::string hit, line;
+  char chunk[1024];
+  while (std::fgets(chunk, sizeof chunk, fp)) {
+    line += chunk;
+    if (line.empty() || line.back() != '\n') continue;
+    if (line.find(want) != std::string::npos) hit = line;
+    line.clear();
+  }
+  std::fclose(fp);
+  int v[7];
+  const char* names[7] = {"mode64", "mode32", "block", "persistent_blocks", "df64_faster", "oseen_qouter64", "qk_f32_tc"};
+  if (hit.empty()) return false;
+  for (int i = 0; i < 7; ++i)
+    if (!read_int(hit, names[i], &v[i])) return false;
+  if ((v[0] | v[1]) & ~1 || (v[2] != 64 && v[2] != 128) || v[3] < 0 || v[3] > 64) return false;
+  op->mode64 = v[0];
+  op->mode32 = v[1];
+  op->block = v[2];
+  op->persistent_blocks = v[3];
+  op->df64_faster = v[4] != 0;
+  op->oseen_qouter64 = v[5] != 0;
+  op->qk_f32_tc = v[6] != 0;
+  op->tune_record = hit.substr(0, hit.size() - 1);
+  return true;
+}
+
+mf_status autotune_measure(mf_op* op) {
   try {
-    if (!op) return fail(MF_EINVAL, "NULL argument");
     MF_TRY(check_fields(op));
     mf_ctx* c = op->ctx;
     const int64_t n = op->n;
@@ -988,13 +1049,6 @@ mf_status mf_autotune(mf_op* op, const char* cache_path) {
       std::snprintf(buf, sizeof buf, "{\"kind\": %d, \"n\": %lld, \"q3_f32_cuda_core_ms\": %.6g, \"q3_f32_tensor_core_ms\": %.6g}",
                     op->p.kind, (long long)n, ms[0], ms[1]);
       op->tune_record = buf;
-      if (cache_path) {
-        FILE* fp = std::fopen(cache_path, "a");
-        if (fp) {
-          std::fprintf(fp, "%s\n", buf);
-          std::fclose(fp);
-        }
-      }
       return MF_OK;
     }
     if (op->p.kind == MF_OP_OSEEN) {
@@ -1028,13 +1082,6 @@ mf_status mf_autotune(mf_op* op, const char* cache_path) {
       std::snprintf(buf, sizeof buf, "{\"kind\": %d, \"n\": %lld, \"component_outer_ms\": %.6g, \"qpoint_outer_ms\": %.6g}",
                     op->p.kind, (long long)n, ms[0], ms[1]);
       op->tune_record = buf;
-      if (cache_path) {
-        FILE* fp = std::fopen(cache_path, "a");
-        if (fp) {
-          std::fprintf(fp, "%s\n", buf);
-          std::fclose(fp);
-        }
-      }
       return MF_OK;
     }
     MF_TRY(ensure_tables(op));
@@ -1106,10 +1153,29 @@ mf_status mf_autotune(mf_op* op, const char* cache_path) {
                   op->p.kind, (long long)n, mode_ms[0][0], mode_ms[0][1], mode_ms[1][0], mode_ms[1][1], op->block,
                   op->persistent_blocks, shape_ms[best_shape], f64_ms, df_ms);
     op->tune_record = buf;
+    return MF_OK;
+  } catch (...) {
+    return fail(MF_ENOMEM, "exception in mf_autotune");
+  }
+}
+
+}  // namespace
+
+extern "C" {
+
+mf_status mf_autotune(mf_op* op, const char* cache_path) {
+  try {
+    if (!op) return fail(MF_EINVAL, "NULL argument");
+    MF_TRY(check_fields(op));
+    if (cache_path && apply_cached_choice(op, cache_path)) return MF_OK;
+    MF_TRY(autotune_measure(op));
+    const std::string rec = "{\"key\": \"" + tune_key(op) + "\", " + tune_choice(op) + ", \"timings\": " +
+                            op->tune_record + "}";
+    op->tune_record = rec;
     if (cache_path) {
       FILE* fp = std::fopen(cache_path, "a");
       if (fp) {
-        std::fprintf(fp, "%s\n", buf);
+        std::fprintf(fp, "%s\n", rec.c_str());
         std::fclose(fp);
       }
     }
