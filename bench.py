@@ -46,6 +46,15 @@ FP64_PEAK_TFLOPS = 1.25      # GB300 FP64 (vector and tensor) rate of the profil
 # point.  With k evaluated in the kernel, the nodal T^n is swept to the Gauss points (270) and
 # k0 + s T applied (27 x 2): 1863.
 HEAT_FLOPS_PER_CELL = {"tabulated": 1539, "inkernel": 1863}
+# The double-float kernel evaluates the same cell operator in pairs of fp32 (tabulated w h k): per
+# cell 8559 fp32 instructions, 11151 flops with an FMA counted as two (a pair product is 1 FMUL + 3
+# FFMA, a pair sum 8 FADD, a renormalisation 3 FADD): value sweeps 1674 / 2160, z fluxes 837 / 1134,
+# z test parts 972 / 1269, x and y gradients, fluxes and test parts 3240 / 4266, renormalisation 81 /
+# 81, transposed x and y sweeps 1170 / 1494, transposed z sweep 585 / 747.  Its roof is the fp32
+# pipe: 152 SMs x 128 lanes x 2 flops x 2.07 GHz (the profiling recipe's unit count and SM clock).
+HEAT_DF64_FLOPS_PER_CELL = 11151
+HEAT_DF64_INSTRUCTIONS_PER_CELL = 8559
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 # Algorithmic HBM bytes of one heat apply: read u, write v, read the nodal T^n (3 words per DoF).
 HEAT_WORDS_PER_DOF = 3
 # Algorithmic flops of one Oseen Q2/Q1 cell apply as each kernel variant performs it.
@@ -915,16 +924,22 @@ def main():
     dst = torch.empty_like(src)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")   # > 129 MB L2
 
-    # warm-up and set-up (Gauss-point coefficient tables) outside the timed region
-    for _ in range(args.warmup):
-        op.apply(src, dst)
+    # warm-up and set-up (Gauss-point coefficient tables) outside the timed region; the fp64-accurate
+    # apply runs in the arithmetic measured faster here: the fp64 pipes or double-float pairs on the
+    # fp32 pipes (both meet the same 1e-12 parity bar)
+    pick = {}
+    for arith in (None, "df64"):
+        for _ in range(args.warmup):
+            op.apply(src, dst, arith=arith)
+        pick[arith] = statistics.median(time_apply(op, src, dst, 5, 0, flush, arith=arith))
+    arith = min(pick, key=pick.get)
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
     l0 = ctx.launch_count()
     with ClockSampler(local) as clocks:
-        times = time_apply(op, src, dst, args.steps, 0, flush)
+        times = time_apply(op, src, dst, args.steps, 0, flush, arith=arith)
     launches = ctx.launch_count() - l0
     variant = op.variant
     total = max_over_ranks(sum(times), dist, "cuda")
@@ -938,14 +953,14 @@ def main():
     dsrc = torch.empty_like(src)
     for _ in range(2):
         dsrc.copy_(hsrc, non_blocking=True)
-        op.apply(dsrc, dst)
+        op.apply(dsrc, dst, arith=arith)
         hdst.copy_(dst, non_blocking=True)
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record()
     for _ in range(args.steps):
         dsrc.copy_(hsrc, non_blocking=True)
-        op.apply(dsrc, dst)
+        op.apply(dsrc, dst, arith=arith)
         hdst.copy_(dst, non_blocking=True)
     e1.record()
     e1.synchronize()
@@ -955,21 +970,28 @@ def main():
 
     peaks = measured_peaks()
     hbm = peaks.get("hbm_gbs", HBM_FALLBACK_GBS)
-    flops = HEAT_FLOPS_PER_CELL["inkernel" if "/inkernel" in variant else "tabulated"] * ncells
+    if arith == "df64":
+        flops = HEAT_DF64_FLOPS_PER_CELL * ncells
+        peak, peak_src, key = FP32_PEAK_TFLOPS, "GB300 fp32 pipe: 152 SMs x 128 lanes x 2 x 2.07 GHz (recipe)", "df64"
+    else:
+        flops = HEAT_FLOPS_PER_CELL["inkernel" if "/inkernel" in variant else "tabulated"] * ncells
+        peak, peak_src, key = FP64_PEAK_TFLOPS, "GB300 FP64 rate of the profiling recipe", "f64"
     alg_bytes = HEAT_WORDS_PER_DOF * 8 * n
     achieved = flops / mean / 1e12
     out = {
         "metric": METRIC, "value": value, "unit": "GDoF/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": mean * 1e3, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "vs_baseline": None, "dtype": "df64" if arith == "df64" else "f64", "data": "synthetic",
         "config": {"workload": f"heat_laser_q2_{args.n}", "n_dofs": n, "cells": ncells, "element": "Q2",
+                   "arithmetic": ("double-float: fp64 vectors, pairs of fp32 in the kernel" if arith == "df64"
+                                  else "fp64") + " (the faster of the two in warm-up; both pass the 1e-12 bar)",
                    "operator": "(rho c_p / dt) M + K(k(T^n)), k = k0 (1 + 0.5 T / T_b), Dirichlet bottom",
                    "parallelism": "replicas" if world > 1 else "single",
                    "l2": "flushed between timed steps (256 MB write); vectors of 136 MB exceed L2",
                    "variant": variant},
-        "roofline": {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                     "frac": achieved / FP64_PEAK_TFLOPS, "traffic": ncu_traffic(f"heat_laser_q2_{args.n}/f64"),
-                     "flops_per_launch": flops, "peak_source": "GB300 FP64 rate of the profiling recipe"},
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                     "frac": achieved / peak, "traffic": ncu_traffic(f"heat_laser_q2_{args.n}/{key}"),
+                     "flops_per_launch": flops, "peak_source": peak_src},
         "hbm_roofline": {"achieved": alg_bytes / mean / 1e9, "peak": hbm, "unit": "GB/s",
                          "frac": alg_bytes / mean / 1e9 / hbm, "bytes_per_launch": alg_bytes,
                          "peak_source": "MEASURED_PEAKS.json (of measured)" if "hbm_gbs" in peaks else "fallback"},
@@ -984,10 +1006,21 @@ def main():
                          "hbm_roofline": {"bytes_per_launch": alg_bytes // 2,
                                           "frac": alg_bytes / 2 / (ms32 * 1e-3) / 1e9 / hbm, "peak": hbm},
                          "traffic": ncu_traffic(f"heat_laser_q2_{args.n}/f32")}
-    tdf = time_apply(op, src, dst, max(5, args.steps // 2), 3, flush, arith="df64")
-    msdf = sum(tdf) / len(tdf) * 1e3
-    out["df64_apply"] = {"value": n / msdf / 1e6, "unit": "GDoF/s", "ms_per_step": msdf, "variant": op.variant,
-                         "note": "fp64 vectors, double-float cell arithmetic on the fp32 pipes"}
+    for name, ar in (("f64_apply", None), ("df64_apply", "df64")):
+        tt = time_apply(op, src, dst, max(5, args.steps // 2), 3, flush, arith=ar)
+        ms = sum(tt) / len(tt) * 1e3
+        out[name] = {"value": n / ms / 1e6, "unit": "GDoF/s", "ms_per_step": ms, "variant": op.variant}
+        if ar == "df64":
+            out[name]["note"] = "fp64 vectors, double-float cell arithmetic on the fp32 pipes"
+            out[name]["roofline"] = {"bound": "alu", "unit": "TFLOP/s", "peak": FP32_PEAK_TFLOPS,
+                                     "achieved": HEAT_DF64_FLOPS_PER_CELL * ncells / ms / 1e9,
+                                     "frac": HEAT_DF64_FLOPS_PER_CELL * ncells / ms / 1e9 / FP32_PEAK_TFLOPS,
+                                     "issue_frac": HEAT_DF64_INSTRUCTIONS_PER_CELL * ncells / ms / 1e9 /
+                                                   (FP32_PEAK_TFLOPS / 2)}
+        else:
+            fl = HEAT_FLOPS_PER_CELL["inkernel" if "/inkernel" in op.variant else "tabulated"] * ncells
+            out[name]["roofline"] = {"bound": "alu", "unit": "TFLOP/s", "peak": FP64_PEAK_TFLOPS,
+                                     "achieved": fl / ms / 1e9, "frac": fl / ms / 1e9 / FP64_PEAK_TFLOPS}
     if rank == 0 and not args.quick:
         out["solve"] = heat_solve_comparison(ctx, op, m, T_prev, args.n)
         del op, m, T_prev, src, dst, src32, dst32, hsrc, hdst, dsrc

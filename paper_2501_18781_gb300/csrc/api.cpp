@@ -421,6 +421,7 @@ mf_status mf_operator_set_field(mf_op* op, int field, const void* ptr, int dtype
   }
   op->tables_ready = false;
   op->tc_ready = false;
+  op->df_ready = false;
   op->diag_ready = false;
   op->h16_cnorm = 0.0f;
   // float copy of the in-kernel nodal field
@@ -708,6 +709,25 @@ mf_status apply_impl(mf_op* op, const T* src, T* dst, int nrhs, int64_t ld, bool
   }
   int m = mode;
   if (heat_tabulated(op) && (op->kq_user || op->rhocp_user || op->betaq_user)) m = 1;
+  if constexpr (sizeof(T) == 8) {
+    // double-float on uniform meshes: the plane-by-plane kernel with the split coefficient table
+    if (df && op->map[0]->uniform && (kind == K_HELM || kind == K_HEAT) && !beta && !transpose && !op->rhocp_user &&
+        nrhs <= 65535) {
+      if (!op->df_ready) {
+        MF_TRY(op->qcoef_dfh.alloc(sizeof(float) * 27 * op->ncells));
+        MF_TRY(op->qcoef_dfl.alloc(sizeof(float) * 27 * op->ncells));
+        MF_TRY(launch_df_coef_split(c, op->map[0], op->qcoef64.as<double>(), op->qcoef_dfh.as<float>(),
+                                    op->qcoef_dfl.as<float>()));
+        op->df_ready = true;
+      }
+      MF_TRY(launch_scalar_df_uniform(c, op->map[0], reinterpret_cast<const double*>(src),
+                                      reinterpret_cast<double*>(dst), nrhs, ld, op->qcoef_dfh.as<float>(),
+                                      op->qcoef_dfl.as<float>(), value_coef(op)));
+      MF_TRY(launch_dirichlet_copy(c, op->map[0], src, dst, nrhs, ld, 0, false));
+      op->variant = std::string(kind == K_HELM ? "helmholtz" : "heat") + "/uniform/df64/tabulated/planes";
+      return MF_OK;
+    }
+  }
   ScalarArgs<T> a = scalar_args<T>(op, src, dst, nrhs, ld);
   MF_TRY(launch_scalar_apply(c, op->map[0], kind, m, beta, transpose, prec, &a));
   MF_TRY(launch_dirichlet_copy(c, op->map[0], src, dst, nrhs, ld, 0, f32));

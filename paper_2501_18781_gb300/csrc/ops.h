@@ -119,6 +119,12 @@ mf_status launch_helmholtz_q3_tc(mf_ctx* ctx, const mf_dofmap* m, const float* s
 // MF_ETIMEOUT (once, then the flag is cleared) if a tensor-core launch timed out; read it after
 // the stream has synchronised to cover the launches of the last call
 mf_status tc_take_error();
+// double-float scalar apply on uniform meshes (Helmholtz, heat without convection or Gauss-point
+// rho_cp): the tabulated coefficient split into float pairs of w_q h c_q, then the apply (dst
+// accumulated, nrhs vectors ld apart)
+mf_status launch_df_coef_split(mf_ctx* ctx, const mf_dofmap* m, const double* qcoef64, float* ch, float* cl);
+mf_status launch_scalar_df_uniform(mf_ctx* ctx, const mf_dofmap* m, const double* src, double* dst, int nrhs,
+                                   int64_t ld, const float* ch, const float* cl, double mass);
 // laser top-face load and its parameter derivatives (uniform maps)
 mf_status launch_laser(mf_ctx* ctx, const mf_dofmap* m, const double lz[5], double* f, double* dF);
 // dJ/dk_q = -w_q h grad(lambda) . grad(theta), [cell][27]
@@ -154,6 +160,8 @@ struct mf_op {
   mf::DevBuf diag64;              // cached diagonal (fp64)
   mf::DevBuf blk64, pdiag64;      // Oseen block Jacobi
   bool tables_ready = false;
+  mf::DevBuf qcoef_dfh, qcoef_dfl;  // [27][ncells] float pairs of w_q h c_q for the double-float kernel
+  bool df_ready = false;
   bool diag_ready = false;
   int mode64 = 1, mode32 = 0;     // coefficient mode per precision (autotuned)
   int f64_prec = 0;               // arithmetic of fp64 applies inside solvers (PREC_F64 or PREC_DF64)
