@@ -16,7 +16,7 @@
 // One thread per cell in 8 x 4 x 4 bricks (the warp-level scatter of the fp64 kernels).  The cell's
 // 27 values at the Gauss points are parked in the thread's own column of shared memory, and the
 // test side is accumulated one z-plane at a time, so no more than 27 value pairs are live in
-// registers (128 registers, 16 warps per SM) and enough warps stay resident to cover
+// registers (96 registers, five blocks of 128 threads per SM) and enough warps stay resident to cover
 // the dependent chains of the double-float arithmetic.  No thread reads another thread's column:
 // no barrier is needed.
 #include "ops.h"
@@ -84,7 +84,8 @@ __device__ __forceinline__ dd cD(int q, int p) { return {cDh[3 * q + p], cDl[3 *
 struct DfArgs {
   const double* src;
   double* dst;
-  int64_t ld;       // distance between right-hand sides (one per blockIdx.y)
+  int nrhs;         // right-hand sides, one per blockIdx.y
+  int64_t ld;       // distance between right-hand sides
   const float* ch;  // [27][ncells] high parts of w_q h c_q (c: conductivity or a(phi) at Gauss point q)
   const float* cl;  // [27][ncells] low parts
   int64_t ncells;
@@ -160,7 +161,7 @@ constexpr int kThreads = 128;
 // the plane's own values, followed by the plane-local x and y transposed sweeps.  Only 9
 // accumulators are live at a time; the swept plane is parked in the shared-memory slots of the
 // plane's Gauss-point values (no longer needed), and the z sweep runs on all 27 at the end.
-__global__ void __launch_bounds__(kThreads, 4) k_scalar_df_uniform(DfArgs A, UniformGeom ug) {
+__global__ void __launch_bounds__(kThreads, 5) k_scalar_df_uniform(DfArgs A, UniformGeom ug) {
   __shared__ float sh[27][kThreads], sl[27][kThreads];
   int i, j, k;
   const bool active = brick_cell(ug, i, j, k);
@@ -168,102 +169,105 @@ __global__ void __launch_bounds__(kThreads, 4) k_scalar_df_uniform(DfArgs A, Uni
   const int64_t cell = active ? i + int64_t(ug.nx) * (j + int64_t(ug.ny) * k) : 0;
   const int64_t base = active ? 2 * int64_t(i) + ug.sx * (2 * int64_t(j)) + ug.sy * (2 * int64_t(k)) : 0;
   const uint32_t dmask = active ? dirichlet_mask(ug, i, j, k) : 0u;
+  int bias = 0;
+  {
+    // gather (Dirichlet nodes read as 0) and interpolate to the Gauss points; right-hand side
+    // blockIdx.y
+    dd U[27];
+    const double* __restrict__ s = A.src + int64_t(blockIdx.y) * A.ld + base;
+    double X[27];
+    int emax = 0;
+#pragma unroll
+    for (int l = 0; l < 27; ++l) {
+      const int a = l % 3, b = (l / 3) % 3, c = l / 9;
+      const double v = active ? __ldg(s + a + ug.sx * b + ug.sy * c) : 0.0;
+      X[l] = ((dmask >> l) & 1u) ? 0.0 : v;
+      emax = max(emax, (__double2hiint(X[l]) >> 20) & 0x7FF);
+    }
+    // one power-of-two scale per warp (its 8 x 4 cells share faces folded below): the largest
+    // input maps to [1, 2)
+    emax = int(__reduce_max_sync(0xffffffffu, unsigned(emax)));
+    bias = emax ? emax - 1023 : 0;
+#pragma unroll
+    for (int l = 0; l < 27; ++l) U[l] = d2dd_bits(X[l], bias);
+    dsweep<0>(U);
+    dsweep<1>(U);
+    dsweep<2>(U);
+#pragma unroll
+    for (int q = 0; q < 27; ++q) {
+      sh[q][t] = U[q].h;
+      sl[q][t] = U[q].l;
+    }
+  }
   auto Uq = [&](int q) { return dd{sh[q][t], sl[q][t]}; };
   auto coef = [&](int q) {
     return active ? dd{__ldg(A.ch + q * A.ncells + cell), __ldg(A.cl + q * A.ncells + cell)} : dd{0.f, 0.f};
   };
-  {
-    const int r = blockIdx.y;   // right-hand side
-    int bias = 0;
-    {
-      // gather (Dirichlet nodes read as 0) and interpolate to the Gauss points
-      dd U[27];
-      const double* __restrict__ s = A.src + r * A.ld + base;
-      double X[27];
-      int emax = 0;
+  dd FZ[27];
 #pragma unroll
-      for (int l = 0; l < 27; ++l) {
-        const int a = l % 3, b = (l / 3) % 3, c = l / 9;
-        const double v = active ? __ldg(s + a + ug.sx * b + ug.sy * c) : 0.0;
-        X[l] = ((dmask >> l) & 1u) ? 0.0 : v;
-        emax = max(emax, (__double2hiint(X[l]) >> 20) & 0x7FF);
-      }
-      // one power-of-two scale per warp (its 8 x 4 cells share faces folded below): the largest
-      // input maps to [1, 2)
-      emax = int(__reduce_max_sync(0xffffffffu, unsigned(emax)));
-      bias = emax ? emax - 1023 : 0;
-#pragma unroll
-      for (int l = 0; l < 27; ++l) U[l] = d2dd_bits(X[l], bias);
-      dsweep<0>(U);
-      dsweep<1>(U);
-      dsweep<2>(U);
-#pragma unroll
-      for (int q = 0; q < 27; ++q) {
-        sh[q][t] = U[q].h;
-        sl[q][t] = U[q].l;
-      }
-    }
-    dd FZ[27];
-#pragma unroll
-    for (int q = 0; q < 27; ++q) {
-      const int qc = q / 9, bz = q - 9 * qc;
-      FZ[q] = dd_norm(dd_mul(coef(q), ddline(qc, Uq(bz), Uq(bz + 9), Uq(bz + 18))));
-    }
-#pragma unroll
-    for (int qc = 0; qc < 3; ++qc) {
-      dd R[9];
-#pragma unroll
-      for (int p = 0; p < 9; ++p) {
-        const int q = p + 9 * qc;
-        dd acc = dd_mul(dd{A.wmh[q], A.wml[q]}, Uq(q));
-#pragma unroll
-        for (int c2 = 0; c2 < 3; ++c2)
-          if (c2 != 1 || qc != 1) acc = dd_fma(acc, cD(c2, qc), FZ[p + 9 * c2]);
-        R[p] = acc;
-      }
-#pragma unroll
-      for (int qb = 0; qb < 3; ++qb)
-#pragma unroll
-        for (int qa = 0; qa < 3; ++qa) {
-          const int p = qa + 3 * qb, q = p + 9 * qc;
-          const int bx = q - qa, by = q - 3 * qb;
-          const dd cq = coef(q);
-          const dd fx = dd_mul(cq, ddline(qa, Uq(bx), Uq(bx + 1), Uq(bx + 2)));
-          const dd fy = dd_mul(cq, ddline(qb, Uq(by), Uq(by + 3), Uq(by + 6)));
-#pragma unroll
-          for (int m = 0; m < 3; ++m) {
-            if (qa != 1 || m != 1) R[p - qa + m] = dd_fma(R[p - qa + m], cD(qa, m), fx);
-            if (qb != 1 || m != 1) R[p - 3 * qb + 3 * m] = dd_fma(R[p - 3 * qb + 3 * m], cD(qb, m), fy);
-          }
-        }
-#pragma unroll
-      for (int p = 0; p < 9; ++p) R[p] = dd_norm(R[p]);
-#pragma unroll
-      for (int b = 0; b < 3; ++b) {   // x, transposed
-        const dd u0 = R[3 * b], u1 = R[3 * b + 1], u2 = R[3 * b + 2];
-        R[3 * b] = dd_norm(dd_add(dd_mul(cS(0, 0), u0), dd_mul(cS(2, 0), u2)));
-        R[3 * b + 1] = dd_norm(dd_add(dd_add(dd_mul(cS(0, 1), u0), u1), dd_mul(cS(2, 1), u2)));
-        R[3 * b + 2] = dd_norm(dd_add(dd_mul(cS(0, 2), u0), dd_mul(cS(2, 2), u2)));
-      }
-#pragma unroll
-      for (int a = 0; a < 3; ++a) {   // y, transposed
-        const dd u0 = R[a], u1 = R[a + 3], u2 = R[a + 6];
-        R[a] = dd_norm(dd_add(dd_mul(cS(0, 0), u0), dd_mul(cS(2, 0), u2)));
-        R[a + 3] = dd_norm(dd_add(dd_add(dd_mul(cS(0, 1), u0), u1), dd_mul(cS(2, 1), u2)));
-        R[a + 6] = dd_norm(dd_add(dd_mul(cS(0, 2), u0), dd_mul(cS(2, 2), u2)));
-      }
-#pragma unroll
-      for (int p = 0; p < 9; ++p) {
-        sh[p + 9 * qc][t] = R[p].h;
-        sl[p + 9 * qc][t] = R[p].l;
-      }
-    }
-    dd R[27];
-#pragma unroll
-    for (int q = 0; q < 27; ++q) R[q] = active ? Uq(q) : dd{0.f, 0.f};
-    dsweep_t<2>(R);
-    scatter_dd_warp(A.dst + r * A.ld, base, ug.sx, ug.sy, dmask, R, active, bias);
+  for (int q = 0; q < 27; ++q) {
+    const int qc = q / 9, bz = q - 9 * qc;
+    FZ[q] = dd_norm(dd_mul(coef(q), ddline(qc, Uq(bz), Uq(bz + 9), Uq(bz + 18))));
   }
+#pragma unroll
+  for (int qc = 0; qc < 3; ++qc) {
+    dd R[9];
+#pragma unroll
+    for (int p = 0; p < 9; ++p) {
+      const int q = p + 9 * qc;
+      dd acc = dd_mul(dd{A.wmh[q], A.wml[q]}, Uq(q));
+#pragma unroll
+      for (int c2 = 0; c2 < 3; ++c2)
+        if (c2 != 1 || qc != 1) acc = dd_fma(acc, cD(c2, qc), FZ[p + 9 * c2]);
+      R[p] = acc;
+    }
+#pragma unroll
+    for (int qb = 0; qb < 3; ++qb)
+#pragma unroll
+      for (int qa = 0; qa < 3; ++qa) {
+        const int p = qa + 3 * qb, q = p + 9 * qc;
+        const int bx = q - qa, by = q - 3 * qb;
+        const dd gx = ddline(qa, Uq(bx), Uq(bx + 1), Uq(bx + 2));
+        const dd gy = ddline(qb, Uq(by), Uq(by + 3), Uq(by + 6));
+        const dd cq = coef(q);
+        const dd fx = dd_mul(cq, gx), fy = dd_mul(cq, gy);
+#pragma unroll
+        for (int m = 0; m < 3; ++m) {
+          if (qa != 1 || m != 1) R[p - qa + m] = dd_fma(R[p - qa + m], cD(qa, m), fx);
+          if (qb != 1 || m != 1) R[p - 3 * qb + 3 * m] = dd_fma(R[p - 3 * qb + 3 * m], cD(qb, m), fy);
+        }
+      }
+#pragma unroll
+    for (int p = 0; p < 9; ++p) R[p] = dd_norm(R[p]);
+#pragma unroll
+    for (int b = 0; b < 3; ++b) {   // x, transposed
+      const dd u0 = R[3 * b], u1 = R[3 * b + 1], u2 = R[3 * b + 2];
+      R[3 * b] = dd_norm(dd_add(dd_mul(cS(0, 0), u0), dd_mul(cS(2, 0), u2)));
+      R[3 * b + 1] = dd_norm(dd_add(dd_add(dd_mul(cS(0, 1), u0), u1), dd_mul(cS(2, 1), u2)));
+      R[3 * b + 2] = dd_norm(dd_add(dd_mul(cS(0, 2), u0), dd_mul(cS(2, 2), u2)));
+    }
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {   // y, transposed
+      const dd u0 = R[a], u1 = R[a + 3], u2 = R[a + 6];
+      R[a] = dd_norm(dd_add(dd_mul(cS(0, 0), u0), dd_mul(cS(2, 0), u2)));
+      R[a + 3] = dd_norm(dd_add(dd_add(dd_mul(cS(0, 1), u0), u1), dd_mul(cS(2, 1), u2)));
+      R[a + 6] = dd_norm(dd_add(dd_mul(cS(0, 2), u0), dd_mul(cS(2, 2), u2)));
+    }
+    // the plane's values at the Gauss points are no longer needed: park the partial result there
+#pragma unroll
+    for (int p = 0; p < 9; ++p) {
+      sh[p + 9 * qc][t] = R[p].h;
+      sl[p + 9 * qc][t] = R[p].l;
+    }
+  }
+  dd R[27];
+#pragma unroll
+  for (int q = 0; q < 27; ++q) R[q] = Uq(q);
+  dsweep_t<2>(R);
+#pragma unroll
+  for (int q = 0; q < 27; ++q)
+    if (!active) R[q] = dd{0.f, 0.f};
+  scatter_dd_warp(A.dst + int64_t(blockIdx.y) * A.ld, base, ug.sx, ug.sy, dmask, R, active, bias);
 }
 
 // w_q h c_q of the Gauss-point coefficient table, split into high and low float parts
@@ -295,6 +299,7 @@ mf_status launch_scalar_df_uniform(mf_ctx* ctx, const mf_dofmap* m, const double
   DfArgs a{};
   a.src = src;
   a.dst = dst;
+  a.nrhs = nrhs;
   a.ld = ld;
   a.ch = ch;
   a.cl = cl;
