@@ -48,8 +48,13 @@ typedef int mf_status;
 #define MF_EUNSUPPORTED (-6)  /* valid request that the library does not implement */
 
 /* MF_DF64: fp64 vectors, cell arithmetic in double-float (pairs of fp32 with error-free
- * products and sums, 48-bit significand) on the fp32 pipes, which GB300 runs at ~62x its fp64
- * rate; accurate to a few 1e-14 relative to |A||u| componentwise. */
+ * products and sums, 47-48-bit significand) on the fp32 pipes, which GB300 runs at 64x its fp64
+ * rate; accurate to a few 1e-14 relative to |A||u| componentwise.  On uniform meshes (Helmholtz,
+ * heat without convection or Gauss-point rho_cp, Oseen without the melt-pool terms) the inputs are
+ * scaled by a power of two per warp of 32 cells (Oseen: velocity and pressure separately), so any
+ * fp64 magnitude keeps 47 bits relative to the largest input of those cells and inputs more than
+ * 2^126 below it count as zero; the other operators keep the fp32 exponent range (magnitudes
+ * between about 1e-38 and 3e38). */
 typedef enum { MF_F64 = 0, MF_F32 = 1, MF_F16 = 2, MF_BF16 = 3, MF_DF64 = 4 } mf_dtype;
 /* mf_solver_params.inner_arith value beside the dtypes: fp32 inner applies on the tensor cores */
 enum { MF_INNER_TENSOR_CORES = 16 };

@@ -690,6 +690,29 @@ mf_status apply_impl(mf_op* op, const T* src, T* dst, int nrhs, int64_t ld, bool
     if (transpose) return fail(MF_EUNSUPPORTED, "transpose of the Oseen operator");
     if (df && op->p.oseen_flags) return fail(MF_EUNSUPPORTED, "double-float Oseen applies without the melt-pool terms");
     const int64_t nu = op->map[0]->n_dofs;
+    if constexpr (sizeof(T) == 8) {
+      if (df && !op->p.oseen_flags) {
+        // double-float: one warp per velocity component over a brick of 32 cells
+        const int64_t nc = op->ncells;
+        if (!op->df_ready) {
+          MF_TRY(op->cm_df.alloc(sizeof(float) * 54 * nc));
+          MF_TRY(op->cv_df.alloc(sizeof(float) * 54 * nc));
+          MF_TRY(op->cb_df.alloc(sizeof(float) * 162 * nc));
+          MF_TRY(launch_split_pairs(c, op->cm64.as<double>(), 27 * nc, op->cm_df.as<float>(), op->cm_df.as<float>() + 27 * nc));
+          MF_TRY(launch_split_pairs(c, op->cv64.as<double>(), 27 * nc, op->cv_df.as<float>(), op->cv_df.as<float>() + 27 * nc));
+          MF_TRY(launch_split_pairs(c, op->cb64.as<double>(), 81 * nc, op->cb_df.as<float>(), op->cb_df.as<float>() + 81 * nc));
+          op->df_ready = true;
+        }
+        for (int r = 0; r < nrhs; ++r) {
+          MF_TRY(launch_oseen_df_uniform(c, op->map[0], reinterpret_cast<const double*>(src + r * ld),
+                                         reinterpret_cast<double*>(dst + r * ld), op->cm_df.as<float>(),
+                                         op->cv_df.as<float>(), op->cb_df.as<float>()));
+          MF_TRY(launch_dirichlet_copy(c, op->map[0], src + r * ld, dst + r * ld, 3, nu, 0, false));
+        }
+        op->variant = "oseen_q2q1/df64/tabulated/warp-per-component";
+        return MF_OK;
+      }
+    }
     for (int r = 0; r < nrhs; ++r) {
       OseenArgs<T> a = oseen_args<T>(op, src + r * ld, dst + r * ld);
       MF_TRY(launch_oseen_apply(c, op->map[0], prec, &a));

@@ -270,6 +270,257 @@ __global__ void __launch_bounds__(kThreads, 5) k_scalar_df_uniform(DfArgs A, Uni
   scatter_dd_warp(A.dst + int64_t(blockIdx.y) * A.ld, base, ug.sx, ug.sy, dmask, R, active, bias);
 }
 
+// ---------------------------------------------------------------------------------------------
+// Double-float Oseen apply (Q2 velocity / Q1 pressure, uniform mesh, folded Gauss-point coefficients
+// cm = w h^3 sigma rho, cv = w h mu, cb = w h^2 rho beta as float pairs).  A block of three warps
+// owns an 8 x 4 x 1 brick of 32 cells; warp c evaluates the test functions of velocity component c
+// for the brick's cells, reading the other components' Gauss-point values (for the symmetric part of
+// the stress) from shared memory.  Velocity and pressure inputs are scaled by their own powers of two
+// (the block's largest velocity / pressure input in [1, 2)); the coefficients are rescaled by exact
+// powers of two so that every velocity test term is accumulated in the larger of the two scales.
+
+struct DfOseenArgs {
+  const double* src;
+  double* dst;
+  int64_t nu;                  // velocity DoFs per component (pressure block starts at 3 nu)
+  const float *cmh, *cml;      // [27][ncells]
+  const float *cvh, *cvl;      // [27][ncells]
+  const float *cbh, *cbl;      // [3][27][ncells]
+  int64_t ncells;
+  float pwh[27][8], pwl[27][8];  // -h^2 w_q psi_n(x_q): pressure / continuity coupling
+  float wph[3][2], wpl[3][2];    // 1D w_g psi_a(g) (Q1 hat a at Gauss point g)
+  float mh2h, mh2l;              // -h^2
+};
+
+__device__ __forceinline__ dd dd_scale(dd a, float s) { return {a.h * s, a.l * s}; }   // s a power of two
+__device__ __forceinline__ float pow2f(int e) {  // 2^e for e in [-126, 127]; 0 below
+  return e < -126 ? 0.f : __uint_as_float(unsigned(min(e, 127) + 127) << 23);
+}
+
+__device__ __forceinline__ void oseen_df_component(const int C, const DfOseenArgs& A, const UniformGeom& ug,
+                                                   float (*sh)[27][32],
+                                                   float (*sl)[27][32], float (*ph)[32], float (*pl)[32],
+                                                   float (*ah)[32], float (*al)[32], int lane, bool active,
+                                                   int64_t cell, int64_t base, uint32_t dmask, float su, int bias_out,
+                                                   int bias_u, double* pdst, int64_t pbase, int64_t px, int64_t pxy) {
+  auto V = [&](int e, int q) { return dd{sh[e][q][lane], sl[e][q][lane]}; };
+  auto load = [&](const float* hh, const float* ll, int64_t off) {
+    return active ? dd_scale(dd{__ldg(hh + off), __ldg(ll + off)}, su) : dd{0.f, 0.f};
+  };
+  const int64_t nc = A.ncells;
+  // derivative of component e along direction d at Gauss point (qa, qb, qc)
+  auto deriv = [&](int e, int d, int qa, int qb, int qc) {
+    const int q = qa + 3 * qb + 9 * qc;
+    if (d == 0) return ddline(qa, V(e, q - qa), V(e, q - qa + 1), V(e, q - qa + 2));
+    if (d == 1) return ddline(qb, V(e, q - 3 * qb), V(e, q - 3 * qb + 3), V(e, q - 3 * qb + 6));
+    return ddline(qc, V(e, q - 9 * qc), V(e, q - 9 * qc + 9), V(e, q - 9 * qc + 18));
+  };
+  // derivative of component e along direction C (a run-time direction, the same for the whole warp)
+  auto derivC = [&](int e, int qa, int qb, int qc) {
+    const int q = qa + 3 * qb + 9 * qc;
+    const int qd = C == 0 ? qa : (C == 1 ? qb : qc), st = C == 0 ? 1 : (C == 1 ? 3 : 9);
+    const int b0 = q - qd * st;
+    return ddline(qd, V(e, b0), V(e, b0 + st), V(e, b0 + 2 * st));
+  };
+  // test flux of component C in direction d: cv (d_d u_C + d_C u_d), plus the pressure on the diagonal
+  auto flux = [&](int d, dd cv, dd gd, int qa, int qb, int qc) {
+    const int q = qa + 3 * qb + 9 * qc;
+    if (d == C) return dd_add(dd_mul(dd_add(cv, cv), gd), dd{ph[q][lane], pl[q][lane]});
+    return dd_mul(cv, dd_add(gd, derivC(d, qa, qb, qc)));
+  };
+  // z part of the test side, column by column, into this thread's accumulator column:
+  // Z(qa, qb, qc) = sum_{qc'} D[qc'][qc] F_z(qa, qb, qc')
+#pragma unroll 1
+  for (int p = 0; p < 9; ++p) {
+    const int qa = p % 3, qb = p / 3;
+    dd fz[3];
+#pragma unroll
+    for (int qc = 0; qc < 3; ++qc)
+      fz[qc] = dd_norm(flux(2, load(A.cvh, A.cvl, (p + 9 * qc) * nc + cell), deriv(C, 2, qa, qb, qc), qa, qb, qc));
+#pragma unroll
+    for (int qc = 0; qc < 3; ++qc) {
+      dd acc = dd{0.f, 0.f};
+#pragma unroll
+      for (int c2 = 0; c2 < 3; ++c2)
+        if (c2 != 1 || qc != 1) acc = dd_fma(acc, cD(c2, qc), fz[c2]);
+      ah[p + 9 * qc][lane] = acc.h;
+      al[p + 9 * qc][lane] = acc.l;
+    }
+  }
+  // plane by plane: value terms and the x and y parts, then the transposed x and y sweeps
+#pragma unroll 1
+  for (int qc = 0; qc < 3; ++qc) {
+    dd P[9];
+#pragma unroll
+    for (int p = 0; p < 9; ++p) P[p] = dd{ah[p + 9 * qc][lane], al[p + 9 * qc][lane]};
+#pragma unroll
+    for (int qb = 0; qb < 3; ++qb)
+#pragma unroll
+      for (int qa = 0; qa < 3; ++qa) {
+        const int p = qa + 3 * qb, q = p + 9 * qc;
+        const dd cm = load(A.cmh, A.cml, q * nc + cell), cv = load(A.cvh, A.cvl, q * nc + cell);
+        const dd gx = deriv(C, 0, qa, qb, qc), gy = deriv(C, 1, qa, qb, qc), gz = deriv(C, 2, qa, qb, qc);
+        // sigma rho u_C + rho beta . grad u_C
+        dd v = dd_mul(cm, V(C, q));
+        v = dd_fma(v, load(A.cbh, A.cbl, (0 * 27 + q) * nc + cell), gx);
+        v = dd_fma(v, load(A.cbh, A.cbl, (1 * 27 + q) * nc + cell), gy);
+        v = dd_fma(v, load(A.cbh, A.cbl, (2 * 27 + q) * nc + cell), gz);
+        P[p] = dd_add(P[p], v);
+        const dd fx = flux(0, cv, gx, qa, qb, qc), fy = flux(1, cv, gy, qa, qb, qc);
+#pragma unroll
+        for (int m = 0; m < 3; ++m) {
+          if (qa != 1 || m != 1) P[p - qa + m] = dd_fma(P[p - qa + m], cD(qa, m), fx);
+          if (qb != 1 || m != 1) P[p - 3 * qb + 3 * m] = dd_fma(P[p - 3 * qb + 3 * m], cD(qb, m), fy);
+        }
+      }
+#pragma unroll
+    for (int p = 0; p < 9; ++p) P[p] = dd_norm(P[p]);
+#pragma unroll
+    for (int b = 0; b < 3; ++b) {
+      const dd u0 = P[3 * b], u1 = P[3 * b + 1], u2 = P[3 * b + 2];
+      P[3 * b] = dd_norm(dd_add(dd_mul(cS(0, 0), u0), dd_mul(cS(2, 0), u2)));
+      P[3 * b + 1] = dd_norm(dd_add(dd_add(dd_mul(cS(0, 1), u0), u1), dd_mul(cS(2, 1), u2)));
+      P[3 * b + 2] = dd_norm(dd_add(dd_mul(cS(0, 2), u0), dd_mul(cS(2, 2), u2)));
+    }
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      const dd u0 = P[a], u1 = P[a + 3], u2 = P[a + 6];
+      P[a] = dd_norm(dd_add(dd_mul(cS(0, 0), u0), dd_mul(cS(2, 0), u2)));
+      P[a + 3] = dd_norm(dd_add(dd_add(dd_mul(cS(0, 1), u0), u1), dd_mul(cS(2, 1), u2)));
+      P[a + 6] = dd_norm(dd_add(dd_mul(cS(0, 2), u0), dd_mul(cS(2, 2), u2)));
+    }
+#pragma unroll
+    for (int p = 0; p < 9; ++p) {
+      ah[p + 9 * qc][lane] = P[p].h;
+      al[p + 9 * qc][lane] = P[p].l;
+    }
+  }
+  {
+    dd R[27];
+#pragma unroll
+    for (int q = 0; q < 27; ++q) R[q] = active ? dd{ah[q][lane], al[q][lane]} : dd{0.f, 0.f};
+    dsweep_t<2>(R);
+    scatter_dd_warp(A.dst + C * A.nu, base, ug.sx, ug.sy, dmask, R, active, bias_out);
+  }
+  // continuity: -int psi_n d_C u_C, this component's share (velocity scale), added by this warp; the
+  // Q1 test functions are tensor products, so the sum over the 27 points factorises into three 1D
+  // contractions with w_g psi_a(g) (the factor -h^2 applied at the end)
+  dd Rp[8];
+#pragma unroll
+  for (int n = 0; n < 8; ++n) Rp[n] = dd{0.f, 0.f};
+  auto wp = [&](int g, int a) { return dd{A.wph[g][a], A.wpl[g][a]}; };
+#pragma unroll 1
+  for (int qc = 0; qc < 3; ++qc) {
+    dd G[9];
+#pragma unroll
+    for (int p = 0; p < 9; ++p) G[p] = derivC(C, p % 3, p / 3, qc);
+    dd T[2][2];
+#pragma unroll
+    for (int na = 0; na < 2; ++na) {
+      dd T1[3];
+#pragma unroll
+      for (int qb = 0; qb < 3; ++qb)
+        T1[qb] = dd_norm(dd_add(dd_add(dd_mul(wp(0, na), G[3 * qb]), dd_mul(wp(1, na), G[3 * qb + 1])),
+                                dd_mul(wp(2, na), G[3 * qb + 2])));
+#pragma unroll
+      for (int nb = 0; nb < 2; ++nb)
+        T[na][nb] = dd_norm(dd_add(dd_add(dd_mul(wp(0, nb), T1[0]), dd_mul(wp(1, nb), T1[1])), dd_mul(wp(2, nb), T1[2])));
+    }
+#pragma unroll
+    for (int n = 0; n < 8; ++n) Rp[n] = dd_fma(Rp[n], wp(qc, n >> 2), T[n & 1][(n >> 1) & 1]);
+  }
+  if (active) {
+    const dd mh2{A.mh2h, A.mh2l};
+#pragma unroll
+    for (int n = 0; n < 8; ++n) {
+      const dd r = dd_mul(mh2, dd_norm(Rp[n]));
+      atomicAdd(pdst + pbase + (n & 1) + px * ((n >> 1) & 1) + pxy * (n >> 2),
+                f2d_bits(r.h, bias_u) + f2d_bits(r.l, bias_u));
+    }
+  }
+}
+
+__global__ void __launch_bounds__(96, 4) k_oseen_df_uniform(DfOseenArgs A, UniformGeom ug) {
+  __shared__ float sh[3][27][32], sl[3][27][32];   // velocity values at the Gauss points
+  __shared__ float ph[27][32], pl[27][32];         // pressure term at the Gauss points (output scale)
+  __shared__ float ah[3][27][32], al[3][27][32];   // each component's test-side accumulators
+  __shared__ int sE[3];
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int nbx = (ug.nx + 7) >> 3, nby = (ug.ny + 3) >> 2;
+  const int b = blockIdx.x;
+  const int i = (b % nbx) * 8 + (lane & 7), j = ((b / nbx) % nby) * 4 + (lane >> 3), k = b / (nbx * nby);
+  const bool active = i < ug.nx && j < ug.ny;
+  const int64_t cell = active ? i + int64_t(ug.nx) * (j + int64_t(ug.ny) * k) : 0;
+  const int64_t base = active ? 2 * int64_t(i) + ug.sx * (2 * int64_t(j)) + ug.sy * (2 * int64_t(k)) : 0;
+  const uint32_t dmask = active ? dirichlet_mask(ug, i, j, k) : 0u;
+  const int64_t px = ug.nx + 1, pxy = px * (ug.ny + 1);
+  const int64_t pbase = active ? i + px * (j + (ug.ny + 1) * int64_t(k)) : 0;
+  // raw inputs: this warp's velocity component and the cell's 8 pressures
+  double X[27], Pn[8];
+  int eu = 0, ep = 0;
+#pragma unroll
+  for (int l = 0; l < 27; ++l) {
+    const int a = l % 3, bb = (l / 3) % 3, c = l / 9;
+    const double v = active ? __ldg(A.src + w * A.nu + base + a + ug.sx * bb + ug.sy * c) : 0.0;
+    X[l] = ((dmask >> l) & 1u) ? 0.0 : v;
+    eu = max(eu, (__double2hiint(X[l]) >> 20) & 0x7FF);
+  }
+#pragma unroll
+  for (int n = 0; n < 8; ++n) {
+    Pn[n] = active ? __ldg(A.src + 3 * A.nu + pbase + (n & 1) + px * ((n >> 1) & 1) + pxy * (n >> 2)) : 0.0;
+    ep = max(ep, (__double2hiint(Pn[n]) >> 20) & 0x7FF);
+  }
+  eu = int(__reduce_max_sync(0xffffffffu, unsigned(eu)));
+  ep = int(__reduce_max_sync(0xffffffffu, unsigned(ep)));   // the same cells in every warp
+  if (lane == 0) sE[w] = eu;
+  __syncthreads();
+  eu = max(sE[0], max(sE[1], sE[2]));
+  const int bias_u = eu ? eu - 1023 : 0, bias_p = ep ? ep - 1023 : 0;
+  const int bias_out = max(bias_u, bias_p);
+  const float su = pow2f(bias_u - bias_out);   // velocity terms into the output scale
+  {
+    dd U[27];
+#pragma unroll
+    for (int l = 0; l < 27; ++l) U[l] = d2dd_bits(X[l], bias_u);
+    dsweep<0>(U);
+    dsweep<1>(U);
+    dsweep<2>(U);
+#pragma unroll
+    for (int q = 0; q < 27; ++q) {
+      sh[w][q][lane] = U[q].h;
+      sl[w][q][lane] = U[q].l;
+    }
+    // pressure term -h^2 w_q sum_n psi_n(x_q) p_n at the warp's plane of Gauss points
+    dd P[8];
+#pragma unroll
+    for (int n = 0; n < 8; ++n) P[n] = d2dd_bits(Pn[n], bias_p);
+    const float sp = pow2f(bias_p - bias_out);
+#pragma unroll
+    for (int p = 0; p < 9; ++p) {
+      const int q = p + 9 * w;
+      dd acc = dd{0.f, 0.f};
+#pragma unroll
+      for (int n = 0; n < 8; ++n) acc = dd_fma(acc, dd{A.pwh[q][n], A.pwl[q][n]}, P[n]);
+      acc = dd_scale(dd_norm(acc), sp);
+      ph[q][lane] = acc.h;
+      pl[q][lane] = acc.l;
+    }
+  }
+  __syncthreads();
+  // one code path for the three warps (component w at run time): the three instruction streams of a
+  // compile-time component kept warps waiting on instruction fetch
+  oseen_df_component(w, A, ug, sh, sl, ph, pl, ah[w], al[w], lane, active, cell, base, dmask, su, bias_out, bias_u,
+                     A.dst + 3 * A.nu, pbase, px, pxy);
+}
+
+__global__ void k_split_plain(const double* __restrict__ c, int64_t n, float* h, float* l) {
+  const int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (t >= n) return;
+  const float hi = __double2float_rn(c[t]);
+  h[t] = hi;
+  l[t] = __double2float_rn(c[t] - double(hi));
+}
+
 // w_q h c_q of the Gauss-point coefficient table, split into high and low float parts
 __global__ void k_split_coef(const double* __restrict__ c, int64_t ncells, double h, float* ch, float* cl) {
   const int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
@@ -312,6 +563,52 @@ mf_status launch_scalar_df_uniform(mf_ctx* ctx, const mf_dofmap* m, const double
   }
   const UniformGeom ug = uniform_geom(m);
   k_scalar_df_uniform<<<dim3(brick_blocks(ug.nx, ug.ny, ug.nz), nrhs), kThreads, 0, ctx->stream>>>(a, ug);
+  ctx->launches++;
+  MF_CUDA_TRY(cudaGetLastError());
+  return MF_OK;
+}
+
+mf_status launch_split_pairs(mf_ctx* ctx, const double* c, int64_t n, float* h, float* l) {
+  k_split_plain<<<int((n + 255) / 256), 256, 0, ctx->stream>>>(c, n, h, l);
+  ctx->launches++;
+  MF_CUDA_TRY(cudaGetLastError());
+  return MF_OK;
+}
+
+mf_status launch_oseen_df_uniform(mf_ctx* ctx, const mf_dofmap* mu, const double* src, double* dst, const float* cm,
+                                  const float* cv, const float* cb) {
+  MF_CUDA_TRY(upload_tables_here());
+  const Tables tb = make_tables();
+  DfOseenArgs a{};
+  a.src = src;
+  a.dst = dst;
+  a.nu = mu->n_dofs;
+  a.ncells = mu->n_cells;
+  const int64_t nc = mu->n_cells;
+  a.cmh = cm;
+  a.cml = cm + 27 * nc;
+  a.cvh = cv;
+  a.cvl = cv + 27 * nc;
+  a.cbh = cb;
+  a.cbl = cb + 81 * nc;
+  const double h = mu->mesh->h0;
+  for (int q = 0; q < 27; ++q)
+    for (int n = 0; n < 8; ++n) {
+      const double v = -(h * h) * tb.PWW[8 * q + n];
+      a.pwh[q][n] = float(v);
+      a.pwl[q][n] = float(v - double(a.pwh[q][n]));
+    }
+  for (int g = 0; g < 3; ++g)
+    for (int q1 = 0; q1 < 2; ++q1) {
+      const double v = tb.W[g] * tb.P[2 * g + q1];
+      a.wph[g][q1] = float(v);
+      a.wpl[g][q1] = float(v - double(a.wph[g][q1]));
+    }
+  a.mh2h = float(-(h * h));
+  a.mh2l = float(-(h * h) - double(a.mh2h));
+  const UniformGeom ug = uniform_geom(mu);
+  const int nb = ((ug.nx + 7) / 8) * ((ug.ny + 3) / 4) * ug.nz;
+  k_oseen_df_uniform<<<nb, 96, 0, ctx->stream>>>(a, ug);
   ctx->launches++;
   MF_CUDA_TRY(cudaGetLastError());
   return MF_OK;

@@ -125,6 +125,11 @@ mf_status tc_take_error();
 mf_status launch_df_coef_split(mf_ctx* ctx, const mf_dofmap* m, const double* qcoef64, float* ch, float* cl);
 mf_status launch_scalar_df_uniform(mf_ctx* ctx, const mf_dofmap* m, const double* src, double* dst, int nrhs,
                                    int64_t ld, const float* ch, const float* cl, double mass);
+// double-float Oseen apply on uniform meshes without the melt-pool terms: the folded coefficient
+// tables cm, cv (27 per cell) and cb (81 per cell) as float pairs (high parts, then low parts)
+mf_status launch_split_pairs(mf_ctx* ctx, const double* c, int64_t n, float* h, float* l);
+mf_status launch_oseen_df_uniform(mf_ctx* ctx, const mf_dofmap* mu, const double* src, double* dst, const float* cm,
+                                  const float* cv, const float* cb);
 // laser top-face load and its parameter derivatives (uniform maps)
 mf_status launch_laser(mf_ctx* ctx, const mf_dofmap* m, const double lz[5], double* f, double* dF);
 // dJ/dk_q = -w_q h grad(lambda) . grad(theta), [cell][27]
@@ -162,6 +167,7 @@ struct mf_op {
   bool tables_ready = false;
   mf::DevBuf qcoef_dfh, qcoef_dfl;  // [27][ncells] float pairs of w_q h c_q for the double-float kernel
   bool df_ready = false;
+  mf::DevBuf cm_df, cv_df, cb_df;   // Oseen: folded coefficients as float pairs (high, then low parts)
   bool diag_ready = false;
   int mode64 = 1, mode32 = 0;     // coefficient mode per precision (autotuned)
   int f64_prec = 0;               // arithmetic of fp64 applies inside solvers (PREC_F64 or PREC_DF64)

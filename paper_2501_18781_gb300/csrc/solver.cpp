@@ -1075,12 +1075,26 @@ mf_status autotune_measure(mf_op* op) {
           if (rep > 0) ms[v] = std::min(ms[v], double(t));
         }
       }
+      op->oseen_qouter64 = ms[1] < ms[0] ? 1 : 0;
+      // fp64-accurate arithmetic: the fp64 pipes or double-float pairs (without the melt-pool terms)
+      double df_ms = 1e30;
+      if (!op->p.oseen_flags) {
+        for (int rep = 0; rep < 4; ++rep) {
+          cudaEventRecord(a0, c->stream);
+          MF_TRY(apply_impl<double>(op, s.as<double>(), d.as<double>(), 1, n, false, PREC_DF64));
+          cudaEventRecord(a1, c->stream);
+          MF_CUDA_TRY(cudaEventSynchronize(a1));
+          float t;
+          cudaEventElapsedTime(&t, a0, a1);
+          if (rep > 0) df_ms = std::min(df_ms, double(t));
+        }
+      }
+      op->df64_faster = df_ms < std::min(ms[0], ms[1]);
       cudaEventDestroy(a0);
       cudaEventDestroy(a1);
-      op->oseen_qouter64 = ms[1] < ms[0] ? 1 : 0;
       char buf[256];
-      std::snprintf(buf, sizeof buf, "{\"kind\": %d, \"n\": %lld, \"component_outer_ms\": %.6g, \"qpoint_outer_ms\": %.6g}",
-                    op->p.kind, (long long)n, ms[0], ms[1]);
+      std::snprintf(buf, sizeof buf, "{\"kind\": %d, \"n\": %lld, \"component_outer_ms\": %.6g, \"qpoint_outer_ms\": %.6g, "
+                    "\"df64_ms\": %.6g}", op->p.kind, (long long)n, ms[0], ms[1], df_ms);
       op->tune_record = buf;
       return MF_OK;
     }
