@@ -140,8 +140,8 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(self.rows)}
 
 
-KERNEL_SOURCES = ("apply_f64.cu", "apply_f32.cu", "apply_df64.cu", "apply_kernels.cuh", "cellops.cuh",
-                  "scalar_local.cuh", "df64.cuh")
+KERNEL_SOURCES = ("apply_f64.cu", "apply_f32.cu", "apply_df64.cu", "apply_df64_uniform.cu", "apply_kernels.cuh",
+                  "cellops.cuh", "scalar_local.cuh", "df64.cuh")
 
 
 def kernel_hash():
@@ -338,10 +338,74 @@ def _timed_solve(op, b, reps=1, **kw):
             "rel_residual": info["rel_residual"], "status": info["status"]}
 
 
+def e2e_applies(op, src, steps, arith=None):
+    """Seconds for `steps` end-to-end applies (pinned host input -> device -> apply -> pinned host
+    output), pipelined and serial.  Pipelined: copies on two non-blocking streams and the apply on the
+    library's stream, ordered by events, with two device input and output buffers, so the upload of
+    step k+1 and the download of step k-1 overlap the apply of step k."""
+    import torch
+    n = src.numel()
+    hsrc = torch.empty(n, dtype=src.dtype, pin_memory=True)
+    hsrc.copy_(src.cpu())
+    hdst = [torch.empty(n, dtype=src.dtype, pin_memory=True) for _ in range(2)]
+    dsrc = [torch.empty_like(src) for _ in range(2)]
+    ddst = [torch.empty_like(src) for _ in range(2)]
+    comp = torch.cuda.current_stream()
+    up, down = torch.cuda.Stream(), torch.cuda.Stream()
+    ev = lambda: torch.cuda.Event()
+    in_ready, in_free = [ev(), ev()], [ev(), ev()]
+    out_ready, out_free = [ev(), ev()], [ev(), ev()]
+    for e in in_free + out_free:
+        e.record(comp)
+
+    def run(k_steps):
+        for k in range(k_steps):
+            b = k % 2
+            with torch.cuda.stream(up):
+                up.wait_event(in_free[b])
+                dsrc[b].copy_(hsrc, non_blocking=True)
+                in_ready[b].record(up)
+            comp.wait_event(in_ready[b])
+            comp.wait_event(out_free[b])
+            op.apply(dsrc[b], ddst[b], arith=arith)
+            in_free[b].record(comp)
+            out_ready[b].record(comp)
+            with torch.cuda.stream(down):
+                down.wait_event(out_ready[b])
+                hdst[b].copy_(ddst[b], non_blocking=True)
+                out_free[b].record(down)
+
+    run(4)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(up)
+    run(steps)
+    for s_ in (comp, up):
+        down.wait_stream(s_)
+    e1.record(down)
+    e1.synchronize()
+    piped = e0.elapsed_time(e1) / 1e3
+    # the same steps one after another on one stream
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(steps):
+        dsrc[0].copy_(hsrc, non_blocking=True)
+        op.apply(dsrc[0], ddst[0], arith=arith)
+        hdst[0].copy_(ddst[0], non_blocking=True)
+    e1.record()
+    e1.synchronize()
+    return piped, e0.elapsed_time(e1) / 1e3
+
+
 # ----------------------------------------------------------------------------- sub-measurements
 
 HEAT_SOLVERS = {"fp64": dict(solver="cg", precond="chebyshev"),
-                "mixed": dict(solver="defect_correction", precond="chebyshev", inner_tol=1e-4, inner_maxit=100)}
+                "mixed": dict(solver="defect_correction", precond="chebyshev", inner_tol=1e-4, inner_maxit=100),
+                # the same two with every fp64-accurate operator apply in double-float on the fp32 pipes
+                "fp64_df64_applies": dict(solver="cg", precond="chebyshev", fp64_arith="df64"),
+                "mixed_df64_outer": dict(solver="defect_correction", precond="chebyshev", inner_tol=1e-4,
+                                         inner_maxit=100, fp64_arith="df64")}
 
 
 def heat_solve_comparison(ctx, op, m, T_prev, n=128):
@@ -355,6 +419,7 @@ def heat_solve_comparison(ctx, op, m, T_prev, n=128):
     for name, kw in HEAT_SOLVERS.items():
         out[name] = _timed_solve(op, b, tol=1e-10, use_graph=True, **kw)
     out["speedup_mixed_over_fp64"] = out["fp64"]["seconds"] / out["mixed"]["seconds"]
+    out["speedup_df64_applies_over_fp64"] = out["fp64"]["seconds"] / out["fp64_df64_applies"]["seconds"]
     br = torch.tensor(syn.uniform_pm1(1, m.n_dofs), device="cuda")
     br[torch.tensor(m.export(cell_map=False, constraints=False, coords=False)["dirichlet"], device="cuda")] = 0
     rnd = {name: _timed_solve(op, br, tol=1e-10, use_graph=True, **kw) for name, kw in HEAT_SOLVERS.items()}
@@ -476,13 +541,18 @@ def oseen_solve(ctx, op, mu, mp):
     kw = dict(solver="gmres", precond="block_triangular", restart=50, maxit=400, tol=1e-10, velocity_steps=10,
               schur_tol=0.1, schur_maxit=30)
     out = {"solver": "fgmres(50) + block-triangular (fp32 inner)", "tol": 1e-10}
-    for key, graph in (("seconds_direct", False), ("seconds", True)):
-        op.solve(bt, use_graph=graph, **kw)                        # set-up + warm-up
+    for key, graph, ar in (("seconds_direct", False, "f64"), ("seconds", True, "f64"), ("seconds_df64_outer", True, "df64")):
+        op.solve(bt, use_graph=graph, fp64_arith=ar, **kw)         # set-up + warm-up
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        _, info = op.solve(bt, use_graph=graph, **kw)
+        _, info2 = op.solve(bt, use_graph=graph, fp64_arith=ar, **kw)
         torch.cuda.synchronize()
         out[key] = time.perf_counter() - t0
+        if ar == "f64":
+            info = info2
+        else:
+            out["df64_outer"] = {"iterations": info2["iterations"], "rel_residual": info2["rel_residual"],
+                                 "status": info2["status"]}
     out.update(iterations=info["iterations"], rel_residual=info["rel_residual"], status=info["status"],
                preconditioner="replayed CUDA graph", schur_steps_per_call=info["inner_steps"] / info["iterations"])
     return out
@@ -946,27 +1016,15 @@ def main():
     value = whole_job_rate(n, args.steps, world, total)
     mean = total / args.steps
 
-    # end to end through the public API: pinned host input -> device -> apply -> host output
-    hsrc = torch.empty(n, dtype=torch.float64, pin_memory=True)
-    hsrc.copy_(src.cpu())
-    hdst = torch.empty(n, dtype=torch.float64, pin_memory=True)
-    dsrc = torch.empty_like(src)
-    for _ in range(2):
-        dsrc.copy_(hsrc, non_blocking=True)
-        op.apply(dsrc, dst, arith=arith)
-        hdst.copy_(dst, non_blocking=True)
-    torch.cuda.synchronize()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record()
-    for _ in range(args.steps):
-        dsrc.copy_(hsrc, non_blocking=True)
-        op.apply(dsrc, dst, arith=arith)
-        hdst.copy_(dst, non_blocking=True)
-    e1.record()
-    e1.synchronize()
-    e2e_t = max_over_ranks(e0.elapsed_time(e1) / 1e3, dist, "cuda")
+    # end to end through the public API: every step copies its input from pinned host memory to the
+    # device, applies the operator and copies the result back to pinned host memory
+    e2e_t, e2e_serial_t = e2e_applies(op, src, args.steps, arith)
+    e2e_t = max_over_ranks(e2e_t, dist, "cuda")
     e2e = {"value": n * args.steps * world / e2e_t / 1e9, "unit": "GDoF/s",
-           "h2d_bytes_per_step": n * 8, "d2h_bytes_per_step": n * 8}
+           "h2d_bytes_per_step": n * 8, "d2h_bytes_per_step": n * 8,
+           "pipelined": "the host-to-device copy of step k+1 and the device-to-host copy of step k-1 run on two "
+                        "copy streams while step k's apply runs (double-buffered device vectors, event-ordered)",
+           "serial_value": n * args.steps * world / max_over_ranks(e2e_serial_t, dist, "cuda") / 1e9}
 
     peaks = measured_peaks()
     hbm = peaks.get("hbm_gbs", HBM_FALLBACK_GBS)
@@ -1023,7 +1081,7 @@ def main():
                                      "achieved": fl / ms / 1e9, "frac": fl / ms / 1e9 / FP64_PEAK_TFLOPS}
     if rank == 0 and not args.quick:
         out["solve"] = heat_solve_comparison(ctx, op, m, T_prev, args.n)
-        del op, m, T_prev, src, dst, src32, dst32, hsrc, hdst, dsrc
+        del op, m, T_prev, src, dst, src32, dst32
         torch.cuda.empty_cache()
         w = out["workloads"] = {}
         w["oseen_q2q1_interface_64"] = oseen_workload(ctx, flush)

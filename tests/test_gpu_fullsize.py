@@ -81,15 +81,16 @@ def test_oseen_64_fgmres_true_residual(ctx):
     mask = np.concatenate([np.tile(d, 3), np.zeros(mp.n_dofs, bool)])
     b[mask] = 0
     bt = torch.tensor(b, device="cuda")
-    x, info = op.solve(bt, solver="gmres", precond="block_triangular", restart=50, maxit=400, tol=1e-10,
-                       use_graph=True)
-    assert info["status"] == 0, info
-    r = bt - op.apply(x)
-    rel = (torch.linalg.vector_norm(r) / torch.linalg.vector_norm(bt)).item()
-    assert rel <= 1e-10 * (1 + 1e-3), (rel, info)
-    assert abs(rel - info["rel_residual"]) <= 1e-3 * max(rel, info["rel_residual"]), (rel, info)
-    assert np.all(x.cpu().numpy()[mask] == 0.0)
-    assert 0 < info["inner_steps"] <= 30 * info["iterations"]
+    for arith in ("f64", "df64"):   # outer applies on the fp64 pipes or in double-float
+        x, info = op.solve(bt, solver="gmres", precond="block_triangular", restart=50, maxit=400, tol=1e-10,
+                           use_graph=True, fp64_arith=arith)
+        assert info["status"] == 0, (arith, info)
+        r = bt - op.apply(x)
+        rel = (torch.linalg.vector_norm(r) / torch.linalg.vector_norm(bt)).item()
+        assert rel <= 1e-10 * (1 + 1e-3), (arith, rel, info)
+        assert abs(rel - info["rel_residual"]) <= 1e-3 * max(rel, info["rel_residual"]), (arith, rel, info)
+        assert np.all(x.cpu().numpy()[mask] == 0.0)
+        assert 0 < info["inner_steps"] <= 30 * info["iterations"]
 
 
 def _heat_case(n, wl, kq=False, beta=False):
