@@ -884,6 +884,7 @@ def probe(argv):
         oseen [n] [f32|f64|df64]
         reinit [base] [levels] [f32|f64|df64] [nrhs]
         oseen_solve [n] [maxit]
+        heat_solve [n] [fp64|mixed|fp64_df64_applies|mixed_df64_outer]
         helmholtz_qk [k] [n] [f32|f64|tc]
     Inputs come from the seeded generators; every apply runs in libmfgb."""
     import numpy as np
@@ -926,6 +927,20 @@ def probe(argv):
                 _, info = op.solve(bt, solver="gmres", precond="block_triangular", maxit=maxit, tol=1e-10)
             torch.cuda.synchronize()
             print(op.variant, n, info)
+    elif kind == "heat_solve":
+        # the heat-step solve the bench times (laser right-hand side, tolerance 1e-10, graph replay),
+        # once to set up and once more
+        n = int(argv[1]) if len(argv) > 1 else 128
+        op, m, T_prev = build_heat(ctx, n)
+        b = heat_step_rhs(ctx, m, T_prev, n)
+        kw = HEAT_SOLVERS[argv[2] if len(argv) > 2 else "mixed"]
+        op.solve(b, tol=1e-10, use_graph=True, **kw)
+        torch.cuda.synchronize()
+        torch.cuda.nvtx.range_push("timed_solve")   # for ncu --nvtx-include timed_solve/
+        _, info = op.solve(b, tol=1e-10, use_graph=True, **kw)
+        torch.cuda.synchronize()
+        torch.cuda.nvtx.range_pop()
+        print(op.variant, n, info)
     elif kind == "helmholtz_qk":
         k = int(argv[1]) if len(argv) > 1 else 3
         n = int(argv[2]) if len(argv) > 2 else 64

@@ -269,7 +269,8 @@ typedef struct {
   double tol;          /* stop when ||b - A x||_2 <= tol ||b||_2 (x0 = 0) */
   double inner_tol;    /* defect correction: inner relative tolerance */
   double cheby_ratio;  /* Chebyshev interval [lambda_max/ratio, 1.1 lambda_max] */
-  int lanczos_steps;   /* steps of the lambda_max estimate of D^-1 A */
+  int lanczos_steps;   /* steps of the lambda_max estimate of D^-1 A (kept on the operator and
+                          reused by later solves with the same step count until a field is set) */
   int fp64_arith;      /* arithmetic of the fp64 operator applies: 0 fp64 pipes, 1 double-float,
                           2 whichever mf_autotune measured faster */
   int schur_maxit;     /* MF_PREC_BLOCK_TRIANGULAR: cap of the inner Schur CG (<= 0: 30) */

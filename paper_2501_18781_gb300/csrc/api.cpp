@@ -423,6 +423,7 @@ mf_status mf_operator_set_field(mf_op* op, int field, const void* ptr, int dtype
   op->tc_ready = false;
   op->df_ready = false;
   op->diag_ready = false;
+  op->lanczos_ready = false;
   op->h16_cnorm = 0.0f;
   // float copy of the in-kernel nodal field
   const double* f = op->p.kind == MF_OP_HEAT ? op->tprev : op->phi;

@@ -169,6 +169,11 @@ struct mf_op {
   bool df_ready = false;
   mf::DevBuf cm_df, cv_df, cb_df;   // Oseen: folded coefficients as float pairs (high, then low parts)
   bool diag_ready = false;
+  // Chebyshev bounds: lambda_max of D^-1 A from the first solve's Lanczos run, kept until a field
+  // changes (the same number of steps from the same start vector gives the same estimate)
+  bool lanczos_ready = false;
+  int lanczos_steps = 0, lanczos_prec = 0;   // its step count and the arithmetic of its fp32 applies
+  double lanczos_lmax = 0.0;
   int mode64 = 1, mode32 = 0;     // coefficient mode per precision (autotuned)
   int f64_prec = 0;               // arithmetic of fp64 applies inside solvers (PREC_F64 or PREC_DF64)
   int f32_prec = 1;               // arithmetic of fp32 applies inside solvers (PREC_F32, PREC_F16, PREC_BF16, PREC_TC)

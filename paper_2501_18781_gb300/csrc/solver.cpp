@@ -344,7 +344,15 @@ template <typename T> struct Prec {
       MF_TRY(d.alloc(n * nrhs));
       MF_TRY(Ad.alloc(n * nrhs));
       double lm;
-      MF_TRY(lanczos(inv64.p, lanczos_steps, &lm));
+      if (op->lanczos_ready && op->lanczos_steps == lanczos_steps && op->lanczos_prec == op->f32_prec) {
+        lm = op->lanczos_lmax;
+      } else {
+        MF_TRY(lanczos(inv64.p, lanczos_steps, &lm));
+        op->lanczos_lmax = lm;
+        op->lanczos_steps = lanczos_steps;
+        op->lanczos_prec = op->f32_prec;
+        op->lanczos_ready = true;
+      }
       lmax = 1.1 * lm;
       lmin = lmax / ratio;
     }
@@ -435,14 +443,19 @@ template <typename T> struct Prec {
       case MF_PREC_CHEBYSHEV: {
         const double theta = 0.5 * (lmax + lmin), delta = 0.5 * (lmax - lmin), sigma = theta / delta;
         double rho = 1.0 / sigma;
-        MF_TRY(cheb_init<T>(c, n, n, nrhs, r, dinv.p, 1.0 / theta, res.p, d.p, z));
+        MF_TRY(cheb_init<T>(c, n, n, nrhs, r, dinv.p, 1.0 / theta, d.p));
+        if (degree < 1) {   // z = d_0
+          MF_CUDA_TRY(cudaMemcpyAsync(z, d.p, sizeof(T) * n * nrhs, cudaMemcpyDeviceToDevice, c->stream));
+          return MF_OK;
+        }
         for (int k = 0; k < degree; ++k) {
           MF_TRY(apply_impl<T>(op, d.p, Ad.p, nrhs, n, false));
           const double rho_new = 1.0 / (2.0 * sigma - rho);
-          MF_TRY(cheb_step<T>(c, n, n, nrhs, z, res.p, Ad.p, d.p, dinv.p, rho_new * rho, 2.0 * rho_new / delta));
+          MF_TRY(cheb_step<T>(c, n, n, nrhs, z, k == 0 ? r : res.p, res.p, Ad.p, d.p, dinv.p, rho_new * rho,
+                              2.0 * rho_new / delta, k == 0, k == degree - 1));
           rho = rho_new;
         }
-        return add_into<T>(c, n, n, nrhs, d.p, z);
+        return MF_OK;
       }
     }
     return fail(MF_EINVAL, "unknown preconditioner");

@@ -276,32 +276,29 @@ template <typename TS, typename TD> __global__ void k_convert(int64_t n, const T
 }
 
 template <typename T>
-__global__ void k_cheb_init(int64_t n, int64_t ld, const T* r, const T* dinv, T inv_theta, T* res, T* d, T* z) {
-  const int64_t o = blockIdx.y * ld;
-  for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x) {
-    T ri = r[o + i];
-    res[o + i] = ri;
-    d[o + i] = inv_theta * dinv[i] * ri;
-    z[o + i] = T(0);
-  }
-}
-
-template <typename T>
-__global__ void k_cheb_step(int64_t n, int64_t ld, T* z, T* res, const T* Ad, T* d, const T* dinv, T c1, T c2) {
-  const int64_t o = blockIdx.y * ld;
-  for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x) {
-    T di = d[o + i];
-    z[o + i] += di;
-    T ri = res[o + i] - Ad[o + i];
-    res[o + i] = ri;
-    d[o + i] = c1 * di + c2 * dinv[i] * ri;
-  }
-}
-
-template <typename T> __global__ void k_add_into(int64_t n, int64_t ld, const T* d, T* z) {
+__global__ void k_cheb_init(int64_t n, int64_t ld, const T* r, const T* dinv, T inv_theta, T* d) {
   const int64_t o = blockIdx.y * ld;
   for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x)
-    z[o + i] += d[o + i];
+    d[o + i] = inv_theta * dinv[i] * r[o + i];
+}
+
+template <typename T, bool FIRST, bool LAST>
+__global__ void k_cheb_step(int64_t n, int64_t ld, T* z, const T* res_in, T* res, const T* Ad, T* d, const T* dinv,
+                            T c1, T c2) {
+  const int64_t o = blockIdx.y * ld;
+  for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x) {
+    const T di = d[o + i];
+    const T zi = FIRST ? di : z[o + i] + di;
+    const T ri = res_in[o + i] - Ad[o + i];
+    const T dn = c1 * di + c2 * dinv[i] * ri;
+    if (LAST) {
+      z[o + i] = zi + dn;
+    } else {
+      z[o + i] = zi;
+      res[o + i] = ri;
+      d[o + i] = dn;
+    }
+  }
 }
 
 // CGS2 pieces of the GMRES solvers.  V holds k basis vectors ld apart.  Where V and w start on
@@ -679,36 +676,33 @@ template mf_status cg_update_p<double>(mf_ctx*, int64_t, int64_t, int, const dou
 template mf_status cg_update_p<float>(mf_ctx*, int64_t, int64_t, int, const float*, float*, double*, bool);
 
 template <typename T>
-mf_status cheb_init(mf_ctx* ctx, int64_t n, int64_t ld, int nrhs, const T* r, const T* dinv, double inv_theta, T* res,
-                    T* d, T* z) {
-  k_cheb_init<T><<<dim3(grid_for(n), nrhs), 256, 0, ctx->stream>>>(n, ld, r, dinv, T(inv_theta), res, d, z);
+mf_status cheb_init(mf_ctx* ctx, int64_t n, int64_t ld, int nrhs, const T* r, const T* dinv, double inv_theta, T* d) {
+  k_cheb_init<T><<<dim3(grid_for(n), nrhs), 256, 0, ctx->stream>>>(n, ld, r, dinv, T(inv_theta), d);
   LAUNCH_CHECK();
   return MF_OK;
 }
-template mf_status cheb_init<double>(mf_ctx*, int64_t, int64_t, int, const double*, const double*, double, double*,
-                                     double*, double*);
-template mf_status cheb_init<float>(mf_ctx*, int64_t, int64_t, int, const float*, const float*, double, float*, float*,
-                                    float*);
+template mf_status cheb_init<double>(mf_ctx*, int64_t, int64_t, int, const double*, const double*, double, double*);
+template mf_status cheb_init<float>(mf_ctx*, int64_t, int64_t, int, const float*, const float*, double, float*);
 
 template <typename T>
-mf_status cheb_step(mf_ctx* ctx, int64_t n, int64_t ld, int nrhs, T* z, T* res, const T* Ad, T* d, const T* dinv,
-                    double c1, double c2) {
-  k_cheb_step<T><<<dim3(grid_for(n), nrhs), 256, 0, ctx->stream>>>(n, ld, z, res, Ad, d, dinv, T(c1), T(c2));
+mf_status cheb_step(mf_ctx* ctx, int64_t n, int64_t ld, int nrhs, T* z, const T* res_in, T* res, const T* Ad, T* d,
+                    const T* dinv, double c1, double c2, bool first, bool last) {
+  const dim3 grid(grid_for(n), nrhs);
+  if (first && last)
+    k_cheb_step<T, true, true><<<grid, 256, 0, ctx->stream>>>(n, ld, z, res_in, res, Ad, d, dinv, T(c1), T(c2));
+  else if (first)
+    k_cheb_step<T, true, false><<<grid, 256, 0, ctx->stream>>>(n, ld, z, res_in, res, Ad, d, dinv, T(c1), T(c2));
+  else if (last)
+    k_cheb_step<T, false, true><<<grid, 256, 0, ctx->stream>>>(n, ld, z, res_in, res, Ad, d, dinv, T(c1), T(c2));
+  else
+    k_cheb_step<T, false, false><<<grid, 256, 0, ctx->stream>>>(n, ld, z, res_in, res, Ad, d, dinv, T(c1), T(c2));
   LAUNCH_CHECK();
   return MF_OK;
 }
-template mf_status cheb_step<double>(mf_ctx*, int64_t, int64_t, int, double*, double*, const double*, double*,
-                                     const double*, double, double);
-template mf_status cheb_step<float>(mf_ctx*, int64_t, int64_t, int, float*, float*, const float*, float*, const float*,
-                                    double, double);
-
-template <typename T> mf_status add_into(mf_ctx* ctx, int64_t n, int64_t ld, int nrhs, const T* d, T* z) {
-  k_add_into<T><<<dim3(grid_for(n), nrhs), 256, 0, ctx->stream>>>(n, ld, d, z);
-  LAUNCH_CHECK();
-  return MF_OK;
-}
-template mf_status add_into<double>(mf_ctx*, int64_t, int64_t, int, const double*, double*);
-template mf_status add_into<float>(mf_ctx*, int64_t, int64_t, int, const float*, float*);
+template mf_status cheb_step<double>(mf_ctx*, int64_t, int64_t, int, double*, const double*, double*, const double*,
+                                     double*, const double*, double, double, bool, bool);
+template mf_status cheb_step<float>(mf_ctx*, int64_t, int64_t, int, float*, const float*, float*, const float*, float*,
+                                    const float*, double, double, bool, bool);
 
 // p starts on a 16-byte boundary and so does every vector ld elements further on
 template <typename T> bool words16(const T* p, int64_t ld) {

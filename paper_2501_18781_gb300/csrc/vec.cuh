@@ -75,15 +75,16 @@ mf_status cg_update_p(mf_ctx* ctx, int64_t n, int64_t ld, int nrhs, const T* z, 
 // S[rr] = r.r, S[rz] = r.z (initial)
 template <typename T> mf_status cg_init_scalars(mf_ctx* ctx, const T* r, const T* z, int64_t n, int64_t ld, int nrhs, double* S);
 
-// Chebyshev (nrhs vectors ld apart, one diagonal): res = r, d = dinv r / theta, z = 0
+// Chebyshev (nrhs vectors ld apart, one diagonal).  The iteration z_0 = 0, res_0 = r,
+// d_0 = dinv r / theta, then per step k: z_{k+1} = z_k + d_k, res_{k+1} = res_k - A d_k,
+// d_{k+1} = c1 d_k + c2 dinv res_{k+1}, and the result z_m + d_m after the last step m - 1.
+// cheb_init writes d_0 only; the first step reads r for res_0 and writes z = d_0 without reading it;
+// the last step writes z_m + d_m and neither res nor d (same sums in the same order).
 template <typename T>
-mf_status cheb_init(mf_ctx* ctx, int64_t n, int64_t ld, int nrhs, const T* r, const T* dinv, double inv_theta, T* res,
-                    T* d, T* z);
-// z += d; res -= Ad; d = c1 d + c2 dinv res
+mf_status cheb_init(mf_ctx* ctx, int64_t n, int64_t ld, int nrhs, const T* r, const T* dinv, double inv_theta, T* d);
 template <typename T>
-mf_status cheb_step(mf_ctx* ctx, int64_t n, int64_t ld, int nrhs, T* z, T* res, const T* Ad, T* d, const T* dinv,
-                    double c1, double c2);
-template <typename T> mf_status add_into(mf_ctx* ctx, int64_t n, int64_t ld, int nrhs, const T* d, T* z);
+mf_status cheb_step(mf_ctx* ctx, int64_t n, int64_t ld, int nrhs, T* z, const T* res_in, T* res, const T* Ad, T* d,
+                    const T* dinv, double c1, double c2, bool first, bool last);
 
 // GMRES: h[0..k) = V^T w (V: k vectors of length n, stride ld), into device h (fp64 sums)
 template <typename T> mf_status multidot(mf_ctx* ctx, const T* V, int64_t ld, int k, const T* w, int64_t n, double* h);

@@ -91,7 +91,7 @@ def test_oseen_64_fgmres_true_residual(ctx):
         # the reported residual is ||b - A' x|| / ||b|| with A' the apply of the solve's arithmetic: by the
         # triangle inequality it lies within ||A' x - A x|| / ||b|| of the recomputed one
         delta = _apply_gap(op, bt, x, arith)
-        assert delta <= 1e-12, (arith, delta)
+        assert delta <= 1e-11, (arith, delta)   # a tenth of the tolerance: the solve saw its residual
         assert abs(rel - info["rel_residual"]) <= 1e-3 * max(rel, info["rel_residual"]) + delta, (arith, rel, info)
         assert np.all(x.cpu().numpy()[mask] == 0.0)
         assert 0 < info["inner_steps"] <= 30 * info["iterations"]
@@ -268,7 +268,9 @@ def test_qk_bench_size_sampled_rows(ctx, k, n):
 def _apply_gap(op, b, x, arith):
     """||A' x - A x|| / ||b|| for A' the fp64-accurate apply in ``arith`` ("df64" or the fp64 pipes) and A
     the fp64 apply: the most by which a residual the solver reports from A' can differ from the one
-    recomputed from A."""
+    recomputed from A.  Both applies are pinned componentwise to 1e-12 (|A| |x|)_i, and ||A| |x|| / ||b||
+    is large for the Oseen system, so the gap is held to a tenth of the solve tolerance: then the
+    residual the solver stopped on is the true one to 10 %."""
     if arith != "df64":
         return 0.0
     d = op.apply(x, arith="df64") - op.apply(x)
@@ -301,7 +303,7 @@ def test_heat_128_step_solves_true_residual(ctx):
             rel = _true_residual(op, rhs, x)[0]
             assert rel <= 1e-10 * (1 + 1e-3), (name, rel, info)
             delta = _apply_gap(op, rhs, x, kw.get("fp64_arith"))
-            assert delta <= 1e-12, (name, delta)
+            assert delta <= 1e-11, (name, delta)   # a tenth of the tolerance
             assert abs(rel - info["rel_residual"]) <= 1e-2 * max(rel, info["rel_residual"]) + delta, (name, rel, info)
             assert torch.all(x[d] == 0)
 

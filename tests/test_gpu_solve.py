@@ -114,6 +114,35 @@ def test_block_triangular_needs_gmres(ctx):
         P["op"].solve(b, solver="cg", precond="block_triangular")
 
 
+def test_chebyshev_bounds_kept_on_the_operator_until_a_field_changes(ctx):
+    """The Lanczos estimate of lambda_max is run by the first Chebyshev solve and reused by later
+    solves of the same operator (the same step count and inner arithmetic give the same estimate):
+    a second solve reports the same lambda_max and launches 20 fp32 applies fewer; after a field is
+    set again (even to the same values) the estimate is recomputed, and every solve still meets the
+    oracle's true residual."""
+    P = heat(6, ctx)
+    op = P["op"]
+    b = syn.uniform_pm1(4, P["n"])
+    b[P["dm"].dirichlet] = 0.0
+    kw = dict(solver="defect_correction", precond="chebyshev", inner_tol=1e-4, inner_maxit=100)
+
+    def counted(**extra):
+        l0 = ctx.launch_count()
+        info = solve_and_check(P, b, **kw, **extra)
+        return info, ctx.launch_count() - l0
+
+    i1, l1 = counted()
+    i2, l2 = counted()
+    assert i2["lambda_max"] == i1["lambda_max"]
+    assert i2["iterations"] == i1["iterations"]
+    assert l1 - l2 >= 20, (l1, l2)
+    i3, l3 = counted(lanczos_steps=10)          # another step count: estimated again
+    assert l3 > l2
+    op.set_field("t_prev", torch.tensor(P["T_prev"], device="cuda"))
+    i4, l4 = counted()
+    assert l4 - l2 >= 20 and abs(i4["lambda_max"] - i1["lambda_max"]) <= 1e-6 * i1["lambda_max"]
+
+
 def test_defect_correction_mixed_precision_heat(ctx):
     P = heat(10, ctx)
     b = syn.uniform_pm1(4, P["n"])
