@@ -425,6 +425,13 @@ def heat_solve_comparison(ctx, op, m, T_prev, n=128):
     rnd = {name: _timed_solve(op, br, tol=1e-10, use_graph=True, **kw) for name, kw in HEAT_SOLVERS.items()}
     rnd["speedup_mixed_over_fp64"] = rnd["fp64"]["seconds"] / rnd["mixed"]["seconds"]
     out["random_rhs"] = rnd
+    # the same solves on the sample the host oracle solves (cpu_baseline.heat_solve): same matrix,
+    # same right-hand side, for a same-size comparison
+    ops, ms, _ = build_heat(ctx, CPU_SAMPLE_N)
+    d = ms.export(cell_map=False, constraints=False, coords=False)["dirichlet"].astype(bool)
+    bs = torch.tensor(sample_heat_rhs(ms.n_dofs, d), device="cuda")
+    out[f"sample_{CPU_SAMPLE_N}"] = {name: _timed_solve(ops, bs, tol=1e-10, use_graph=True, **HEAT_SOLVERS[name])
+                                     for name in ("fp64", "mixed")}
     return out
 
 
@@ -758,7 +765,7 @@ def interface_sources_timing(ctx, op, mu, flush, reps=10):
 CPU_SAMPLE_N = 32   # 32^3 cells of the heat workload: 274,625 DoFs, 16.6M nonzeros (past the host caches)
 
 
-def _oracle_heat_matrix(n):
+def _oracle_heat_matrix(n, with_map=False):
     """The oracle's assembled heat-step matrix of the headline workload on an n^3 mesh (the same
     recipe: 600 um box, Dirichlet bottom, k(T^n) from the seeded hot spot)."""
     import synthetic as syn
@@ -768,7 +775,38 @@ def _oracle_heat_matrix(n):
     p = wl.params
     dm = omesh.uniform_dofmap(n, wl.lo, wl.hi, 2, 1 << 4)
     T = syn.heat_initial_temperature(*dm.dof_coords().T, p["laser"]["radius"], wl.hi[2])
-    return asm.heat_matrix(dm, p["rhocp"], p["dt"], p["k0"], p["t_boil"], T_prev=T), wl.name
+    A = asm.heat_matrix(dm, p["rhocp"], p["dt"], p["k0"], p["t_boil"], T_prev=T)
+    return (A, wl.name, dm) if with_map else (A, wl.name)
+
+
+def sample_heat_rhs(n_dofs, dirichlet):
+    """The seeded uniform right-hand side of the heat-step sample solves, zero on Dirichlet rows (the
+    same vector on the host and on the GPU)."""
+    import synthetic as syn
+    b = syn.uniform_pm1(1, n_dofs)
+    b[dirichlet] = 0.0
+    return b
+
+
+def cpu_oracle_heat_solve(n=CPU_SAMPLE_N):
+    """The oracle's fp64 CG with Chebyshev(4)-Jacobi (lambda_max from 20 Lanczos steps, x 1.1, on
+    [lambda_max / 30, lambda_max]) to 1e-10 on the n^3 instance of the heat step (one host core,
+    scipy's CSR product): the CPU side of the headline solve, at the sample size the oracle assembles
+    in about a second."""
+    import synthetic as syn
+    from oracle import krylov
+    t0 = time.perf_counter()
+    A, name, dm = _oracle_heat_matrix(n, with_map=True)
+    t_asm = time.perf_counter() - t0
+    b = sample_heat_rhs(dm.n_dofs, dm.dirichlet)
+    op = lambda v: A @ v
+    t0 = time.perf_counter()
+    diag = A.diagonal()
+    lmax = 1.1 * krylov.lanczos_lambda_max(op, diag, syn.uniform_pm1(9, dm.n_dofs), steps=20)
+    _, its, res = krylov.cg(op, b, krylov.chebyshev(op, diag, lmax / 30.0, lmax, 4), tol=1e-10)
+    return {"workload": name, "n_dofs": dm.n_dofs, "cores": 1, "assembly_seconds": t_asm,
+            "seconds": time.perf_counter() - t0, "cg_iterations": its, "rel_residual": res,
+            "solver": "fp64 CG + Chebyshev(4)-Jacobi, Lanczos set-up included"}
 
 
 def _spmv_worker(args):
@@ -991,6 +1029,7 @@ def main():
     if rank == 0 and world == 1 and not args.no_cpu_baseline and not args.quick:
         cpu = cpu_oracle_baseline()
         cpu["helmholtz_16_cg"] = cpu_oracle_helmholtz_cg()
+        cpu["heat_solve"] = cpu_oracle_heat_solve()
 
     import torch
     torch.cuda.set_device(local)

@@ -282,21 +282,59 @@ __global__ void k_cheb_init(int64_t n, int64_t ld, const T* r, const T* dinv, T 
     d[o + i] = inv_theta * dinv[i] * r[o + i];
 }
 
+// One element of the Chebyshev step (the recurrence is spelled out where cheb_step is declared).
 template <typename T, bool FIRST, bool LAST>
+__device__ __forceinline__ void cheb_elem(T& zo, T zi_in, T ri_in, T adi, T& di_io, T dv, T c1, T c2, T& ro) {
+  const T di = di_io;
+  const T zi = FIRST ? di : zi_in + di;
+  const T ri = ri_in - adi;
+  const T dn = c1 * di + c2 * dv * ri;
+  if (LAST) {
+    zo = zi + dn;
+  } else {
+    zo = zi;
+    ro = ri;
+    di_io = dn;
+  }
+}
+
+template <typename T, int W> struct alignas(sizeof(T) * W) ChebWord {
+  T c[W];
+};
+
+// W = 1: one element per step of a thread; W > 1: 16-byte words of W elements (every vector starts
+// on a 16-byte boundary and so does each right-hand side ld elements further on), the last n % W
+// elements one by one.
+template <typename T, bool FIRST, bool LAST, int W>
 __global__ void k_cheb_step(int64_t n, int64_t ld, T* z, const T* res_in, T* res, const T* Ad, T* d, const T* dinv,
                             T c1, T c2) {
-  const int64_t o = blockIdx.y * ld;
-  for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x) {
-    const T di = d[o + i];
-    const T zi = FIRST ? di : z[o + i] + di;
-    const T ri = res_in[o + i] - Ad[o + i];
-    const T dn = c1 * di + c2 * dinv[i] * ri;
-    if (LAST) {
-      z[o + i] = zi + dn;
-    } else {
-      z[o + i] = zi;
-      res[o + i] = ri;
-      d[o + i] = dn;
+  using V = ChebWord<T, W>;
+  const int64_t o = blockIdx.y * ld, stride = int64_t(gridDim.x) * blockDim.x;
+  const int64_t t0 = int64_t(blockIdx.x) * blockDim.x + threadIdx.x, nw = n / W;
+  for (int64_t w = t0; w < nw; w += stride) {
+    V dv = reinterpret_cast<const V*>(d + o)[w];
+    const V rv = reinterpret_cast<const V*>(res_in + o)[w];
+    const V av = reinterpret_cast<const V*>(Ad + o)[w];
+    const V iv = reinterpret_cast<const V*>(dinv)[w];
+    V zv;
+    if (!FIRST) zv = reinterpret_cast<const V*>(z + o)[w];
+    V zo, ro;
+#pragma unroll
+    for (int c = 0; c < W; ++c)
+      cheb_elem<T, FIRST, LAST>(zo.c[c], FIRST ? T(0) : zv.c[c], rv.c[c], av.c[c], dv.c[c], iv.c[c], c1, c2, ro.c[c]);
+    reinterpret_cast<V*>(z + o)[w] = zo;
+    if (!LAST) {
+      reinterpret_cast<V*>(res + o)[w] = ro;
+      reinterpret_cast<V*>(d + o)[w] = dv;
+    }
+  }
+  for (int64_t i = nw * W + t0; i < n; i += stride) {
+    T di = d[o + i], zo, ro;
+    cheb_elem<T, FIRST, LAST>(zo, FIRST ? T(0) : z[o + i], res_in[o + i], Ad[o + i], di, dinv[i], c1, c2, ro);
+    z[o + i] = zo;
+    if (!LAST) {
+      res[o + i] = ro;
+      d[o + i] = di;
     }
   }
 }
@@ -684,18 +722,30 @@ mf_status cheb_init(mf_ctx* ctx, int64_t n, int64_t ld, int nrhs, const T* r, co
 template mf_status cheb_init<double>(mf_ctx*, int64_t, int64_t, int, const double*, const double*, double, double*);
 template mf_status cheb_init<float>(mf_ctx*, int64_t, int64_t, int, const float*, const float*, double, float*);
 
+template <typename T, int W>
+static void cheb_launch(mf_ctx* ctx, dim3 grid, int64_t n, int64_t ld, T* z, const T* res_in, T* res, const T* Ad,
+                        T* d, const T* dinv, T c1, T c2, bool first, bool last) {
+  if (first && last)
+    k_cheb_step<T, true, true, W><<<grid, 256, 0, ctx->stream>>>(n, ld, z, res_in, res, Ad, d, dinv, c1, c2);
+  else if (first)
+    k_cheb_step<T, true, false, W><<<grid, 256, 0, ctx->stream>>>(n, ld, z, res_in, res, Ad, d, dinv, c1, c2);
+  else if (last)
+    k_cheb_step<T, false, true, W><<<grid, 256, 0, ctx->stream>>>(n, ld, z, res_in, res, Ad, d, dinv, c1, c2);
+  else
+    k_cheb_step<T, false, false, W><<<grid, 256, 0, ctx->stream>>>(n, ld, z, res_in, res, Ad, d, dinv, c1, c2);
+}
+
 template <typename T>
 mf_status cheb_step(mf_ctx* ctx, int64_t n, int64_t ld, int nrhs, T* z, const T* res_in, T* res, const T* Ad, T* d,
                     const T* dinv, double c1, double c2, bool first, bool last) {
   const dim3 grid(grid_for(n), nrhs);
-  if (first && last)
-    k_cheb_step<T, true, true><<<grid, 256, 0, ctx->stream>>>(n, ld, z, res_in, res, Ad, d, dinv, T(c1), T(c2));
-  else if (first)
-    k_cheb_step<T, true, false><<<grid, 256, 0, ctx->stream>>>(n, ld, z, res_in, res, Ad, d, dinv, T(c1), T(c2));
-  else if (last)
-    k_cheb_step<T, false, true><<<grid, 256, 0, ctx->stream>>>(n, ld, z, res_in, res, Ad, d, dinv, T(c1), T(c2));
+  const auto a16 = [&](const void* p) { return reinterpret_cast<uintptr_t>(p) % 16 == 0; };
+  const bool words = a16(z) && a16(res_in) && a16(res) && a16(Ad) && a16(d) && a16(dinv) &&
+                     (nrhs == 1 || (ld * int64_t(sizeof(T))) % 16 == 0);
+  if (words)
+    cheb_launch<T, int(16 / sizeof(T))>(ctx, grid, n, ld, z, res_in, res, Ad, d, dinv, T(c1), T(c2), first, last);
   else
-    k_cheb_step<T, false, false><<<grid, 256, 0, ctx->stream>>>(n, ld, z, res_in, res, Ad, d, dinv, T(c1), T(c2));
+    cheb_launch<T, 1>(ctx, grid, n, ld, z, res_in, res, Ad, d, dinv, T(c1), T(c2), first, last);
   LAUNCH_CHECK();
   return MF_OK;
 }
