@@ -398,6 +398,14 @@ mf_status mf_autotune(mf_op* op, const char* cache_path);
 /* Describe the variant the next apply will launch (host string, owned by the library). */
 const char* mf_operator_variant(const mf_op* op);
 
+/* Select an apply variant by name, in place of mf_autotune's choice (until the next mf_autotune):
+ *   "q2_line"  1: fp64 and fp32 applies of Q2 Helmholtz and heat operators (uniform mesh, forward,
+ *              no convection, no per-point heat capacity) by the line-per-thread kernel, nine threads
+ *              per cell with the coefficients from the Gauss-point tables; 0: one thread per cell.
+ *              Other applies (double-float, octree, convection, transpose) are unaffected.
+ * MF_EINVAL for a NULL argument, an unknown name or a value other than 0 or 1.  Host only. */
+mf_status mf_operator_set_variant(mf_op* op, const char* name, int value);
+
 /* Number of kernel launches the library has issued on this context so far. */
 int64_t mf_context_launch_count(const mf_ctx* ctx);
 

@@ -310,6 +310,10 @@ class Operator:
     def variant(self):
         return _lib.load().mf_operator_variant(self.h).decode()
 
+    def set_variant(self, name, value):
+        """Select an apply variant by name in place of the autotuner's choice ("q2_line": 0 or 1)."""
+        check(_lib.load().mf_operator_set_variant(self.h, name.encode(), int(value)))
+
     def __del__(self):
         try:
             if self.h:

@@ -121,6 +121,7 @@ SIGNATURES = {
                                         DP, DP, P, P, P]),
     "mf_autotune": (C.c_int, [P, C.c_char_p]),
     "mf_operator_variant": (C.c_char_p, [P]),
+    "mf_operator_set_variant": (C.c_int, [P, C.c_char_p, C.c_int]),
     "mf_context_launch_count": (I64, [P]),
     "mf_meltpool_create": (C.c_int, [P, C.POINTER(MeltPoolParams), P, P, P, P, C.POINTER(P)]),
     "mf_meltpool_destroy": (None, [P]),

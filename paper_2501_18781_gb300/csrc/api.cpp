@@ -384,6 +384,18 @@ mf_status mf_operator_size(const mf_op* op, int64_t* n) {
 
 const char* mf_operator_variant(const mf_op* op) { return op ? op->variant.c_str() : ""; }
 
+mf_status mf_operator_set_variant(mf_op* op, const char* name, int value) {
+  MF_GUARD_BEGIN
+  if (!op || !name) return fail(MF_EINVAL, "NULL argument");
+  if (value != 0 && value != 1) return fail(MF_EINVAL, "variant values are 0 or 1");
+  if (std::string(name) == "q2_line") {
+    op->q2_line64 = op->q2_line32 = value;
+    return MF_OK;
+  }
+  return fail(MF_EINVAL, std::string("unknown variant name: ") + name);
+  MF_GUARD_END
+}
+
 mf_status mf_operator_set_field(mf_op* op, int field, const void* ptr, int dtype, int64_t n) {
   MF_GUARD_BEGIN
   if (!op || !ptr) return fail(MF_EINVAL, "NULL argument");
@@ -751,6 +763,17 @@ mf_status apply_impl(mf_op* op, const T* src, T* dst, int nrhs, int64_t ld, bool
       op->variant = std::string(kind == K_HELM ? "helmholtz" : "heat") + "/uniform/df64/tabulated/planes";
       return MF_OK;
     }
+  }
+  if ((f32 ? op->q2_line32 : op->q2_line64) && (prec == PREC_F64 || prec == PREC_F32) && op->map[0]->uniform &&
+      (kind == K_HELM || kind == K_HEAT) && !beta && !transpose && !op->rhocp_user) {
+    // small meshes: 9 threads per cell (the degree-2 line kernel), coefficients from the tables
+    MF_TRY(ensure_tables(op));
+    const T* coef = f32 ? reinterpret_cast<const T*>(op->qcoef32.as<float>())
+                        : reinterpret_cast<const T*>(op->qcoef64.as<double>());
+    for (int r = 0; r < nrhs; ++r) MF_TRY(launch_q2_line<T>(c, op->map[0], src + r * ld, dst + r * ld, coef, value_coef(op)));
+    MF_TRY(launch_dirichlet_copy(c, op->map[0], src, dst, nrhs, ld, 0, f32));
+    op->variant = std::string(kind == K_HELM ? "helmholtz" : "heat") + "/uniform" + pname + "/tabulated/line-per-thread";
+    return MF_OK;
   }
   ScalarArgs<T> a = scalar_args<T>(op, src, dst, nrhs, ld);
   MF_TRY(launch_scalar_apply(c, op->map[0], kind, m, beta, transpose, prec, &a));

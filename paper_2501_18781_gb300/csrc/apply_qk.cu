@@ -3,6 +3,10 @@
 // B).  A cell is worked on by (k+1)^2 threads; thread (i, j) keeps the z-line through (i, j) in
 // registers, contractions along z run in registers and those along x and y through shared memory.
 // The coefficient a is tabulated per Gauss point in fp64 (stored fp64 and fp32, [cell][q]).
+// The same kernel at k = 2 (the Gauss-Lobatto points {0, 1/2, 1} are the Q2 nodes) serves the Q2
+// Helmholtz and heat operators on small uniform meshes, where one thread per cell leaves most SMs
+// idle: 9 threads per cell, the Q2 Gauss-point tables read in their [q][cell] layout, Dirichlet
+// nodes read as 0 and left out of the scatter.
 #include <cmath>
 
 #include "ops.h"
@@ -16,12 +20,24 @@ namespace {
 
 // 1D tables of degree K (P = K + 1 support points, P Gauss points): S[q][a] = l_a(g_q),
 // Sp[q][a] = l_a'(g_q), D[q][p] = lambda_p'(g_q) (Lagrange basis through the Gauss points), W[q].
+__constant__ double cQS2[9], cQSp2[9], cQD2[9], cQW2[3];
+__constant__ float fQS2[9], fQD2[9], fQW2[3];
 __constant__ double cQS3[16], cQSp3[16], cQD3[16], cQW3[4];
 __constant__ double cQS4[25], cQSp4[25], cQD4[25], cQW4[5];
 __constant__ float fQS3[16], fQD3[16], fQW3[4];
 __constant__ float fQS4[25], fQD4[25], fQW4[5];
 
 template <typename T, int K> struct Qt;
+template <> struct Qt<double, 2> {
+  static __device__ __forceinline__ double S(int q, int a) { return cQS2[3 * q + a]; }
+  static __device__ __forceinline__ double D(int q, int p) { return cQD2[3 * q + p]; }
+  static __device__ __forceinline__ double W(int q) { return cQW2[q]; }
+};
+template <> struct Qt<float, 2> {
+  static __device__ __forceinline__ float S(int q, int a) { return fQS2[3 * q + a]; }
+  static __device__ __forceinline__ float D(int q, int p) { return fQD2[3 * q + p]; }
+  static __device__ __forceinline__ float W(int q) { return fQW2[q]; }
+};
 template <> struct Qt<double, 3> {
   static __device__ __forceinline__ double S(int q, int a) { return cQS3[4 * q + a]; }
   static __device__ __forceinline__ double D(int q, int p) { return cQD3[4 * q + p]; }
@@ -50,7 +66,16 @@ struct Tables1D {
 // Gauss points and weights on [0, 1] (closed forms of the Legendre roots) and Gauss-Lobatto
 // support points (the ends and the roots of P_k').
 void rule(int k, double* g, double* w, double* x) {
-  if (k == 3) {
+  if (k == 2) {
+    const double a = std::sqrt(3.0 / 5.0);
+    const double gg[3] = {-a, 0.0, a}, ww[3] = {5.0 / 9.0, 8.0 / 9.0, 5.0 / 9.0};
+    for (int i = 0; i < 3; ++i) {
+      g[i] = 0.5 * (1.0 + gg[i]);
+      w[i] = 0.5 * ww[i];
+    }
+    const double xx[3] = {0.0, 0.5, 1.0};
+    for (int i = 0; i < 3; ++i) x[i] = xx[i];
+  } else if (k == 3) {
     const double a = std::sqrt(3.0 / 7.0 - 2.0 / 7.0 * std::sqrt(6.0 / 5.0));
     const double b = std::sqrt(3.0 / 7.0 + 2.0 / 7.0 * std::sqrt(6.0 / 5.0));
     const double wa = (18.0 + std::sqrt(30.0)) / 36.0, wb = (18.0 - std::sqrt(30.0)) / 36.0;
@@ -115,7 +140,7 @@ cudaError_t upload_qk_tables() {
   static bool done = false;
   if (done) return cudaSuccess;
   cudaError_t e = cudaSuccess;
-  for (int k = 3; k <= 4; ++k) {
+  for (int k = 2; k <= 4; ++k) {
     const Tables1D t = make_qk_tables(k);
     const int n = (k + 1) * (k + 1);
     float f[25];
@@ -126,7 +151,10 @@ cudaError_t upload_qk_tables() {
       for (int i = 0; i < cnt; ++i) f[i] = float(src[i]);
       if (e == cudaSuccess) e = cudaMemcpyToSymbol(sym, f, cnt * sizeof(float));
     };
-    if (k == 3) {
+    if (k == 2) {
+      up(cQS2, t.S, n); up(cQSp2, t.Sp, n); up(cQD2, t.D, n); up(cQW2, t.W, 3);
+      upf(fQS2, t.S, n); upf(fQD2, t.D, n); upf(fQW2, t.W, 3);
+    } else if (k == 3) {
       up(cQS3, t.S, n); up(cQSp3, t.Sp, n); up(cQD3, t.D, n); up(cQW3, t.W, 4);
       upf(fQS3, t.S, n); upf(fQD3, t.D, n); upf(fQW3, t.W, 4);
     } else {
@@ -138,29 +166,41 @@ cudaError_t upload_qk_tables() {
   return e;
 }
 
-template <int K> __host__ __device__ constexpr int cells_per_block() { return K == 3 ? 8 : 5; }
+template <int K> __host__ __device__ constexpr int cells_per_block() { return K == 2 ? 14 : (K == 3 ? 8 : 5); }
 
 struct QkGeom {
   int nx, ny, nz;
   int64_t sx, sy;  // lattice strides (K n + 1 per axis)
   int64_t ncells;
   double h;
+  int64_t cq, cc;  // coefficient of Gauss point q of a cell at coef[q cq + cell cc]
+  uint32_t dir;    // Dirichlet faces (bits x-, x+, y-, y+, z-, z+): their nodes read as 0, get no update
 };
 
-// Cell and in-cell thread coordinates of this thread; false for the idle tail of the block.
+// Cell and in-cell thread coordinates of this thread and the Dirichlet nodes of its z-line (bit z);
+// false for the idle tail of the block.
 template <int K>
-__device__ __forceinline__ bool qk_thread(const QkGeom& g, int& slot, int& i, int& j, int64_t& cell, int64_t& base) {
+__device__ __forceinline__ bool qk_thread(const QkGeom& g, int& slot, int& i, int& j, int64_t& cell, int64_t& base,
+                                          uint32_t& zdir) {
   constexpr int P = K + 1, CPB = cells_per_block<K>();
   const int t = threadIdx.x;
   slot = t / (P * P);
   const int r = t % (P * P);
   i = r % P;
   j = r / P;
+  zdir = 0u;
   if (slot >= CPB) return false;
   cell = int64_t(blockIdx.x) * CPB + slot;
   if (cell >= g.ncells) return false;
   const int64_t cx = cell % g.nx, cy = (cell / g.nx) % g.ny, cz = cell / (int64_t(g.nx) * g.ny);
   base = K * cx + i + g.sx * (K * cy + j) + g.sy * (K * cz);
+  if (g.dir) {
+    const bool side = ((g.dir & 1u) && cx == 0 && i == 0) || ((g.dir & 2u) && cx == g.nx - 1 && i == K) ||
+                      ((g.dir & 4u) && cy == 0 && j == 0) || ((g.dir & 8u) && cy == g.ny - 1 && j == K);
+    zdir = side ? (1u << P) - 1u : 0u;
+    if ((g.dir & 16u) && cz == 0) zdir |= 1u;
+    if ((g.dir & 32u) && cz == g.nz - 1) zdir |= 1u << K;
+  }
   return true;
 }
 
@@ -173,12 +213,13 @@ __global__ void __launch_bounds__(128) k_helmholtz_qk(QkGeom g, const T* __restr
   __shared__ T s0[CPB][P3], s1[CPB][P3], s2[CPB][P3];
   int slot, i, j;
   int64_t cell = 0, base = 0;
-  const bool on = qk_thread<K>(g, slot, i, j, cell, base);
+  uint32_t zdir;
+  const bool on = qk_thread<K>(g, slot, i, j, cell, base, zdir);
   const int sl = slot < CPB ? slot : 0;
   T r[P], v[P];
   // nodes -> Gauss points: z in registers, then y and x through shared memory
 #pragma unroll
-  for (int z = 0; z < P; ++z) r[z] = on ? __ldg(src + base + g.sy * z) : T(0);
+  for (int z = 0; z < P; ++z) r[z] = (on && !((zdir >> z) & 1u)) ? __ldg(src + base + g.sy * z) : T(0);
 #pragma unroll
   for (int q = 0; q < P; ++q) {
     T s = T(0);
@@ -225,7 +266,7 @@ __global__ void __launch_bounds__(128) k_helmholtz_qk(QkGeom g, const T* __restr
       }
       const int q = i + P * (j + P * qz);
       const T w = Qt<T, K>::W(i) * Qt<T, K>::W(j) * Qt<T, K>::W(qz);
-      const T a = on ? coef[cell * P3 + q] : T(0);
+      const T a = on ? coef[q * g.cq + cell * g.cc] : T(0);
       const T c = w * a * h;
       R[qz] = w * mass * h3 * U[qz];
       Fz[qz] = c * gz;
@@ -270,7 +311,7 @@ __global__ void __launch_bounds__(128) k_helmholtz_qk(QkGeom g, const T* __restr
     T s = T(0);
 #pragma unroll
     for (int q = 0; q < P; ++q) s += Qt<T, K>::S(q, z) * v[q];
-    atomicAdd(dst + base + g.sy * z, s);
+    if (!((zdir >> z) & 1u)) atomicAdd(dst + base + g.sy * z, s);
   }
 }
 
@@ -367,6 +408,9 @@ QkGeom qk_geom(const mf_dofmap* m) {
   g.sy = g.sx * (m->R[1] + 1);
   g.ncells = m->n_cells;
   g.h = m->mesh->h0;
+  g.cq = 1;
+  g.cc = int64_t(m->degree + 1) * (m->degree + 1) * (m->degree + 1);
+  g.dir = 0u;
   return g;
 }
 
@@ -404,6 +448,23 @@ mf_status launch_helmholtz_qk(mf_ctx* ctx, const mf_dofmap* m, const T* src, T* 
 template mf_status launch_helmholtz_qk<double>(mf_ctx*, const mf_dofmap*, const double*, double*, const double*,
                                                double);
 template mf_status launch_helmholtz_qk<float>(mf_ctx*, const mf_dofmap*, const float*, float*, const float*, double);
+
+template <typename T>
+mf_status launch_q2_line(mf_ctx* ctx, const mf_dofmap* m, const T* src, T* dst, const T* coef, double mass) {
+  if (m->degree != 2 || !m->uniform) return fail(MF_EINVAL, "the line kernel takes uniform Q2 maps");
+  MF_CUDA_TRY(upload_qk_tables());
+  QkGeom g = qk_geom(m);
+  g.cq = m->n_cells;   // the Q2 Gauss-point tables are [q][cell]
+  g.cc = 1;
+  g.dir = m->dirichlet_faces;
+  const int nb = int((g.ncells + cells_per_block<2>() - 1) / cells_per_block<2>());
+  k_helmholtz_qk<T, 2><<<nb, 128, 0, ctx->stream>>>(g, src, dst, coef, T(mass));
+  ctx->launches++;
+  MF_CUDA_TRY(cudaGetLastError());
+  return MF_OK;
+}
+template mf_status launch_q2_line<double>(mf_ctx*, const mf_dofmap*, const double*, double*, const double*, double);
+template mf_status launch_q2_line<float>(mf_ctx*, const mf_dofmap*, const float*, float*, const float*, double);
 
 mf_status launch_qk_diag(mf_ctx* ctx, const mf_dofmap* m, const double* coef, double mass, double* diag) {
   MF_CUDA_TRY(upload_qk_tables());

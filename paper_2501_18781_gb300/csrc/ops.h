@@ -109,6 +109,11 @@ mf_status launch_qk_coef(mf_ctx* ctx, const mf_dofmap* m, const double* phi, dou
                          double eps, double* c64, float* c32);
 template <typename T>
 mf_status launch_helmholtz_qk(mf_ctx* ctx, const mf_dofmap* m, const T* src, T* dst, const T* coef, double mass);
+// Q2 Helmholtz / heat (no convection) on a uniform map by the line-per-thread kernel of degree 2:
+// coef the [q][cell] Gauss-point table of the scalar coefficient, mass the value coefficient; dst is
+// accumulated (zero it first); Dirichlet rows receive nothing
+template <typename T>
+mf_status launch_q2_line(mf_ctx* ctx, const mf_dofmap* m, const T* src, T* dst, const T* coef, double mass);
 mf_status launch_qk_diag(mf_ctx* ctx, const mf_dofmap* m, const double* coef, double mass, double* diag);
 // Q3 Helmholtz on the tensor cores (fp32 vectors, dst accumulated; coef per tile of 128 cells,
 // [tile][q][row], from launch_tc_coef_layout).  A launch returns MF_ETIMEOUT when an earlier one
@@ -180,7 +185,8 @@ struct mf_op {
   float h16_cnorm = 0.0f;         // 16-bit applies: power of two >= every coefficient (0: not computed)
   int block = 128;                // octree cells per block (autotuned: 64 or 128)
   int persistent_blocks = 0;      // > 0: persistent launch with this many blocks per SM (autotuned)
-  bool df64_faster = false;       // autotuned: double-float beats the fp64 pipes (used when fp64_arith = 2)
+  bool df64_faster = false;
+  int q2_line64 = 0, q2_line32 = 0;  // uniform Q2 Helmholtz / heat: the line-per-thread kernel (autotuned)       // autotuned: double-float beats the fp64 pipes (used when fp64_arith = 2)
   int oseen_qouter64 = 0;         // Oseen fp64 kernel variant (autotuned)
   std::string tune_record;        // JSON of the last autotuning
   std::string variant;

@@ -982,8 +982,9 @@ std::string tune_key(const mf_op* op) {
 std::string tune_choice(const mf_op* op) {
   char buf[256];
   std::snprintf(buf, sizeof buf, "\"mode64\": %d, \"mode32\": %d, \"block\": %d, \"persistent_blocks\": %d, "
-                "\"df64_faster\": %d, \"oseen_qouter64\": %d, \"qk_f32_tc\": %d", op->mode64, op->mode32, op->block,
-                op->persistent_blocks, op->df64_faster ? 1 : 0, op->oseen_qouter64, op->qk_f32_tc);
+                "\"df64_faster\": %d, \"oseen_qouter64\": %d, \"qk_f32_tc\": %d, \"q2_line64\": %d, "
+                "\"q2_line32\": %d", op->mode64, op->mode32, op->block, op->persistent_blocks, op->df64_faster ? 1 : 0,
+                op->oseen_qouter64, op->qk_f32_tc, op->q2_line64, op->q2_line32);
   return buf;
 }
 
@@ -1020,6 +1021,12 @@ bool apply_cached_choice(mf_op* op, const char* cache_path) {
   op->df64_faster = v[4] != 0;
   op->oseen_qouter64 = v[5] != 0;
   op->qk_f32_tc = v[6] != 0;
+  // records written before the line kernel was a choice leave it off
+  int l64 = 0, l32 = 0;
+  read_int(hit, "q2_line64", &l64);
+  read_int(hit, "q2_line32", &l32);
+  op->q2_line64 = l64 != 0;
+  op->q2_line32 = l32 != 0;
   op->tune_record = hit.substr(0, hit.size() - 1);
   return true;
 }
@@ -1165,20 +1172,34 @@ mf_status autotune_measure(mf_op* op) {
     }
     op->block = shapes[best_shape][0];
     op->persistent_blocks = shapes[best_shape][1];
-    // 3) fp64-accurate arithmetic: fp64 pipes vs double-float on the fp32 pipes
-    double f64_ms, df_ms;
+    // 3) fp64-accurate arithmetic: fp64 pipes vs double-float on the fp32 pipes; on uniform Q2
+    //    Helmholtz / heat operators also the line-per-thread kernel in fp64 and fp32 (small meshes)
+    double f64_ms, df_ms, line64_ms = -1.0, line32_ms = -1.0;
+    op->q2_line64 = op->q2_line32 = 0;
     MF_TRY(time_variant(PREC_F64, &f64_ms));
     MF_TRY(time_variant(PREC_DF64, &df_ms));
-    op->df64_faster = df_ms < f64_ms;
+    const int kind = scalar_kind(op);
+    if (op->map[0]->uniform && op->map[0]->degree == 2 && (kind == K_HELM || kind == K_HEAT) && !heat_convection(op) &&
+        !op->rhocp_user) {
+      op->q2_line64 = 1;
+      MF_TRY(time_variant(PREC_F64, &line64_ms));
+      op->q2_line64 = 0;
+      op->q2_line32 = 1;
+      MF_TRY(time_variant(PREC_F32, &line32_ms));
+      op->q2_line64 = line64_ms < f64_ms ? 1 : 0;
+      op->q2_line32 = line32_ms < shape_ms[best_shape] ? 1 : 0;
+    }
+    op->df64_faster = df_ms < (op->q2_line64 ? line64_ms : f64_ms);
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     char buf[512];
     std::snprintf(buf, sizeof buf,
                   "{\"kind\": %d, \"n\": %lld, \"f64_inkernel_ms\": %.6g, \"f64_tabulated_ms\": %.6g, "
                   "\"f32_inkernel_ms\": %.6g, \"f32_tabulated_ms\": %.6g, \"block\": %d, \"persistent_blocks\": %d, "
-                  "\"f32_shape_ms\": %.6g, \"f64_ms\": %.6g, \"df64_ms\": %.6g}",
+                  "\"f32_shape_ms\": %.6g, \"f64_ms\": %.6g, \"df64_ms\": %.6g, \"f64_line_ms\": %.6g, "
+                  "\"f32_line_ms\": %.6g}",
                   op->p.kind, (long long)n, mode_ms[0][0], mode_ms[0][1], mode_ms[1][0], mode_ms[1][1], op->block,
-                  op->persistent_blocks, shape_ms[best_shape], f64_ms, df_ms);
+                  op->persistent_blocks, shape_ms[best_shape], f64_ms, df_ms, line64_ms, line32_ms);
     op->tune_record = buf;
     return MF_OK;
   } catch (...) {

@@ -74,6 +74,30 @@ def test_heat_k_of_T_with_dirichlet(ctx, mode):
     assert np.array_equal(v[d], u.cpu().numpy()[d])
 
 
+@pytest.mark.parametrize("case", [("helmholtz", 3, 0), ("helmholtz", 5, 1), ("heat", 4, 0), ("heat", 7, 1)])
+def test_q2_line_per_thread_kernel(ctx, case):
+    """The degree-2 instance of the line-per-thread kernel (nine threads per cell, coefficients from
+    the Q2 Gauss-point tables) against the oracle: fp64 at 1e-12 and fp32 at 2e-5 componentwise, with
+    the Dirichlet bottom face of the heat operator and two right-hand sides per call; then the
+    one-thread-per-cell kernel again on the same operator."""
+    from paper_2501_18781_gb300 import MFError
+    kind, n, mode = case
+    P = (heat if kind == "heat" else helmholtz)(n, ctx, coef_mode=mode)
+    op = P["op"]
+    op.set_variant("q2_line", 1)
+    check_apply(P, nrhs=2)
+    assert op.variant.endswith("/f32/tabulated/line-per-thread"), op.variant
+    op.apply(torch.zeros(P["n"], dtype=torch.float64, device="cuda"))
+    assert op.variant.endswith("/f64/tabulated/line-per-thread"), op.variant
+    op.set_variant("q2_line", 0)
+    check_apply(P)
+    assert "line-per-thread" not in op.variant
+    with pytest.raises(MFError):
+        op.set_variant("q2_line", 2)
+    with pytest.raises(MFError):
+        op.set_variant("no_such_variant", 1)
+
+
 def test_heat_convection_kq_and_transpose(ctx):
     P = heat(9, ctx, with_beta=True, kq=True)
     check_apply(P)
