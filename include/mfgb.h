@@ -264,7 +264,10 @@ typedef struct {
   int cheby_degree;    /* operator applications per Chebyshev preconditioner call */
   int maxit;           /* iteration cap (outer steps for defect correction) */
   int inner_maxit;     /* defect correction: inner CG cap */
-  int use_graph;       /* replay recorded CUDA graphs: the CG iteration body, and each call of
+  int use_graph;       /* replay recorded CUDA graphs: CG steps with the stopping test on the
+                          device, eight per replay when n * nrhs <= 2^20 and one otherwise (a
+                          system that has stopped is left untouched by the remaining steps; the
+                          reported iterations are the steps it took), and each call of
                           MF_PREC_BLOCK_TRIANGULAR (recorded at its second call) */
   double tol;          /* stop when ||b - A x||_2 <= tol ||b||_2 (x0 = 0) */
   double inner_tol;    /* defect correction: inner relative tolerance */

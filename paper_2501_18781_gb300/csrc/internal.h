@@ -70,6 +70,7 @@ constexpr int kScalarsGmres = 1536;  // 2 (m + 1) <= 128
 constexpr int kScalarsScale = 2048;  // 64
 constexpr int kScalarsHeat = 2560;   // 8
 constexpr int kScalarsTri = 3072;    // Oseen block-triangular inner solves: 2 (k + 1) + 8 <= 512
+constexpr int kScalarsCGSteps = 3584;  // 64 step counters of the batched CG's on-device stopping test
 constexpr int kScalarsTotal = 4096;
 }  // namespace mf
 

@@ -29,6 +29,8 @@ template <typename T> mf_status oseen_coupling(mf_op* op, int which, const T* sr
 // device-side stopping test and Givens kernels of the inner solves (solver_kernels.cu)
 mf_status dev_cg_tol_init(mf_ctx* c, double* S, double tol2);
 mf_status dev_cg_tol_check(mf_ctx* c, double* S, double* steps);
+mf_status dev_cg_tol_init_batched(mf_ctx* c, double* S, double tol2, int nrhs);
+mf_status dev_cg_tol_check_batched(mf_ctx* c, double* S, double* steps, int nrhs);
 mf_status dev_gmres_begin(mf_ctx* c, const double* nrm2, double* G, int m);
 mf_status dev_gmres_column(mf_ctx* c, const double* h, double* G, int m, int j);
 mf_status dev_gmres_solve(mf_ctx* c, const double* G, int m, int j, double* y);
@@ -490,6 +492,8 @@ namespace {
 // Batched preconditioned CG in precision T from x = 0: nrhs systems stored n apart.
 // Stops each system at ||r_k|| <= tol_r ||b_r|| (recursive residual).
 template <typename T> struct CG {
+  static constexpr int kGraphSteps = 8;              // CG steps per graph replay on small systems
+  static constexpr int64_t kSmallSystem = 1 << 20;   // unknowns (times right-hand sides) of a small system
   mf_op* op;
   Prec<T>* P;
   int nrhs;
@@ -515,23 +519,27 @@ template <typename T> struct CG {
     return MF_OK;
   }
 
-  mf_status iteration(T* x, double* S) {
+  // One CG step for every system.  With steps (the on-device stopping test): systems whose active
+  // flag is 0 are left untouched, and the test runs at the end of the step.
+  mf_status iteration(T* x, double* S, double* steps = nullptr) {
     mf_ctx* c = op->ctx;
     const int64_t n = op->n;
+    const bool skip = steps != nullptr;
     MF_TRY(apply_impl<T>(op, p.p, Ap.p, nrhs, n, false));
     MF_TRY(cg_alpha<T>(c, p.p, Ap.p, n, n, nrhs, S));
     if (P->kind == MF_PREC_JACOBI) {
-      MF_TRY(cg_update_xr<T>(c, n, n, nrhs, x, r.p, p.p, Ap.p, P->dinv.p, z.p, 1, S));
-      MF_TRY(cg_update_p<T>(c, n, n, nrhs, z.p, p.p, S));
+      MF_TRY(cg_update_xr<T>(c, n, n, nrhs, x, r.p, p.p, Ap.p, P->dinv.p, z.p, 1, S, skip));
+      MF_TRY(cg_update_p<T>(c, n, n, nrhs, z.p, p.p, S, skip));
     } else if (P->kind == MF_PREC_NONE) {
-      MF_TRY(cg_update_xr<T>(c, n, n, nrhs, x, r.p, p.p, Ap.p, nullptr, nullptr, 0, S));
-      MF_TRY(cg_update_p<T>(c, n, n, nrhs, r.p, p.p, S));
+      MF_TRY(cg_update_xr<T>(c, n, n, nrhs, x, r.p, p.p, Ap.p, nullptr, nullptr, 0, S, skip));
+      MF_TRY(cg_update_p<T>(c, n, n, nrhs, r.p, p.p, S, skip));
     } else {
-      MF_TRY(cg_update_xr<T>(c, n, n, nrhs, x, r.p, p.p, Ap.p, nullptr, nullptr, 2, S));
+      MF_TRY(cg_update_xr<T>(c, n, n, nrhs, x, r.p, p.p, Ap.p, nullptr, nullptr, 2, S, skip));
       MF_TRY(P->apply(r.p, z.p));
       MF_TRY(cg_rz<T>(c, r.p, z.p, n, n, nrhs, S));
-      MF_TRY(cg_update_p<T>(c, n, n, nrhs, z.p, p.p, S));
+      MF_TRY(cg_update_p<T>(c, n, n, nrhs, z.p, p.p, S, skip));
     }
+    if (steps) MF_TRY(dev_cg_tol_check_batched(c, S, steps, nrhs));
     return MF_OK;
   }
 
@@ -568,25 +576,47 @@ template <typename T> struct CG {
       }
     }
     int it = 0;
+    // With graph replay the stopping test runs on the device after every step, and on small
+    // systems (launch-bound steps) a replay holds kGraphSteps steps, so the host waits once per
+    // kGraphSteps steps; steps after a system has stopped leave it untouched (their applies still
+    // run, which is why large systems replay one step at a time), and the device counts the steps
+    // each system took.
+    double* steps = use_graph ? c->scalars.as<double>() + kScalarsCGSteps : nullptr;
+    const int per = use_graph ? (n * nrhs <= kSmallSystem ? kGraphSteps : 1) : check_every;
+    if (steps) {
+      MF_CUDA_TRY(cudaMemsetAsync(steps, 0, sizeof(double) * nrhs, c->stream));
+      MF_TRY(dev_cg_tol_init_batched(c, S, tol * tol, nrhs));
+    }
     if (use_graph && !exec)
       MF_TRY(capture_graph(c, [&]() {
-        for (int k = 0; k < check_every; ++k) MF_TRY(iteration(x, S));
+        for (int k = 0; k < per; ++k) MF_TRY(iteration(x, S, steps));
         return MF_OK;
       }, &exec, &graph_kernels));
+    std::vector<double> hsteps(nrhs, 0.0);
     while (ndone < nrhs && it < maxit) {
-      if (exec) {
+      if (exec && maxit - it >= per) {
         MF_CUDA_TRY(cudaGraphLaunch(exec, c->stream));
         c->launches += graph_kernels;
+        it += per;
       } else {
-        for (int k = 0; k < check_every; ++k) MF_TRY(iteration(x, S));
+        const int m = std::min(per, maxit - it);
+        for (int k = 0; k < m; ++k) MF_TRY(iteration(x, S, steps));
+        it += m;
       }
-      it += check_every;
+      if (steps) MF_CUDA_TRY(cudaMemcpyAsync(hsteps.data(), steps, sizeof(double) * nrhs, cudaMemcpyDeviceToHost,
+                                             c->stream));
       MF_TRY(sync_copy(c, hS, S, size_t(nrhs) * S_NSCAL));
       for (int k = 0; k < nrhs; ++k) {
         if (done[k]) continue;
         const double rk = hS[k * S_NSCAL + S_RR];
         if (!std::isfinite(rk)) return fail(MF_ENOTCONV, "CG breakdown (non-finite residual)");
-        if (rk <= tol * tol * bb[k]) {
+        if (steps) {   // the device stopped this system: converged, or p.Ap <= 0 (breakdown)
+          if (hS[k * S_NSCAL + S_ACTIVE] == 0.0) {
+            if (!(rk <= tol * tol * bb[k])) return fail(MF_ENOTCONV, "CG breakdown (p.Ap <= 0)");
+            done[k] = 1;
+            ++ndone;
+          }
+        } else if (rk <= tol * tol * bb[k]) {
           done[k] = 1;
           ++ndone;
           hS[k * S_NSCAL + S_ACTIVE] = 0.0;
@@ -597,7 +627,7 @@ template <typename T> struct CG {
     }
     MF_CUDA_TRY(cudaStreamSynchronize(c->stream));
     for (int k = 0; k < nrhs; ++k) relres[k] = bb[k] > 0 ? std::sqrt(hS[k * S_NSCAL + S_RR] / bb[k]) : 0.0;
-    *iters = it;
+    *iters = steps ? int(*std::max_element(hsteps.begin(), hsteps.end())) : it;
     return ndone == nrhs ? MF_OK : MF_ENOTCONV;
   }
 };

@@ -51,6 +51,23 @@ __global__ void k_cg_tol_check(double* S, double* steps) {
   if (steps && S[S_ACTIVE] != 0.0) steps[0] += 1.0;
   if (S[S_RR] <= S[7] || !(S[S_PAP] > 0.0)) S[S_ACTIVE] = 0.0;
 }
+// the same for the nrhs systems of the batched CG (one thread each; a system already stopped by the
+// host stays stopped): the threshold tol2 ||r_0||^2 into slot 7, then per iteration the step count
+// and the stopping test
+__global__ void k_cg_tol_init_batched(double* S, double tol2, int nrhs) {
+  const int k = threadIdx.x;
+  if (k >= nrhs) return;
+  double* s = S + k * S_NSCAL;
+  s[7] = tol2 * s[S_RR];
+}
+__global__ void k_cg_tol_check_batched(double* S, double* steps, int nrhs) {
+  const int k = threadIdx.x;
+  if (k >= nrhs) return;
+  double* s = S + k * S_NSCAL;
+  if (s[S_ACTIVE] == 0.0) return;
+  steps[k] += 1.0;
+  if (s[S_RR] <= s[7] || !(s[S_PAP] > 0.0)) s[S_ACTIVE] = 0.0;
+}
 // G layout (m = restart): cs[m], sn[m], g[m + 1], inv (1/norm of the newest vector), R[m][m]
 __global__ void k_gmres_begin(const double* nrm2, double* G, int m) {
   const double beta = sqrt(nrm2[0]);
@@ -134,6 +151,14 @@ mf_status dev_cg_tol_init(mf_ctx* c, double* S, double tol2) {
 }
 mf_status dev_cg_tol_check(mf_ctx* c, double* S, double* steps) {
   k_cg_tol_check<<<1, 1, 0, c->stream>>>(S, steps);
+  LAUNCHED();
+}
+mf_status dev_cg_tol_init_batched(mf_ctx* c, double* S, double tol2, int nrhs) {
+  k_cg_tol_init_batched<<<1, 64, 0, c->stream>>>(S, tol2, nrhs);
+  LAUNCHED();
+}
+mf_status dev_cg_tol_check_batched(mf_ctx* c, double* S, double* steps, int nrhs) {
+  k_cg_tol_check_batched<<<1, 64, 0, c->stream>>>(S, steps, nrhs);
   LAUNCHED();
 }
 mf_status dev_gmres_begin(mf_ctx* c, const double* nrm2, double* G, int m) {
