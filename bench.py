@@ -531,8 +531,20 @@ def heat_adjoint_workload(ctx, flush):
     t0 = time.perf_counter()
     J, g, gk, _, _ = op.heat_step_gradient(lzt, tp, tt, p["box_half"], p["box_depth"], **kw)
     torch.cuda.synchronize()
-    return {"workload": wl.name, "n_dofs": m.n_dofs, "gradient_seconds": time.perf_counter() - t0, "J": J,
-            "dJ_dlaser": g, "apply": _apply_rates(op, m.n_dofs, 1, flush)}
+    sec = time.perf_counter() - t0
+    # the same with the forward and adjoint GMRES applies in double-float (the convective operator
+    # and its transpose on the fp32 pipes); J and the gradients agree to the solves' tolerance
+    kwd = dict(kw, fp64_arith="df64")
+    op.heat_step_gradient(lzt, tp, tt, p["box_half"], p["box_depth"], **kwd)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    Jd, gd, _, _, _ = op.heat_step_gradient(lzt, tp, tt, p["box_half"], p["box_depth"], **kwd)
+    torch.cuda.synchronize()
+    secd = time.perf_counter() - t0
+    return {"workload": wl.name, "n_dofs": m.n_dofs, "gradient_seconds": sec,
+            "gradient_seconds_df64_applies": secd, "J": J, "dJ_dlaser": g,
+            "J_rel_diff_df64_applies": abs(Jd - J) / abs(J) if J else 0.0,
+            "apply": _apply_rates(op, m.n_dofs, 1, flush)}
 
 
 def oseen_solve(ctx, op, mu, mp):

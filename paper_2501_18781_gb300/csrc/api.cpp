@@ -747,20 +747,32 @@ mf_status apply_impl(mf_op* op, const T* src, T* dst, int nrhs, int64_t ld, bool
   if (heat_tabulated(op) && (op->kq_user || op->rhocp_user || op->betaq_user)) m = 1;
   if constexpr (sizeof(T) == 8) {
     // double-float on uniform meshes: the plane-by-plane kernel with the split coefficient table
-    if (df && op->map[0]->uniform && (kind == K_HELM || kind == K_HEAT) && !beta && !transpose && !op->rhocp_user &&
-        nrhs <= 65535) {
+    if (df && op->map[0]->uniform && (kind == K_HELM || kind == K_HEAT) && !op->rhocp_user && nrhs <= 65535) {
       if (!op->df_ready) {
         MF_TRY(op->qcoef_dfh.alloc(sizeof(float) * 27 * op->ncells));
         MF_TRY(op->qcoef_dfl.alloc(sizeof(float) * 27 * op->ncells));
         MF_TRY(launch_df_coef_split(c, op->map[0], op->qcoef64.as<double>(), op->qcoef_dfh.as<float>(),
                                     op->qcoef_dfl.as<float>()));
+        if (beta) {
+          MF_TRY(op->qvec_dfh.alloc(sizeof(float) * 81 * op->ncells));
+          MF_TRY(op->qvec_dfl.alloc(sizeof(float) * 81 * op->ncells));
+          MF_TRY(launch_df_vec_split(c, op->map[0], op->qvec64.as<double>(), op->qvec_dfh.as<float>(),
+                                     op->qvec_dfl.as<float>()));
+        }
         op->df_ready = true;
       }
-      MF_TRY(launch_scalar_df_uniform(c, op->map[0], reinterpret_cast<const double*>(src),
-                                      reinterpret_cast<double*>(dst), nrhs, ld, op->qcoef_dfh.as<float>(),
-                                      op->qcoef_dfl.as<float>(), value_coef(op)));
+      if (beta)
+        MF_TRY(launch_scalar_df_uniform_conv(c, op->map[0], reinterpret_cast<const double*>(src),
+                                             reinterpret_cast<double*>(dst), nrhs, ld, op->qcoef_dfh.as<float>(),
+                                             op->qcoef_dfl.as<float>(), op->qvec_dfh.as<float>(),
+                                             op->qvec_dfl.as<float>(), value_coef(op), transpose));
+      else
+        MF_TRY(launch_scalar_df_uniform(c, op->map[0], reinterpret_cast<const double*>(src),
+                                        reinterpret_cast<double*>(dst), nrhs, ld, op->qcoef_dfh.as<float>(),
+                                        op->qcoef_dfl.as<float>(), value_coef(op)));
       MF_TRY(launch_dirichlet_copy(c, op->map[0], src, dst, nrhs, ld, 0, false));
-      op->variant = std::string(kind == K_HELM ? "helmholtz" : "heat") + "/uniform/df64/tabulated/planes";
+      op->variant = std::string(kind == K_HELM ? "helmholtz" : "heat") + "/uniform/df64/tabulated/planes" +
+                    (beta ? (transpose ? "/conv-T" : "/conv") : "");
       return MF_OK;
     }
   }

@@ -270,6 +270,155 @@ __global__ void __launch_bounds__(kThreads, 5) k_scalar_df_uniform(DfArgs A, Uni
   scatter_dd_warp(A.dst + int64_t(blockIdx.y) * A.ld, base, ug.sx, ug.sy, dmask, R, active, bias);
 }
 
+// The heat operator with convection, rho_cp (beta . grad u) v, and its transpose, in the same plane
+// structure.  cb_d = w_q h^2 rho_cp beta_d at the Gauss points (float pairs, [d][q][cell]).  Transpose:
+// the term adds cb_d u to the gradient-test fluxes (F_z in the z-flux pass, F_x and F_y in the plane
+// loop).  Forward: it is a value-test term, cb . grad u: its x and y parts are added where the plane
+// loop forms grad u, its z part is formed with the z fluxes and parked in a second shared-memory
+// column (dynamic shared memory, four blocks per SM).
+struct DfConvArgs {
+  const double* src;
+  double* dst;
+  int nrhs;
+  int64_t ld;
+  const float* ch;  // [27][ncells] w_q h c_q
+  const float* cl;
+  const float* bh;  // [3][27][ncells] w_q h^2 rho_cp beta_d
+  const float* bl;
+  int64_t ncells;
+  float wmh[27], wml[27];
+};
+
+template <bool TR>
+__global__ void __launch_bounds__(kThreads, TR ? 5 : 4) k_scalar_df_uniform_conv(DfConvArgs A, UniformGeom ug) {
+  extern __shared__ float conv_smem[];
+  float(*sh)[kThreads] = reinterpret_cast<float(*)[kThreads]>(conv_smem);
+  float(*sl)[kThreads] = reinterpret_cast<float(*)[kThreads]>(conv_smem + 27 * kThreads);
+  float(*zh)[kThreads] = reinterpret_cast<float(*)[kThreads]>(conv_smem + 54 * kThreads);
+  float(*zl)[kThreads] = reinterpret_cast<float(*)[kThreads]>(conv_smem + 81 * kThreads);
+  int i, j, k;
+  const bool active = brick_cell(ug, i, j, k);
+  const int t = threadIdx.x;
+  const int64_t cell = active ? i + int64_t(ug.nx) * (j + int64_t(ug.ny) * k) : 0;
+  const int64_t base = active ? 2 * int64_t(i) + ug.sx * (2 * int64_t(j)) + ug.sy * (2 * int64_t(k)) : 0;
+  const uint32_t dmask = active ? dirichlet_mask(ug, i, j, k) : 0u;
+  int bias = 0;
+  {
+    dd U[27];
+    const double* __restrict__ s = A.src + int64_t(blockIdx.y) * A.ld + base;
+    double X[27];
+    int emax = 0;
+#pragma unroll
+    for (int l = 0; l < 27; ++l) {
+      const int a = l % 3, b = (l / 3) % 3, c = l / 9;
+      const double v = active ? __ldg(s + a + ug.sx * b + ug.sy * c) : 0.0;
+      X[l] = ((dmask >> l) & 1u) ? 0.0 : v;
+      emax = max(emax, (__double2hiint(X[l]) >> 20) & 0x7FF);
+    }
+    emax = int(__reduce_max_sync(0xffffffffu, unsigned(emax)));
+    bias = emax ? emax - 1023 : 0;
+#pragma unroll
+    for (int l = 0; l < 27; ++l) U[l] = d2dd_bits(X[l], bias);
+    dsweep<0>(U);
+    dsweep<1>(U);
+    dsweep<2>(U);
+#pragma unroll
+    for (int q = 0; q < 27; ++q) {
+      sh[q][t] = U[q].h;
+      sl[q][t] = U[q].l;
+    }
+  }
+  auto Uq = [&](int q) { return dd{sh[q][t], sl[q][t]}; };
+  auto coef = [&](int q) {
+    return active ? dd{__ldg(A.ch + q * A.ncells + cell), __ldg(A.cl + q * A.ncells + cell)} : dd{0.f, 0.f};
+  };
+  auto bet = [&](int d, int q) {
+    const int64_t o = (d * 27 + q) * A.ncells + cell;
+    return active ? dd{__ldg(A.bh + o), __ldg(A.bl + o)} : dd{0.f, 0.f};
+  };
+  dd FZ[27];
+#pragma unroll
+  for (int q = 0; q < 27; ++q) {
+    const int qc = q / 9, bz = q - 9 * qc;
+    const dd gz = ddline(qc, Uq(bz), Uq(bz + 9), Uq(bz + 18));
+    dd f = dd_mul(coef(q), gz);
+    if (TR) {
+      f = dd_fma(f, bet(2, q), Uq(q));
+    } else {
+      const dd cz = dd_norm(dd_mul(bet(2, q), gz));
+      zh[q][t] = cz.h;
+      zl[q][t] = cz.l;
+    }
+    FZ[q] = dd_norm(f);
+  }
+#pragma unroll
+  for (int qc = 0; qc < 3; ++qc) {
+    dd R[9];
+#pragma unroll
+    for (int p = 0; p < 9; ++p) {
+      const int q = p + 9 * qc;
+      dd acc = dd_mul(dd{A.wmh[q], A.wml[q]}, Uq(q));
+      if (!TR) acc = dd_add(acc, dd{zh[q][t], zl[q][t]});
+#pragma unroll
+      for (int c2 = 0; c2 < 3; ++c2)
+        if (c2 != 1 || qc != 1) acc = dd_fma(acc, cD(c2, qc), FZ[p + 9 * c2]);
+      R[p] = acc;
+    }
+#pragma unroll
+    for (int qb = 0; qb < 3; ++qb)
+#pragma unroll
+      for (int qa = 0; qa < 3; ++qa) {
+        const int p = qa + 3 * qb, q = p + 9 * qc;
+        const int bx = q - qa, by = q - 3 * qb;
+        const dd gx = ddline(qa, Uq(bx), Uq(bx + 1), Uq(bx + 2));
+        const dd gy = ddline(qb, Uq(by), Uq(by + 3), Uq(by + 6));
+        const dd cq = coef(q);
+        dd fx = dd_mul(cq, gx), fy = dd_mul(cq, gy);
+        if (TR) {
+          const dd u = Uq(q);
+          fx = dd_fma(fx, bet(0, q), u);
+          fy = dd_fma(fy, bet(1, q), u);
+        } else {
+          R[p] = dd_fma(dd_fma(R[p], bet(0, q), gx), bet(1, q), gy);
+        }
+#pragma unroll
+        for (int m = 0; m < 3; ++m) {
+          if (qa != 1 || m != 1) R[p - qa + m] = dd_fma(R[p - qa + m], cD(qa, m), fx);
+          if (qb != 1 || m != 1) R[p - 3 * qb + 3 * m] = dd_fma(R[p - 3 * qb + 3 * m], cD(qb, m), fy);
+        }
+      }
+#pragma unroll
+    for (int p = 0; p < 9; ++p) R[p] = dd_norm(R[p]);
+#pragma unroll
+    for (int b = 0; b < 3; ++b) {   // x, transposed
+      const dd u0 = R[3 * b], u1 = R[3 * b + 1], u2 = R[3 * b + 2];
+      R[3 * b] = dd_norm(dd_add(dd_mul(cS(0, 0), u0), dd_mul(cS(2, 0), u2)));
+      R[3 * b + 1] = dd_norm(dd_add(dd_add(dd_mul(cS(0, 1), u0), u1), dd_mul(cS(2, 1), u2)));
+      R[3 * b + 2] = dd_norm(dd_add(dd_mul(cS(0, 2), u0), dd_mul(cS(2, 2), u2)));
+    }
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {   // y, transposed
+      const dd u0 = R[a], u1 = R[a + 3], u2 = R[a + 6];
+      R[a] = dd_norm(dd_add(dd_mul(cS(0, 0), u0), dd_mul(cS(2, 0), u2)));
+      R[a + 3] = dd_norm(dd_add(dd_add(dd_mul(cS(0, 1), u0), u1), dd_mul(cS(2, 1), u2)));
+      R[a + 6] = dd_norm(dd_add(dd_mul(cS(0, 2), u0), dd_mul(cS(2, 2), u2)));
+    }
+#pragma unroll
+    for (int p = 0; p < 9; ++p) {
+      sh[p + 9 * qc][t] = R[p].h;
+      sl[p + 9 * qc][t] = R[p].l;
+    }
+  }
+  dd R[27];
+#pragma unroll
+  for (int q = 0; q < 27; ++q) R[q] = Uq(q);
+  dsweep_t<2>(R);
+#pragma unroll
+  for (int q = 0; q < 27; ++q)
+    if (!active) R[q] = dd{0.f, 0.f};
+  scatter_dd_warp(A.dst + int64_t(blockIdx.y) * A.ld, base, ug.sx, ug.sy, dmask, R, active, bias);
+}
+
 // ---------------------------------------------------------------------------------------------
 // Double-float Oseen apply (Q2 velocity / Q1 pressure, uniform mesh, folded Gauss-point coefficients
 // cm = w h^3 sigma rho, cv = w h mu, cb = w h^2 rho beta as float pairs).  A block of three warps
@@ -532,7 +681,66 @@ __global__ void k_split_coef(const double* __restrict__ c, int64_t ncells, doubl
   cl[t] = __double2float_rn(v - double(hi));
 }
 
+// [3][27][ncells] rho_cp beta_d -> w_q h^2 rho_cp beta_d as float pairs
+__global__ void k_split_vec(const double* __restrict__ b, int64_t ncells, double h2, float* bh, float* bl) {
+  const int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (t >= 81 * ncells) return;
+  const int q = int((t / ncells) % 27);
+  const double v = b[t] * cW364[q] * h2;
+  const float hi = __double2float_rn(v);
+  bh[t] = hi;
+  bl[t] = __double2float_rn(v - double(hi));
+}
+
 }  // namespace
+
+mf_status launch_df_vec_split(mf_ctx* ctx, const mf_dofmap* m, const double* qvec64, float* bh, float* bl) {
+  MF_CUDA_TRY(upload_tables_here());
+  const int64_t n = 81 * m->n_cells;
+  const double h = m->mesh->h0;
+  k_split_vec<<<int((n + 255) / 256), 256, 0, ctx->stream>>>(qvec64, m->n_cells, h * h, bh, bl);
+  ctx->launches++;
+  MF_CUDA_TRY(cudaGetLastError());
+  return MF_OK;
+}
+
+mf_status launch_scalar_df_uniform_conv(mf_ctx* ctx, const mf_dofmap* m, const double* src, double* dst, int nrhs,
+                                        int64_t ld, const float* ch, const float* cl, const float* bh, const float* bl,
+                                        double mass, bool transpose) {
+  MF_CUDA_TRY(upload_tables_here());
+  static bool attrs = false;
+  if (!attrs) {
+    MF_CUDA_TRY(cudaFuncSetAttribute(k_scalar_df_uniform_conv<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     int(108 * kThreads * sizeof(float))));
+    attrs = true;
+  }
+  const Tables tb = make_tables();
+  DfConvArgs a{};
+  a.src = src;
+  a.dst = dst;
+  a.nrhs = nrhs;
+  a.ld = ld;
+  a.ch = ch;
+  a.cl = cl;
+  a.bh = bh;
+  a.bl = bl;
+  a.ncells = m->n_cells;
+  const double h = m->mesh->h0;
+  for (int q = 0; q < 27; ++q) {
+    const double v = tb.W3[q] * mass * h * h * h;
+    a.wmh[q] = float(v);
+    a.wml[q] = float(v - double(a.wmh[q]));
+  }
+  const UniformGeom ug = uniform_geom(m);
+  const dim3 grid(brick_blocks(ug.nx, ug.ny, ug.nz), nrhs);
+  if (transpose)
+    k_scalar_df_uniform_conv<true><<<grid, kThreads, 54 * kThreads * sizeof(float), ctx->stream>>>(a, ug);
+  else
+    k_scalar_df_uniform_conv<false><<<grid, kThreads, 108 * kThreads * sizeof(float), ctx->stream>>>(a, ug);
+  ctx->launches++;
+  MF_CUDA_TRY(cudaGetLastError());
+  return MF_OK;
+}
 
 mf_status launch_df_coef_split(mf_ctx* ctx, const mf_dofmap* m, const double* qcoef64, float* ch, float* cl) {
   MF_CUDA_TRY(upload_tables_here());

@@ -128,6 +128,12 @@ mf_status tc_take_error();
 // rho_cp): the tabulated coefficient split into float pairs of w_q h c_q, then the apply (dst
 // accumulated, nrhs vectors ld apart)
 mf_status launch_df_coef_split(mf_ctx* ctx, const mf_dofmap* m, const double* qcoef64, float* ch, float* cl);
+// the convective heat operator (transpose: its adjoint) in double-float on a uniform mesh; bh, bl the
+// float pairs of w_q h^2 rho_cp beta_d ([3][27][ncells], from launch_df_vec_split)
+mf_status launch_scalar_df_uniform_conv(mf_ctx* ctx, const mf_dofmap* m, const double* src, double* dst, int nrhs,
+                                        int64_t ld, const float* ch, const float* cl, const float* bh, const float* bl,
+                                        double mass, bool transpose);
+mf_status launch_df_vec_split(mf_ctx* ctx, const mf_dofmap* m, const double* qvec64, float* bh, float* bl);
 mf_status launch_scalar_df_uniform(mf_ctx* ctx, const mf_dofmap* m, const double* src, double* dst, int nrhs,
                                    int64_t ld, const float* ch, const float* cl, double mass);
 // double-float Oseen apply on uniform meshes without the melt-pool terms: the folded coefficient
@@ -171,6 +177,7 @@ struct mf_op {
   mf::DevBuf blk64, pdiag64;      // Oseen block Jacobi
   bool tables_ready = false;
   mf::DevBuf qcoef_dfh, qcoef_dfl;  // [27][ncells] float pairs of w_q h c_q for the double-float kernel
+  mf::DevBuf qvec_dfh, qvec_dfl;    // [3][27][ncells] float pairs of w_q h^2 rho_cp beta (convection)
   bool df_ready = false;
   mf::DevBuf cm_df, cv_df, cb_df;   // Oseen: folded coefficients as float pairs (high, then low parts)
   bool diag_ready = false;

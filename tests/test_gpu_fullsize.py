@@ -144,7 +144,7 @@ def test_heat_128_apply_sampled_rows(ctx):
         assert np.all(v[dir_rows] == uu[dir_rows].astype(v.dtype))
 
 
-def test_heat_adjoint_64_transpose_sampled_rows(ctx):
+def test_heat_adjoint_64_sampled_rows(ctx):
     n = 64
     wl = syn.scaled(syn.HEAT_ADJOINT, n)
     p = wl.params
@@ -153,12 +153,17 @@ def test_heat_adjoint_64_transpose_sampled_rows(ctx):
     free, _ = _lattice_sample(n, 60, 8, dm.dirichlet)
     build = lambda d, nod, cw: asm.heat_matrix(d, p["rhocp"], p["dt"], kq=cw["kq"], beta=nod["beta"])
     u = syn.uniform_pm1(13, dm.n_dofs)
-    v = op.apply(torch.tensor(u, device="cuda"), transpose=True).cpu().numpy()
-    kw = dict(cellwise={"kq": k}, transpose=True)
-    ref = patch.scalar_rows(n, wl.lo, wl.hi, free, build, {"beta": b}, u, dm.dirichlet, **kw)
-    bound = patch.scalar_rows(n, wl.lo, wl.hi, free, build, {"beta": b}, u, dm.dirichlet, absolute=True, **kw)
-    ok, worst = componentwise_ok(v[free], ref, bound, 1e-12)
-    assert ok, worst
+    ut = torch.tensor(u, device="cuda")
+    for tr in (True, False):   # the adjoint rows, then the forward rows; fp64 pipes and double-float
+        kw = dict(cellwise={"kq": k}, transpose=tr)
+        ref = patch.scalar_rows(n, wl.lo, wl.hi, free, build, {"beta": b}, u, dm.dirichlet, **kw)
+        bound = patch.scalar_rows(n, wl.lo, wl.hi, free, build, {"beta": b}, u, dm.dirichlet, absolute=True, **kw)
+        for arith in (None, "df64"):
+            v = op.apply(ut, transpose=tr, arith=arith).cpu().numpy()
+            ok, worst = componentwise_ok(v[free], ref, bound, 1e-12)
+            assert ok, (tr, arith, worst)
+            if arith == "df64":
+                assert op.variant.endswith("/conv-T" if tr else "/conv"), op.variant
 
 
 def test_helmholtz_16_whole_vector(ctx):
