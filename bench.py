@@ -935,6 +935,7 @@ def probe(argv):
         reinit [base] [levels] [f32|f64|df64] [nrhs]
         oseen_solve [n] [maxit]
         heat_solve [n] [fp64|mixed|fp64_df64_applies|mixed_df64_outer]
+        heat_adjoint [n] [f64|df64] [forward|transpose]
         helmholtz_qk [k] [n] [f32|f64|tc]
     Inputs come from the seeded generators; every apply runs in libmfgb."""
     import numpy as np
@@ -977,6 +978,28 @@ def probe(argv):
                 _, info = op.solve(bt, solver="gmres", precond="block_triangular", maxit=maxit, tol=1e-10)
             torch.cuda.synchronize()
             print(op.variant, n, info)
+    elif kind == "heat_adjoint":
+        # the convective heat operator of the adjoint workload (nodal beta, k per Gauss point)
+        n = int(argv[1]) if len(argv) > 1 else 64
+        prec = argv[2] if len(argv) > 2 else "df64"
+        tr = len(argv) > 3 and argv[3] == "transpose"
+        wl = syn.scaled(syn.HEAT_ADJOINT, n)
+        p = wl.params
+        m = DofMap(Mesh.uniform(ctx, n, wl.lo, wl.hi), 2, 1 << 4)
+        x = m.coords()
+        op = Operator(ctx, "heat", [m], rhocp=p["rhocp"], dt=p["dt"], k0=p["k0"], t_boil=p["t_boil"])
+        keep = [torch.tensor(np.array(syn.convection_field(*x.T, wl.seed, wl.lo, wl.hi)).ravel(), device="cuda"),
+                torch.tensor(syn.kq_field(m.n_cells * 27, wl.seed, p["k0"]), device="cuda")]
+        op.set_field("beta", keep[0])
+        op.set_field("k_qpoint", keep[1])
+        u = torch.tensor(syn.uniform_pm1(1, m.n_dofs), device="cuda")
+        if prec == "f32":
+            u = u.float()
+        v = torch.empty_like(u)
+        for _ in range(4):
+            op.apply(u, v, transpose=tr, arith="df64" if prec == "df64" else None)
+        torch.cuda.synchronize()
+        print(op.variant, m.n_dofs)
     elif kind == "heat_solve":
         # the heat-step solve the bench times (laser right-hand side, tolerance 1e-10, graph replay),
         # once to set up and once more
