@@ -184,12 +184,20 @@ def test_octree_without_refinement_matches_the_uniform_operator(ctx):
         assert abs(D).max() <= 1e-12 * abs(Au).max()
 
 
+def _line(P):
+    P["op"].set_variant("q2_line", 1)   # the nine-threads-per-cell kernel
+    return P
+
+
 def test_strided_batches_leave_the_padding_alone(ctx):
     from paper_2501_18781_gb300 import _lib
     lib = _lib.load()
     for P, dt, code, rtol in ((heat(4, ctx, with_beta=True, kq=True), torch.float64, _lib.MF_F64, 1e-12),
+                              (_line(heat(4, ctx)), torch.float64, _lib.MF_F64, 1e-12),
+                              (_line(helmholtz(3, ctx)), torch.float32, _lib.MF_F32, 2e-5),
                               (helmholtz(4, ctx), torch.float32, _lib.MF_F32, 2e-5),
-                              (heat(5, ctx), torch.float64, _lib.MF_DF64, 1e-12)):
+                              (heat(5, ctx), torch.float64, _lib.MF_DF64, 1e-12),
+                              (heat(5, ctx, with_beta=True, kq=True), torch.float64, _lib.MF_DF64, 1e-12)):
         n, ld, R = P["n"], P["n"] + 37, 3
         U = np.zeros((R, ld))
         for r in range(R):
