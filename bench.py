@@ -140,8 +140,8 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(self.rows)}
 
 
-KERNEL_SOURCES = ("apply_f64.cu", "apply_f32.cu", "apply_df64.cu", "apply_df64_uniform.cu", "apply_kernels.cuh",
-                  "cellops.cuh", "scalar_local.cuh", "df64.cuh")
+KERNEL_SOURCES = ("apply_f64.cu", "apply_f32.cu", "apply_df64.cu", "apply_df64_uniform.cu", "df_pairs.cuh",
+                  "apply_kernels.cuh", "cellops.cuh", "scalar_local.cuh", "df64.cuh")
 
 
 def kernel_hash():

@@ -19,7 +19,7 @@ NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 COMMON = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-ffp-contract=off",
           "-I", CSRC, "-I", INCLUDE]
 SOURCES = ["mesh.cpp", "cellops_host.cpp", "api.cpp", "solver.cpp",
-           "apply.cu", "apply_f64.cu", "apply_f32.cu", "apply_df64.cu", "apply_df64_uniform.cu", "aux.cu", "vec.cu",
+           "apply.cu", "apply_f64.cu", "apply_f32.cu", "apply_df64.cu", "apply_df64_uniform.cu", "apply_df64_octree.cu", "aux.cu", "vec.cu",
            "solver_kernels.cu", "sources.cu", "apply_h16.cu", "step.cu", "step.cpp", "apply_qk.cu", "apply_qk_tc.cu"]
 
 

@@ -746,6 +746,22 @@ mf_status apply_impl(mf_op* op, const T* src, T* dst, int nrhs, int64_t ld, bool
   int m = mode;
   if (heat_tabulated(op) && (op->kq_user || op->rhocp_user || op->betaq_user)) m = 1;
   if constexpr (sizeof(T) == 8) {
+    // double-float reinitialisation on octree meshes: the plane-by-plane kernel through the cell map
+    if (df && !op->map[0]->uniform && kind == K_REINIT && nrhs <= 65535) {
+      if (!op->df_ready) {
+        MF_TRY(op->qvec_dfh.alloc(sizeof(float) * 81 * op->ncells));
+        MF_TRY(op->qvec_dfl.alloc(sizeof(float) * 81 * op->ncells));
+        MF_TRY(launch_split_pairs(c, op->qvec64.as<double>(), 81 * op->ncells, op->qvec_dfh.as<float>(),
+                                  op->qvec_dfl.as<float>()));
+        op->df_ready = true;
+      }
+      MF_TRY(launch_reinit_df_octree(c, op->map[0], reinterpret_cast<const double*>(src),
+                                     reinterpret_cast<double*>(dst), nrhs, ld, op->qvec_dfh.as<float>(),
+                                     op->qvec_dfl.as<float>(), op->p.eps, value_coef(op)));
+      MF_TRY(launch_dirichlet_copy(c, op->map[0], src, dst, nrhs, ld, 0, false));
+      op->variant = "reinit/octree/df64/tabulated/planes";
+      return MF_OK;
+    }
     // double-float on uniform meshes: the plane-by-plane kernel with the split coefficient table
     if (df && op->map[0]->uniform && (kind == K_HELM || kind == K_HEAT) && !op->rhocp_user && nrhs <= 65535) {
       if (!op->df_ready) {

@@ -134,6 +134,10 @@ mf_status launch_scalar_df_uniform_conv(mf_ctx* ctx, const mf_dofmap* m, const d
                                         int64_t ld, const float* ch, const float* cl, const float* bh, const float* bl,
                                         double mass, bool transpose);
 mf_status launch_df_vec_split(mf_ctx* ctx, const mf_dofmap* m, const double* qvec64, float* bh, float* bl);
+// the reinitialisation operator in double-float on an octree map (normals from the float pairs of
+// the fp64 Gauss-point table, [3][27][ncells]); dst zeroed by the caller, Dirichlet rows left alone
+mf_status launch_reinit_df_octree(mf_ctx* ctx, const mf_dofmap* m, const double* src, double* dst, int nrhs,
+                                  int64_t ld, const float* nh, const float* nl, double eps, double mass);
 mf_status launch_scalar_df_uniform(mf_ctx* ctx, const mf_dofmap* m, const double* src, double* dst, int nrhs,
                                    int64_t ld, const float* ch, const float* cl, double mass);
 // double-float Oseen apply on uniform meshes without the melt-pool terms: the folded coefficient

@@ -496,9 +496,11 @@ def test_reinit_octree_full_size_maps_and_sampled_rows(ctx):
     for r in (0, R - 1):
         u = U[r * dm.n_dofs:(r + 1) * dm.n_dofs]
         refs[r] = (patch.constrained_rows(dm, rows, emat, u), patch.constrained_rows(dm, rows, emat, u, absolute=True))
-    for arith, rtol in (("f64", 1e-12), ("f32", 5e-5)):
+    for arith, rtol in (("f64", 1e-12), ("df64", 1e-12), ("f32", 5e-5)):
         t = torch.tensor(U, device="cuda", dtype=torch.float32 if arith == "f32" else torch.float64)
-        V = op.apply(t, nrhs=R).cpu().double().numpy()
+        V = op.apply(t, nrhs=R, arith="df64" if arith == "df64" else None).cpu().double().numpy()
+        if arith == "df64":
+            assert op.variant == "reinit/octree/df64/tabulated/planes", op.variant
         for r, (ref, bound) in refs.items():
             ok, worst = componentwise_ok(V[r * dm.n_dofs + rows], ref, bound, rtol)
             assert ok, (arith, r, worst)
