@@ -389,9 +389,11 @@ mf_status mf_heat_step_gradient(mf_op* op, const mf_laser* laser, const mf_solve
                                 double box_half, double box_depth, double* J, double* dJ_dlaser,
                                 double* dJ_dkq, double* theta, double* lambda);
 
-/* Time the apply variants of this operator (cells per block, coefficient mode; Oseen: the fp64
- * loop order; Q3 Helmholtz: the CUDA-core or the tensor-core kernel for fp32 applies, which then
- * also serves the fp32 applies inside solvers) and keep the fastest.  cache_path (may be NULL) is a
+/* Time the apply variants of this operator (cells per block and persistent grids, timed on eight
+ * right-hand sides for octree maps and on one for uniform ones; coefficient mode; one or nine threads
+ * per cell for uniform Q2 Helmholtz and heat; fp64 pipes or double-float; Oseen: the fp64 loop order;
+ * Q3 Helmholtz: the CUDA-core or the tensor-core kernel for fp32 applies, which then also serves the
+ * fp32 applies inside solvers) and keep the fastest.  cache_path (may be NULL) is a
  * text file of one JSON record per line, keyed by the operator's configuration (kind, degree, mesh
  * type and sizes, optional fields, melt-pool flags, the device's SM count): if it holds a record with
  * this operator's key, the last such record's choice is applied and nothing is timed; otherwise the

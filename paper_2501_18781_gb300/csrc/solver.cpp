@@ -1161,12 +1161,25 @@ mf_status autotune_measure(mf_op* op) {
     MF_TRY(s32.alloc(sizeof(float) * n));
     MF_TRY(d32.alloc(sizeof(float) * n));
     MF_TRY(convert<double, float>(c, n, src.as<double>(), s32.as<float>()));
+    // the launch shape of octree operators is timed on a batch of eight right-hand sides (their
+    // batched reinitialisation; one and eight right-hand sides prefer different shapes)
+    const int shape_rhs = op->map[0]->uniform ? 1 : 8;
+    DevBuf sb, db;
+    if (shape_rhs > 1) {
+      MF_TRY(sb.alloc(sizeof(float) * n * shape_rhs));
+      MF_TRY(db.alloc(sizeof(float) * n * shape_rhs));
+      for (int r = 0; r < shape_rhs; ++r)
+        MF_CUDA_TRY(cudaMemcpyAsync(sb.as<float>() + r * n, s32.as<float>(), sizeof(float) * n,
+                                    cudaMemcpyDeviceToDevice, c->stream));
+    }
     // median-free best-of-5 event timing of one apply variant
-    auto time_variant = [&](int prec, double* out_ms) -> mf_status {
+    auto time_variant = [&](int prec, double* out_ms, int nr = 1) -> mf_status {
       double best = 1e30;
       for (int rep = 0; rep < 6; ++rep) {
         cudaEventRecord(e0, c->stream);
-        if (prec == PREC_F32) MF_TRY(apply_impl<float>(op, s32.as<float>(), d32.as<float>(), 1, n, false, PREC_F32));
+        if (prec == PREC_F32 && nr > 1)
+          MF_TRY(apply_impl<float>(op, sb.as<float>(), db.as<float>(), nr, n, false, PREC_F32));
+        else if (prec == PREC_F32) MF_TRY(apply_impl<float>(op, s32.as<float>(), d32.as<float>(), 1, n, false, PREC_F32));
         else MF_TRY(apply_impl<double>(op, src.as<double>(), dst.as<double>(), 1, n, false, prec));
         cudaEventRecord(e1, c->stream);
         MF_CUDA_TRY(cudaEventSynchronize(e1));
@@ -1197,7 +1210,7 @@ mf_status autotune_measure(mf_op* op) {
       if (op->map[0]->uniform && shapes[si][0] != 128) continue;
       op->block = shapes[si][0];
       op->persistent_blocks = shapes[si][1];
-      MF_TRY(time_variant(PREC_F32, &shape_ms[si]));
+      MF_TRY(time_variant(PREC_F32, &shape_ms[si], shape_rhs));
       if (shape_ms[si] < shape_ms[best_shape]) best_shape = si;
     }
     op->block = shapes[best_shape][0];
