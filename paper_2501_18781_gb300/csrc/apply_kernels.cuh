@@ -120,12 +120,15 @@ __device__ __forceinline__ void scalar_cell(const ScalarArgs<typename Store<T>::
 
 // One launch sweeps all nwork work units; with fewer blocks than units (the persistent
 // variant, grid = a few blocks per SM) each block strides over them.  All right-hand sides of
-// a cell are applied while its coefficients sit in registers.  The fp32 octree reinitialisation
-// instance is held to five blocks of 128 per SM (96 registers, no spills): its indirect gathers are
+// a cell are applied while its coefficients sit in registers.  Two fp32 instances are held to five
+// blocks of 128 per SM (96 registers): the octree reinitialisation (no spills; its indirect gathers are
 // latency-bound, and 20 warps per SM instead of 16 measured 2.41 -> 2.32 ms for the 8-RHS base-32
-// octree apply (the other octree instances would spill at that bound).
+// octree apply) and the uniform heat operator without convection (48 bytes of spills; 128^3 apply
+// 0.168 -> 0.161 ms).  The other instances would spill more at that bound.
 template <typename T, int KIND, int MODE, bool BETA, bool TR, bool OCT>
-__global__ void __launch_bounds__(128, (OCT && sizeof(T) == 4 && KIND == K_REINIT) ? 5 : 1) k_scalar(ScalarArgs<typename Store<T>::type> A, UniformGeom ug, OctGeom og,
+__global__ void __launch_bounds__(128, (sizeof(T) == 4 && ((OCT && KIND == K_REINIT) ||
+                                                           (!OCT && KIND == K_HEAT && !BETA))) ? 5 : 1)
+    k_scalar(ScalarArgs<typename Store<T>::type> A, UniformGeom ug, OctGeom og,
                                                 int64_t nwork) {
   for (int64_t w = blockIdx.x; w < nwork; w += gridDim.x) {
     CellLoc L;
