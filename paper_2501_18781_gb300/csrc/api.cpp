@@ -701,12 +701,13 @@ mf_status apply_impl(mf_op* op, const T* src, T* dst, int nrhs, int64_t ld, bool
   const char* pname = f32 ? "/f32" : (df ? "/df64" : "/f64");
   if (op->p.kind == MF_OP_OSEEN) {
     if (transpose) return fail(MF_EUNSUPPORTED, "transpose of the Oseen operator");
-    if (df && op->p.oseen_flags) return fail(MF_EUNSUPPORTED, "double-float Oseen applies without the melt-pool terms");
     const int64_t nu = op->map[0]->n_dofs;
     if constexpr (sizeof(T) == 8) {
-      if (df && !op->p.oseen_flags) {
-        // double-float: one warp per velocity component over a brick of 32 cells
+      if (df) {
+        // double-float: one warp per velocity component over a brick of 32 cells (the Darcy term is
+        // folded into cm; the trace correction reads the interface normal pairs)
         const int64_t nc = op->ncells;
+        const bool ext = op->p.oseen_flags != 0;
         if (!op->df_ready) {
           MF_TRY(op->cm_df.alloc(sizeof(float) * 54 * nc));
           MF_TRY(op->cv_df.alloc(sizeof(float) * 54 * nc));
@@ -714,15 +715,21 @@ mf_status apply_impl(mf_op* op, const T* src, T* dst, int nrhs, int64_t ld, bool
           MF_TRY(launch_split_pairs(c, op->cm64.as<double>(), 27 * nc, op->cm_df.as<float>(), op->cm_df.as<float>() + 27 * nc));
           MF_TRY(launch_split_pairs(c, op->cv64.as<double>(), 27 * nc, op->cv_df.as<float>(), op->cv_df.as<float>() + 27 * nc));
           MF_TRY(launch_split_pairs(c, op->cb64.as<double>(), 81 * nc, op->cb_df.as<float>(), op->cb_df.as<float>() + 81 * nc));
+          if (ext) {
+            MF_TRY(op->nrm_df.alloc(sizeof(float) * 162 * nc));
+            MF_TRY(launch_split_pairs(c, op->nrm64.as<double>(), 81 * nc, op->nrm_df.as<float>(),
+                                      op->nrm_df.as<float>() + 81 * nc));
+          }
           op->df_ready = true;
         }
         for (int r = 0; r < nrhs; ++r) {
           MF_TRY(launch_oseen_df_uniform(c, op->map[0], reinterpret_cast<const double*>(src + r * ld),
                                          reinterpret_cast<double*>(dst + r * ld), op->cm_df.as<float>(),
-                                         op->cv_df.as<float>(), op->cb_df.as<float>()));
+                                         op->cv_df.as<float>(), op->cb_df.as<float>(),
+                                         ext ? op->nrm_df.as<float>() : nullptr));
           MF_TRY(launch_dirichlet_copy(c, op->map[0], src + r * ld, dst + r * ld, 3, nu, 0, false));
         }
-        op->variant = "oseen_q2q1/df64/tabulated/warp-per-component";
+        op->variant = std::string("oseen_q2q1/df64/tabulated/warp-per-component") + (ext ? "/meltpool" : "");
         return MF_OK;
       }
     }

@@ -360,6 +360,7 @@ struct DfOseenArgs {
   float pwh[27][8], pwl[27][8];  // -h^2 w_q psi_n(x_q): pressure / continuity coupling
   float wph[3][2], wpl[3][2];    // 1D w_g psi_a(g) (Q1 hat a at Gauss point g)
   float mh2h, mh2l;              // -h^2
+  const float *nrh, *nrl;        // melt-pool trace correction: interface normal per Gauss point, [3][27][ncells]
 };
 
 __device__ __forceinline__ dd dd_scale(dd a, float s) { return {a.h * s, a.l * s}; }   // s a power of two
@@ -367,6 +368,9 @@ __device__ __forceinline__ float pow2f(int e) {  // 2^e for e in [-126, 127]; 0 
   return e < -126 ? 0.f : __uint_as_float(unsigned(min(e, 127) + 127) << 23);
 }
 
+// EXT: the melt-pool trace correction -2 mu (div u) n (x) n : grad v adds t n_C n_d to the flux of
+// component C in direction d, t = -2 cv div u (the Darcy term sits in cm)
+template <bool EXT>
 __device__ __forceinline__ void oseen_df_component(const int C, const DfOseenArgs& A, const UniformGeom& ug,
                                                    float (*sh)[27][32],
                                                    float (*sl)[27][32], float (*ph)[32], float (*pl)[32],
@@ -392,6 +396,18 @@ __device__ __forceinline__ void oseen_df_component(const int C, const DfOseenArg
     const int b0 = q - qd * st;
     return ddline(qd, V(e, b0), V(e, b0 + st), V(e, b0 + 2 * st));
   };
+  // interface normal component d at Gauss point q (unscaled: a unit vector)
+  auto nrm = [&](int d, int q) {
+    const int64_t o = (d * 27 + q) * nc + cell;
+    return active ? dd{__ldg(A.nrh + o), __ldg(A.nrl + o)} : dd{0.f, 0.f};
+  };
+  // t n_C = -2 cv (div u) n_C at Gauss point (qa, qb, qc)
+  auto trace_tn = [&](dd cv, int qa, int qb, int qc) {
+    const int q = qa + 3 * qb + 9 * qc;
+    const dd div = dd_add(dd_add(deriv(0, 0, qa, qb, qc), deriv(1, 1, qa, qb, qc)), deriv(2, 2, qa, qb, qc));
+    const dd m2cv = dd{-2.f * cv.h, -2.f * cv.l};
+    return dd_mul(dd_mul(m2cv, dd_norm(div)), nrm(C, q));
+  };
   // test flux of component C in direction d: cv (d_d u_C + d_C u_d), plus the pressure on the diagonal
   auto flux = [&](int d, dd cv, dd gd, int qa, int qb, int qc) {
     const int q = qa + 3 * qb + 9 * qc;
@@ -405,8 +421,12 @@ __device__ __forceinline__ void oseen_df_component(const int C, const DfOseenArg
     const int qa = p % 3, qb = p / 3;
     dd fz[3];
 #pragma unroll
-    for (int qc = 0; qc < 3; ++qc)
-      fz[qc] = dd_norm(flux(2, load(A.cvh, A.cvl, (p + 9 * qc) * nc + cell), deriv(C, 2, qa, qb, qc), qa, qb, qc));
+    for (int qc = 0; qc < 3; ++qc) {
+      const dd cv = load(A.cvh, A.cvl, (p + 9 * qc) * nc + cell);
+      dd f = flux(2, cv, deriv(C, 2, qa, qb, qc), qa, qb, qc);
+      if (EXT) f = dd_fma(f, trace_tn(cv, qa, qb, qc), nrm(2, p + 9 * qc));
+      fz[qc] = dd_norm(f);
+    }
 #pragma unroll
     for (int qc = 0; qc < 3; ++qc) {
       dd acc = dd{0.f, 0.f};
@@ -436,7 +456,12 @@ __device__ __forceinline__ void oseen_df_component(const int C, const DfOseenArg
         v = dd_fma(v, load(A.cbh, A.cbl, (1 * 27 + q) * nc + cell), gy);
         v = dd_fma(v, load(A.cbh, A.cbl, (2 * 27 + q) * nc + cell), gz);
         P[p] = dd_add(P[p], v);
-        const dd fx = flux(0, cv, gx, qa, qb, qc), fy = flux(1, cv, gy, qa, qb, qc);
+        dd fx = flux(0, cv, gx, qa, qb, qc), fy = flux(1, cv, gy, qa, qb, qc);
+        if (EXT) {
+          const dd tn = trace_tn(cv, qa, qb, qc);
+          fx = dd_fma(fx, tn, nrm(0, q));
+          fy = dd_fma(fy, tn, nrm(1, q));
+        }
 #pragma unroll
         for (int m = 0; m < 3; ++m) {
           if (qa != 1 || m != 1) P[p - qa + m] = dd_fma(P[p - qa + m], cD(qa, m), fx);
@@ -510,6 +535,7 @@ __device__ __forceinline__ void oseen_df_component(const int C, const DfOseenArg
   }
 }
 
+template <bool EXT>
 __global__ void __launch_bounds__(96, 4) k_oseen_df_uniform(DfOseenArgs A, UniformGeom ug) {
   __shared__ float sh[3][27][32], sl[3][27][32];   // velocity values at the Gauss points
   __shared__ float ph[27][32], pl[27][32];         // pressure term at the Gauss points (output scale)
@@ -579,8 +605,8 @@ __global__ void __launch_bounds__(96, 4) k_oseen_df_uniform(DfOseenArgs A, Unifo
   __syncthreads();
   // one code path for the three warps (component w at run time): the three instruction streams of a
   // compile-time component kept warps waiting on instruction fetch
-  oseen_df_component(w, A, ug, sh, sl, ph, pl, ah[w], al[w], lane, active, cell, base, dmask, su, bias_out, bias_u,
-                     A.dst + 3 * A.nu, pbase, px, pxy);
+  oseen_df_component<EXT>(w, A, ug, sh, sl, ph, pl, ah[w], al[w], lane, active, cell, base, dmask, su, bias_out,
+                          bias_u, A.dst + 3 * A.nu, pbase, px, pxy);
 }
 
 __global__ void k_split_plain(const double* __restrict__ c, int64_t n, float* h, float* l) {
@@ -705,7 +731,7 @@ mf_status launch_split_pairs(mf_ctx* ctx, const double* c, int64_t n, float* h, 
 }
 
 mf_status launch_oseen_df_uniform(mf_ctx* ctx, const mf_dofmap* mu, const double* src, double* dst, const float* cm,
-                                  const float* cv, const float* cb) {
+                                  const float* cv, const float* cb, const float* nr) {
   MF_CUDA_TRY(upload_tables_here());
   const Tables tb = make_tables();
   DfOseenArgs a{};
@@ -737,7 +763,13 @@ mf_status launch_oseen_df_uniform(mf_ctx* ctx, const mf_dofmap* mu, const double
   a.mh2l = float(-(h * h) - double(a.mh2h));
   const UniformGeom ug = uniform_geom(mu);
   const int nb = ((ug.nx + 7) / 8) * ((ug.ny + 3) / 4) * ug.nz;
-  k_oseen_df_uniform<<<nb, 96, 0, ctx->stream>>>(a, ug);
+  if (nr) {
+    a.nrh = nr;
+    a.nrl = nr + 81 * nc;
+    k_oseen_df_uniform<true><<<nb, 96, 0, ctx->stream>>>(a, ug);
+  } else {
+    k_oseen_df_uniform<false><<<nb, 96, 0, ctx->stream>>>(a, ug);
+  }
   ctx->launches++;
   MF_CUDA_TRY(cudaGetLastError());
   return MF_OK;

@@ -140,11 +140,12 @@ mf_status launch_reinit_df_octree(mf_ctx* ctx, const mf_dofmap* m, const double*
                                   int64_t ld, const float* nh, const float* nl, double eps, double mass);
 mf_status launch_scalar_df_uniform(mf_ctx* ctx, const mf_dofmap* m, const double* src, double* dst, int nrhs,
                                    int64_t ld, const float* ch, const float* cl, double mass);
-// double-float Oseen apply on uniform meshes without the melt-pool terms: the folded coefficient
-// tables cm, cv (27 per cell) and cb (81 per cell) as float pairs (high parts, then low parts)
+// double-float Oseen apply on uniform meshes: the folded coefficient tables cm, cv (27 per cell) and
+// cb (81 per cell) as float pairs (high parts, then low parts); nr: the melt-pool interface normal
+// table (81 per cell, pairs) for the trace correction, or NULL without the melt-pool terms
 mf_status launch_split_pairs(mf_ctx* ctx, const double* c, int64_t n, float* h, float* l);
 mf_status launch_oseen_df_uniform(mf_ctx* ctx, const mf_dofmap* mu, const double* src, double* dst, const float* cm,
-                                  const float* cv, const float* cb);
+                                  const float* cv, const float* cb, const float* nr);
 // laser top-face load and its parameter derivatives (uniform maps)
 mf_status launch_laser(mf_ctx* ctx, const mf_dofmap* m, const double lz[5], double* f, double* dF);
 // dJ/dk_q = -w_q h grad(lambda) . grad(theta), [cell][27]
@@ -184,6 +185,7 @@ struct mf_op {
   mf::DevBuf qvec_dfh, qvec_dfl;    // [3][27][ncells] float pairs of w_q h^2 rho_cp beta (convection)
   bool df_ready = false;
   mf::DevBuf cm_df, cv_df, cb_df;   // Oseen: folded coefficients as float pairs (high, then low parts)
+  mf::DevBuf nrm_df;                // Oseen melt-pool terms: the interface normal table as float pairs
   bool diag_ready = false;
   // Chebyshev bounds: lambda_max of D^-1 A from the first solve's Lanczos run, kept until a field
   // changes (the same number of steps from the same start vector gives the same estimate)

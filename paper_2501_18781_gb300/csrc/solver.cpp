@@ -1126,9 +1126,9 @@ mf_status autotune_measure(mf_op* op) {
         }
       }
       op->oseen_qouter64 = ms[1] < ms[0] ? 1 : 0;
-      // fp64-accurate arithmetic: the fp64 pipes or double-float pairs (without the melt-pool terms)
+      // fp64-accurate arithmetic: the fp64 pipes or double-float pairs
       double df_ms = 1e30;
-      if (!op->p.oseen_flags) {
+      {
         for (int rep = 0; rep < 4; ++rep) {
           cudaEventRecord(a0, c->stream);
           MF_TRY(apply_impl<double>(op, s.as<double>(), d.as<double>(), 1, n, false, PREC_DF64));

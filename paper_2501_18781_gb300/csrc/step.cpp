@@ -327,6 +327,7 @@ mf_status mf_meltpool_advance(mf_meltpool_step* step, const double* u_prev, cons
     fs.schur_maxit = p.flow_schur_maxit;
     fs.schur_tol = p.flow_schur_tol;
     fs.use_graph = 1;
+    fs.fp64_arith = 1;   // the outer Oseen applies in double-float (fp64-accurate, 1.14x the fp64 pipes at 64^3)
     MF_TRY(run_solve(S.flow, fs, bf, up, &inf.flow_iterations, &inf.flow_residual, &worst));
     MF_TRY(lap(3, t));
     inf.seconds[4] = std::chrono::duration<double>(clk::now() - t0).count();

@@ -25,7 +25,7 @@ def ctx():
     return Context(0)
 
 
-def meltpool(n, ctx, flags, darcy_c=1e6):
+def meltpool(n, ctx, flags, darcy_c=1e6, with_temperature=True):
     from paper_2501_18781_gb300 import DofMap, Mesh, Operator
     from paper_2501_18781_gb300._lib import MF_OSEEN_DARCY, MF_OSEEN_THREE_PHASE, MF_OSEEN_TRACE_CORRECTION
     wl = syn.scaled(syn.OSEEN_INTERFACE, n)
@@ -51,7 +51,8 @@ def meltpool(n, ctx, flags, darcy_c=1e6):
                   darcy_c=darcy_c, darcy_b=1.0, oseen_flags=bits)
     op.set_field("phi", torch.tensor(phi, device="cuda"))
     op.set_field("beta", torch.tensor(beta.ravel(), device="cuda"))
-    op.set_field("t_prev", torch.tensor(T, device="cuda"))
+    if with_temperature:
+        op.set_field("t_prev", torch.tensor(T, device="cuda"))
     return dict(A=A, op=op, n=A.shape[0], dmu=dmu, dmp=dmp)
 
 
@@ -64,6 +65,10 @@ def test_meltpool_oseen_apply_matches_oracle(ctx, flags):
     v = P["op"].apply(torch.tensor(u, device="cuda")).cpu().numpy()
     ok, worst = componentwise_ok(v, ref, bound, 1e-12)
     assert ok, (flags, worst)
+    vd = P["op"].apply(torch.tensor(u, device="cuda"), arith="df64").cpu().numpy()   # double-float
+    ok, worst = componentwise_ok(vd, ref, bound, 1e-12)
+    assert ok, (flags, "df64", worst)
+    assert P["op"].variant.startswith("oseen_q2q1/df64/") and P["op"].variant.endswith("/meltpool"), P["op"].variant
     u32 = u.astype(np.float32)
     v32 = P["op"].apply(torch.tensor(u32, device="cuda")).cpu().numpy().astype(np.float64)
     ok, worst = componentwise_ok(v32, P["A"] @ u32.astype(np.float64), abs(P["A"]) @ np.abs(u32.astype(np.float64)),
@@ -113,9 +118,12 @@ def test_meltpool_oseen_solve_with_block_preconditioner(ctx):
     assert res <= 1e-10 * (1 + 1e-3), (res, info)
 
 
-def test_meltpool_rejects_double_float_and_missing_temperature(ctx):
+def test_meltpool_rejects_missing_temperature(ctx):
+    """Three-phase and Darcy terms need the nodal temperature: without it every arithmetic refuses."""
     from paper_2501_18781_gb300._lib import MFError
-    P = meltpool(3, ctx, ("darcy",))
-    u = torch.tensor(syn.uniform_pm1(1, P["n"]), device="cuda")
-    with pytest.raises(MFError):
-        P["op"].apply(u, arith="df64")
+    for flags in (("darcy",), ("three",)):
+        P = meltpool(3, ctx, flags, with_temperature=False)
+        u = torch.tensor(syn.uniform_pm1(1, P["n"]), device="cuda")
+        for arith in (None, "df64"):
+            with pytest.raises(MFError):
+                P["op"].apply(u, arith=arith)
