@@ -60,7 +60,15 @@ def test_autotune_cache_is_written_then_read_back(ctx, tmp_path):
     op3.autotune(path)
     want = "/tabulated" if forced["mode32"] == 1 else "/inkernel"
     assert want in _f32_variant(op3, m.n_dofs)
+    # so is the choice of one or nine threads per cell (the line-per-thread kernel)
+    assert rec["q2_line32"] in (0, 1) and rec["q2_line64"] in (0, 1)
+    line = dict(rec, q2_line32=1 - rec["q2_line32"])
+    with open(path, "a") as f:
+        f.write(json.dumps(line) + "\n")
+    op5, _ = _heat(ctx)
+    op5.autotune(path)
+    assert ("line-per-thread" in _f32_variant(op5, m.n_dofs)) == bool(line["q2_line32"])
     # another configuration (other mesh size) does not match the key: it is timed and appended
     op4, _ = _heat(ctx, 5)
     op4.autotune(path)
-    assert len(open(path).read().splitlines()) == 3
+    assert len(open(path).read().splitlines()) == 4
