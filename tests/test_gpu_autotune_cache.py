@@ -52,8 +52,9 @@ def test_autotune_cache_is_written_then_read_back(ctx, tmp_path):
     op2.autotune(path)
     assert len(open(path).read().splitlines()) == 1
     assert _f32_variant(op2, m.n_dofs) == _f32_variant(op, m.n_dofs)
-    # a record that forces the other fp32 coefficient mode is honoured (the last matching record wins)
-    forced = dict(rec, mode32=1 - rec["mode32"])
+    # a record that forces the other fp32 coefficient mode is honoured (the last matching record wins);
+    # it also selects one thread per cell, the kernel whose variant shows the coefficient mode
+    forced = dict(rec, mode32=1 - rec["mode32"], q2_line32=0)
     with open(path, "a") as f:
         f.write(json.dumps(forced) + "\n")
     op3, _ = _heat(ctx)
