@@ -949,6 +949,7 @@ def probe(argv):
         heat_solve [n] [fp64|mixed|fp64_df64_applies|mixed_df64_outer]
         heat_adjoint [n] [f64|df64] [forward|transpose]
         helmholtz_qk [k] [n] [f32|f64|tc]
+        meltpool_step [n]
     Inputs come from the seeded generators; every apply runs in libmfgb."""
     import numpy as np
     import torch
@@ -1026,6 +1027,18 @@ def probe(argv):
         torch.cuda.synchronize()
         torch.cuda.nvtx.range_pop()
         print(op.variant, n, info)
+    elif kind == "meltpool_step":
+        # one melt-pool algorithm step after a warm-up step, inside the NVTX range "timed_step"
+        n = int(argv[1]) if len(argv) > 1 else 64
+        _, _, state, step = build_meltpool_step(ctx, n)
+        step.advance(state)
+        torch.cuda.synchronize()
+        torch.cuda.nvtx.range_push("timed_step")   # for ncu --nvtx-include timed_step/
+        _, info = step.advance(state)
+        torch.cuda.synchronize()
+        torch.cuda.nvtx.range_pop()
+        print(n, {k: info[k] for k in ("seconds", "advection_iterations", "reinit_iterations", "heat_iterations",
+                                       "flow_iterations", "status")})
     elif kind == "helmholtz_qk":
         k = int(argv[1]) if len(argv) > 1 else 3
         n = int(argv[2]) if len(argv) > 2 else 64

@@ -623,6 +623,15 @@ template <typename T> OseenArgs<T> oseen_args(const mf_op* op, const T* src, T* 
 }
 template OseenArgs<double> oseen_args<double>(const mf_op*, const double*, double*);
 
+// the block-triangular preconditioner's fp32 block inverses (entry-major, 9 nu) and inverse pressure
+// scaling (n_p), from the fp32 Gauss-point tables
+mf_status oseen_blocks32(mf_op* op, float* blk, float* pinv) {
+  if (op->p.kind != MF_OP_OSEEN) return fail(MF_EINVAL, "nodal blocks exist for the Oseen operator only");
+  MF_TRY(check_fields(op));
+  MF_TRY(ensure_tables(op));
+  return launch_oseen_blockdiag32(op->ctx, op->map[0], op->map[1], oseen_args<float>(op, nullptr, nullptr), blk, pinv);
+}
+
 // Packed 16-bit arithmetic (two right-hand sides per thread) on fp32 vectors: scalar operators
 // with tabulated coefficients and no convection.
 mf_status apply_h16(mf_op* op, const float* src, float* dst, int nrhs, int64_t ld, bool transpose, int prec) {
@@ -770,7 +779,9 @@ mf_status apply_impl(mf_op* op, const T* src, T* dst, int nrhs, int64_t ld, bool
       return MF_OK;
     }
     // double-float on uniform meshes: the plane-by-plane kernel with the split coefficient table
-    if (df && op->map[0]->uniform && (kind == K_HELM || kind == K_HEAT) && !op->rhocp_user && nrhs <= 65535) {
+    // (a value coefficient per Gauss point, rho_cp,q / dt, needs the convective kernel)
+    const bool qm = kind == K_HEAT && op->rhocp_user;
+    if (df && op->map[0]->uniform && (kind == K_HELM || kind == K_HEAT) && (!qm || beta) && nrhs <= 65535) {
       if (!op->df_ready) {
         MF_TRY(op->qcoef_dfh.alloc(sizeof(float) * 27 * op->ncells));
         MF_TRY(op->qcoef_dfl.alloc(sizeof(float) * 27 * op->ncells));
@@ -782,13 +793,21 @@ mf_status apply_impl(mf_op* op, const T* src, T* dst, int nrhs, int64_t ld, bool
           MF_TRY(launch_df_vec_split(c, op->map[0], op->qvec64.as<double>(), op->qvec_dfh.as<float>(),
                                      op->qvec_dfl.as<float>()));
         }
+        if (qm) {
+          MF_TRY(op->qmass_dfh.alloc(sizeof(float) * 27 * op->ncells));
+          MF_TRY(op->qmass_dfl.alloc(sizeof(float) * 27 * op->ncells));
+          MF_TRY(launch_df_mass_split(c, op->map[0], op->qmass64.as<double>(), op->qmass_dfh.as<float>(),
+                                      op->qmass_dfl.as<float>()));
+        }
         op->df_ready = true;
       }
       if (beta)
         MF_TRY(launch_scalar_df_uniform_conv(c, op->map[0], reinterpret_cast<const double*>(src),
                                              reinterpret_cast<double*>(dst), nrhs, ld, op->qcoef_dfh.as<float>(),
                                              op->qcoef_dfl.as<float>(), op->qvec_dfh.as<float>(),
-                                             op->qvec_dfl.as<float>(), value_coef(op), transpose));
+                                             op->qvec_dfl.as<float>(), value_coef(op), transpose,
+                                             qm ? op->qmass_dfh.as<float>() : nullptr,
+                                             qm ? op->qmass_dfl.as<float>() : nullptr));
       else
         MF_TRY(launch_scalar_df_uniform(c, op->map[0], reinterpret_cast<const double*>(src),
                                         reinterpret_cast<double*>(dst), nrhs, ld, op->qcoef_dfh.as<float>(),
@@ -833,20 +852,21 @@ template <typename T> mf_status oseen_coupling(mf_op* op, int which, const T* sr
   const int64_t nu = op->map[0]->n_dofs, np = op->map[1]->n_dofs;
   if (which == 2) {
     MF_TRY(check_fields(op));
-    MF_TRY(diag64(op, nullptr));
     DevBuf ua, ub;
     if constexpr (sizeof(T) == 4) {
       // the preconditioner's form: the assembled 125-point stencil from the fp32 block inverses
       const int* gn = op->map[0]->mesh->n;
-      DevBuf sc;
+      DevBuf sc, pinv;
       MF_TRY(ua.alloc(sizeof(float) * 9 * size_t(nu)));
       MF_TRY(ub.alloc(2 * size_t(stencil_halves(np))));
       MF_TRY(sc.alloc(sizeof(float) * size_t(np)));
-      MF_TRY(blocks_soa32(op->ctx, nu, op->blk64.as<double>(), ua.as<float>()));
+      MF_TRY(pinv.alloc(sizeof(float) * size_t(np)));
+      MF_TRY(oseen_blocks32(op, ua.as<float>(), pinv.as<float>()));
       MF_TRY(launch_schur_assemble_f32(op->ctx, op->map[0], ua.as<float>(), ub.p, sc.as<float>()));
       MF_TRY(stencil125_apply(op->ctx, ub.p, sc.as<float>(), src, dst, gn[0], gn[1], gn[2], nullptr));
       MF_CUDA_TRY(cudaStreamSynchronize(op->ctx->stream));  // before sc is freed
     } else {
+      MF_TRY(diag64(op, nullptr));
       MF_TRY(ua.alloc(sizeof(T) * 3 * size_t(nu)));
       MF_TRY(ub.alloc(sizeof(T) * 3 * size_t(nu)));
       MF_TRY(oseen_coupling<T>(op, 0, src, ua.as<T>()));

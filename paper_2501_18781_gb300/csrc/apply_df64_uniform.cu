@@ -208,9 +208,11 @@ struct DfConvArgs {
   const float* bl;
   int64_t ncells;
   float wmh[27], wml[27];
+  const float* mh;  // QM: [27][ncells] w_q h^3 m_q per Gauss point (m_q = rho_cp,q / dt) instead of wmh
+  const float* ml;
 };
 
-template <bool TR>
+template <bool TR, bool QM>
 __global__ void __launch_bounds__(kThreads, TR ? 5 : 4) k_scalar_df_uniform_conv(DfConvArgs A, UniformGeom ug) {
   extern __shared__ float conv_smem[];
   float(*sh)[kThreads] = reinterpret_cast<float(*)[kThreads]>(conv_smem);
@@ -278,7 +280,10 @@ __global__ void __launch_bounds__(kThreads, TR ? 5 : 4) k_scalar_df_uniform_conv
 #pragma unroll
     for (int p = 0; p < 9; ++p) {
       const int q = p + 9 * qc;
-      dd acc = dd_mul(dd{A.wmh[q], A.wml[q]}, Uq(q));
+      const dd wm = !QM ? dd{A.wmh[q], A.wml[q]}
+                        : active ? dd{__ldg(A.mh + q * A.ncells + cell), __ldg(A.ml + q * A.ncells + cell)}
+                                 : dd{0.f, 0.f};
+      dd acc = dd_mul(wm, Uq(q));
       if (!TR) acc = dd_add(acc, dd{zh[q][t], zl[q][t]});
 #pragma unroll
       for (int c2 = 0; c2 < 3; ++c2)
@@ -617,7 +622,8 @@ __global__ void k_split_plain(const double* __restrict__ c, int64_t n, float* h,
   l[t] = __double2float_rn(c[t] - double(hi));
 }
 
-// w_q h c_q of the Gauss-point coefficient table, split into high and low float parts
+// w_q s c_q of a Gauss-point coefficient table (s = h for the conductivity, h^3 for the value
+// coefficient), split into high and low float parts
 __global__ void k_split_coef(const double* __restrict__ c, int64_t ncells, double h, float* ch, float* cl) {
   const int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (t >= 27 * ncells) return;
@@ -653,14 +659,17 @@ mf_status launch_df_vec_split(mf_ctx* ctx, const mf_dofmap* m, const double* qve
 
 mf_status launch_scalar_df_uniform_conv(mf_ctx* ctx, const mf_dofmap* m, const double* src, double* dst, int nrhs,
                                         int64_t ld, const float* ch, const float* cl, const float* bh, const float* bl,
-                                        double mass, bool transpose) {
+                                        double mass, bool transpose, const float* mh, const float* ml) {
   MF_CUDA_TRY(upload_tables_here());
   static bool attrs = false;
   if (!attrs) {
-    MF_CUDA_TRY(cudaFuncSetAttribute(k_scalar_df_uniform_conv<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     int(108 * kThreads * sizeof(float))));
+    MF_CUDA_TRY(cudaFuncSetAttribute(k_scalar_df_uniform_conv<false, false>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, int(108 * kThreads * sizeof(float))));
+    MF_CUDA_TRY(cudaFuncSetAttribute(k_scalar_df_uniform_conv<false, true>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, int(108 * kThreads * sizeof(float))));
     attrs = true;
   }
+  if ((mh == nullptr) != (ml == nullptr)) return fail(MF_EINVAL, "per-Gauss-point mass: both parts or neither");
   const Tables tb = make_tables();
   DfConvArgs a{};
   a.src = src;
@@ -672,6 +681,8 @@ mf_status launch_scalar_df_uniform_conv(mf_ctx* ctx, const mf_dofmap* m, const d
   a.bh = bh;
   a.bl = bl;
   a.ncells = m->n_cells;
+  a.mh = mh;
+  a.ml = ml;
   const double h = m->mesh->h0;
   for (int q = 0; q < 27; ++q) {
     const double v = tb.W3[q] * mass * h * h * h;
@@ -680,10 +691,25 @@ mf_status launch_scalar_df_uniform_conv(mf_ctx* ctx, const mf_dofmap* m, const d
   }
   const UniformGeom ug = uniform_geom(m);
   const dim3 grid(brick_blocks(ug.nx, ug.ny, ug.nz), nrhs);
-  if (transpose)
-    k_scalar_df_uniform_conv<true><<<grid, kThreads, 54 * kThreads * sizeof(float), ctx->stream>>>(a, ug);
+  const size_t sm_tr = 54 * kThreads * sizeof(float), sm_fw = 108 * kThreads * sizeof(float);
+  if (transpose && mh)
+    k_scalar_df_uniform_conv<true, true><<<grid, kThreads, sm_tr, ctx->stream>>>(a, ug);
+  else if (transpose)
+    k_scalar_df_uniform_conv<true, false><<<grid, kThreads, sm_tr, ctx->stream>>>(a, ug);
+  else if (mh)
+    k_scalar_df_uniform_conv<false, true><<<grid, kThreads, sm_fw, ctx->stream>>>(a, ug);
   else
-    k_scalar_df_uniform_conv<false><<<grid, kThreads, 108 * kThreads * sizeof(float), ctx->stream>>>(a, ug);
+    k_scalar_df_uniform_conv<false, false><<<grid, kThreads, sm_fw, ctx->stream>>>(a, ug);
+  ctx->launches++;
+  MF_CUDA_TRY(cudaGetLastError());
+  return MF_OK;
+}
+
+mf_status launch_df_mass_split(mf_ctx* ctx, const mf_dofmap* m, const double* qmass64, float* mh, float* ml) {
+  MF_CUDA_TRY(upload_tables_here());
+  const int64_t n = 27 * m->n_cells;
+  const double h = m->mesh->h0;
+  k_split_coef<<<int((n + 255) / 256), 256, 0, ctx->stream>>>(qmass64, m->n_cells, h * h * h, mh, ml);
   ctx->launches++;
   MF_CUDA_TRY(cudaGetLastError());
   return MF_OK;

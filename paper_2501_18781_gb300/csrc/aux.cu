@@ -245,15 +245,15 @@ __global__ void k_oseen_fold(int64_t nc, double h, double sigma, const double* r
 
 // ---------------------------------------------------------------- diagonals
 // out[l] += sum_q c[q] X[qa][a] Y[qb][b] Z[qc][c] with 1D tables X, Y, Z (3x3, [q][a]).
-__device__ __forceinline__ void separable_add(const double* c, const double* X, const double* Y, const double* Z,
-                                              double* out) {
-  double t[27];
+template <typename T>
+__device__ __forceinline__ void separable_add(const T* c, const T* X, const T* Y, const T* Z, T* out) {
+  T t[27];
 #pragma unroll
   for (int i = 0; i < 27; ++i) t[i] = c[i];
   // x: t[a, qb, qc] = sum_qa X[qa][a] t[qa, qb, qc]
 #pragma unroll
   for (int j = 0; j < 9; ++j) {
-    double u0 = t[3 * j], u1 = t[3 * j + 1], u2 = t[3 * j + 2];
+    T u0 = t[3 * j], u1 = t[3 * j + 1], u2 = t[3 * j + 2];
     t[3 * j] = X[0] * u0 + X[3] * u1 + X[6] * u2;
     t[3 * j + 1] = X[1] * u0 + X[4] * u1 + X[7] * u2;
     t[3 * j + 2] = X[2] * u0 + X[5] * u1 + X[8] * u2;
@@ -261,14 +261,14 @@ __device__ __forceinline__ void separable_add(const double* c, const double* X, 
 #pragma unroll
   for (int j = 0; j < 9; ++j) {
     const int b = (j % 3) + 9 * (j / 3);
-    double u0 = t[b], u1 = t[b + 3], u2 = t[b + 6];
+    T u0 = t[b], u1 = t[b + 3], u2 = t[b + 6];
     t[b] = Y[0] * u0 + Y[3] * u1 + Y[6] * u2;
     t[b + 3] = Y[1] * u0 + Y[4] * u1 + Y[7] * u2;
     t[b + 6] = Y[2] * u0 + Y[5] * u1 + Y[8] * u2;
   }
 #pragma unroll
   for (int j = 0; j < 9; ++j) {
-    double u0 = t[j], u1 = t[j + 9], u2 = t[j + 18];
+    T u0 = t[j], u1 = t[j + 9], u2 = t[j + 18];
     out[j] += Z[0] * u0 + Z[3] * u1 + Z[6] * u2;
     out[j + 9] += Z[1] * u0 + Z[4] * u1 + Z[7] * u2;
     out[j + 18] += Z[2] * u0 + Z[5] * u1 + Z[8] * u2;
@@ -480,11 +480,181 @@ __global__ void k_invert_blocks(double* blk, const uint8_t* dir, int64_t n) {
   B[6] = A2 * inv; B[7] = -(a * hh - b * g) * inv; B[8] = (a * e - b * d) * inv;
 }
 
-__global__ void k_pressure_scaling(const double* pm, const double* pk, double* pinv, int64_t n) {
+template <typename T> __global__ void k_pressure_scaling(const T* pm, const T* pk, T* pinv, int64_t n) {
   int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (i >= n) return;
   // Schur complement diagonal ~ (1/pm + 1/pk)^-1; store its inverse
-  pinv[i] = 1.0 / pm[i] + 1.0 / pk[i];
+  pinv[i] = T(1) / pm[i] + T(1) / pk[i];
+}
+
+// The same blocks and pressure scaling in fp32, for the block-triangular preconditioner (which
+// applies them in fp32): built from the folded fp32 Gauss-point tables cm = w h^3 (sigma rho +
+// Darcy), cb_d = w h^2 rho beta_d and cv = w h mu.  One thread per cell; its 27 x 9 block entries
+// accumulate in the thread's own shared-memory column (entry (e, l) at [(9 l + e) kBlk32][thread])
+// and leave with one atomic each into the entry-major output blk[e nu + node].
+constexpr int kBlk32 = 32;
+__global__ void __launch_bounds__(kBlk32) k_oseen_blocks32(OseenArgs<float> A, UniformGeom ug, float* blk, float* pm,
+                                                           float* pk) {
+  __shared__ float sB[243 * kBlk32];
+  Loc L;
+  OctGeom og{};
+  const int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (!natural_cell<false>(ug, og, t, L)) return;
+  const int64_t nc = int64_t(ug.nx) * ug.ny * ug.nz, cell = L.cell;
+  float* B = sB + threadIdx.x;
+  auto at = [&](int e, int l) -> float& { return B[(9 * l + e) * kBlk32]; };
+  float c[27], s[27];
+  // scalar part sigma rho mass (+ Darcy) + rho convection, on the three diagonal entries
+#pragma unroll
+  for (int q = 0; q < 27; ++q) {
+    c[q] = A.cm[q * nc + cell];
+    s[q] = 0.f;
+  }
+  separable_add<float>(c, cSS32, cSS32, cSS32, s);
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+#pragma unroll
+    for (int q = 0; q < 27; ++q) c[q] = A.cb[(d * 27 + q) * nc + cell];
+    separable_add<float>(c, d == 0 ? cSSp32 : cSS32, d == 1 ? cSSp32 : cSS32, d == 2 ? cSSp32 : cSS32, s);
+  }
+#pragma unroll
+  for (int l = 0; l < 27; ++l)
+#pragma unroll
+    for (int e = 0; e < 9; ++e) at(e, l) = (e % 4 == 0) ? s[l] : 0.f;
+  // viscous part: B[d][e] = delta_de mu |grad N|^2 + mu d_e N d_d N
+#pragma unroll
+  for (int q = 0; q < 27; ++q) c[q] = A.cv[q * nc + cell];
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+#pragma unroll
+    for (int l = 0; l < 27; ++l) s[l] = 0.f;
+    separable_add<float>(c, d == 0 ? cSpSp32 : cSS32, d == 1 ? cSpSp32 : cSS32, d == 2 ? cSpSp32 : cSS32, s);
+#pragma unroll
+    for (int l = 0; l < 27; ++l) {
+      at(0, l) += d == 0 ? 2.f * s[l] : s[l];
+      at(4, l) += d == 1 ? 2.f * s[l] : s[l];
+      at(8, l) += d == 2 ? 2.f * s[l] : s[l];
+    }
+  }
+#pragma unroll
+  for (int p = 0; p < 3; ++p) {
+    const int d = p == 2 ? 1 : 0, e = p == 0 ? 1 : 2;  // (0,1), (0,2), (1,2)
+#pragma unroll
+    for (int l = 0; l < 27; ++l) s[l] = 0.f;
+    separable_add<float>(c, (d == 0) ? cSSp32 : cSS32, (d == 1 || e == 1) ? cSSp32 : cSS32,
+                         (e == 2) ? cSSp32 : cSS32, s);
+#pragma unroll
+    for (int l = 0; l < 27; ++l) {
+      at(3 * d + e, l) += s[l];
+      at(3 * e + d, l) += s[l];
+    }
+  }
+  if (A.ext) {
+    // trace correction: B[d][e] += sum_q -2 cv n_d (n . grad N) d_e N (nonsymmetric)
+    float n0[27], n1[27], n2[27];
+#pragma unroll
+    for (int q = 0; q < 27; ++q) {
+      n0[q] = A.nrm[q * nc + cell];
+      n1[q] = A.nrm[(27 + q) * nc + cell];
+      n2[q] = A.nrm[(54 + q) * nc + cell];
+      c[q] *= -2.f;
+    }
+    for (int l = 0; l < 27; ++l) {
+      const int a = l % 3, b = (l / 3) % 3, cc = l / 9;
+      float Sa[3], Pa[3], Sb[3], Pb[3], Sc[3], Pc[3];
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        Sa[k] = cS32[3 * k + a];
+        Pa[k] = cSp32[3 * k + a];
+        Sb[k] = cS32[3 * k + b];
+        Pb[k] = cSp32[3 * k + b];
+        Sc[k] = cS32[3 * k + cc];
+        Pc[k] = cSp32[3 * k + cc];
+      }
+      float acc[9];
+#pragma unroll
+      for (int e = 0; e < 9; ++e) acc[e] = 0.f;
+#pragma unroll
+      for (int q = 0; q < 27; ++q) {
+        const int qa = q % 3, qb = (q / 3) % 3, qc = q / 9;
+        const float g0 = Pa[qa] * Sb[qb] * Sc[qc], g1 = Sa[qa] * Pb[qb] * Sc[qc], g2 = Sa[qa] * Sb[qb] * Pc[qc];
+        const float tq = c[q] * (n0[q] * g0 + n1[q] * g1 + n2[q] * g2);
+        const float tn[3] = {tq * n0[q], tq * n1[q], tq * n2[q]};
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+          acc[3 * d] += tn[d] * g0;
+          acc[3 * d + 1] += tn[d] * g1;
+          acc[3 * d + 2] += tn[d] * g2;
+        }
+      }
+#pragma unroll
+      for (int e = 0; e < 9; ++e) at(e, l) += acc[e];
+    }
+  }
+  const int64_t nu = A.nu;
+  for (int l = 0; l < 27; ++l) {
+    if ((L.dmask >> l) & 1u) continue;
+    const int a = l % 3, b = (l / 3) % 3, cc = l / 9;
+    const int64_t id = L.base + a + ug.sx * b + ug.sy * cc;
+#pragma unroll
+    for (int e = 0; e < 9; ++e) atomicAdd(blk + e * nu + id, at(e, l));
+  }
+  // pressure: sum_q psi_i^2 w h^3 / mu and sum_q |grad psi_i|^2 w h / (sigma rho + Darcy), with
+  // w h^3 / mu = (w h^2)^2 / cv and w h / (sigma rho + Darcy) = (w h^2)^2 / cm
+  const float h = float(L.h);
+  float r1[27], r2[27];
+#pragma unroll
+  for (int q = 0; q < 27; ++q) {
+    const float whh = cW332[q] * h * h;
+    r1[q] = whh * (whh / A.cv[q * nc + cell]);
+    r2[q] = whh * (whh / A.cm[q * nc + cell]);
+  }
+  const int64_t px = ug.nx + 1, pxy = px * (ug.ny + 1);
+  const int64_t pbase = L.i + px * (L.j + (ug.ny + 1) * int64_t(L.k));
+#pragma unroll
+  for (int n = 0; n < 8; ++n) {
+    const int a = n & 1, b = (n >> 1) & 1, cc = n >> 2;
+    float m = 0.f, kk = 0.f;
+#pragma unroll
+    for (int q = 0; q < 27; ++q) {
+      const int qa = q % 3, qb = (q / 3) % 3, qc = q / 9;
+      const float pa = cP32[2 * qa + a], pb = cP32[2 * qb + b], pc = cP32[2 * qc + cc];
+      const float psi = pa * pb * pc;
+      m += psi * psi * r1[q];
+      kk += (pb * pb * pc * pc + pa * pa * pc * pc + pa * pa * pb * pb) * r2[q];
+    }
+    const int64_t id = pbase + a + px * b + pxy * cc;
+    atomicAdd(pm + id, m);
+    atomicAdd(pk + id, kk);
+  }
+}
+
+// inverse of each entry-major fp32 3 x 3 block in place
+__global__ void k_invert_blocks_soa32(float* blk, int64_t n) {
+  const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const float a = blk[i], b = blk[n + i], c = blk[2 * n + i], d = blk[3 * n + i], e = blk[4 * n + i];
+  const float f = blk[5 * n + i], g = blk[6 * n + i], hh = blk[7 * n + i], k = blk[8 * n + i];
+  const float A0 = e * k - f * hh, A1 = -(d * k - f * g), A2 = d * hh - e * g;
+  const float inv = 1.f / (a * A0 + b * A1 + c * A2);
+  blk[i] = A0 * inv;
+  blk[n + i] = -(b * k - c * hh) * inv;
+  blk[2 * n + i] = (b * f - c * e) * inv;
+  blk[3 * n + i] = A1 * inv;
+  blk[4 * n + i] = (a * k - c * g) * inv;
+  blk[5 * n + i] = -(a * f - c * d) * inv;
+  blk[6 * n + i] = A2 * inv;
+  blk[7 * n + i] = -(a * hh - b * g) * inv;
+  blk[8 * n + i] = (a * e - b * d) * inv;
+}
+
+// identity blocks at the listed (Dirichlet) nodes, entry-major
+__global__ void k_identity_blocks_soa32(float* blk, const int32_t* list, int64_t nl, int64_t n) {
+  const int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (t >= nl) return;
+  const int64_t i = list[t];
+#pragma unroll
+  for (int e = 0; e < 9; ++e) blk[e * n + i] = (e % 4 == 0) ? 1.f : 0.f;
 }
 
 // ---------------------------------------------------------------- laser load
@@ -661,10 +831,33 @@ mf_status launch_oseen_blockdiag(mf_ctx* ctx, const mf_dofmap* mu, const mf_dofm
   DevBuf dflag;
   if (!mu->dirichlet_list.empty()) MF_TRY(dflag.upload(mu->dirichlet, ctx->stream));
   k_invert_blocks<<<blocks(nu, 256), 256, 0, ctx->stream>>>(blk, dflag.as<uint8_t>(), nu);
-  k_pressure_scaling<<<blocks(np, 256), 256, 0, ctx->stream>>>(pm, pk, pdiag, np);
+  k_pressure_scaling<double><<<blocks(np, 256), 256, 0, ctx->stream>>>(pm, pk, pdiag, np);
   ctx->launches += 3;
   MF_CUDA_TRY(cudaGetLastError());
   MF_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+  return MF_OK;
+}
+
+mf_status launch_oseen_blockdiag32(mf_ctx* ctx, const mf_dofmap* mu, const mf_dofmap* mp, const OseenArgs<float>& a,
+                                   float* blk, float* pinv) {
+  MF_CUDA_TRY(upload_tables_here());
+  if (!mu->uniform) return fail(MF_EUNSUPPORTED, "Oseen blocks: uniform meshes");
+  UniformGeom ug = uniform_geom(mu);
+  const int64_t nu = mu->n_dofs, np = mp->n_dofs;
+  DevBuf tmp;
+  MF_TRY(tmp.alloc(sizeof(float) * 2 * np));
+  float* pm = tmp.as<float>();
+  float* pk = pm + np;
+  MF_CUDA_TRY(cudaMemsetAsync(blk, 0, sizeof(float) * 9 * nu, ctx->stream));
+  MF_CUDA_TRY(cudaMemsetAsync(pm, 0, sizeof(float) * 2 * np, ctx->stream));
+  k_oseen_blocks32<<<blocks(mu->n_cells, kBlk32), kBlk32, 0, ctx->stream>>>(a, ug, blk, pm, pk);
+  k_invert_blocks_soa32<<<blocks(nu, 256), 256, 0, ctx->stream>>>(blk, nu);
+  const int64_t nd = int64_t(mu->dirichlet_list.size());
+  if (nd) k_identity_blocks_soa32<<<blocks(nd, 256), 256, 0, ctx->stream>>>(blk, mu->d_dir_list.as<int32_t>(), nd, nu);
+  k_pressure_scaling<float><<<blocks(np, 256), 256, 0, ctx->stream>>>(pm, pk, pinv, np);
+  ctx->launches += nd ? 4 : 3;
+  MF_CUDA_TRY(cudaGetLastError());
+  MF_CUDA_TRY(cudaStreamSynchronize(ctx->stream));  // before the scratch is freed
   return MF_OK;
 }
 

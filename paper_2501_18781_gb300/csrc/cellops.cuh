@@ -29,6 +29,7 @@ struct Tables {
 static __constant__ double cS64[9], cD64[9], cW64[3], cP64[6], cSp64[9], cW364[27];
 static __constant__ float cS32[9], cD32[9], cW32[3], cP32[6], cSp32[9], cW332[27];
 static __constant__ double cSS64[9], cSSp64[9], cSpSp64[9], cPP64[6], cPpPp64[6];
+static __constant__ float cSS32[9], cSSp32[9], cSpSp32[9];
 static __constant__ double cPW64[216], cG64[3], cPWW64[216];
 static __constant__ float cPW32[216], cPWW32[216];
 // double-float copies (hi, lo) for the df64 kernels
@@ -87,6 +88,7 @@ Tables make_tables();           // host: closed forms (cellops_host.cpp)
     up32(cPW32, t.PW, 216); up64(cPWW64, t.PWW, 216); up32(cPWW32, t.PWW, 216);           \
     up32(cS32, t.S, 9); up32(cD32, t.D, 9); up32(cW32, t.W, 3); up32(cP32, t.P, 6);       \
     up32(cSp32, t.Sp, 9); up32(cW332, t.W3, 27);                                          \
+    up32(cSS32, t.SS, 9); up32(cSSp32, t.SSp, 9); up32(cSpSp32, t.SpSp, 9);               \
     auto updf = [&](const void* sh, const void* sl, const double* src, int n) {           \
       for (int i = 0; i < n; ++i) {                                                       \
         f[i] = float(src[i]);                                                             \

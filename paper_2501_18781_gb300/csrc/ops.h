@@ -93,6 +93,10 @@ mf_status launch_scalar_diag(mf_ctx* ctx, const mf_dofmap* m, int kind, bool bet
 // Oseen block-Jacobi: 3x3 velocity blocks (inverted in place) and pressure scaling
 mf_status launch_oseen_blockdiag(mf_ctx* ctx, const mf_dofmap* mu, const mf_dofmap* mp, const OseenArgs<double>& a,
                                  double* blk, double* pdiag);
+// the same in fp32 from the folded fp32 tables (a: oseen_args<float>): blk = the inverted blocks,
+// entry-major (blk[e nu + node], identity at Dirichlet nodes), pinv = the inverse pressure scaling
+mf_status launch_oseen_blockdiag32(mf_ctx* ctx, const mf_dofmap* mu, const mf_dofmap* mp, const OseenArgs<float>& a,
+                                   float* blk, float* pinv);
 // dst[dir] = src[dir] for nrhs vectors (Dirichlet identity rows)
 mf_status launch_dirichlet_copy(mf_ctx* ctx, const mf_dofmap* m, const void* src, void* dst, int nrhs, int64_t ld,
                                 int64_t offset, bool f32);
@@ -132,8 +136,11 @@ mf_status launch_df_coef_split(mf_ctx* ctx, const mf_dofmap* m, const double* qc
 // float pairs of w_q h^2 rho_cp beta_d ([3][27][ncells], from launch_df_vec_split)
 mf_status launch_scalar_df_uniform_conv(mf_ctx* ctx, const mf_dofmap* m, const double* src, double* dst, int nrhs,
                                         int64_t ld, const float* ch, const float* cl, const float* bh, const float* bl,
-                                        double mass, bool transpose);
+                                        double mass, bool transpose, const float* mh = nullptr,
+                                        const float* ml = nullptr);
 mf_status launch_df_vec_split(mf_ctx* ctx, const mf_dofmap* m, const double* qvec64, float* bh, float* bl);
+// [27][ncells] value coefficients m_q -> w_q h^3 m_q as float pairs (the mh, ml of the kernel above)
+mf_status launch_df_mass_split(mf_ctx* ctx, const mf_dofmap* m, const double* qmass64, float* mh, float* ml);
 // the reinitialisation operator in double-float on an octree map (normals from the float pairs of
 // the fp64 Gauss-point table, [3][27][ncells]); dst zeroed by the caller, Dirichlet rows left alone
 mf_status launch_reinit_df_octree(mf_ctx* ctx, const mf_dofmap* m, const double* src, double* dst, int nrhs,
@@ -172,6 +179,7 @@ struct mf_op {
   mf::DevBuf qcoef64, qcoef32;    // [27][ncells]
   mf::DevBuf qvec64, qvec32;      // [3][27][ncells]
   mf::DevBuf qmass64, qmass32;    // [27][ncells] heat value term rho_cp,q / dt
+  mf::DevBuf qmass_dfh, qmass_dfl;  // the same times w_q h^3 as float pairs (double-float applies)
   mf::DevBuf qcoef_tc;            // Q3 tensor-core apply: fp32 coefficients [tile of 128 cells][q][row]
   bool tc_ready = false;
   int qk_f32_tc = 0;              // Q3: plain fp32 applies run on the tensor cores (autotuned)

@@ -17,6 +17,7 @@ namespace mf {
 template <typename T>
 mf_status apply_impl(mf_op* op, const T* src, T* dst, int nrhs, int64_t ld, bool transpose, int prec = -1);
 mf_status diag64(mf_op* op, double** out);
+mf_status oseen_blocks32(mf_op* op, float* blk, float* pinv);
 mf_status check_fields(const mf_op* op);
 bool heat_convection(const mf_op* op);
 int qk_degree(const mf_op* op);
@@ -189,16 +190,16 @@ struct OseenBlockTri {
     if (ku > 60) return fail(MF_EINVAL, "velocity_steps must be at most 60");
     smax = schur_maxit > 0 ? schur_maxit : 30;
     stol = schur_tol > 0 ? schur_tol : 0.1;
-    MF_TRY(diag64(op, nullptr));  // 3x3 block inverses and the pressure scaling
+    // fp32 3x3 block inverses and inverse pressure scaling, computed in fp32 (the preconditioner
+    // applies them in fp32)
     MF_TRY(blk32.alloc(9 * nu));
-    MF_TRY(blocks_soa32(c, nu, op->blk64.as<double>(), blk32.p));
+    for (Vec<float>* v : {&pinv32, &xp, &rp, &zp, &pp, &sp}) MF_TRY(v->alloc(np));
+    MF_TRY(oseen_blocks32(op, blk32.p, pinv32.p));
     for (int d = 0; d < 3; ++d) gn[d] = op->map[0]->mesh->n[d];
     MF_TRY(stil.alloc(2 * size_t(stencil_halves(np))));
     MF_TRY(stscale.alloc(np));
     MF_TRY(launch_schur_assemble_f32(c, op->map[0], blk32.p, stil.p, stscale.p));
     MF_TRY(ua.alloc(nu3));
-    for (Vec<float>* v : {&pinv32, &xp, &rp, &zp, &pp, &sp}) MF_TRY(v->alloc(np));
-    MF_TRY((convert<double, float>(c, np, op->pdiag64.as<double>(), pinv32.p)));
     // Jacobi of the Schur CG: diag(S~)^-1 (the pressure scaling above where it is not positive)
     MF_TRY(stencil_diag_inverse(c, stil.p, stscale.p, np, pinv32.p));
     ldv = basis_stride(n);

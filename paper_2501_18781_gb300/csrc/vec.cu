@@ -264,12 +264,6 @@ __global__ void k_block_jacobi_scaled32(int64_t nu, const float* __restrict__ bl
     z[2 * nu + i] = blk[6 * nu + i] * r0 + blk[7 * nu + i] * r1 + blk[8 * nu + i] * r2;
   }
 }
-__global__ void k_blocks_soa32(int64_t nu, const double* __restrict__ blk, float* __restrict__ out) {
-  for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < nu; i += int64_t(gridDim.x) * blockDim.x)
-#pragma unroll
-    for (int e = 0; e < 9; ++e) out[e * nu + i] = float(blk[9 * i + e]);
-}
-
 template <typename TS, typename TD> __global__ void k_convert(int64_t n, const TS* s, TD* d) {
   for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x)
     d[i] = TD(s[i]);
@@ -610,11 +604,6 @@ mf_status block_jacobi_u32_scaled(mf_ctx* ctx, int64_t nu, const float* blk, con
 }
 mf_status block_jacobi_u32(mf_ctx* ctx, int64_t nu, const float* blk, const float* r, float* z) {
   k_block_jacobi_soa32<<<grid_for(nu), 256, 0, ctx->stream>>>(nu, blk, r, z);
-  LAUNCH_CHECK();
-  return MF_OK;
-}
-mf_status blocks_soa32(mf_ctx* ctx, int64_t nu, const double* blk, float* out) {
-  k_blocks_soa32<<<grid_for(nu), 256, 0, ctx->stream>>>(nu, blk, out);
   LAUNCH_CHECK();
   return MF_OK;
 }

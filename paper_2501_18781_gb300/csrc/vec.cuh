@@ -34,8 +34,6 @@ mf_status block_jacobi_u32(mf_ctx* ctx, int64_t nu, const float* blk, const floa
 // velocity part only: dst = s[0] src (s device; dst may equal src), then z_u = B^-1 dst per node
 mf_status block_jacobi_u32_scaled(mf_ctx* ctx, int64_t nu, const float* blk, const double* s, const float* src,
                                   float* dst, float* z);
-// the fp64 block inverses (9 per node, row major) as entry-major fp32
-mf_status blocks_soa32(mf_ctx* ctx, int64_t nu, const double* blk, float* out);
 
 // Batched CG pieces: nrhs systems, vectors ld apart, device scalars S[r * S_NSCAL + k]:
 // 0 rz, 1 pAp, 2 alpha, 3 beta, 4 rr, 5 rz_new, 6 active (1 = still iterating)

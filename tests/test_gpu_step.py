@@ -54,6 +54,11 @@ def test_heat_operator_with_gauss_point_rho_cp_and_velocity(ctx):
         v = op.apply(_cuda(u), transpose=transpose).cpu().numpy()
         ok, worst = componentwise_ok(v, M @ u, abs(M) @ np.abs(u), 1e-12)
         assert ok, (transpose, worst)
+        # double-float: the convective kernel with the value coefficient per Gauss point
+        v = op.apply(_cuda(u), transpose=transpose, arith="df64").cpu().numpy()
+        ok, worst = componentwise_ok(v, M @ u, abs(M) @ np.abs(u), 1e-12)
+        assert ok, (transpose, "df64", worst)
+        assert op.variant.endswith("/conv-T" if transpose else "/conv") and "/df64/" in op.variant, op.variant
         v32 = op.apply(_cuda(u).float(), transpose=transpose).cpu().double().numpy()
         ok, worst = componentwise_ok(v32, M @ u, abs(M) @ np.abs(u), 2e-5)
         assert ok, (transpose, worst)
