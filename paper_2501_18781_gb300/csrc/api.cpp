@@ -3,6 +3,7 @@
 #include <atomic>
 #include <cmath>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <string>
 
@@ -22,6 +23,55 @@ void set_error(const std::string& msg) { g_error = msg; }
 mf_status fail(mf_status st, const std::string& msg) {
   set_error(msg);
   return st;
+}
+
+// every live context's pool, so that a failed allocation anywhere can free the kept blocks
+static std::mutex g_pools_mu;
+static std::vector<BlockPool*> g_pools;
+thread_local BlockPool* tl_pool = nullptr;
+
+BlockPool::BlockPool() {
+  std::lock_guard<std::mutex> lk(g_pools_mu);
+  g_pools.push_back(this);
+}
+BlockPool::~BlockPool() {
+  trim();
+  std::lock_guard<std::mutex> lk(g_pools_mu);
+  g_pools.erase(std::remove(g_pools.begin(), g_pools.end(), this), g_pools.end());
+}
+mf_status BlockPool::get(size_t n, void** out) {
+  const size_t r = rounded(n);
+  auto it = keep.find(r);
+  if (it != keep.end()) {
+    *out = it->second;
+    keep.erase(it);
+    kept -= r;
+    return MF_OK;
+  }
+  if (cudaMalloc(out, r) != cudaSuccess) {
+    cudaGetLastError();
+    trim_block_pools();
+    if (cudaMalloc(out, r) != cudaSuccess) {
+      cudaGetLastError();
+      *out = nullptr;
+      return fail(MF_ENOMEM, "cudaMalloc of " + std::to_string(r) + " bytes failed");
+    }
+  }
+  return MF_OK;
+}
+void BlockPool::put(void* blk, size_t n) {
+  const size_t r = rounded(n);
+  keep.emplace(r, blk);
+  kept += r;
+}
+void BlockPool::trim() {
+  for (auto& kv : keep) cudaFree(kv.second);
+  keep.clear();
+  kept = 0;
+}
+void trim_block_pools() {
+  std::lock_guard<std::mutex> lk(g_pools_mu);
+  for (BlockPool* p : g_pools) p->trim();
 }
 
 }  // namespace mf

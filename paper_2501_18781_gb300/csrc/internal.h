@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <map>
 #include <string>
 #include <vector>
 
@@ -27,6 +28,9 @@ mf_status fail(mf_status st, const std::string& msg);
     if (s_ != MF_OK) return s_;      \
   } while (0)
 
+// frees the blocks that every context keeps for reuse (after a failed cudaMalloc)
+void trim_block_pools();
+
 // Device buffer owned by a handle.
 struct DevBuf {
   void* p = nullptr;
@@ -40,13 +44,20 @@ struct DevBuf {
     p = nullptr;
     bytes = 0;
   }
+  // a buffer that already has n bytes is kept (its user rewrites it; work queued on the stream
+  // before still reads the old contents first)
   mf_status alloc(size_t n) {
+    if (p && n == bytes) return MF_OK;
     release();
     if (n == 0) return MF_OK;
     if (cudaMalloc(&p, n) != cudaSuccess) {
       cudaGetLastError();
-      p = nullptr;
-      return fail(MF_ENOMEM, "cudaMalloc of " + std::to_string(n) + " bytes failed");
+      trim_block_pools();
+      if (cudaMalloc(&p, n) != cudaSuccess) {
+        cudaGetLastError();
+        p = nullptr;
+        return fail(MF_ENOMEM, "cudaMalloc of " + std::to_string(n) + " bytes failed");
+      }
     }
     bytes = n;
     return MF_OK;
@@ -57,6 +68,35 @@ struct DevBuf {
     if (!v.empty()) MF_CUDA_TRY(cudaMemcpyAsync(p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, s));
     return MF_OK;
   }
+};
+
+// Device blocks a context keeps for reuse (the solvers' work vectors, allocated and freed on every
+// solve).  A block handed back may still be read by work queued on the context's stream; every
+// later user queues its work on the same stream, so the reuse needs no synchronisation.  Sizes
+// are rounded up (to 512 bytes, or to 2 MiB from 1 MiB on) and matched exactly; when cudaMalloc
+// fails, the kept blocks of every context are freed and the allocation is retried.
+struct BlockPool {
+  std::multimap<size_t, void*> keep;
+  size_t kept = 0;
+  BlockPool();
+  ~BlockPool();
+  BlockPool(const BlockPool&) = delete;
+  BlockPool& operator=(const BlockPool&) = delete;
+  static size_t rounded(size_t n) {
+    const size_t big = size_t(2) << 20, small = 512;
+    return n >= (size_t(1) << 20) ? (n + big - 1) / big * big : (n + small - 1) / small * small;
+  }
+  mf_status get(size_t n, void** out);
+  void put(void* blk, size_t n);
+  void trim();
+};
+
+// the pool of the context whose solve runs on this thread (set by a PoolScope), or NULL
+extern thread_local BlockPool* tl_pool;
+struct PoolScope {
+  BlockPool* prev;
+  explicit PoolScope(BlockPool* p) : prev(tl_pool) { tl_pool = p; }
+  ~PoolScope() { tl_pool = prev; }
 };
 
 }  // namespace mf
@@ -88,6 +128,7 @@ struct mf_ctx {
   // captured), fenced against `stream` with an event on both sides.
   cudaStream_t capture_stream = nullptr;
   cudaEvent_t fence = nullptr;
+  mf::BlockPool pool;   // work vectors of the solvers, reused in this stream's order
 };
 
 struct mf_mesh {

@@ -43,12 +43,37 @@ namespace {
 
 using clk = std::chrono::steady_clock;
 
+// Work vector of a solver: inside a solve its memory comes from the context's block pool and goes
+// back there when the vector dies; elsewhere it is a plain device buffer.
 template <typename T> struct Vec {
   DevBuf b;
+  BlockPool* pool = nullptr;
+  void* blk = nullptr;
+  size_t nb = 0;
   T* p = nullptr;
+  Vec() = default;
+  Vec(const Vec&) = delete;
+  Vec& operator=(const Vec&) = delete;
+  ~Vec() { drop(); }
+  void drop() {
+    if (blk) pool->put(blk, nb);
+    blk = nullptr;
+    pool = nullptr;
+    b.release();
+    p = nullptr;
+  }
   mf_status alloc(int64_t n) {
-    MF_TRY(b.alloc(sizeof(T) * size_t(n)));
-    p = b.as<T>();
+    drop();
+    const size_t bytes = sizeof(T) * size_t(n);
+    if (tl_pool && bytes > 0) {
+      MF_TRY(tl_pool->get(bytes, &blk));
+      pool = tl_pool;
+      nb = bytes;
+      p = static_cast<T*>(blk);
+    } else {
+      MF_TRY(b.alloc(bytes));
+      p = b.as<T>();
+    }
     return MF_OK;
   }
 };
@@ -750,6 +775,7 @@ mf_status solve_impl(mf_op* op, const mf_solver_params* sp, const double* b, dou
   mf_ctx* c = op->ctx;
   const int64_t n = op->n;
   MF_TRY(check_fields(op));
+  PoolScope pool_scope(&c->pool);  // the work vectors below come from (and go back to) the context's pool
   // fp64 applies of this solve run on the fp64 pipes or in double-float
   struct Restore {
     mf_op* op;
