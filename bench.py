@@ -1169,6 +1169,11 @@ def main():
                          "peak_source": "MEASURED_PEAKS.json (of measured)" if "hbm_gbs" in peaks else "fallback"},
         "e2e": e2e, "gpu_launches": launches, "clocks": clocks.summary(),
     }
+    if arith == "df64":
+        # the pair arithmetic is mostly additions, which fill an fp32-pipe issue slot for one flop:
+        # the same work as a fraction of the pipe's instruction rate (one per lane per clock)
+        out["roofline"]["issue_frac"] = HEAT_DF64_INSTRUCTIONS_PER_CELL * ncells / mean / 1e12 / (FP32_PEAK_TFLOPS / 2)
+        out["roofline"]["fp32_instructions_per_launch"] = HEAT_DF64_INSTRUCTIONS_PER_CELL * ncells
     # the same operator in fp32 (the arithmetic of the mixed solver's inner applies) and in
     # double-float, with their HBM fractions
     src32, dst32 = src.float(), torch.empty(n, dtype=torch.float32, device="cuda")
