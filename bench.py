@@ -541,9 +541,20 @@ def heat_adjoint_workload(ctx, flush):
     Jd, gd, _, _, _ = op.heat_step_gradient(lzt, tp, tt, p["box_half"], p["box_depth"], **kwd)
     torch.cuda.synchronize()
     secd = time.perf_counter() - t0
+    # mixed precision: defect correction with fp32 inner GMRES on the operator and on its
+    # transpose, the outer residuals in double-float
+    kwm = dict(solver="defect_correction", precond="jacobi", tol=1e-10, restart=30, maxit=50, fp64_arith="df64")
+    op.heat_step_gradient(lzt, tp, tt, p["box_half"], p["box_depth"], **kwm)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    Jm, gm, _, _, _ = op.heat_step_gradient(lzt, tp, tt, p["box_half"], p["box_depth"], **kwm)
+    torch.cuda.synchronize()
+    secm = time.perf_counter() - t0
     return {"workload": wl.name, "n_dofs": m.n_dofs, "gradient_seconds": sec,
-            "gradient_seconds_df64_applies": secd, "J": J, "dJ_dlaser": g,
+            "gradient_seconds_df64_applies": secd, "gradient_seconds_mixed": secm, "J": J, "dJ_dlaser": g,
             "J_rel_diff_df64_applies": abs(Jd - J) / abs(J) if J else 0.0,
+            "J_rel_diff_mixed": abs(Jm - J) / abs(J) if J else 0.0,
+            "dJ_dlaser_max_rel_diff_mixed": max(abs(a - b) for a, b in zip(gm, g)) / max(abs(v) for v in g),
             "apply": _apply_rates(op, m.n_dofs, 1, flush)}
 
 

@@ -258,12 +258,15 @@ typedef enum {
 
 typedef struct {
   int solver;          /* mf_solver_kind */
-  int precond;         /* mf_prec_kind (defect correction: preconditioner of the inner CG) */
-  int inner_dtype;     /* defect correction: precision of the inner solve (MF_F32) */
-  int restart;         /* GMRES restart length */
+  int precond;         /* mf_prec_kind (defect correction: preconditioner of the inner solve) */
+  int inner_dtype;     /* defect correction: precision of the inner solve (MF_F32): CG on the
+                          symmetric operators, GMRES(restart, default 30) with MF_PREC_JACOBI or
+                          MF_PREC_NONE on the convective heat operator and its transpose; the
+                          outer residuals b - A x in the fp64 arithmetic fp64_arith selects */
+  int restart;         /* GMRES restart length (<= 63) */
   int cheby_degree;    /* operator applications per Chebyshev preconditioner call */
   int maxit;           /* iteration cap (outer steps for defect correction) */
-  int inner_maxit;     /* defect correction: inner CG cap */
+  int inner_maxit;     /* defect correction: inner iteration cap per step (<= 0: 100) */
   int use_graph;       /* replay recorded CUDA graphs: CG steps with the stopping test on the
                           device, eight per replay when n * nrhs <= 2^20 and one otherwise (a
                           system that has stopped is left untouched by the remaining steps; the
@@ -421,10 +424,10 @@ int64_t mf_context_launch_count(const mf_ctx* ctx);
  * faces keep T^n.  With x* = 2 x^n - x^(n-1) (step 1):
  *  2. u_G = u*_h + mdot(T*_h) / rho(phi*_h) n_G(phi*_h) at the Gauss points (variant 1, eq.
  *     transport_vel_local_continuous); (M/dt + C(u_G)) phi_a = M phi^n / dt (eq. transport, backward
- *     Euler, GMRES); reinit_steps pseudo-time steps (M/dtau + eps N_n) psi' = M psi / dtau + F(psi),
+ *     Euler, defect correction: fp32 inner GMRES); reinit_steps pseudo-time steps (M/dtau + eps N_n) psi' = M psi / dtau + F(psi),
  *     F_i = int (1 - psi_h^2)/2 n . grad N_i, n the unit normal of phi_a (Olsson's conservative
  *     reinitialisation for phi in [-1, 1], CG), phi^(n+1) = the last psi;
- *  3. heat (eq. heat_transfer, GMRES): (M_{rho_cp/dt} + K_k + C_{rho_cp}(u*)) T^(n+1) =
+ *  3. heat (eq. heat_transfer, defect correction: fp32 inner GMRES): (M_{rho_cp/dt} + K_k + C_{rho_cp}(u*)) T^(n+1) =
  *     M_{rho_cp/dt} T^n + s with rho_cp, k of phi^(n+1) (eq. muEff) and s = evaporative cooling
  *     (mdot of T*, eq. vapor_heat_loss) + laser (eq. laser_gauss with <n_G . e_L>, n_G pointing into
  *     the dense phase, e_L the beam direction); solved for T^(n+1) - T^n;
@@ -432,7 +435,8 @@ int64_t mf_context_launch_count(const mf_ctx* ctx);
  *     Oseen operator about u* with sigma = 1/dt, phi^(n+1), T^(n+1), velocity load sigma M_rho u^n
  *     + rho g + surface tension (eq. surface_tension, kappa = -div n_G from the Hessian of phi_h) +
  *     hybrid recoil force, pressure rows -int q sdot (eq. evaporDil).
- * The tanh Heaviside throughout (mf_op_params heaviside 0).  Every value in fp64. */
+ * The tanh Heaviside throughout (mf_op_params heaviside 0).  Every value in fp64; the residuals
+ * that decide each solve's tolerance are evaluated fp64-accurately (double-float applies). */
 typedef struct mf_meltpool_step mf_meltpool_step;
 
 typedef struct {

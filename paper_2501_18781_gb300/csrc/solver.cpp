@@ -660,10 +660,10 @@ template <typename T> struct CG {
 
 // true residual ||b - A x|| / ||b|| per RHS in fp64 (r receives b - A x)
 mf_status true_residual(mf_op* op, const double* b, const double* x, double* r, int nrhs, std::vector<double>& rel,
-                        std::vector<double>* rnorm = nullptr) {
+                        std::vector<double>* rnorm = nullptr, bool transpose = false) {
   mf_ctx* c = op->ctx;
   const int64_t n = op->n;
-  MF_TRY(apply_impl<double>(op, x, r, nrhs, n, false));
+  MF_TRY(apply_impl<double>(op, x, r, nrhs, n, transpose));
   rel.assign(nrhs, 0.0);
   if (rnorm) rnorm->assign(nrhs, 0.0);
   double* ds = c->scalars.as<double>() + kScalarsResid;
@@ -681,17 +681,23 @@ mf_status true_residual(mf_op* op, const double* b, const double* x, double* r, 
   return MF_OK;
 }
 
+// |x|^2 into device out (fp64 sum)
+inline mf_status nrm2sq(mf_ctx* c, const double* x, int64_t n, double* out) { return norm2_sq(c, x, n, out); }
+inline mf_status nrm2sq(mf_ctx* c, const float* x, int64_t n, double* out) { return dot<float, float>(c, x, x, n, out); }
+
 // Restarted GMRES(m), right preconditioning, classical Gram-Schmidt with one
-// reorthogonalisation (CGS2), Givens rotations on the host.  fp64, one RHS.
-mf_status gmres(mf_op* op, Prec<double>& P, const double* b, double* x, int m, double tol, int maxit, bool transpose,
-                int* iters, double* relres) {
+// reorthogonalisation (CGS2), Givens rotations on the host.  One RHS; T = double (the solver),
+// or float (the inner solve of defect correction on a nonsymmetric operator).
+template <typename T>
+mf_status gmres(mf_op* op, Prec<T>& P, const T* b, T* x, int m, double tol, int maxit, bool transpose, int* iters,
+                double* relres) {
   mf_ctx* c = op->ctx;
   const int64_t n = op->n;
   // a preconditioner that changes from call to call (inner Krylov solves) needs the flexible
   // variant (FGMRES): keep Z_j = P^-1 V_j and update x with Z y
   const bool flexible = P.kind == MF_PREC_BLOCK_TRIANGULAR;
   if (flexible && transpose) return fail(MF_EUNSUPPORTED, "block-triangular preconditioner: forward operator only");
-  Vec<double> V, t, r, Z;
+  Vec<T> V, t, r, Z;
   const int64_t ldv = basis_stride(n);
   MF_TRY(V.alloc(ldv * (m + 1)));
   MF_TRY(t.alloc(n));
@@ -700,8 +706,8 @@ mf_status gmres(mf_op* op, Prec<double>& P, const double* b, double* x, int m, d
   double* dh = c->scalars.as<double>() + kScalarsGmres;  // room for 2 (m+1) <= 128 values
   if (2 * (m + 1) > 128) return fail(MF_EINVAL, "GMRES restart too long (max 63)");
   double* hh = c->host_scalars + kScalarsGmres;
-  MF_CUDA_TRY(cudaMemsetAsync(x, 0, sizeof(double) * n, c->stream));
-  MF_TRY(norm2_sq(c, b, n, dh));
+  MF_CUDA_TRY(cudaMemsetAsync(x, 0, sizeof(T) * n, c->stream));
+  MF_TRY(nrm2sq(c, b, n, dh));
   MF_TRY(sync_copy(c, hh, dh, 1));
   const double bn = std::sqrt(hh[0]);
   *iters = 0;
@@ -709,21 +715,21 @@ mf_status gmres(mf_op* op, Prec<double>& P, const double* b, double* x, int m, d
     *relres = 0.0;
     return MF_OK;
   }
-  MF_CUDA_TRY(cudaMemcpyAsync(r.p, b, sizeof(double) * n, cudaMemcpyDeviceToDevice, c->stream));
+  MF_CUDA_TRY(cudaMemcpyAsync(r.p, b, sizeof(T) * n, cudaMemcpyDeviceToDevice, c->stream));
   double beta = bn;
   int it = 0;
   std::vector<double> H((m + 1) * m), cs(m), sn(m), g(m + 1), y(m);
   while (it < maxit) {
-    MF_TRY(axpby<double, double>(c, n, 1.0 / beta, r.p, 0.0, V.p));
+    MF_TRY((axpby<T, T>(c, n, 1.0 / beta, r.p, 0.0, V.p)));
     std::fill(g.begin(), g.end(), 0.0);
     g[0] = beta;
     int j = 0;
     bool conv = false;
     for (; j < m && it < maxit; ++j) {
-      double* w = V.p + (j + 1) * ldv;
-      double* zj = flexible ? Z.p + j * ldv : t.p;
+      T* w = V.p + (j + 1) * ldv;
+      T* zj = flexible ? Z.p + j * ldv : t.p;
       MF_TRY(P.apply(V.p + j * ldv, zj));
-      MF_TRY(apply_impl<double>(op, zj, w, 1, n, transpose));
+      MF_TRY(apply_impl<T>(op, zj, w, 1, n, transpose));
       MF_TRY(multidot(c, V.p, ldv, j + 1, w, n, dh));
       MF_TRY(axpy_multidot(c, V.p, ldv, j + 1, dh, -1.0, w, n, dh + (m + 1)));
       MF_TRY(multiaxpy(c, V.p, ldv, j + 1, dh + (m + 1), -1.0, w, n, dh + 2 * (m + 1) - 1));  // and |w|^2
@@ -731,7 +737,7 @@ mf_status gmres(mf_op* op, Prec<double>& P, const double* b, double* x, int m, d
       for (int i = 0; i <= j; ++i) H[i * m + j] = hh[i] + hh[(m + 1) + i];
       double hn = std::sqrt(hh[2 * (m + 1) - 1]);
       H[(j + 1) * m + j] = hn;
-      if (hn > 0) MF_TRY(axpby<double, double>(c, n, 1.0 / hn, w, 0.0, w));
+      if (hn > 0) MF_TRY((axpby<T, T>(c, n, 1.0 / hn, w, 0.0, w)));
       givens_column(H, m, j, cs, sn, g);
       ++it;
       if (std::fabs(g[j + 1]) <= tol * bn || hn == 0.0) {
@@ -747,15 +753,15 @@ mf_status gmres(mf_op* op, Prec<double>& P, const double* b, double* x, int m, d
     if (flexible) {
       MF_TRY(multiaxpy(c, Z.p, ldv, j, dh, 1.0, x, n));
     } else {
-      MF_CUDA_TRY(cudaMemsetAsync(r.p, 0, sizeof(double) * n, c->stream));
+      MF_CUDA_TRY(cudaMemsetAsync(r.p, 0, sizeof(T) * n, c->stream));
       MF_TRY(multiaxpy(c, V.p, ldv, j, dh, 1.0, r.p, n));
       MF_TRY(P.apply(r.p, t.p));
-      MF_TRY(axpby<double, double>(c, n, 1.0, t.p, 1.0, x));
+      MF_TRY((axpby<T, T>(c, n, 1.0, t.p, 1.0, x)));
     }
     // true residual
-    MF_TRY(apply_impl<double>(op, x, r.p, 1, n, transpose));
-    MF_TRY(axpby<double, double>(c, n, 1.0, b, -1.0, r.p));
-    MF_TRY(norm2_sq(c, r.p, n, dh));
+    MF_TRY(apply_impl<T>(op, x, r.p, 1, n, transpose));
+    MF_TRY((axpby<T, T>(c, n, 1.0, b, -1.0, r.p)));
+    MF_TRY(nrm2sq(c, r.p, n, dh));
     MF_TRY(sync_copy(c, hh, dh, 1));
     beta = std::sqrt(hh[0]);
     *relres = beta / bn;
@@ -865,14 +871,23 @@ mf_status solve_impl(mf_op* op, const mf_solver_params* sp, const double* b, dou
     }
   } else if (sp->solver == MF_SOLVER_DEFECT_CORRECTION) {
     if (sp->inner_dtype != MF_F32) return fail(MF_EUNSUPPORTED, "inner precision must be MF_F32");
-    if (op->p.kind == MF_OP_OSEEN) return fail(MF_EUNSUPPORTED, "defect correction uses CG: symmetric operators");
+    if (op->p.kind == MF_OP_OSEEN) return fail(MF_EUNSUPPORTED, "defect correction: scalar operators");
+    // inner fp32 solve: CG on the symmetric operators, GMRES on the convective heat operator (and
+    // its transpose)
+    const bool nonsym = heat_convection(op);
+    if (nonsym && sp->precond == MF_PREC_CHEBYSHEV)
+      return fail(MF_EINVAL, "Chebyshev needs a symmetric operator (the convective inner GMRES takes Jacobi)");
+    const bool tr = nonsym && transpose;
+    const int m = sp->restart > 0 ? sp->restart : 30;
     Prec<float> P;
-    MF_TRY(P.setup(op, sp->precond, deg, ratio, lsteps, nrhs));
+    MF_TRY(P.setup(op, sp->precond, deg, ratio, lsteps, nonsym ? 1 : nrhs));
     inf.lambda_max = P.lmax;
     CG<float> cg;
-    MF_TRY(cg.setup(op, &P, nrhs));
-    cg.use_graph = sp->use_graph != 0;
-    cg.check_every = 1;
+    if (!nonsym) {
+      MF_TRY(cg.setup(op, &P, nrhs));
+      cg.use_graph = sp->use_graph != 0;
+      cg.check_every = 1;
+    }
     Vec<double> r;
     Vec<float> r32, d32;
     MF_TRY(r.alloc(n * nrhs));
@@ -884,7 +899,7 @@ mf_status solve_impl(mf_op* op, const mf_solver_params* sp, const double* b, dou
     std::vector<double> rn(nrhs), bnorm(nrhs);
     {
       std::vector<double> rl;
-      MF_TRY(true_residual(op, b, x, r.p, nrhs, rl, &bnorm));  // x = 0: r = b
+      MF_TRY(true_residual(op, b, x, r.p, nrhs, rl, &bnorm, tr));  // x = 0: r = b
     }
     const double itol = sp->inner_tol > 0 ? sp->inner_tol : 1e-4;
     const int imax = sp->inner_maxit > 0 ? sp->inner_maxit : 100;
@@ -899,15 +914,25 @@ mf_status solve_impl(mf_op* op, const mf_solver_params* sp, const double* b, dou
       MF_CUDA_TRY(cudaMemcpyAsync(dscale, sc.data(), sizeof(double) * nrhs, cudaMemcpyHostToDevice, c->stream));
       MF_TRY(dev_scale_rhs(c, r.p, r32.p, dscale, n, nrhs));
       int its = 0;
-      std::vector<double> irel;
-      mf_status si = cg.solve(r32.p, d32.p, itol, imax, &its, irel);
-      if (si != MF_OK && si != MF_ENOTCONV) return si;
+      if (nonsym) {
+        for (int k = 0; k < nrhs; ++k) {
+          int ik = 0;
+          double rr = 0;
+          const mf_status si = gmres<float>(op, P, r32.p + k * n, d32.p + k * n, m, itol, imax, tr, &ik, &rr);
+          if (si != MF_OK && si != MF_ENOTCONV) return si;
+          its += ik;
+        }
+      } else {
+        std::vector<double> irel;
+        const mf_status si = cg.solve(r32.p, d32.p, itol, imax, &its, irel);
+        if (si != MF_OK && si != MF_ENOTCONV) return si;
+      }
       inf.iterations += its;
       for (int k = 0; k < nrhs; ++k) sc[k] = rn[k];
       MF_CUDA_TRY(cudaMemcpyAsync(dscale, sc.data(), sizeof(double) * nrhs, cudaMemcpyHostToDevice, c->stream));
       MF_TRY(dev_add_scaled(c, d32.p, x, dscale, n, nrhs));
       ++outer;
-      MF_TRY(true_residual(op, b, x, r.p, nrhs, rel));
+      MF_TRY(true_residual(op, b, x, r.p, nrhs, rel, nullptr, tr));
       for (double v : rel)
         if (!std::isfinite(v)) {
           inf.outer_iterations = outer;

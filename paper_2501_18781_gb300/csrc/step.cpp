@@ -250,8 +250,10 @@ mf_status mf_meltpool_advance(mf_meltpool_step* step, const double* u_prev, cons
       MF_TRY(copy_out(c, trace->u_gamma, S.ug.as<double>(), 81 * S.nc));
       MF_TRY(copy_out(c, trace->b_advection, b, nu));
     }
-    mf_solver_params as = scalar_solver(MF_SOLVER_GMRES, p.tol, maxit);
-    as.fp64_arith = 1;   // the applies in double-float (fp64-accurate, on the fp32 pipes)
+    // defect correction: fp32 inner GMRES, the outer residuals with double-float applies
+    mf_solver_params as = scalar_solver(MF_SOLVER_DEFECT_CORRECTION, p.tol, maxit);
+    as.inner_dtype = MF_F32;
+    as.fp64_arith = 1;
     MF_TRY(run_solve(S.adv, as, b, phia, &inf.advection_iterations, &inf.advection_residual, &worst));
     if (trace) MF_TRY(copy_out(c, trace->phi_advected, phia, nu));
     MF_TRY(lap(0, t));
@@ -295,8 +297,9 @@ mf_status mf_meltpool_advance(mf_meltpool_step* step, const double* u_prev, cons
     MF_TRY(mf::axpby<double, double>(c, nu, 1.0, b, -1.0, r));
     MF_TRY(mf::launch_dirichlet_copy(c, S.mT, S.zero.p, r, 1, nu, 0, false));
     if (trace) MF_TRY(copy_out(c, trace->r_heat, r, nu));
-    mf_solver_params hs = scalar_solver(MF_SOLVER_GMRES, p.tol, maxit);
-    hs.fp64_arith = 1;   // double-float applies with the per-Gauss-point rho_cp
+    mf_solver_params hs = scalar_solver(MF_SOLVER_DEFECT_CORRECTION, p.tol, maxit);  // as the advection
+    hs.inner_dtype = MF_F32;
+    hs.fp64_arith = 1;
     MF_TRY(run_solve(S.heat, hs, r, S.d.as<double>(), &inf.heat_iterations, &inf.heat_residual, &worst));
     if (trace) MF_TRY(copy_out(c, trace->T_update, S.d.as<double>(), nu));
     MF_CUDA_TRY(cudaMemcpyAsync(T_out, T, sizeof(double) * nu, cudaMemcpyDeviceToDevice, c->stream));

@@ -178,7 +178,10 @@ def _gradient_case(ctx, n=4):
     return P, laser, th_prev, target
 
 
-def test_heat_adjoint_gradient_matches_oracle(ctx):
+@pytest.mark.parametrize("solver", ["gmres", "defect_correction"])
+def test_heat_adjoint_gradient_matches_oracle(ctx, solver):
+    """defect_correction: fp32 inner GMRES on the convective operator and on its transpose (the
+    adjoint solve), outer residuals in double-float."""
     from oracle import heat as oheat
     P, laser, th_prev, target = _gradient_case(ctx)
     p = P["wl"].params
@@ -186,9 +189,10 @@ def test_heat_adjoint_gradient_matches_oracle(ctx):
     cells = oheat.box_cells(P["dm"], 200e-6, 200e-6)
     J, gl, gk, th, lam = oheat.gradients(st, th_prev, target, laser, cells)
     lz = (laser["power"], laser["radius"], laser["x0"], laser["y0"], laser["absorptivity"])
+    kw = dict(solver="gmres", precond="jacobi", tol=1e-13, restart=50) if solver == "gmres" else \
+        dict(solver="defect_correction", precond="jacobi", tol=1e-12, restart=30, maxit=20, fp64_arith="df64")
     Jg, glg, gkg, thg, lamg = P["op"].heat_step_gradient(lz, torch.tensor(th_prev, device="cuda"),
-                                                         torch.tensor(target, device="cuda"), 200e-6, 200e-6,
-                                                         solver="gmres", precond="jacobi", tol=1e-13, restart=50)
+                                                         torch.tensor(target, device="cuda"), 200e-6, 200e-6, **kw)
     assert abs(Jg - J) <= 1e-9 * abs(J)
     assert np.allclose(glg, gl, rtol=1e-8, atol=1e-10 * np.abs(gl).max())
     gkg = gkg.cpu().numpy().reshape(gk.shape)

@@ -69,6 +69,34 @@ def test_heat_operator_with_gauss_point_rho_cp_and_velocity(ctx):
         op.apply(_cuda(u).float(), arith="bf16")
 
 
+@pytest.mark.parametrize("arith", ["f64", "df64"])
+def test_defect_correction_on_the_convective_heat_operator(ctx, arith):
+    """Mixed-precision defect correction on the nonsymmetric heat operator of the melt-pool step
+    (rho_cp, k and the velocity per Gauss point): fp32 inner GMRES, outer residuals in fp64 or
+    double-float; the true residual from the oracle's assembled matrix meets the tolerance."""
+    from paper_2501_18781_gb300 import DofMap, Mesh, Operator
+    n, dt = 6, 1e-3
+    dm = omesh.uniform_dofmap(n, (0, 0, 0), (1, 1, 1), 2, T_FACES)
+    nq = dm.n_cells * 27
+    rc = 1.0 + 3.0 * syn.uniform_01(13, nq).reshape(dm.n_cells, 27)
+    kq = syn.kq_field(nq, 14, 2.0).reshape(dm.n_cells, 27)
+    bq = 20.0 * syn.uniform_pm1(15, 3 * nq).reshape(dm.n_cells, 27, 3)
+    A = asm.assemble_scalar(dm, rc / dt, diff=kq, conv=rc[..., None] * bq)
+    op = Operator(ctx, "heat", [DofMap(Mesh.uniform(ctx, n), 2, T_FACES)], rhocp=7.0, dt=dt, coef_mode=1)
+    keep = [_cuda(kq.ravel()), _cuda(rc.ravel()), _cuda(bq.ravel())]
+    for name, t in zip(("k_qpoint", "rhocp_qpoint", "beta_qpoint"), keep):
+        op.set_field(name, t)
+    b = syn.uniform_pm1(16, dm.n_dofs)
+    b[dm.dirichlet] = 0.0
+    x, info = op.solve(_cuda(b), solver="defect_correction", precond="jacobi", tol=1e-10, restart=30, maxit=20,
+                       fp64_arith=arith)
+    assert info["status"] == 0 and info["outer_iterations"] >= 2, info
+    r = b - A @ x.cpu().numpy()
+    assert np.linalg.norm(r) <= (1e-10 + 1e-13) * np.linalg.norm(b), (np.linalg.norm(r) / np.linalg.norm(b), info)
+    with pytest.raises(Exception):
+        op.solve(_cuda(b), solver="defect_correction", precond="chebyshev", tol=1e-10)
+
+
 def _workload(n, **over):
     wl = syn.scaled(syn.MELTPOOL_STEP, n)
     p = dict(wl.params)
@@ -204,10 +232,13 @@ def test_meltpool_step_hydrostatics(ctx):
     discrete solution is u = 0, p = rho |g| (z_top - z) exactly, and T, phi do not move.
 
     The bars on u and p are derived, not fitted: the oracle checks that the hydrostatic state x*
-    solves its assembled flow system K x* = b to rounding, and that the GPU's solution x has a true
-    residual r = b - K x with |r| <= tol |b| (tol = 1e-12, the flow solve's tolerance).  Then
-    x - x* = -K^-1 r, so |x_i - x*_i| <= |row i of K^-1|_2 tol |b|: the bound is formed from the dense
-    inverse of the 2312 x 2312 system.  (At the 0.01 us step sigma rho h^2 / mu = 2.6e6 makes K
+    solves its assembled flow system K0 x* = b0 (phi = 1, T = 800) to rounding.  The GPU's flow
+    stage sees the phi and T its own level-set and heat solves returned (equal to 1 and 800 up to
+    those solves' tolerance), so the oracle assembles that system, K x = b - r, from the GPU's
+    outputs, and checks the true residual |r| <= tol |b| (tol = 1e-12, the flow solve's tolerance).
+    Then x - x* = K^-1 (b - K x* - r), so |x_i - x*_i| <= |row i of K^-1|_2 (|b - K x*| + tol |b|):
+    the bound is formed from the dense inverse of the 2312 x 2312 system (|b - K x*| vanishes
+    when phi and T came back exact).  (At the 0.01 us step sigma rho h^2 / mu = 2.6e6 makes K
     mass-dominated and its pressure Schur complement a scaled Laplacian; the bound comes to about
     5e-4 rho |g| L for p and 1.2e-3 |g| dt for u.)"""
     wl, prm = _workload(4, laser=None, solid=None, darcy=None, trace_correction=False, reinit_steps=0)
@@ -221,13 +252,16 @@ def test_meltpool_step_hydrostatics(ctx):
     out, info = step.advance({k: _cuda(v.ravel()) for k, v in s.items()})
     assert info["status"] == 0, info
     zp = maps[1].dof_coords()[:, 2]
-    A_ns, b_ns = ost.flow_system(maps, s["u"], s["u"], s["phi"], s["T"], prm)
+    A0, b0 = ost.flow_system(maps, s["u"], s["u"], s["phi"], s["T"], prm)
     xs = np.concatenate([np.zeros(3 * nu), TI["rho_l"] * 9.81 * (wl.hi[2] - zp)])
-    assert np.linalg.norm(b_ns - A_ns @ xs) <= 1e-13 * np.linalg.norm(b_ns)      # x* is the discrete solution
+    assert np.linalg.norm(b0 - A0 @ xs) <= 1e-13 * np.linalg.norm(b0)            # x* is the discrete solution
+    phi_g, T_g = out["phi"].cpu().numpy(), out["T"].cpu().numpy()
+    A_ns, b_ns = ost.flow_system(maps, s["u"], s["u"], phi_g, T_g, prm)         # the system the GPU solved
     x = np.concatenate([out["u"].cpu().numpy().ravel(), out["p"].cpu().numpy()])
     tol = 1e-12 * (1 + 1e-3)
     assert np.linalg.norm(b_ns - A_ns @ x) <= tol * np.linalg.norm(b_ns)          # the GPU's true residual
-    bound = np.linalg.norm(np.linalg.inv(A_ns.toarray()), axis=1) * tol * np.linalg.norm(b_ns)
+    rs = np.linalg.norm(b_ns - A_ns @ xs)
+    bound = np.linalg.norm(np.linalg.inv(A_ns.toarray()), axis=1) * (rs + tol * np.linalg.norm(b_ns))
     assert np.all(np.abs(x - xs) <= bound + 2.0 ** -52 * np.abs(xs)), np.max(np.abs(x - xs) / bound)
     assert np.array_equal(out["T"].cpu().numpy(), s["T"]) or np.abs(out["T"].cpu().numpy() - 800.0).max() <= 1e-9
     assert np.abs(out["phi"].cpu().numpy() - 1.0).max() <= 1e-12
