@@ -41,12 +41,15 @@ BlockPool::~BlockPool() {
 }
 mf_status BlockPool::get(size_t n, void** out) {
   const size_t r = rounded(n);
-  auto it = keep.find(r);
-  if (it != keep.end()) {
-    *out = it->second;
-    keep.erase(it);
-    kept -= r;
-    return MF_OK;
+  {
+    std::lock_guard<std::mutex> lk(mu);
+    auto it = keep.find(r);
+    if (it != keep.end()) {
+      *out = it->second;
+      keep.erase(it);
+      kept -= r;
+      return MF_OK;
+    }
   }
   if (cudaMalloc(out, r) != cudaSuccess) {
     cudaGetLastError();
@@ -61,10 +64,13 @@ mf_status BlockPool::get(size_t n, void** out) {
 }
 void BlockPool::put(void* blk, size_t n) {
   const size_t r = rounded(n);
+  std::lock_guard<std::mutex> lk(mu);
   keep.emplace(r, blk);
   kept += r;
 }
+// cudaFree waits for the device, so work still queued on a block finishes before it is freed
 void BlockPool::trim() {
+  std::lock_guard<std::mutex> lk(mu);
   for (auto& kv : keep) cudaFree(kv.second);
   keep.clear();
   kept = 0;

@@ -5,6 +5,7 @@
 #include <stdint.h>
 
 #include <map>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -76,6 +77,7 @@ struct DevBuf {
 // are rounded up (to 512 bytes, or to 2 MiB from 1 MiB on) and matched exactly; when cudaMalloc
 // fails, the kept blocks of every context are freed and the allocation is retried.
 struct BlockPool {
+  std::mutex mu;  // guards keep (trim_block_pools may run on another thread)
   std::multimap<size_t, void*> keep;
   size_t kept = 0;
   BlockPool();

@@ -152,6 +152,29 @@ def test_defect_correction_mixed_precision_heat(ctx):
     assert info["outer_iterations"] >= 2
 
 
+def test_repeated_solves_on_pooled_work_vectors(ctx):
+    """The solvers' work vectors come from the context's block pool, so a repeated solve runs on the
+    blocks the previous one left, with its values still in them: a solver that read a work vector
+    before writing it would start from those.  Each repeat must meet the tolerance on the oracle's
+    true residual in the same number of iterations (one more or fewer allowed: the atomic scatter
+    of the applies sums in a run-dependent order) and agree with the first to the solve's accuracy."""
+    for P, kw in ((helmholtz(6, ctx), dict(solver="cg", precond="chebyshev", use_graph=True)),
+                  (heat(5, ctx, with_beta=True, kq=True), dict(solver="gmres", precond="jacobi", restart=20)),
+                  (heat(5, ctx, with_beta=True, kq=True), dict(solver="defect_correction", precond="jacobi",
+                                                               fp64_arith="df64"))):
+        b = syn.uniform_pm1(21, P["n"])
+        b[P["dm"].dirichlet] = 0.0
+        xs = []
+        for _ in range(3):
+            x, info = P["op"].solve(torch.tensor(b, device="cuda"), tol=1e-10, **kw)
+            assert info["status"] == 0, (kw, info)
+            xs.append((x.cpu().numpy(), info["iterations"]))
+        for x, it in xs:
+            assert abs(it - xs[0][1]) <= 1, kw
+            assert true_residual(P["A"], b, x) <= 1e-10 * (1 + 1e-3), kw
+            assert np.abs(x - xs[0][0]).max() <= 1e-7 * np.abs(xs[0][0]).max(), kw
+
+
 def test_defect_correction_batched_reinit_octree(ctx):
     P = reinit(band_octree(), ctx)
     b = np.stack([syn.uniform_pm1(s, P["n"]) for s in range(1, 5)])
