@@ -62,6 +62,15 @@ template <typename T> struct Vec {
     b.release();
     p = nullptr;
   }
+  // exchange two vectors' memory (pooled or not) and ownership
+  void swap_with(Vec& o) {
+    std::swap(b.p, o.b.p);
+    std::swap(b.bytes, o.b.bytes);
+    std::swap(pool, o.pool);
+    std::swap(blk, o.blk);
+    std::swap(nb, o.nb);
+    std::swap(p, o.p);
+  }
   mf_status alloc(int64_t n) {
     drop();
     const size_t bytes = sizeof(T) * size_t(n);
@@ -434,8 +443,7 @@ template <typename T> struct Prec {
       beta = std::sqrt(hs[0]);
       if (beta == 0.0 || !std::isfinite(beta)) break;
       be.push_back(beta);
-      std::swap(vp.p, v.p);
-      std::swap(vp.b.p, v.b.p);
+      vp.swap_with(v);
       MF_TRY(axpby<double, double>(c, n, 1.0 / beta, w.p, 0.0, v.p));
     }
     if (al.empty()) return fail(MF_EINVAL, "Lanczos failed");
