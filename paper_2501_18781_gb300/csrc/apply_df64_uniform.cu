@@ -556,6 +556,23 @@ __global__ void __launch_bounds__(96, 4) k_oseen_df_uniform(DfOseenArgs A, Unifo
   const uint32_t dmask = active ? dirichlet_mask(ug, i, j, k) : 0u;
   const int64_t px = ug.nx + 1, pxy = px * (ug.ny + 1);
   const int64_t pbase = active ? i + px * (j + (ug.ny + 1) * int64_t(k)) : 0;
+  // L2 prefetch of the coefficient tables cv (read in the z pass), cm and cb (read in the plane loop)
+  // while the inputs load and the sweeps run: a brick row's 8 cells share one 32-byte sector per
+  // table row, so each lane fetches that sector for its brick row and every 24th of the 270 table
+  // rows (high and low parts: cv 54, cm 54, cb 162).  Fetching the normal table of the melt-pool
+  // terms as well measured slower (1.57 against 1.54 ms at 64^3).
+  if (j < ug.ny) {
+    const int64_t row_cell = int64_t(i - (lane & 7)) + int64_t(ug.nx) * (j + int64_t(ug.ny) * k);
+#pragma unroll 1
+    for (int r = w * 8 + (lane & 7); r < 270; r += 24) {
+      const float* t;
+      int rr;
+      if (r < 54) { rr = r; t = (rr & 1) ? A.cvl : A.cvh; }
+      else if (r < 108) { rr = r - 54; t = (rr & 1) ? A.cml : A.cmh; }
+      else { rr = r - 108; t = (rr & 1) ? A.cbl : A.cbh; }
+      asm volatile("prefetch.global.L2 [%0];" ::"l"(t + int64_t(rr >> 1) * A.ncells + row_cell));
+    }
+  }
   // raw inputs: this warp's velocity component and the cell's 8 pressures
   double X[27], Pn[8];
   int eu = 0, ep = 0;
