@@ -265,6 +265,17 @@ __global__ void __launch_bounds__(128) k_oseen_qouter(OseenArgs<typename Store<T
   const int64_t px = ug.nx + 1, pxy = px * (ug.ny + 1);
   const int64_t pbase = i + px * (j + (ug.ny + 1) * int64_t(k));
   const T h = T(ug.h), mh2 = -(h * h);
+  if constexpr (sizeof(T) == 4) {
+    // L2 prefetch of the Gauss-point coefficient rows cm, cv and cb while the inputs load: a brick
+    // row's 8 cells share one 32-byte sector per table row, so each lane fetches that sector for its
+    // brick row and every 8th of the 135 rows
+    const int64_t row_cell = cell - (threadIdx.x & 7);
+#pragma unroll 1
+    for (int r = threadIdx.x & 7; r < 135; r += 8) {
+      const St* t = r < 27 ? A.cm + r * nc : (r < 54 ? A.cv + (r - 27) * nc : A.cb + (r - 54) * nc);
+      asm volatile("prefetch.global.L2 [%0];" ::"l"(t + row_cell));
+    }
+  }
   T U0[27], U1[27], U2[27];
   gather_uniform<T>(A.src, base, ug.sx, ug.sy, dmask, U0);
   gather_uniform<T>(A.src + A.nu, base, ug.sx, ug.sy, dmask, U1);
