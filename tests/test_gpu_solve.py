@@ -1,4 +1,4 @@
-"""Krylov solves on the GPU, judged by the TRUE residual computed with the oracle's own
+"""Krylov solves on the GPU, checked on the TRUE residual computed with the oracle's own
 assembled matrix: ||b - A_oracle x_gpu|| <= tol ||b|| (1 + 1e-3); adjoint gradients against
 the oracle and against central finite differences of the GPU heat step."""
 import numpy as np
