@@ -227,8 +227,9 @@ mf_status mf_apply_tc(mf_op* op, const float* src, float* dst, int nrhs, int64_t
  *           read as 0), dst = a pressure vector;
  *   which = MF_COUPLING_SCHUR (2): dst = B D^-1 B^T src, pressure to pressure, with D the 3 x 3
  *           nodal blocks of A_uu (the Schur complement approximation that MF_PREC_BLOCK_TRIANGULAR
- *           inverts; its fp32 form is the preconditioner's own: S~ assembled as a 125-point
- *           stencil on the pressure grid from the 1D couplings of B and applied as such).  Needs the
+ *           inverts; its fp32 form is the preconditioner's own: D and its inverses built in
+ *           fp32 from the fp32 Gauss-point tables, S~ assembled as a 125-point stencil on the
+ *           pressure grid from the 1D couplings of B and applied as such).  Needs the
  *           operator's fields; allocates work vectors and returns after the result is written.
  * These are the blocks of A [0; p] and A [u; 0] that mf_apply computes together with A_uu.
  * Device vectors of dtype MF_F64 or MF_F32; dst is overwritten.  MF_EINVAL for other
